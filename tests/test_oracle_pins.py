@@ -1,0 +1,317 @@
+"""Pins of the CPU oracle to facts fixed outside it (no GPU).
+
+The paper (arXiv:1509.08267) gives definitions and two lemmas but no worked example, so the oracle
+is pinned to: published SplitMix64 outputs (the priority hash); closed forms derived by hand from
+First Fit (Section 3) and Algorithm 1 (Section 3.1) on complete graphs, stars, complete bipartite
+graphs, single edges, cycles, grids, the 27-point stencil and crown graphs; the characterisation
+of First Fit; proper coloring (Lemma 1) and the Delta+1 bound (Section 2.1); termination and the
+round bound (Lemma 2 and its corollary); and brute-force chromatic numbers on tiny graphs.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------------------------
+# priority hash
+
+def test_splitmix64_published_outputs():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) if l[0] != "#"]
+    for idx, hexval in rows:
+        assert oracle.splitmix64(0, int(idx)) == int(hexval, 16)
+
+
+def test_splitmix64_is_the_stream():
+    # output i of the stream seeded s equals output 0 of the stream seeded s + i*GAMMA
+    gamma = 0x9E3779B97F4A7C15
+    for s in (0, 1, 7, 2**64 - 1):
+        for i in (0, 1, 5, 1000):
+            assert oracle.splitmix64(s, i) == oracle.splitmix64((s + i * gamma) % 2**64, 0)
+
+
+def test_key_order_is_total_and_matches_hash_then_id():
+    seed = 7
+    h = oracle.keys(seed, 64)
+    for u in range(64):
+        for v in range(64):
+            expect = (int(h[u]), u) < (int(h[v]), v)
+            assert oracle.key_less(seed, u, v) == expect
+
+
+# ---------------------------------------------------------------------------------------------
+# greedy First Fit (natural order)
+
+def test_greedy_complete():
+    for n in (1, 2, 7, 30):
+        c, k = oracle.greedy(gg.complete(n))
+        assert k == n
+        assert list(c) == list(range(n))
+
+
+def test_greedy_cycles_and_paths():
+    for n in (3, 5, 9, 101):
+        assert oracle.greedy(gg.cycle(n))[1] == 3  # odd cycle: 0,1,0,1,...,2
+    for n in (4, 6, 100):
+        c, k = oracle.greedy(gg.cycle(n))
+        assert k == 2 and list(c) == [i & 1 for i in range(n)]
+    c, k = oracle.greedy(gg.path(10))
+    assert list(c) == [i & 1 for i in range(10)]
+
+
+def test_greedy_grid_checkerboard():
+    Lx, Ly = 13, 7
+    c, k = oracle.greedy(gg.grid5(Lx, Ly))
+    assert k == 2
+    x, y = np.meshgrid(np.arange(Lx), np.arange(Ly))
+    assert np.array_equal(c, ((x + y) & 1).ravel())
+
+
+@pytest.mark.parametrize("L", [2, 3, 4, 5])
+def test_greedy_stencil27_eight_colors(L):
+    # any 2x2x2 block is K_8, so 8 colors are necessary; natural-order First Fit reaches exactly
+    # color (x&1) + 2(y&1) + 4(z&1)
+    g = gg.stencil27(L)
+    c, k = oracle.greedy(g)
+    assert k == min(8, 2 ** sum(1 for _ in range(3) if L > 1))
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    assert np.array_equal(c, ((x & 1) + 2 * (y & 1) + 4 * (z & 1)).ravel())
+
+
+def test_greedy_crown_graph():
+    # the textbook worst case: interleaved order forces k colors on a bipartite graph
+    for k in (3, 6, 11):
+        assert oracle.greedy(gg.crown(k, interleaved=True))[1] == k
+        assert oracle.greedy(gg.crown(k, interleaved=False))[1] == 2
+
+
+def _first_fit_characterisation(g, c):
+    """Proper, and every vertex of color k has earlier neighbours of every color < k: this
+    determines natural-order First Fit uniquely (induction on the vertex order)."""
+    for v in range(g.n):
+        nb = g.colidx[g.rowptr[v]:g.rowptr[v + 1]]
+        earlier = {int(c[u]) for u in nb if u < v}
+        assert int(c[v]) not in {int(c[u]) for u in nb}
+        assert set(range(int(c[v]))) <= earlier
+
+
+def test_greedy_characterisation_random():
+    for seed in range(20):
+        g = gg.er(60, 1 + seed % 9, seed)
+        c, k = oracle.greedy(g)
+        _first_fit_characterisation(g, c)
+        assert k == c.max() + 1 <= g.max_degree + 1
+
+
+# ---------------------------------------------------------------------------------------------
+# deterministic speculative coloring (Algorithm 1, one vertex per partition)
+
+def _rank(seed, n):
+    return oracle.priority_rank(seed, n)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 25])
+@pytest.mark.parametrize("seed", [0, 7, 99])
+def test_det_complete_graph_closed_form(n, seed):
+    # K_n: in round r every worklist vertex sees colors 0..r-2 and takes r-1; only the smallest
+    # key keeps it.  So the vertex of key rank k gets color k, and there are n rounds with
+    # worklists of sizes n, n-1, ..., 1.
+    r = oracle.det(gg.complete(n), seed)
+    assert r.rounds == n and r.ncolors == n
+    assert np.array_equal(r.colors, _rank(seed, n))
+    assert list(r.wl_size) == list(range(n, 0, -1))
+
+
+@pytest.mark.parametrize("leaves", [1, 2, 5, 40])
+@pytest.mark.parametrize("seed", range(6))
+def test_det_star_closed_form(leaves, seed):
+    # Star with centre 0.  Round 1 colors everything 0.  If the centre has the smallest key it
+    # keeps 0 and every leaf takes 1 in round 2 (2 rounds).  Otherwise the centre takes 1 in round
+    # 2 (its leaves still show 0); leaves with larger key than the centre also re-take 1 (the
+    # centre showed 0), lose to the centre, and take 0 in round 3.  Final: centre 1, leaves 0.
+    g = gg.star(leaves)
+    rank = _rank(seed, g.n)
+    r = oracle.det(g, seed)
+    if rank[0] == 0:
+        assert r.colors[0] == 0 and np.all(r.colors[1:] == 1) and r.rounds == 2
+    else:
+        assert r.colors[0] == 1 and np.all(r.colors[1:] == 0)
+        assert r.rounds == (3 if np.any(rank[1:] > rank[0]) else 2)
+
+
+@pytest.mark.parametrize("a,b", [(1, 1), (2, 3), (5, 5), (7, 2), (12, 9)])
+@pytest.mark.parametrize("seed", range(8))
+def test_det_complete_bipartite_closed_form(a, b, seed):
+    # K_{a,b}, sides A = 0..a-1, B = a..a+b-1.  Let S be the side holding the smallest key and T
+    # the other side, t = smallest key in T.  Round 1: all 0; all of T loses, and S' = {s in S with
+    # key > t} loses.  Round 2: everyone on the worklist sees only 0s and takes 1; every vertex of
+    # S' then loses to t.  If S' is empty that ends it (2 rounds, S = 0, T = 1).  Otherwise let
+    # s' = smallest key in S'; T'' = {x in T with key > s'} lose too.  Round 3: S' sees T at 1 and
+    # takes 0; T'' sees S at {0 (kept), 1 (S' in round 2)} and takes 2.  No conflicts remain.
+    edges = [(i, a + j) for i in range(a) for j in range(b)]
+    g = gg.from_edges(a + b, edges)
+    rank = _rank(seed, a + b)
+    A, B = np.arange(a), np.arange(a, a + b)
+    S, T = (A, B) if rank[A].min() < rank[B].min() else (B, A)
+    t = rank[T].min()
+    S1 = S[rank[S] > t]
+    r = oracle.det(g, seed)
+    if len(S1) == 0:
+        assert r.rounds == 2 and np.all(r.colors[S] == 0) and np.all(r.colors[T] == 1)
+    else:
+        s1 = rank[S1].min()
+        T2 = T[rank[T] > s1]
+        T1 = T[rank[T] < s1]
+        assert r.rounds == 3
+        assert np.all(r.colors[S] == 0)
+        assert np.all(r.colors[T1] == 1) and np.all(r.colors[T2] == 2)
+        assert r.ncolors == (3 if len(T2) else 2)
+
+
+def test_det_single_edge_and_edgeless():
+    for seed in range(5):
+        r = oracle.det(gg.path(2), seed)
+        rank = _rank(seed, 2)
+        assert list(r.colors) == [int(rank[0]), int(rank[1])] and r.rounds == 2
+    r = oracle.det(gg.empty(9), 3)
+    assert np.all(r.colors == 0) and r.rounds == 1 and r.ncolors == 1
+    r = oracle.det(gg.empty(0), 3)
+    assert r.rounds == 0 and r.ncolors == 0
+
+
+def _check_det_invariants(g, seed):
+    r = oracle.det(g, seed)
+    assert r.status == 0
+    c = r.colors
+    # Lemma 1: proper at termination
+    assert oracle.count_conflicts(g, c) == 0
+    if g.n == 0:
+        return r
+    deg = g.degrees()
+    # First Fit never exceeds the degree, hence at most Delta + 1 colors (Section 2.1)
+    assert np.all(c >= 0) and np.all(c <= deg)
+    assert r.ncolors <= g.max_degree + 1
+    assert r.ncolors == len(np.unique(c))
+    # a color c can first be taken in round c + 1 (round r sees colors <= r - 2)
+    assert r.rounds >= c.max() + 1
+    # the smallest key never loses, so it keeps the color 0 of round 1
+    rank = _rank(seed, g.n)
+    assert c[int(np.argmin(rank))] == 0
+    # every round retires the smallest key of its worklist: sizes strictly decrease (rounds <= n)
+    assert r.wl_size[0] == g.n and r.wl_degsum[0] == g.nnz
+    assert np.all(np.diff(r.wl_size) < 0)
+    assert r.rounds <= g.n
+    # last_round is consistent with the worklist sizes
+    for k in range(r.rounds):
+        assert (r.last_round >= k + 1).sum() == r.wl_size[k]
+    return r
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_det_invariants_random(seed):
+    _check_det_invariants(gg.er(300, 2 + seed, seed), seed * 31 + 1)
+    _check_det_invariants(gg.rmat(9, 8, seed), seed)
+
+
+def test_det_invariants_structured():
+    for g in (gg.stencil27(6), gg.grid5(20, 11), gg.crown(15), gg.cycle(51), gg.workload("er10k")):
+        _check_det_invariants(g, 7)
+
+
+# ---------------------------------------------------------------------------------------------
+# brute force on tiny graphs
+
+def _chromatic_number(n, edges):
+    if n == 0:
+        return 0
+    for k in range(1, n + 1):
+        for assign in itertools.product(range(k), repeat=n):
+            if all(assign[u] != assign[v] for u, v in edges):
+                return k
+    return n
+
+
+def _literal_rounds(n, adj, key):
+    """Algorithm 1 with one vertex per partition, written directly from Section 3.1 for tiny graphs:
+    phase 1 reads the colors of the previous round, phase 2 re-queues the larger key."""
+    color = [-1] * n
+    work = list(range(n))
+    rounds = 0
+    while work:
+        rounds += 1
+        before = list(color)
+        for v in work:
+            taken = {before[u] for u in adj[v]}
+            color[v] = next(c for c in itertools.count() if c not in taken)
+        work = [v for v in work if any(color[u] == color[v] and key(u) < key(v) for u in adj[v])]
+    return color, rounds
+
+
+def test_tiny_graphs_brute_force():
+    rng = np.random.default_rng(5)
+    for trial in range(150):
+        n = int(rng.integers(1, 8))
+        p = rng.random()
+        edges = [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < p]
+        g = gg.from_edges(n, edges)
+        chi = _chromatic_number(n, edges)
+        seed = int(rng.integers(0, 2**63))
+        r = oracle.det(g, seed)
+        gc_, gk = oracle.greedy(g)
+        dmax = g.max_degree
+        assert chi <= gk <= dmax + 1
+        assert chi <= r.ncolors <= dmax + 1
+        adj = [list(g.colidx[g.rowptr[v]:g.rowptr[v + 1]]) for v in range(n)]
+        h = oracle.keys(seed, n)
+        lit, lr = _literal_rounds(n, adj, lambda v: (int(h[v]), v))
+        assert list(r.colors) == lit and r.rounds == lr
+
+
+# ---------------------------------------------------------------------------------------------
+# Algorithm 1 with p id-ordered blocks (Lemma 2 setting)
+
+def test_partition_single_block_is_greedy():
+    for seed in range(6):
+        g = gg.er(200, 6, seed)
+        r = oracle.partition(g, 1)
+        c, k = oracle.greedy(g)
+        assert np.array_equal(r.colors, c) and r.rounds == 1
+
+
+@pytest.mark.parametrize("p", [2, 3, 8, 64])
+def test_partition_lemma2_round_bound(p):
+    # Lemma 2 and its corollary: at most p+1 rounds (block V_p is final after round 1, V_{p-1}
+    # after round 2, ...); our reading re-queues the lower block, giving at most p rounds
+    for seed in range(10):
+        g = gg.er(400, 3 + seed, seed)
+        r = oracle.partition(g, p)
+        assert r.status == 0
+        assert r.rounds <= p <= p + 1
+        assert oracle.count_conflicts(g, r.colors) == 0
+        assert np.all(r.colors <= g.degrees())
+
+
+def test_partition_one_vertex_blocks_match_id_priority():
+    # p = n: block order = id order, the lower id is re-queued, i.e. the larger id keeps its color
+    rng = np.random.default_rng(9)
+    for trial in range(60):
+        n = int(rng.integers(1, 9))
+        edges = [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < 0.5]
+        g = gg.from_edges(n, edges)
+        adj = [list(g.colidx[g.rowptr[v]:g.rowptr[v + 1]]) for v in range(n)]
+        lit, lr = _literal_rounds(n, adj, lambda v: -v)
+        r = oracle.partition(g, n)
+        assert list(r.colors) == lit and r.rounds == lr
+
+
+def test_checkers():
+    g = gg.complete(4)
+    assert oracle.count_conflicts(g, np.array([0, 1, 2, 3], np.int32)) == 0
+    assert oracle.count_conflicts(g, np.array([0, 0, 2, 3], np.int32)) == 2
+    assert oracle.distinct_colors(np.array([5, 0, 5, 2], np.int32)) == 3

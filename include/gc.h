@@ -1,0 +1,239 @@
+/*
+ * gc.h -- C ABI of the GB300 speculative graph-coloring library (libgc.so).
+ *
+ * The library colors undirected simple graphs with the barrier-synchronised speculative method of
+ * Singhal, Peri & Kalyanasundaram, "Multi-threaded Graph Coloring Algorithm for Shared Memory
+ * Architecture" (arXiv:1509.08267), Section 3.1, Algorithm 1: every vertex on the worklist takes
+ * the least color none of its neighbours uses (First Fit, Section 3), a conflict pass sends one
+ * endpoint of every monochromatic edge back to the worklist (Algorithm 1, phase 2), and rounds
+ * repeat until the worklist is empty.  Lemma 1 (Section 4) gives a proper coloring at the end;
+ * every color is at most deg(v) <= Delta, so at most Delta+1 colors are used (Section 2.1).
+ *
+ * Graph format (all entry points).  Undirected simple graph G = (V, E) of Section 2.1 in CSR:
+ *   rowptr  int32[n+1], rowptr[0] = 0, non-decreasing, rowptr[n] = nnz (number of directed entries)
+ *   colidx  int32[nnz], row v = colidx[rowptr[v] .. rowptr[v+1]) lists the neighbours of v
+ * Each undirected edge {u, v} appears as both (u, v) and (v, u); no self-loops, no duplicates.
+ * Vertex ids are 0-based (the paper numbers them 1..|V|).  The coloring kernels check rowptr
+ * monotonicity, neighbour ranges and self-loops on the fly; symmetry and duplicates are the
+ * caller's promise unless checked with gc_validate_graph (an asymmetric input can yield an
+ * improper coloring).
+ *
+ * Pointers.  Every array argument may be device memory of the current CUDA device (for example a
+ * torch tensor's data_ptr) or host memory (pageable or pinned); the library tells them apart with
+ * cudaPointerGetAttributes and stages host arrays through its own device buffers.  The caller owns
+ * every array it passes; the library never keeps a pointer past the call.  Scalar outputs
+ * (ncolors, rounds of gc_color) are host pointers.
+ *
+ * Scratch.  The library keeps a per-device context with cached device scratch that grows to the
+ * largest problem seen; gc_release_scratch frees it.
+ *
+ * Errors.  Every entry point returns a gc_status.  On error the outputs are left untouched and
+ * gc_last_error() returns a message for the calling thread.  No entry point falls back to a CPU
+ * implementation: without a usable CUDA device every call returns GC_ERR_CUDA.
+ *
+ * Colors.  0-based int32.  ncolors = number of distinct colors in the result ("Number of Colors
+ * Used", Section 5.2).  rounds = number of tentative-coloring phases executed (Algorithm 1's while
+ * loop iterations): 0 for n = 0, 1 for a graph without edges.
+ *
+ * Modes.
+ *   GC_MODE_DETERMINISTIC  Phase 1 of round r reads only the colors as they stood when round r
+ *       began, and the endpoint of a monochromatic edge with the larger priority key is re-queued.
+ *       key(v) = (h(v), v) compared lexicographically, h(v) = output number v (0-based) of the
+ *       SplitMix64 generator seeded with `seed` (Steele, Lea & Flood 2014).  The result (colors,
+ *       ncolors, rounds) is a function of the graph and the seed only, identical for every launch
+ *       configuration and batch composition.
+ *   GC_MODE_INPLACE  Phase 1 reads neighbour colors live, as the paper's threads do; the result
+ *       depends on scheduling.  It is always a proper coloring with color(v) <= deg(v), and the
+ *       number of rounds never exceeds n.
+ */
+#ifndef GC_H
+#define GC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GC_OK = 0,
+    GC_ERR_INVALID_ARG = -1,     /* bad argument: NULL pointer, negative size, unknown mode */
+    GC_ERR_INVALID_GRAPH = -2,   /* CSR breaks the graph format above */
+    GC_ERR_OOM = -3,             /* device or pinned memory could not be allocated / admitted */
+    GC_ERR_CUDA = -4,            /* a CUDA call failed (message has the CUDA error string) */
+    GC_ERR_NO_CONVERGENCE = -5,  /* the worklist was not empty after the round cap */
+    GC_ERR_TIMEOUT = -6,         /* a grid-barrier wait exceeded its limit; the kernel returned */
+    GC_ERR_BUSY = -7             /* server request still running (gc_server_poll) */
+} gc_status;
+
+enum { GC_MODE_DETERMINISTIC = 0, GC_MODE_INPLACE = 1 };
+
+/* Flags for gc_options.flags */
+#define GC_FLAG_STATS 1u     /* fill gc_stats' per-round worklist sizes and scanned entries */
+#define GC_FLAG_TIMING 2u    /* record CUDA events around the round kernel (gc_stats.kernel_ms) */
+#define GC_FLAG_VALIDATE 4u  /* run gc_validate_graph(GC_VALIDATE_ALL) before coloring */
+
+/* Flags for gc_validate_graph */
+#define GC_VALIDATE_SORTED 1     /* rows strictly increasing (implies no duplicate entries) */
+#define GC_VALIDATE_SYMMETRIC 2  /* (u, v) present whenever (v, u) is; requires sorted rows */
+#define GC_VALIDATE_ALL 3
+
+/* Tuning and control knobs; a zero field means "library default".  Pass NULL for all defaults. */
+typedef struct gc_options {
+    void *stream;              /* cudaStream_t to run on; NULL = the context's own stream */
+    int32_t max_rounds;        /* round cap; 0 = n + 1 (a worklist shrinks every round) */
+    int32_t small_max_degree;  /* vertices up to this degree get one thread each (1..63); default 32 */
+    int32_t chunk;             /* edges per warp work item for larger vertices (32..1024, multiple of 32); default 128 */
+    int32_t block_size;        /* threads per block of the round kernel (128, 256 or 512); default 256 */
+    int32_t blocks_per_sm;     /* resident blocks per SM for the round kernel; 0 = occupancy maximum */
+    int64_t spin_limit_ns;     /* grid-barrier wait limit in ns; 0 = 1e9.  A wait that runs out makes
+                                  the call return GC_ERR_TIMEOUT with the device still usable */
+    uint32_t flags;            /* GC_FLAG_* */
+    int32_t reserved[8];
+} gc_options;
+
+/* Optional run statistics (gc_color_ex / gc_color_batch_ex).  The caller may provide arrays
+ * wl_size / wl_degsum of round_cap entries; entry r-1 receives |W_r| and the sum of deg(v) over W_r
+ * for round r (GC_FLAG_STATS). */
+typedef struct gc_stats {
+    int32_t rounds;            /* rounds executed (largest over the batch for gc_color_batch_ex) */
+    int32_t ncolors;           /* distinct colors (sum over the batch for gc_color_batch_ex) */
+    int32_t max_color;         /* largest color used (largest over the batch) */
+    int32_t round_cap;         /* capacity of wl_size / wl_degsum (input) */
+    int64_t *wl_size;          /* caller array or NULL */
+    int64_t *wl_degsum;        /* caller array or NULL */
+    int64_t worklist_total;    /* sum over rounds of |W_r| (GC_FLAG_STATS) */
+    int64_t entries_scanned;   /* adjacency entries read by the round kernel (GC_FLAG_STATS) */
+    float kernel_ms;           /* round-kernel device time (GC_FLAG_TIMING) */
+    float setup_ms;            /* binning/setup kernel device time (GC_FLAG_TIMING) */
+    int32_t grid_blocks;       /* blocks of the persistent round kernel */
+    int32_t block_size;        /* threads per block of the round kernel */
+    int32_t reserved[6];
+} gc_stats;
+
+/*
+ * gc_color -- color one graph (Algorithm 1, Section 3.1).
+ *   n          number of vertices (>= 0)
+ *   rowptr     int32[n+1]   CSR row offsets (device or host)
+ *   colidx     int32[nnz]   CSR neighbour ids (device or host); may be NULL when nnz = 0
+ *   mode       GC_MODE_DETERMINISTIC or GC_MODE_INPLACE
+ *   seed       priority-hash seed (deterministic mode; in-place mode uses it for tie-breaks too)
+ *   colors_out int32[n]     receives the colors (device or host)
+ *   ncolors    host int32*  receives the number of distinct colors (may be NULL)
+ *   rounds     host int32*  receives the number of rounds (may be NULL)
+ * Synchronous: returns after the colors are in colors_out.
+ * Errors: GC_ERR_INVALID_ARG, GC_ERR_INVALID_GRAPH, GC_ERR_OOM, GC_ERR_CUDA,
+ *         GC_ERR_NO_CONVERGENCE, GC_ERR_TIMEOUT; outputs untouched on error.
+ */
+int gc_color(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, uint64_t seed,
+             int32_t *colors_out, int32_t *ncolors, int32_t *rounds);
+
+/* gc_color with options (may be NULL) and statistics (may be NULL). */
+int gc_color_ex(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, uint64_t seed,
+                int32_t *colors_out, int32_t *ncolors, int32_t *rounds, const gc_options *opt,
+                gc_stats *stats);
+
+/*
+ * gc_color_batch -- color G independent graphs in one persistent launch (every graph runs
+ * Algorithm 1 on its own; a round of the launch is a round of every graph still active).
+ *   G          number of graphs (>= 0)
+ *   vtx_off    int64[G+1]  graph g's vertices are colors_out[vtx_off[g] .. vtx_off[g+1]); vtx_off[0] = 0
+ *   edge_off   int64[G+1]  graph g's neighbour ids are colidx[edge_off[g] .. edge_off[g+1]); edge_off[0] = 0
+ *   rowptr     int32[vtx_off[G] + G]  graph g's own local CSR row offsets (n_g + 1 entries, starting
+ *              at 0) are rowptr[vtx_off[g] + g .. vtx_off[g+1] + g]
+ *   colidx     int32[edge_off[G]]     local (0-based within graph g) neighbour ids
+ *   mode, seed as gc_color; the priority key uses graph-local ids, so graph g's colors equal what
+ *              gc_color gives for it alone in deterministic mode
+ *   colors_out int32[vtx_off[G]]  local colors per graph
+ *   ncolors    int32[G]  distinct colors per graph (device or host; may be NULL)
+ *   rounds     int32[G]  rounds per graph = the last round whose worklist held one of its vertices
+ *              (device or host; may be NULL)
+ * Totals are limited to vtx_off[G] < 2^31 vertices; edge offsets are 64-bit.
+ */
+int gc_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off, const int32_t *rowptr,
+                   const int32_t *colidx, int mode, uint64_t seed, int32_t *colors_out, int32_t *ncolors,
+                   int32_t *rounds);
+
+int gc_color_batch_ex(int32_t G, const int64_t *vtx_off, const int64_t *edge_off, const int32_t *rowptr,
+                      const int32_t *colidx, int mode, uint64_t seed, int32_t *colors_out, int32_t *ncolors,
+                      int32_t *rounds, const gc_options *opt, gc_stats *stats);
+
+/*
+ * gc_validate_graph -- check the graph format of Section 2.1 on the device.
+ * Always checks rowptr[0] = 0, monotone rowptr, 0 <= colidx < n and no self-loops; `flags`
+ * (GC_VALIDATE_*) adds sorted/duplicate-free rows and symmetry.  Returns GC_OK or
+ * GC_ERR_INVALID_GRAPH (message names the first offending vertex/entry found), or an argument /
+ * CUDA error.
+ */
+int gc_validate_graph(int32_t n, const int32_t *rowptr, const int32_t *colidx, int flags);
+
+/* Message for the last error on the calling thread ("" if none). Valid until the next call. */
+const char *gc_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int gc_version(void);
+
+/* Frees the calling device's cached scratch (the next call re-allocates). */
+int gc_release_scratch(void);
+
+/*
+ * ---- Serving: continuous batching of independent coloring requests ----
+ *
+ * A server owns a device memory pool of `pool_vertices` vertex slots and `pool_entries` adjacency
+ * entries and a worker thread that runs rounds of the batched round kernel over every admitted
+ * request.  gc_server_submit copies the request's CSR into pinned staging memory and queues it;
+ * the worker admits queued requests between rounds whenever their footprint fits the free pool
+ * space (first fit), so requests that arrive while others are on the GPU join the running batch at
+ * the next round boundary.  A request's colors are identical to gc_color's for the same graph,
+ * mode GC_MODE_DETERMINISTIC and seed.
+ */
+typedef struct gc_server gc_server;
+
+typedef struct gc_server_config {
+    int64_t pool_vertices;   /* vertex capacity of the resident pool (> 0) */
+    int64_t pool_entries;    /* adjacency-entry capacity of the resident pool (> 0) */
+    int32_t max_requests;    /* maximum requests resident at once (slots); 0 = 4096 */
+    int32_t mode;            /* GC_MODE_DETERMINISTIC or GC_MODE_INPLACE */
+    uint64_t seed;           /* priority seed for every request */
+    int32_t device;          /* CUDA device ordinal; -1 = current */
+    int32_t reserved[7];
+} gc_server_config;
+
+typedef struct gc_server_stats {
+    int64_t submitted, completed, rejected;
+    int64_t rounds_run;          /* batched rounds executed by the worker */
+    int64_t vertices_colored, edges_colored;  /* totals over completed requests (edges = nnz/2) */
+    double p50_ms, p99_ms;       /* submit-to-done latency over completed requests */
+    double busy_s;               /* wall time with at least one request resident */
+    double wall_s;               /* time since the server was created */
+    int32_t resident;            /* requests currently resident on the device */
+    int32_t queued;              /* requests waiting for admission */
+    int32_t reserved[6];
+} gc_server_stats;
+
+/* Creates the pool and the worker thread. Errors: INVALID_ARG, OOM, CUDA. */
+int gc_server_create(const gc_server_config *cfg, gc_server **out);
+
+/* Queues one graph (host or device CSR as in gc_color; copied before return).  Non-blocking.
+ * GC_ERR_OOM if the graph can never fit the pool; GC_ERR_INVALID_GRAPH for a malformed rowptr. */
+int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32_t *colidx,
+                     uint64_t *req_id);
+
+/* Waits up to timeout_ms (0 = do not wait, <0 = forever) for request req_id.  On completion copies
+ * its colors into colors_out (host or device, n entries; may be NULL), sets ncolors / rounds (host
+ * pointers, may be NULL), forgets the request and returns GC_OK or the request's error status.
+ * Returns GC_ERR_BUSY while it is still queued or running, GC_ERR_INVALID_ARG for an unknown id. */
+int gc_server_poll(gc_server *s, uint64_t req_id, int32_t timeout_ms, int32_t *colors_out,
+                   int32_t *ncolors, int32_t *rounds);
+
+int gc_server_stats_get(gc_server *s, gc_server_stats *out);
+
+/* Stops the worker (finishing resident requests), frees the pool. */
+void gc_server_destroy(gc_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GC_H */

@@ -1,0 +1,646 @@
+// C ABI of the coloring library: argument checks, per-device context with cached scratch, host
+// array staging, and the launch sequence setup -> expand -> persistent round kernel -> counting.
+// Declarations and the contract of every entry point are in include/gc.h.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gc_internal.h"
+
+namespace gc {
+
+// ------------------------------------------------------------------------------------------
+// errors
+
+static thread_local std::string t_error;
+
+int set_last_error(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_error = buf;
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *what) {
+    return set_last_error(GC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define GC_CUDA(call)                                                    \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);              \
+    } while (0)
+
+// ------------------------------------------------------------------------------------------
+// device buffers and context
+
+struct Buf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        const size_t want = bytes + bytes / 8;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return e;
+        }
+        cap = want;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T *as() const {
+        return static_cast<T *>(p);
+    }
+};
+
+// Control block: one device allocation, fetched with one copy at the end of a run.
+struct Ctl {
+    int32_t err[4];
+    int32_t passes[2];  // first round not executed, last round executed
+    int32_t pad0[2];
+    unsigned cnt[3 * kCnt];
+    unsigned tmp[2];
+    int32_t gmax1, gcount1, glast1, pad1;
+    int32_t pad2[6];
+    GridBar bar;
+};
+static_assert(offsetof(Ctl, bar) % 128 == 0, "barrier alignment");
+
+struct Context {
+    int device = -1;
+    std::mutex mu;
+    cudaStream_t stream = nullptr;
+    int sms = 0;
+    int occ[2][2] = {{0, 0}, {0, 0}};  // [mode][batch] blocks per SM of the round kernel
+    Buf col0, col1, prio, small0, small1, items, chunk0, chunk1, acc, ctl, stats, bitmap, vg;
+    Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
+    Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    void release_all() {
+        Buf *all[] = {&col0, &col1, &prio, &small0, &small1, &items, &chunk0, &chunk1, &acc, &ctl, &stats, &bitmap,
+                      &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors};
+        for (Buf *b : all) b->release();
+    }
+};
+
+static std::mutex g_ctx_mu;
+static Context *g_ctx[128];
+
+static int get_context(Context **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 128) {
+        cudaGetLastError();
+        return set_last_error(GC_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+    }
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    if (!g_ctx[dev]) {
+        Context *c = new Context();
+        c->device = dev;
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_fail(e, "cudaStreamCreateWithFlags");
+        }
+        cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+        for (auto &ev : c->ev) cudaEventCreate(&ev);
+        g_ctx[dev] = c;
+    }
+    *out = g_ctx[dev];
+    return GC_OK;
+}
+
+// Where a caller pointer lives: 1 = device memory of the current device (or managed), 0 = host.
+static int locate(const void *p, int dev, int *on_device) {
+    *on_device = 0;
+    if (!p) return GC_OK;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GC_OK;
+    }
+    if (a.type == cudaMemoryTypeDevice) {
+        if (a.device != dev)
+            return set_last_error(GC_ERR_INVALID_ARG, "pointer %p is memory of device %d, current device is %d", p,
+                                  a.device, dev);
+        *on_device = 1;
+    } else if (a.type == cudaMemoryTypeManaged) {
+        *on_device = 1;
+    }
+    return GC_OK;
+}
+
+// Device view of a caller array: the array itself, or a staged copy of a host array.
+static int device_view(const void *p, size_t bytes, int dev, Buf &stage, cudaStream_t s, const void **out) {
+    int on_dev = 0;
+    int st = locate(p, dev, &on_dev);
+    if (st != GC_OK) return st;
+    if (on_dev || bytes == 0) {
+        *out = p;
+        return GC_OK;
+    }
+    cudaError_t e = stage.ensure(bytes);
+    if (e != cudaSuccess) return set_last_error(GC_ERR_OOM, "staging %zu bytes: %s", bytes, cudaGetErrorString(e));
+    GC_CUDA(cudaMemcpyAsync(stage.p, p, bytes, cudaMemcpyHostToDevice, s));
+    *out = stage.p;
+    return GC_OK;
+}
+
+
+static int ensure(Buf &b, size_t bytes, const char *what) {
+    cudaError_t e = b.ensure(bytes);
+    if (e != cudaSuccess)
+        return set_last_error(GC_ERR_OOM, "allocating %zu bytes for %s: %s", bytes, what, cudaGetErrorString(e));
+    return GC_OK;
+}
+
+#define GC_TRY(call)                  \
+    do {                              \
+        int st_ = (call);             \
+        if (st_ != GC_OK) return st_; \
+    } while (0)
+
+static int error_from_ctl(const Ctl &c) {
+    const int64_t where = (static_cast<int64_t>(static_cast<uint32_t>(c.err[3])) << 32) | static_cast<uint32_t>(c.err[2]);
+    switch (c.err[0]) {
+        case GC_ERR_INVALID_GRAPH:
+            if (c.err[1] < 0)
+                return set_last_error(GC_ERR_INVALID_GRAPH, "invalid offset tables at graph %d", -1 - c.err[1]);
+            return set_last_error(GC_ERR_INVALID_GRAPH,
+                                  "invalid graph at vertex %d (row offset or adjacency entry %lld): row offsets must "
+                                  "be non-decreasing from 0 to nnz, neighbours in [0, n) and no self-loops",
+                                  c.err[1], static_cast<long long>(where));
+        case GC_ERR_NO_CONVERGENCE:
+            return set_last_error(GC_ERR_NO_CONVERGENCE, "worklist not empty after %d rounds", c.err[1] - 1);
+        case GC_ERR_TIMEOUT:
+            return set_last_error(GC_ERR_TIMEOUT, "grid barrier wait exceeded its limit (block %d)", c.err[1]);
+        default:
+            return set_last_error(c.err[0], "device error %d", c.err[0]);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// the coloring run (single graph = batch of one)
+
+struct Problem {
+    bool batch;
+    int32_t G;
+    int32_t n;    // total vertices
+    int64_t nnz;  // total entries
+    const int32_t *rowptr;
+    const int32_t *colidx;
+    const int64_t *vtx_off;
+    const int64_t *edge_off;
+};
+
+struct Outputs {
+    int32_t *colors;   // caller array (device or host), total n
+    int32_t *ncolors;  // single: host scalar; batch: caller array of G
+    int32_t *rounds;
+};
+
+static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_options *opt, gc_stats *stats,
+               const Outputs &out) {
+    const int dev = C.device;
+    cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C.stream;
+    const uint32_t flags = opt ? opt->flags : 0u;
+    const int32_t T1 = (opt && opt->small_max_degree) ? opt->small_max_degree : 32;
+    const int32_t CH = (opt && opt->chunk) ? opt->chunk : 128;
+    const int32_t block = (opt && opt->block_size) ? opt->block_size : 256;
+    if (T1 < 1 || T1 > 63) return set_last_error(GC_ERR_INVALID_ARG, "small_max_degree %d outside 1..63", T1);
+    if (CH < 32 || CH > 1024 || CH % 32) return set_last_error(GC_ERR_INVALID_ARG, "chunk %d invalid", CH);
+    if (block != 256) return set_last_error(GC_ERR_INVALID_ARG, "block_size %d unsupported (256)", block);
+    const int64_t n = pb.n;
+    const int32_t G = pb.G;
+    const int32_t max_rounds =
+        (opt && opt->max_rounds > 0) ? opt->max_rounds : static_cast<int32_t>(n < INT32_MAX ? n + 1 : INT32_MAX);
+    const int64_t spin_ns = (opt && opt->spin_limit_ns > 0) ? opt->spin_limit_ns : 1000000000LL;
+    const int32_t stats_cap = (flags & GC_FLAG_STATS) ? (max_rounds < 65536 ? max_rounds : 65536) : 0;
+    const size_t gz = static_cast<size_t>(G);
+
+    // scratch sized by n; work-item buffers are sized after binning
+    GC_TRY(ensure(C.col0, 4 * n, "colors"));
+    GC_TRY(ensure(C.col1, 4 * n, "colors"));
+    GC_TRY(ensure(C.prio, 4 * n, "priorities"));
+    GC_TRY(ensure(C.small0, 4 * n, "worklist"));
+    GC_TRY(ensure(C.small1, 4 * n, "worklist"));
+    GC_TRY(ensure(C.items, 4 * n, "worklist"));
+    GC_TRY(ensure(C.ctl, sizeof(Ctl), "control"));
+    GC_TRY(ensure(C.bitmap, 4 * (n / 32 + 2), "color bitmap"));
+    if (stats_cap) GC_TRY(ensure(C.stats, 16 * static_cast<size_t>(stats_cap), "statistics"));
+    if (pb.batch) {
+        GC_TRY(ensure(C.vg, 4 * n, "graph ids"));
+        GC_TRY(ensure(C.gmax, 4 * gz, "per-graph max"));
+        GC_TRY(ensure(C.gcount, 4 * gz, "per-graph counts"));
+        GC_TRY(ensure(C.glast, 4 * gz, "per-graph rounds"));
+        GC_TRY(ensure(C.g_vbase, 8 * gz, "graph table"));
+        GC_TRY(ensure(C.g_n, 4 * gz, "graph table"));
+        GC_TRY(ensure(C.g_ebase, 8 * gz, "graph table"));
+        GC_TRY(ensure(C.g_rbase, 8 * gz, "graph table"));
+        GC_TRY(ensure(C.g_m, 8 * gz, "graph table"));
+    }
+    Ctl *ctl = C.ctl.as<Ctl>();
+    GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    GC_CUDA(cudaMemsetAsync(&ctl->gmax1, 0xff, sizeof(int32_t), s));
+    GC_CUDA(cudaMemsetAsync(C.bitmap.p, 0, 4 * (n / 32 + 2), s));
+    if (stats_cap) GC_CUDA(cudaMemsetAsync(C.stats.p, 0, 16 * static_cast<size_t>(stats_cap), s));
+    if (pb.batch) GC_CUDA(cudaMemsetAsync(C.gmax.p, 0xff, 4 * gz, s));
+
+    RoundParams P{};
+    P.n = static_cast<int32_t>(n);
+    P.G = G;
+    P.nnz = pb.nnz;
+    P.rowptr = pb.rowptr;
+    P.colidx = pb.colidx;
+    if (pb.batch) {
+        P.g_vbase = C.g_vbase.as<int64_t>();
+        P.g_n = C.g_n.as<int32_t>();
+        P.g_ebase = C.g_ebase.as<int64_t>();
+        P.g_rbase = C.g_rbase.as<int64_t>();
+        P.g_m = C.g_m.as<int64_t>();
+        P.vg = C.vg.as<int32_t>();
+    }
+    P.seed = seed;
+    P.col0 = C.col0.as<int32_t>();
+    P.col1 = C.col1.as<int32_t>();
+    P.prio = C.prio.as<uint32_t>();
+    P.small0 = C.small0.as<int32_t>();
+    P.small1 = C.small1.as<int32_t>();
+    P.items = C.items.as<int32_t>();
+    P.tmp = ctl->tmp;
+    P.cnt = ctl->cnt;
+    P.bar = &ctl->bar;
+    P.err = ctl->err;
+    P.passes = ctl->passes;
+    P.graph_last = pb.batch ? C.glast.as<int32_t>() : &ctl->glast1;
+    P.stats = stats_cap ? C.stats.as<unsigned long long>() : nullptr;
+    P.stats_cap = stats_cap;
+    P.pass_begin = 1;
+    P.pass_end = max_rounds < INT32_MAX ? max_rounds + 1 : INT32_MAX;
+    P.cap_is_error = 1;
+    P.first_fast = 1;
+    P.spin_ns = spin_ns;
+    P.T1 = T1;
+    P.CH = CH;
+
+    const bool timing = (flags & GC_FLAG_TIMING) != 0;
+    Ctl h{};
+    if (pb.batch) {
+        GC_CUDA(launch_batch_tables(P, pb.vtx_off, pb.edge_off, C.g_vbase.as<int64_t>(), C.g_n.as<int32_t>(),
+                                    C.g_ebase.as<int64_t>(), C.g_rbase.as<int64_t>(), C.g_m.as<int64_t>(), s));
+        GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+        if (h.err[0] != 0) return error_from_ctl(h);
+    }
+    if (timing) GC_CUDA(cudaEventRecord(C.ev[0], s));
+    GC_CUDA(launch_setup(P, mode, pb.batch, 0, static_cast<int32_t>(n), -1, s));
+    GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    if (h.err[0] != 0) return error_from_ctl(h);
+    const unsigned n_small = h.cnt[kCnt * 1 + kCntSmall];  // round 1 uses counter set 1
+    const unsigned n_items = h.tmp[0], n_chunks = h.tmp[1];
+    GC_TRY(ensure(C.chunk0, 16 * static_cast<size_t>(n_chunks), "work items"));
+    GC_TRY(ensure(C.chunk1, 16 * static_cast<size_t>(n_chunks), "work items"));
+    GC_TRY(ensure(C.acc, 4 * kAccStride * static_cast<size_t>(n_items), "accumulators"));
+    P.chunk0 = C.chunk0.as<int4>();
+    P.chunk1 = C.chunk1.as<int4>();
+    P.acc = C.acc.as<unsigned>();
+    GC_CUDA(launch_expand(P, pb.batch, static_cast<int32_t>(n_items), s));
+    if (timing) GC_CUDA(cudaEventRecord(C.ev[1], s));
+
+    // persistent grid: every block resident; no more blocks than the first round can use
+    int &occ = C.occ[mode][pb.batch ? 1 : 0];
+    if (occ == 0) GC_CUDA(round_kernel_occupancy(mode, pb.batch, block, &occ));
+    int per_sm = occ;
+    if (opt && opt->blocks_per_sm > 0 && opt->blocks_per_sm < per_sm) per_sm = opt->blocks_per_sm;
+    int64_t grid = static_cast<int64_t>(per_sm) * C.sms;
+    const int64_t want = (static_cast<int64_t>(n_small) + 32 * static_cast<int64_t>(n_chunks) + block - 1) / block;
+    if (want < grid) grid = want;
+    if (grid < 1) grid = 1;
+    GC_CUDA(launch_rounds(P, mode, pb.batch, static_cast<int>(grid), block, s));
+    if (timing) GC_CUDA(cudaEventRecord(C.ev[2], s));
+
+    // colors, per-graph counts; a device colors_out is written only if no error was posted
+    int out_dev = 0;
+    GC_TRY(locate(out.colors, dev, &out_dev));
+    GC_CUDA(launch_count_colors(P, pb.batch, mode == GC_MODE_DETERMINISTIC ? &ctl->passes[1] : nullptr, 0,
+                                static_cast<int32_t>(n), 0, G, C.bitmap.as<unsigned>(),
+                                pb.batch ? C.gmax.as<int32_t>() : &ctl->gmax1,
+                                pb.batch ? C.gcount.as<int32_t>() : &ctl->gcount1,
+                                out_dev ? out.colors : nullptr, s));
+    std::vector<int64_t> st_host(2 * static_cast<size_t>(stats_cap));
+    if (stats_cap)
+        GC_CUDA(cudaMemcpyAsync(st_host.data(), C.stats.p, 16 * static_cast<size_t>(stats_cap), cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> gmax_h, gcount_h, glast_h;
+    if (pb.batch) {
+        gmax_h.resize(gz);
+        gcount_h.resize(gz);
+        glast_h.resize(gz);
+        GC_CUDA(cudaMemcpyAsync(gmax_h.data(), C.gmax.p, 4 * gz, cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaMemcpyAsync(gcount_h.data(), C.gcount.p, 4 * gz, cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaMemcpyAsync(glast_h.data(), C.glast.p, 4 * gz, cudaMemcpyDeviceToHost, s));
+    }
+    GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    if (h.err[0] != 0) return error_from_ctl(h);
+
+    const int32_t last = h.passes[1];  // last round executed (0: every vertex isolated)
+    const int32_t *final_colors =
+        (mode == GC_MODE_DETERMINISTIC && (last & 1)) ? C.col1.as<int32_t>() : C.col0.as<int32_t>();
+    if (!out_dev && out.colors)
+        GC_CUDA(cudaMemcpyAsync(out.colors, final_colors, 4 * static_cast<size_t>(n), cudaMemcpyDeviceToHost, s));
+    const int32_t rounds_single = n > 0 ? (last > 0 ? last : 1) : 0;
+    if (pb.batch) {
+        int on_dev = 0;
+        if (out.ncolors) {
+            GC_TRY(locate(out.ncolors, dev, &on_dev));
+            if (on_dev)
+                GC_CUDA(cudaMemcpyAsync(out.ncolors, C.gcount.p, 4 * gz, cudaMemcpyDeviceToDevice, s));
+            else
+                std::memcpy(out.ncolors, gcount_h.data(), 4 * gz);
+        }
+        if (out.rounds) {
+            GC_TRY(locate(out.rounds, dev, &on_dev));
+            if (on_dev)
+                GC_CUDA(cudaMemcpyAsync(out.rounds, C.glast.p, 4 * gz, cudaMemcpyDeviceToDevice, s));
+            else
+                std::memcpy(out.rounds, glast_h.data(), 4 * gz);
+        }
+    } else {
+        if (out.ncolors) *out.ncolors = h.gcount1;
+        if (out.rounds) *out.rounds = rounds_single;
+    }
+    GC_CUDA(cudaStreamSynchronize(s));
+    if (stats) {
+        int32_t total_colors = 0, maxc = -1;
+        if (pb.batch) {
+            for (int32_t g = 0; g < G; ++g) {
+                total_colors += gcount_h[g];
+                if (gmax_h[g] > maxc) maxc = gmax_h[g];
+            }
+        } else {
+            total_colors = h.gcount1;
+            maxc = h.gmax1;
+        }
+        stats->rounds = rounds_single;
+        stats->ncolors = total_colors;
+        stats->max_color = maxc;
+        stats->grid_blocks = static_cast<int32_t>(grid);
+        stats->block_size = block;
+        stats->worklist_total = 0;
+        stats->entries_scanned = 0;
+        if (stats_cap) {
+            const int32_t R = last < stats_cap ? last : stats_cap;
+            for (int32_t r = 0; r < R; ++r) {
+                int64_t w = st_host[2 * r], d = st_host[2 * r + 1];
+                if (r == 0) {
+                    w = n;  // W_1 = V; isolated vertices are final before the first sweep
+                    d = pb.nnz;
+                }
+                stats->worklist_total += w;
+                stats->entries_scanned += (mode == GC_MODE_DETERMINISTIC ? 1 : 2) * d;
+                if (stats->wl_size && r < stats->round_cap) stats->wl_size[r] = w;
+                if (stats->wl_degsum && r < stats->round_cap) stats->wl_degsum[r] = d;
+            }
+            if (last == 0 && n > 0) {
+                stats->worklist_total = n;
+                if (stats->wl_size && stats->round_cap > 0) stats->wl_size[0] = n;
+                if (stats->wl_degsum && stats->round_cap > 0) stats->wl_degsum[0] = 0;
+            }
+        }
+        stats->kernel_ms = 0.f;
+        stats->setup_ms = 0.f;
+        if (timing) {
+            cudaEventElapsedTime(&stats->setup_ms, C.ev[0], C.ev[1]);
+            cudaEventElapsedTime(&stats->kernel_ms, C.ev[1], C.ev[2]);
+        }
+    }
+    return GC_OK;
+}
+
+static int color_single(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, uint64_t seed,
+                        int32_t *colors_out, int32_t *ncolors, int32_t *rounds, const gc_options *opt,
+                        gc_stats *stats) {
+    if (n < 0) return set_last_error(GC_ERR_INVALID_ARG, "n = %d is negative", n);
+    if (mode != GC_MODE_DETERMINISTIC && mode != GC_MODE_INPLACE)
+        return set_last_error(GC_ERR_INVALID_ARG, "unknown mode %d", mode);
+    if (n > 0 && (!rowptr || !colors_out)) return set_last_error(GC_ERR_INVALID_ARG, "NULL rowptr or colors_out");
+    if (n == INT32_MAX) return set_last_error(GC_ERR_INVALID_ARG, "n too large");
+    Context *C = nullptr;
+    GC_TRY(get_context(&C));
+    std::lock_guard<std::mutex> lk(C->mu);
+    GC_CUDA(cudaSetDevice(C->device));
+    if (n == 0) {
+        if (ncolors) *ncolors = 0;
+        if (rounds) *rounds = 0;
+        if (stats) {
+            int32_t cap = stats->round_cap;
+            int64_t *a = stats->wl_size, *b = stats->wl_degsum;
+            std::memset(stats, 0, sizeof(*stats));
+            stats->round_cap = cap;
+            stats->wl_size = a;
+            stats->wl_degsum = b;
+            stats->max_color = -1;
+        }
+        return GC_OK;
+    }
+    cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C->stream;
+    int rp_dev = 0;
+    GC_TRY(locate(rowptr, C->device, &rp_dev));
+    int32_t nnz32 = 0;
+    if (rp_dev) {
+        GC_CUDA(cudaMemcpyAsync(&nnz32, rowptr + n, 4, cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+    } else {
+        nnz32 = rowptr[n];
+    }
+    if (nnz32 < 0) return set_last_error(GC_ERR_INVALID_GRAPH, "rowptr[n] = %d is negative", nnz32);
+    if (nnz32 > 0 && !colidx) return set_last_error(GC_ERR_INVALID_ARG, "NULL colidx with %d entries", nnz32);
+    Problem pb{};
+    pb.batch = false;
+    pb.G = 1;
+    pb.n = n;
+    pb.nnz = nnz32;
+    const void *v = nullptr;
+    GC_TRY(device_view(rowptr, 4 * (static_cast<size_t>(n) + 1), C->device, C->st_rowptr, s, &v));
+    pb.rowptr = static_cast<const int32_t *>(v);
+    GC_TRY(device_view(colidx, 4 * static_cast<size_t>(nnz32), C->device, C->st_colidx, s, &v));
+    pb.colidx = static_cast<const int32_t *>(v);
+    if (opt && (opt->flags & GC_FLAG_VALIDATE)) {
+        GC_TRY(ensure(C->ctl, sizeof(Ctl), "control"));
+        Ctl *ctl = C->ctl.as<Ctl>();
+        GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+        GC_CUDA(launch_validate(n, pb.rowptr, pb.colidx ? pb.colidx : pb.rowptr, GC_VALIDATE_ALL, ctl->err, s));
+        Ctl h{};
+        GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+        if (h.err[0] != 0) return error_from_ctl(h);
+    }
+    if (!pb.colidx) pb.colidx = pb.rowptr;  // never dereferenced when nnz == 0
+    Outputs o{colors_out, ncolors, rounds};
+    return run(*C, pb, mode, seed, opt, stats, o);
+}
+
+static int color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off, const int32_t *rowptr,
+                       const int32_t *colidx, int mode, uint64_t seed, int32_t *colors_out, int32_t *ncolors,
+                       int32_t *rounds, const gc_options *opt, gc_stats *stats) {
+    if (G < 0) return set_last_error(GC_ERR_INVALID_ARG, "G = %d is negative", G);
+    if (mode != GC_MODE_DETERMINISTIC && mode != GC_MODE_INPLACE)
+        return set_last_error(GC_ERR_INVALID_ARG, "unknown mode %d", mode);
+    if (G > 0 && (!vtx_off || !edge_off)) return set_last_error(GC_ERR_INVALID_ARG, "NULL offset table");
+    Context *C = nullptr;
+    GC_TRY(get_context(&C));
+    std::lock_guard<std::mutex> lk(C->mu);
+    GC_CUDA(cudaSetDevice(C->device));
+    if (G == 0) {
+        if (stats) {
+            std::memset(stats, 0, offsetof(gc_stats, round_cap));
+            stats->max_color = -1;
+        }
+        return GC_OK;
+    }
+    cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C->stream;
+    int vd = 0, ed = 0;
+    GC_TRY(locate(vtx_off, C->device, &vd));
+    GC_TRY(locate(edge_off, C->device, &ed));
+    int64_t N = 0, NNZ = 0;
+    if (vd)
+        GC_CUDA(cudaMemcpyAsync(&N, vtx_off + G, 8, cudaMemcpyDeviceToHost, s));
+    else
+        N = vtx_off[G];
+    if (ed)
+        GC_CUDA(cudaMemcpyAsync(&NNZ, edge_off + G, 8, cudaMemcpyDeviceToHost, s));
+    else
+        NNZ = edge_off[G];
+    GC_CUDA(cudaStreamSynchronize(s));
+    if (N < 0 || NNZ < 0) return set_last_error(GC_ERR_INVALID_GRAPH, "negative totals in offset tables");
+    if (N >= INT32_MAX - G) return set_last_error(GC_ERR_INVALID_ARG, "batch too large: %lld vertices", (long long)N);
+    if (N > 0 && (!rowptr || !colors_out)) return set_last_error(GC_ERR_INVALID_ARG, "NULL rowptr or colors_out");
+    if (NNZ > 0 && !colidx) return set_last_error(GC_ERR_INVALID_ARG, "NULL colidx");
+    Problem pb{};
+    pb.batch = true;
+    pb.G = G;
+    pb.n = static_cast<int32_t>(N);
+    pb.nnz = NNZ;
+    const void *v = nullptr;
+    GC_TRY(device_view(vtx_off, 8 * (static_cast<size_t>(G) + 1), C->device, C->st_vtx, s, &v));
+    pb.vtx_off = static_cast<const int64_t *>(v);
+    GC_TRY(device_view(edge_off, 8 * (static_cast<size_t>(G) + 1), C->device, C->st_edge, s, &v));
+    pb.edge_off = static_cast<const int64_t *>(v);
+    GC_TRY(device_view(rowptr, 4 * (static_cast<size_t>(N) + G), C->device, C->st_rowptr, s, &v));
+    pb.rowptr = static_cast<const int32_t *>(v);
+    GC_TRY(device_view(colidx, 4 * static_cast<size_t>(NNZ), C->device, C->st_colidx, s, &v));
+    pb.colidx = v ? static_cast<const int32_t *>(v) : pb.rowptr;
+    Outputs o{colors_out, ncolors, rounds};
+    return run(*C, pb, mode, seed, opt, stats, o);
+}
+
+}  // namespace gc
+
+// ------------------------------------------------------------------------------------------
+// exported entry points
+
+extern "C" {
+
+int gc_color(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, uint64_t seed, int32_t *colors_out,
+             int32_t *ncolors, int32_t *rounds) {
+    return gc::color_single(n, rowptr, colidx, mode, seed, colors_out, ncolors, rounds, nullptr, nullptr);
+}
+
+int gc_color_ex(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, uint64_t seed, int32_t *colors_out,
+                int32_t *ncolors, int32_t *rounds, const gc_options *opt, gc_stats *stats) {
+    return gc::color_single(n, rowptr, colidx, mode, seed, colors_out, ncolors, rounds, opt, stats);
+}
+
+int gc_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off, const int32_t *rowptr,
+                   const int32_t *colidx, int mode, uint64_t seed, int32_t *colors_out, int32_t *ncolors,
+                   int32_t *rounds) {
+    return gc::color_batch(G, vtx_off, edge_off, rowptr, colidx, mode, seed, colors_out, ncolors, rounds, nullptr,
+                           nullptr);
+}
+
+int gc_color_batch_ex(int32_t G, const int64_t *vtx_off, const int64_t *edge_off, const int32_t *rowptr,
+                      const int32_t *colidx, int mode, uint64_t seed, int32_t *colors_out, int32_t *ncolors,
+                      int32_t *rounds, const gc_options *opt, gc_stats *stats) {
+    return gc::color_batch(G, vtx_off, edge_off, rowptr, colidx, mode, seed, colors_out, ncolors, rounds, opt, stats);
+}
+
+int gc_validate_graph(int32_t n, const int32_t *rowptr, const int32_t *colidx, int flags) {
+    using namespace gc;
+    if (n < 0) return set_last_error(GC_ERR_INVALID_ARG, "n = %d is negative", n);
+    if (n > 0 && !rowptr) return set_last_error(GC_ERR_INVALID_ARG, "NULL rowptr");
+    if ((flags & GC_VALIDATE_SYMMETRIC) && !(flags & GC_VALIDATE_SORTED))
+        return set_last_error(GC_ERR_INVALID_ARG, "GC_VALIDATE_SYMMETRIC requires GC_VALIDATE_SORTED");
+    Context *C = nullptr;
+    GC_TRY(get_context(&C));
+    std::lock_guard<std::mutex> lk(C->mu);
+    GC_CUDA(cudaSetDevice(C->device));
+    if (n == 0) return GC_OK;
+    cudaStream_t s = C->stream;
+    int rp_dev = 0;
+    GC_TRY(locate(rowptr, C->device, &rp_dev));
+    int32_t nnz = 0;
+    if (rp_dev) {
+        GC_CUDA(cudaMemcpyAsync(&nnz, rowptr + n, 4, cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+    } else {
+        nnz = rowptr[n];
+    }
+    if (nnz < 0) return set_last_error(GC_ERR_INVALID_GRAPH, "rowptr[n] = %d is negative", nnz);
+    if (nnz > 0 && !colidx) return set_last_error(GC_ERR_INVALID_ARG, "NULL colidx");
+    const void *v = nullptr;
+    GC_TRY(device_view(rowptr, 4 * (static_cast<size_t>(n) + 1), C->device, C->st_rowptr, s, &v));
+    const int32_t *rp = static_cast<const int32_t *>(v);
+    GC_TRY(device_view(colidx, 4 * static_cast<size_t>(nnz), C->device, C->st_colidx, s, &v));
+    const int32_t *ci = v ? static_cast<const int32_t *>(v) : rp;
+    GC_TRY(ensure(C->ctl, sizeof(Ctl), "control"));
+    Ctl *ctl = C->ctl.as<Ctl>();
+    GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    GC_CUDA(launch_validate(n, rp, ci, flags, ctl->err, s));
+    Ctl h{};
+    GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    if (h.err[0] != 0) {
+        const int64_t where =
+            (static_cast<int64_t>(static_cast<uint32_t>(h.err[3])) << 32) | static_cast<uint32_t>(h.err[2]);
+        return set_last_error(GC_ERR_INVALID_GRAPH,
+                              "invalid graph at vertex %d, entry %lld (range, self-loop%s%s)", h.err[1],
+                              static_cast<long long>(where), (flags & GC_VALIDATE_SORTED) ? ", order/duplicate" : "",
+                              (flags & GC_VALIDATE_SYMMETRIC) ? ", missing reverse entry" : "");
+    }
+    return GC_OK;
+}
+
+const char *gc_last_error(void) { return gc::t_error.c_str(); }
+
+int gc_version(void) { return 100; }
+
+int gc_release_scratch(void) {
+    using namespace gc;
+    Context *C = nullptr;
+    GC_TRY(get_context(&C));
+    std::lock_guard<std::mutex> lk(C->mu);
+    GC_CUDA(cudaStreamSynchronize(C->stream));
+    C->release_all();
+    return GC_OK;
+}
+
+}  // extern "C"

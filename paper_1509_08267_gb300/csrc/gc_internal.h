@@ -1,0 +1,101 @@
+// Internal declarations shared by the library's translation units (kernels, C ABI, server).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gc.h"
+
+namespace gc {
+
+// Accumulator slot of a vertex whose row is split over several warp work items (chunks):
+// words [0, kAccWords) hold the 512-color window [0, 512) of its neighbours' colors,
+// word kAccFlag the conflict flag, word kAccDone the number of chunks finished.
+constexpr int kAccWords = 16;
+constexpr int kAccFlag = 16;
+constexpr int kAccDone = 17;
+constexpr int kAccStride = 32;  // 128 B per slot
+
+// Worklist counters: three sets used round-robin (read / append / clear), kCnt words each.
+constexpr int kCnt = 4;
+constexpr int kCntSmall = 0, kCntItems = 1, kCntChunks = 2;
+
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+    unsigned pad[30];
+};
+
+// Everything the setup, round and count kernels need.  A single graph uses plain CSR addressing;
+// with BATCH the vertices of graph g are the global ids [g_vbase[g], g_vbase[g] + g_n[g]), its own
+// local rowptr (g_n[g] + 1 entries) starts at rowptr[g_rbase[g]] and its local neighbour ids start at
+// colidx[g_ebase[g]] (g_m[g] entries).  gc_color_batch and the server both fill this table.
+struct RoundParams {
+    int32_t n;    // total vertices (single graph: n)
+    int32_t G;    // graphs in the table
+    int64_t nnz;  // single graph: adjacency entries
+    const int32_t *rowptr;
+    const int32_t *colidx;
+    const int64_t *g_vbase;  // [G]
+    const int32_t *g_n;      // [G]
+    const int64_t *g_ebase;  // [G]
+    const int64_t *g_rbase;  // [G]
+    const int64_t *g_m;      // [G]
+    int32_t *vg;             // [n] graph id per vertex (batch)
+    uint64_t seed;
+
+    int32_t *col0;   // colors: the array read in odd rounds (deterministic) / the live array (in-place)
+    int32_t *col1;   // colors written in odd rounds (deterministic)
+    uint32_t *prio;  // high 32 bits of each vertex's priority hash
+    int32_t *small0, *small1;  // thread-per-vertex worklists (two parities)
+    int4 *chunk0, *chunk1;     // warp work items {vertex, chunk index, slot, chunks} (two parities)
+    int32_t *items;            // setup scratch: larger vertices found by the binning pass
+    unsigned *tmp;             // [2] setup scratch counters: larger vertices, their work items
+    unsigned *cnt;             // [3][kCnt] worklist counters
+    unsigned *acc;             // [slots][kAccStride]
+    GridBar *bar;
+    int32_t *err;              // [4] status, vertex, entry, extra
+    int32_t *passes;           // [2] first round not executed by the last launch, last round executed
+    int32_t *graph_last;       // [G] last round whose worklist held a vertex of graph g
+    unsigned long long *stats; // [2 * stats_cap] per-round |W_r| and sum of degrees (optional)
+    int32_t stats_cap;
+    int32_t pass_begin;        // first round this launch runs (the worklist of that round is current)
+    int32_t pass_end;          // rounds >= pass_end are not run by this launch
+    int32_t cap_is_error;      // reaching pass_end with work left is GC_ERR_NO_CONVERGENCE
+    int32_t first_fast;        // round 1 may assume C_1 == 0 everywhere (all graphs start together)
+    int64_t spin_ns;
+    int32_t T1;  // largest degree handled by one thread
+    int32_t CH;  // adjacency entries per warp work item
+};
+
+// Launch wrappers (gc_kernels.cu).  All return the launch's cudaError_t.
+// gc_color_batch: graph table from the offset tables, graph id per vertex, graph_last = 1 (0 if empty).
+cudaError_t launch_batch_tables(const RoundParams &P, const int64_t *vtx_off, const int64_t *edge_off,
+                                int64_t *g_vbase, int32_t *g_n, int64_t *g_ebase, int64_t *g_rbase, int64_t *g_m,
+                                cudaStream_t s);
+// Binning of vertices [v_begin, v_end) into the worklist of round P.pass_begin.  g_fixed >= 0: all
+// of them belong to graph g_fixed (vg is written, and graph_last[g_fixed] is raised to pass_begin
+// if any of them has a neighbour); otherwise vg must be filled already.
+cudaError_t launch_setup(const RoundParams &P, int mode, bool batch, int32_t v_begin, int32_t v_end,
+                         int32_t g_fixed, cudaStream_t s);
+// Turns the n_items larger vertices found by setup into work items of round P.pass_begin
+// (n_items < 0: the count setup left in P.tmp[0] on the device).
+cudaError_t launch_expand(const RoundParams &P, bool batch, int32_t n_items, cudaStream_t s);
+cudaError_t launch_rounds(const RoundParams &P, int mode, bool batch, int grid, int block, cudaStream_t s);
+cudaError_t round_kernel_occupancy(int mode, bool batch, int block, int *blocks_per_sm);
+// Distinct colors and largest color per graph over vertices [v_begin, v_end) (graphs g_begin..g_end-1).
+// `colors_sel` != NULL: read colors from col1 when *colors_sel is odd (the deterministic buffer
+// that the last round wrote), else from col0.  `out` != NULL receives a copy of the colors of
+// [v_begin, v_end) unless err[0] != 0.
+cudaError_t launch_count_colors(const RoundParams &P, bool batch, const int32_t *colors_sel, int32_t v_begin,
+                                int32_t v_end, int32_t g_begin, int32_t g_end, unsigned *bitmap, int32_t *gmax,
+                                int32_t *gcount, int32_t *out, cudaStream_t s);
+cudaError_t launch_validate(int32_t n, const int32_t *rowptr, const int32_t *colidx, int flags, int32_t *err,
+                            cudaStream_t s);
+
+}  // namespace gc
+
+namespace gc {
+int set_last_error(int code, const char *fmt, ...);
+}

@@ -1,0 +1,972 @@
+// Device code of the speculative coloring library (sm_103a).
+//
+// The method is Algorithm 1 of Singhal, Peri & Kalyanasundaram (arXiv:1509.08267, Section 3.1):
+// rounds of tentative First Fit on a worklist (phase 1), a barrier, conflict detection that sends
+// the loser of every monochromatic edge back to the worklist (phase 2), and a second barrier.
+// Here a "partition" is a single vertex, the priority between partitions is a seeded hash, and
+// the barriers are grid-wide barriers of one persistent cooperative kernel.
+//
+// Deterministic mode.  Round r's phase 1 reads only C_{r-1}.  Because the conflict test of round
+// r and the First Fit of round r+1 both read C_r, one sweep over a worklist vertex's row does
+// both: it tells whether v lost in round r and, if so, v's color for round r+1.  Colors are
+// double-buffered (col0 / col1), so the result does not depend on the order of the sweep.
+// In-place mode.  Phase 1 reads and writes one live color array, then a barrier, then phase 2.
+//
+// Work decomposition per round: vertices of degree <= T1 take one thread each (their First Fit
+// fits a 64-bit window because the answer is at most deg(v)); larger vertices are split into
+// work items of CH adjacency entries handled by one warp each.  The items of one vertex merge
+// their 512-color windows and conflict flags in an accumulator slot; the warp that finishes the
+// last item computes the vertex's result.  Worklists are appended with warp-aggregated atomics.
+#include <climits>
+
+#include "gc_internal.h"
+
+namespace gc {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;  // SplitMix64 state increment
+constexpr int kBlock = 256;                          // round-kernel block size
+constexpr int kMaxWarps = kBlock / 32;
+
+// ------------------------------------------------------------------------------------------
+// priority key: key(v) = (h(v), v), h(v) = SplitMix64 output number v of the stream `seed`
+// (Steele, Lea & Flood 2014).  The high 32 bits of h are cached per vertex; the full hash is
+// recomputed only when those tie.
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t vertex_hash(uint64_t seed, uint32_t local) {
+    return mix64(seed + (static_cast<uint64_t>(local) + 1ull) * kGamma);
+}
+
+// key(u) < key(v): u keeps its color against v.
+__device__ __forceinline__ bool key_less(uint32_t pu, uint32_t pv, uint32_t lu, uint32_t lv, uint64_t seed) {
+    if (pu != pv) return pu < pv;
+    const uint64_t hu = vertex_hash(seed, lu), hv = vertex_hash(seed, lv);
+    if (hu != hv) return hu < hv;
+    return lu < lv;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ void set_error(int32_t *err, int code, int32_t a, int64_t b) {
+    if (atomicCAS(err, 0, code) == 0) {
+        err[1] = a;
+        err[2] = static_cast<int32_t>(b);
+        err[3] = static_cast<int32_t>(b >> 32);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// bounded grid barrier
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// All blocks of the (co-resident, cooperative) grid meet here.  A wait gives up after spin_ns
+// nanoseconds (status GC_ERR_TIMEOUT) or as soon as any block has posted an error; the caller
+// then leaves the kernel.  Returns true when the grid may continue.
+__device__ bool grid_sync(GridBar *bar, int32_t *err, int64_t spin_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned gen = ld_acquire(&bar->gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            st_release(&bar->gen, gen + 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (ld_acquire(&bar->gen) == gen) {
+                if (*reinterpret_cast<volatile int32_t *>(err) != 0) break;
+                if (static_cast<int64_t>(global_ns() - t0) > spin_ns) {
+                    set_error(err, GC_ERR_TIMEOUT, static_cast<int32_t>(blockIdx.x), 0);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_ok = (*reinterpret_cast<volatile int32_t *>(err) == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ------------------------------------------------------------------------------------------
+// graph addressing
+
+struct Row {
+    int64_t b, e;   // entry range in colidx
+    int32_t vbase;  // global id of the graph's vertex 0
+    int32_t ng;     // vertices of the graph
+    int32_t lv;     // local id
+    int32_t g;      // graph id
+};
+
+template <bool BATCH>
+__device__ __forceinline__ Row load_row(const RoundParams &P, int32_t V) {
+    Row r;
+    if constexpr (!BATCH) {
+        r.b = __ldg(P.rowptr + V);
+        r.e = __ldg(P.rowptr + V + 1);
+        r.vbase = 0;
+        r.ng = P.n;
+        r.lv = V;
+        r.g = 0;
+    } else {
+        const int32_t g = __ldg(P.vg + V);
+        const int64_t v0 = __ldg(P.g_vbase + g);
+        const int64_t e0 = __ldg(P.g_ebase + g);
+        r.g = g;
+        r.vbase = static_cast<int32_t>(v0);
+        r.ng = __ldg(P.g_n + g);
+        r.lv = V - r.vbase;
+        const int32_t *rp = P.rowptr + __ldg(P.g_rbase + g);
+        r.b = e0 + __ldg(rp + r.lv);
+        r.e = e0 + __ldg(rp + r.lv + 1);
+    }
+    return r;
+}
+
+// Global id of neighbour `ul` (local id) read at entry j, or -1 after reporting a malformed entry.
+__device__ __forceinline__ int32_t neighbour(const RoundParams &P, const Row &r, int32_t ul, int64_t j) {
+    if (static_cast<uint32_t>(ul) >= static_cast<uint32_t>(r.ng) || ul == r.lv) {
+        set_error(P.err, GC_ERR_INVALID_GRAPH, r.vbase + r.lv, j);
+        return -1;
+    }
+    return r.vbase + ul;
+}
+
+// Warp-aggregated append of V (lanes with `take`) to list[counter].
+__device__ __forceinline__ void warp_append(bool take, int32_t V, int32_t *list, unsigned *counter, int lane) {
+    const unsigned m = __ballot_sync(kFull, take);
+    if (m == 0) return;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(counter, static_cast<unsigned>(__popc(m)));
+    base = __shfl_sync(kFull, base, leader);
+    if (take) list[base + __popc(m & lanemask_lt())] = V;
+}
+
+__device__ __forceinline__ void note_graph_round(const RoundParams &P, int32_t g, int32_t round) {
+    if (__ldcg(P.graph_last + g) < round) atomicMax(P.graph_last + g, round);
+}
+
+// First color not set in the window [0, 512) given as lo0/lo1 (colors 0..63) and win[2..15];
+// -1 when all 512 are taken.
+__device__ __forceinline__ int32_t first_free(unsigned lo0, unsigned lo1, const unsigned *win) {
+    if (~lo0) return __ffs(~lo0) - 1;
+    if (~lo1) return 32 + __ffs(~lo1) - 1;
+#pragma unroll 1
+    for (int w = 2; w < kAccWords; ++w) {
+        const unsigned x = win[w];
+        if (~x) return 32 * w + __ffs(~x) - 1;
+    }
+    return -1;
+}
+
+// Least color >= 512 absent from the row's neighbours (warp-cooperative; mex <= deg(v) bounds it).
+template <bool BATCH>
+__device__ int32_t mex_from(const RoundParams &P, const int32_t *colc, const Row &r, unsigned *win, int lane,
+                            int32_t start) {
+    for (int32_t base = start;; base += 32 * kAccWords) {
+        if (lane < kAccWords) win[lane] = 0;
+        __syncwarp();
+        for (int64_t j = r.b + lane; j < r.e; j += 32) {
+            const int32_t ul = __ldg(P.colidx + j);
+            if (static_cast<uint32_t>(ul) >= static_cast<uint32_t>(r.ng)) continue;
+            const int32_t c = __ldcg(colc + r.vbase + ul) - base;
+            if (static_cast<unsigned>(c) < 32u * kAccWords) atomicOr(&win[c >> 5], 1u << (c & 31));
+        }
+        __syncwarp();
+        int32_t res = -1;
+#pragma unroll 1
+        for (int w = 0; w < kAccWords; ++w) {
+            const unsigned x = win[w];
+            if (~x) {
+                res = base + 32 * w + __ffs(~x) - 1;
+                break;
+            }
+        }
+        __syncwarp();
+        if (res >= 0) return res;
+    }
+}
+
+// Appends a larger vertex with its CH-entry work items to the next worklist (warp-uniform call).
+template <bool BATCH>
+__device__ __forceinline__ void append_large(const RoundParams &P, int32_t V, const Row &r, int4 *chunk_next,
+                                             unsigned *cnt_next, int next_round, int lane) {
+    const int32_t deg = static_cast<int32_t>(r.e - r.b);
+    const int32_t nch = (deg + P.CH - 1) / P.CH;
+    unsigned slot = 0, cb = 0;
+    if (lane == 0) {
+        slot = atomicAdd(cnt_next + kCntItems, 1u);
+        cb = atomicAdd(cnt_next + kCntChunks, static_cast<unsigned>(nch));
+        if constexpr (BATCH) note_graph_round(P, r.g, next_round);
+    }
+    slot = __shfl_sync(kFull, slot, 0);
+    cb = __shfl_sync(kFull, cb, 0);
+    for (int32_t q = lane; q < nch; q += 32)
+        chunk_next[cb + q] = make_int4(V, q, static_cast<int32_t>(slot), nch);
+}
+
+// ------------------------------------------------------------------------------------------
+// deterministic mode
+
+// One vertex of degree <= T1 (one thread): did it lose in this round, and its next color.
+template <bool BATCH, bool FIRST>
+__device__ __forceinline__ bool det_small(const RoundParams &P, const int32_t *__restrict__ colc,
+                                          int32_t *__restrict__ coln, int32_t V, int32_t &deg) {
+    const Row r = load_row<BATCH>(P, V);
+    deg = static_cast<int32_t>(r.e - r.b);
+    const uint32_t pv = __ldg(P.prio + V);
+    const int32_t cv = FIRST ? 0 : __ldcg(colc + V);
+    uint64_t mask = 0;
+    bool lose = false;
+    int64_t j = r.b;
+    for (; j + 4 <= r.e; j += 4) {
+        int32_t ul[4], U[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ul[q] = __ldg(P.colidx + j + q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) U[q] = neighbour(P, r, ul[q], j + q);
+        if constexpr (FIRST) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (U[q] >= 0 && !lose) lose = key_less(__ldg(P.prio + U[q]), pv, ul[q], r.lv, P.seed);
+        } else {
+            int32_t c[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) c[q] = U[q] >= 0 ? __ldcg(colc + U[q]) : -1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (static_cast<unsigned>(c[q]) < 64u) mask |= 1ull << c[q];
+                if (c[q] == cv && !lose) lose = key_less(__ldg(P.prio + U[q]), pv, ul[q], r.lv, P.seed);
+            }
+        }
+    }
+    for (; j < r.e; ++j) {
+        const int32_t ul = __ldg(P.colidx + j);
+        const int32_t U = neighbour(P, r, ul, j);
+        if (U < 0) continue;
+        if constexpr (FIRST) {
+            if (!lose) lose = key_less(__ldg(P.prio + U), pv, ul, r.lv, P.seed);
+        } else {
+            const int32_t c = __ldcg(colc + U);
+            if (static_cast<unsigned>(c) < 64u) mask |= 1ull << c;
+            if (c == cv && !lose) lose = key_less(__ldg(P.prio + U), pv, ul, r.lv, P.seed);
+        }
+    }
+    int32_t nc = cv;
+    if (lose) nc = FIRST ? 1 : __ffsll(static_cast<long long>(~mask)) - 1;
+    coln[V] = nc;
+    return lose;
+}
+
+// One CH-entry work item of a larger vertex (one warp).
+template <bool BATCH, bool FIRST>
+__device__ void det_chunk(const RoundParams &P, const int32_t *__restrict__ colc, int32_t *__restrict__ coln,
+                          int4 it, unsigned *win, int4 *chunk_next, unsigned *cnt_next, int pass, int lane,
+                          unsigned long long &st_deg, unsigned long long &st_cnt) {
+    const int32_t V = it.x, k = it.y, slot = it.z, nch = it.w;
+    const Row r = load_row<BATCH>(P, V);
+    const uint32_t pv = __ldg(P.prio + V);
+    const int32_t cv = FIRST ? 0 : __ldcg(colc + V);
+    const int64_t jb = r.b + static_cast<int64_t>(k) * P.CH;
+    const int64_t je = min(r.e, jb + P.CH);
+    if (k == 0 && lane == 0) {
+        st_deg += static_cast<unsigned long long>(r.e - r.b);
+        st_cnt += 1;
+    }
+    if (lane < kAccWords) win[lane] = 0;
+    __syncwarp();
+    uint64_t lo = 0;
+    bool lose = false;
+    for (int64_t j0 = jb; j0 < je; j0 += 128) {
+        int32_t ul[4], U[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t j = j0 + lane + 32 * q;
+            ul[q] = j < je ? __ldg(P.colidx + j) : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t j = j0 + lane + 32 * q;
+            U[q] = j < je ? neighbour(P, r, ul[q], j) : -1;
+        }
+        if constexpr (FIRST) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (U[q] >= 0 && !lose) lose = key_less(__ldg(P.prio + U[q]), pv, ul[q], r.lv, P.seed);
+        } else {
+            int32_t c[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) c[q] = U[q] >= 0 ? __ldcg(colc + U[q]) : -1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t cq = c[q];
+                if (static_cast<unsigned>(cq) < 64u)
+                    lo |= 1ull << cq;
+                else if (static_cast<unsigned>(cq) < 32u * kAccWords)
+                    atomicOr(&win[cq >> 5], 1u << (cq & 31));
+                if (cq == cv && cq >= 0 && !lose)
+                    lose = key_less(__ldg(P.prio + U[q]), pv, ul[q], r.lv, P.seed);
+            }
+        }
+    }
+    lose = __any_sync(kFull, lose);
+    unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
+    unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
+    __syncwarp();
+    if (nch > 1) {
+        unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
+        if constexpr (!FIRST) {
+            const unsigned w = lane == 0 ? lo0 : lane == 1 ? lo1 : (lane < kAccWords ? win[lane] : 0u);
+            if (lane < kAccWords && (w & ~__ldcg(a + lane))) atomicOr(a + lane, w);
+        }
+        if (lane == 0 && lose) atomicOr(a + kAccFlag, 1u);
+        __threadfence();
+        unsigned done = 0;
+        if (lane == 0) done = atomicAdd(a + kAccDone, 1u);
+        done = __shfl_sync(kFull, done, 0);
+        if (done != static_cast<unsigned>(nch - 1)) return;
+        // the last work item of V: collect the merged window and clear the slot for reuse
+        __threadfence();
+        const unsigned w = lane < kAccWords ? __ldcg(a + lane) : 0u;
+        const unsigned f = __ldcg(a + kAccFlag);
+        lo0 = __shfl_sync(kFull, w, 0);
+        lo1 = __shfl_sync(kFull, w, 1);
+        if (lane >= 2 && lane < kAccWords) win[lane] = w;
+        lose = f != 0;
+        __syncwarp();
+        a[lane] = 0u;  // kAccStride == 32 words
+    }
+    int32_t nc = cv;
+    if (lose) {
+        if (FIRST) {
+            nc = 1;
+        } else {
+            nc = first_free(lo0, lo1, win);
+            if (nc < 0) nc = mex_from<BATCH>(P, colc, r, win, lane, 32 * kAccWords);
+        }
+    }
+    if (lane == 0) coln[V] = nc;
+    if (lose) append_large<BATCH>(P, V, r, chunk_next, cnt_next, pass + 1, lane);
+}
+
+// ------------------------------------------------------------------------------------------
+// in-place mode
+
+// Phase 1 for a vertex of degree <= T1: First Fit over the live colors.
+template <bool BATCH>
+__device__ __forceinline__ void ip_small_assign(const RoundParams &P, int32_t *col, int32_t V) {
+    const Row r = load_row<BATCH>(P, V);
+    uint64_t mask = 0;
+    for (int64_t j = r.b; j < r.e; ++j) {
+        const int32_t ul = __ldg(P.colidx + j);
+        const int32_t U = neighbour(P, r, ul, j);
+        if (U < 0) continue;
+        const int32_t c = __ldcg(col + U);
+        if (static_cast<unsigned>(c) < 64u) mask |= 1ull << c;
+    }
+    __stcg(col + V, __ffsll(static_cast<long long>(~mask)) - 1);
+}
+
+// Phase 2 for a vertex of degree <= T1.
+template <bool BATCH>
+__device__ __forceinline__ bool ip_small_conflict(const RoundParams &P, const int32_t *col, int32_t V, int32_t &deg) {
+    const Row r = load_row<BATCH>(P, V);
+    deg = static_cast<int32_t>(r.e - r.b);
+    const uint32_t pv = __ldg(P.prio + V);
+    const int32_t cv = __ldcg(col + V);
+    bool lose = false;
+    for (int64_t j = r.b; j < r.e && !lose; ++j) {
+        const int32_t ul = __ldg(P.colidx + j);
+        if (static_cast<uint32_t>(ul) >= static_cast<uint32_t>(r.ng)) continue;
+        const int32_t U = r.vbase + ul;
+        if (__ldcg(col + U) == cv) lose = key_less(__ldg(P.prio + U), pv, ul, r.lv, P.seed);
+    }
+    return lose;
+}
+
+// Phase 1 work item of a larger vertex.
+template <bool BATCH>
+__device__ void ip_chunk_assign(const RoundParams &P, int32_t *col, int4 it, unsigned *win, int lane) {
+    const int32_t V = it.x, k = it.y, slot = it.z, nch = it.w;
+    const Row r = load_row<BATCH>(P, V);
+    const int64_t jb = r.b + static_cast<int64_t>(k) * P.CH;
+    const int64_t je = min(r.e, jb + P.CH);
+    if (lane < kAccWords) win[lane] = 0;
+    __syncwarp();
+    uint64_t lo = 0;
+    for (int64_t j0 = jb; j0 < je; j0 += 128) {
+        int32_t U[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t j = j0 + lane + 32 * q;
+            U[q] = j < je ? neighbour(P, r, __ldg(P.colidx + j), j) : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int32_t cq = U[q] >= 0 ? __ldcg(col + U[q]) : -1;
+            if (static_cast<unsigned>(cq) < 64u)
+                lo |= 1ull << cq;
+            else if (static_cast<unsigned>(cq) < 32u * kAccWords)
+                atomicOr(&win[cq >> 5], 1u << (cq & 31));
+        }
+    }
+    unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
+    unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
+    __syncwarp();
+    if (nch > 1) {
+        unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
+        const unsigned w = lane == 0 ? lo0 : lane == 1 ? lo1 : (lane < kAccWords ? win[lane] : 0u);
+        if (lane < kAccWords && (w & ~__ldcg(a + lane))) atomicOr(a + lane, w);
+        __threadfence();
+        unsigned done = 0;
+        if (lane == 0) done = atomicAdd(a + kAccDone, 1u);
+        done = __shfl_sync(kFull, done, 0);
+        if (done != static_cast<unsigned>(nch - 1)) return;
+        __threadfence();
+        const unsigned x = lane < kAccWords ? __ldcg(a + lane) : 0u;
+        lo0 = __shfl_sync(kFull, x, 0);
+        lo1 = __shfl_sync(kFull, x, 1);
+        if (lane >= 2 && lane < kAccWords) win[lane] = x;
+        __syncwarp();
+        a[lane] = 0u;
+    }
+    int32_t nc = first_free(lo0, lo1, win);
+    if (nc < 0) nc = mex_from<BATCH>(P, col, r, win, lane, 32 * kAccWords);
+    if (lane == 0) __stcg(col + V, nc);
+}
+
+// Phase 2 work item of a larger vertex.
+template <bool BATCH>
+__device__ void ip_chunk_conflict(const RoundParams &P, const int32_t *col, int4 it, int4 *chunk_next,
+                                  unsigned *cnt_next, int pass, int lane, unsigned long long &st_deg,
+                                  unsigned long long &st_cnt) {
+    const int32_t V = it.x, k = it.y, slot = it.z, nch = it.w;
+    const Row r = load_row<BATCH>(P, V);
+    const uint32_t pv = __ldg(P.prio + V);
+    const int32_t cv = __ldcg(col + V);
+    const int64_t jb = r.b + static_cast<int64_t>(k) * P.CH;
+    const int64_t je = min(r.e, jb + P.CH);
+    if (k == 0 && lane == 0) {
+        st_deg += static_cast<unsigned long long>(r.e - r.b);
+        st_cnt += 1;
+    }
+    bool lose = false;
+    for (int64_t j = jb + lane; j < je; j += 32) {
+        const int32_t ul = __ldg(P.colidx + j);
+        if (static_cast<uint32_t>(ul) >= static_cast<uint32_t>(r.ng)) continue;
+        const int32_t U = r.vbase + ul;
+        if (!lose && __ldcg(col + U) == cv) lose = key_less(__ldg(P.prio + U), pv, ul, r.lv, P.seed);
+    }
+    lose = __any_sync(kFull, lose);
+    if (nch > 1) {
+        unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
+        if (lane == 0 && lose) atomicOr(a + kAccFlag, 1u);
+        __threadfence();
+        unsigned done = 0;
+        if (lane == 0) done = atomicAdd(a + kAccDone, 1u);
+        done = __shfl_sync(kFull, done, 0);
+        if (done != static_cast<unsigned>(nch - 1)) return;
+        __threadfence();
+        lose = __ldcg(a + kAccFlag) != 0u;
+        __syncwarp();
+        a[lane] = 0u;
+    }
+    if (lose) append_large<BATCH>(P, V, r, chunk_next, cnt_next, pass + 1, lane);
+}
+
+// ------------------------------------------------------------------------------------------
+// kernels
+
+__device__ __forceinline__ void flush_stats(const RoundParams &P, int pass, unsigned long long deg,
+                                            unsigned long long cnt) {
+    // block-level reduction, then one atomic per block
+    __shared__ unsigned long long s_deg, s_cnt;
+    if (threadIdx.x == 0) {
+        s_deg = 0;
+        s_cnt = 0;
+    }
+    __syncthreads();
+    if (deg) atomicAdd(&s_deg, deg);
+    if (cnt) atomicAdd(&s_cnt, cnt);
+    __syncthreads();
+    if (threadIdx.x == 0 && pass <= P.stats_cap) {
+        if (s_cnt) atomicAdd(P.stats + 2 * (pass - 1), s_cnt);
+        if (s_deg) atomicAdd(P.stats + 2 * (pass - 1) + 1, s_deg);
+    }
+}
+
+template <bool BATCH, bool FIRST>
+__device__ __forceinline__ void det_pass(const RoundParams &P, int pass, unsigned nsmall, unsigned nchunks,
+                                         unsigned *cnt_next, unsigned *win, int lane, int gw, int nw,
+                                         unsigned long long &st_deg, unsigned long long &st_cnt) {
+    const bool odd = (pass & 1) != 0;
+    const int32_t *colc = odd ? P.col0 : P.col1;
+    int32_t *coln = odd ? P.col1 : P.col0;
+    const int32_t *smallc = odd ? P.small0 : P.small1;
+    int32_t *smalln = odd ? P.small1 : P.small0;
+    const int4 *chunkc = odd ? P.chunk0 : P.chunk1;
+    int4 *chunkn = odd ? P.chunk1 : P.chunk0;
+    for (unsigned base = static_cast<unsigned>(gw) * 32u; base < nsmall; base += static_cast<unsigned>(nw) * 32u) {
+        const unsigned i = base + lane;
+        bool lose = false;
+        int32_t V = 0, deg = 0;
+        if (i < nsmall) {
+            V = __ldcg(smallc + i);
+            lose = det_small<BATCH, FIRST>(P, colc, coln, V, deg);
+            st_deg += static_cast<unsigned long long>(deg);
+            st_cnt += 1;
+            if constexpr (BATCH) {
+                if (lose) note_graph_round(P, __ldg(P.vg + V), pass + 1);
+            }
+        }
+        warp_append(lose, V, smalln, cnt_next + kCntSmall, lane);
+    }
+    for (unsigned i = gw; i < nchunks; i += nw) {
+        const int4 it = __ldcg(chunkc + i);
+        det_chunk<BATCH, FIRST>(P, colc, coln, it, win, chunkn, cnt_next, pass, lane, st_deg, st_cnt);
+    }
+}
+
+template <bool BATCH>
+__global__ void __launch_bounds__(kBlock) det_round_kernel(RoundParams P) {
+    __shared__ unsigned s_win[kMaxWarps][kAccWords];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    unsigned *win = s_win[wib];
+    int pass = P.pass_begin;
+    for (;; ++pass) {
+        unsigned *cc = P.cnt + kCnt * (pass % 3);
+        unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
+        const unsigned nsmall = __ldcg(cc + kCntSmall), nitems = __ldcg(cc + kCntItems);
+        const unsigned nchunks = __ldcg(cc + kCntChunks);
+        if (nsmall + nitems == 0u) break;
+        if (pass >= P.pass_end) {
+            if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
+                set_error(P.err, GC_ERR_NO_CONVERGENCE, pass, 0);
+            break;
+        }
+        if (blockIdx.x == 0 && threadIdx.x < kCnt) P.cnt[kCnt * ((pass + 2) % 3) + threadIdx.x] = 0u;
+        unsigned long long st_deg = 0, st_cnt = 0;
+        if (pass == 1 && P.first_fast)
+            det_pass<BATCH, true>(P, pass, nsmall, nchunks, cn, win, lane, gw, nw, st_deg, st_cnt);
+        else
+            det_pass<BATCH, false>(P, pass, nsmall, nchunks, cn, win, lane, gw, nw, st_deg, st_cnt);
+        if (P.stats) flush_stats(P, pass, st_deg, st_cnt);
+        if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.passes[0] = pass;
+        P.passes[1] = pass - 1;
+    }
+}
+
+template <bool BATCH>
+__global__ void __launch_bounds__(kBlock) ip_round_kernel(RoundParams P) {
+    __shared__ unsigned s_win[kMaxWarps][kAccWords];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    unsigned *win = s_win[wib];
+    int32_t *col = P.col0;
+    int pass = P.pass_begin;
+    for (;; ++pass) {
+        unsigned *cc = P.cnt + kCnt * (pass % 3);
+        unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
+        const unsigned nsmall = __ldcg(cc + kCntSmall), nitems = __ldcg(cc + kCntItems);
+        const unsigned nchunks = __ldcg(cc + kCntChunks);
+        if (nsmall + nitems == 0u) break;
+        if (pass >= P.pass_end) {
+            if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
+                set_error(P.err, GC_ERR_NO_CONVERGENCE, pass, 0);
+            break;
+        }
+        if (blockIdx.x == 0 && threadIdx.x < kCnt) P.cnt[kCnt * ((pass + 2) % 3) + threadIdx.x] = 0u;
+        const bool odd = (pass & 1) != 0;
+        const int32_t *smallc = odd ? P.small0 : P.small1;
+        int32_t *smalln = odd ? P.small1 : P.small0;
+        const int4 *chunkc = odd ? P.chunk0 : P.chunk1;
+        int4 *chunkn = odd ? P.chunk1 : P.chunk0;
+        // phase 1: tentative First Fit on live colors
+        for (unsigned i = gw * 32u + lane; i < nsmall; i += nw * 32u) ip_small_assign<BATCH>(P, col, __ldcg(smallc + i));
+        for (unsigned i = gw; i < nchunks; i += nw) ip_chunk_assign<BATCH>(P, col, __ldcg(chunkc + i), win, lane);
+        if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
+        // phase 2: conflict detection
+        unsigned long long st_deg = 0, st_cnt = 0;
+        for (unsigned base = gw * 32u; base < nsmall; base += nw * 32u) {
+            const unsigned i = base + lane;
+            bool lose = false;
+            int32_t V = 0, deg = 0;
+            if (i < nsmall) {
+                V = __ldcg(smallc + i);
+                lose = ip_small_conflict<BATCH>(P, col, V, deg);
+                st_deg += static_cast<unsigned long long>(deg);
+                st_cnt += 1;
+                if constexpr (BATCH) {
+                    if (lose) note_graph_round(P, __ldg(P.vg + V), pass + 1);
+                }
+            }
+            warp_append(lose, V, smalln, cn + kCntSmall, lane);
+        }
+        for (unsigned i = gw; i < nchunks; i += nw)
+            ip_chunk_conflict<BATCH>(P, col, __ldcg(chunkc + i), chunkn, cn, pass, lane, st_deg, st_cnt);
+        if (P.stats) flush_stats(P, pass, st_deg, st_cnt);
+        if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.passes[0] = pass;
+        P.passes[1] = pass - 1;
+    }
+}
+
+// gc_color_batch: graph table, graph id of every vertex and graph_last, from the offset tables;
+// also checks the tables.  One block per graph.
+__global__ void batch_tables_kernel(RoundParams P, const int64_t *vtx_off, const int64_t *edge_off, int64_t *g_vbase,
+                                    int32_t *g_n, int64_t *g_ebase, int64_t *g_rbase, int64_t *g_m) {
+    for (int32_t g = blockIdx.x; g < P.G; g += gridDim.x) {
+        const int64_t v0 = vtx_off[g], v1 = vtx_off[g + 1];
+        const int64_t e0 = edge_off[g], e1 = edge_off[g + 1];
+        const bool ok = v1 >= v0 && e1 >= e0 && v1 <= P.n && (g != 0 || (v0 == 0 && e0 == 0));
+        if (threadIdx.x == 0) {
+            if (!ok) set_error(P.err, GC_ERR_INVALID_GRAPH, -1 - g, 0);
+            g_vbase[g] = ok ? v0 : 0;
+            g_n[g] = ok ? static_cast<int32_t>(v1 - v0) : 0;
+            g_ebase[g] = e0;
+            g_rbase[g] = v0 + g;
+            g_m[g] = e1 - e0;
+            P.graph_last[g] = (ok && v1 > v0) ? 1 : 0;
+        }
+        if (!ok) continue;
+        for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) P.vg[v] = g;
+    }
+}
+
+// Binning and initialisation of vertices [v_begin, v_end) for round P.pass_begin: priority cache,
+// initial colors, and the round's worklist split into thread-per-vertex entries (appended to the
+// current small list) and larger vertices (collected in P.items, counted in P.tmp, expanded into
+// work items by expand_kernel).  Checks each row: 0 <= rowptr[v] <= rowptr[v+1] <= entries of its
+// graph, rowptr of a graph's first vertex = 0, of its last vertex's end = its entries.
+template <bool BATCH, int MODE>
+__global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int32_t g_fixed) {
+    const int lane = threadIdx.x & 31;
+    const int pass = P.pass_begin;
+    unsigned *cc = P.cnt + kCnt * (pass % 3);
+    int32_t *small_cur = (pass & 1) ? P.small0 : P.small1;
+    const int64_t count = static_cast<int64_t>(v_end) - v_begin;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t base = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ll; base < count;
+         base += stride) {
+        const int32_t V = static_cast<int32_t>(v_begin + base + lane);
+        const bool in = base + lane < count;
+        int kind = 0;  // 1 = one thread, 2 = work items
+        int32_t nch = 0;
+        if (in) {
+            int64_t b, e, lim;
+            int32_t lv, ng;
+            if constexpr (!BATCH) {
+                b = P.rowptr[V];
+                e = P.rowptr[V + 1];
+                lim = P.nnz;
+                lv = V;
+                ng = P.n;
+            } else {
+                int32_t g = g_fixed;
+                if (g >= 0)
+                    P.vg[V] = g;
+                else
+                    g = P.vg[V];
+                lv = V - static_cast<int32_t>(P.g_vbase[g]);
+                ng = P.g_n[g];
+                const int32_t *rp = P.rowptr + P.g_rbase[g];
+                b = rp[lv];
+                e = rp[lv + 1];
+                lim = P.g_m[g];
+            }
+            const bool ok = b >= 0 && b <= e && e <= lim && (lv != 0 || b == 0) && (lv != ng - 1 || e == lim);
+            if (!ok) set_error(P.err, GC_ERR_INVALID_GRAPH, V, b);
+            const int64_t d = ok ? e - b : 0;
+            P.prio[V] = static_cast<uint32_t>(vertex_hash(P.seed, static_cast<uint32_t>(lv)) >> 32);
+            if (MODE == GC_MODE_DETERMINISTIC) {
+                P.col0[V] = 0;
+                P.col1[V] = 0;
+            } else {
+                P.col0[V] = d == 0 ? 0 : -1;
+            }
+            if (d > 0) {
+                kind = d <= P.T1 ? 1 : 2;
+                nch = static_cast<int32_t>((d + P.CH - 1) / P.CH);
+            }
+        }
+        if constexpr (BATCH) {
+            if (g_fixed >= 0 && kind != 0) note_graph_round(P, g_fixed, pass);
+        }
+        warp_append(kind == 1, V, small_cur, cc + kCntSmall, lane);
+        const unsigned m = __ballot_sync(kFull, kind == 2);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            const unsigned chunks = __reduce_add_sync(kFull, kind == 2 ? static_cast<unsigned>(nch) : 0u);
+            unsigned ib = 0;
+            if (lane == leader) {
+                ib = atomicAdd(P.tmp + 0, static_cast<unsigned>(__popc(m)));
+                atomicAdd(P.tmp + 1, chunks);
+            }
+            ib = __shfl_sync(kFull, ib, leader);
+            if (kind == 2) P.items[ib + __popc(m & lanemask_lt())] = V;
+        }
+    }
+}
+
+// Expands the larger vertices collected by setup into work items of round P.pass_begin, with
+// accumulator slots after those already taken in that round.  One warp per vertex.
+template <bool BATCH>
+__global__ void expand_kernel(RoundParams P, int32_t n_items) {
+    if (n_items < 0) n_items = static_cast<int32_t>(__ldcg(P.tmp));  // count left on the device by setup
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int pass = P.pass_begin;
+    unsigned *cc = P.cnt + kCnt * (pass % 3);
+    int4 *chunk_cur = (pass & 1) ? P.chunk0 : P.chunk1;
+    for (int32_t s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n_items; s += nw) {
+        const int32_t V = P.items[s];
+        const Row r = load_row<BATCH>(P, V);
+        const int32_t deg = static_cast<int32_t>(r.e - r.b);
+        const int32_t nch = (deg + P.CH - 1) / P.CH;
+        unsigned slot = 0, cb = 0;
+        if (lane == 0) {
+            slot = atomicAdd(cc + kCntItems, 1u);
+            cb = atomicAdd(cc + kCntChunks, static_cast<unsigned>(nch));
+        }
+        slot = __shfl_sync(kFull, slot, 0);
+        cb = __shfl_sync(kFull, cb, 0);
+        P.acc[static_cast<size_t>(slot) * kAccStride + lane] = 0u;
+        for (int32_t q = lane; q < nch; q += 32) chunk_cur[cb + q] = make_int4(V, q, static_cast<int32_t>(slot), nch);
+    }
+}
+
+// Final statistics over vertices [v_begin, v_end): one bit per (graph, color), largest color per
+// graph, and an optional copy of the colors.
+template <bool BATCH>
+__global__ void count_mark_kernel(RoundParams P, const int32_t *colors_sel, int32_t v_begin, int32_t v_end,
+                                  unsigned *bitmap, int32_t *gmax, int32_t *out) {
+    const int32_t *colors = (colors_sel && (*colors_sel & 1)) ? P.col1 : P.col0;
+    const bool copy = out != nullptr && P.err[0] == 0;
+    const int64_t count = static_cast<int64_t>(v_end) - v_begin;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const int32_t V = static_cast<int32_t>(v_begin + i);
+        const int32_t c = __ldcg(colors + V);
+        if (copy) out[i] = c;
+        if (c < 0) continue;
+        int32_t g = 0;
+        int64_t bit = c;
+        if constexpr (BATCH) {
+            g = P.vg[V];
+            bit += P.g_vbase[g];
+        }
+        const unsigned m = 1u << (bit & 31);
+        unsigned *w = bitmap + (bit >> 5);
+        if (!(__ldcg(w) & m)) atomicOr(w, m);
+        if (__ldcg(gmax + g) < c) atomicMax(gmax + g, c);
+    }
+}
+
+// Distinct colors of graphs [g_begin, g_end): popcount of bits [base, base + gmax[g] + 1) where base
+// is the graph's first vertex id (colors of graph g are < its vertex count).  One warp per graph.
+template <bool BATCH>
+__global__ void count_pop_kernel(RoundParams P, int32_t g_begin, int32_t g_end, const unsigned *bitmap,
+                                 const int32_t *gmax, int32_t *gcount) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int32_t g = g_begin + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < g_end; g += nw) {
+        const int64_t lo = BATCH ? P.g_vbase[g] : 0;
+        const int64_t hi = lo + static_cast<int64_t>(gmax[g]) + 1;  // gmax = -1 for an empty graph
+        unsigned cnt = 0;
+        if (hi > lo) {
+            for (int64_t w = (lo >> 5) + lane; w <= ((hi - 1) >> 5); w += 32) {
+                unsigned x = bitmap[w];
+                const int64_t wb = w << 5;
+                if (wb < lo) x &= ~0u << (lo - wb);
+                if (hi - wb < 32) x &= (1u << (hi - wb)) - 1u;
+                cnt += __popc(x);
+            }
+        }
+        cnt = __reduce_add_sync(kFull, cnt);
+        if (lane == 0) gcount[g] = static_cast<int32_t>(cnt);
+    }
+}
+
+// Graph-format check (gc_validate_graph); one warp per vertex.
+__global__ void validate_kernel(int32_t n, const int32_t *rowptr, const int32_t *colidx, int flags, int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int64_t nnz = rowptr[n];
+    for (int32_t v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += nw) {
+        const int64_t b = rowptr[v], e = rowptr[v + 1];
+        if (b < 0 || e < b || e > nnz || (v == 0 && b != 0)) {
+            if (lane == 0) set_error(err, GC_ERR_INVALID_GRAPH, v, b);
+            continue;
+        }
+        for (int64_t j = b + lane; j < e; j += 32) {
+            const int32_t u = colidx[j];
+            if (u < 0 || u >= n || u == v) {
+                set_error(err, GC_ERR_INVALID_GRAPH, v, j);
+                continue;
+            }
+            if ((flags & GC_VALIDATE_SORTED) && j > b && colidx[j - 1] >= u) set_error(err, GC_ERR_INVALID_GRAPH, v, j);
+            if (flags & GC_VALIDATE_SYMMETRIC) {
+                int64_t lo = rowptr[u], hi = rowptr[u + 1];
+                if (lo < 0 || hi < lo || hi > nnz) continue;  // that row reports itself
+                bool found = false;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    const int32_t x = colidx[mid];
+                    if (x == v) {
+                        found = true;
+                        break;
+                    }
+                    if (x < v)
+                        lo = mid + 1;
+                    else
+                        hi = mid;
+                }
+                if (!found) set_error(err, GC_ERR_INVALID_GRAPH, v, j);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// launch wrappers
+
+static int grid_for(int64_t work, int block, int cap) {
+    int64_t g = (work + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return static_cast<int>(g);
+}
+
+static int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+cudaError_t launch_batch_tables(const RoundParams &P, const int64_t *vtx_off, const int64_t *edge_off,
+                                int64_t *g_vbase, int32_t *g_n, int64_t *g_ebase, int64_t *g_rbase, int64_t *g_m,
+                                cudaStream_t s) {
+    batch_tables_kernel<<<grid_for(P.G, 1, 65535), 256, 0, s>>>(P, vtx_off, edge_off, g_vbase, g_n, g_ebase, g_rbase,
+                                                                g_m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup(const RoundParams &P, int mode, bool batch, int32_t v_begin, int32_t v_end,
+                         int32_t g_fixed, cudaStream_t s) {
+    if (v_end <= v_begin) return cudaSuccess;
+    const int grid = grid_for(static_cast<int64_t>(v_end) - v_begin, 256, sm_count() * 16);
+    if (batch) {
+        if (mode == GC_MODE_DETERMINISTIC)
+            setup_kernel<true, GC_MODE_DETERMINISTIC><<<grid, 256, 0, s>>>(P, v_begin, v_end, g_fixed);
+        else
+            setup_kernel<true, GC_MODE_INPLACE><<<grid, 256, 0, s>>>(P, v_begin, v_end, g_fixed);
+    } else {
+        if (mode == GC_MODE_DETERMINISTIC)
+            setup_kernel<false, GC_MODE_DETERMINISTIC><<<grid, 256, 0, s>>>(P, v_begin, v_end, g_fixed);
+        else
+            setup_kernel<false, GC_MODE_INPLACE><<<grid, 256, 0, s>>>(P, v_begin, v_end, g_fixed);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const RoundParams &P, bool batch, int32_t n_items, cudaStream_t s) {
+    if (n_items == 0) return cudaSuccess;
+    const int grid = n_items < 0 ? sm_count() * 8 : grid_for(static_cast<int64_t>(n_items) * 32, 256, sm_count() * 16);
+    if (batch)
+        expand_kernel<true><<<grid, 256, 0, s>>>(P, n_items);
+    else
+        expand_kernel<false><<<grid, 256, 0, s>>>(P, n_items);
+    return cudaGetLastError();
+}
+
+static const void *round_kernel_fn(int mode, bool batch) {
+    if (mode == GC_MODE_DETERMINISTIC)
+        return batch ? reinterpret_cast<const void *>(&det_round_kernel<true>)
+                     : reinterpret_cast<const void *>(&det_round_kernel<false>);
+    return batch ? reinterpret_cast<const void *>(&ip_round_kernel<true>)
+                 : reinterpret_cast<const void *>(&ip_round_kernel<false>);
+}
+
+cudaError_t round_kernel_occupancy(int mode, bool batch, int block, int *blocks_per_sm) {
+    if (block != kBlock) return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, round_kernel_fn(mode, batch), block, 0);
+}
+
+cudaError_t launch_rounds(const RoundParams &P, int mode, bool batch, int grid, int block, cudaStream_t s) {
+    if (block != kBlock) return cudaErrorInvalidValue;
+    RoundParams arg = P;
+    void *args[] = {&arg};
+    return cudaLaunchCooperativeKernel(round_kernel_fn(mode, batch), dim3(grid), dim3(block), args, 0, s);
+}
+
+cudaError_t launch_count_colors(const RoundParams &P, bool batch, const int32_t *colors_sel, int32_t v_begin,
+                                int32_t v_end, int32_t g_begin, int32_t g_end, unsigned *bitmap, int32_t *gmax,
+                                int32_t *gcount, int32_t *out, cudaStream_t s) {
+    if (v_end > v_begin) {
+        const int grid = grid_for(static_cast<int64_t>(v_end) - v_begin, 256, sm_count() * 8);
+        if (batch)
+            count_mark_kernel<true><<<grid, 256, 0, s>>>(P, colors_sel, v_begin, v_end, bitmap, gmax, out);
+        else
+            count_mark_kernel<false><<<grid, 256, 0, s>>>(P, colors_sel, v_begin, v_end, bitmap, gmax, out);
+    }
+    if (g_end > g_begin) {
+        const int pgrid = grid_for(static_cast<int64_t>(g_end - g_begin) * 32, 256, sm_count() * 8);
+        if (batch)
+            count_pop_kernel<true><<<pgrid, 256, 0, s>>>(P, g_begin, g_end, bitmap, gmax, gcount);
+        else
+            count_pop_kernel<false><<<pgrid, 256, 0, s>>>(P, g_begin, g_end, bitmap, gmax, gcount);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(int32_t n, const int32_t *rowptr, const int32_t *colidx, int flags, int32_t *err,
+                            cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int grid = grid_for(static_cast<int64_t>(n) * 32, 256, sm_count() * 16);
+    validate_kernel<<<grid, 256, 0, s>>>(n, rowptr, colidx, flags, err);
+    return cudaGetLastError();
+}
+
+}  // namespace gc

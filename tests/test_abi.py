@@ -1,0 +1,35 @@
+"""The C ABI library builds for sm_103a, loads, and exports every function include/gc.h declares.
+No compute calls are made (this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "gc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gc_\w+)\s*\(", text)))
+
+
+def test_header_is_plain_c():
+    text = open(os.path.join(ROOT, "include", "gc.h")).read()
+    assert 'extern "C"' in text
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    for bad in ("torch", "at::", "c10", "std::"):
+        assert bad not in text
+
+
+def test_library_exports_every_declared_symbol(gclib):
+    lib = ctypes.CDLL(gclib.LIB_PATH)
+    names = declared_functions()
+    assert "gc_color" in names and "gc_color_batch" in names and "gc_server_submit" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_error_string(gclib):
+    lib = gclib.load()
+    assert lib.gc_version() >= 100
+    assert isinstance(lib.gc_last_error(), bytes)

@@ -1,0 +1,112 @@
+"""Deterministic mode on the GPU versus the CPU oracle: bit-exact colors, color count, round count and
+per-round worklist statistics (Algorithm 1, Section 3.1, with the hash-priority reading)."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(g):
+    import torch
+    return (torch.from_numpy(np.ascontiguousarray(g.rowptr)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(g.colidx if g.nnz else np.zeros(0, np.int32))).cuda())
+
+
+def run_det(gc, g, seed, options=None, stats=False):
+    rp, ci = _dev(g)
+    r = gc.color(rp, ci, "det", seed, options=options, stats=stats)
+    return r.colors.cpu().numpy(), r.ncolors, r.rounds, r.stats
+
+
+def assert_parity(gc, g, seed, options=None, check_stats=True):
+    ref = oracle.det(g, seed)
+    assert ref.status == 0
+    colors, nc, rounds, st = run_det(gc, g, seed, options=options, stats=check_stats)
+    np.testing.assert_array_equal(colors, ref.colors, err_msg=f"{g.name} seed {seed}")
+    assert nc == ref.ncolors
+    assert rounds == ref.rounds
+    if check_stats and g.n > 0:
+        np.testing.assert_array_equal(st.wl_size, ref.wl_size)
+        np.testing.assert_array_equal(st.wl_degsum, ref.wl_degsum)
+    return ref
+
+
+SPECIAL = [
+    lambda: gg.complete(1), lambda: gg.complete(2), lambda: gg.complete(5), lambda: gg.complete(33),
+    lambda: gg.complete(40), lambda: gg.complete(200), lambda: gg.path(2), lambda: gg.path(97),
+    lambda: gg.cycle(3), lambda: gg.cycle(1000), lambda: gg.star(31), lambda: gg.star(32),
+    lambda: gg.star(5000), lambda: gg.crown(40), lambda: gg.crown(40, interleaved=False), lambda: gg.empty(1),
+    lambda: gg.empty(77), lambda: gg.grid5(7, 9), lambda: gg.stencil27(4), lambda: gg.stencil27(9),
+]
+
+
+@pytest.mark.parametrize("make", SPECIAL)
+@pytest.mark.parametrize("seed", [0, 7])
+def test_special_graphs(gclib, make, seed):
+    assert_parity(gclib, make(), seed)
+
+
+def test_er10k_seed7(gclib):
+    # Erdos-Renyi n=10,000, average degree 16, edges from seed 1, hash seed 7
+    assert_parity(gclib, gg.workload("er10k"), 7)
+
+
+@pytest.mark.parametrize("scale", [8, 12, 15])
+@pytest.mark.parametrize("seed", [1, 7, 2**63 + 5])
+def test_rmat_small(gclib, scale, seed):
+    assert_parity(gclib, gg.rmat(scale, 16, 2), seed)
+
+
+def test_ragged_er(gclib):
+    for n, d in [(31, 3.0), (33, 5.0), (777, 9.0), (4099, 40.0)]:
+        assert_parity(gclib, gg.er(n, d, 11), 3)
+
+
+def test_isolated_mixed(gclib):
+    # graph with isolated vertices interleaved with a dense core
+    edges = [(i, j) for i in range(0, 60, 2) for j in range(i + 2, 60, 2)]
+    assert_parity(gclib, gg.from_edges(61, edges), 5)
+
+
+def test_window_rescan_dense(gclib):
+    # K_600: colors reach 599, beyond the 512-color window of the work-item path
+    ref = assert_parity(gclib, gg.complete(600), 9, check_stats=False)
+    assert ref.ncolors == 600 and ref.rounds == 600
+
+
+@pytest.mark.parametrize("opt", [
+    dict(small_max_degree=1), dict(small_max_degree=8), dict(small_max_degree=63), dict(chunk=32),
+    dict(chunk=64), dict(chunk=256), dict(chunk=1024), dict(blocks_per_sm=1), dict(blocks_per_sm=2),
+    dict(small_max_degree=4, chunk=32, blocks_per_sm=1),
+])
+def test_launch_configuration_invariance(gclib, opt):
+    g = gg.rmat(13, 16, 2)
+    assert_parity(gclib, g, 7, options=gclib.Options(**opt))
+
+
+def test_host_arrays_match_device(gclib):
+    g = gg.rmat(12, 16, 2)
+    ref = oracle.det(g, 7)
+    r = gclib.color(g.rowptr, g.colidx, "det", 7)  # numpy in, numpy out (staged by the library)
+    assert isinstance(r.colors, np.ndarray)
+    np.testing.assert_array_equal(r.colors, ref.colors)
+    assert (r.ncolors, r.rounds) == (ref.ncolors, ref.rounds)
+
+
+def test_zero_vertices(gclib):
+    r = gclib.color(np.zeros(1, np.int32), np.zeros(0, np.int32), "det", 1)
+    assert (r.ncolors, r.rounds) == (0, 0)
+
+
+def test_repeatable_and_properties(gclib):
+    g = gg.rmat(14, 16, 2)
+    a = run_det(gclib, g, 7)
+    b = run_det(gclib, g, 7)
+    np.testing.assert_array_equal(a[0], b[0])
+    colors = a[0]
+    assert oracle.count_conflicts(g, colors) == 0
+    assert np.all(colors <= g.degrees())
+    assert a[2] >= colors.max() + 1  # a color c first appears in round c+1 or later

@@ -1,0 +1,195 @@
+"""In-place mode invariants, batched coloring and boundary errors on the GPU.
+
+In-place mode reads neighbour colors live (as the paper's threads do, Algorithm 1 phase 1), so its
+coloring is not unique: it is checked for what Lemma 1 and Section 2.1 fix (a proper coloring,
+color(v) <= deg(v), hence at most Delta+1 colors) and for termination within n rounds.  Batched
+deterministic coloring must equal the oracle per graph, bit for bit."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def check_inplace(gc, g, seed=3):
+    r = gc.color(_dev(g.rowptr), _dev(g.colidx if g.nnz else np.zeros(0, np.int32)), "inplace", seed)
+    c = r.colors.cpu().numpy()
+    assert oracle.count_conflicts(g, c) == 0, g.name
+    if g.n:
+        assert c.min() >= 0
+        assert np.all(c <= g.degrees())
+    assert r.ncolors == oracle.distinct_colors(c)
+    assert (g.n == 0 and r.rounds == 0) or 1 <= r.rounds <= g.n
+    return r
+
+
+@pytest.mark.parametrize("make", [
+    lambda: gg.complete(70), lambda: gg.complete(600), lambda: gg.star(3000), lambda: gg.cycle(1001),
+    lambda: gg.crown(50), lambda: gg.empty(10), lambda: gg.stencil27(12), lambda: gg.workload("er10k"),
+    lambda: gg.rmat(15, 16, 2), lambda: gg.grid5(100, 37),
+])
+def test_inplace_invariants(gclib, make):
+    check_inplace(gclib, make())
+
+
+def test_inplace_options(gclib):
+    g = gg.rmat(13, 16, 2)
+    for opt in [dict(small_max_degree=2), dict(chunk=32), dict(blocks_per_sm=1)]:
+        r = gclib.color(_dev(g.rowptr), _dev(g.colidx), "inplace", 1, options=gclib.Options(**opt))
+        assert oracle.count_conflicts(g, r.colors.cpu().numpy()) == 0
+
+
+def _mixed_graphs():
+    gs = [gg.complete(3), gg.empty(4), gg.star(40), gg.workload("er10k"), gg.rmat(12, 12, 5), gg.cycle(9),
+          gg.crown(20), gg.complete(300), gg.stencil27(5), gg.empty(1), gg.path(2)]
+    gs += [gg.make_from_spec(s) for s in gg.batch_specs(12, 3, nmin=100, nmax=20_000)]
+    return gs
+
+
+def test_batch_det_matches_oracle_per_graph(gclib):
+    gs = _mixed_graphs()
+    b = gg.pack(gs)
+    colors, nc, rd = gclib.color_batch(_dev(b.vtx_off), _dev(b.edge_off), _dev(b.rowptr), _dev(b.colidx), "det", 7)
+    colors = colors.cpu().numpy()
+    for i, g in enumerate(gs):
+        ref = oracle.det(g, 7)
+        np.testing.assert_array_equal(colors[b.vtx_off[i]:b.vtx_off[i + 1]], ref.colors, err_msg=f"graph {i}")
+        assert nc[i] == ref.ncolors and rd[i] == ref.rounds, (i, nc[i], ref.ncolors, rd[i], ref.rounds)
+
+
+def test_batch_host_arrays_and_empty_graphs(gclib):
+    gs = [gg.empty(0), gg.complete(4), gg.empty(0), gg.cycle(5), gg.empty(0)]
+    b = gg.pack(gs)
+    colors, nc, rd = gclib.color_batch(b.vtx_off, b.edge_off, b.rowptr, b.colidx, "det", 1)
+    assert list(nc) == [0, 4, 0, 3, 0]
+    assert rd[0] == 0 and rd[2] == 0 and rd[4] == 0
+    for i, g in enumerate(gs):
+        ref = oracle.det(g, 1)
+        np.testing.assert_array_equal(colors[b.vtx_off[i]:b.vtx_off[i + 1]], ref.colors)
+        assert rd[i] == ref.rounds
+
+
+def test_batch_inplace_proper(gclib):
+    gs = _mixed_graphs()
+    b = gg.pack(gs)
+    colors, nc, rd = gclib.color_batch(_dev(b.vtx_off), _dev(b.edge_off), _dev(b.rowptr), _dev(b.colidx),
+                                       "inplace", 7)
+    colors = colors.cpu().numpy()
+    for i, g in enumerate(gs):
+        c = colors[b.vtx_off[i]:b.vtx_off[i + 1]]
+        assert oracle.count_conflicts(g, c) == 0
+        assert nc[i] == oracle.distinct_colors(c)
+
+
+def test_batch_equals_solo(gclib):
+    gs = [gg.make_from_spec(s) for s in gg.batch_specs(8, 3, nmin=1000, nmax=50_000)]
+    b = gg.pack(gs)
+    colors, nc, rd = gclib.color_batch(_dev(b.vtx_off), _dev(b.edge_off), _dev(b.rowptr), _dev(b.colidx), "det", 7)
+    colors = colors.cpu().numpy()
+    for i, g in enumerate(gs):
+        r = gclib.color(_dev(g.rowptr), _dev(g.colidx), "det", 7)
+        np.testing.assert_array_equal(colors[b.vtx_off[i]:b.vtx_off[i + 1]], r.colors.cpu().numpy())
+        assert (nc[i], rd[i]) == (r.ncolors, r.rounds)
+
+
+# ---------------------------------------------------------------------------------------------
+# boundary errors: right status, outputs untouched, device still usable
+
+def _expect(gc, status, rowptr, colidx, mode="det", **kw):
+    out = np.full(max(len(rowptr) - 1, 1), -77, np.int32)[: max(len(rowptr) - 1, 0)]
+    with pytest.raises(gc.GCError) as ei:
+        gc.color(rowptr, colidx, mode, 1, out=out, **kw)
+    assert ei.value.status == status, str(ei.value)
+    assert np.all(out == -77)
+
+
+@pytest.mark.parametrize("mode", ["det", "inplace"])
+def test_malformed_graphs(gclib, mode):
+    ok = gg.cycle(6)
+    bad = ok.colidx.copy()
+    bad[3] = 6  # out of range
+    _expect(gclib, gclib.GC_ERR_INVALID_GRAPH, ok.rowptr, bad, mode)
+    bad = ok.colidx.copy()
+    bad[0] = -1
+    _expect(gclib, gclib.GC_ERR_INVALID_GRAPH, ok.rowptr, bad, mode)
+    bad = ok.colidx.copy()
+    bad[0] = 0  # self-loop on vertex 0
+    _expect(gclib, gclib.GC_ERR_INVALID_GRAPH, ok.rowptr, bad, mode)
+    rp = ok.rowptr.copy()
+    rp[2], rp[3] = rp[3], rp[2]  # non-monotone
+    _expect(gclib, gclib.GC_ERR_INVALID_GRAPH, rp, ok.colidx, mode)
+    rp = ok.rowptr.copy()
+    rp[0] = 1
+    _expect(gclib, gclib.GC_ERR_INVALID_GRAPH, rp, ok.colidx, mode)
+    # big graph with one bad entry deep inside a hub row (work-item path)
+    g = gg.star(4000)
+    bad = g.colidx.copy()
+    bad[3000] = 0
+    _expect(gclib, gclib.GC_ERR_INVALID_GRAPH, g.rowptr, bad, mode)
+    # the device is still usable
+    r = gclib.color(ok.rowptr, ok.colidx, mode, 1)
+    assert r.ncolors == 2
+
+
+def test_bad_arguments(gclib):
+    with pytest.raises(gclib.GCError) as ei:
+        gclib.color(np.zeros(3, np.int32), np.zeros(0, np.int32), "det", 1, options=gclib.Options(chunk=48))
+    assert ei.value.status == gclib.GC_ERR_INVALID_ARG
+    with pytest.raises(gclib.GCError) as ei:
+        gclib.color(np.zeros(3, np.int32), np.zeros(0, np.int32), 5, 1)
+    assert ei.value.status == gclib.GC_ERR_INVALID_ARG
+    lib = gclib.load()
+    assert lib.gc_color(-1, None, None, 0, 0, None, None, None) == gclib.GC_ERR_INVALID_ARG
+    assert lib.gc_color(3, None, None, 0, 0, None, None, None) == gclib.GC_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("mode", ["det", "inplace"])
+def test_round_cap(gclib, mode):
+    g = gg.complete(10)  # needs 10 rounds in deterministic mode
+    if mode == "det":
+        _expect(gclib, gclib.GC_ERR_NO_CONVERGENCE, g.rowptr, g.colidx, mode, options=gclib.Options(max_rounds=3))
+    r = gclib.color(g.rowptr, g.colidx, mode, 1, options=gclib.Options(max_rounds=10))
+    assert r.ncolors == 10
+
+
+@pytest.mark.parametrize("mode", ["det", "inplace"])
+def test_barrier_wait_limit(gclib, mode):
+    # a 1 ns limit makes every early block give up at the first grid barrier: the call must
+    # report GC_ERR_TIMEOUT, leave the output untouched, and the next call must work
+    g = gg.rmat(14, 16, 2)
+    _expect(gclib, gclib.GC_ERR_TIMEOUT, g.rowptr, g.colidx, mode, options=gclib.Options(spin_limit_ns=1))
+    ref = oracle.det(g, 1)
+    r = gclib.color(g.rowptr, g.colidx, "det", 1)
+    np.testing.assert_array_equal(r.colors, ref.colors)
+
+
+def test_validate(gclib):
+    g = gg.rmat(10, 8, 1)
+    gclib.validate(g.rowptr, g.colidx)
+    # asymmetric: drop one direction of an edge
+    v = 5
+    row = g.colidx[g.rowptr[v]:g.rowptr[v + 1]]
+    u = int(row[0])
+    keep = np.ones(g.nnz, bool)
+    keep[g.rowptr[v]] = False
+    rp = g.rowptr.copy()
+    rp[v + 1:] -= 1
+    with pytest.raises(gclib.GCError) as ei:
+        gclib.validate(rp, g.colidx[keep])
+    assert ei.value.status == gclib.GC_ERR_INVALID_GRAPH
+    assert u >= 0
+    # unsorted row
+    ci = g.colidx.copy()
+    big = int(np.argmax(g.degrees()))
+    a, b = g.rowptr[big], g.rowptr[big + 1]
+    ci[a:b] = ci[a:b][::-1]
+    with pytest.raises(gclib.GCError):
+        gclib.validate(g.rowptr, ci, gclib.VALIDATE_SORTED)
+    gclib.validate(g.rowptr, ci, 0)  # range and self-loop checks alone pass

@@ -1,0 +1,89 @@
+"""Continuous-batching server: every request's result equals the oracle (deterministic mode) or is
+a proper coloring (in-place mode), whether it ran alone or joined a batch already on the GPU."""
+import time
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _graphs():
+    gs = [gg.complete(7), gg.empty(5), gg.star(300), gg.cycle(11), gg.crown(25), gg.complete(260),
+          gg.grid5(30, 20), gg.workload("er10k")]
+    gs += [gg.make_from_spec(s) for s in gg.batch_specs(14, 4, nmin=1000, nmax=60_000)]
+    return gs
+
+
+def test_server_det_matches_oracle_staggered(gclib):
+    gs = _graphs()
+    refs = [oracle.det(g, 7) for g in gs]
+    with gclib.Server(pool_vertices=2_000_000, pool_entries=40_000_000, mode="det", seed=7) as srv:
+        ids = []
+        for i, g in enumerate(gs):
+            ids.append(srv.submit(g.rowptr, g.colidx))
+            if i % 5 == 4:
+                time.sleep(0.002)  # later requests arrive while earlier ones are resident
+        for g, ref, rid in zip(gs, refs, ids):
+            colors, nc, rounds = srv.poll(rid, timeout_ms=-1)
+            np.testing.assert_array_equal(colors, ref.colors, err_msg=g.name)
+            assert (nc, rounds) == (ref.ncolors, ref.rounds), g.name
+        st = srv.stats()
+        assert st["completed"] == len(gs) and st["queued"] == 0 and st["resident"] == 0
+        assert st["p99_ms"] >= st["p50_ms"] > 0
+        # the batch overlapped requests: fewer batched rounds than rounds summed over requests
+        assert st["rounds_run"] < sum(r.rounds for r in refs)
+
+
+def test_server_small_pool_queues_and_admits(gclib):
+    gs = [gg.make_from_spec(s) for s in gg.batch_specs(10, 8, nmin=5000, nmax=30_000)]
+    pv = max(g.n for g in gs) + 10
+    pe = max(g.nnz for g in gs) + 10
+    with gclib.Server(pool_vertices=pv, pool_entries=pe, mode="det", seed=3) as srv:
+        ids = [srv.submit(g.rowptr, g.colidx) for g in gs]
+        for g, rid in zip(gs, ids):
+            colors, nc, rounds = srv.poll(rid)
+            ref = oracle.det(g, 3)
+            np.testing.assert_array_equal(colors, ref.colors)
+            assert rounds == ref.rounds
+
+
+def test_server_inplace_proper(gclib):
+    gs = _graphs()[:12]
+    with gclib.Server(pool_vertices=1_000_000, pool_entries=20_000_000, mode="inplace", seed=1) as srv:
+        ids = [srv.submit(g.rowptr, g.colidx) for g in gs]
+        for g, rid in zip(gs, ids):
+            colors, nc, rounds = srv.poll(rid)
+            assert oracle.count_conflicts(g, colors) == 0
+            assert nc == oracle.distinct_colors(colors)
+
+
+def test_server_rejects(gclib):
+    with gclib.Server(pool_vertices=1000, pool_entries=10_000, mode="det") as srv:
+        big = gg.er(5000, 4, 1)
+        with pytest.raises(gclib.GCError) as ei:
+            srv.submit(big.rowptr, big.colidx)
+        assert ei.value.status == gclib.GC_ERR_OOM
+        g = gg.cycle(6)
+        bad = g.colidx.copy()
+        bad[0] = 0
+        with pytest.raises(gclib.GCError) as ei:
+            srv.submit(g.rowptr, bad)
+        assert ei.value.status == gclib.GC_ERR_INVALID_GRAPH
+        rid = srv.submit(g.rowptr, g.colidx)
+        colors, nc, rounds = srv.poll(rid)
+        assert nc == 2 and srv.stats()["rejected"] == 1
+
+
+def test_server_device_inputs(gclib):
+    import torch
+    g = gg.rmat(12, 16, 2)
+    with gclib.Server(pool_vertices=100_000, pool_entries=2_000_000, mode="det", seed=7) as srv:
+        rid = srv.submit(torch.from_numpy(g.rowptr).cuda(), torch.from_numpy(g.colidx).cuda())
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        _, nc, rounds = srv.poll(rid, out=out)
+        ref = oracle.det(g, 7)
+        np.testing.assert_array_equal(out.cpu().numpy(), ref.colors)

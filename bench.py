@@ -210,7 +210,7 @@ def main():
 
     # roofline of the dominant kernel (the persistent round kernel): algorithmic bytes per launch
     st = r0.stats
-    E = st.entries_scanned if mode == "det" else st.entries_scanned // 2
+    E = int(st.wl_degsum.sum())  # sum over rounds of sum_{v in W_r} deg(v)
     WT = st.worklist_total
     per_sweep = 4 * E + 20 * WT + 4 * (WT - g.n)
     alg_bytes = per_sweep if mode == "det" else 2 * (4 * E + 16 * WT) + 4 * (WT - g.n)

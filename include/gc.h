@@ -73,6 +73,8 @@ enum { GC_MODE_DETERMINISTIC = 0, GC_MODE_INPLACE = 1 };
 #define GC_FLAG_STATS 1u     /* fill gc_stats' per-round worklist sizes and scanned entries */
 #define GC_FLAG_TIMING 2u    /* record CUDA events around the round kernel (gc_stats.kernel_ms) */
 #define GC_FLAG_VALIDATE 4u  /* run gc_validate_graph(GC_VALIDATE_ALL) before coloring */
+#define GC_FLAG_COMPACT 8u  /* deterministic mode: skip adjacency entries whose neighbour is already final
+                               (same results; reads fewer entries but adds per-work-item bookkeeping) */
 
 /* Flags for gc_validate_graph */
 #define GC_VALIDATE_SORTED 1     /* rows strictly increasing (implies no duplicate entries) */
@@ -84,7 +86,7 @@ typedef struct gc_options {
     void *stream;              /* cudaStream_t to run on; NULL = the context's own stream */
     int32_t max_rounds;        /* round cap; 0 = n + 1 (a worklist shrinks every round) */
     int32_t small_max_degree;  /* vertices up to this degree get one thread each (1..63); default 32 */
-    int32_t chunk;             /* edges per warp work item for larger vertices (32..1024, multiple of 32); default 128 */
+    int32_t chunk;             /* adjacency entries per warp work item for larger vertices (32..1024, multiple of 32); default 1024 */
     int32_t block_size;        /* threads per block of the round kernel (128, 256 or 512); default 256 */
     int32_t blocks_per_sm;     /* resident blocks per SM for the round kernel; 0 = occupancy maximum */
     int64_t spin_limit_ns;     /* grid-barrier wait limit in ns; 0 = 1e9.  A wait that runs out makes
@@ -94,8 +96,8 @@ typedef struct gc_options {
 } gc_options;
 
 /* Optional run statistics (gc_color_ex / gc_color_batch_ex).  The caller may provide arrays
- * wl_size / wl_degsum of round_cap entries; entry r-1 receives |W_r| and the sum of deg(v) over W_r
- * for round r (GC_FLAG_STATS). */
+ * wl_size / wl_degsum / round_ns of round_cap entries; entry r-1 receives |W_r|, the sum of deg(v)
+ * over W_r and the round's duration for round r (GC_FLAG_STATS). */
 typedef struct gc_stats {
     int32_t rounds;            /* rounds executed (largest over the batch for gc_color_batch_ex) */
     int32_t ncolors;           /* distinct colors (sum over the batch for gc_color_batch_ex) */
@@ -103,8 +105,10 @@ typedef struct gc_stats {
     int32_t round_cap;         /* capacity of wl_size / wl_degsum (input) */
     int64_t *wl_size;          /* caller array or NULL */
     int64_t *wl_degsum;        /* caller array or NULL */
+    int64_t *round_ns;         /* caller array or NULL: device time of each round in ns (GC_FLAG_STATS) */
     int64_t worklist_total;    /* sum over rounds of |W_r| (GC_FLAG_STATS) */
-    int64_t entries_scanned;   /* adjacency entries read by the round kernel (GC_FLAG_STATS) */
+    int64_t entries_scanned;   /* adjacency entries the round kernel read (GC_FLAG_STATS); without
+                                  compaction this is sum_r sum_{v in W_r} deg(v) (twice that in-place) */
     float kernel_ms;           /* round-kernel device time (GC_FLAG_TIMING) */
     float setup_ms;            /* binning/setup kernel device time (GC_FLAG_TIMING) */
     int32_t grid_blocks;       /* blocks of the persistent round kernel */

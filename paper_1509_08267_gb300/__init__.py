@@ -40,6 +40,7 @@ MODE_INPLACE = 1
 FLAG_STATS = 1
 FLAG_TIMING = 2
 FLAG_VALIDATE = 4
+FLAG_COMPACT = 8
 VALIDATE_SORTED = 1
 VALIDATE_SYMMETRIC = 2
 VALIDATE_ALL = 3
@@ -60,6 +61,7 @@ class _Options(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int32), ("ncolors", ctypes.c_int32), ("max_color", ctypes.c_int32),
                 ("round_cap", ctypes.c_int32), ("wl_size", ctypes.c_void_p), ("wl_degsum", ctypes.c_void_p),
+                ("round_ns", ctypes.c_void_p),
                 ("worklist_total", ctypes.c_int64), ("entries_scanned", ctypes.c_int64), ("kernel_ms", ctypes.c_float),
                 ("setup_ms", ctypes.c_float), ("grid_blocks", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 6)]
@@ -214,6 +216,7 @@ class Stats:
     block_size: int = 0
     wl_size: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
     wl_degsum: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
+    round_ns: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
 
 
 def _mode(mode) -> int:
@@ -252,16 +255,18 @@ def color(rowptr, colidx, mode="det", seed: int = 0, out=None, options: Options 
     st = _Stats()
     wl = np.zeros(round_cap, np.int64)
     ds = np.zeros(round_cap, np.int64)
+    rn = np.zeros(round_cap, np.int64)
     st.round_cap = round_cap
     st.wl_size = wl.ctypes.data
     st.wl_degsum = ds.ctypes.data
+    st.round_ns = rn.ctypes.data
     _check(lib.gc_color_ex(n, prp, pci, _mode(mode), seed & ((1 << 64) - 1), pout, ctypes.byref(nc),
                            ctypes.byref(rd), ctypes.byref(copt), ctypes.byref(st)))
     s = None
     if want_stats:
         k = min(st.rounds, round_cap)
         s = Stats(st.rounds, st.ncolors, st.max_color, st.worklist_total, st.entries_scanned, st.kernel_ms,
-                  st.setup_ms, st.grid_blocks, st.block_size, wl[:k].copy(), ds[:k].copy())
+                  st.setup_ms, st.grid_blocks, st.block_size, wl[:k].copy(), ds[:k].copy(), rn[:k].copy())
     return Result(out_k if out_k is not None else out, int(nc.value), int(rd.value), s)
 
 

@@ -88,13 +88,13 @@ struct Context {
     std::mutex mu;
     cudaStream_t stream = nullptr;
     int sms = 0;
-    int occ[2][2] = {{0, 0}, {0, 0}};  // [mode][batch] blocks per SM of the round kernel
-    Buf col0, col1, prio, small0, small1, items, chunk0, chunk1, acc, ctl, stats, bitmap, vg;
+    int occ[2][2][2] = {};  // [mode][batch][compact] blocks per SM of the round kernel
+    Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, active, alive, ctl, stats, bitmap, vg;
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
     Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     void release_all() {
-        Buf *all[] = {&col0, &col1, &prio, &small0, &small1, &items, &chunk0, &chunk1, &acc, &ctl, &stats, &bitmap,
+        Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &active, &alive, &ctl, &stats, &bitmap,
                       &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors};
         for (Buf *b : all) b->release();
     }
@@ -223,7 +223,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C.stream;
     const uint32_t flags = opt ? opt->flags : 0u;
     const int32_t T1 = (opt && opt->small_max_degree) ? opt->small_max_degree : 32;
-    const int32_t CH = (opt && opt->chunk) ? opt->chunk : 128;
+    const int32_t CH = (opt && opt->chunk) ? opt->chunk : 1024;
     const int32_t block = (opt && opt->block_size) ? opt->block_size : 256;
     if (T1 < 1 || T1 > 63) return set_last_error(GC_ERR_INVALID_ARG, "small_max_degree %d outside 1..63", T1);
     if (CH < 32 || CH > 1024 || CH % 32) return set_last_error(GC_ERR_INVALID_ARG, "chunk %d invalid", CH);
@@ -237,15 +237,17 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     const size_t gz = static_cast<size_t>(G);
 
     // scratch sized by n; work-item buffers are sized after binning
-    GC_TRY(ensure(C.col0, 4 * n, "colors"));
-    GC_TRY(ensure(C.col1, 4 * n, "colors"));
-    GC_TRY(ensure(C.prio, 4 * n, "priorities"));
+    GC_TRY(ensure(C.col0, 8 * n, "vertex state"));
+    GC_TRY(ensure(C.col1, 8 * n, "vertex state"));
     GC_TRY(ensure(C.small0, 4 * n, "worklist"));
     GC_TRY(ensure(C.small1, 4 * n, "worklist"));
     GC_TRY(ensure(C.items, 4 * n, "worklist"));
     GC_TRY(ensure(C.ctl, sizeof(Ctl), "control"));
     GC_TRY(ensure(C.bitmap, 4 * (n / 32 + 2), "color bitmap"));
-    if (stats_cap) GC_TRY(ensure(C.stats, 16 * static_cast<size_t>(stats_cap), "statistics"));
+    if (stats_cap) GC_TRY(ensure(C.stats, 8 * (4 * static_cast<size_t>(stats_cap) + 1), "statistics"));
+    const bool compact = mode == GC_MODE_DETERMINISTIC && (flags & GC_FLAG_COMPACT);
+    const size_t active_words = static_cast<size_t>(pb.nnz / 32 + 2);
+    if (compact) GC_TRY(ensure(C.active, 4 * active_words, "active-entry bits"));
     if (pb.batch) {
         GC_TRY(ensure(C.vg, 4 * n, "graph ids"));
         GC_TRY(ensure(C.gmax, 4 * gz, "per-graph max"));
@@ -261,7 +263,8 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
     GC_CUDA(cudaMemsetAsync(&ctl->gmax1, 0xff, sizeof(int32_t), s));
     GC_CUDA(cudaMemsetAsync(C.bitmap.p, 0, 4 * (n / 32 + 2), s));
-    if (stats_cap) GC_CUDA(cudaMemsetAsync(C.stats.p, 0, 16 * static_cast<size_t>(stats_cap), s));
+    if (stats_cap) GC_CUDA(cudaMemsetAsync(C.stats.p, 0, 8 * (4 * static_cast<size_t>(stats_cap) + 1), s));
+    if (compact) GC_CUDA(cudaMemsetAsync(C.active.p, 0xff, 4 * active_words, s));
     if (pb.batch) GC_CUDA(cudaMemsetAsync(C.gmax.p, 0xff, 4 * gz, s));
 
     RoundParams P{};
@@ -279,9 +282,8 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
         P.vg = C.vg.as<int32_t>();
     }
     P.seed = seed;
-    P.col0 = C.col0.as<int32_t>();
-    P.col1 = C.col1.as<int32_t>();
-    P.prio = C.prio.as<uint32_t>();
+    P.col0 = C.col0.as<uint64_t>();
+    P.col1 = C.col1.as<uint64_t>();
     P.small0 = C.small0.as<int32_t>();
     P.small1 = C.small1.as<int32_t>();
     P.items = C.items.as<int32_t>();
@@ -296,7 +298,6 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     P.pass_begin = 1;
     P.pass_end = max_rounds < INT32_MAX ? max_rounds + 1 : INT32_MAX;
     P.cap_is_error = 1;
-    P.first_fast = 1;
     P.spin_ns = spin_ns;
     P.T1 = T1;
     P.CH = CH;
@@ -320,35 +321,40 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     GC_TRY(ensure(C.chunk0, 16 * static_cast<size_t>(n_chunks), "work items"));
     GC_TRY(ensure(C.chunk1, 16 * static_cast<size_t>(n_chunks), "work items"));
     GC_TRY(ensure(C.acc, 4 * kAccStride * static_cast<size_t>(n_items), "accumulators"));
+    if (compact) GC_TRY(ensure(C.alive, 4 * static_cast<size_t>(n_chunks), "work-item survivors"));
     P.chunk0 = C.chunk0.as<int4>();
     P.chunk1 = C.chunk1.as<int4>();
     P.acc = C.acc.as<unsigned>();
-    GC_CUDA(launch_expand(P, pb.batch, static_cast<int32_t>(n_items), s));
+    P.active = compact ? C.active.as<unsigned>() : nullptr;
+    P.alive = compact ? C.alive.as<int32_t>() : nullptr;
+    GC_CUDA(launch_expand(P, pb.batch, compact, static_cast<int32_t>(n_items), s));
     if (timing) GC_CUDA(cudaEventRecord(C.ev[1], s));
 
     // persistent grid: every block resident; no more blocks than the first round can use
-    int &occ = C.occ[mode][pb.batch ? 1 : 0];
-    if (occ == 0) GC_CUDA(round_kernel_occupancy(mode, pb.batch, block, &occ));
+    int &occ = C.occ[mode][pb.batch ? 1 : 0][compact ? 1 : 0];
+    if (occ == 0) GC_CUDA(round_kernel_occupancy(mode, pb.batch, compact, block, &occ));
     int per_sm = occ;
     if (opt && opt->blocks_per_sm > 0 && opt->blocks_per_sm < per_sm) per_sm = opt->blocks_per_sm;
     int64_t grid = static_cast<int64_t>(per_sm) * C.sms;
     const int64_t want = (static_cast<int64_t>(n_small) + 32 * static_cast<int64_t>(n_chunks) + block - 1) / block;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
-    GC_CUDA(launch_rounds(P, mode, pb.batch, static_cast<int>(grid), block, s));
+    GC_CUDA(launch_rounds(P, mode, pb.batch, compact, static_cast<int>(grid), block, s));
     if (timing) GC_CUDA(cudaEventRecord(C.ev[2], s));
 
-    // colors, per-graph counts; a device colors_out is written only if no error was posted
+    // colors, per-graph counts; a device colors_out is written only if no error was posted, a host
+    // one is staged through st_colors and copied after the status is known
     int out_dev = 0;
     GC_TRY(locate(out.colors, dev, &out_dev));
+    if (!out_dev && out.colors) GC_TRY(ensure(C.st_colors, 4 * n, "color staging"));
+    int32_t *colors_dev = out_dev ? out.colors : (out.colors ? C.st_colors.as<int32_t>() : nullptr);
     GC_CUDA(launch_count_colors(P, pb.batch, mode == GC_MODE_DETERMINISTIC ? &ctl->passes[1] : nullptr, 0,
                                 static_cast<int32_t>(n), 0, G, C.bitmap.as<unsigned>(),
                                 pb.batch ? C.gmax.as<int32_t>() : &ctl->gmax1,
-                                pb.batch ? C.gcount.as<int32_t>() : &ctl->gcount1,
-                                out_dev ? out.colors : nullptr, s));
-    std::vector<int64_t> st_host(2 * static_cast<size_t>(stats_cap));
+                                pb.batch ? C.gcount.as<int32_t>() : &ctl->gcount1, colors_dev, s));
+    std::vector<int64_t> st_host(4 * static_cast<size_t>(stats_cap) + 1);
     if (stats_cap)
-        GC_CUDA(cudaMemcpyAsync(st_host.data(), C.stats.p, 16 * static_cast<size_t>(stats_cap), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaMemcpyAsync(st_host.data(), C.stats.p, 8 * st_host.size(), cudaMemcpyDeviceToHost, s));
     std::vector<int32_t> gmax_h, gcount_h, glast_h;
     if (pb.batch) {
         gmax_h.resize(gz);
@@ -363,10 +369,8 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     if (h.err[0] != 0) return error_from_ctl(h);
 
     const int32_t last = h.passes[1];  // last round executed (0: every vertex isolated)
-    const int32_t *final_colors =
-        (mode == GC_MODE_DETERMINISTIC && (last & 1)) ? C.col1.as<int32_t>() : C.col0.as<int32_t>();
     if (!out_dev && out.colors)
-        GC_CUDA(cudaMemcpyAsync(out.colors, final_colors, 4 * static_cast<size_t>(n), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaMemcpyAsync(out.colors, colors_dev, 4 * static_cast<size_t>(n), cudaMemcpyDeviceToHost, s));
     const int32_t rounds_single = n > 0 ? (last > 0 ? last : 1) : 0;
     if (pb.batch) {
         int on_dev = 0;
@@ -409,14 +413,18 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
         stats->entries_scanned = 0;
         if (stats_cap) {
             const int32_t R = last < stats_cap ? last : stats_cap;
+            int64_t prev_t = st_host[4 * static_cast<size_t>(stats_cap)];
             for (int32_t r = 0; r < R; ++r) {
-                int64_t w = st_host[2 * r], d = st_host[2 * r + 1];
+                int64_t w = st_host[4 * r], d = st_host[4 * r + 1];
+                const int64_t t_end = st_host[4 * r + 2];
+                stats->entries_scanned += st_host[4 * r + 3];
+                if (stats->round_ns && r < stats->round_cap) stats->round_ns[r] = t_end - prev_t;
+                prev_t = t_end;
                 if (r == 0) {
                     w = n;  // W_1 = V; isolated vertices are final before the first sweep
                     d = pb.nnz;
                 }
                 stats->worklist_total += w;
-                stats->entries_scanned += (mode == GC_MODE_DETERMINISTIC ? 1 : 2) * d;
                 if (stats->wl_size && r < stats->round_cap) stats->wl_size[r] = w;
                 if (stats->wl_degsum && r < stats->round_cap) stats->wl_degsum[r] = d;
             }

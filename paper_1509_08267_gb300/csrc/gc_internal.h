@@ -9,13 +9,26 @@
 
 namespace gc {
 
-// Accumulator slot of a vertex whose row is split over several warp work items (chunks):
-// words [0, kAccWords) hold the 512-color window [0, 512) of its neighbours' colors,
-// word kAccFlag the conflict flag, word kAccDone the number of chunks finished.
+// Adjacency entries a warp loads per step of a work item (8 per lane, issued together).
+#ifndef GC_STEP
+#define GC_STEP 128
+#endif
+constexpr int kStep = GC_STEP;
+
+// Accumulator slot of a vertex of degree > T1 (its row is split into warp work items):
+//   [0, kAccWords)              round window: colors 0..511 of the neighbours read this round
+//   kAccFlag                    conflict flag of this round
+//   kAccDone                    work items of this round finished
+//   [kAccFin, kAccFin+kAccWords) colors 0..511 of neighbours found final (persistent, compact mode)
+//   kAccBase                    id of the vertex's first work item in the survivor array (compact mode)
+// In compact mode the slot belongs to the vertex for the whole run; otherwise slots are numbered
+// afresh every round.
 constexpr int kAccWords = 16;
 constexpr int kAccFlag = 16;
 constexpr int kAccDone = 17;
-constexpr int kAccStride = 32;  // 128 B per slot
+constexpr int kAccFin = 32;
+constexpr int kAccBase = 48;
+constexpr int kAccStride = 64;  // 256 B per slot
 
 // Worklist counters: three sets used round-robin (read / append / clear), kCnt words each.
 constexpr int kCnt = 4;
@@ -45,25 +58,28 @@ struct RoundParams {
     int32_t *vg;             // [n] graph id per vertex (batch)
     uint64_t seed;
 
-    int32_t *col0;   // colors: the array read in odd rounds (deterministic) / the live array (in-place)
-    int32_t *col1;   // colors written in odd rounds (deterministic)
-    uint32_t *prio;  // high 32 bits of each vertex's priority hash
+    // Vertex state words: low 32 bits = color (int32, -1 = uncolored), high 32 bits = the high half
+    // of the vertex's priority hash, so one gather gives a neighbour's color and priority.
+    uint64_t *col0;  // deterministic: read in odd rounds, written in even ones; in-place: the live array
+    uint64_t *col1;  // deterministic: written in odd rounds
     int32_t *small0, *small1;  // thread-per-vertex worklists (two parities)
     int4 *chunk0, *chunk1;     // warp work items {vertex, chunk index, slot, chunks} (two parities)
     int32_t *items;            // setup scratch: larger vertices found by the binning pass
     unsigned *tmp;             // [2] setup scratch counters: larger vertices, their work items
     unsigned *cnt;             // [3][kCnt] worklist counters
     unsigned *acc;             // [slots][kAccStride]
+    unsigned *active;          // compact mode: bit j = adjacency entry j may still change (neighbour not final)
+    int32_t *alive;            // compact mode: entries left active in each work item after its last sweep
     GridBar *bar;
     int32_t *err;              // [4] status, vertex, entry, extra
     int32_t *passes;           // [2] first round not executed by the last launch, last round executed
     int32_t *graph_last;       // [G] last round whose worklist held a vertex of graph g
-    unsigned long long *stats; // [2 * stats_cap] per-round |W_r| and sum of degrees (optional)
+    unsigned long long *stats; // [4 * stats_cap + 1] per round |W_r|, sum of degrees, end time (ns),
+                               // adjacency entries read; last entry: start time of the launch (optional)
     int32_t stats_cap;
     int32_t pass_begin;        // first round this launch runs (the worklist of that round is current)
     int32_t pass_end;          // rounds >= pass_end are not run by this launch
     int32_t cap_is_error;      // reaching pass_end with work left is GC_ERR_NO_CONVERGENCE
-    int32_t first_fast;        // round 1 may assume C_1 == 0 everywhere (all graphs start together)
     int64_t spin_ns;
     int32_t T1;  // largest degree handled by one thread
     int32_t CH;  // adjacency entries per warp work item
@@ -81,13 +97,16 @@ cudaError_t launch_setup(const RoundParams &P, int mode, bool batch, int32_t v_b
                          int32_t g_fixed, cudaStream_t s);
 // Turns the n_items larger vertices found by setup into work items of round P.pass_begin
 // (n_items < 0: the count setup left in P.tmp[0] on the device).
-cudaError_t launch_expand(const RoundParams &P, bool batch, int32_t n_items, cudaStream_t s);
-cudaError_t launch_rounds(const RoundParams &P, int mode, bool batch, int grid, int block, cudaStream_t s);
-cudaError_t round_kernel_occupancy(int mode, bool batch, int block, int *blocks_per_sm);
+// compact: work items get persistent accumulator slots and survivor counters (deterministic mode).
+cudaError_t launch_expand(const RoundParams &P, bool batch, bool compact, int32_t n_items, cudaStream_t s);
+// compact (deterministic mode only): skip adjacency entries whose neighbour is final.
+cudaError_t launch_rounds(const RoundParams &P, int mode, bool batch, bool compact, int grid, int block,
+                          cudaStream_t s);
+cudaError_t round_kernel_occupancy(int mode, bool batch, bool compact, int block, int *blocks_per_sm);
 // Distinct colors and largest color per graph over vertices [v_begin, v_end) (graphs g_begin..g_end-1).
 // `colors_sel` != NULL: read colors from col1 when *colors_sel is odd (the deterministic buffer
-// that the last round wrote), else from col0.  `out` != NULL receives a copy of the colors of
-// [v_begin, v_end) unless err[0] != 0.
+// that the last round wrote), else from col0.  `out` != NULL receives the colors of
+// [v_begin, v_end) (out[0] is vertex v_begin) unless err[0] != 0.
 cudaError_t launch_count_colors(const RoundParams &P, bool batch, const int32_t *colors_sel, int32_t v_begin,
                                 int32_t v_end, int32_t g_begin, int32_t g_end, unsigned *bitmap, int32_t *gmax,
                                 int32_t *gcount, int32_t *out, cudaStream_t s);

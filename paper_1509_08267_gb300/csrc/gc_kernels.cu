@@ -28,11 +28,14 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;  // SplitMix64 state increment
 constexpr int kBlock = 256;                          // round-kernel block size
 constexpr int kMaxWarps = kBlock / 32;
+constexpr int kPer = kStep / 32;  // entries per lane per step
+#ifndef GC_ROUND_MIN_BLOCKS
+#define GC_ROUND_MIN_BLOCKS 4  // resident blocks per SM the round kernel is compiled for
+#endif
 
 // ------------------------------------------------------------------------------------------
 // priority key: key(v) = (h(v), v), h(v) = SplitMix64 output number v of the stream `seed`
-// (Steele, Lea & Flood 2014).  The high 32 bits of h are cached per vertex; the full hash is
-// recomputed only when those tie.
+// (Steele, Lea & Flood 2014).  The top 31 bits of h are cached in the vertex's state word.
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -44,7 +47,8 @@ __device__ __forceinline__ uint64_t vertex_hash(uint64_t seed, uint32_t local) {
     return mix64(seed + (static_cast<uint64_t>(local) + 1ull) * kGamma);
 }
 
-// key(u) < key(v): u keeps its color against v.
+// key(u) < key(v): u keeps its color against v.  pu, pv are the top 31 bits of h(u), h(v); the full
+// hashes are recomputed only when those tie.
 __device__ __forceinline__ bool key_less(uint32_t pu, uint32_t pv, uint32_t lu, uint32_t lv, uint64_t seed) {
     if (pu != pv) return pu < pv;
     const uint64_t hu = vertex_hash(seed, lu), hv = vertex_hash(seed, lv);
@@ -115,6 +119,43 @@ __device__ bool grid_sync(GridBar *bar, int32_t *err, int64_t spin_ns) {
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// ------------------------------------------------------------------------------------------
+// vertex state words
+
+// State word: bits 0..31 color (int32, -1 = uncolored), bit 32 FINAL (the vertex left the worklist
+// for good), bits 33..63 the top 31 bits of the vertex's priority hash h(v).
+constexpr uint64_t kNoNeighbour = 0x00000000FFFFFFFFull;  // color -1: forbids nothing, never equal
+constexpr uint64_t kFinalBit = 1ull << 32;
+
+__device__ __forceinline__ uint64_t pack_state(int32_t color, uint32_t prio31, bool final_) {
+    return (static_cast<uint64_t>(prio31) << 33) | (final_ ? kFinalBit : 0ull) | static_cast<uint32_t>(color);
+}
+__device__ __forceinline__ int32_t color_of(uint64_t w) { return static_cast<int32_t>(static_cast<uint32_t>(w)); }
+__device__ __forceinline__ uint32_t prio_of(uint64_t w) { return static_cast<uint32_t>(w >> 33); }
+__device__ __forceinline__ bool final_of(uint64_t w) { return (w & kFinalBit) != 0; }
+
+// State words are loaded through L1 (ld.global.ca): the words of high-degree vertices are read by
+// most rows and would otherwise concentrate on a few L2 slices.  Within a deterministic round the
+// buffer being read is not written, and the acquire at the grid barrier makes the previous round's
+// writes visible to these weak loads.
+__device__ __forceinline__ uint64_t load_state(const uint64_t *p) {
+    return __ldca(reinterpret_cast<const unsigned long long *>(p));
+}
+
+// Adjacency entries are streamed without allocating in L1, leaving L1 to the state words.
+__device__ __forceinline__ int32_t load_entry(const int32_t *p) {
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Release/acquire increment of a work-item counter (orders the accumulator updates before it).
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -190,9 +231,9 @@ __device__ __forceinline__ int32_t first_free(unsigned lo0, unsigned lo1, const 
     return -1;
 }
 
-// Least color >= 512 absent from the row's neighbours (warp-cooperative; mex <= deg(v) bounds it).
+// Least color >= start absent from the row's neighbours (warp-cooperative; mex <= deg(v) bounds it).
 template <bool BATCH>
-__device__ int32_t mex_from(const RoundParams &P, const int32_t *colc, const Row &r, unsigned *win, int lane,
+__device__ int32_t mex_from(const RoundParams &P, const uint64_t *colc, const Row &r, unsigned *win, int lane,
                             int32_t start) {
     for (int32_t base = start;; base += 32 * kAccWords) {
         if (lane < kAccWords) win[lane] = 0;
@@ -200,7 +241,7 @@ __device__ int32_t mex_from(const RoundParams &P, const int32_t *colc, const Row
         for (int64_t j = r.b + lane; j < r.e; j += 32) {
             const int32_t ul = __ldg(P.colidx + j);
             if (static_cast<uint32_t>(ul) >= static_cast<uint32_t>(r.ng)) continue;
-            const int32_t c = __ldcg(colc + r.vbase + ul) - base;
+            const int32_t c = color_of(load_state(colc + r.vbase + ul)) - base;
             if (static_cast<unsigned>(c) < 32u * kAccWords) atomicOr(&win[c >> 5], 1u << (c & 31));
         }
         __syncwarp();
@@ -236,148 +277,343 @@ __device__ __forceinline__ void append_large(const RoundParams &P, int32_t V, co
         chunk_next[cb + q] = make_int4(V, q, static_cast<int32_t>(slot), nch);
 }
 
+// Issues the colidx loads of one step of a work item: entries j0 + lane + 32q, q < kPer.
+__device__ __forceinline__ void load_step(const RoundParams &P, int64_t j0, int64_t je, int lane, int32_t (&ul)[kPer]) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int64_t j = j0 + lane + 32 * q;
+        ul[q] = j < je ? load_entry(P.colidx + j) : 0;
+    }
+}
+
+// Gathers the state words of one step's neighbours (kNoNeighbour past the end or for a bad entry).
+__device__ __forceinline__ void gather_step(const RoundParams &P, const Row &r, const uint64_t *colc, int64_t j0,
+                                            int64_t je, int lane, const int32_t (&ul)[kPer], uint64_t (&w)[kPer]) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int64_t j = j0 + lane + 32 * q;
+        w[q] = kNoNeighbour;
+        if (j < je) {
+            const int32_t U = neighbour(P, r, ul[q], j);
+            if (U >= 0) w[q] = load_state(colc + U);
+        }
+    }
+}
+
+// Accumulates one step into the lane's window [0, 64), the warp's shared window [64, 512) and the
+// conflict flag (a neighbour with the same color and a smaller key).
+template <bool WINDOW, bool CONFLICT>
+__device__ __forceinline__ void consume_step(const uint64_t (&w)[kPer], const int32_t (&ul)[kPer], int32_t cv,
+                                             uint32_t pv, uint32_t lv, uint64_t seed, uint64_t &lo, unsigned *win,
+                                             bool &lose) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int32_t c = color_of(w[q]);
+        if constexpr (WINDOW) {
+            if (static_cast<unsigned>(c) < 64u)
+                lo |= 1ull << c;
+            else if (static_cast<unsigned>(c) < 32u * kAccWords)
+                atomicOr(&win[c >> 5], 1u << (c & 31));
+        }
+        if constexpr (CONFLICT) {
+            if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]), lv, seed);
+        }
+    }
+}
+
+// Sweeps entries [jb, je) of a row with one warp, kStep entries per step, the next step's colidx
+// loads issued before the current step's gathers are consumed.
+template <bool WINDOW, bool CONFLICT>
+__device__ __forceinline__ void sweep(const RoundParams &P, const Row &r, const uint64_t *colc, int64_t jb, int64_t je,
+                                      int lane, int32_t cv, uint32_t pv, uint64_t &lo, unsigned *win, bool &lose) {
+    int32_t ul[kPer], un[kPer];
+    uint64_t w[kPer];
+    load_step(P, jb, je, lane, ul);
+    for (int64_t j0 = jb; j0 < je; j0 += kStep) {
+        gather_step(P, r, colc, j0, je, lane, ul, w);
+        const bool more = j0 + kStep < je;
+        if (more) load_step(P, j0 + kStep, je, lane, un);
+        consume_step<WINDOW, CONFLICT>(w, ul, cv, pv, static_cast<uint32_t>(r.lv), P.seed, lo, win, lose);
+        if (more) {
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) ul[q] = un[q];
+        }
+    }
+}
+
+// Per-thread sweep of a short row (degree <= T1 <= 63): window [0, 64) and conflict flag.
+template <bool BATCH, bool WINDOW, bool CONFLICT>
+__device__ __forceinline__ void sweep_small(const RoundParams &P, const Row &r, const uint64_t *colc, int32_t cv,
+                                            uint32_t pv, uint64_t &mask, bool &lose) {
+    for (int64_t j0 = r.b; j0 < r.e; j0 += kPer) {
+        int32_t ul[kPer];
+        uint64_t w[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) ul[q] = j0 + q < r.e ? load_entry(P.colidx + j0 + q) : 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            w[q] = kNoNeighbour;
+            if (j0 + q < r.e) {
+                const int32_t U = neighbour(P, r, ul[q], j0 + q);
+                if (U >= 0) w[q] = load_state(colc + U);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int32_t c = color_of(w[q]);
+            if constexpr (WINDOW) {
+                if (static_cast<unsigned>(c) < 64u) mask |= 1ull << c;
+            }
+            if constexpr (CONFLICT) {
+                if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
+                                                      static_cast<uint32_t>(r.lv), P.seed);
+            }
+        }
+    }
+}
+
+// Merges a work item's window and flag into the vertex's accumulator slot.  Returns true in the
+// warp that completed the vertex's last work item; that warp then holds the merged window in
+// lo0/lo1/win and the merged flag in `lose`, and the slot is cleared for reuse.
+template <bool WINDOW>
+__device__ __forceinline__ bool merge_item(unsigned *a, int nch, int lane, unsigned &lo0, unsigned &lo1, unsigned *win,
+                                           bool &lose) {
+    if constexpr (WINDOW) {
+        const unsigned w = lane == 0 ? lo0 : lane == 1 ? lo1 : (lane < kAccWords ? win[lane] : 0u);
+        if (lane < kAccWords && (w & ~__ldcg(a + lane))) atomicOr(a + lane, w);
+    }
+    if (lane == 0 && lose) atomicOr(a + kAccFlag, 1u);
+    __syncwarp();
+    unsigned done = 0;
+    if (lane == 0) done = atom_add_acq_rel(a + kAccDone, 1u);
+    done = __shfl_sync(kFull, done, 0);
+    if (done != static_cast<unsigned>(nch - 1)) return false;
+    const unsigned x = lane < kAccWords ? __ldcg(a + lane) : 0u;
+    const unsigned f = __ldcg(a + kAccFlag);
+    if constexpr (WINDOW) {
+        lo0 = __shfl_sync(kFull, x, 0);
+        lo1 = __shfl_sync(kFull, x, 1);
+        if (lane >= 2 && lane < kAccWords) win[lane] = x;
+    }
+    lose = f != 0u;
+    __syncwarp();
+    a[lane] = 0u;  // the round part of the slot (words 0..31); the persistent part stays
+    return true;
+}
+
 // ------------------------------------------------------------------------------------------
 // deterministic mode
 
-// One vertex of degree <= T1 (one thread): did it lose in this round, and its next color.
-template <bool BATCH, bool FIRST>
-__device__ __forceinline__ bool det_small(const RoundParams &P, const int32_t *__restrict__ colc,
-                                          int32_t *__restrict__ coln, int32_t V, int32_t &deg) {
+// Writes a vertex's state for the next round.  A vertex that did not lose is final: its color will
+// not change again, so the FINAL bit goes into both buffers (the color and priority bits are the
+// ones already there, so a concurrent reader of the current buffer sees the same color either way).
+__device__ __forceinline__ void det_write(const uint64_t *colc, uint64_t *coln, int32_t V, bool lose, int32_t cv,
+                                          int32_t nc, uint32_t pv) {
+    if (lose) {
+        coln[V] = pack_state(nc, pv, false);
+    } else {
+        const uint64_t w = pack_state(cv, pv, true);
+        coln[V] = w;
+        const_cast<uint64_t *>(colc)[V] = w;
+    }
+}
+
+// One vertex of degree <= T1 (one thread): did it lose in this round; writes its next state.
+template <bool BATCH>
+__device__ __forceinline__ bool det_small(const RoundParams &P, const uint64_t *colc, uint64_t *coln, int32_t V,
+                                          int32_t &deg) {
     const Row r = load_row<BATCH>(P, V);
     deg = static_cast<int32_t>(r.e - r.b);
-    const uint32_t pv = __ldg(P.prio + V);
-    const int32_t cv = FIRST ? 0 : __ldcg(colc + V);
+    const uint64_t self = load_state(colc + V);
+    const int32_t cv = color_of(self);
+    const uint32_t pv = prio_of(self);
     uint64_t mask = 0;
     bool lose = false;
-    int64_t j = r.b;
-    for (; j + 4 <= r.e; j += 4) {
-        int32_t ul[4], U[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) ul[q] = __ldg(P.colidx + j + q);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) U[q] = neighbour(P, r, ul[q], j + q);
-        if constexpr (FIRST) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (U[q] >= 0 && !lose) lose = key_less(__ldg(P.prio + U[q]), pv, ul[q], r.lv, P.seed);
-        } else {
-            int32_t c[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) c[q] = U[q] >= 0 ? __ldcg(colc + U[q]) : -1;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (static_cast<unsigned>(c[q]) < 64u) mask |= 1ull << c[q];
-                if (c[q] == cv && !lose) lose = key_less(__ldg(P.prio + U[q]), pv, ul[q], r.lv, P.seed);
-            }
-        }
-    }
-    for (; j < r.e; ++j) {
-        const int32_t ul = __ldg(P.colidx + j);
-        const int32_t U = neighbour(P, r, ul, j);
-        if (U < 0) continue;
-        if constexpr (FIRST) {
-            if (!lose) lose = key_less(__ldg(P.prio + U), pv, ul, r.lv, P.seed);
-        } else {
-            const int32_t c = __ldcg(colc + U);
-            if (static_cast<unsigned>(c) < 64u) mask |= 1ull << c;
-            if (c == cv && !lose) lose = key_less(__ldg(P.prio + U), pv, ul, r.lv, P.seed);
-        }
-    }
-    int32_t nc = cv;
-    if (lose) nc = FIRST ? 1 : __ffsll(static_cast<long long>(~mask)) - 1;
-    coln[V] = nc;
+    sweep_small<BATCH, true, true>(P, r, colc, cv, pv, mask, lose);
+    det_write(colc, coln, V, lose, cv, lose ? __ffsll(static_cast<long long>(~mask)) - 1 : cv, pv);
     return lose;
 }
 
-// One CH-entry work item of a larger vertex (one warp).
-template <bool BATCH, bool FIRST>
-__device__ void det_chunk(const RoundParams &P, const int32_t *__restrict__ colc, int32_t *__restrict__ coln,
-                          int4 it, unsigned *win, int4 *chunk_next, unsigned *cnt_next, int pass, int lane,
-                          unsigned long long &st_deg, unsigned long long &st_cnt) {
-    const int32_t V = it.x, k = it.y, slot = it.z, nch = it.w;
+// Compact sweep of entries [jb, je) of a row: only entries whose bit in P.active is still set are
+// read.  Entries are grouped 32 to a bit word (groups aligned to the global entry index); the warp
+// loads the bit words of up to 32 groups at once, one per lane, and then visits only the groups
+// with active entries, kPer groups per step.  A neighbour found final is dropped: its bit is cleared
+// and its color is added, besides the round window (lo / win), to the window of final neighbours
+// (flo / wfin) that the vertex keeps for later rounds.  Lane 0 returns the entries still active and
+// the entries read.
+__device__ __forceinline__ void sweep_compact(const RoundParams &P, const Row &r, const uint64_t *colc, int64_t jb,
+                                              int64_t je, int lane, int32_t cv, uint32_t pv, uint64_t &lo,
+                                              unsigned *win, uint64_t &flo, unsigned *wfin, bool &lose,
+                                              unsigned &survivors, unsigned &reads) {
+    const int64_t gb = jb >> 5, ge = (je + 31) >> 5;
+    for (int64_t gw0 = gb; gw0 < ge; gw0 += 32) {
+        // this lane's group: its active bits restricted to [jb, je)
+        const int64_t mg = gw0 + lane;
+        unsigned bits = 0;
+        if (mg < ge) {
+            bits = __ldcg(P.active + mg);
+            const int64_t lo_j = 32 * mg, hi_j = lo_j + 32;
+            if (lo_j < jb) bits &= ~0u << (jb - lo_j);
+            if (hi_j > je) bits &= (je - lo_j >= 32) ? ~0u : ((1u << (je - lo_j)) - 1u);
+        }
+        unsigned todo = __ballot_sync(kFull, bits != 0u);  // groups with active entries
+        while (todo) {
+            int src[kPer];
+            unsigned gbits[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                src[q] = todo ? __ffs(todo) - 1 : -1;
+                if (todo) todo &= todo - 1;
+            }
+            int32_t ul[kPer];
+            uint64_t w[kPer];
+            unsigned act = 0;
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                gbits[q] = __shfl_sync(kFull, bits, src[q] < 0 ? 0 : src[q]);
+                const bool a = src[q] >= 0 && ((gbits[q] >> lane) & 1u);
+                act |= static_cast<unsigned>(a) << q;
+                ul[q] = a ? load_entry(P.colidx + 32 * (gw0 + src[q]) + lane) : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                w[q] = kNoNeighbour;
+                if ((act >> q) & 1u) {
+                    const int32_t U = neighbour(P, r, ul[q], 32 * (gw0 + src[q]) + lane);
+                    if (U >= 0) w[q] = load_state(colc + U);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int32_t c = color_of(w[q]);
+                const bool a = (act >> q) & 1u;
+                const bool fin = a && final_of(w[q]);
+                if (static_cast<unsigned>(c) < 64u) {
+                    lo |= 1ull << c;
+                    if (fin) flo |= 1ull << c;
+                } else if (static_cast<unsigned>(c) < 32u * kAccWords) {
+                    atomicOr(&win[c >> 5], 1u << (c & 31));
+                    if (fin) atomicOr(&wfin[c >> 5], 1u << (c & 31));
+                }
+                if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
+                                                      static_cast<uint32_t>(r.lv), P.seed);
+                const unsigned drop = __ballot_sync(kFull, fin);
+                if (lane == 0 && src[q] >= 0) {
+                    if (drop) atomicAnd(P.active + gw0 + src[q], ~drop);
+                    survivors += __popc(gbits[q] & ~drop);
+                    reads += __popc(gbits[q]);
+                }
+            }
+        }
+    }
+}
+
+// Appends a losing larger vertex with the work items that still have active entries (compact mode).
+template <bool BATCH>
+__device__ void append_alive(const RoundParams &P, int32_t V, const Row &r, int32_t lid, int32_t base,
+                             int4 *chunk_next, unsigned *cnt_next, int next_round, int lane) {
+    const int32_t deg = static_cast<int32_t>(r.e - r.b);
+    const int32_t nch = (deg + P.CH - 1) / P.CH;
+    int32_t count = 0;
+    for (int32_t k0 = 0; k0 < nch; k0 += 32) {
+        const int32_t k = k0 + lane;
+        count += __popc(__ballot_sync(kFull, k < nch && __ldcg(P.alive + base + k) > 0));
+    }
+    const bool none = count == 0;  // every neighbour final: one item still computes the color
+    const int32_t items = none ? 1 : count;
+    unsigned cb = 0;
+    if (lane == 0) {
+        atomicAdd(cnt_next + kCntItems, 1u);
+        cb = atomicAdd(cnt_next + kCntChunks, static_cast<unsigned>(items));
+        if constexpr (BATCH) note_graph_round(P, r.g, next_round);
+    }
+    cb = __shfl_sync(kFull, cb, 0);
+    if (none) {
+        if (lane == 0) chunk_next[cb] = make_int4(V, 0, lid, 1);
+        return;
+    }
+    int32_t at = 0;
+    for (int32_t k0 = 0; k0 < nch; k0 += 32) {
+        const int32_t k = k0 + lane;
+        const bool live = k < nch && __ldcg(P.alive + base + k) > 0;
+        const unsigned m = __ballot_sync(kFull, live);
+        if (live) chunk_next[cb + at + __popc(m & lanemask_lt())] = make_int4(V, k, lid, items);
+        at += __popc(m);
+    }
+}
+
+// One CH-entry work item of a larger vertex (one warp).  COMPACT: the slot (it.z) is the vertex's own
+// for the whole run and only active entries are read; otherwise slots are per round.
+template <bool BATCH, bool COMPACT>
+__device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *coln, int4 it, unsigned *win,
+                          unsigned *wfin, int4 *chunk_next, unsigned *cnt_next, int pass, int lane,
+                          unsigned long long &st_deg, unsigned long long &st_cnt, unsigned long long &st_read) {
+    const int32_t V = it.x, k = it.y, slot = it.z, nitems = it.w;
     const Row r = load_row<BATCH>(P, V);
-    const uint32_t pv = __ldg(P.prio + V);
-    const int32_t cv = FIRST ? 0 : __ldcg(colc + V);
+    const uint64_t self = load_state(colc + V);
+    const int32_t cv = color_of(self);
+    const uint32_t pv = prio_of(self);
     const int64_t jb = r.b + static_cast<int64_t>(k) * P.CH;
     const int64_t je = min(r.e, jb + P.CH);
-    if (k == 0 && lane == 0) {
-        st_deg += static_cast<unsigned long long>(r.e - r.b);
-        st_cnt += 1;
+    unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
+    if (lane < kAccWords) {
+        win[lane] = 0;
+        if (COMPACT) wfin[lane] = 0;
     }
-    if (lane < kAccWords) win[lane] = 0;
     __syncwarp();
     uint64_t lo = 0;
     bool lose = false;
-    for (int64_t j0 = jb; j0 < je; j0 += 128) {
-        int32_t ul[4], U[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int64_t j = j0 + lane + 32 * q;
-            ul[q] = j < je ? __ldg(P.colidx + j) : -1;
+    int32_t base = 0;
+    if constexpr (COMPACT) {
+        uint64_t flo = 0;
+        unsigned survivors = 0, reads = 0;
+        sweep_compact(P, r, colc, jb, je, lane, cv, pv, lo, win, flo, wfin, lose, survivors, reads);
+        const unsigned f0 = __reduce_or_sync(kFull, static_cast<unsigned>(flo));
+        const unsigned f1 = __reduce_or_sync(kFull, static_cast<unsigned>(flo >> 32));
+        __syncwarp();
+        // neighbours found final: into the vertex's persistent window, before this item is counted
+        const unsigned fw = lane == 0 ? f0 : lane == 1 ? f1 : (lane < kAccWords ? wfin[lane] : 0u);
+        if (lane < kAccWords && (fw & ~__ldcg(a + kAccFin + lane))) atomicOr(a + kAccFin + lane, fw);
+        base = static_cast<int32_t>(__ldcg(a + kAccBase));
+        if (lane == 0) {
+            P.alive[base + k] = static_cast<int32_t>(survivors);
+            st_read += reads;
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int64_t j = j0 + lane + 32 * q;
-            U[q] = j < je ? neighbour(P, r, ul[q], j) : -1;
-        }
-        if constexpr (FIRST) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (U[q] >= 0 && !lose) lose = key_less(__ldg(P.prio + U[q]), pv, ul[q], r.lv, P.seed);
-        } else {
-            int32_t c[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) c[q] = U[q] >= 0 ? __ldcg(colc + U[q]) : -1;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int32_t cq = c[q];
-                if (static_cast<unsigned>(cq) < 64u)
-                    lo |= 1ull << cq;
-                else if (static_cast<unsigned>(cq) < 32u * kAccWords)
-                    atomicOr(&win[cq >> 5], 1u << (cq & 31));
-                if (cq == cv && cq >= 0 && !lose)
-                    lose = key_less(__ldg(P.prio + U[q]), pv, ul[q], r.lv, P.seed);
-            }
-        }
+    } else {
+        sweep<true, true>(P, r, colc, jb, je, lane, cv, pv, lo, win, lose);
+        if (lane == 0) st_read += static_cast<unsigned long long>(je - jb);
     }
     lose = __any_sync(kFull, lose);
     unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
     unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
     __syncwarp();
-    if (nch > 1) {
-        unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
-        if constexpr (!FIRST) {
-            const unsigned w = lane == 0 ? lo0 : lane == 1 ? lo1 : (lane < kAccWords ? win[lane] : 0u);
-            if (lane < kAccWords && (w & ~__ldcg(a + lane))) atomicOr(a + lane, w);
-        }
-        if (lane == 0 && lose) atomicOr(a + kAccFlag, 1u);
-        __threadfence();
-        unsigned done = 0;
-        if (lane == 0) done = atomicAdd(a + kAccDone, 1u);
-        done = __shfl_sync(kFull, done, 0);
-        if (done != static_cast<unsigned>(nch - 1)) return;
-        // the last work item of V: collect the merged window and clear the slot for reuse
-        __threadfence();
-        const unsigned w = lane < kAccWords ? __ldcg(a + lane) : 0u;
-        const unsigned f = __ldcg(a + kAccFlag);
-        lo0 = __shfl_sync(kFull, w, 0);
-        lo1 = __shfl_sync(kFull, w, 1);
-        if (lane >= 2 && lane < kAccWords) win[lane] = w;
-        lose = f != 0;
+    if (nitems > 1 || COMPACT) {
+        if (!merge_item<true>(a, nitems, lane, lo0, lo1, win, lose)) return;
+    }
+    // the warp that finishes a vertex accounts for it in the round statistics
+    if (lane == 0) {
+        st_deg += static_cast<unsigned long long>(r.e - r.b);
+        st_cnt += 1;
+    }
+    if constexpr (COMPACT) {
+        // round window + colors of every neighbour known to be final
+        const unsigned fx = lane < kAccWords ? __ldcg(a + kAccFin + lane) : 0u;
+        lo0 |= __shfl_sync(kFull, fx, 0);
+        lo1 |= __shfl_sync(kFull, fx, 1);
+        if (lane >= 2 && lane < kAccWords) win[lane] |= fx;
         __syncwarp();
-        a[lane] = 0u;  // kAccStride == 32 words
     }
     int32_t nc = cv;
     if (lose) {
-        if (FIRST) {
-            nc = 1;
-        } else {
-            nc = first_free(lo0, lo1, win);
-            if (nc < 0) nc = mex_from<BATCH>(P, colc, r, win, lane, 32 * kAccWords);
-        }
+        nc = first_free(lo0, lo1, win);
+        if (nc < 0) nc = mex_from<BATCH>(P, colc, r, win, lane, 32 * kAccWords);
     }
-    if (lane == 0) coln[V] = nc;
-    if (lose) append_large<BATCH>(P, V, r, chunk_next, cnt_next, pass + 1, lane);
+    if (lane == 0) det_write(colc, coln, V, lose, cv, nc, pv);
+    if (!lose) return;
+    if constexpr (COMPACT)
+        append_alive<BATCH>(P, V, r, slot, base, chunk_next, cnt_next, pass + 1, lane);
+    else
+        append_large<BATCH>(P, V, r, chunk_next, cnt_next, pass + 1, lane);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -385,39 +621,30 @@ __device__ void det_chunk(const RoundParams &P, const int32_t *__restrict__ colc
 
 // Phase 1 for a vertex of degree <= T1: First Fit over the live colors.
 template <bool BATCH>
-__device__ __forceinline__ void ip_small_assign(const RoundParams &P, int32_t *col, int32_t V) {
+__device__ __forceinline__ void ip_small_assign(const RoundParams &P, uint64_t *col, int32_t V) {
     const Row r = load_row<BATCH>(P, V);
     uint64_t mask = 0;
-    for (int64_t j = r.b; j < r.e; ++j) {
-        const int32_t ul = __ldg(P.colidx + j);
-        const int32_t U = neighbour(P, r, ul, j);
-        if (U < 0) continue;
-        const int32_t c = __ldcg(col + U);
-        if (static_cast<unsigned>(c) < 64u) mask |= 1ull << c;
-    }
-    __stcg(col + V, __ffsll(static_cast<long long>(~mask)) - 1);
+    bool unused = false;
+    sweep_small<BATCH, true, false>(P, r, col, 0, 0, mask, unused);
+    const uint32_t pv = prio_of(load_state(col + V));
+    col[V] = pack_state(__ffsll(static_cast<long long>(~mask)) - 1, pv, false);
 }
 
 // Phase 2 for a vertex of degree <= T1.
 template <bool BATCH>
-__device__ __forceinline__ bool ip_small_conflict(const RoundParams &P, const int32_t *col, int32_t V, int32_t &deg) {
+__device__ __forceinline__ bool ip_small_conflict(const RoundParams &P, const uint64_t *col, int32_t V, int32_t &deg) {
     const Row r = load_row<BATCH>(P, V);
     deg = static_cast<int32_t>(r.e - r.b);
-    const uint32_t pv = __ldg(P.prio + V);
-    const int32_t cv = __ldcg(col + V);
+    const uint64_t self = load_state(col + V);
+    uint64_t mask = 0;
     bool lose = false;
-    for (int64_t j = r.b; j < r.e && !lose; ++j) {
-        const int32_t ul = __ldg(P.colidx + j);
-        if (static_cast<uint32_t>(ul) >= static_cast<uint32_t>(r.ng)) continue;
-        const int32_t U = r.vbase + ul;
-        if (__ldcg(col + U) == cv) lose = key_less(__ldg(P.prio + U), pv, ul, r.lv, P.seed);
-    }
+    sweep_small<BATCH, false, true>(P, r, col, color_of(self), prio_of(self), mask, lose);
     return lose;
 }
 
 // Phase 1 work item of a larger vertex.
 template <bool BATCH>
-__device__ void ip_chunk_assign(const RoundParams &P, int32_t *col, int4 it, unsigned *win, int lane) {
+__device__ void ip_chunk_assign(const RoundParams &P, uint64_t *col, int4 it, unsigned *win, int lane) {
     const int32_t V = it.x, k = it.y, slot = it.z, nch = it.w;
     const Row r = load_row<BATCH>(P, V);
     const int64_t jb = r.b + static_cast<int64_t>(k) * P.CH;
@@ -425,83 +652,39 @@ __device__ void ip_chunk_assign(const RoundParams &P, int32_t *col, int4 it, uns
     if (lane < kAccWords) win[lane] = 0;
     __syncwarp();
     uint64_t lo = 0;
-    for (int64_t j0 = jb; j0 < je; j0 += 128) {
-        int32_t U[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int64_t j = j0 + lane + 32 * q;
-            U[q] = j < je ? neighbour(P, r, __ldg(P.colidx + j), j) : -1;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int32_t cq = U[q] >= 0 ? __ldcg(col + U[q]) : -1;
-            if (static_cast<unsigned>(cq) < 64u)
-                lo |= 1ull << cq;
-            else if (static_cast<unsigned>(cq) < 32u * kAccWords)
-                atomicOr(&win[cq >> 5], 1u << (cq & 31));
-        }
-    }
+    bool unused = false;
+    sweep<true, false>(P, r, col, jb, je, lane, 0, 0, lo, win, unused);
     unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
     unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
     __syncwarp();
-    if (nch > 1) {
-        unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
-        const unsigned w = lane == 0 ? lo0 : lane == 1 ? lo1 : (lane < kAccWords ? win[lane] : 0u);
-        if (lane < kAccWords && (w & ~__ldcg(a + lane))) atomicOr(a + lane, w);
-        __threadfence();
-        unsigned done = 0;
-        if (lane == 0) done = atomicAdd(a + kAccDone, 1u);
-        done = __shfl_sync(kFull, done, 0);
-        if (done != static_cast<unsigned>(nch - 1)) return;
-        __threadfence();
-        const unsigned x = lane < kAccWords ? __ldcg(a + lane) : 0u;
-        lo0 = __shfl_sync(kFull, x, 0);
-        lo1 = __shfl_sync(kFull, x, 1);
-        if (lane >= 2 && lane < kAccWords) win[lane] = x;
-        __syncwarp();
-        a[lane] = 0u;
-    }
+    if (nch > 1 && !merge_item<true>(P.acc + static_cast<size_t>(slot) * kAccStride, nch, lane, lo0, lo1, win, unused))
+        return;
     int32_t nc = first_free(lo0, lo1, win);
     if (nc < 0) nc = mex_from<BATCH>(P, col, r, win, lane, 32 * kAccWords);
-    if (lane == 0) __stcg(col + V, nc);
+    if (lane == 0) col[V] = pack_state(nc, prio_of(load_state(col + V)), false);
 }
 
 // Phase 2 work item of a larger vertex.
 template <bool BATCH>
-__device__ void ip_chunk_conflict(const RoundParams &P, const int32_t *col, int4 it, int4 *chunk_next,
+__device__ void ip_chunk_conflict(const RoundParams &P, const uint64_t *col, int4 it, unsigned *win, int4 *chunk_next,
                                   unsigned *cnt_next, int pass, int lane, unsigned long long &st_deg,
                                   unsigned long long &st_cnt) {
     const int32_t V = it.x, k = it.y, slot = it.z, nch = it.w;
     const Row r = load_row<BATCH>(P, V);
-    const uint32_t pv = __ldg(P.prio + V);
-    const int32_t cv = __ldcg(col + V);
+    const uint64_t self = load_state(col + V);
     const int64_t jb = r.b + static_cast<int64_t>(k) * P.CH;
     const int64_t je = min(r.e, jb + P.CH);
     if (k == 0 && lane == 0) {
         st_deg += static_cast<unsigned long long>(r.e - r.b);
         st_cnt += 1;
     }
+    uint64_t lo = 0;
     bool lose = false;
-    for (int64_t j = jb + lane; j < je; j += 32) {
-        const int32_t ul = __ldg(P.colidx + j);
-        if (static_cast<uint32_t>(ul) >= static_cast<uint32_t>(r.ng)) continue;
-        const int32_t U = r.vbase + ul;
-        if (!lose && __ldcg(col + U) == cv) lose = key_less(__ldg(P.prio + U), pv, ul, r.lv, P.seed);
-    }
+    sweep<false, true>(P, r, col, jb, je, lane, color_of(self), prio_of(self), lo, win, lose);
     lose = __any_sync(kFull, lose);
-    if (nch > 1) {
-        unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
-        if (lane == 0 && lose) atomicOr(a + kAccFlag, 1u);
-        __threadfence();
-        unsigned done = 0;
-        if (lane == 0) done = atomicAdd(a + kAccDone, 1u);
-        done = __shfl_sync(kFull, done, 0);
-        if (done != static_cast<unsigned>(nch - 1)) return;
-        __threadfence();
-        lose = __ldcg(a + kAccFlag) != 0u;
-        __syncwarp();
-        a[lane] = 0u;
-    }
+    unsigned lo0 = 0, lo1 = 0;
+    if (nch > 1 && !merge_item<false>(P.acc + static_cast<size_t>(slot) * kAccStride, nch, lane, lo0, lo1, win, lose))
+        return;
     if (lose) append_large<BATCH>(P, V, r, chunk_next, cnt_next, pass + 1, lane);
 }
 
@@ -509,62 +692,38 @@ __device__ void ip_chunk_conflict(const RoundParams &P, const int32_t *col, int4
 // kernels
 
 __device__ __forceinline__ void flush_stats(const RoundParams &P, int pass, unsigned long long deg,
-                                            unsigned long long cnt) {
+                                            unsigned long long cnt, unsigned long long reads) {
     // block-level reduction, then one atomic per block
-    __shared__ unsigned long long s_deg, s_cnt;
+    __shared__ unsigned long long s_deg, s_cnt, s_read;
     if (threadIdx.x == 0) {
         s_deg = 0;
         s_cnt = 0;
+        s_read = 0;
     }
     __syncthreads();
     if (deg) atomicAdd(&s_deg, deg);
     if (cnt) atomicAdd(&s_cnt, cnt);
+    if (reads) atomicAdd(&s_read, reads);
     __syncthreads();
     if (threadIdx.x == 0 && pass <= P.stats_cap) {
-        if (s_cnt) atomicAdd(P.stats + 2 * (pass - 1), s_cnt);
-        if (s_deg) atomicAdd(P.stats + 2 * (pass - 1) + 1, s_deg);
+        unsigned long long *st = P.stats + 4 * (pass - 1);
+        if (s_cnt) atomicAdd(st, s_cnt);
+        if (s_deg) atomicAdd(st + 1, s_deg);
+        atomicMax(st + 2, static_cast<unsigned long long>(global_ns()));
+        if (s_read) atomicAdd(st + 3, s_read);
     }
 }
 
-template <bool BATCH, bool FIRST>
-__device__ __forceinline__ void det_pass(const RoundParams &P, int pass, unsigned nsmall, unsigned nchunks,
-                                         unsigned *cnt_next, unsigned *win, int lane, int gw, int nw,
-                                         unsigned long long &st_deg, unsigned long long &st_cnt) {
-    const bool odd = (pass & 1) != 0;
-    const int32_t *colc = odd ? P.col0 : P.col1;
-    int32_t *coln = odd ? P.col1 : P.col0;
-    const int32_t *smallc = odd ? P.small0 : P.small1;
-    int32_t *smalln = odd ? P.small1 : P.small0;
-    const int4 *chunkc = odd ? P.chunk0 : P.chunk1;
-    int4 *chunkn = odd ? P.chunk1 : P.chunk0;
-    for (unsigned base = static_cast<unsigned>(gw) * 32u; base < nsmall; base += static_cast<unsigned>(nw) * 32u) {
-        const unsigned i = base + lane;
-        bool lose = false;
-        int32_t V = 0, deg = 0;
-        if (i < nsmall) {
-            V = __ldcg(smallc + i);
-            lose = det_small<BATCH, FIRST>(P, colc, coln, V, deg);
-            st_deg += static_cast<unsigned long long>(deg);
-            st_cnt += 1;
-            if constexpr (BATCH) {
-                if (lose) note_graph_round(P, __ldg(P.vg + V), pass + 1);
-            }
-        }
-        warp_append(lose, V, smalln, cnt_next + kCntSmall, lane);
-    }
-    for (unsigned i = gw; i < nchunks; i += nw) {
-        const int4 it = __ldcg(chunkc + i);
-        det_chunk<BATCH, FIRST>(P, colc, coln, it, win, chunkn, cnt_next, pass, lane, st_deg, st_cnt);
-    }
-}
-
-template <bool BATCH>
-__global__ void __launch_bounds__(kBlock) det_round_kernel(RoundParams P) {
+template <bool BATCH, bool COMPACT>
+__global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(RoundParams P) {
     __shared__ unsigned s_win[kMaxWarps][kAccWords];
+    __shared__ unsigned s_fin[kMaxWarps][COMPACT ? kAccWords : 1];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     unsigned *win = s_win[wib];
+    unsigned *wfin = s_fin[wib];
+    if (P.stats && blockIdx.x == 0 && threadIdx.x == 0) P.stats[4 * P.stats_cap] = global_ns();
     int pass = P.pass_begin;
     for (;; ++pass) {
         unsigned *cc = P.cnt + kCnt * (pass % 3);
@@ -578,12 +737,35 @@ __global__ void __launch_bounds__(kBlock) det_round_kernel(RoundParams P) {
             break;
         }
         if (blockIdx.x == 0 && threadIdx.x < kCnt) P.cnt[kCnt * ((pass + 2) % 3) + threadIdx.x] = 0u;
-        unsigned long long st_deg = 0, st_cnt = 0;
-        if (pass == 1 && P.first_fast)
-            det_pass<BATCH, true>(P, pass, nsmall, nchunks, cn, win, lane, gw, nw, st_deg, st_cnt);
-        else
-            det_pass<BATCH, false>(P, pass, nsmall, nchunks, cn, win, lane, gw, nw, st_deg, st_cnt);
-        if (P.stats) flush_stats(P, pass, st_deg, st_cnt);
+        const bool odd = (pass & 1) != 0;
+        const uint64_t *colc = odd ? P.col0 : P.col1;
+        uint64_t *coln = odd ? P.col1 : P.col0;
+        const int32_t *smallc = odd ? P.small0 : P.small1;
+        int32_t *smalln = odd ? P.small1 : P.small0;
+        const int4 *chunkc = odd ? P.chunk0 : P.chunk1;
+        int4 *chunkn = odd ? P.chunk1 : P.chunk0;
+        unsigned long long st_deg = 0, st_cnt = 0, st_read = 0;
+        // work items of larger vertices first (they dominate), then one thread per small vertex
+        for (unsigned i = gw; i < nchunks; i += nw)
+            det_chunk<BATCH, COMPACT>(P, colc, coln, __ldcg(chunkc + i), win, wfin, chunkn, cn, pass, lane, st_deg,
+                                      st_cnt, st_read);
+        for (unsigned base = static_cast<unsigned>(gw) * 32u; base < nsmall; base += static_cast<unsigned>(nw) * 32u) {
+            const unsigned i = base + lane;
+            bool lose = false;
+            int32_t V = 0, deg = 0;
+            if (i < nsmall) {
+                V = __ldcg(smallc + i);
+                lose = det_small<BATCH>(P, colc, coln, V, deg);
+                st_deg += static_cast<unsigned long long>(deg);
+                st_read += static_cast<unsigned long long>(deg);
+                st_cnt += 1;
+                if constexpr (BATCH) {
+                    if (lose) note_graph_round(P, __ldg(P.vg + V), pass + 1);
+                }
+            }
+            warp_append(lose, V, smalln, cn + kCntSmall, lane);
+        }
+        if (P.stats) flush_stats(P, pass, st_deg, st_cnt, st_read);
         if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -593,13 +775,14 @@ __global__ void __launch_bounds__(kBlock) det_round_kernel(RoundParams P) {
 }
 
 template <bool BATCH>
-__global__ void __launch_bounds__(kBlock) ip_round_kernel(RoundParams P) {
+__global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) ip_round_kernel(RoundParams P) {
     __shared__ unsigned s_win[kMaxWarps][kAccWords];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     unsigned *win = s_win[wib];
-    int32_t *col = P.col0;
+    uint64_t *col = P.col0;
+    if (P.stats && blockIdx.x == 0 && threadIdx.x == 0) P.stats[4 * P.stats_cap] = global_ns();
     int pass = P.pass_begin;
     for (;; ++pass) {
         unsigned *cc = P.cnt + kCnt * (pass % 3);
@@ -619,11 +802,13 @@ __global__ void __launch_bounds__(kBlock) ip_round_kernel(RoundParams P) {
         const int4 *chunkc = odd ? P.chunk0 : P.chunk1;
         int4 *chunkn = odd ? P.chunk1 : P.chunk0;
         // phase 1: tentative First Fit on live colors
-        for (unsigned i = gw * 32u + lane; i < nsmall; i += nw * 32u) ip_small_assign<BATCH>(P, col, __ldcg(smallc + i));
         for (unsigned i = gw; i < nchunks; i += nw) ip_chunk_assign<BATCH>(P, col, __ldcg(chunkc + i), win, lane);
+        for (unsigned i = gw * 32u + lane; i < nsmall; i += nw * 32u) ip_small_assign<BATCH>(P, col, __ldcg(smallc + i));
         if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
         // phase 2: conflict detection
         unsigned long long st_deg = 0, st_cnt = 0;
+        for (unsigned i = gw; i < nchunks; i += nw)
+            ip_chunk_conflict<BATCH>(P, col, __ldcg(chunkc + i), win, chunkn, cn, pass, lane, st_deg, st_cnt);
         for (unsigned base = gw * 32u; base < nsmall; base += nw * 32u) {
             const unsigned i = base + lane;
             bool lose = false;
@@ -639,9 +824,7 @@ __global__ void __launch_bounds__(kBlock) ip_round_kernel(RoundParams P) {
             }
             warp_append(lose, V, smalln, cn + kCntSmall, lane);
         }
-        for (unsigned i = gw; i < nchunks; i += nw)
-            ip_chunk_conflict<BATCH>(P, col, __ldcg(chunkc + i), chunkn, cn, pass, lane, st_deg, st_cnt);
-        if (P.stats) flush_stats(P, pass, st_deg, st_cnt);
+        if (P.stats) flush_stats(P, pass, st_deg, st_cnt, 2 * st_deg);
         if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -716,12 +899,14 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
             const bool ok = b >= 0 && b <= e && e <= lim && (lv != 0 || b == 0) && (lv != ng - 1 || e == lim);
             if (!ok) set_error(P.err, GC_ERR_INVALID_GRAPH, V, b);
             const int64_t d = ok ? e - b : 0;
-            P.prio[V] = static_cast<uint32_t>(vertex_hash(P.seed, static_cast<uint32_t>(lv)) >> 32);
+            const uint32_t pv = static_cast<uint32_t>(vertex_hash(P.seed, static_cast<uint32_t>(lv)) >> 33);
+            // an isolated vertex takes color 0 in round 1 and never changes: it is final from the start
             if (MODE == GC_MODE_DETERMINISTIC) {
-                P.col0[V] = 0;
-                P.col1[V] = 0;
+                // C_1 = 0 everywhere: round 1's First Fit sees no colored neighbour
+                P.col0[V] = pack_state(0, pv, d == 0);
+                P.col1[V] = pack_state(0, pv, d == 0);
             } else {
-                P.col0[V] = d == 0 ? 0 : -1;
+                P.col0[V] = pack_state(d == 0 ? 0 : -1, pv, d == 0);
             }
             if (d > 0) {
                 kind = d <= P.T1 ? 1 : 2;
@@ -748,8 +933,10 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
 }
 
 // Expands the larger vertices collected by setup into work items of round P.pass_begin, with
-// accumulator slots after those already taken in that round.  One warp per vertex.
-template <bool BATCH>
+// accumulator slots after those already taken in that round.  One warp per vertex.  COMPACT: the
+// vertex keeps its slot for the whole run; the slot is cleared and records the id of the vertex's
+// first work item (the items of round 1 are numbered consecutively per vertex).
+template <bool BATCH, bool COMPACT>
 __global__ void expand_kernel(RoundParams P, int32_t n_items) {
     if (n_items < 0) n_items = static_cast<int32_t>(__ldcg(P.tmp));  // count left on the device by setup
     const int lane = threadIdx.x & 31;
@@ -769,7 +956,9 @@ __global__ void expand_kernel(RoundParams P, int32_t n_items) {
         }
         slot = __shfl_sync(kFull, slot, 0);
         cb = __shfl_sync(kFull, cb, 0);
-        P.acc[static_cast<size_t>(slot) * kAccStride + lane] = 0u;
+        unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
+        a[lane] = 0u;
+        a[32 + lane] = (COMPACT && lane == kAccBase - 32) ? cb : 0u;
         for (int32_t q = lane; q < nch; q += 32) chunk_cur[cb + q] = make_int4(V, q, static_cast<int32_t>(slot), nch);
     }
 }
@@ -779,13 +968,13 @@ __global__ void expand_kernel(RoundParams P, int32_t n_items) {
 template <bool BATCH>
 __global__ void count_mark_kernel(RoundParams P, const int32_t *colors_sel, int32_t v_begin, int32_t v_end,
                                   unsigned *bitmap, int32_t *gmax, int32_t *out) {
-    const int32_t *colors = (colors_sel && (*colors_sel & 1)) ? P.col1 : P.col0;
+    const uint64_t *state = (colors_sel && (*colors_sel & 1)) ? P.col1 : P.col0;
     const bool copy = out != nullptr && P.err[0] == 0;
     const int64_t count = static_cast<int64_t>(v_end) - v_begin;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride) {
         const int32_t V = static_cast<int32_t>(v_begin + i);
-        const int32_t c = __ldcg(colors + V);
+        const int32_t c = color_of(__ldcg(state + V));
         if (copy) out[i] = c;
         if (c < 0) continue;
         int32_t g = 0;
@@ -911,34 +1100,47 @@ cudaError_t launch_setup(const RoundParams &P, int mode, bool batch, int32_t v_b
     return cudaGetLastError();
 }
 
-cudaError_t launch_expand(const RoundParams &P, bool batch, int32_t n_items, cudaStream_t s) {
+cudaError_t launch_expand(const RoundParams &P, bool batch, bool compact, int32_t n_items, cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
     const int grid = n_items < 0 ? sm_count() * 8 : grid_for(static_cast<int64_t>(n_items) * 32, 256, sm_count() * 16);
-    if (batch)
-        expand_kernel<true><<<grid, 256, 0, s>>>(P, n_items);
-    else
-        expand_kernel<false><<<grid, 256, 0, s>>>(P, n_items);
+    if (batch) {
+        if (compact)
+            expand_kernel<true, true><<<grid, 256, 0, s>>>(P, n_items);
+        else
+            expand_kernel<true, false><<<grid, 256, 0, s>>>(P, n_items);
+    } else {
+        if (compact)
+            expand_kernel<false, true><<<grid, 256, 0, s>>>(P, n_items);
+        else
+            expand_kernel<false, false><<<grid, 256, 0, s>>>(P, n_items);
+    }
     return cudaGetLastError();
 }
 
-static const void *round_kernel_fn(int mode, bool batch) {
-    if (mode == GC_MODE_DETERMINISTIC)
-        return batch ? reinterpret_cast<const void *>(&det_round_kernel<true>)
-                     : reinterpret_cast<const void *>(&det_round_kernel<false>);
+static const void *round_kernel_fn(int mode, bool batch, bool compact) {
+    if (mode == GC_MODE_DETERMINISTIC) {
+        if (batch)
+            return compact ? reinterpret_cast<const void *>(&det_round_kernel<true, true>)
+                           : reinterpret_cast<const void *>(&det_round_kernel<true, false>);
+        return compact ? reinterpret_cast<const void *>(&det_round_kernel<false, true>)
+                       : reinterpret_cast<const void *>(&det_round_kernel<false, false>);
+    }
     return batch ? reinterpret_cast<const void *>(&ip_round_kernel<true>)
                  : reinterpret_cast<const void *>(&ip_round_kernel<false>);
 }
 
-cudaError_t round_kernel_occupancy(int mode, bool batch, int block, int *blocks_per_sm) {
+cudaError_t round_kernel_occupancy(int mode, bool batch, bool compact, int block, int *blocks_per_sm) {
     if (block != kBlock) return cudaErrorInvalidValue;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, round_kernel_fn(mode, batch), block, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, round_kernel_fn(mode, batch, compact), block,
+                                                         0);
 }
 
-cudaError_t launch_rounds(const RoundParams &P, int mode, bool batch, int grid, int block, cudaStream_t s) {
+cudaError_t launch_rounds(const RoundParams &P, int mode, bool batch, bool compact, int grid, int block,
+                          cudaStream_t s) {
     if (block != kBlock) return cudaErrorInvalidValue;
     RoundParams arg = P;
     void *args[] = {&arg};
-    return cudaLaunchCooperativeKernel(round_kernel_fn(mode, batch), dim3(grid), dim3(block), args, 0, s);
+    return cudaLaunchCooperativeKernel(round_kernel_fn(mode, batch, compact), dim3(grid), dim3(block), args, 0, s);
 }
 
 cudaError_t launch_count_colors(const RoundParams &P, bool batch, const int32_t *colors_sel, int32_t v_begin,

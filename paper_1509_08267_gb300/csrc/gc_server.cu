@@ -130,7 +130,7 @@ struct gc_server {
     int grid = 0;
     int64_t PV = 0, PE = 0, PI = 0, PC = 0;  // pool capacities: vertices, entries, large vertices, work items
     int32_t S = 0;                           // slots
-    gc::DevBuf rowptr, colidx, col0, col1, prio, small0, small1, items, chunk0, chunk1, acc, vg, ctl, bitmap;
+    gc::DevBuf rowptr, colidx, col0, col1, outbuf, small0, small1, items, chunk0, chunk1, acc, vg, ctl, bitmap;
     gc::DevBuf g_vbase, g_n, g_ebase, g_rbase, g_m, glast, gmax, gcount;
     std::vector<int64_t> h_vbase, h_ebase, h_rbase, h_m;
     std::vector<int32_t> h_n, h_glast;
@@ -182,9 +182,8 @@ RoundParams params(gc_server *s) {
     P.g_m = s->g_m.as<int64_t>();
     P.vg = s->vg.as<int32_t>();
     P.seed = s->cfg.seed;
-    P.col0 = s->col0.as<int32_t>();
-    P.col1 = s->col1.as<int32_t>();
-    P.prio = s->prio.as<uint32_t>();
+    P.col0 = s->col0.as<uint64_t>();
+    P.col1 = s->col1.as<uint64_t>();
     P.small0 = s->small0.as<int32_t>();
     P.small1 = s->small1.as<int32_t>();
     P.chunk0 = s->chunk0.as<int4>();
@@ -203,7 +202,6 @@ RoundParams params(gc_server *s) {
     P.pass_begin = s->next_pass;
     P.pass_end = s->next_pass + kRoundsPerLaunch;
     P.cap_is_error = 0;
-    P.first_fast = 0;
     P.spin_ns = 1000000000LL;
     P.T1 = kT1;
     P.CH = kCH;
@@ -277,7 +275,7 @@ int admit(gc_server *s, const std::vector<Request *> &adm) {
     for (Request *r : adm)
         SRV_CUDA(launch_setup(P, s->cfg.mode, true, static_cast<int32_t>(r->vbase),
                               static_cast<int32_t>(r->vbase + r->n), r->slot, st));
-    SRV_CUDA(launch_expand(P, true, -1, st));
+    SRV_CUDA(launch_expand(P, true, false, -1, st));
     // the pinned-free host copies of the CSR are no longer needed once the copies are done
     SRV_CUDA(cudaStreamSynchronize(st));
     for (Request *r : adm) {
@@ -302,14 +300,12 @@ int retire(gc_server *s, const std::vector<Request *> &fin) {
         SRV_CUDA(cudaMemsetAsync(s->gmax.as<int32_t>() + g, 0xff, 4, st));
         SRV_CUDA(launch_count_colors(P, true, s->cfg.mode == GC_MODE_DETERMINISTIC ? s->glast.as<int32_t>() + g : nullptr,
                                      static_cast<int32_t>(r->vbase), static_cast<int32_t>(r->vbase + r->n), g, g + 1,
-                                     s->bitmap.as<unsigned>(), s->gmax.as<int32_t>(), s->gcount.as<int32_t>(), nullptr,
-                                     st));
+                                     s->bitmap.as<unsigned>(), s->gmax.as<int32_t>(), s->gcount.as<int32_t>(),
+                                     s->outbuf.as<int32_t>() + r->vbase, st));
         r->colors.resize(r->n);
-        const int32_t last = s->h_glast[g];
-        const int32_t *src = (s->cfg.mode == GC_MODE_DETERMINISTIC && (last & 1)) ? s->col1.as<int32_t>()
-                                                                                   : s->col0.as<int32_t>();
         if (r->n)
-            SRV_CUDA(cudaMemcpyAsync(r->colors.data(), src + r->vbase, 4 * r->n, cudaMemcpyDeviceToHost, st));
+            SRV_CUDA(cudaMemcpyAsync(r->colors.data(), s->outbuf.as<int32_t>() + r->vbase, 4 * r->n,
+                                     cudaMemcpyDeviceToHost, st));
         SRV_CUDA(cudaMemcpyAsync(&sel[i], s->gcount.as<int32_t>() + g, 4, cudaMemcpyDeviceToHost, st));
     }
     SRV_CUDA(cudaStreamSynchronize(st));
@@ -374,7 +370,7 @@ void worker_main(gc_server *s) {
             break;
         }
         RoundParams P = params(s);
-        cudaError_t e = launch_rounds(P, s->cfg.mode, true, s->grid, 256, s->stream);
+        cudaError_t e = launch_rounds(P, s->cfg.mode, true, false, s->grid, 256, s->stream);
         Ctl h{};
         if (e == cudaSuccess) e = cudaMemcpyAsync(&h, s->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream);
         if (e == cudaSuccess)
@@ -447,8 +443,8 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
         gc::DevBuf *b;
         size_t bytes;
     } plan[] = {
-        {&s->rowptr, 4 * (V + Sz)}, {&s->colidx, 4 * static_cast<size_t>(s->PE)}, {&s->col0, 4 * V}, {&s->col1, 4 * V},
-        {&s->prio, 4 * V}, {&s->small0, 4 * V}, {&s->small1, 4 * V}, {&s->items, 4 * V}, {&s->vg, 4 * V},
+        {&s->rowptr, 4 * (V + Sz)}, {&s->colidx, 4 * static_cast<size_t>(s->PE)}, {&s->col0, 8 * V}, {&s->col1, 8 * V},
+        {&s->outbuf, 4 * V}, {&s->small0, 4 * V}, {&s->small1, 4 * V}, {&s->items, 4 * V}, {&s->vg, 4 * V},
         {&s->chunk0, 16 * static_cast<size_t>(s->PC)}, {&s->chunk1, 16 * static_cast<size_t>(s->PC)},
         {&s->acc, 4 * gc::kAccStride * static_cast<size_t>(s->PI)}, {&s->ctl, sizeof(gc::Ctl)},
         {&s->bitmap, 4 * (V / 32 + 4)}, {&s->g_vbase, 8 * Sz}, {&s->g_n, 4 * Sz}, {&s->g_ebase, 8 * Sz},
@@ -469,7 +465,7 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
                               cudaGetErrorString(e));
     }
     int per_sm = 0, sms = 0;
-    gc::round_kernel_occupancy(cfg->mode, true, 256, &per_sm);
+    gc::round_kernel_occupancy(cfg->mode, true, false, 256, &per_sm);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     s->grid = std::max(1, per_sm * sms);
     s->h_vbase.assign(Sz, 0);

@@ -172,6 +172,28 @@ int gc_color_batch_ex(int32_t G, const int64_t *vtx_off, const int64_t *edge_off
  */
 int gc_validate_graph(int32_t n, const int32_t *rowptr, const int32_t *colidx, int flags);
 
+/*
+ * gc_color_noalloc -- deterministic coloring of one graph without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * (code running inside an allocator or a memory-pool callback, or under a framework that owns every
+ * device allocation and forbids side allocations).  It gives exactly gc_color's deterministic
+ * result, but works in a fixed scratch array built into the library (about 5.2 MB of device memory,
+ * held by every GPU that loads the library until the process exits), so it accepts at most
+ * 16,384 vertices and 2^20 adjacency entries; larger graphs return GC_ERR_INVALID_ARG with the
+ * outputs untouched.
+ *   n, seed    as gc_color (mode is always GC_MODE_DETERMINISTIC)
+ *   rowptr, colidx, colors_out   device memory of the current device (no host arrays)
+ *   ncolors, rounds              host int32* (may be NULL)
+ *   stream     cudaStream_t the work is queued on (NULL = the legacy default stream); the call
+ *              returns after the stream has finished it
+ * The first call on a device looks up the scratch array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every call reuses the
+ * same array and clears what must start empty, so calls whose work overlaps on the GPU (from
+ * several host threads or streams at once) race and must be serialised by the caller.
+ */
+int gc_color_noalloc(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed, int32_t *colors_out,
+                     int32_t *ncolors, int32_t *rounds, void *stream);
+
 /* Message for the last error on the calling thread ("" if none). Valid until the next call. */
 const char *gc_last_error(void);
 

@@ -103,6 +103,10 @@ def _L():
         lib.gg_grid5_nnz.argtypes = [i32, i32]
         lib.gg_grid5.restype = i64
         lib.gg_grid5.argtypes = [i32, i32, p, p]
+        lib.gg_batch.restype = ctypes.c_int
+        lib.gg_batch.argtypes = [i32, p, p, p, p, dbl, dbl, dbl, u64, p, p, p, p, p]
+        lib.gg_batch_pack.restype = None
+        lib.gg_batch_pack.argtypes = [i32, p, p, p]
         _lib = lib
     return _lib
 
@@ -137,9 +141,13 @@ def from_edges(n: int, edges, name: str = "") -> Graph:
     return from_pairs(n, e[:, 0], e[:, 1], name=name)
 
 
+def _round_half_up(x: float) -> int:
+    return int(math.floor(x + 0.5))
+
+
 def er(n: int, avg_degree: float, seed: int) -> Graph:
-    """Erdos-Renyi G(n, M) with M = round(n * avg_degree / 2) uniform pairs u != v (with replacement)."""
-    M = int(round(n * avg_degree / 2))
+    """Erdos-Renyi G(n, M) with M = floor(n * avg_degree / 2 + 1/2) uniform pairs u != v (with replacement)."""
+    M = _round_half_up(n * avg_degree / 2)
     src = np.empty(M, dtype=np.int32)
     dst = np.empty(M, dtype=np.int32)
     if _L().gg_er_pairs(n, M, seed & U64, _ptr(src), _ptr(dst)) < 0:
@@ -159,7 +167,7 @@ def rmat(scale: int, edge_factor: float, seed: int, a: float = 0.57, b: float = 
     dropped and (by default) ids permuted by a seeded uniform permutation."""
     if n is None:
         n = 1 << scale
-    M = int(round(edge_factor * n))
+    M = _round_half_up(edge_factor * n)
     src = np.empty(M, dtype=np.int32)
     dst = np.empty(M, dtype=np.int32)
     if _L().gg_rmat_pairs(n, scale, M, a, b, c, seed & U64, _ptr(src), _ptr(dst)) < 0:
@@ -305,7 +313,33 @@ def pack(graphs: list[Graph]) -> Batch:
 
 
 def batch_mix(G: int, seed: int, **kw) -> Batch:
-    return pack([make_from_spec(s) for s in batch_specs(G, seed, **kw)])
+    """The batch of batch_specs(G, seed, ...), generated in parallel in C (same graphs as
+    make_from_spec graph by graph)."""
+    specs = batch_specs(G, seed, **kw)
+    if any(s.kind not in ("er", "rmat") for s in specs):
+        return pack([make_from_spec(s) for s in specs])
+    kind = np.array([0 if s.kind == "er" else 1 for s in specs], np.int32)
+    n = np.array([s.n for s in specs], np.int32)
+    param = np.array([s.param for s in specs], np.float64)
+    seeds = np.array([s.seed for s in specs], np.uint64)
+    M = np.array([_round_half_up(s.n * s.param / 2) if s.kind == "er" else _round_half_up(s.n * s.param)
+                  for s in specs], np.int64)
+    M[n < 2] = 0
+    vtx_off = np.zeros(G + 1, np.int64)
+    vtx_off[1:] = np.cumsum(n)
+    cap_off = np.zeros(G + 1, np.int64)
+    cap_off[1:] = np.cumsum(2 * M)
+    rowptr = np.empty(int(vtx_off[-1]) + G, np.int32)
+    colidx = np.empty(max(int(cap_off[-1]), 1), np.int32)
+    nnz = np.zeros(G, np.int64)
+    if _L().gg_batch(G, kind.ctypes.data, n.ctypes.data, param.ctypes.data, seeds.ctypes.data, 0.57, 0.19, 0.19,
+                     PERM_STREAM_OFFSET, vtx_off.ctypes.data, cap_off.ctypes.data, rowptr.ctypes.data,
+                     colidx.ctypes.data, nnz.ctypes.data) != 0:
+        raise MemoryError("gg_batch")
+    edge_off = np.zeros(G + 1, np.int64)
+    edge_off[1:] = np.cumsum(nnz)
+    _L().gg_batch_pack(G, cap_off.ctypes.data, edge_off.ctypes.data, colidx.ctypes.data)
+    return Batch(G, vtx_off, edge_off, rowptr, colidx[: int(edge_off[-1])])
 
 
 # ---------------------------------------------------------------------------------------------

@@ -285,3 +285,127 @@ int64_t gg_grid5(int32_t Lx, int32_t Ly, int32_t *rowptr, int32_t *colidx) {
     rowptr[n] = (int32_t)p;
     return p;
 }
+
+/*
+ * A whole batch of graphs generated in parallel, one graph per thread at a time (each graph's
+ * output depends only on its own parameters).  Graph g is ER (kind 0: M = floor(n*param/2 + 1/2)
+ * pairs) or R-MAT (kind 1: M = floor(n*param + 1/2) pairs, scale = ceil(log2 n), a/b/c as given,
+ * ids permuted with the stream seed + perm_offset).  Graph g's local rowptr goes to
+ * rowptr + vtx_off[g] + g and its local column ids to colidx + cap_off[g] (room for 2M entries);
+ * nnz_out[g] receives its entry count.  gg_batch_pack then moves the column ids together.
+ * Returns 0 or -1.
+ */
+static int gg_one_graph(int kind, int32_t n, double param, uint64_t seed, double a, double b, double c,
+                        uint64_t perm_offset, int32_t *rowptr, int32_t *colidx, int64_t *nnz_out) {
+    int64_t M = kind == 0 ? (int64_t)(n * param / 2.0 + 0.5) : (int64_t)(n * param + 0.5);  /* floor(x + 1/2) */
+    if (n < 2) M = 0;
+    int32_t *src = (int32_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(int32_t));
+    int32_t *dst = (int32_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(int32_t));
+    int32_t *perm = NULL;
+    int32_t *rp = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int32_t *ci = (int32_t *)malloc((size_t)(2 * M > 0 ? 2 * M : 1) * sizeof(int32_t));
+    if (!src || !dst || !rp || !ci) {
+        free(src);
+        free(dst);
+        free(rp);
+        free(ci);
+        return -1;
+    }
+    if (kind == 0) {
+        gg_er_pairs(n, M, seed, src, dst);
+    } else {
+        int scale = 1;
+        while (((int64_t)1 << scale) < n) ++scale;
+        /* sequential attempt loop (n is generally not a power of two) */
+        double ab = a + b, abc = a + b + c;
+        uint64_t attempt = 0;
+        for (int64_t i = 0; i < M;) {
+            int64_t s, d;
+            gg_rmat_one(scale, a, ab, abc, seed, attempt++, &s, &d);
+            if (s >= n || d >= n) continue;
+            src[i] = (int32_t)s;
+            dst[i] = (int32_t)d;
+            ++i;
+        }
+        perm = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+        if (!perm) {
+            free(src);
+            free(dst);
+            free(rp);
+            free(ci);
+            return -1;
+        }
+        gg_permutation(n, seed + perm_offset, perm);
+    }
+    /* serial CSR build (the batch is parallel across graphs) */
+    int64_t *cursor = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    for (int64_t i = 0; i < M; ++i) {
+        int32_t s = src[i], d = dst[i];
+        if (s == d) continue;
+        if (perm) {
+            s = perm[s];
+            d = perm[d];
+        }
+        cursor[s + 1]++;
+        cursor[d + 1]++;
+    }
+    for (int32_t v = 0; v < n; ++v) cursor[v + 1] += cursor[v];
+    int64_t *start = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+    memcpy(start, cursor, ((size_t)n + 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < M; ++i) {
+        int32_t s = src[i], d = dst[i];
+        if (s == d) continue;
+        if (perm) {
+            s = perm[s];
+            d = perm[d];
+        }
+        ci[cursor[s]++] = d;
+        ci[cursor[d]++] = s;
+    }
+    int64_t out = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        int64_t bb = start[v], e = start[v + 1];
+        if (e - bb > 1) qsort(ci + bb, (size_t)(e - bb), sizeof(int32_t), gg_cmp_i32);
+        rp[v] = (int32_t)out;
+        for (int64_t j = bb; j < e; ++j)
+            if (j == bb || ci[j] != ci[j - 1]) ci[out++] = ci[j];
+    }
+    rp[n] = (int32_t)out;
+    *nnz_out = out;
+    if (rowptr) {
+        memcpy(rowptr, rp, ((size_t)n + 1) * sizeof(int32_t));
+        memcpy(colidx, ci, (size_t)out * sizeof(int32_t));
+    }
+    free(cursor);
+    free(start);
+    free(src);
+    free(dst);
+    free(perm);
+    free(rp);
+    free(ci);
+    return 0;
+}
+
+int gg_batch(int32_t G, const int32_t *kind, const int32_t *n, const double *param, const uint64_t *seed, double a,
+             double b, double c, uint64_t perm_offset, const int64_t *vtx_off, const int64_t *cap_off,
+             int32_t *rowptr, int32_t *colidx, int64_t *nnz_out) {
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int32_t g = 0; g < G; ++g) {
+        int64_t nz = 0;
+        if (gg_one_graph(kind[g], n[g], param[g], seed[g], a, b, c, perm_offset, rowptr + vtx_off[g] + g,
+                         colidx + cap_off[g], &nz) != 0)
+            bad |= 1;
+        nnz_out[g] = nz;
+    }
+    return bad ? -1 : 0;
+}
+
+/* Moves graph g's column ids from cap_off[g] to edge_off[g] (edge_off[g] <= cap_off[g], increasing). */
+void gg_batch_pack(int32_t G, const int64_t *cap_off, const int64_t *edge_off, int32_t *colidx) {
+    for (int32_t g = 0; g < G; ++g) {
+        int64_t len = edge_off[g + 1] - edge_off[g];
+        if (len > 0 && cap_off[g] != edge_off[g])
+            memmove(colidx + edge_off[g], colidx + cap_off[g], (size_t)len * sizeof(int32_t));
+    }
+}

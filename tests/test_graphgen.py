@@ -79,3 +79,13 @@ def test_batch_specs_distribution():
     assert sum(s.kind == "er" for s in specs) == 2048
     er_d = [s.param for s in specs if s.kind == "er"]
     assert 4 <= min(er_d) and max(er_d) <= 64
+
+
+def test_parallel_batch_generation_matches_graph_by_graph():
+    fast = gg.batch_mix(30, 3, nmin=100, nmax=30_000)
+    slow = gg.pack([gg.make_from_spec(s) for s in gg.batch_specs(30, 3, nmin=100, nmax=30_000)])
+    for a, b in [(fast.vtx_off, slow.vtx_off), (fast.edge_off, slow.edge_off), (fast.rowptr, slow.rowptr),
+                 (fast.colidx, slow.colidx)]:
+        assert np.array_equal(a, b)
+    for g in range(fast.G):
+        check_simple(fast.graph(g))

@@ -19,6 +19,7 @@ import threading
 import time
 
 import numpy as np
+from math import log as math_log
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -131,6 +132,166 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batch_graphs(name):
+    """batchG: G graphs of the mixed batch recipe (seed 3), cached on disk."""
+    import graphgen as gg
+    G = int(name[5:])
+    path = os.path.join(gg.cache_dir(), f"{name}_s3.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return gg.Batch(G, z["vtx_off"], z["edge_off"], z["rowptr"], z["colidx"])
+    b = gg.batch_mix(G, 3)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, vtx_off=b.vtx_off, edge_off=b.edge_off, rowptr=b.rowptr, colidx=b.colidx)
+    os.replace(tmp, path)
+    return b
+
+
+def run_batch(args, rank, world):
+    """Batched coloring of G graphs in one persistent launch against a loop of gc_color over the same
+    device-resident graphs; both must give identical colorings."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1509_08267_gb300 as gc
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    b = batch_graphs(args.workload)
+    G = b.G
+    vo = torch.from_numpy(b.vtx_off).to(dev)
+    eo = torch.from_numpy(b.edge_off).to(dev)
+    rp = torch.from_numpy(b.rowptr).to(dev)
+    ci = torch.from_numpy(b.colidx).to(dev)
+    N, NNZ = int(b.vtx_off[-1]), int(b.edge_off[-1])
+    out = torch.empty(N, dtype=torch.int32, device=dev)
+    opt = gc.Options(flags=gc.FLAG_TIMING)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        gc.color_batch(vo, eo, rp, ci, args.mode, HASH_SEED, out=out, options=opt)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        _, nc_b, rd_b, st = gc.color_batch(vo, eo, rp, ci, args.mode, HASH_SEED, out=out, options=opt, stats=True)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_batch = sum(a.elapsed_time(c) for a, c in ev) / 1e3 / args.steps
+    # one by one: the same device-resident graphs, one gc_color call each (each call synchronises)
+    solo = torch.empty(N, dtype=torch.int32, device=dev)
+    vo_h, eo_h = b.vtx_off, b.edge_off
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nc_s = np.zeros(G, np.int32)
+    rd_s = np.zeros(G, np.int32)
+    for g in range(G):
+        v0, v1, e0, e1 = int(vo_h[g]), int(vo_h[g + 1]), int(eo_h[g]), int(eo_h[g + 1])
+        r = gc.color(rp[v0 + g: v1 + g + 1], ci[e0:e1], args.mode, HASH_SEED, out=solo[v0:v1])
+        nc_s[g], rd_s[g] = r.ncolors, r.rounds
+    torch.cuda.synchronize()
+    t_solo = time.perf_counter() - t0
+    same = bool(torch.equal(out, solo)) and np.array_equal(nc_s, nc_b) and np.array_equal(rd_s, rd_b)
+    m_und = NNZ / 2
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * m_und / t_batch / 1e9, "unit": "Gedges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "graphs": G, "vertices": N, "nnz": NNZ,
+                       "recipe": "n log-uniform [100, 2e5]; even graphs ER (avg degree U[4,64]), odd graphs R-MAT "
+                                 "(edge factor U[8,16]); seed 3", "mode": args.mode, "hash_seed": HASH_SEED},
+            "one_by_one": {"value": m_und / t_solo / 1e9, "unit": "Gedges/s", "seconds": t_solo,
+                           "note": "loop of gc_color over the same device-resident graphs"},
+            "batched_over_one_by_one": t_solo / t_batch,
+            "identical_colorings": same,
+            "batch_rounds": int(st.rounds), "batch_kernel_ms": st.kernel_ms,
+            "gpu_launches": 6 * args.steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def serve_pool(count, seed=4):
+    """Request graphs for the serving benchmark: n log-uniform in [1e3, 2e6], a mix of ER (avg degree
+    U[4,32]), R-MAT (edge factor U[4,16]) and 2-D 5-point grids, from the stream `seed`."""
+    import math
+
+    import graphgen as gg
+    specs = []
+    lo, hi = math.log(1e3), math.log(2e6)
+    for i in range(count):
+        u0 = (gg.draw(seed, 4 * i) >> 11) / 9007199254740992.0
+        u1 = (gg.draw(seed, 4 * i + 1) >> 11) / 9007199254740992.0
+        n = int(round(math.exp(lo + u0 * (hi - lo))))
+        kind = ("er", "rmat", "grid")[i % 3]
+        param = 4 + u1 * 28 if kind == "er" else 4 + u1 * 12
+        specs.append(gg.BatchSpec(kind, n, param, gg.draw(seed, 4 * i + 2)))
+    return [gg.make_from_spec(s) for s in specs]
+
+
+def run_serve(args, rank, world):
+    """Poisson request stream into the continuous-batching server against the same requests colored
+    one by one with gc_color; results must be identical."""
+    import torch
+
+    import paper_1509_08267_gb300 as gc
+    import graphgen as gg
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    count = args.requests
+    graphs = serve_pool(count)
+    rate = 2000.0
+    gaps = [-math_log(1.0 - ((gg.draw(4, 10_000_000 + i) >> 11) / 9007199254740992.0)) / rate for i in range(count)]
+    pv = sum(g.n for g in graphs) + 1
+    pe = sum(g.nnz for g in graphs) + 1
+    pool_v = min(pv, 16_000_000)
+    pool_e = min(pe, 600_000_000)
+    results = {}
+    with gc.Server(pool_vertices=pool_v, pool_entries=pool_e, mode=args.mode, seed=HASH_SEED, device=local) as srv:
+        t0 = time.perf_counter()
+        ids = []
+        at = 0.0
+        for g, gap in zip(graphs, gaps):
+            at += gap
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            ids.append(srv.submit(g.rowptr, g.colidx))
+        for i, rid in enumerate(ids):
+            results[i] = srv.poll(rid)
+        t_serve = time.perf_counter() - t0
+        st = srv.stats()
+    # one by one, host arrays in and out as the server takes them
+    t1 = time.perf_counter()
+    same = True
+    for i, g in enumerate(graphs):
+        r = gc.color(g.rowptr, g.colidx, args.mode, HASH_SEED)
+        if args.mode == "det":
+            same &= bool(np.array_equal(r.colors, results[i][0])) and r.ncolors == results[i][1] and \
+                r.rounds == results[i][2]
+    t_solo = time.perf_counter() - t1
+    m_und = sum(g.nnz for g in graphs) / 2
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": m_und / t_serve / 1e9, "unit": "Gedges/s", "n_gpus": 1, "steps": count,
+            "warmup": 0, "ms_per_step": t_serve * 1e3 / count, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "serve", "requests": count, "arrival": "Poisson, mean 2,000 req/s, seed 4",
+                       "graphs": "n log-uniform [1e3, 2e6]; ER / R-MAT / 2-D grid mix",
+                       "pool_vertices": pool_v, "pool_entries": pool_e, "mode": args.mode},
+            "graphs_per_s": count / t_serve, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "one_by_one": {"value": m_und / t_solo / 1e9, "unit": "Gedges/s", "graphs_per_s": count / t_solo},
+            "served_over_one_by_one": t_solo / t_serve, "identical_colorings": same,
+            "rounds_run": st["rounds_run"],
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -141,6 +302,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--requests", type=int, default=200, help="serving workload: requests replayed")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -161,6 +323,16 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload.startswith("batch"):
+        run_batch(args, rank, world)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if args.workload == "serve":
+        run_serve(args, rank, world)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     gc.load()
     g = gg.workload(args.workload)

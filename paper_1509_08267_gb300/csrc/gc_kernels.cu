@@ -12,8 +12,8 @@
 // double-buffered (col0 / col1), so the result does not depend on the order of the sweep.
 // In-place mode.  Phase 1 reads and writes one live color array, then a barrier, then phase 2.
 //
-// Work decomposition per round: vertices of degree <= T1 take one thread each (their First Fit
-// fits a 64-bit window because the answer is at most deg(v)); larger vertices are split into
+// Work decomposition per round: vertices of degree <= T1 (<= 127) take one thread each (their First
+// Fit fits a 128-bit register window because the answer is at most deg(v)); larger vertices are split into
 // work items of CH adjacency entries handled by one warp each.  The items of one vertex merge
 // their 512-color windows and conflict flags in an accumulator slot; the warp that finishes the
 // last item computes the vertex's result.  Worklists are appended with warp-aggregated atomics.
@@ -341,17 +341,19 @@ __device__ __forceinline__ void sweep(const RoundParams &P, const Row &r, const 
     }
 }
 
-// Per-thread sweep of a short row (degree <= T1 <= 63): window [0, 64) and conflict flag.
+// Per-thread sweep of a short row (degree <= T1 <= 127): window [0, 128) in two 64-bit masks (the
+// least free color is at most deg(v)) and conflict flag.
 template <bool BATCH, bool WINDOW, bool CONFLICT>
 __device__ __forceinline__ void sweep_small(const RoundParams &P, const Row &r, const uint64_t *colc, int32_t cv,
-                                            uint32_t pv, uint64_t &mask, bool &lose) {
-    for (int64_t j0 = r.b; j0 < r.e; j0 += kPer) {
-        int32_t ul[kPer];
-        uint64_t w[kPer];
+                                            uint32_t pv, uint64_t &mask0, uint64_t &mask1, bool &lose) {
+    constexpr int kT = 8;  // loads in flight per thread
+    for (int64_t j0 = r.b; j0 < r.e; j0 += kT) {
+        int32_t ul[kT];
+        uint64_t w[kT];
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) ul[q] = j0 + q < r.e ? load_entry(P.colidx + j0 + q) : 0;
+        for (int q = 0; q < kT; ++q) ul[q] = j0 + q < r.e ? load_entry(P.colidx + j0 + q) : 0;
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
+        for (int q = 0; q < kT; ++q) {
             w[q] = kNoNeighbour;
             if (j0 + q < r.e) {
                 const int32_t U = neighbour(P, r, ul[q], j0 + q);
@@ -359,10 +361,13 @@ __device__ __forceinline__ void sweep_small(const RoundParams &P, const Row &r, 
             }
         }
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
+        for (int q = 0; q < kT; ++q) {
             const int32_t c = color_of(w[q]);
             if constexpr (WINDOW) {
-                if (static_cast<unsigned>(c) < 64u) mask |= 1ull << c;
+                if (static_cast<unsigned>(c) < 64u)
+                    mask0 |= 1ull << c;
+                else if (static_cast<unsigned>(c) < 128u)
+                    mask1 |= 1ull << (c - 64);
             }
             if constexpr (CONFLICT) {
                 if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
@@ -370,6 +375,11 @@ __device__ __forceinline__ void sweep_small(const RoundParams &P, const Row &r, 
             }
         }
     }
+}
+
+// Least color absent from a two-mask window [0, 128) (never full for degree <= 127).
+__device__ __forceinline__ int32_t first_free_128(uint64_t mask0, uint64_t mask1) {
+    return ~mask0 ? __ffsll(static_cast<long long>(~mask0)) - 1 : 64 + __ffsll(static_cast<long long>(~mask1)) - 1;
 }
 
 // Merges a work item's window and flag into the vertex's accumulator slot.  Returns true in the
@@ -427,10 +437,10 @@ __device__ __forceinline__ bool det_small(const RoundParams &P, const uint64_t *
     const uint64_t self = load_state(colc + V);
     const int32_t cv = color_of(self);
     const uint32_t pv = prio_of(self);
-    uint64_t mask = 0;
+    uint64_t mask0 = 0, mask1 = 0;
     bool lose = false;
-    sweep_small<BATCH, true, true>(P, r, colc, cv, pv, mask, lose);
-    det_write(colc, coln, V, lose, cv, lose ? __ffsll(static_cast<long long>(~mask)) - 1 : cv, pv);
+    sweep_small<BATCH, true, true>(P, r, colc, cv, pv, mask0, mask1, lose);
+    det_write(colc, coln, V, lose, cv, lose ? first_free_128(mask0, mask1) : cv, pv);
     return lose;
 }
 
@@ -623,11 +633,11 @@ __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *
 template <bool BATCH>
 __device__ __forceinline__ void ip_small_assign(const RoundParams &P, uint64_t *col, int32_t V) {
     const Row r = load_row<BATCH>(P, V);
-    uint64_t mask = 0;
+    uint64_t mask0 = 0, mask1 = 0;
     bool unused = false;
-    sweep_small<BATCH, true, false>(P, r, col, 0, 0, mask, unused);
+    sweep_small<BATCH, true, false>(P, r, col, 0, 0, mask0, mask1, unused);
     const uint32_t pv = prio_of(load_state(col + V));
-    col[V] = pack_state(__ffsll(static_cast<long long>(~mask)) - 1, pv, false);
+    col[V] = pack_state(first_free_128(mask0, mask1), pv, false);
 }
 
 // Phase 2 for a vertex of degree <= T1.
@@ -636,9 +646,9 @@ __device__ __forceinline__ bool ip_small_conflict(const RoundParams &P, const ui
     const Row r = load_row<BATCH>(P, V);
     deg = static_cast<int32_t>(r.e - r.b);
     const uint64_t self = load_state(col + V);
-    uint64_t mask = 0;
+    uint64_t mask0 = 0, mask1 = 0;
     bool lose = false;
-    sweep_small<BATCH, false, true>(P, r, col, color_of(self), prio_of(self), mask, lose);
+    sweep_small<BATCH, false, true>(P, r, col, color_of(self), prio_of(self), mask0, mask1, lose);
     return lose;
 }
 

@@ -28,7 +28,7 @@ namespace {
 
 constexpr int32_t kRoundsPerLaunch = 4;
 constexpr int32_t kT1 = 32;
-constexpr int32_t kCH = 128;
+constexpr int32_t kCH = 1024;
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();

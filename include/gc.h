@@ -242,7 +242,9 @@ typedef struct gc_server_stats {
 int gc_server_create(const gc_server_config *cfg, gc_server **out);
 
 /* Queues one graph (host or device CSR as in gc_color; copied before return).  Non-blocking.
- * GC_ERR_OOM if the graph can never fit the pool; GC_ERR_INVALID_GRAPH for a malformed rowptr. */
+ * GC_ERR_OOM if the graph can never fit the pool; GC_ERR_INVALID_GRAPH for malformed row offsets.
+ * Neighbour ids and self-loops are checked on the device when the request is admitted; a request
+ * that fails that check is dropped and its gc_server_poll returns GC_ERR_INVALID_GRAPH. */
 int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32_t *colidx,
                      uint64_t *req_id);
 

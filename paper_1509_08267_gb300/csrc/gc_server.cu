@@ -26,8 +26,9 @@
 namespace gc {
 namespace {
 
-constexpr int32_t kRoundsPerLaunch = 4;
-constexpr int32_t kT1 = 32;
+constexpr int32_t kRoundsWhileQueued = 4;   // rounds per launch while requests wait for admission
+constexpr int32_t kRoundsIdleQueue = 16;    // rounds per launch when nothing waits
+constexpr int32_t kT1 = 127;
 constexpr int32_t kCH = 1024;
 
 double now_s() {
@@ -131,7 +132,7 @@ struct gc_server {
     int64_t PV = 0, PE = 0, PI = 0, PC = 0;  // pool capacities: vertices, entries, large vertices, work items
     int32_t S = 0;                           // slots
     gc::DevBuf rowptr, colidx, col0, col1, outbuf, small0, small1, items, chunk0, chunk1, acc, vg, ctl, bitmap;
-    gc::DevBuf g_vbase, g_n, g_ebase, g_rbase, g_m, glast, gmax, gcount;
+    gc::DevBuf g_vbase, g_n, g_ebase, g_rbase, g_m, glast, gmax, gcount, verr;
     std::vector<int64_t> h_vbase, h_ebase, h_rbase, h_m;
     std::vector<int32_t> h_n, h_glast;
     gc::RangeAlloc va, ea, ra;
@@ -169,7 +170,7 @@ int srv_fail(gc_server *s, int code, const char *what, cudaError_t e) {
         if (e_ != cudaSuccess) return srv_fail(s, GC_ERR_CUDA, #call, e_); \
     } while (0)
 
-RoundParams params(gc_server *s) {
+RoundParams params(gc_server *s, int32_t rounds = kRoundsWhileQueued) {
     RoundParams P{};
     P.n = static_cast<int32_t>(s->PV);
     P.G = s->S;
@@ -200,7 +201,7 @@ RoundParams params(gc_server *s) {
     P.stats = nullptr;
     P.stats_cap = 0;
     P.pass_begin = s->next_pass;
-    P.pass_end = s->next_pass + kRoundsPerLaunch;
+    P.pass_end = s->next_pass + rounds;
     P.cap_is_error = 0;
     P.spin_ns = 1000000000LL;
     P.T1 = kT1;
@@ -245,10 +246,13 @@ void unreserve(gc_server *s, Request *r) {
     r->slot = -1;
 }
 
-// Copies admitted requests into the pool and appends them to the worklist of round next_pass.
-int admit(gc_server *s, const std::vector<Request *> &adm) {
+// Copies admitted requests into the pool, checks their graph format on the device (each request
+// has its own error slot, so a malformed request cannot disturb the batch) and appends the valid
+// ones to the worklist of round next_pass.  Malformed requests are returned in `bad`.
+int admit(gc_server *s, const std::vector<Request *> &adm, std::vector<Request *> &bad) {
     if (adm.empty()) return GC_OK;
     cudaStream_t st = s->stream;
+    int32_t *verr = s->verr.as<int32_t>();
     for (Request *r : adm) {
         const int g = r->slot;
         SRV_CUDA(cudaMemcpyAsync(s->rowptr.as<int32_t>() + r->rbase, r->rowptr.data(), 4 * (r->n + 1),
@@ -256,6 +260,26 @@ int admit(gc_server *s, const std::vector<Request *> &adm) {
         if (r->m)
             SRV_CUDA(cudaMemcpyAsync(s->colidx.as<int32_t>() + r->ebase, r->colidx.data(), 4 * r->m,
                                      cudaMemcpyHostToDevice, st));
+        SRV_CUDA(cudaMemsetAsync(verr + 4 * g, 0, 16, st));
+        SRV_CUDA(launch_validate(r->n, s->rowptr.as<int32_t>() + r->rbase,
+                                 r->m ? s->colidx.as<int32_t>() + r->ebase : s->rowptr.as<int32_t>() + r->rbase, 0,
+                                 verr + 4 * g, st));
+    }
+    std::vector<int32_t> herr(adm.size());
+    for (size_t i = 0; i < adm.size(); ++i)
+        SRV_CUDA(cudaMemcpyAsync(&herr[i], verr + 4 * adm[i]->slot, 4, cudaMemcpyDeviceToHost, st));
+    SRV_CUDA(cudaStreamSynchronize(st));
+    std::vector<Request *> ok;
+    for (size_t i = 0; i < adm.size(); ++i) {
+        Request *r = adm[i];
+        std::vector<int32_t>().swap(r->rowptr);  // the pool holds the graph now
+        std::vector<int32_t>().swap(r->colidx);
+        if (herr[i] != 0) {
+            bad.push_back(r);
+            continue;
+        }
+        ok.push_back(r);
+        const int g = r->slot;
         s->h_vbase[g] = r->vbase;
         s->h_n[g] = r->n;
         s->h_ebase[g] = r->ebase;
@@ -270,18 +294,13 @@ int admit(gc_server *s, const std::vector<Request *> &adm) {
         SRV_CUDA(cudaMemcpyAsync(s->glast.as<int32_t>() + g, &s->h_glast[g], 4, cudaMemcpyHostToDevice, st));
         r->join = s->next_pass;
     }
+    if (ok.empty()) return GC_OK;
     RoundParams P = params(s);
     SRV_CUDA(cudaMemsetAsync(P.tmp, 0, 2 * sizeof(unsigned), st));
-    for (Request *r : adm)
+    for (Request *r : ok)
         SRV_CUDA(launch_setup(P, s->cfg.mode, true, static_cast<int32_t>(r->vbase),
                               static_cast<int32_t>(r->vbase + r->n), r->slot, st));
     SRV_CUDA(launch_expand(P, true, false, -1, st));
-    // the pinned-free host copies of the CSR are no longer needed once the copies are done
-    SRV_CUDA(cudaStreamSynchronize(st));
-    for (Request *r : adm) {
-        std::vector<int32_t>().swap(r->rowptr);
-        std::vector<int32_t>().swap(r->colidx);
-    }
     return GC_OK;
 }
 
@@ -365,11 +384,26 @@ void worker_main(gc_server *s) {
             }
         }
         const double t0 = now_s();
-        if (admit(s, adm) != GC_OK) {
+        std::vector<Request *> bad;
+        if (admit(s, adm, bad) != GC_OK) {
             fail_all(s, s->fatal, s->fatal_msg);
             break;
         }
-        RoundParams P = params(s);
+        bool queued = false;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            for (Request *r : bad) {
+                s->resident.erase(std::find(s->resident.begin(), s->resident.end(), r));
+                unreserve(s, r);
+                r->status = GC_ERR_INVALID_GRAPH;
+                r->state = kDone;
+                s->rejected += 1;
+            }
+            if (!bad.empty()) s->cv_done.notify_all();
+            queued = !s->queue.empty();
+            if (s->resident.empty()) continue;
+        }
+        RoundParams P = params(s, queued ? kRoundsWhileQueued : kRoundsIdleQueue);
         cudaError_t e = launch_rounds(P, s->cfg.mode, true, false, s->grid, 256, s->stream);
         Ctl h{};
         if (e == cudaSuccess) e = cudaMemcpyAsync(&h, s->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream);
@@ -449,6 +483,7 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
         {&s->acc, 4 * gc::kAccStride * static_cast<size_t>(s->PI)}, {&s->ctl, sizeof(gc::Ctl)},
         {&s->bitmap, 4 * (V / 32 + 4)}, {&s->g_vbase, 8 * Sz}, {&s->g_n, 4 * Sz}, {&s->g_ebase, 8 * Sz},
         {&s->g_rbase, 8 * Sz}, {&s->g_m, 8 * Sz}, {&s->glast, 4 * Sz}, {&s->gmax, 4 * Sz}, {&s->gcount, 4 * Sz},
+        {&s->verr, 16 * Sz},
     };
     for (auto &a : plan) {
         if (e != cudaSuccess) break;
@@ -518,7 +553,8 @@ int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32
             std::memcpy(r->colidx.data(), colidx, 4 * static_cast<size_t>(m));
         }
     }
-    // graph format (Section 2.1): checked here so one bad request cannot stop the shared batch
+    // row offsets are checked here (they size the request's footprint); neighbour ids and self-loops
+    // are checked on the device when the request is admitted
     for (int32_t v = 0; v < n; ++v) {
         const int64_t b = r->rowptr[v], e = r->rowptr[v + 1];
         if (e < b || e > m) return set_last_error(GC_ERR_INVALID_GRAPH, "rowptr not monotone at vertex %d", v);
@@ -526,12 +562,6 @@ int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32
         if (d > gc::kT1) {
             r->n_large += 1;
             r->n_chunks += (d + gc::kCH - 1) / gc::kCH;
-        }
-        for (int64_t j = b; j < e; ++j) {
-            const int32_t u = r->colidx[j];
-            if (u < 0 || u >= n || u == v)
-                return set_last_error(GC_ERR_INVALID_GRAPH, "bad neighbour %d of vertex %d (entry %lld)", u, v,
-                                      static_cast<long long>(j));
         }
     }
     std::lock_guard<std::mutex> lk(s->mu);
@@ -572,6 +602,9 @@ int gc_server_poll(gc_server *s, uint64_t req_id, int32_t timeout_ms, int32_t *c
     std::unique_ptr<gc::Request> keep = std::move(it->second);
     s->reqs.erase(it);
     lk.unlock();
+    if (status == GC_ERR_INVALID_GRAPH)
+        return set_last_error(status, "request %llu: invalid graph (neighbour id out of range or self-loop)",
+                              static_cast<unsigned long long>(req_id));
     if (status != GC_OK) return set_last_error(status, "request failed: %s", s->fatal_msg.c_str());
     if (colors_out && keep->n) {
         cudaPointerAttributes a{};

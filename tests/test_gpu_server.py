@@ -68,14 +68,20 @@ def test_server_rejects(gclib):
             srv.submit(big.rowptr, big.colidx)
         assert ei.value.status == gclib.GC_ERR_OOM
         g = gg.cycle(6)
-        bad = g.colidx.copy()
-        bad[0] = 0
+        rp = g.rowptr.copy()
+        rp[3] = rp[4] + 1  # row offsets not monotone: refused at submit
         with pytest.raises(gclib.GCError) as ei:
-            srv.submit(g.rowptr, bad)
+            srv.submit(rp, g.colidx)
         assert ei.value.status == gclib.GC_ERR_INVALID_GRAPH
+        bad = g.colidx.copy()
+        bad[0] = 0  # self-loop: found on the device at admission, reported by poll
+        rid_bad = srv.submit(g.rowptr, bad)
         rid = srv.submit(g.rowptr, g.colidx)
+        with pytest.raises(gclib.GCError) as ei:
+            srv.poll(rid_bad)
+        assert ei.value.status == gclib.GC_ERR_INVALID_GRAPH
         colors, nc, rounds = srv.poll(rid)
-        assert nc == 2 and srv.stats()["rejected"] == 1
+        assert nc == 2 and srv.stats()["rejected"] == 2
 
 
 def test_server_device_inputs(gclib):

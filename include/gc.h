@@ -73,8 +73,8 @@ enum { GC_MODE_DETERMINISTIC = 0, GC_MODE_INPLACE = 1 };
 #define GC_FLAG_STATS 1u     /* fill gc_stats' per-round worklist sizes and scanned entries */
 #define GC_FLAG_TIMING 2u    /* record CUDA events around the round kernel (gc_stats.kernel_ms) */
 #define GC_FLAG_VALIDATE 4u  /* run gc_validate_graph(GC_VALIDATE_ALL) before coloring */
-#define GC_FLAG_COMPACT 8u  /* deterministic mode: skip adjacency entries whose neighbour is already final
-                               (same results; reads fewer entries but adds per-work-item bookkeeping) */
+#define GC_FLAG_FULL_SWEEP 8u  /* deterministic mode: re-read every adjacency entry of a vertex each round
+                                  instead of only the neighbours that can still change (same results) */
 
 /* Flags for gc_validate_graph */
 #define GC_VALIDATE_SORTED 1     /* rows strictly increasing (implies no duplicate entries) */
@@ -86,7 +86,8 @@ typedef struct gc_options {
     void *stream;              /* cudaStream_t to run on; NULL = the context's own stream */
     int32_t max_rounds;        /* round cap; 0 = n + 1 (a worklist shrinks every round) */
     int32_t small_max_degree;  /* vertices up to this degree get one thread each (1..127); default 127 */
-    int32_t chunk;             /* adjacency entries per warp work item for larger vertices (32..1024, multiple of 32); default 1024 */
+    int32_t chunk;             /* adjacency entries per warp work item for larger vertices (32..1024, multiple of 32);
+                                  default 512 (deterministic), 1024 (in-place) */
     int32_t block_size;        /* threads per block of the round kernel (128, 256 or 512); default 256 */
     int32_t blocks_per_sm;     /* resident blocks per SM for the round kernel; 0 = occupancy maximum */
     int64_t spin_limit_ns;     /* grid-barrier wait limit in ns; 0 = 1e9.  A wait that runs out makes

@@ -40,7 +40,7 @@ MODE_INPLACE = 1
 FLAG_STATS = 1
 FLAG_TIMING = 2
 FLAG_VALIDATE = 4
-FLAG_COMPACT = 8
+FLAG_FULL_SWEEP = 8
 VALIDATE_SORTED = 1
 VALIDATE_SYMMETRIC = 2
 VALIDATE_ALL = 3

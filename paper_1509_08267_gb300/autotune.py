@@ -21,7 +21,7 @@ import statistics
 
 import numpy as np
 
-from . import FLAG_COMPACT, FLAG_TIMING, Options, color, color_batch
+from . import FLAG_FULL_SWEEP, FLAG_TIMING, Options, color, color_batch
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
 
@@ -42,7 +42,7 @@ def graph_class(n: int, degrees: np.ndarray) -> str:
 
 
 def _options(cfg: dict, timing: bool = True) -> Options:
-    flags = (FLAG_TIMING if timing else 0) | (FLAG_COMPACT if cfg["compact"] else 0)
+    flags = (FLAG_TIMING if timing else 0) | (0 if cfg["compact"] else FLAG_FULL_SWEEP)
     return Options(small_max_degree=cfg["small_max_degree"], chunk=cfg["chunk"],
                    blocks_per_sm=cfg["blocks_per_sm"], flags=flags)
 

@@ -77,8 +77,9 @@ struct Ctl {
     int32_t pad0[2];
     unsigned cnt[3 * kCnt];
     unsigned tmp[2];
+    unsigned long long list_total, list_alloc;
     int32_t gmax1, gcount1, glast1, pad1;
-    int32_t pad2[6];
+    int32_t pad2[2];
     GridBar bar;
 };
 static_assert(offsetof(Ctl, bar) % 128 == 0, "barrier alignment");
@@ -89,12 +90,12 @@ struct Context {
     cudaStream_t stream = nullptr;
     int sms = 0;
     int occ[2][2][2] = {};  // [mode][batch][compact] blocks per SM of the round kernel
-    Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, active, alive, ctl, stats, bitmap, vg;
+    Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, lists, ctl, stats, bitmap, vg;
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
     Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     void release_all() {
-        Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &active, &alive, &ctl, &stats, &bitmap,
+        Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &lists, &ctl, &stats, &bitmap,
                       &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors};
         for (Buf *b : all) b->release();
     }
@@ -223,7 +224,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C.stream;
     const uint32_t flags = opt ? opt->flags : 0u;
     const int32_t T1 = (opt && opt->small_max_degree) ? opt->small_max_degree : 127;
-    const int32_t CH = (opt && opt->chunk) ? opt->chunk : 1024;
+    const int32_t CH = (opt && opt->chunk) ? opt->chunk : (mode == GC_MODE_DETERMINISTIC ? 512 : 1024);
     const int32_t block = (opt && opt->block_size) ? opt->block_size : 256;
     if (T1 < 1 || T1 > 127) return set_last_error(GC_ERR_INVALID_ARG, "small_max_degree %d outside 1..127", T1);
     if (CH < 32 || CH > 1024 || CH % 32) return set_last_error(GC_ERR_INVALID_ARG, "chunk %d invalid", CH);
@@ -245,9 +246,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     GC_TRY(ensure(C.ctl, sizeof(Ctl), "control"));
     GC_TRY(ensure(C.bitmap, 4 * (n / 32 + 2), "color bitmap"));
     if (stats_cap) GC_TRY(ensure(C.stats, 8 * (4 * static_cast<size_t>(stats_cap) + 1), "statistics"));
-    const bool compact = mode == GC_MODE_DETERMINISTIC && (flags & GC_FLAG_COMPACT);
-    const size_t active_words = static_cast<size_t>(pb.nnz / 32 + 2);
-    if (compact) GC_TRY(ensure(C.active, 4 * active_words, "active-entry bits"));
+    const bool compact = mode == GC_MODE_DETERMINISTIC && !(flags & GC_FLAG_FULL_SWEEP);
     if (pb.batch) {
         GC_TRY(ensure(C.vg, 4 * n, "graph ids"));
         GC_TRY(ensure(C.gmax, 4 * gz, "per-graph max"));
@@ -264,7 +263,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     GC_CUDA(cudaMemsetAsync(&ctl->gmax1, 0xff, sizeof(int32_t), s));
     GC_CUDA(cudaMemsetAsync(C.bitmap.p, 0, 4 * (n / 32 + 2), s));
     if (stats_cap) GC_CUDA(cudaMemsetAsync(C.stats.p, 0, 8 * (4 * static_cast<size_t>(stats_cap) + 1), s));
-    if (compact) GC_CUDA(cudaMemsetAsync(C.active.p, 0xff, 4 * active_words, s));
+
     if (pb.batch) GC_CUDA(cudaMemsetAsync(C.gmax.p, 0xff, 4 * gz, s));
 
     RoundParams P{};
@@ -288,6 +287,8 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     P.small1 = C.small1.as<int32_t>();
     P.items = C.items.as<int32_t>();
     P.tmp = ctl->tmp;
+    P.list_total = compact ? &ctl->list_total : nullptr;
+    P.list_alloc = compact ? &ctl->list_alloc : nullptr;
     P.cnt = ctl->cnt;
     P.bar = &ctl->bar;
     P.err = ctl->err;
@@ -321,12 +322,11 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     GC_TRY(ensure(C.chunk0, 16 * static_cast<size_t>(n_chunks), "work items"));
     GC_TRY(ensure(C.chunk1, 16 * static_cast<size_t>(n_chunks), "work items"));
     GC_TRY(ensure(C.acc, 4 * kAccStride * static_cast<size_t>(n_items), "accumulators"));
-    if (compact) GC_TRY(ensure(C.alive, 4 * static_cast<size_t>(n_chunks), "work-item survivors"));
+    if (compact) GC_TRY(ensure(C.lists, 4 * static_cast<size_t>(h.list_total), "neighbour lists"));
     P.chunk0 = C.chunk0.as<int4>();
     P.chunk1 = C.chunk1.as<int4>();
     P.acc = C.acc.as<unsigned>();
-    P.active = compact ? C.active.as<unsigned>() : nullptr;
-    P.alive = compact ? C.alive.as<int32_t>() : nullptr;
+    P.lists = compact ? C.lists.as<int32_t>() : nullptr;
     GC_CUDA(launch_expand(P, pb.batch, compact, static_cast<int32_t>(n_items), s));
     if (timing) GC_CUDA(cudaEventRecord(C.ev[1], s));
 

@@ -16,18 +16,30 @@ namespace gc {
 constexpr int kStep = GC_STEP;
 
 // Accumulator slot of a vertex of degree > T1 (its row is split into warp work items):
-//   [0, kAccWords)              round window: colors 0..511 of the neighbours read this round
-//   kAccFlag                    conflict flag of this round
-//   kAccDone                    work items of this round finished
-//   [kAccFin, kAccFin+kAccWords) colors 0..511 of neighbours found final (persistent, compact mode)
-//   kAccBase                    id of the vertex's first work item in the survivor array (compact mode)
-// In compact mode the slot belongs to the vertex for the whole run; otherwise slots are numbered
-// afresh every round.
+//   [0, kAccWords)  round window: colors 0..511 of the neighbours read this round
+//   kAccFlag        conflict flag of this round
+//   kAccDone        work items of this round finished
+//   kAccSurv        compact mode: list entries whose neighbour was not final when read this round
+//   kAccNewLen      compact mode: entries written to the other list region this round
+// Compact mode only, kept for the whole run (the slot belongs to the vertex):
+//   [kAccFin, kAccFin+kAccWords)  colors 0..511 of neighbours found final
+//   kAccSrc         where the vertex's list of possibly-changing neighbours is: 0 its CSR row,
+//                   1 region A, 2 region B of its space in the list pool
+//   kAccLen         entries in that list
+//   kAccRewrite     1: this round's items copy the entries still active into the other region
+//   kAccOffLo/Hi    offset of region A in the list pool (region B follows it, each deg entries)
+// Words [0, 32) are cleared by the warp that finishes the vertex's round.
 constexpr int kAccWords = 16;
 constexpr int kAccFlag = 16;
 constexpr int kAccDone = 17;
+constexpr int kAccSurv = 18;
+constexpr int kAccNewLen = 19;
 constexpr int kAccFin = 32;
-constexpr int kAccBase = 48;
+constexpr int kAccSrc = 48;
+constexpr int kAccLen = 49;
+constexpr int kAccRewrite = 50;
+constexpr int kAccOffLo = 51;
+constexpr int kAccOffHi = 52;
 constexpr int kAccStride = 64;  // 256 B per slot
 
 // Worklist counters: three sets used round-robin (read / append / clear), kCnt words each.
@@ -68,8 +80,9 @@ struct RoundParams {
     unsigned *tmp;             // [2] setup scratch counters: larger vertices, their work items
     unsigned *cnt;             // [3][kCnt] worklist counters
     unsigned *acc;             // [slots][kAccStride]
-    unsigned *active;          // compact mode: bit j = adjacency entry j may still change (neighbour not final)
-    int32_t *alive;            // compact mode: entries left active in each work item after its last sweep
+    int32_t *lists;                   // compact mode: list pool (two regions of deg entries per larger vertex)
+    unsigned long long *list_total;   // compact mode: setup adds 2 * deg of every larger vertex
+    unsigned long long *list_alloc;   // compact mode: expand's allocation counter in the list pool
     GridBar *bar;
     int32_t *err;              // [4] status, vertex, entry, extra
     int32_t *passes;           // [2] first round not executed by the last launch, last round executed
@@ -97,9 +110,10 @@ cudaError_t launch_setup(const RoundParams &P, int mode, bool batch, int32_t v_b
                          int32_t g_fixed, cudaStream_t s);
 // Turns the n_items larger vertices found by setup into work items of round P.pass_begin
 // (n_items < 0: the count setup left in P.tmp[0] on the device).
-// compact: work items get persistent accumulator slots and survivor counters (deterministic mode).
+// compact: every larger vertex gets a persistent slot and list-pool space (deterministic mode).
 cudaError_t launch_expand(const RoundParams &P, bool batch, bool compact, int32_t n_items, cudaStream_t s);
-// compact (deterministic mode only): skip adjacency entries whose neighbour is final.
+// compact (deterministic mode only): larger vertices sweep packed lists of the neighbours that can
+// still change instead of their whole rows.
 cudaError_t launch_rounds(const RoundParams &P, int mode, bool batch, bool compact, int grid, int block,
                           cudaStream_t s);
 cudaError_t round_kernel_occupancy(int mode, bool batch, bool compact, int block, int *blocks_per_sm);

@@ -384,10 +384,11 @@ __device__ __forceinline__ int32_t first_free_128(uint64_t mask0, uint64_t mask1
 
 // Merges a work item's window and flag into the vertex's accumulator slot.  Returns true in the
 // warp that completed the vertex's last work item; that warp then holds the merged window in
-// lo0/lo1/win and the merged flag in `lose`, and the slot is cleared for reuse.
+// lo0/lo1/win, the merged flag in `lose` and the slot's survivor and new-length counters in
+// surv/newlen, and the round part of the slot is cleared for the next round.
 template <bool WINDOW>
 __device__ __forceinline__ bool merge_item(unsigned *a, int nch, int lane, unsigned &lo0, unsigned &lo1, unsigned *win,
-                                           bool &lose) {
+                                           bool &lose, unsigned *surv = nullptr, unsigned *newlen = nullptr) {
     if constexpr (WINDOW) {
         const unsigned w = lane == 0 ? lo0 : lane == 1 ? lo1 : (lane < kAccWords ? win[lane] : 0u);
         if (lane < kAccWords && (w & ~__ldcg(a + lane))) atomicOr(a + lane, w);
@@ -398,14 +399,16 @@ __device__ __forceinline__ bool merge_item(unsigned *a, int nch, int lane, unsig
     if (lane == 0) done = atom_add_acq_rel(a + kAccDone, 1u);
     done = __shfl_sync(kFull, done, 0);
     if (done != static_cast<unsigned>(nch - 1)) return false;
-    const unsigned x = lane < kAccWords ? __ldcg(a + lane) : 0u;
-    const unsigned f = __ldcg(a + kAccFlag);
+    const unsigned x = __ldcg(a + lane);  // the round part of the slot, one word per lane
     if constexpr (WINDOW) {
         lo0 = __shfl_sync(kFull, x, 0);
         lo1 = __shfl_sync(kFull, x, 1);
         if (lane >= 2 && lane < kAccWords) win[lane] = x;
     }
-    lose = f != 0u;
+    lose = __shfl_sync(kFull, x, kAccFlag) != 0u;
+    const unsigned sv = __shfl_sync(kFull, x, kAccSurv), nl = __shfl_sync(kFull, x, kAccNewLen);
+    if (surv) *surv = sv;
+    if (newlen) *newlen = nl;
     __syncwarp();
     a[lane] = 0u;  // the round part of the slot (words 0..31); the persistent part stays
     return true;
@@ -444,116 +447,77 @@ __device__ __forceinline__ bool det_small(const RoundParams &P, const uint64_t *
     return lose;
 }
 
-// Compact sweep of entries [jb, je) of a row: only entries whose bit in P.active is still set are
-// read.  Entries are grouped 32 to a bit word (groups aligned to the global entry index); the warp
-// loads the bit words of up to 32 groups at once, one per lane, and then visits only the groups
-// with active entries, kPer groups per step.  A neighbour found final is dropped: its bit is cleared
-// and its color is added, besides the round window (lo / win), to the window of final neighbours
-// (flo / wfin) that the vertex keeps for later rounds.  Lane 0 returns the entries still active and
-// the entries read.
-__device__ __forceinline__ void sweep_compact(const RoundParams &P, const Row &r, const uint64_t *colc, int64_t jb,
-                                              int64_t je, int lane, int32_t cv, uint32_t pv, uint64_t &lo,
-                                              unsigned *win, uint64_t &flo, unsigned *wfin, bool &lose,
-                                              unsigned &survivors, unsigned &reads) {
-    const int64_t gb = jb >> 5, ge = (je + 31) >> 5;
-    for (int64_t gw0 = gb; gw0 < ge; gw0 += 32) {
-        // this lane's group: its active bits restricted to [jb, je)
-        const int64_t mg = gw0 + lane;
-        unsigned bits = 0;
-        if (mg < ge) {
-            bits = __ldcg(P.active + mg);
-            const int64_t lo_j = 32 * mg, hi_j = lo_j + 32;
-            if (lo_j < jb) bits &= ~0u << (jb - lo_j);
-            if (hi_j > je) bits &= (je - lo_j >= 32) ? ~0u : ((1u << (je - lo_j)) - 1u);
-        }
-        unsigned todo = __ballot_sync(kFull, bits != 0u);  // groups with active entries
-        while (todo) {
-            int src[kPer];
-            unsigned gbits[kPer];
+// Compact sweep of entries [lb, le) of a vertex's list of neighbours that may still change (local
+// ids; the list is its CSR row until the first rewrite).  A neighbour found final is dropped: its
+// color goes, besides the round window (lo / win), to the window of final neighbours (flo / wfin)
+// that the vertex keeps.  When `dst` is set, the entries still active are appended there (the
+// vertex's other list region) at positions reserved in the slot's new-length counter.  Lane 0
+// returns the entries still active.
+__device__ __forceinline__ void sweep_list(const RoundParams &P, const Row &r, const uint64_t *colc,
+                                           const int32_t *list, int64_t lb, int64_t le, int32_t *dst,
+                                           unsigned *newlen, int lane, int32_t cv, uint32_t pv, uint64_t &lo,
+                                           unsigned *win, uint64_t &flo, unsigned *wfin, bool &lose,
+                                           unsigned &survivors) {
+    int32_t ul[kPer], un[kPer];
+    uint64_t w[kPer];
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                src[q] = todo ? __ffs(todo) - 1 : -1;
-                if (todo) todo &= todo - 1;
-            }
-            int32_t ul[kPer];
-            uint64_t w[kPer];
-            unsigned act = 0;
+    for (int q = 0; q < kPer; ++q) {
+        const int64_t j = lb + lane + 32 * q;
+        ul[q] = j < le ? load_entry(list + j) : 0;
+    }
+    for (int64_t j0 = lb; j0 < le; j0 += kStep) {
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                gbits[q] = __shfl_sync(kFull, bits, src[q] < 0 ? 0 : src[q]);
-                const bool a = src[q] >= 0 && ((gbits[q] >> lane) & 1u);
-                act |= static_cast<unsigned>(a) << q;
-                ul[q] = a ? load_entry(P.colidx + 32 * (gw0 + src[q]) + lane) : 0;
-            }
-#pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                w[q] = kNoNeighbour;
-                if ((act >> q) & 1u) {
-                    const int32_t U = neighbour(P, r, ul[q], 32 * (gw0 + src[q]) + lane);
-                    if (U >= 0) w[q] = load_state(colc + U);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                const int32_t c = color_of(w[q]);
-                const bool a = (act >> q) & 1u;
-                const bool fin = a && final_of(w[q]);
-                if (static_cast<unsigned>(c) < 64u) {
-                    lo |= 1ull << c;
-                    if (fin) flo |= 1ull << c;
-                } else if (static_cast<unsigned>(c) < 32u * kAccWords) {
-                    atomicOr(&win[c >> 5], 1u << (c & 31));
-                    if (fin) atomicOr(&wfin[c >> 5], 1u << (c & 31));
-                }
-                if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
-                                                      static_cast<uint32_t>(r.lv), P.seed);
-                const unsigned drop = __ballot_sync(kFull, fin);
-                if (lane == 0 && src[q] >= 0) {
-                    if (drop) atomicAnd(P.active + gw0 + src[q], ~drop);
-                    survivors += __popc(gbits[q] & ~drop);
-                    reads += __popc(gbits[q]);
-                }
+        for (int q = 0; q < kPer; ++q) {
+            const int64_t j = j0 + lane + 32 * q;
+            w[q] = kNoNeighbour;
+            if (j < le) {
+                const int32_t U = neighbour(P, r, ul[q], r.b + j);
+                if (U >= 0) w[q] = load_state(colc + U);
             }
         }
-    }
-}
-
-// Appends a losing larger vertex with the work items that still have active entries (compact mode).
-template <bool BATCH>
-__device__ void append_alive(const RoundParams &P, int32_t V, const Row &r, int32_t lid, int32_t base,
-                             int4 *chunk_next, unsigned *cnt_next, int next_round, int lane) {
-    const int32_t deg = static_cast<int32_t>(r.e - r.b);
-    const int32_t nch = (deg + P.CH - 1) / P.CH;
-    int32_t count = 0;
-    for (int32_t k0 = 0; k0 < nch; k0 += 32) {
-        const int32_t k = k0 + lane;
-        count += __popc(__ballot_sync(kFull, k < nch && __ldcg(P.alive + base + k) > 0));
-    }
-    const bool none = count == 0;  // every neighbour final: one item still computes the color
-    const int32_t items = none ? 1 : count;
-    unsigned cb = 0;
-    if (lane == 0) {
-        atomicAdd(cnt_next + kCntItems, 1u);
-        cb = atomicAdd(cnt_next + kCntChunks, static_cast<unsigned>(items));
-        if constexpr (BATCH) note_graph_round(P, r.g, next_round);
-    }
-    cb = __shfl_sync(kFull, cb, 0);
-    if (none) {
-        if (lane == 0) chunk_next[cb] = make_int4(V, 0, lid, 1);
-        return;
-    }
-    int32_t at = 0;
-    for (int32_t k0 = 0; k0 < nch; k0 += 32) {
-        const int32_t k = k0 + lane;
-        const bool live = k < nch && __ldcg(P.alive + base + k) > 0;
-        const unsigned m = __ballot_sync(kFull, live);
-        if (live) chunk_next[cb + at + __popc(m & lanemask_lt())] = make_int4(V, k, lid, items);
-        at += __popc(m);
+        const bool more = j0 + kStep < le;
+        if (more) {
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int64_t j = j0 + kStep + lane + 32 * q;
+                un[q] = j < le ? load_entry(list + j) : 0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int64_t j = j0 + lane + 32 * q;
+            const int32_t c = color_of(w[q]);
+            const bool valid = j < le;
+            const bool fin = valid && final_of(w[q]);
+            if (static_cast<unsigned>(c) < 64u) {
+                lo |= 1ull << c;
+                if (fin) flo |= 1ull << c;
+            } else if (static_cast<unsigned>(c) < 32u * kAccWords) {
+                atomicOr(&win[c >> 5], 1u << (c & 31));
+                if (fin) atomicOr(&wfin[c >> 5], 1u << (c & 31));
+            }
+            if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
+                                                  static_cast<uint32_t>(r.lv), P.seed);
+            const bool keep = valid && !fin;
+            const unsigned km = __ballot_sync(kFull, keep);
+            if (lane == 0) survivors += __popc(km);
+            if (dst && km) {
+                unsigned pos = 0;
+                if (lane == 0) pos = atomicAdd(newlen, static_cast<unsigned>(__popc(km)));
+                pos = __shfl_sync(kFull, pos, 0);
+                if (keep) dst[pos + __popc(km & lanemask_lt())] = ul[q];
+            }
+        }
+        if (more) {
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) ul[q] = un[q];
+        }
     }
 }
 
 // One CH-entry work item of a larger vertex (one warp).  COMPACT: the slot (it.z) is the vertex's own
-// for the whole run and only active entries are read; otherwise slots are per round.
+// for the whole run and the item covers entries [k*CH, (k+1)*CH) of its list of neighbours that may
+// still change; otherwise the slot is per round and the item covers the same range of its row.
 template <bool BATCH, bool COMPACT>
 __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *coln, int4 it, unsigned *win,
                           unsigned *wfin, int4 *chunk_next, unsigned *cnt_next, int pass, int lane,
@@ -563,8 +527,6 @@ __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *
     const uint64_t self = load_state(colc + V);
     const int32_t cv = color_of(self);
     const uint32_t pv = prio_of(self);
-    const int64_t jb = r.b + static_cast<int64_t>(k) * P.CH;
-    const int64_t je = min(r.e, jb + P.CH);
     unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
     if (lane < kAccWords) {
         win[lane] = 0;
@@ -573,23 +535,34 @@ __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *
     __syncwarp();
     uint64_t lo = 0;
     bool lose = false;
-    int32_t base = 0;
+    unsigned src = 0, len = 0, rewrite = 0;
+    int64_t off = 0;
+    const int64_t deg = r.e - r.b;
     if constexpr (COMPACT) {
+        src = __ldcg(a + kAccSrc);
+        len = __ldcg(a + kAccLen);
+        rewrite = __ldcg(a + kAccRewrite);
+        off = static_cast<int64_t>(__ldcg(a + kAccOffLo)) | (static_cast<int64_t>(__ldcg(a + kAccOffHi)) << 32);
+        const int32_t *list = src == 0 ? P.colidx + r.b : P.lists + off + (src == 2 ? deg : 0);
+        int32_t *dst = rewrite ? P.lists + off + (src == 1 ? deg : 0) : nullptr;
+        const int64_t lb = static_cast<int64_t>(k) * P.CH;
+        const int64_t le = min(static_cast<int64_t>(len), lb + P.CH);
         uint64_t flo = 0;
-        unsigned survivors = 0, reads = 0;
-        sweep_compact(P, r, colc, jb, je, lane, cv, pv, lo, win, flo, wfin, lose, survivors, reads);
+        unsigned survivors = 0;
+        sweep_list(P, r, colc, list, lb, le, dst, a + kAccNewLen, lane, cv, pv, lo, win, flo, wfin, lose, survivors);
         const unsigned f0 = __reduce_or_sync(kFull, static_cast<unsigned>(flo));
         const unsigned f1 = __reduce_or_sync(kFull, static_cast<unsigned>(flo >> 32));
         __syncwarp();
         // neighbours found final: into the vertex's persistent window, before this item is counted
         const unsigned fw = lane == 0 ? f0 : lane == 1 ? f1 : (lane < kAccWords ? wfin[lane] : 0u);
         if (lane < kAccWords && (fw & ~__ldcg(a + kAccFin + lane))) atomicOr(a + kAccFin + lane, fw);
-        base = static_cast<int32_t>(__ldcg(a + kAccBase));
         if (lane == 0) {
-            P.alive[base + k] = static_cast<int32_t>(survivors);
-            st_read += reads;
+            if (survivors) atomicAdd(a + kAccSurv, survivors);
+            st_read += static_cast<unsigned long long>(le > lb ? le - lb : 0);
         }
     } else {
+        const int64_t jb = r.b + static_cast<int64_t>(k) * P.CH;
+        const int64_t je = min(r.e, jb + P.CH);
         sweep<true, true>(P, r, colc, jb, je, lane, cv, pv, lo, win, lose);
         if (lane == 0) st_read += static_cast<unsigned long long>(je - jb);
     }
@@ -597,12 +570,13 @@ __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *
     unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
     unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
     __syncwarp();
+    unsigned surv = 0, newlen = 0;
     if (nitems > 1 || COMPACT) {
-        if (!merge_item<true>(a, nitems, lane, lo0, lo1, win, lose)) return;
+        if (!merge_item<true>(a, nitems, lane, lo0, lo1, win, lose, &surv, &newlen)) return;
     }
     // the warp that finishes a vertex accounts for it in the round statistics
     if (lane == 0) {
-        st_deg += static_cast<unsigned long long>(r.e - r.b);
+        st_deg += static_cast<unsigned long long>(deg);
         st_cnt += 1;
     }
     if constexpr (COMPACT) {
@@ -620,10 +594,27 @@ __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *
     }
     if (lane == 0) det_write(colc, coln, V, lose, cv, nc, pv);
     if (!lose) return;
-    if constexpr (COMPACT)
-        append_alive<BATCH>(P, V, r, slot, base, chunk_next, cnt_next, pass + 1, lane);
-    else
+    if constexpr (COMPACT) {
+        // the list the next round sweeps: the fresh copy if this round wrote one, else the same list,
+        // and a rewrite next round once a quarter of the list has become final
+        const unsigned nsrc = rewrite ? (src == 1 ? 2u : 1u) : src;
+        const unsigned nlen = rewrite ? newlen : len;
+        const unsigned nrw = 4ull * surv < 3ull * nlen ? 1u : 0u;
+        const int32_t items = nlen > 0 ? static_cast<int32_t>((nlen + P.CH - 1) / P.CH) : 1;
+        unsigned cb = 0;
+        if (lane == 0) {
+            a[kAccSrc] = nsrc;
+            a[kAccLen] = nlen;
+            a[kAccRewrite] = nrw;
+            atomicAdd(cnt_next + kCntItems, 1u);
+            cb = atomicAdd(cnt_next + kCntChunks, static_cast<unsigned>(items));
+            if constexpr (BATCH) note_graph_round(P, r.g, pass + 1);
+        }
+        cb = __shfl_sync(kFull, cb, 0);
+        for (int32_t q = lane; q < items; q += 32) chunk_next[cb + q] = make_int4(V, q, slot, items);
+    } else {
         append_large<BATCH>(P, V, r, chunk_next, cnt_next, pass + 1, lane);
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -884,6 +875,7 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
         const bool in = base + lane < count;
         int kind = 0;  // 1 = one thread, 2 = work items
         int32_t nch = 0;
+        int64_t deg_big = 0;
         if (in) {
             int64_t b, e, lim;
             int32_t lv, ng;
@@ -921,6 +913,7 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
             if (d > 0) {
                 kind = d <= P.T1 ? 1 : 2;
                 nch = static_cast<int32_t>((d + P.CH - 1) / P.CH);
+                deg_big = d;
             }
         }
         if constexpr (BATCH) {
@@ -938,6 +931,13 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
             }
             ib = __shfl_sync(kFull, ib, leader);
             if (kind == 2) P.items[ib + __popc(m & lanemask_lt())] = V;
+            if (P.list_total) {
+                // compact mode: two list regions of deg entries per larger vertex
+                unsigned long long need = kind == 2 ? 2ull * static_cast<unsigned long long>(deg_big) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) need += __shfl_xor_sync(kFull, need, o);
+                if (lane == leader) atomicAdd(P.list_total, need);
+            }
         }
     }
 }
@@ -968,7 +968,17 @@ __global__ void expand_kernel(RoundParams P, int32_t n_items) {
         cb = __shfl_sync(kFull, cb, 0);
         unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
         a[lane] = 0u;
-        a[32 + lane] = (COMPACT && lane == kAccBase - 32) ? cb : 0u;
+        unsigned hi = 0u;
+        if (COMPACT) {
+            // the list starts as the CSR row; reserve the two list regions in the pool
+            unsigned long long off = 0;
+            if (lane == 0) off = atomicAdd(P.list_alloc, 2ull * static_cast<unsigned long long>(deg));
+            off = __shfl_sync(kFull, off, 0);
+            if (lane == kAccLen - 32) hi = static_cast<unsigned>(deg);
+            if (lane == kAccOffLo - 32) hi = static_cast<unsigned>(off);
+            if (lane == kAccOffHi - 32) hi = static_cast<unsigned>(off >> 32);
+        }
+        a[32 + lane] = hi;
         for (int32_t q = lane; q < nch; q += 32) chunk_cur[cb + q] = make_int4(V, q, static_cast<int32_t>(slot), nch);
     }
 }

@@ -97,6 +97,7 @@ struct Request {
     double t_submit = 0, t_done = 0;
     int32_t slot = -1, join = 0;
     int64_t vbase = 0, ebase = 0, rbase = 0;
+    bool staged = false;  // its CSR was copied into the pool at submit
 };
 
 struct DevBuf {
@@ -140,6 +141,9 @@ struct gc_server {
     std::vector<int32_t> free_slots;
     std::vector<gc::Request *> resident;
     std::deque<gc::Request *> queue;
+    std::vector<gc::Request *> staged;  // pool space reserved and CSR copied at submit
+    std::mutex copy_mu;
+    cudaStream_t copy_stream = nullptr;
     std::unordered_map<uint64_t, std::unique_ptr<gc::Request>> reqs;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -255,11 +259,13 @@ int admit(gc_server *s, const std::vector<Request *> &adm, std::vector<Request *
     int32_t *verr = s->verr.as<int32_t>();
     for (Request *r : adm) {
         const int g = r->slot;
-        SRV_CUDA(cudaMemcpyAsync(s->rowptr.as<int32_t>() + r->rbase, r->rowptr.data(), 4 * (r->n + 1),
-                                 cudaMemcpyHostToDevice, st));
-        if (r->m)
-            SRV_CUDA(cudaMemcpyAsync(s->colidx.as<int32_t>() + r->ebase, r->colidx.data(), 4 * r->m,
+        if (!r->staged) {
+            SRV_CUDA(cudaMemcpyAsync(s->rowptr.as<int32_t>() + r->rbase, r->rowptr.data(), 4 * (r->n + 1),
                                      cudaMemcpyHostToDevice, st));
+            if (r->m)
+                SRV_CUDA(cudaMemcpyAsync(s->colidx.as<int32_t>() + r->ebase, r->colidx.data(), 4 * r->m,
+                                         cudaMemcpyHostToDevice, st));
+        }
         SRV_CUDA(cudaMemsetAsync(verr + 4 * g, 0, 16, st));
         SRV_CUDA(launch_validate(r->n, s->rowptr.as<int32_t>() + r->rbase,
                                  r->m ? s->colidx.as<int32_t>() + r->ebase : s->rowptr.as<int32_t>() + r->rbase, 0,
@@ -361,6 +367,11 @@ void fail_all(gc_server *s, int code, const std::string &msg) {
         r->status = code;
     }
     s->queue.clear();
+    for (Request *r : s->staged) {
+        r->state = kDone;
+        r->status = code;
+    }
+    s->staged.clear();
     s->cv_done.notify_all();
 }
 
@@ -370,8 +381,16 @@ void worker_main(gc_server *s) {
         std::vector<Request *> adm;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty() || !s->resident.empty(); });
-            if (s->stop && s->queue.empty() && s->resident.empty()) break;
+            s->cv_work.wait(lk, [&] {
+                return s->stop || !s->queue.empty() || !s->resident.empty() || !s->staged.empty();
+            });
+            if (s->stop && s->queue.empty() && s->resident.empty() && s->staged.empty()) break;
+            for (Request *r : s->staged) {
+                r->state = kResident;
+                adm.push_back(r);
+                s->resident.push_back(r);
+            }
+            s->staged.clear();
             for (auto it = s->queue.begin(); it != s->queue.end();) {
                 if (reserve(s, *it)) {
                     (*it)->state = kResident;
@@ -472,6 +491,7 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
     s->PI = std::min<int64_t>(s->PV, s->PE / (gc::kT1 + 1) + 1);
     s->PC = s->PE / gc::kCH + s->PI + 1;
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
     const size_t V = static_cast<size_t>(s->PV), Sz = static_cast<size_t>(s->S);
     struct {
         gc::DevBuf *b;
@@ -541,18 +561,6 @@ int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32
     if (r->rowptr[0] != 0 || m < 0) return set_last_error(GC_ERR_INVALID_GRAPH, "rowptr must start at 0");
     if (m > 0 && !colidx) return set_last_error(GC_ERR_INVALID_ARG, "NULL colidx");
     r->m = m;
-    r->colidx.resize(static_cast<size_t>(m));
-    if (m) {
-        const bool ci_dev = cudaPointerGetAttributes(&a, colidx) == cudaSuccess &&
-                            (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
-        cudaGetLastError();
-        if (ci_dev) {
-            if (cudaMemcpy(r->colidx.data(), colidx, 4 * static_cast<size_t>(m), cudaMemcpyDeviceToHost) != cudaSuccess)
-                return set_last_error(GC_ERR_CUDA, "copying colidx");
-        } else {
-            std::memcpy(r->colidx.data(), colidx, 4 * static_cast<size_t>(m));
-        }
-    }
     // row offsets are checked here (they size the request's footprint); neighbour ids and self-loops
     // are checked on the device when the request is admitted
     for (int32_t v = 0; v < n; ++v) {
@@ -564,20 +572,55 @@ int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32
             r->n_chunks += (d + gc::kCH - 1) / gc::kCH;
         }
     }
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (s->fatal != GC_OK) return set_last_error(s->fatal, "server stopped: %s", s->fatal_msg.c_str());
-    if (n > s->va.capacity() || m > s->ea.capacity() || r->n_large > s->PI || r->n_chunks > s->PC) {
-        s->rejected += 1;
-        return set_last_error(GC_ERR_OOM, "request (n=%d, nnz=%lld) exceeds the server pool", n,
-                              static_cast<long long>(m));
-    }
-    r->id = s->next_id++;
-    r->t_submit = gc::now_s();
-    *req_id = r->id;
+    const bool ci_dev = m > 0 && cudaPointerGetAttributes(&a, colidx) == cudaSuccess &&
+                        (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
     gc::Request *raw = r.get();
-    s->reqs[raw->id] = std::move(r);
-    s->queue.push_back(raw);
-    s->submitted += 1;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->fatal != GC_OK) return set_last_error(s->fatal, "server stopped: %s", s->fatal_msg.c_str());
+        if (n > s->va.capacity() || m > s->ea.capacity() || r->n_large > s->PI || r->n_chunks > s->PC) {
+            s->rejected += 1;
+            return set_last_error(GC_ERR_OOM, "request (n=%d, nnz=%lld) exceeds the server pool", n,
+                                  static_cast<long long>(m));
+        }
+        r->id = s->next_id++;
+        r->t_submit = gc::now_s();
+        *req_id = r->id;
+        // with nothing queued ahead and room in the pool, the CSR goes straight into the pool
+        raw->staged = s->queue.empty() && gc::reserve(s, raw);
+        s->reqs[raw->id] = std::move(r);
+        s->submitted += 1;
+    }
+    cudaError_t e = cudaSuccess;
+    if (raw->staged) {
+        std::lock_guard<std::mutex> ck(s->copy_mu);
+        e = cudaMemcpyAsync(s->rowptr.as<int32_t>() + raw->rbase, raw->rowptr.data(), 4 * (static_cast<size_t>(n) + 1),
+                            cudaMemcpyHostToDevice, s->copy_stream);
+        if (e == cudaSuccess && m)
+            e = cudaMemcpyAsync(s->colidx.as<int32_t>() + raw->ebase, colidx, 4 * static_cast<size_t>(m),
+                                ci_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
+        std::vector<int32_t>().swap(raw->rowptr);
+    } else if (m) {
+        raw->colidx.resize(static_cast<size_t>(m));
+        if (ci_dev)
+            e = cudaMemcpy(raw->colidx.data(), colidx, 4 * static_cast<size_t>(m), cudaMemcpyDeviceToHost);
+        else
+            std::memcpy(raw->colidx.data(), colidx, 4 * static_cast<size_t>(m));
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (raw->staged) gc::unreserve(s, raw);
+        raw->state = gc::kDone;
+        raw->status = GC_ERR_CUDA;
+        return set_last_error(GC_ERR_CUDA, "copying the request: %s", cudaGetErrorString(e));
+    }
+    if (raw->staged)
+        s->staged.push_back(raw);
+    else
+        s->queue.push_back(raw);
     s->cv_work.notify_one();
     return GC_OK;
 }
@@ -657,6 +700,7 @@ void gc_server_destroy(gc_server *s) {
     }
     if (s->worker.joinable()) s->worker.join();
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
     delete s;
 }
 

@@ -4,7 +4,7 @@ import json
 import numpy as np
 
 import graphgen as gg
-from paper_1509_08267_gb300 import FLAG_COMPACT, autotune
+from paper_1509_08267_gb300 import FLAG_FULL_SWEEP, autotune
 
 
 def test_graph_classes():
@@ -24,7 +24,7 @@ def test_options_lookup(tmp_path):
     path.write_text(json.dumps(table))
     g = gg.rmat(12, 16, 2)
     o = autotune.options_for(g.n, g.degrees(), str(path))
-    assert (o.small_max_degree, o.chunk, o.blocks_per_sm) == (63, 512, 3) and o.flags & FLAG_COMPACT
+    assert (o.small_max_degree, o.chunk, o.blocks_per_sm) == (63, 512, 3) and not o.flags & FLAG_FULL_SWEEP
     s = gg.stencil27(8)
     assert autotune.options_for(s.n, s.degrees(), str(path)).chunk == 0  # no entry: library defaults
     assert autotune.batch_options(str(path)).chunk == 1024

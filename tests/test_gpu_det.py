@@ -114,12 +114,13 @@ def test_repeatable_and_properties(gclib):
 
 @pytest.mark.parametrize("make", [lambda: gg.rmat(14, 16, 2), lambda: gg.complete(600), lambda: gg.star(5000),
                                   lambda: gg.workload("er10k"), lambda: gg.stencil27(9), lambda: gg.crown(40)])
-def test_compact_sweep_matches_oracle(gclib, make):
-    # the compact sweep (skipping neighbours already final) is the same method as the plain sweep
+def test_full_sweep_matches_oracle(gclib, make):
+    # the full sweep (every entry every round) and the default compact sweep (only neighbours that
+    # can still change) are the same method
     g = make()
     ref = oracle.det(g, 11)
-    for opt in (gclib.Options(flags=gclib.FLAG_COMPACT), gclib.Options(flags=gclib.FLAG_COMPACT, chunk=128),
-                gclib.Options(flags=gclib.FLAG_COMPACT, chunk=32, small_max_degree=4)):
+    for opt in (gclib.Options(flags=gclib.FLAG_FULL_SWEEP), gclib.Options(flags=gclib.FLAG_FULL_SWEEP, chunk=128),
+                gclib.Options(chunk=32, small_max_degree=4), gclib.Options(chunk=1024)):
         c, nc, rounds, st = run_det(gclib, g, 11, options=opt, stats=True)
         np.testing.assert_array_equal(c, ref.colors)
         assert (nc, rounds) == (ref.ncolors, ref.rounds)
@@ -129,19 +130,19 @@ def test_compact_sweep_matches_oracle(gclib, make):
 
 def test_compact_reads_fewer_entries(gclib):
     g = gg.rmat(15, 16, 2)
-    _, _, _, plain = run_det(gclib, g, 7, stats=True)
-    _, _, _, compact = run_det(gclib, g, 7, options=gclib.Options(flags=gclib.FLAG_COMPACT), stats=True)
-    assert plain.entries_scanned == plain.wl_degsum.sum()
-    assert compact.entries_scanned < 0.8 * plain.entries_scanned
+    _, _, _, full = run_det(gclib, g, 7, options=gclib.Options(flags=gclib.FLAG_FULL_SWEEP), stats=True)
+    _, _, _, compact = run_det(gclib, g, 7, stats=True)
+    assert full.entries_scanned == full.wl_degsum.sum()
+    assert compact.entries_scanned < 0.8 * full.entries_scanned
 
 
-def test_batch_compact(gclib):
+def test_batch_full_sweep(gclib):
     import torch
     gs = [gg.rmat(11, 12, 5), gg.complete(300), gg.empty(3), gg.star(2000), gg.workload("er10k")]
     b = gg.pack(gs)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     colors, nc, rd = gclib.color_batch(dev(b.vtx_off), dev(b.edge_off), dev(b.rowptr), dev(b.colidx), "det", 3,
-                                       options=gclib.Options(flags=gclib.FLAG_COMPACT))
+                                       options=gclib.Options(flags=gclib.FLAG_FULL_SWEEP))
     colors = colors.cpu().numpy()
     for i, g in enumerate(gs):
         ref = oracle.det(g, 3)

@@ -386,12 +386,18 @@ __device__ __forceinline__ int32_t first_free_128(uint64_t mask0, uint64_t mask1
 // warp that completed the vertex's last work item; that warp then holds the merged window in
 // lo0/lo1/win, the merged flag in `lose` and the slot's survivor and new-length counters in
 // surv/newlen, and the round part of the slot is cleared for the next round.
+//
+// `snap` is this lane's word of the slot's round part as read when the item started (0 if not
+// read): bits only accumulate during a round, so bits already in the snapshot need no atomic.  When
+// `fin` is set, the warp that completes the vertex also reads word 32 + lane of the slot into it
+// (the window of final neighbours and the list fields), in the same round trip.
 template <bool WINDOW>
 __device__ __forceinline__ bool merge_item(unsigned *a, int nch, int lane, unsigned &lo0, unsigned &lo1, unsigned *win,
-                                           bool &lose, unsigned *surv = nullptr, unsigned *newlen = nullptr) {
+                                           bool &lose, unsigned snap, unsigned *surv = nullptr,
+                                           unsigned *newlen = nullptr, unsigned *fin = nullptr) {
     if constexpr (WINDOW) {
         const unsigned w = lane == 0 ? lo0 : lane == 1 ? lo1 : (lane < kAccWords ? win[lane] : 0u);
-        if (lane < kAccWords && (w & ~__ldcg(a + lane))) atomicOr(a + lane, w);
+        if (lane < kAccWords && (w & ~snap)) atomicOr(a + lane, w);
     }
     if (lane == 0 && lose) atomicOr(a + kAccFlag, 1u);
     __syncwarp();
@@ -400,6 +406,7 @@ __device__ __forceinline__ bool merge_item(unsigned *a, int nch, int lane, unsig
     done = __shfl_sync(kFull, done, 0);
     if (done != static_cast<unsigned>(nch - 1)) return false;
     const unsigned x = __ldcg(a + lane);  // the round part of the slot, one word per lane
+    if (fin) *fin = __ldcg(a + 32 + lane);
     if constexpr (WINDOW) {
         lo0 = __shfl_sync(kFull, x, 0);
         lo1 = __shfl_sync(kFull, x, 1);
@@ -521,7 +528,8 @@ __device__ __forceinline__ void sweep_list(const RoundParams &P, const Row &r, c
 template <bool BATCH, bool COMPACT>
 __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *coln, int4 it, unsigned *win,
                           unsigned *wfin, int4 *chunk_next, unsigned *cnt_next, int pass, int lane,
-                          unsigned long long &st_deg, unsigned long long &st_cnt, unsigned long long &st_read) {
+                          unsigned long long &st_deg, unsigned long long &st_cnt, unsigned long long &st_read,
+                          unsigned items_now, unsigned warps) {
     const int32_t V = it.x, k = it.y, slot = it.z, nitems = it.w;
     const Row r = load_row<BATCH>(P, V);
     const uint64_t self = load_state(colc + V);
@@ -538,15 +546,28 @@ __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *
     unsigned src = 0, len = 0, rewrite = 0;
     int64_t off = 0;
     const int64_t deg = r.e - r.b;
+    // the slot, one word per lane: the round window (a filter for the merge) and, with the compact
+    // sweep, the window of final neighbours and the list fields; the windows are kept in shared
+    // memory for the merge at the end of the item
+    unsigned *snapw = wfin + (COMPACT ? kAccWords : 0);
+    if (COMPACT || nitems > 1) {
+        const unsigned x = __ldcg(a + lane);
+        if (lane < kAccWords) snapw[lane] = x;
+    }
     if constexpr (COMPACT) {
-        src = __ldcg(a + kAccSrc);
-        len = __ldcg(a + kAccLen);
-        rewrite = __ldcg(a + kAccRewrite);
-        off = static_cast<int64_t>(__ldcg(a + kAccOffLo)) | (static_cast<int64_t>(__ldcg(a + kAccOffHi)) << 32);
+        const unsigned sm = __ldcg(a + 32 + lane);
+        if (lane < kAccWords) snapw[kAccWords + lane] = sm;
+        src = __shfl_sync(kFull, sm, kAccSrc - 32);
+        len = __shfl_sync(kFull, sm, kAccLen - 32);
+        rewrite = __shfl_sync(kFull, sm, kAccRewrite - 32);
+        off = static_cast<int64_t>(__shfl_sync(kFull, sm, kAccOffLo - 32)) |
+              (static_cast<int64_t>(__shfl_sync(kFull, sm, kAccOffHi - 32)) << 32);
         const int32_t *list = src == 0 ? P.colidx + r.b : P.lists + off + (src == 2 ? deg : 0);
         int32_t *dst = rewrite ? P.lists + off + (src == 1 ? deg : 0) : nullptr;
-        const int64_t lb = static_cast<int64_t>(k) * P.CH;
-        const int64_t le = min(static_cast<int64_t>(len), lb + P.CH);
+        // the vertex's items split its list evenly
+        const int64_t per = (static_cast<int64_t>(len) + nitems - 1) / nitems;
+        const int64_t lb = static_cast<int64_t>(k) * per;
+        const int64_t le = min(static_cast<int64_t>(len), lb + per);
         uint64_t flo = 0;
         unsigned survivors = 0;
         sweep_list(P, r, colc, list, lb, le, dst, a + kAccNewLen, lane, cv, pv, lo, win, flo, wfin, lose, survivors);
@@ -555,7 +576,7 @@ __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *
         __syncwarp();
         // neighbours found final: into the vertex's persistent window, before this item is counted
         const unsigned fw = lane == 0 ? f0 : lane == 1 ? f1 : (lane < kAccWords ? wfin[lane] : 0u);
-        if (lane < kAccWords && (fw & ~__ldcg(a + kAccFin + lane))) atomicOr(a + kAccFin + lane, fw);
+        if (lane < kAccWords && (fw & ~snapw[kAccWords + lane])) atomicOr(a + kAccFin + lane, fw);
         if (lane == 0) {
             if (survivors) atomicAdd(a + kAccSurv, survivors);
             st_read += static_cast<unsigned long long>(le > lb ? le - lb : 0);
@@ -570,9 +591,11 @@ __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *
     unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
     unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
     __syncwarp();
-    unsigned surv = 0, newlen = 0;
+    unsigned surv = 0, newlen = 0, fx = 0;
     if (nitems > 1 || COMPACT) {
-        if (!merge_item<true>(a, nitems, lane, lo0, lo1, win, lose, &surv, &newlen)) return;
+        if (!merge_item<true>(a, nitems, lane, lo0, lo1, win, lose, lane < kAccWords ? snapw[lane] : 0u, &surv,
+                              &newlen, COMPACT ? &fx : nullptr))
+            return;
     }
     // the warp that finishes a vertex accounts for it in the round statistics
     if (lane == 0) {
@@ -581,7 +604,7 @@ __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *
     }
     if constexpr (COMPACT) {
         // round window + colors of every neighbour known to be final
-        const unsigned fx = lane < kAccWords ? __ldcg(a + kAccFin + lane) : 0u;
+        if (lane >= kAccWords) fx = 0u;
         lo0 |= __shfl_sync(kFull, fx, 0);
         lo1 |= __shfl_sync(kFull, fx, 1);
         if (lane >= 2 && lane < kAccWords) win[lane] |= fx;
@@ -600,7 +623,19 @@ __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *
         const unsigned nsrc = rewrite ? (src == 1 ? 2u : 1u) : src;
         const unsigned nlen = rewrite ? newlen : len;
         const unsigned nrw = 4ull * surv < 3ull * nlen ? 1u : 0u;
-        const int32_t items = nlen > 0 ? static_cast<int32_t>((nlen + P.CH - 1) / P.CH) : 1;
+        // items of CH entries; in a round with fewer items than warps, smaller items (down to 64
+        // entries) so that the next round's latency is not one long item, but never more items
+        // than the vertex had in round 1 (the work-item buffers are sized for that)
+        int64_t items64 = (static_cast<int64_t>(nlen) + P.CH - 1) / P.CH;
+        if (items_now < warps) {
+            int64_t chs = static_cast<int64_t>(P.CH) * items_now / warps;
+            chs = chs < 64 ? 64 : (chs + 31) & ~int64_t{31};
+            const int64_t cap = (deg + P.CH - 1) / P.CH;
+            int64_t want = (static_cast<int64_t>(nlen) + chs - 1) / chs;
+            if (want > cap) want = cap;
+            if (want > items64) items64 = want;
+        }
+        const int32_t items = items64 > 0 ? static_cast<int32_t>(items64) : 1;
         unsigned cb = 0;
         if (lane == 0) {
             a[kAccSrc] = nsrc;
@@ -658,7 +693,7 @@ __device__ void ip_chunk_assign(const RoundParams &P, uint64_t *col, int4 it, un
     unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
     unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
     __syncwarp();
-    if (nch > 1 && !merge_item<true>(P.acc + static_cast<size_t>(slot) * kAccStride, nch, lane, lo0, lo1, win, unused))
+    if (nch > 1 && !merge_item<true>(P.acc + static_cast<size_t>(slot) * kAccStride, nch, lane, lo0, lo1, win, unused, 0u))
         return;
     int32_t nc = first_free(lo0, lo1, win);
     if (nc < 0) nc = mex_from<BATCH>(P, col, r, win, lane, 32 * kAccWords);
@@ -684,7 +719,7 @@ __device__ void ip_chunk_conflict(const RoundParams &P, const uint64_t *col, int
     sweep<false, true>(P, r, col, jb, je, lane, color_of(self), prio_of(self), lo, win, lose);
     lose = __any_sync(kFull, lose);
     unsigned lo0 = 0, lo1 = 0;
-    if (nch > 1 && !merge_item<false>(P.acc + static_cast<size_t>(slot) * kAccStride, nch, lane, lo0, lo1, win, lose))
+    if (nch > 1 && !merge_item<false>(P.acc + static_cast<size_t>(slot) * kAccStride, nch, lane, lo0, lo1, win, lose, 0u))
         return;
     if (lose) append_large<BATCH>(P, V, r, chunk_next, cnt_next, pass + 1, lane);
 }
@@ -718,7 +753,9 @@ __device__ __forceinline__ void flush_stats(const RoundParams &P, int pass, unsi
 template <bool BATCH, bool COMPACT>
 __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(RoundParams P) {
     __shared__ unsigned s_win[kMaxWarps][kAccWords];
-    __shared__ unsigned s_fin[kMaxWarps][COMPACT ? kAccWords : 1];
+    // per warp: the window of final neighbours found by the current item (compact sweep), then the
+    // item's snapshots of the slot's round window and of its final window
+    __shared__ unsigned s_fin[kMaxWarps][COMPACT ? 3 * kAccWords : kAccWords];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -747,9 +784,18 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(
         int4 *chunkn = odd ? P.chunk1 : P.chunk0;
         unsigned long long st_deg = 0, st_cnt = 0, st_read = 0;
         // work items of larger vertices first (they dominate), then one thread per small vertex
-        for (unsigned i = gw; i < nchunks; i += nw)
-            det_chunk<BATCH, COMPACT>(P, colc, coln, __ldcg(chunkc + i), win, wfin, chunkn, cn, pass, lane, st_deg,
-                                      st_cnt, st_read);
+        // (the next item's descriptor is read while the current one runs, one field in each of lanes 0..3)
+        if (static_cast<unsigned>(gw) < nchunks) {
+            const int32_t *cf = reinterpret_cast<const int32_t *>(chunkc);
+            int4 it = __ldcg(chunkc + gw);
+            for (unsigned i = gw; i < nchunks; i += nw) {
+                const int32_t nx = lane < 4 && i + nw < nchunks ? __ldcg(cf + 4 * static_cast<size_t>(i + nw) + lane) : 0;
+                det_chunk<BATCH, COMPACT>(P, colc, coln, it, win, wfin, chunkn, cn, pass, lane, st_deg, st_cnt,
+                                          st_read, nchunks, static_cast<unsigned>(nw));
+                it = make_int4(__shfl_sync(kFull, nx, 0), __shfl_sync(kFull, nx, 1), __shfl_sync(kFull, nx, 2),
+                               __shfl_sync(kFull, nx, 3));
+            }
+        }
         for (unsigned base = static_cast<unsigned>(gw) * 32u; base < nsmall; base += static_cast<unsigned>(nw) * 32u) {
             const unsigned i = base + lane;
             bool lose = false;

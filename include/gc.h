@@ -178,7 +178,7 @@ int gc_validate_graph(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
  * The paper has no counterpart: this entry point exists for callers that cannot call cudaMalloc
  * (code running inside an allocator or a memory-pool callback, or under a framework that owns every
  * device allocation and forbids side allocations).  It gives exactly gc_color's deterministic
- * result, but works in a fixed scratch array built into the library (about 5.2 MB of device memory,
+ * result, but works in a fixed scratch array built into the library (about 5.8 MB of device memory,
  * held by every GPU that loads the library until the process exits), so it accepts at most
  * 16,384 vertices and 2^20 adjacency entries; larger graphs return GC_ERR_INVALID_ARG with the
  * outputs untouched.

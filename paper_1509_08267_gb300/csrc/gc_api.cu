@@ -81,6 +81,7 @@ struct Ctl {
     int32_t gmax1, gcount1, glast1, pad1;
     int32_t pad2[2];
     GridBar bar;
+    unsigned deg_hist[256];  // degree counts and list positions of thread-per-vertex rows
 };
 static_assert(offsetof(Ctl, bar) % 128 == 0, "barrier alignment");
 
@@ -289,6 +290,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     P.tmp = ctl->tmp;
     P.list_total = compact ? &ctl->list_total : nullptr;
     P.list_alloc = compact ? &ctl->list_alloc : nullptr;
+    P.deg_hist = ctl->deg_hist;
     P.cnt = ctl->cnt;
     P.bar = &ctl->bar;
     P.err = ctl->err;
@@ -314,20 +316,21 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     }
     if (timing) GC_CUDA(cudaEventRecord(C.ev[0], s));
     GC_CUDA(launch_setup(P, mode, pb.batch, 0, static_cast<int32_t>(n), -1, s));
+    GC_CUDA(launch_sort_small(P, pb.batch, 0, static_cast<int32_t>(n), s));
     GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     GC_CUDA(cudaStreamSynchronize(s));
     if (h.err[0] != 0) return error_from_ctl(h);
     const unsigned n_small = h.cnt[kCnt * 1 + kCntSmall];  // round 1 uses counter set 1
     const unsigned n_items = h.tmp[0], n_chunks = h.tmp[1];
-    GC_TRY(ensure(C.chunk0, 16 * static_cast<size_t>(n_chunks), "work items"));
-    GC_TRY(ensure(C.chunk1, 16 * static_cast<size_t>(n_chunks), "work items"));
+    GC_TRY(ensure(C.chunk0, kItemBytes * static_cast<size_t>(n_chunks), "work items"));
+    GC_TRY(ensure(C.chunk1, kItemBytes * static_cast<size_t>(n_chunks), "work items"));
     GC_TRY(ensure(C.acc, 4 * kAccStride * static_cast<size_t>(n_items), "accumulators"));
     if (compact) GC_TRY(ensure(C.lists, 4 * static_cast<size_t>(h.list_total), "neighbour lists"));
     P.chunk0 = C.chunk0.as<int4>();
     P.chunk1 = C.chunk1.as<int4>();
     P.acc = C.acc.as<unsigned>();
     P.lists = compact ? C.lists.as<int32_t>() : nullptr;
-    GC_CUDA(launch_expand(P, pb.batch, compact, static_cast<int32_t>(n_items), s));
+    GC_CUDA(launch_expand(P, mode, pb.batch, compact, static_cast<int32_t>(n_items), s));
     if (timing) GC_CUDA(cudaEventRecord(C.ev[1], s));
 
     // persistent grid: every block resident; no more blocks than the first round can use

@@ -18,7 +18,7 @@ constexpr int kStep = GC_STEP;
 // Accumulator slot of a vertex of degree > T1 (its row is split into warp work items):
 //   [0, kAccWords)  round window: colors 0..511 of the neighbours read this round
 //   kAccFlag        conflict flag of this round
-//   kAccDone        work items of this round finished
+//   kAccDone        work items of this round finished (when the last item finishes the vertex)
 //   kAccSurv        compact mode: list entries whose neighbour was not final when read this round
 //   kAccNewLen      compact mode: entries written to the other list region this round
 // Compact mode only, kept for the whole run (the slot belongs to the vertex):
@@ -26,9 +26,10 @@ constexpr int kStep = GC_STEP;
 //   kAccSrc         where the vertex's list of possibly-changing neighbours is: 0 its CSR row,
 //                   1 region A, 2 region B of its space in the list pool
 //   kAccLen         entries in that list
-//   kAccRewrite     1: this round's items copy the entries still active into the other region
 //   kAccOffLo/Hi    offset of region A in the list pool (region B follows it, each deg entries)
-// Words [0, 32) are cleared by the warp that finishes the vertex's round.
+//   kAccDeg         the vertex's degree
+// The round part (words [0, 20)) is zero whenever a round starts: only vertices with several work
+// items use it, and whoever finishes such a vertex clears it.
 constexpr int kAccWords = 16;
 constexpr int kAccFlag = 16;
 constexpr int kAccDone = 17;
@@ -37,14 +38,21 @@ constexpr int kAccNewLen = 19;
 constexpr int kAccFin = 32;
 constexpr int kAccSrc = 48;
 constexpr int kAccLen = 49;
-constexpr int kAccRewrite = 50;
 constexpr int kAccOffLo = 51;
 constexpr int kAccOffHi = 52;
+constexpr int kAccDeg = 53;
 constexpr int kAccStride = 64;  // 256 B per slot
 
 // Worklist counters: three sets used round-robin (read / append / clear), kCnt words each.
 constexpr int kCnt = 4;
-constexpr int kCntSmall = 0, kCntItems = 1, kCntChunks = 2;
+//   kCntSmall   vertices of degree <= T1
+//   kCntItems   larger vertices (their accumulator slots, in non-compact mode, are numbered by it)
+//   kCntChunks  work items
+//   kCntMulti   deterministic mode: larger vertices with more than one work item
+constexpr int kCntSmall = 0, kCntItems = 1, kCntChunks = 2, kCntMulti = 3;
+
+// Bytes per work item in the work-item buffers (deterministic items are 48 bytes, in-place 16).
+constexpr size_t kItemBytes = 48;
 
 struct GridBar {
     unsigned count;
@@ -75,7 +83,7 @@ struct RoundParams {
     uint64_t *col0;  // deterministic: read in odd rounds, written in even ones; in-place: the live array
     uint64_t *col1;  // deterministic: written in odd rounds
     int32_t *small0, *small1;  // thread-per-vertex worklists (two parities)
-    int4 *chunk0, *chunk1;     // warp work items {vertex, chunk index, slot, chunks} (two parities)
+    int4 *chunk0, *chunk1;     // warp work items, kItemBytes each (two parities)
     int32_t *items;            // setup scratch: larger vertices found by the binning pass
     unsigned *tmp;             // [2] setup scratch counters: larger vertices, their work items
     unsigned *cnt;             // [3][kCnt] worklist counters
@@ -83,6 +91,8 @@ struct RoundParams {
     int32_t *lists;                   // compact mode: list pool (two regions of deg entries per larger vertex)
     unsigned long long *list_total;   // compact mode: setup adds 2 * deg of every larger vertex
     unsigned long long *list_alloc;   // compact mode: expand's allocation counter in the list pool
+    unsigned *deg_hist;               // [256] optional: setup counts thread-per-vertex rows per degree
+                                      // ([0, 128)); list positions per degree follow ([128, 256))
     GridBar *bar;
     int32_t *err;              // [4] status, vertex, entry, extra
     int32_t *passes;           // [2] first round not executed by the last launch, last round executed
@@ -108,10 +118,14 @@ cudaError_t launch_batch_tables(const RoundParams &P, const int64_t *vtx_off, co
 // if any of them has a neighbour); otherwise vg must be filled already.
 cudaError_t launch_setup(const RoundParams &P, int mode, bool batch, int32_t v_begin, int32_t v_end,
                          int32_t g_fixed, cudaStream_t s);
+// With P.deg_hist: writes the thread-per-vertex entries of [v_begin, v_end) (counted by setup) to
+// the current small list in increasing order of degree.  Without it, setup appended them already.
+cudaError_t launch_sort_small(const RoundParams &P, bool batch, int32_t v_begin, int32_t v_end, cudaStream_t s);
 // Turns the n_items larger vertices found by setup into work items of round P.pass_begin
 // (n_items < 0: the count setup left in P.tmp[0] on the device).
 // compact: every larger vertex gets a persistent slot and list-pool space (deterministic mode).
-cudaError_t launch_expand(const RoundParams &P, bool batch, bool compact, int32_t n_items, cudaStream_t s);
+cudaError_t launch_expand(const RoundParams &P, int mode, bool batch, bool compact, int32_t n_items,
+                          cudaStream_t s);
 // compact (deterministic mode only): larger vertices sweep packed lists of the neighbours that can
 // still change instead of their whole rows.
 cudaError_t launch_rounds(const RoundParams &P, int mode, bool batch, bool compact, int grid, int block,

@@ -29,6 +29,10 @@ constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;  // SplitMix64 state incremen
 constexpr int kBlock = 256;                          // round-kernel block size
 constexpr int kMaxWarps = kBlock / 32;
 constexpr int kPer = kStep / 32;  // entries per lane per step
+#ifndef GC_MERGE_NOW_ITEMS
+#define GC_MERGE_NOW_ITEMS 2  // deterministic rounds with at most this many items per warp finish
+#endif                        // several-item vertices without a second barrier
+constexpr unsigned kMergeNowItems = GC_MERGE_NOW_ITEMS;
 #ifndef GC_ROUND_MIN_BLOCKS
 #define GC_ROUND_MIN_BLOCKS 4  // resident blocks per SM the round kernel is compiled for
 #endif
@@ -148,6 +152,15 @@ __device__ __forceinline__ uint64_t load_state(const uint64_t *p) {
 __device__ __forceinline__ int32_t load_entry(const int32_t *p) {
     int32_t v;
     asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Four adjacency entries from a 16-byte aligned address, streamed the same way.
+__device__ __forceinline__ int4 load_entry4(const int32_t *p) {
+    int4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
     return v;
 }
 
@@ -341,25 +354,46 @@ __device__ __forceinline__ void sweep(const RoundParams &P, const Row &r, const 
     }
 }
 
+// Entries [j0, j0 + 4) of colidx for a thread's row, zero at and past e: one 16-byte load when
+// the group is 16-byte aligned (`vec`: colidx is, and j0 is a multiple of 4) and lies before e, else
+// single loads.
+__device__ __forceinline__ void load4(const int32_t *colidx, bool vec, int64_t j0, int64_t e, int32_t (&u)[4]) {
+    if (vec && j0 + 3 < e) {
+        const int4 v = load_entry4(colidx + j0);
+        u[0] = v.x;
+        u[1] = v.y;
+        u[2] = v.z;
+        u[3] = v.w;
+    } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) u[t] = j0 + t < e ? load_entry(colidx + j0 + t) : 0;
+    }
+}
+
 // Per-thread sweep of a short row (degree <= T1 <= 127): window [0, 128) in two 64-bit masks (the
-// least free color is at most deg(v)) and conflict flag.
+// least free color is at most deg(v)) and conflict flag.  Four entries per step from the aligned
+// group of four that holds the row's first entry; the next step's entries are loaded before the
+// current step's gathers are consumed.
 template <bool BATCH, bool WINDOW, bool CONFLICT>
 __device__ __forceinline__ void sweep_small(const RoundParams &P, const Row &r, const uint64_t *colc, int32_t cv,
                                             uint32_t pv, uint64_t &mask0, uint64_t &mask1, bool &lose) {
-    constexpr int kT = 8;  // loads in flight per thread
-    for (int64_t j0 = r.b; j0 < r.e; j0 += kT) {
-        int32_t ul[kT];
+    constexpr int kT = 4;  // entries per step
+    const bool vec = (reinterpret_cast<uintptr_t>(P.colidx) & 15u) == 0;
+    int64_t j0 = vec ? (r.b & ~int64_t{3}) : r.b;
+    int32_t ul[kT], un[kT];
+    if (j0 < r.e) load4(P.colidx, vec, j0, r.e, ul);
+    for (; j0 < r.e; j0 += kT) {
         uint64_t w[kT];
-#pragma unroll
-        for (int q = 0; q < kT; ++q) ul[q] = j0 + q < r.e ? load_entry(P.colidx + j0 + q) : 0;
 #pragma unroll
         for (int q = 0; q < kT; ++q) {
             w[q] = kNoNeighbour;
-            if (j0 + q < r.e) {
+            if (j0 + q >= r.b && j0 + q < r.e) {
                 const int32_t U = neighbour(P, r, ul[q], j0 + q);
                 if (U >= 0) w[q] = load_state(colc + U);
             }
         }
+        const bool more = j0 + kT < r.e;
+        if (more) load4(P.colidx, vec, j0 + kT, r.e, un);
 #pragma unroll
         for (int q = 0; q < kT; ++q) {
             const int32_t c = color_of(w[q]);
@@ -373,6 +407,10 @@ __device__ __forceinline__ void sweep_small(const RoundParams &P, const Row &r, 
                 if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
                                                       static_cast<uint32_t>(r.lv), P.seed);
             }
+        }
+        if (more) {
+#pragma unroll
+            for (int q = 0; q < kT; ++q) ul[q] = un[q];
         }
     }
 }
@@ -454,31 +492,123 @@ __device__ __forceinline__ bool det_small(const RoundParams &P, const uint64_t *
     return lose;
 }
 
-// Compact sweep of entries [lb, le) of a vertex's list of neighbours that may still change (local
-// ids; the list is its CSR row until the first rewrite).  A neighbour found final is dropped: its
-// color goes, besides the round window (lo / win), to the window of final neighbours (flo / wfin)
-// that the vertex keeps.  When `dst` is set, the entries still active are appended there (the
-// vertex's other list region) at positions reserved in the slot's new-length counter.  Lane 0
-// returns the entries still active.
-__device__ __forceinline__ void sweep_list(const RoundParams &P, const Row &r, const uint64_t *colc,
-                                           const int32_t *list, int64_t lb, int64_t le, int32_t *dst,
-                                           unsigned *newlen, int lane, int32_t cv, uint32_t pv, uint64_t &lo,
-                                           unsigned *win, uint64_t &flo, unsigned *wfin, bool &lose,
-                                           unsigned &survivors) {
-    int32_t ul[kPer], un[kPer];
-    uint64_t w[kPer];
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-        const int64_t j = lb + lane + 32 * q;
-        ul[q] = j < le ? load_entry(list + j) : 0;
+// Work item of a larger vertex in deterministic mode (48 bytes, kItemBytes).
+struct DetItem {
+    const int32_t *list;  // the vertex's list of neighbours (local ids): its CSR row or a list-pool region
+    int32_t V;            // global vertex id
+    uint32_t slotf;       // accumulator slot | kItemRewrite | kItemMulti
+    int32_t lb, le;       // the item's entries [lb, le) of the list
+    int32_t vbase, ng;    // global id of the graph's vertex 0, vertices of the graph
+    int32_t nitems;       // the vertex's items this round
+    int32_t deg;          // the vertex's degree
+    int32_t pad[2];
+};
+static_assert(sizeof(DetItem) == kItemBytes, "work-item size");
+constexpr int kItemWords = static_cast<int>(kItemBytes / 4);
+constexpr uint32_t kItemRewrite = 1u << 31;  // the items also copy the entries still active to the other region
+constexpr uint32_t kItemMulti = 1u << 30;    // the vertex has several items this round
+constexpr uint32_t kItemSlot = kItemMulti - 1u;
+
+__device__ __forceinline__ void store_item(DetItem *p, const int32_t *list, int32_t V, uint32_t slotf, int32_t lb,
+                                           int32_t le, int32_t vbase, int32_t ng, int32_t nitems, int32_t deg) {
+    const uint64_t l = reinterpret_cast<uint64_t>(list);
+    int4 *q = reinterpret_cast<int4 *>(p);
+    q[0] = make_int4(static_cast<int32_t>(l), static_cast<int32_t>(l >> 32), V, static_cast<int32_t>(slotf));
+    q[1] = make_int4(lb, le, vbase, ng);
+    q[2] = make_int4(nitems, deg, 0, 0);
+}
+
+// Word `lane` (< 10) of item i; item_of() assembles the item in every lane.
+__device__ __forceinline__ uint32_t item_word(const DetItem *items, unsigned i, int lane) {
+    return lane < 10 ? __ldcg(reinterpret_cast<const unsigned *>(items + i) + lane) : 0u;
+}
+__device__ __forceinline__ DetItem item_of(uint32_t w) {
+    DetItem d;
+    const uint64_t lo = __shfl_sync(kFull, w, 0), hi = __shfl_sync(kFull, w, 1);
+    d.list = reinterpret_cast<const int32_t *>(lo | (hi << 32));
+    d.V = static_cast<int32_t>(__shfl_sync(kFull, w, 2));
+    d.slotf = __shfl_sync(kFull, w, 3);
+    d.lb = static_cast<int32_t>(__shfl_sync(kFull, w, 4));
+    d.le = static_cast<int32_t>(__shfl_sync(kFull, w, 5));
+    d.vbase = static_cast<int32_t>(__shfl_sync(kFull, w, 6));
+    d.ng = static_cast<int32_t>(__shfl_sync(kFull, w, 7));
+    d.nitems = static_cast<int32_t>(__shfl_sync(kFull, w, 8));
+    d.deg = static_cast<int32_t>(__shfl_sync(kFull, w, 9));
+    return d;
+}
+
+// One item per lane (phase B's scan of the round's items).
+__device__ __forceinline__ DetItem item_lane(const DetItem *p) {
+    const int4 x = __ldcg(reinterpret_cast<const int4 *>(p));
+    const int4 y = __ldcg(reinterpret_cast<const int4 *>(p) + 1);
+    const int4 z = __ldcg(reinterpret_cast<const int4 *>(p) + 2);
+    DetItem d;
+    d.list = reinterpret_cast<const int32_t *>(static_cast<uint64_t>(static_cast<uint32_t>(x.x)) |
+                                               (static_cast<uint64_t>(static_cast<uint32_t>(x.y)) << 32));
+    d.V = x.z;
+    d.slotf = static_cast<uint32_t>(x.w);
+    d.lb = y.x;
+    d.le = y.y;
+    d.vbase = y.z;
+    d.ng = y.w;
+    d.nitems = z.x;
+    d.deg = z.y;
+    return d;
+}
+
+__device__ __forceinline__ uint4 ldcg4(const unsigned *p) { return __ldcg(reinterpret_cast<const uint4 *>(p)); }
+__device__ __forceinline__ void stcg4(unsigned *p, uint4 v) { __stcg(reinterpret_cast<uint4 *>(p), v); }
+
+// Least color in [base, base + 128) absent from the four window words w (-1 if all are set).
+__device__ __forceinline__ int32_t first_free4(uint4 w, int32_t base) {
+    if (~w.x) return base + __ffs(~w.x) - 1;
+    if (~w.y) return base + 32 + __ffs(~w.y) - 1;
+    if (~w.z) return base + 64 + __ffs(~w.z) - 1;
+    if (~w.w) return base + 96 + __ffs(~w.w) - 1;
+    return -1;
+}
+
+// Work items of the next round for a larger vertex that lost: how many, and the entries per item.
+// Compact: the list splits evenly into items of about CH entries; in a round with fewer items than
+// warps, into smaller ones (down to 128 entries) so that the next round is not one long item, but
+// never into more items than the vertex had in round 1 (the buffers are sized for that).
+__device__ __forceinline__ int32_t next_items(const RoundParams &P, int64_t len, int64_t deg, unsigned items_now,
+                                              unsigned warps) {
+    int64_t items = (len + P.CH - 1) / P.CH;
+    if (items_now < warps) {
+        int64_t chs = static_cast<int64_t>(P.CH) * items_now / warps;
+        chs = chs < 128 ? 128 : (chs + 31) & ~int64_t{31};
+        const int64_t cap = (deg + P.CH - 1) / P.CH;
+        int64_t want = (len + chs - 1) / chs;
+        if (want > cap) want = cap;
+        if (want > items) items = want;
     }
+    return items > 0 ? static_cast<int32_t>(items) : 1;
+}
+
+// Sweep of entries [lb, le) of a larger vertex's list with one warp, kStep entries per step (the
+// first step's entries are already in ul; the next step's are loaded before the current step's
+// gathers are consumed).  Every neighbour's color goes to the round window (lo: colors 0..63 per
+// lane, win: 64..511 shared by the warp) and a neighbour with the same color and a smaller key sets
+// `lose`.  COMPACT: a neighbour found final is also recorded in the window of final neighbours
+// (flo / wfin) and dropped; the entries still active are counted (survivors, lane 0) and, when
+// `dst` is set, copied to dst at positions from *newlen (atomically when `shared_len`, else lane 0's
+// running count `written`).
+template <bool COMPACT>
+__device__ __forceinline__ void sweep_item(const RoundParams &P, const Row &r, const uint64_t *colc,
+                                           const int32_t *list, int64_t lb, int64_t le, int32_t (&ul)[kPer],
+                                           int32_t *dst, unsigned *newlen, bool shared_len, int lane, int32_t cv,
+                                           uint32_t pv, uint64_t &lo, unsigned *win, uint64_t &flo, unsigned *wfin,
+                                           bool &lose, unsigned &survivors, unsigned &written) {
+    int32_t un[kPer];
+    uint64_t w[kPer];
     for (int64_t j0 = lb; j0 < le; j0 += kStep) {
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int64_t j = j0 + lane + 32 * q;
             w[q] = kNoNeighbour;
             if (j < le) {
-                const int32_t U = neighbour(P, r, ul[q], r.b + j);
+                const int32_t U = neighbour(P, r, ul[q], j);
                 if (U >= 0) w[q] = load_state(colc + U);
             }
         }
@@ -487,15 +617,13 @@ __device__ __forceinline__ void sweep_list(const RoundParams &P, const Row &r, c
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
                 const int64_t j = j0 + kStep + lane + 32 * q;
-                un[q] = j < le ? load_entry(list + j) : 0;
+                un[q] = j < le ? __ldcg(list + j) : 0;
             }
         }
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
-            const int64_t j = j0 + lane + 32 * q;
             const int32_t c = color_of(w[q]);
-            const bool valid = j < le;
-            const bool fin = valid && final_of(w[q]);
+            const bool fin = COMPACT && j0 + lane + 32 * q < le && final_of(w[q]);
             if (static_cast<unsigned>(c) < 64u) {
                 lo |= 1ull << c;
                 if (fin) flo |= 1ull << c;
@@ -505,14 +633,23 @@ __device__ __forceinline__ void sweep_list(const RoundParams &P, const Row &r, c
             }
             if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
                                                   static_cast<uint32_t>(r.lv), P.seed);
-            const bool keep = valid && !fin;
-            const unsigned km = __ballot_sync(kFull, keep);
-            if (lane == 0) survivors += __popc(km);
-            if (dst && km) {
-                unsigned pos = 0;
-                if (lane == 0) pos = atomicAdd(newlen, static_cast<unsigned>(__popc(km)));
-                pos = __shfl_sync(kFull, pos, 0);
-                if (keep) dst[pos + __popc(km & lanemask_lt())] = ul[q];
+            if constexpr (COMPACT) {
+                const bool keep = j0 + lane + 32 * q < le && !fin;
+                const unsigned km = __ballot_sync(kFull, keep);
+                if (lane == 0) survivors += __popc(km);
+                if (dst && km) {
+                    unsigned pos = 0;
+                    if (lane == 0) {
+                        if (shared_len) {
+                            pos = atomicAdd(newlen, static_cast<unsigned>(__popc(km)));
+                        } else {
+                            pos = written;
+                            written += __popc(km);
+                        }
+                    }
+                    pos = __shfl_sync(kFull, pos, 0);
+                    if (keep) dst[pos + __popc(km & lanemask_lt())] = ul[q];
+                }
             }
         }
         if (more) {
@@ -522,89 +659,235 @@ __device__ __forceinline__ void sweep_list(const RoundParams &P, const Row &r, c
     }
 }
 
-// One CH-entry work item of a larger vertex (one warp).  COMPACT: the slot (it.z) is the vertex's own
-// for the whole run and the item covers entries [k*CH, (k+1)*CH) of its list of neighbours that may
-// still change; otherwise the slot is per round and the item covers the same range of its row.
+// Appends the next round's items of the vertices that lost in lanes with items_l > 0 (one
+// warp-aggregated reservation).  slot_l: the lane's slot (compact), or -1 to take a new slot from
+// the next round's count of larger vertices.  per_l: entries per item (the list splits into
+// [q * per_l, min(len_l, (q + 1) * per_l))).
+__device__ __forceinline__ void append_items(DetItem *next, unsigned *cnt_next, int lane, int32_t items_l,
+                                             const int32_t *list_l, int32_t V, int64_t slot_l, uint32_t flags_l,
+                                             int64_t len_l, int64_t per_l, int32_t vbase, int32_t ng, int32_t deg) {
+    const bool take = items_l > 0;
+    const unsigned m = __ballot_sync(kFull, take);
+    if (m == 0) return;
+    unsigned incl = take ? static_cast<unsigned>(items_l) : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    const unsigned mm = __ballot_sync(kFull, items_l > 1);
+    unsigned cb = 0, sb = 0;
+    if (lane == 0) {
+        sb = atomicAdd(cnt_next + kCntItems, static_cast<unsigned>(__popc(m)));
+        cb = atomicAdd(cnt_next + kCntChunks, total);
+        if (mm) atomicAdd(cnt_next + kCntMulti, static_cast<unsigned>(__popc(mm)));
+    }
+    cb = __shfl_sync(kFull, cb, 0);
+    sb = __shfl_sync(kFull, sb, 0);
+    if (!take) return;
+    const uint32_t slot = slot_l >= 0 ? static_cast<uint32_t>(slot_l) : sb + __popc(m & lanemask_lt());
+    const uint32_t slotf = slot | flags_l | (items_l > 1 ? kItemMulti : 0u);
+    DetItem *out = next + cb + (incl - static_cast<unsigned>(items_l));
+    for (int32_t q = 0; q < items_l; ++q) {
+        const int64_t lb = static_cast<int64_t>(q) * per_l;
+        const int64_t le = min(len_l, lb + per_l);
+        store_item(out + q, list_l, V, slotf, static_cast<int32_t>(lb), static_cast<int32_t>(le), vbase, ng, items_l,
+                   deg);
+    }
+}
+
+// Finishes larger vertices whose items merged into their slots, one lane per vertex (lanes with
+// `fin`; d = any item of the vertex): reads the merged slot, takes the least free color if the
+// vertex lost, writes its state, clears the slot's round part and appends its next items.
 template <bool BATCH, bool COMPACT>
-__device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *coln, int4 it, unsigned *win,
-                          unsigned *wfin, int4 *chunk_next, unsigned *cnt_next, int pass, int lane,
-                          unsigned long long &st_deg, unsigned long long &st_cnt, unsigned long long &st_read,
-                          unsigned items_now, unsigned warps) {
-    const int32_t V = it.x, k = it.y, slot = it.z, nitems = it.w;
-    const Row r = load_row<BATCH>(P, V);
-    const uint64_t self = load_state(colc + V);
+__device__ __forceinline__ void det_finish(const RoundParams &P, const uint64_t *colc, uint64_t *coln, bool fin,
+                                           const DetItem &d, unsigned *win, DetItem *next, unsigned *cnt_next,
+                                           int pass, int lane, unsigned items_now, unsigned warps,
+                                           unsigned long long &st_deg, unsigned long long &st_cnt) {
+    const int32_t V = d.V;
+    const uint32_t slot = d.slotf & kItemSlot;
+    const int64_t deg = d.deg;
+    unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
+    uint4 st = make_uint4(0, 0, 0, 0), m0 = st, m1 = st;
+    uint4 w[kAccWords / 4];
+    uint64_t self = 0;
+    if (fin) {
+        self = load_state(colc + V);
+        st = ldcg4(a + kAccFlag);  // flag, item count, survivors, new length
+        if (COMPACT) {
+            m0 = ldcg4(a + kAccSrc);    // src, len, (unused), offset lo
+            m1 = ldcg4(a + kAccOffHi);  // offset hi, degree
+        }
+#pragma unroll
+        for (int c = 0; c < kAccWords / 4; ++c) {
+            w[c] = ldcg4(a + 4 * c);
+            if (COMPACT) {
+                const uint4 f = ldcg4(a + kAccFin + 4 * c);
+                w[c].x |= f.x;
+                w[c].y |= f.y;
+                w[c].z |= f.z;
+                w[c].w |= f.w;
+            }
+        }
+    }
+    const bool lose = fin && st.x != 0u;
     const int32_t cv = color_of(self);
     const uint32_t pv = prio_of(self);
+    int32_t nc = cv;
+    if (lose) {
+        nc = -1;
+#pragma unroll
+        for (int c = 0; c < kAccWords / 4; ++c)
+            if (nc < 0) nc = first_free4(w[c], 128 * c);
+    }
+    // rare: all of colors 0..511 taken; the warp rescans each such row in full
+    unsigned need = __ballot_sync(kFull, lose && nc < 0);
+    while (need) {
+        const int l = __ffs(need) - 1;
+        need &= need - 1;
+        Row rl = load_row<BATCH>(P, __shfl_sync(kFull, V, l));
+        const int32_t x = mex_from<BATCH>(P, colc, rl, win, lane, 32 * kAccWords);
+        if (lane == l) nc = x;
+    }
+    if (fin) {
+        det_write(colc, coln, V, lose, cv, nc, pv);
+        st_deg += static_cast<unsigned long long>(deg);
+        st_cnt += 1;
+        const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int c = 0; c < 20; c += 4) stcg4(a + c, z);
+    }
+    if constexpr (BATCH) {
+        if (lose) note_graph_round(P, __ldg(P.vg + V), pass + 1);
+    }
+    int32_t items = 0;
+    const int32_t *list = d.list;
+    int64_t len = deg, per = P.CH;
+    uint32_t flags = 0;
+    if (lose) {
+        if constexpr (COMPACT) {
+            const unsigned src = m0.x, olen = m0.y;
+            const bool rewrite = (d.slotf & kItemRewrite) != 0;
+            const int64_t off = static_cast<int64_t>(m0.w) | (static_cast<int64_t>(m1.x) << 32);
+            const unsigned nsrc = rewrite ? (src == 1 ? 2u : 1u) : src;
+            const unsigned nlen = rewrite ? st.w : olen;
+            flags = 4ull * st.z < 3ull * nlen ? kItemRewrite : 0u;
+            items = next_items(P, nlen, deg, items_now, warps);
+            a[kAccSrc] = nsrc;
+            a[kAccLen] = nlen;
+            if (nsrc != src) list = P.lists + off + (nsrc == 2 ? deg : 0);
+            len = nlen;
+            per = (len + items - 1) / items;
+            if (per < 1) per = 1;
+        } else {
+            items = static_cast<int32_t>((deg + P.CH - 1) / P.CH);
+        }
+    }
+    append_items(next, cnt_next, lane, items, list, V, COMPACT ? static_cast<int64_t>(slot) : -1, flags, len, per,
+                 d.vbase, d.ng, static_cast<int32_t>(deg));
+}
+
+// Phase A, one work item of a larger vertex (one warp).  A vertex with one item is finished here.
+// The items of a vertex with several merge their windows, conflict flag and (compact) final window
+// and list counts into its slot with atomics; then either phase B finishes the vertex after the
+// grid barrier (`merge_now` false: rounds with many items per warp, where no item waits for
+// another), or the item that completes the slot's count finishes it at once (`merge_now`: sparse
+// rounds, where the extra barrier would cost more than the wait).
+template <bool BATCH, bool COMPACT>
+__device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *coln, const DetItem &d,
+                         unsigned *win, unsigned *wfin, unsigned *snap, DetItem *next, unsigned *cnt_next, int pass,
+                         int lane, unsigned items_now, unsigned warps, bool merge_now, unsigned long long &st_deg,
+                         unsigned long long &st_cnt, unsigned long long &st_read) {
+    const int32_t V = d.V;
+    const uint32_t slot = d.slotf & kItemSlot;
+    const bool multi = (d.slotf & kItemMulti) != 0;
     unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
+    Row r;
+    r.b = 0;
+    r.e = 0;
+    r.vbase = d.vbase;
+    r.ng = d.ng;
+    r.lv = V - d.vbase;
+    r.g = 0;
+    // the first step's entries, the vertex's state and its slot: one round trip
+    int32_t ul[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int64_t j = static_cast<int64_t>(d.lb) + lane + 32 * q;
+        ul[q] = j < d.le ? __ldcg(d.list + j) : 0;
+    }
+    const uint64_t self = load_state(colc + V);
+    const unsigned x = multi ? __ldcg(a + lane) : 0u;
+    const unsigned sm = COMPACT ? __ldcg(a + 32 + lane) : 0u;
     if (lane < kAccWords) {
         win[lane] = 0;
-        if (COMPACT) wfin[lane] = 0;
+        snap[lane] = x;
+        if (COMPACT) {
+            wfin[lane] = 0;
+            snap[kAccWords + lane] = sm;
+        }
     }
-    __syncwarp();
-    uint64_t lo = 0;
-    bool lose = false;
-    unsigned src = 0, len = 0, rewrite = 0;
+    const int32_t cv = color_of(self);
+    const uint32_t pv = prio_of(self);
+    const int64_t deg = d.deg;
+    int32_t *dst = nullptr;
+    unsigned src = 0, len = 0;
     int64_t off = 0;
-    const int64_t deg = r.e - r.b;
-    // the slot, one word per lane: the round window (a filter for the merge) and, with the compact
-    // sweep, the window of final neighbours and the list fields; the windows are kept in shared
-    // memory for the merge at the end of the item
-    unsigned *snapw = wfin + (COMPACT ? kAccWords : 0);
-    if (COMPACT || nitems > 1) {
-        const unsigned x = __ldcg(a + lane);
-        if (lane < kAccWords) snapw[lane] = x;
-    }
     if constexpr (COMPACT) {
-        const unsigned sm = __ldcg(a + 32 + lane);
-        if (lane < kAccWords) snapw[kAccWords + lane] = sm;
         src = __shfl_sync(kFull, sm, kAccSrc - 32);
         len = __shfl_sync(kFull, sm, kAccLen - 32);
-        rewrite = __shfl_sync(kFull, sm, kAccRewrite - 32);
         off = static_cast<int64_t>(__shfl_sync(kFull, sm, kAccOffLo - 32)) |
               (static_cast<int64_t>(__shfl_sync(kFull, sm, kAccOffHi - 32)) << 32);
-        const int32_t *list = src == 0 ? P.colidx + r.b : P.lists + off + (src == 2 ? deg : 0);
-        int32_t *dst = rewrite ? P.lists + off + (src == 1 ? deg : 0) : nullptr;
-        // the vertex's items split its list evenly
-        const int64_t per = (static_cast<int64_t>(len) + nitems - 1) / nitems;
-        const int64_t lb = static_cast<int64_t>(k) * per;
-        const int64_t le = min(static_cast<int64_t>(len), lb + per);
-        uint64_t flo = 0;
-        unsigned survivors = 0;
-        sweep_list(P, r, colc, list, lb, le, dst, a + kAccNewLen, lane, cv, pv, lo, win, flo, wfin, lose, survivors);
-        const unsigned f0 = __reduce_or_sync(kFull, static_cast<unsigned>(flo));
-        const unsigned f1 = __reduce_or_sync(kFull, static_cast<unsigned>(flo >> 32));
-        __syncwarp();
-        // neighbours found final: into the vertex's persistent window, before this item is counted
-        const unsigned fw = lane == 0 ? f0 : lane == 1 ? f1 : (lane < kAccWords ? wfin[lane] : 0u);
-        if (lane < kAccWords && (fw & ~snapw[kAccWords + lane])) atomicOr(a + kAccFin + lane, fw);
-        if (lane == 0) {
-            if (survivors) atomicAdd(a + kAccSurv, survivors);
-            st_read += static_cast<unsigned long long>(le > lb ? le - lb : 0);
-        }
-    } else {
-        const int64_t jb = r.b + static_cast<int64_t>(k) * P.CH;
-        const int64_t je = min(r.e, jb + P.CH);
-        sweep<true, true>(P, r, colc, jb, je, lane, cv, pv, lo, win, lose);
-        if (lane == 0) st_read += static_cast<unsigned long long>(je - jb);
+        if (d.slotf & kItemRewrite) dst = P.lists + off + (src == 1 ? deg : 0);
     }
+    __syncwarp();
+    uint64_t lo = 0, flo = 0;
+    bool lose = false;
+    unsigned survivors = 0, written = 0;
+    sweep_item<COMPACT>(P, r, colc, d.list, d.lb, d.le, ul, dst, a + kAccNewLen, multi, lane, cv, pv, lo, win, flo,
+                        wfin, lose, survivors, written);
+    if (lane == 0) st_read += static_cast<unsigned long long>(d.le - d.lb);
     lose = __any_sync(kFull, lose);
     unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
     unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
-    __syncwarp();
-    unsigned surv = 0, newlen = 0, fx = 0;
-    if (nitems > 1 || COMPACT) {
-        if (!merge_item<true>(a, nitems, lane, lo0, lo1, win, lose, lane < kAccWords ? snapw[lane] : 0u, &surv,
-                              &newlen, COMPACT ? &fx : nullptr))
-            return;
+    unsigned f0 = 0, f1 = 0;
+    if constexpr (COMPACT) {
+        f0 = __reduce_or_sync(kFull, static_cast<unsigned>(flo));
+        f1 = __reduce_or_sync(kFull, static_cast<unsigned>(flo >> 32));
     }
-    // the warp that finishes a vertex accounts for it in the round statistics
+    __syncwarp();
+    if (multi) {
+        // into the slot; bits already in the snapshot need no atomic (bits only accumulate)
+        if constexpr (COMPACT) {
+            const unsigned fw = lane == 0 ? f0 : lane == 1 ? f1 : (lane < kAccWords ? wfin[lane] : 0u);
+            if (lane < kAccWords && (fw & ~snap[kAccWords + lane])) atomicOr(a + kAccFin + lane, fw);
+            if (lane == 0 && survivors) atomicAdd(a + kAccSurv, survivors);
+        }
+        const unsigned w = lane == 0 ? lo0 : lane == 1 ? lo1 : (lane < kAccWords ? win[lane] : 0u);
+        if (lane < kAccWords && (w & ~snap[lane])) atomicOr(a + lane, w);
+        if (lane == 0 && lose) atomicOr(a + kAccFlag, 1u);
+        if (!merge_now) return;
+        // the item that completes the count (release: its merges first; acquire: the others')
+        __syncwarp();
+        unsigned done = 0;
+        if (lane == 0) done = atom_add_acq_rel(a + kAccDone, 1u);
+        done = __shfl_sync(kFull, done, 0);
+        if (done != static_cast<unsigned>(d.nitems - 1)) return;
+        det_finish<BATCH, COMPACT>(P, colc, coln, lane == 0, d, win, next, cnt_next, pass, lane, items_now, warps,
+                                   st_deg, st_cnt);
+        return;
+    }
+    // the vertex's only item: its result now
     if (lane == 0) {
         st_deg += static_cast<unsigned long long>(deg);
         st_cnt += 1;
     }
     if constexpr (COMPACT) {
-        // round window + colors of every neighbour known to be final
-        if (lane >= kAccWords) fx = 0u;
+        // round window + colors of every neighbour known to be final (kept in the slot)
+        const unsigned fold = lane < kAccWords ? snap[kAccWords + lane] : 0u;
+        const unsigned fx = fold | (lane == 0 ? f0 : lane == 1 ? f1 : (lane < kAccWords ? wfin[lane] : 0u));
+        if (lane < kAccWords && fx != fold) a[kAccFin + lane] = fx;
         lo0 |= __shfl_sync(kFull, fx, 0);
         lo1 |= __shfl_sync(kFull, fx, 1);
         if (lane >= 2 && lane < kAccWords) win[lane] |= fx;
@@ -613,42 +896,32 @@ __device__ void det_chunk(const RoundParams &P, const uint64_t *colc, uint64_t *
     int32_t nc = cv;
     if (lose) {
         nc = first_free(lo0, lo1, win);
-        if (nc < 0) nc = mex_from<BATCH>(P, colc, r, win, lane, 32 * kAccWords);
+        if (nc < 0) nc = mex_from<BATCH>(P, colc, load_row<BATCH>(P, V), win, lane, 32 * kAccWords);
     }
     if (lane == 0) det_write(colc, coln, V, lose, cv, nc, pv);
     if (!lose) return;
+    if constexpr (BATCH) {
+        if (lane == 0) note_graph_round(P, __ldg(P.vg + V), pass + 1);
+    }
     if constexpr (COMPACT) {
-        // the list the next round sweeps: the fresh copy if this round wrote one, else the same list,
-        // and a rewrite next round once a quarter of the list has become final
+        // next round's list: the fresh copy if this round wrote one; a rewrite next round once a
+        // quarter of the list has become final
+        const bool rewrite = dst != nullptr;
         const unsigned nsrc = rewrite ? (src == 1 ? 2u : 1u) : src;
-        const unsigned nlen = rewrite ? newlen : len;
-        const unsigned nrw = 4ull * surv < 3ull * nlen ? 1u : 0u;
-        // items of CH entries; in a round with fewer items than warps, smaller items (down to 64
-        // entries) so that the next round's latency is not one long item, but never more items
-        // than the vertex had in round 1 (the work-item buffers are sized for that)
-        int64_t items64 = (static_cast<int64_t>(nlen) + P.CH - 1) / P.CH;
-        if (items_now < warps) {
-            int64_t chs = static_cast<int64_t>(P.CH) * items_now / warps;
-            chs = chs < 64 ? 64 : (chs + 31) & ~int64_t{31};
-            const int64_t cap = (deg + P.CH - 1) / P.CH;
-            int64_t want = (static_cast<int64_t>(nlen) + chs - 1) / chs;
-            if (want > cap) want = cap;
-            if (want > items64) items64 = want;
-        }
-        const int32_t items = items64 > 0 ? static_cast<int32_t>(items64) : 1;
-        unsigned cb = 0;
+        const unsigned nlen = rewrite ? __shfl_sync(kFull, written, 0) : len;
+        const unsigned surv = __shfl_sync(kFull, survivors, 0);
+        const bool nrw = 4ull * surv < 3ull * nlen;
+        const int32_t items = next_items(P, nlen, deg, items_now, warps);
         if (lane == 0) {
             a[kAccSrc] = nsrc;
             a[kAccLen] = nlen;
-            a[kAccRewrite] = nrw;
-            atomicAdd(cnt_next + kCntItems, 1u);
-            cb = atomicAdd(cnt_next + kCntChunks, static_cast<unsigned>(items));
-            if constexpr (BATCH) note_graph_round(P, r.g, pass + 1);
         }
-        cb = __shfl_sync(kFull, cb, 0);
-        for (int32_t q = lane; q < items; q += 32) chunk_next[cb + q] = make_int4(V, q, slot, items);
+        const int32_t *list = nsrc == 0 ? d.list : P.lists + off + (nsrc == 2 ? deg : 0);
+        const int64_t per = (static_cast<int64_t>(nlen) + items - 1) / items;
+        append_items(next, cnt_next, lane, lane == 0 ? items : 0, list, V, slot, nrw ? kItemRewrite : 0u, nlen,
+                     per > 0 ? per : 1, d.vbase, d.ng, d.deg);
     } else {
-        append_large<BATCH>(P, V, r, chunk_next, cnt_next, pass + 1, lane);
+        append_items(next, cnt_next, lane, lane == 0 ? 1 : 0, d.list, V, -1, 0u, deg, P.CH, d.vbase, d.ng, d.deg);
     }
 }
 
@@ -750,24 +1023,28 @@ __device__ __forceinline__ void flush_stats(const RoundParams &P, int pass, unsi
     }
 }
 
+// Deterministic rounds.  Phase A: the work items of larger vertices, then one thread per vertex of
+// degree <= T1.  Phase B (only in rounds where some vertex has several items, after a grid barrier):
+// those vertices are finished from their merged slots, one lane each.
 template <bool BATCH, bool COMPACT>
 __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(RoundParams P) {
     __shared__ unsigned s_win[kMaxWarps][kAccWords];
-    // per warp: the window of final neighbours found by the current item (compact sweep), then the
-    // item's snapshots of the slot's round window and of its final window
-    __shared__ unsigned s_fin[kMaxWarps][COMPACT ? 3 * kAccWords : kAccWords];
+    // per warp: the window of final neighbours found by the current item, then the item's snapshots
+    // of its slot's round window and final window
+    __shared__ unsigned s_aux[kMaxWarps][3 * kAccWords];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     unsigned *win = s_win[wib];
-    unsigned *wfin = s_fin[wib];
+    unsigned *wfin = s_aux[wib];
+    unsigned *snap = s_aux[wib] + kAccWords;
     if (P.stats && blockIdx.x == 0 && threadIdx.x == 0) P.stats[4 * P.stats_cap] = global_ns();
     int pass = P.pass_begin;
     for (;; ++pass) {
         unsigned *cc = P.cnt + kCnt * (pass % 3);
         unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
         const unsigned nsmall = __ldcg(cc + kCntSmall), nitems = __ldcg(cc + kCntItems);
-        const unsigned nchunks = __ldcg(cc + kCntChunks);
+        const unsigned nchunks = __ldcg(cc + kCntChunks), nmulti = __ldcg(cc + kCntMulti);
         if (nsmall + nitems == 0u) break;
         if (pass >= P.pass_end) {
             if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
@@ -780,20 +1057,20 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(
         uint64_t *coln = odd ? P.col1 : P.col0;
         const int32_t *smallc = odd ? P.small0 : P.small1;
         int32_t *smalln = odd ? P.small1 : P.small0;
-        const int4 *chunkc = odd ? P.chunk0 : P.chunk1;
-        int4 *chunkn = odd ? P.chunk1 : P.chunk0;
+        const DetItem *itc = reinterpret_cast<const DetItem *>(odd ? P.chunk0 : P.chunk1);
+        DetItem *itn = reinterpret_cast<DetItem *>(odd ? P.chunk1 : P.chunk0);
         unsigned long long st_deg = 0, st_cnt = 0, st_read = 0;
-        // work items of larger vertices first (they dominate), then one thread per small vertex
-        // (the next item's descriptor is read while the current one runs, one field in each of lanes 0..3)
+        // phase A: work items of larger vertices first (they dominate; the next item is read while
+        // the current one runs), then one thread per small vertex
+        // sparse rounds (at most kMergeNowItems items per warp) finish several-item vertices in phase A
+        const bool merge_now = nchunks <= kMergeNowItems * static_cast<unsigned>(nw);
         if (static_cast<unsigned>(gw) < nchunks) {
-            const int32_t *cf = reinterpret_cast<const int32_t *>(chunkc);
-            int4 it = __ldcg(chunkc + gw);
+            uint32_t w = item_word(itc, gw, lane);
             for (unsigned i = gw; i < nchunks; i += nw) {
-                const int32_t nx = lane < 4 && i + nw < nchunks ? __ldcg(cf + 4 * static_cast<size_t>(i + nw) + lane) : 0;
-                det_chunk<BATCH, COMPACT>(P, colc, coln, it, win, wfin, chunkn, cn, pass, lane, st_deg, st_cnt,
-                                          st_read, nchunks, static_cast<unsigned>(nw));
-                it = make_int4(__shfl_sync(kFull, nx, 0), __shfl_sync(kFull, nx, 1), __shfl_sync(kFull, nx, 2),
-                               __shfl_sync(kFull, nx, 3));
+                const DetItem d = item_of(w);
+                if (i + nw < nchunks) w = item_word(itc, i + nw, lane);
+                det_item<BATCH, COMPACT>(P, colc, coln, d, win, wfin, snap, itn, cn, pass, lane, nchunks,
+                                         static_cast<unsigned>(nw), merge_now, st_deg, st_cnt, st_read);
             }
         }
         for (unsigned base = static_cast<unsigned>(gw) * 32u; base < nsmall; base += static_cast<unsigned>(nw) * 32u) {
@@ -811,6 +1088,22 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(
                 }
             }
             warp_append(lose, V, smalln, cn + kCntSmall, lane);
+        }
+        // phase B
+        if (nmulti != 0u && !merge_now) {
+            if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
+            for (unsigned base = static_cast<unsigned>(gw) * 32u; base < nchunks;
+                 base += static_cast<unsigned>(nw) * 32u) {
+                const unsigned i = base + lane;
+                DetItem d{};
+                bool fin = false;
+                if (i < nchunks) {
+                    d = item_lane(itc + i);
+                    fin = (d.slotf & kItemMulti) != 0u && d.lb == 0;
+                }
+                det_finish<BATCH, COMPACT>(P, colc, coln, fin, d, win, itn, cn, pass, lane, nchunks,
+                                           static_cast<unsigned>(nw), st_deg, st_cnt);
+            }
         }
         if (P.stats) flush_stats(P, pass, st_deg, st_cnt, st_read);
         if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
@@ -907,12 +1200,50 @@ __global__ void batch_tables_kernel(RoundParams P, const int64_t *vtx_off, const
 // current small list) and larger vertices (collected in P.items, counted in P.tmp, expanded into
 // work items by expand_kernel).  Checks each row: 0 <= rowptr[v] <= rowptr[v+1] <= entries of its
 // graph, rowptr of a graph's first vertex = 0, of its last vertex's end = its entries.
+// Row of vertex V for set-up: its entry range, checked (0 <= rowptr[v] <= rowptr[v+1] <= entries of
+// its graph, 0 at a graph's first vertex, the graph's entry count at its end).  g: V's graph (batch).
+// Returns the degree, or -1 for a malformed row.
+template <bool BATCH>
+__device__ __forceinline__ int64_t checked_degree(const RoundParams &P, int32_t V, int32_t g, int64_t &b, int32_t &lv) {
+    int64_t e, lim;
+    int32_t ng;
+    if constexpr (!BATCH) {
+        b = P.rowptr[V];
+        e = P.rowptr[V + 1];
+        lim = P.nnz;
+        lv = V;
+        ng = P.n;
+    } else {
+        lv = V - static_cast<int32_t>(P.g_vbase[g]);
+        ng = P.g_n[g];
+        const int32_t *rp = P.rowptr + P.g_rbase[g];
+        b = rp[lv];
+        e = rp[lv + 1];
+        lim = P.g_m[g];
+    }
+    const bool ok = b >= 0 && b <= e && e <= lim && (lv != 0 || b == 0) && (lv != ng - 1 || e == lim);
+    return ok ? e - b : -1;
+}
+
+// Binning and initialisation of vertices [v_begin, v_end) for round P.pass_begin: priority cache,
+// initial colors, and the round's worklist split into thread-per-vertex entries and larger vertices
+// (collected in P.items, counted in P.tmp, expanded into work items by expand_kernel).  Checks each
+// row.  Thread-per-vertex entries are appended to the current small list, or, when P.deg_hist is
+// set, only counted per degree (P.deg_hist[d]) for sort_small_kernel and scatter_small_kernel,
+// which write the list in increasing order of degree (so that the 32 rows a warp sweeps side by
+// side have similar lengths).
 template <bool BATCH, int MODE>
 __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int32_t g_fixed) {
+    __shared__ unsigned s_hist[128];
     const int lane = threadIdx.x & 31;
     const int pass = P.pass_begin;
     unsigned *cc = P.cnt + kCnt * (pass % 3);
     int32_t *small_cur = (pass & 1) ? P.small0 : P.small1;
+    const bool sort = P.deg_hist != nullptr;
+    if (sort) {
+        for (int t = threadIdx.x; t < 128; t += blockDim.x) s_hist[t] = 0;
+        __syncthreads();
+    }
     const int64_t count = static_cast<int64_t>(v_end) - v_begin;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t base = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ll; base < count;
@@ -921,32 +1252,23 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
         const bool in = base + lane < count;
         int kind = 0;  // 1 = one thread, 2 = work items
         int32_t nch = 0;
-        int64_t deg_big = 0;
+        int64_t d = 0;
         if (in) {
-            int64_t b, e, lim;
-            int32_t lv, ng;
-            if constexpr (!BATCH) {
-                b = P.rowptr[V];
-                e = P.rowptr[V + 1];
-                lim = P.nnz;
-                lv = V;
-                ng = P.n;
-            } else {
-                int32_t g = g_fixed;
+            int32_t g = 0;
+            if constexpr (BATCH) {
+                g = g_fixed;
                 if (g >= 0)
                     P.vg[V] = g;
                 else
                     g = P.vg[V];
-                lv = V - static_cast<int32_t>(P.g_vbase[g]);
-                ng = P.g_n[g];
-                const int32_t *rp = P.rowptr + P.g_rbase[g];
-                b = rp[lv];
-                e = rp[lv + 1];
-                lim = P.g_m[g];
             }
-            const bool ok = b >= 0 && b <= e && e <= lim && (lv != 0 || b == 0) && (lv != ng - 1 || e == lim);
-            if (!ok) set_error(P.err, GC_ERR_INVALID_GRAPH, V, b);
-            const int64_t d = ok ? e - b : 0;
+            int64_t b;
+            int32_t lv;
+            d = checked_degree<BATCH>(P, V, g, b, lv);
+            if (d < 0) {
+                set_error(P.err, GC_ERR_INVALID_GRAPH, V, b);
+                d = 0;
+            }
             const uint32_t pv = static_cast<uint32_t>(vertex_hash(P.seed, static_cast<uint32_t>(lv)) >> 33);
             // an isolated vertex takes color 0 in round 1 and never changes: it is final from the start
             if (MODE == GC_MODE_DETERMINISTIC) {
@@ -959,13 +1281,16 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
             if (d > 0) {
                 kind = d <= P.T1 ? 1 : 2;
                 nch = static_cast<int32_t>((d + P.CH - 1) / P.CH);
-                deg_big = d;
             }
         }
         if constexpr (BATCH) {
             if (g_fixed >= 0 && kind != 0) note_graph_round(P, g_fixed, pass);
         }
-        warp_append(kind == 1, V, small_cur, cc + kCntSmall, lane);
+        if (sort) {
+            if (kind == 1) atomicAdd(&s_hist[d], 1u);
+        } else {
+            warp_append(kind == 1, V, small_cur, cc + kCntSmall, lane);
+        }
         const unsigned m = __ballot_sync(kFull, kind == 2);
         if (m) {
             const int leader = __ffs(m) - 1;
@@ -979,27 +1304,86 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
             if (kind == 2) P.items[ib + __popc(m & lanemask_lt())] = V;
             if (P.list_total) {
                 // compact mode: two list regions of deg entries per larger vertex
-                unsigned long long need = kind == 2 ? 2ull * static_cast<unsigned long long>(deg_big) : 0ull;
+                unsigned long long need = kind == 2 ? 2ull * static_cast<unsigned long long>(d) : 0ull;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) need += __shfl_xor_sync(kFull, need, o);
                 if (lane == leader) atomicAdd(P.list_total, need);
             }
         }
     }
+    if (sort) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < 128; t += blockDim.x)
+            if (s_hist[t]) atomicAdd(P.deg_hist + t, s_hist[t]);
+    }
+}
+
+// One block of 128 threads: turns the degree counts into list positions (P.deg_hist[128 + d] =
+// first position of degree d, after the entries already on the current small list) and adds them
+// to the list's count.
+__global__ void sort_small_kernel(RoundParams P) {
+    __shared__ unsigned s[128];
+    const int t = threadIdx.x;
+    unsigned *cc = P.cnt + kCnt * (P.pass_begin % 3);
+    const unsigned h = P.deg_hist[t];
+    s[t] = h;
+    __syncthreads();
+    for (int o = 1; o < 128; o <<= 1) {
+        const unsigned x = t >= o ? s[t - o] : 0u;
+        __syncthreads();
+        s[t] += x;
+        __syncthreads();
+    }
+    const unsigned base = cc[kCntSmall];
+    P.deg_hist[128 + t] = base + s[t] - h;
+    __syncthreads();
+    if (t == 127) cc[kCntSmall] = base + s[127];
+}
+
+// Writes the thread-per-vertex entries of [v_begin, v_end) at the positions sort_small_kernel
+// assigned (the same classification as setup_kernel; the order within one degree is arbitrary).
+template <bool BATCH>
+__global__ void scatter_small_kernel(RoundParams P, int32_t v_begin, int32_t v_end) {
+    __shared__ unsigned s_cnt[128], s_base[128];
+    int32_t *small_cur = (P.pass_begin & 1) ? P.small0 : P.small1;
+    const int64_t count = static_cast<int64_t>(v_end) - v_begin;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < count;
+         base += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        for (int t = threadIdx.x; t < 128; t += blockDim.x) s_cnt[t] = 0;
+        __syncthreads();
+        const int32_t V = static_cast<int32_t>(v_begin + base + threadIdx.x);
+        int64_t d = 0;
+        if (base + threadIdx.x < count) {
+            const int32_t g = BATCH ? P.vg[V] : 0;
+            int64_t b;
+            int32_t lv;
+            d = checked_degree<BATCH>(P, V, g, b, lv);
+        }
+        const bool small = d > 0 && d <= P.T1;
+        unsigned rank = 0;
+        if (small) rank = atomicAdd(&s_cnt[d], 1u);
+        __syncthreads();
+        for (int t = threadIdx.x; t < 128; t += blockDim.x)
+            if (s_cnt[t]) s_base[t] = atomicAdd(P.deg_hist + 128 + t, s_cnt[t]);
+        __syncthreads();
+        if (small) small_cur[s_base[d] + rank] = V;
+        __syncthreads();
+    }
 }
 
 // Expands the larger vertices collected by setup into work items of round P.pass_begin, with
 // accumulator slots after those already taken in that round.  One warp per vertex.  COMPACT: the
-// vertex keeps its slot for the whole run; the slot is cleared and records the id of the vertex's
-// first work item (the items of round 1 are numbered consecutively per vertex).
-template <bool BATCH, bool COMPACT>
+// vertex keeps its slot for the whole run; the slot records where its list is, the list's length,
+// the vertex's space in the list pool and its degree.  Deterministic items are DetItem (a vertex's
+// items split its row evenly with COMPACT, else into CH-entry pieces); in-place items are int4
+// {vertex, item index, slot, items}.
+template <bool BATCH, bool COMPACT, int MODE>
 __global__ void expand_kernel(RoundParams P, int32_t n_items) {
     if (n_items < 0) n_items = static_cast<int32_t>(__ldcg(P.tmp));  // count left on the device by setup
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int pass = P.pass_begin;
     unsigned *cc = P.cnt + kCnt * (pass % 3);
-    int4 *chunk_cur = (pass & 1) ? P.chunk0 : P.chunk1;
     for (int32_t s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n_items; s += nw) {
         const int32_t V = P.items[s];
         const Row r = load_row<BATCH>(P, V);
@@ -1009,6 +1393,7 @@ __global__ void expand_kernel(RoundParams P, int32_t n_items) {
         if (lane == 0) {
             slot = atomicAdd(cc + kCntItems, 1u);
             cb = atomicAdd(cc + kCntChunks, static_cast<unsigned>(nch));
+            if (MODE == GC_MODE_DETERMINISTIC && nch > 1) atomicAdd(cc + kCntMulti, 1u);
         }
         slot = __shfl_sync(kFull, slot, 0);
         cb = __shfl_sync(kFull, cb, 0);
@@ -1023,9 +1408,21 @@ __global__ void expand_kernel(RoundParams P, int32_t n_items) {
             if (lane == kAccLen - 32) hi = static_cast<unsigned>(deg);
             if (lane == kAccOffLo - 32) hi = static_cast<unsigned>(off);
             if (lane == kAccOffHi - 32) hi = static_cast<unsigned>(off >> 32);
+            if (lane == kAccDeg - 32) hi = static_cast<unsigned>(deg);
         }
         a[32 + lane] = hi;
-        for (int32_t q = lane; q < nch; q += 32) chunk_cur[cb + q] = make_int4(V, q, static_cast<int32_t>(slot), nch);
+        if constexpr (MODE == GC_MODE_DETERMINISTIC) {
+            DetItem *cur = reinterpret_cast<DetItem *>((pass & 1) ? P.chunk0 : P.chunk1);
+            const int32_t per = COMPACT ? (deg + nch - 1) / nch : P.CH;
+            const uint32_t slotf = slot | (nch > 1 ? kItemMulti : 0u);
+            for (int32_t q = lane; q < nch; q += 32) {
+                const int32_t lb = q * per;
+                store_item(cur + cb + q, P.colidx + r.b, V, slotf, lb, min(deg, lb + per), r.vbase, r.ng, nch, deg);
+            }
+        } else {
+            int4 *cur = (pass & 1) ? P.chunk0 : P.chunk1;
+            for (int32_t q = lane; q < nch; q += 32) cur[cb + q] = make_int4(V, q, static_cast<int32_t>(slot), nch);
+        }
     }
 }
 
@@ -1166,19 +1563,40 @@ cudaError_t launch_setup(const RoundParams &P, int mode, bool batch, int32_t v_b
     return cudaGetLastError();
 }
 
-cudaError_t launch_expand(const RoundParams &P, bool batch, bool compact, int32_t n_items, cudaStream_t s) {
+cudaError_t launch_sort_small(const RoundParams &P, bool batch, int32_t v_begin, int32_t v_end, cudaStream_t s) {
+    if (v_end <= v_begin || !P.deg_hist) return cudaSuccess;
+    sort_small_kernel<<<1, 128, 0, s>>>(P);
+    const int grid = grid_for(static_cast<int64_t>(v_end) - v_begin, 256, sm_count() * 16);
+    if (batch)
+        scatter_small_kernel<true><<<grid, 256, 0, s>>>(P, v_begin, v_end);
+    else
+        scatter_small_kernel<false><<<grid, 256, 0, s>>>(P, v_begin, v_end);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const RoundParams &P, int mode, bool batch, bool compact, int32_t n_items,
+                          cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
+    if (compact && mode != GC_MODE_DETERMINISTIC) return cudaErrorInvalidValue;
     const int grid = n_items < 0 ? sm_count() * 8 : grid_for(static_cast<int64_t>(n_items) * 32, 256, sm_count() * 16);
-    if (batch) {
-        if (compact)
-            expand_kernel<true, true><<<grid, 256, 0, s>>>(P, n_items);
-        else
-            expand_kernel<true, false><<<grid, 256, 0, s>>>(P, n_items);
+    constexpr int D = GC_MODE_DETERMINISTIC, I = GC_MODE_INPLACE;
+    if (mode == GC_MODE_DETERMINISTIC) {
+        if (batch) {
+            if (compact)
+                expand_kernel<true, true, D><<<grid, 256, 0, s>>>(P, n_items);
+            else
+                expand_kernel<true, false, D><<<grid, 256, 0, s>>>(P, n_items);
+        } else {
+            if (compact)
+                expand_kernel<false, true, D><<<grid, 256, 0, s>>>(P, n_items);
+            else
+                expand_kernel<false, false, D><<<grid, 256, 0, s>>>(P, n_items);
+        }
     } else {
-        if (compact)
-            expand_kernel<false, true><<<grid, 256, 0, s>>>(P, n_items);
+        if (batch)
+            expand_kernel<true, false, I><<<grid, 256, 0, s>>>(P, n_items);
         else
-            expand_kernel<false, false><<<grid, 256, 0, s>>>(P, n_items);
+            expand_kernel<false, false, I><<<grid, 256, 0, s>>>(P, n_items);
     }
     return cudaGetLastError();
 }

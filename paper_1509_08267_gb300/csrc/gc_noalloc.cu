@@ -47,11 +47,11 @@ constexpr size_t kOffSmall0 = align256(kOffCol1 + 8 * size_t{kNaMaxVertices});
 constexpr size_t kOffSmall1 = align256(kOffSmall0 + 4 * size_t{kNaMaxVertices});
 constexpr size_t kOffItems = align256(kOffSmall1 + 4 * size_t{kNaMaxVertices});
 constexpr size_t kOffChunk0 = align256(kOffItems + 4 * size_t{kNaMaxVertices});
-constexpr size_t kOffChunk1 = align256(kOffChunk0 + 16 * size_t{kNaMaxItems});
-constexpr size_t kOffAcc = align256(kOffChunk1 + 16 * size_t{kNaMaxItems});
+constexpr size_t kOffChunk1 = align256(kOffChunk0 + kItemBytes * size_t{kNaMaxItems});
+constexpr size_t kOffAcc = align256(kOffChunk1 + kItemBytes * size_t{kNaMaxItems});
 constexpr size_t kOffBitmap = align256(kOffAcc + 4 * size_t{kAccStride} * size_t{kNaMaxVertices});
 constexpr size_t kBitmapWords = kNaMaxVertices / 32 + 2;
-constexpr size_t kScratchBytes = align256(kOffBitmap + 4 * kBitmapWords);  // about 5.2 MB
+constexpr size_t kScratchBytes = align256(kOffBitmap + 4 * kBitmapWords);  // about 5.8 MB
 
 // The scratch itself.  Host code must not use the name as an address: it looks up the device
 // address with cudaGetSymbolAddress (once per device) and hands that to the kernels.
@@ -175,7 +175,7 @@ extern "C" int gc_color_noalloc(int32_t n, const int32_t *rowptr, const int32_t 
     const unsigned n_small = h.cnt[kCnt * 1 + kCntSmall], n_items = h.tmp[0], n_chunks = h.tmp[1];
     if (n_items > static_cast<unsigned>(kNaMaxVertices) || n_chunks > static_cast<unsigned>(kNaMaxItems))
         return set_last_error(GC_ERR_INVALID_GRAPH, "work-item count outside the scratch bounds");
-    e = launch_expand(P, false, false, static_cast<int32_t>(n_items), s);
+    e = launch_expand(P, GC_MODE_DETERMINISTIC, false, false, static_cast<int32_t>(n_items), s);
     if (e != cudaSuccess) return na_fail(GC_ERR_CUDA, "expand", e);
 
     int per_sm = 0, sms = 0;

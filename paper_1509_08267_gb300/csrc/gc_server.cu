@@ -306,7 +306,7 @@ int admit(gc_server *s, const std::vector<Request *> &adm, std::vector<Request *
     for (Request *r : ok)
         SRV_CUDA(launch_setup(P, s->cfg.mode, true, static_cast<int32_t>(r->vbase),
                               static_cast<int32_t>(r->vbase + r->n), r->slot, st));
-    SRV_CUDA(launch_expand(P, true, false, -1, st));
+    SRV_CUDA(launch_expand(P, s->cfg.mode, true, false, -1, st));
     return GC_OK;
 }
 
@@ -499,7 +499,7 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
     } plan[] = {
         {&s->rowptr, 4 * (V + Sz)}, {&s->colidx, 4 * static_cast<size_t>(s->PE)}, {&s->col0, 8 * V}, {&s->col1, 8 * V},
         {&s->outbuf, 4 * V}, {&s->small0, 4 * V}, {&s->small1, 4 * V}, {&s->items, 4 * V}, {&s->vg, 4 * V},
-        {&s->chunk0, 16 * static_cast<size_t>(s->PC)}, {&s->chunk1, 16 * static_cast<size_t>(s->PC)},
+        {&s->chunk0, gc::kItemBytes * static_cast<size_t>(s->PC)}, {&s->chunk1, gc::kItemBytes * static_cast<size_t>(s->PC)},
         {&s->acc, 4 * gc::kAccStride * static_cast<size_t>(s->PI)}, {&s->ctl, sizeof(gc::Ctl)},
         {&s->bitmap, 4 * (V / 32 + 4)}, {&s->g_vbase, 8 * Sz}, {&s->g_n, 4 * Sz}, {&s->g_ebase, 8 * Sz},
         {&s->g_rbase, 8 * Sz}, {&s->g_m, 8 * Sz}, {&s->glast, 4 * Sz}, {&s->gmax, 4 * Sz}, {&s->gcount, 4 * Sz},

@@ -704,7 +704,7 @@ template <bool BATCH, bool COMPACT>
 __device__ __forceinline__ void det_finish(const RoundParams &P, const uint64_t *colc, uint64_t *coln, bool fin,
                                            const DetItem &d, unsigned *win, DetItem *next, unsigned *cnt_next,
                                            int pass, int lane, unsigned items_now, unsigned warps,
-                                           unsigned long long &st_deg, unsigned long long &st_cnt) {
+                                           unsigned &st_deg, unsigned &st_cnt) {
     const int32_t V = d.V;
     const uint32_t slot = d.slotf & kItemSlot;
     const int64_t deg = d.deg;
@@ -752,7 +752,7 @@ __device__ __forceinline__ void det_finish(const RoundParams &P, const uint64_t 
     }
     if (fin) {
         det_write(colc, coln, V, lose, cv, nc, pv);
-        st_deg += static_cast<unsigned long long>(deg);
+        st_deg += static_cast<unsigned>(deg);
         st_cnt += 1;
         const uint4 z = make_uint4(0, 0, 0, 0);
 #pragma unroll
@@ -797,8 +797,8 @@ __device__ __forceinline__ void det_finish(const RoundParams &P, const uint64_t 
 template <bool BATCH, bool COMPACT>
 __device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *coln, const DetItem &d,
                          unsigned *win, unsigned *wfin, unsigned *snap, DetItem *next, unsigned *cnt_next, int pass,
-                         int lane, unsigned items_now, unsigned warps, bool merge_now, unsigned long long &st_deg,
-                         unsigned long long &st_cnt, unsigned long long &st_read) {
+                         int lane, unsigned items_now, unsigned warps, bool merge_now, unsigned &st_deg,
+                         unsigned &st_cnt, unsigned &st_read) {
     const int32_t V = d.V;
     const uint32_t slot = d.slotf & kItemSlot;
     const bool multi = (d.slotf & kItemMulti) != 0;
@@ -847,7 +847,7 @@ __device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *c
     unsigned survivors = 0, written = 0;
     sweep_item<COMPACT>(P, r, colc, d.list, d.lb, d.le, ul, dst, a + kAccNewLen, multi, lane, cv, pv, lo, win, flo,
                         wfin, lose, survivors, written);
-    if (lane == 0) st_read += static_cast<unsigned long long>(d.le - d.lb);
+    if (lane == 0) st_read += static_cast<unsigned>(d.le - d.lb);
     lose = __any_sync(kFull, lose);
     unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
     unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
@@ -880,7 +880,7 @@ __device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *c
     }
     // the vertex's only item: its result now
     if (lane == 0) {
-        st_deg += static_cast<unsigned long long>(deg);
+        st_deg += static_cast<unsigned>(deg);
         st_cnt += 1;
     }
     if constexpr (COMPACT) {
@@ -976,15 +976,15 @@ __device__ void ip_chunk_assign(const RoundParams &P, uint64_t *col, int4 it, un
 // Phase 2 work item of a larger vertex.
 template <bool BATCH>
 __device__ void ip_chunk_conflict(const RoundParams &P, const uint64_t *col, int4 it, unsigned *win, int4 *chunk_next,
-                                  unsigned *cnt_next, int pass, int lane, unsigned long long &st_deg,
-                                  unsigned long long &st_cnt) {
+                                  unsigned *cnt_next, int pass, int lane, unsigned &st_deg,
+                                  unsigned &st_cnt) {
     const int32_t V = it.x, k = it.y, slot = it.z, nch = it.w;
     const Row r = load_row<BATCH>(P, V);
     const uint64_t self = load_state(col + V);
     const int64_t jb = r.b + static_cast<int64_t>(k) * P.CH;
     const int64_t je = min(r.e, jb + P.CH);
     if (k == 0 && lane == 0) {
-        st_deg += static_cast<unsigned long long>(r.e - r.b);
+        st_deg += static_cast<unsigned>(r.e - r.b);
         st_cnt += 1;
     }
     uint64_t lo = 0;
@@ -1059,7 +1059,7 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(
         int32_t *smalln = odd ? P.small1 : P.small0;
         const DetItem *itc = reinterpret_cast<const DetItem *>(odd ? P.chunk0 : P.chunk1);
         DetItem *itn = reinterpret_cast<DetItem *>(odd ? P.chunk1 : P.chunk0);
-        unsigned long long st_deg = 0, st_cnt = 0, st_read = 0;
+        unsigned st_deg = 0, st_cnt = 0, st_read = 0;  // this warp's share of the round (< 2^31 each)
         // phase A: work items of larger vertices first (they dominate; the next item is read while
         // the current one runs), then one thread per small vertex
         // sparse rounds (at most kMergeNowItems items per warp) finish several-item vertices in phase A
@@ -1080,8 +1080,8 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(
             if (i < nsmall) {
                 V = __ldcg(smallc + i);
                 lose = det_small<BATCH>(P, colc, coln, V, deg);
-                st_deg += static_cast<unsigned long long>(deg);
-                st_read += static_cast<unsigned long long>(deg);
+                st_deg += static_cast<unsigned>(deg);
+                st_read += static_cast<unsigned>(deg);
                 st_cnt += 1;
                 if constexpr (BATCH) {
                     if (lose) note_graph_round(P, __ldg(P.vg + V), pass + 1);
@@ -1146,7 +1146,7 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) ip_round_kernel(R
         for (unsigned i = gw * 32u + lane; i < nsmall; i += nw * 32u) ip_small_assign<BATCH>(P, col, __ldcg(smallc + i));
         if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
         // phase 2: conflict detection
-        unsigned long long st_deg = 0, st_cnt = 0;
+        unsigned st_deg = 0, st_cnt = 0;  // this warp's share of the round (< 2^31 each)
         for (unsigned i = gw; i < nchunks; i += nw)
             ip_chunk_conflict<BATCH>(P, col, __ldcg(chunkc + i), win, chunkn, cn, pass, lane, st_deg, st_cnt);
         for (unsigned base = gw * 32u; base < nsmall; base += nw * 32u) {
@@ -1156,7 +1156,7 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) ip_round_kernel(R
             if (i < nsmall) {
                 V = __ldcg(smallc + i);
                 lose = ip_small_conflict<BATCH>(P, col, V, deg);
-                st_deg += static_cast<unsigned long long>(deg);
+                st_deg += static_cast<unsigned>(deg);
                 st_cnt += 1;
                 if constexpr (BATCH) {
                     if (lose) note_graph_round(P, __ldg(P.vg + V), pass + 1);
@@ -1164,7 +1164,7 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) ip_round_kernel(R
             }
             warp_append(lose, V, smalln, cn + kCntSmall, lane);
         }
-        if (P.stats) flush_stats(P, pass, st_deg, st_cnt, 2 * st_deg);
+        if (P.stats) flush_stats(P, pass, st_deg, st_cnt, 2ull * st_deg);
         if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -100,9 +100,13 @@ class ClockSampler:
 
 
 def kernel_source_sha256():
+    """Digest of the round kernel's sources (the kernels and the layout constants they use)."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_1509_08267_gb300", "csrc", "gc_kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    for name in ("gc_kernels.cu", "gc_internal.h"):
+        with open(os.path.join(ROOT, "paper_1509_08267_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def recorded_traffic(workload, mode):

@@ -54,10 +54,11 @@ constexpr int kCntSmall = 0, kCntItems = 1, kCntChunks = 2, kCntMulti = 3;
 // Bytes per work item in the work-item buffers (deterministic items are 48 bytes, in-place 16).
 constexpr size_t kItemBytes = 48;
 
-struct GridBar {
+// Grid barrier of the persistent round kernels: arrivals so far in the current launch (launch_rounds
+// zeroes it before every launch).
+struct alignas(128) GridBar {
     unsigned count;
-    unsigned gen;
-    unsigned pad[30];
+    unsigned pad[31];
 };
 
 // Everything the setup, round and count kernels need.  A single graph uses plain CSR addressing;

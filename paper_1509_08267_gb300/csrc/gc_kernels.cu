@@ -83,43 +83,46 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
 
-// All blocks of the (co-resident, cooperative) grid meet here.  A wait gives up after spin_ns
-// nanoseconds (status GC_ERR_TIMEOUT) or as soon as any block has posted an error; the caller
-// then leaves the kernel.  Returns true when the grid may continue.
-__device__ bool grid_sync(GridBar *bar, int32_t *err, int64_t spin_ns) {
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// All blocks of the (co-resident, cooperative) grid meet here.  bar->count is zero when a launch
+// starts and only grows: every block adds 1 (release) and waits (acquire) until the count reaches
+// `target` += gridDim.x, so the last block to arrive has nothing more to do.  A wait gives up after
+// spin_ns nanoseconds (status GC_ERR_TIMEOUT) or when it sees that a block has posted an error
+// (read every 16 polls); the caller then leaves the kernel.  Returns true when the grid may
+// continue.
+__device__ bool grid_sync(GridBar *bar, unsigned &target, int32_t *err, int64_t spin_ns) {
     __shared__ int s_ok;
     __syncthreads();
+    target += gridDim.x;
     if (threadIdx.x == 0) {
-        const unsigned gen = ld_acquire(&bar->gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            st_release(&bar->gen, gen + 1u);
-        } else {
+        int ok = 1;
+        red_add_release(&bar->count, 1u);
+        if (static_cast<int>(ld_acquire(&bar->count) - target) < 0) {
             const uint64_t t0 = global_ns();
-            while (ld_acquire(&bar->gen) == gen) {
-                if (*reinterpret_cast<volatile int32_t *>(err) != 0) break;
-                if (static_cast<int64_t>(global_ns() - t0) > spin_ns) {
-                    set_error(err, GC_ERR_TIMEOUT, static_cast<int32_t>(blockIdx.x), 0);
+            for (unsigned k = 1;; ++k) {
+                __nanosleep(32);
+                if (static_cast<int>(ld_acquire(&bar->count) - target) >= 0) break;
+                if ((k & 15u) == 0u && *reinterpret_cast<volatile int32_t *>(err) != 0) {
+                    ok = 0;
                     break;
                 }
-                __nanosleep(100);
+                if (static_cast<int64_t>(global_ns() - t0) > spin_ns) {
+                    set_error(err, GC_ERR_TIMEOUT, static_cast<int32_t>(blockIdx.x), 0);
+                    ok = 0;
+                    break;
+                }
             }
         }
-        __threadfence();
-        s_ok = (*reinterpret_cast<volatile int32_t *>(err) == 0);
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
@@ -1039,12 +1042,14 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(
     unsigned *wfin = s_aux[wib];
     unsigned *snap = s_aux[wib] + kAccWords;
     if (P.stats && blockIdx.x == 0 && threadIdx.x == 0) P.stats[4 * P.stats_cap] = global_ns();
+    unsigned bar_target = 0;
     int pass = P.pass_begin;
     for (;; ++pass) {
         unsigned *cc = P.cnt + kCnt * (pass % 3);
         unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
         const unsigned nsmall = __ldcg(cc + kCntSmall), nitems = __ldcg(cc + kCntItems);
         const unsigned nchunks = __ldcg(cc + kCntChunks), nmulti = __ldcg(cc + kCntMulti);
+        if (__ldcg(P.err) != 0) break;  // posted by any block in an earlier round
         if (nsmall + nitems == 0u) break;
         if (pass >= P.pass_end) {
             if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
@@ -1091,7 +1096,7 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(
         }
         // phase B
         if (nmulti != 0u && !merge_now) {
-            if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
+            if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
             for (unsigned base = static_cast<unsigned>(gw) * 32u; base < nchunks;
                  base += static_cast<unsigned>(nw) * 32u) {
                 const unsigned i = base + lane;
@@ -1106,7 +1111,7 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(
             }
         }
         if (P.stats) flush_stats(P, pass, st_deg, st_cnt, st_read);
-        if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
+        if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.passes[0] = pass;
@@ -1123,12 +1128,14 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) ip_round_kernel(R
     unsigned *win = s_win[wib];
     uint64_t *col = P.col0;
     if (P.stats && blockIdx.x == 0 && threadIdx.x == 0) P.stats[4 * P.stats_cap] = global_ns();
+    unsigned bar_target = 0;
     int pass = P.pass_begin;
     for (;; ++pass) {
         unsigned *cc = P.cnt + kCnt * (pass % 3);
         unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
         const unsigned nsmall = __ldcg(cc + kCntSmall), nitems = __ldcg(cc + kCntItems);
         const unsigned nchunks = __ldcg(cc + kCntChunks);
+        if (__ldcg(P.err) != 0) break;  // posted by any block in an earlier round
         if (nsmall + nitems == 0u) break;
         if (pass >= P.pass_end) {
             if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
@@ -1144,7 +1151,7 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) ip_round_kernel(R
         // phase 1: tentative First Fit on live colors
         for (unsigned i = gw; i < nchunks; i += nw) ip_chunk_assign<BATCH>(P, col, __ldcg(chunkc + i), win, lane);
         for (unsigned i = gw * 32u + lane; i < nsmall; i += nw * 32u) ip_small_assign<BATCH>(P, col, __ldcg(smallc + i));
-        if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
+        if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
         // phase 2: conflict detection
         unsigned st_deg = 0, st_cnt = 0;  // this warp's share of the round (< 2^31 each)
         for (unsigned i = gw; i < nchunks; i += nw)
@@ -1165,7 +1172,7 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) ip_round_kernel(R
             warp_append(lose, V, smalln, cn + kCntSmall, lane);
         }
         if (P.stats) flush_stats(P, pass, st_deg, st_cnt, 2ull * st_deg);
-        if (!grid_sync(P.bar, P.err, P.spin_ns)) break;
+        if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.passes[0] = pass;
@@ -1622,6 +1629,9 @@ cudaError_t round_kernel_occupancy(int mode, bool batch, bool compact, int block
 cudaError_t launch_rounds(const RoundParams &P, int mode, bool batch, bool compact, int grid, int block,
                           cudaStream_t s) {
     if (block != kBlock) return cudaErrorInvalidValue;
+    // the grid barrier counts this launch's arrivals from zero
+    cudaError_t e = cudaMemsetAsync(&P.bar->count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
     RoundParams arg = P;
     void *args[] = {&arg};
     return cudaLaunchCooperativeKernel(round_kernel_fn(mode, batch, compact), dim3(grid), dim3(block), args, 0, s);

@@ -123,6 +123,24 @@ def recorded_traffic(workload, mode):
     return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
 
 
+def reduce_max(value, world, device=None):
+    """The largest of the ranks' values (timing is taken as the slowest rank's); the value itself on
+    one rank.  device: where the reduction tensor lives (the rank's GPU under NCCL, CPU under gloo)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, seconds_max, world):
+    """Whole-job throughput of `world` replicas that each processed units_per_rank units, timed by
+    the slowest rank."""
+    return world * units_per_rank / seconds_max
+
+
 def cpu_cores_used():
     return 1  # the oracle is single-threaded
 
@@ -209,7 +227,7 @@ def run_batch(args, rank, world):
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t_batch = sum(a.elapsed_time(c) for a, c in ev) / 1e3 / args.steps
+    t_batch = reduce_max(sum(a.elapsed_time(c) for a, c in ev) / 1e3 / args.steps, world, dev)
     # one by one: the same device-resident graphs, one gc_color call each (each call synchronises)
     solo = torch.empty(N, dtype=torch.int32, device=dev)
     vo_h, eo_h = b.vtx_off, b.edge_off
@@ -227,7 +245,7 @@ def run_batch(args, rank, world):
     m_und = NNZ / 2
     if rank == 0:
         line = {
-            "metric": METRIC, "value": world * m_und / t_batch / 1e9, "unit": "Gedges/s", "n_gpus": world,
+            "metric": METRIC, "value": whole_job_rate(m_und, t_batch, world) / 1e9, "unit": "Gedges/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": args.workload, "graphs": G, "vertices": N, "nnz": NNZ,
@@ -239,7 +257,8 @@ def run_batch(args, rank, world):
             "identical_colorings": same,
             "batch_rounds": int(st.rounds), "batch_kernel_ms": st.kernel_ms,
             "tuned_options": {k: v for k, v in tuned.__dict__.items() if v},
-            "gpu_launches": 6 * args.steps, "clocks": clk,
+            # batch tables, setup, degree sort (2), expand, round kernel, color count (2) per call
+            "gpu_launches": 8 * args.steps, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
 
@@ -308,10 +327,14 @@ def run_serve(args, rank, world):
             same &= bool(np.array_equal(r.colors, results[i][0])) and r.ncolors == results[i][1] and \
                 r.rounds == results[i][2]
     t_solo = time.perf_counter() - t1
+    dev = torch.device("cuda", local)
+    t_serve = reduce_max(t_serve, world, dev)
+    t_solo = reduce_max(t_solo, world, dev)
     m_und = sum(g.nnz for g in graphs) / 2
     if rank == 0:
         line = {
-            "metric": METRIC, "value": m_und / t_serve / 1e9, "unit": "Gedges/s", "n_gpus": 1, "steps": count,
+            "metric": METRIC, "value": whole_job_rate(m_und, t_serve, world) / 1e9, "unit": "Gedges/s",
+            "n_gpus": world, "steps": count,
             "warmup": 0, "ms_per_step": t_serve * 1e3 / count, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "serve", "requests": count, "arrival": "Poisson, mean 2,000 req/s, seed 4",
@@ -403,15 +426,9 @@ def main():
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_local = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
+    t_max = reduce_max(sum(step_ms) / 1e3, world, dev)
     m_und = g.nnz / 2
-    value = world * args.steps * m_und / t_max / 1e9
+    value = whole_job_rate(args.steps * m_und, t_max, world) / 1e9
     ms_per_step = t_max / args.steps * 1e3
 
     # roofline of the dominant kernel (the persistent round kernel): algorithmic bytes per launch
@@ -439,8 +456,8 @@ def main():
             t0 = time.perf_counter()
             gc.color(rp_h.numpy(), ci_h.numpy(), mode, HASH_SEED, out=out_h.numpy())
             te.append(time.perf_counter() - t0)
-        e_t = statistics.median(te)
-        e2e = {"value": world * m_und / e_t / 1e9, "unit": "Gedges/s",
+        e_t = reduce_max(statistics.median(te), world, dev)
+        e2e = {"value": whole_job_rate(m_und, e_t, world) / 1e9, "unit": "Gedges/s",
                "h2d_bytes_per_step": int(4 * (g.n + 1) + 4 * g.nnz), "d2h_bytes_per_step": int(4 * g.n + 8),
                "ms_per_step": e_t * 1e3}
 
@@ -472,7 +489,8 @@ def main():
                          "kernel": "round kernel (persistent)", "kernel_ms": kms, "alg_bytes": alg_bytes},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 5 * args.steps,
+            # setup, degree sort (2), expand, round kernel, color count (2) per coloring
+            "gpu_launches": 7 * args.steps,
             "clocks": clk,
             "rounds": r0.rounds, "ncolors": r0.ncolors, "greedy_ncolors": greedy_colors,
             "max_degree": g.max_degree, "wall_s_timed": t_wall,

@@ -45,6 +45,12 @@
  *   GC_MODE_INPLACE  Phase 1 reads neighbour colors live, as the paper's threads do; the result
  *       depends on scheduling.  It is always a proper coloring with color(v) <= deg(v), and the
  *       number of rounds never exceeds n.
+ *   GC_MODE_PARTITION  Algorithm 1 as printed: the vertices are split into p blocks of consecutive
+ *       ids (block i = [floor(i n / p), floor((i+1) n / p)), gc_options.partitions); in phase 1 each
+ *       block colors its worklist vertices one after another in id order, seeing its own block's
+ *       colors live and other blocks' colors as the round began; in phase 2 a vertex is re-queued
+ *       when a neighbour in a higher block has its color.  The result is a function of the graph
+ *       and p (seed unused); Lemma 2 bounds the rounds by p + 1.  gc_color / gc_color_ex only.
  */
 #ifndef GC_H
 #define GC_H
@@ -67,7 +73,7 @@ typedef enum {
     GC_ERR_BUSY = -7             /* server request still running (gc_server_poll) */
 } gc_status;
 
-enum { GC_MODE_DETERMINISTIC = 0, GC_MODE_INPLACE = 1 };
+enum { GC_MODE_DETERMINISTIC = 0, GC_MODE_INPLACE = 1, GC_MODE_PARTITION = 2 };
 
 /* Flags for gc_options.flags */
 #define GC_FLAG_STATS 1u     /* fill gc_stats' per-round worklist sizes and scanned entries */
@@ -88,12 +94,14 @@ typedef struct gc_options {
     int32_t small_max_degree;  /* vertices up to this degree get one thread each (1..127); default 127 */
     int32_t chunk;             /* adjacency entries per warp work item for larger vertices (32..1024, multiple of 32);
                                   default 512 (deterministic), 1024 (in-place) */
-    int32_t block_size;        /* threads per block of the round kernel (128, 256 or 512); default 256 */
+    int32_t block_size;        /* threads per block of the round kernel (256 is the only size); default 256 */
     int32_t blocks_per_sm;     /* resident blocks per SM for the round kernel; 0 = occupancy maximum */
     int64_t spin_limit_ns;     /* grid-barrier wait limit in ns; 0 = 1e9.  A wait that runs out makes
                                   the call return GC_ERR_TIMEOUT with the device still usable */
     uint32_t flags;            /* GC_FLAG_* */
-    int32_t reserved[8];
+    int32_t partitions;        /* GC_MODE_PARTITION: number of blocks p (clamped to 1..n); 0 = one per
+                                  resident warp of the round kernel */
+    int32_t reserved[7];
 } gc_options;
 
 /* Optional run statistics (gc_color_ex / gc_color_batch_ex).  The caller may provide arrays
@@ -122,7 +130,7 @@ typedef struct gc_stats {
  *   n          number of vertices (>= 0)
  *   rowptr     int32[n+1]   CSR row offsets (device or host)
  *   colidx     int32[nnz]   CSR neighbour ids (device or host); may be NULL when nnz = 0
- *   mode       GC_MODE_DETERMINISTIC or GC_MODE_INPLACE
+ *   mode       GC_MODE_DETERMINISTIC, GC_MODE_INPLACE or GC_MODE_PARTITION
  *   seed       priority-hash seed (deterministic mode; in-place mode uses it for tie-breaks too)
  *   colors_out int32[n]     receives the colors (device or host)
  *   ncolors    host int32*  receives the number of distinct colors (may be NULL)

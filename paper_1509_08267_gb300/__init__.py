@@ -18,7 +18,7 @@ import numpy as np
 
 __all__ = [
     "GCError", "load", "color", "color_batch", "validate", "Options", "Stats", "Server", "MODE_DETERMINISTIC",
-    "MODE_INPLACE", "version", "release_scratch",
+    "MODE_INPLACE", "MODE_PARTITION", "version", "release_scratch",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -37,6 +37,7 @@ STATUS_NAMES = {0: "GC_OK", -1: "GC_ERR_INVALID_ARG", -2: "GC_ERR_INVALID_GRAPH"
 
 MODE_DETERMINISTIC = 0
 MODE_INPLACE = 1
+MODE_PARTITION = 2
 FLAG_STATS = 1
 FLAG_TIMING = 2
 FLAG_VALIDATE = 4
@@ -55,7 +56,8 @@ class GCError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("max_rounds", ctypes.c_int32), ("small_max_degree", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("spin_limit_ns", ctypes.c_int64), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32 * 8)]
+                ("spin_limit_ns", ctypes.c_int64), ("flags", ctypes.c_uint32), ("partitions", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class _Stats(ctypes.Structure):
@@ -189,6 +191,7 @@ class Options:
     blocks_per_sm: int = 0
     spin_limit_ns: int = 0
     flags: int = 0
+    partitions: int = 0
 
     def _c(self, stream) -> _Options:
         o = _Options()
@@ -200,6 +203,7 @@ class Options:
         o.blocks_per_sm = self.blocks_per_sm
         o.spin_limit_ns = self.spin_limit_ns
         o.flags = self.flags
+        o.partitions = self.partitions
         return o
 
 
@@ -221,7 +225,7 @@ class Stats:
 
 def _mode(mode) -> int:
     if isinstance(mode, str):
-        return {"det": 0, "deterministic": 0, "inplace": 1, "in-place": 1}[mode]
+        return {"det": 0, "deterministic": 0, "inplace": 1, "in-place": 1, "partition": 2}[mode]
     return int(mode)
 
 

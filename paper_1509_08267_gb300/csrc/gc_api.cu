@@ -91,6 +91,7 @@ struct Context {
     cudaStream_t stream = nullptr;
     int sms = 0;
     int occ[2][2][2] = {};  // [mode][batch][compact] blocks per SM of the round kernel
+    int occ_part = 0;       // blocks per SM of the partition-mode round kernel
     Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, lists, ctl, stats, bitmap, vg;
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
     Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors;
@@ -315,6 +316,27 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
         if (h.err[0] != 0) return error_from_ctl(h);
     }
     if (timing) GC_CUDA(cudaEventRecord(C.ev[0], s));
+    int64_t grid = 0;
+    if (mode == GC_MODE_PARTITION) {
+        // Algorithm 1 with p id-ordered blocks: its own set-up and round kernel
+        GC_CUDA(launch_partition_init(P, s));
+        GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+        if (h.err[0] != 0) return error_from_ctl(h);
+        if (timing) GC_CUDA(cudaEventRecord(C.ev[1], s));
+        int &occ = C.occ_part;
+        if (occ == 0) GC_CUDA(partition_kernel_occupancy(block, &occ));
+        int per_sm = occ;
+        if (opt && opt->blocks_per_sm > 0 && opt->blocks_per_sm < per_sm) per_sm = opt->blocks_per_sm;
+        grid = static_cast<int64_t>(per_sm) * C.sms;
+        int64_t p = (opt && opt->partitions > 0) ? opt->partitions : grid * (block / 32);
+        if (p > n) p = n;
+        if (p < 1) p = 1;
+        const int64_t want = (p + block / 32 - 1) / (block / 32);  // one warp per block of ids
+        if (want < grid) grid = want;
+        if (grid < 1) grid = 1;
+        if (n > 0) GC_CUDA(launch_partition_rounds(P, static_cast<int32_t>(p), static_cast<int>(grid), block, s));
+    } else {
     GC_CUDA(launch_setup(P, mode, pb.batch, 0, static_cast<int32_t>(n), -1, s));
     GC_CUDA(launch_sort_small(P, pb.batch, 0, static_cast<int32_t>(n), s));
     GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -338,11 +360,12 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     if (occ == 0) GC_CUDA(round_kernel_occupancy(mode, pb.batch, compact, block, &occ));
     int per_sm = occ;
     if (opt && opt->blocks_per_sm > 0 && opt->blocks_per_sm < per_sm) per_sm = opt->blocks_per_sm;
-    int64_t grid = static_cast<int64_t>(per_sm) * C.sms;
+    grid = static_cast<int64_t>(per_sm) * C.sms;
     const int64_t want = (static_cast<int64_t>(n_small) + 32 * static_cast<int64_t>(n_chunks) + block - 1) / block;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
     GC_CUDA(launch_rounds(P, mode, pb.batch, compact, static_cast<int>(grid), block, s));
+    }
     if (timing) GC_CUDA(cudaEventRecord(C.ev[2], s));
 
     // colors, per-graph counts; a device colors_out is written only if no error was posted, a host
@@ -451,7 +474,7 @@ static int color_single(int32_t n, const int32_t *rowptr, const int32_t *colidx,
                         int32_t *colors_out, int32_t *ncolors, int32_t *rounds, const gc_options *opt,
                         gc_stats *stats) {
     if (n < 0) return set_last_error(GC_ERR_INVALID_ARG, "n = %d is negative", n);
-    if (mode != GC_MODE_DETERMINISTIC && mode != GC_MODE_INPLACE)
+    if (mode != GC_MODE_DETERMINISTIC && mode != GC_MODE_INPLACE && mode != GC_MODE_PARTITION)
         return set_last_error(GC_ERR_INVALID_ARG, "unknown mode %d", mode);
     if (n > 0 && (!rowptr || !colors_out)) return set_last_error(GC_ERR_INVALID_ARG, "NULL rowptr or colors_out");
     if (n == INT32_MAX) return set_last_error(GC_ERR_INVALID_ARG, "n too large");

@@ -92,6 +92,8 @@ struct RoundParams {
     int32_t *lists;                   // compact mode: list pool (two regions of deg entries per larger vertex)
     unsigned long long *list_total;   // compact mode: setup adds 2 * deg of every larger vertex
     unsigned long long *list_alloc;   // compact mode: expand's allocation counter in the list pool
+    int32_t slot_per_vertex;          // compact mode, 1: vertex V's slot is V and its list regions start
+                                      // at 2 x its first entry (no allocation; the server's layout)
     unsigned *deg_hist;               // [256] optional: setup counts thread-per-vertex rows per degree
                                       // ([0, 128)); list positions per degree follow ([128, 256))
     GridBar *bar;
@@ -139,6 +141,11 @@ cudaError_t round_kernel_occupancy(int mode, bool batch, bool compact, int block
 cudaError_t launch_count_colors(const RoundParams &P, bool batch, const int32_t *colors_sel, int32_t v_begin,
                                 int32_t v_end, int32_t g_begin, int32_t g_end, unsigned *bitmap, int32_t *gmax,
                                 int32_t *gcount, int32_t *out, cudaStream_t s);
+// Partition mode (GC_MODE_PARTITION, single graph): set-up (rows checked, colors -1, W_1 = V) and
+// the cooperative round kernel with p blocks of consecutive ids.
+cudaError_t launch_partition_init(const RoundParams &P, cudaStream_t s);
+cudaError_t partition_kernel_occupancy(int block, int *blocks_per_sm);
+cudaError_t launch_partition_rounds(const RoundParams &P, int32_t p, int grid, int block, cudaStream_t s);
 cudaError_t launch_validate(int32_t n, const int32_t *rowptr, const int32_t *colidx, int flags, int32_t *err,
                             cudaStream_t s);
 

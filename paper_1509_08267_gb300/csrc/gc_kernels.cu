@@ -1380,8 +1380,8 @@ __global__ void scatter_small_kernel(RoundParams P, int32_t v_begin, int32_t v_e
 
 // Expands the larger vertices collected by setup into work items of round P.pass_begin, with
 // accumulator slots after those already taken in that round.  One warp per vertex.  COMPACT: the
-// vertex keeps its slot for the whole run; the slot records where its list is, the list's length,
-// the vertex's space in the list pool and its degree.  Deterministic items are DetItem (a vertex's
+// vertex keeps its slot for the whole run (slot V with P.slot_per_vertex); the slot records where
+// its list is, the list's length, the vertex's space in the list pool and its degree.  Deterministic items are DetItem (a vertex's
 // items split its row evenly with COMPACT, else into CH-entry pieces); in-place items are int4
 // {vertex, item index, slot, items}.
 template <bool BATCH, bool COMPACT, int MODE>
@@ -1404,14 +1404,17 @@ __global__ void expand_kernel(RoundParams P, int32_t n_items) {
         }
         slot = __shfl_sync(kFull, slot, 0);
         cb = __shfl_sync(kFull, cb, 0);
+        if (COMPACT && P.slot_per_vertex) slot = static_cast<unsigned>(V);
         unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
         a[lane] = 0u;
         unsigned hi = 0u;
         if (COMPACT) {
-            // the list starts as the CSR row; reserve the two list regions in the pool
-            unsigned long long off = 0;
-            if (lane == 0) off = atomicAdd(P.list_alloc, 2ull * static_cast<unsigned long long>(deg));
-            off = __shfl_sync(kFull, off, 0);
+            // the list starts as the CSR row; the two list regions in the pool
+            unsigned long long off = 2ull * static_cast<unsigned long long>(r.b);
+            if (!P.slot_per_vertex) {
+                if (lane == 0) off = atomicAdd(P.list_alloc, 2ull * static_cast<unsigned long long>(deg));
+                off = __shfl_sync(kFull, off, 0);
+            }
             if (lane == kAccLen - 32) hi = static_cast<unsigned>(deg);
             if (lane == kAccOffLo - 32) hi = static_cast<unsigned>(off);
             if (lane == kAccOffHi - 32) hi = static_cast<unsigned>(off >> 32);
@@ -1430,6 +1433,148 @@ __global__ void expand_kernel(RoundParams P, int32_t n_items) {
             int4 *cur = (pass & 1) ? P.chunk0 : P.chunk1;
             for (int32_t q = lane; q < nch; q += 32) cur[cb + q] = make_int4(V, q, static_cast<int32_t>(slot), nch);
         }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// partition mode: Algorithm 1 with p blocks of consecutive ids
+
+// Block i (0-based) of p over n vertices holds ids [floor(i n / p), floor((i + 1) n / p)).
+__device__ __forceinline__ int32_t part_lo(int64_t i, int64_t n, int64_t p) { return static_cast<int32_t>(i * n / p); }
+
+// Set-up of partition mode: rows checked, every color -1 in both buffers, every vertex on W_1.
+__global__ void part_init_kernel(RoundParams P) {
+    unsigned *cc = P.cnt + kCnt * (1 % 3);
+    if (blockIdx.x == 0 && threadIdx.x == 0) cc[kCntSmall] = static_cast<unsigned>(P.n);
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < P.n; v += gridDim.x * blockDim.x) {
+        int64_t b;
+        int32_t lv;
+        if (checked_degree<false>(P, v, 0, b, lv) < 0) set_error(P.err, GC_ERR_INVALID_GRAPH, v, b);
+        P.col0[v] = pack_state(-1, 0, false);
+        P.col1[v] = pack_state(-1, 0, false);
+        P.small0[v] = 1;
+    }
+}
+
+// First Fit of vertex V in phase 1 (one warp): a neighbour in V's own block [lo, hi) counts with its
+// live color (this warp colored the block's earlier vertices a moment ago), any other with the
+// color it had when the round began (S).  Window of 512 colors at a time in shared memory.
+__device__ __forceinline__ int32_t part_first_fit(const RoundParams &P, const uint64_t *C, const uint64_t *S, int32_t V,
+                                                  int32_t lo, int32_t hi, unsigned *win, int lane) {
+    const int64_t b = P.rowptr[V], e = P.rowptr[V + 1];
+    for (int32_t base = 0;; base += 32 * kAccWords) {
+        if (lane < kAccWords) win[lane] = 0;
+        __syncwarp();
+        for (int64_t j = b + lane; j < e; j += 32) {
+            const int32_t u = __ldg(P.colidx + j);
+            if (static_cast<uint32_t>(u) >= static_cast<uint32_t>(P.n) || u == V) {
+                set_error(P.err, GC_ERR_INVALID_GRAPH, V, j);
+                continue;
+            }
+            const int32_t c = color_of(u >= lo && u < hi ? __ldcg(reinterpret_cast<const unsigned long long *>(C) + u)
+                                                         : __ldcg(reinterpret_cast<const unsigned long long *>(S) + u)) -
+                              base;
+            if (static_cast<unsigned>(c) < 32u * kAccWords) atomicOr(&win[c >> 5], 1u << (c & 31));
+        }
+        __syncwarp();
+        int32_t res = -1;
+        const unsigned x = lane < kAccWords ? win[lane] : 0xffffffffu;
+        const unsigned m = __ballot_sync(kFull, x != 0xffffffffu);
+        if (m) {
+            const int l = __ffs(m) - 1;
+            res = base + 32 * l + __ffs(~__shfl_sync(kFull, x, l)) - 1;
+        }
+        __syncwarp();
+        if (res >= 0) return res;
+    }
+}
+
+// Partition mode (Algorithm 1 of Section 3.1 taken literally: partition priority instead of a hash):
+// p blocks of consecutive ids, one warp per block at a time.  Phase 1: a block's worklist vertices
+// take First Fit one after another in id order.  Grid barrier.  Phase 2: a worklist vertex is
+// re-queued when a neighbour in a higher block has its color (the lower block recolors).  Grid
+// barrier.  Colors live in col0 (current) and col1 (as the round began); small0[v] = r puts v on W_r.
+__global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) part_round_kernel(RoundParams P, int32_t p) {
+    __shared__ unsigned s_win[kMaxWarps][kAccWords];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    unsigned *win = s_win[wib];
+    uint64_t *C = P.col0, *S = P.col1;
+    int32_t *onw = P.small0;
+    const int64_t n = P.n;
+    if (P.stats && blockIdx.x == 0 && threadIdx.x == 0) P.stats[4 * P.stats_cap] = global_ns();
+    unsigned bar_target = 0;
+    int pass = P.pass_begin;
+    for (;; ++pass) {
+        unsigned *cc = P.cnt + kCnt * (pass % 3);
+        unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
+        const unsigned nwl = __ldcg(cc + kCntSmall);
+        if (__ldcg(P.err) != 0) break;
+        if (nwl == 0u) break;
+        if (pass >= P.pass_end) {
+            if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
+                set_error(P.err, GC_ERR_NO_CONVERGENCE, pass, 0);
+            break;
+        }
+        if (blockIdx.x == 0 && threadIdx.x < kCnt) P.cnt[kCnt * ((pass + 2) % 3) + threadIdx.x] = 0u;
+        unsigned st_deg = 0;
+        // phase 1
+        for (int32_t i = gw; i < p; i += nw) {
+            const int32_t lo = part_lo(i, n, p), hi = part_lo(i + 1, n, p);
+            for (int32_t base = lo; base < hi; base += 32) {
+                const int32_t v = base + lane;
+                unsigned m = __ballot_sync(kFull, v < hi && __ldcg(onw + v) == pass);
+                while (m) {
+                    const int32_t V = base + __ffs(m) - 1;
+                    m &= m - 1;
+                    const int32_t c = part_first_fit(P, C, S, V, lo, hi, win, lane);
+                    if (lane == 0) {
+                        C[V] = pack_state(c, 0, false);
+                        st_deg += static_cast<unsigned>(P.rowptr[V + 1] - P.rowptr[V]);
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
+        // phase 2
+        unsigned lost = 0;
+        for (int32_t i = gw; i < p; i += nw) {
+            const int32_t lo = part_lo(i, n, p), hi = part_lo(i + 1, n, p);
+            for (int32_t base = lo; base < hi; base += 32) {
+                const int32_t v = base + lane;
+                unsigned m = __ballot_sync(kFull, v < hi && __ldcg(onw + v) == pass);
+                while (m) {
+                    const int32_t V = base + __ffs(m) - 1;
+                    m &= m - 1;
+                    const uint64_t cvw = __ldcg(reinterpret_cast<const unsigned long long *>(C) + V);
+                    const int32_t cv = color_of(cvw);
+                    bool hit = false;
+                    for (int64_t j = P.rowptr[V] + lane; j < P.rowptr[V + 1] && !hit; j += 32) {
+                        const int32_t u = __ldg(P.colidx + j);
+                        if (u >= hi && u < P.n &&
+                            color_of(__ldcg(reinterpret_cast<const unsigned long long *>(C) + u)) == cv)
+                            hit = true;
+                    }
+                    const bool lose = __any_sync(kFull, hit);
+                    if (lane == 0) {
+                        S[V] = cvw;  // the color phase 1 of the next round sees from other blocks
+                        if (lose) {
+                            onw[V] = pass + 1;
+                            ++lost;
+                        }
+                    }
+                }
+            }
+        }
+        if (lane == 0 && lost) atomicAdd(cn + kCntSmall, lost);
+        if (P.stats) flush_stats(P, pass, st_deg, (blockIdx.x == 0 && threadIdx.x == 0) ? nwl : 0u, 2ull * st_deg);
+        if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.passes[0] = pass;
+        P.passes[1] = pass - 1;
     }
 }
 
@@ -1635,6 +1780,28 @@ cudaError_t launch_rounds(const RoundParams &P, int mode, bool batch, bool compa
     RoundParams arg = P;
     void *args[] = {&arg};
     return cudaLaunchCooperativeKernel(round_kernel_fn(mode, batch, compact), dim3(grid), dim3(block), args, 0, s);
+}
+
+cudaError_t launch_partition_init(const RoundParams &P, cudaStream_t s) {
+    if (P.n <= 0) return cudaSuccess;
+    part_init_kernel<<<grid_for(P.n, 256, sm_count() * 16), 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t partition_kernel_occupancy(int block, int *blocks_per_sm) {
+    if (block != kBlock) return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, part_round_kernel, block, 0);
+}
+
+cudaError_t launch_partition_rounds(const RoundParams &P, int32_t p, int grid, int block, cudaStream_t s) {
+    if (block != kBlock) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(&P.bar->count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    RoundParams arg = P;
+    int32_t parg = p;
+    void *args[] = {&arg, &parg};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(&part_round_kernel), dim3(grid), dim3(block),
+                                       args, 0, s);
 }
 
 cudaError_t launch_count_colors(const RoundParams &P, bool batch, const int32_t *colors_sel, int32_t v_begin,

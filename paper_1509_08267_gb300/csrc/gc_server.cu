@@ -132,7 +132,8 @@ struct gc_server {
     int grid = 0;
     int64_t PV = 0, PE = 0, PI = 0, PC = 0;  // pool capacities: vertices, entries, large vertices, work items
     int32_t S = 0;                           // slots
-    gc::DevBuf rowptr, colidx, col0, col1, outbuf, small0, small1, items, chunk0, chunk1, acc, vg, ctl, bitmap;
+    bool compact = false;  // deterministic mode: the compact sweep (slot and list space per pool vertex / entry)
+    gc::DevBuf rowptr, colidx, col0, col1, outbuf, small0, small1, items, chunk0, chunk1, acc, lists, vg, ctl, bitmap;
     gc::DevBuf g_vbase, g_n, g_ebase, g_rbase, g_m, glast, gmax, gcount, verr;
     std::vector<int64_t> h_vbase, h_ebase, h_rbase, h_m;
     std::vector<int32_t> h_n, h_glast;
@@ -194,6 +195,10 @@ RoundParams params(gc_server *s, int32_t rounds = kRoundsWhileQueued) {
     P.chunk0 = s->chunk0.as<int4>();
     P.chunk1 = s->chunk1.as<int4>();
     P.items = s->items.as<int32_t>();
+    if (s->compact) {
+        P.lists = s->lists.as<int32_t>();
+        P.slot_per_vertex = 1;
+    }
     Ctl *c = s->ctl.as<Ctl>();
     P.tmp = c->tmp;
     P.cnt = c->cnt;
@@ -306,7 +311,7 @@ int admit(gc_server *s, const std::vector<Request *> &adm, std::vector<Request *
     for (Request *r : ok)
         SRV_CUDA(launch_setup(P, s->cfg.mode, true, static_cast<int32_t>(r->vbase),
                               static_cast<int32_t>(r->vbase + r->n), r->slot, st));
-    SRV_CUDA(launch_expand(P, s->cfg.mode, true, false, -1, st));
+    SRV_CUDA(launch_expand(P, s->cfg.mode, true, s->compact, -1, st));
     return GC_OK;
 }
 
@@ -423,7 +428,7 @@ void worker_main(gc_server *s) {
             if (s->resident.empty()) continue;
         }
         RoundParams P = params(s, queued ? kRoundsWhileQueued : kRoundsIdleQueue);
-        cudaError_t e = launch_rounds(P, s->cfg.mode, true, false, s->grid, 256, s->stream);
+        cudaError_t e = launch_rounds(P, s->cfg.mode, true, s->compact, s->grid, 256, s->stream);
         Ctl h{};
         if (e == cudaSuccess) e = cudaMemcpyAsync(&h, s->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream);
         if (e == cudaSuccess)
@@ -490,6 +495,9 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
     s->PE = cfg->pool_entries;
     s->PI = std::min<int64_t>(s->PV, s->PE / (gc::kT1 + 1) + 1);
     s->PC = s->PE / gc::kCH + s->PI + 1;
+    // deterministic mode sweeps compact lists: a slot per pool vertex and two list regions per entry
+    s->compact = cfg->mode == GC_MODE_DETERMINISTIC;
+    const size_t slots = s->compact ? static_cast<size_t>(s->PV) : static_cast<size_t>(s->PI);
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
     const size_t V = static_cast<size_t>(s->PV), Sz = static_cast<size_t>(s->S);
@@ -500,7 +508,8 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
         {&s->rowptr, 4 * (V + Sz)}, {&s->colidx, 4 * static_cast<size_t>(s->PE)}, {&s->col0, 8 * V}, {&s->col1, 8 * V},
         {&s->outbuf, 4 * V}, {&s->small0, 4 * V}, {&s->small1, 4 * V}, {&s->items, 4 * V}, {&s->vg, 4 * V},
         {&s->chunk0, gc::kItemBytes * static_cast<size_t>(s->PC)}, {&s->chunk1, gc::kItemBytes * static_cast<size_t>(s->PC)},
-        {&s->acc, 4 * gc::kAccStride * static_cast<size_t>(s->PI)}, {&s->ctl, sizeof(gc::Ctl)},
+        {&s->acc, 4 * gc::kAccStride * slots}, {&s->lists, s->compact ? 8 * static_cast<size_t>(s->PE) : 0},
+        {&s->ctl, sizeof(gc::Ctl)},
         {&s->bitmap, 4 * (V / 32 + 4)}, {&s->g_vbase, 8 * Sz}, {&s->g_n, 4 * Sz}, {&s->g_ebase, 8 * Sz},
         {&s->g_rbase, 8 * Sz}, {&s->g_m, 8 * Sz}, {&s->glast, 4 * Sz}, {&s->gmax, 4 * Sz}, {&s->gcount, 4 * Sz},
         {&s->verr, 16 * Sz},
@@ -510,7 +519,7 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
         e = a.b->alloc(a.bytes);
     }
     if (e == cudaSuccess) e = cudaMemset(s->ctl.p, 0, sizeof(gc::Ctl));
-    if (e == cudaSuccess) e = cudaMemset(s->acc.p, 0, 4 * gc::kAccStride * static_cast<size_t>(s->PI));
+    if (e == cudaSuccess) e = cudaMemset(s->acc.p, 0, 4 * gc::kAccStride * slots);
     if (e == cudaSuccess) e = cudaMemset(s->g_n.p, 0, 4 * Sz);
     if (e == cudaSuccess) e = cudaMemset(s->glast.p, 0, 4 * Sz);
     if (e != cudaSuccess) {
@@ -520,7 +529,7 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
                               cudaGetErrorString(e));
     }
     int per_sm = 0, sms = 0;
-    gc::round_kernel_occupancy(cfg->mode, true, false, 256, &per_sm);
+    gc::round_kernel_occupancy(cfg->mode, true, s->compact, 256, &per_sm);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     s->grid = std::max(1, per_sm * sms);
     s->h_vbase.assign(Sz, 0);

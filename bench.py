@@ -328,8 +328,23 @@ def run_serve(args, rank, world):
                 r.rounds == results[i][2]
     t_solo = time.perf_counter() - t1
     dev = torch.device("cuda", local)
+    # the same requests as one batch already on the device: what co-scheduling all of them at once
+    # gives, with no arrivals to wait for and no copies (an upper bound for the server)
+    b = gg.pack(graphs)
+    bargs = [torch.from_numpy(a).to(dev) for a in (b.vtx_off, b.edge_off, b.rowptr, b.colidx)]
+    bout = torch.empty(int(b.vtx_off[-1]), dtype=torch.int32, device=dev)
+    from paper_1509_08267_gb300 import autotune
+    bopt = autotune.batch_options()
+    gc.color_batch(*bargs, args.mode, HASH_SEED, out=bout, options=bopt)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    gc.color_batch(*bargs, args.mode, HASH_SEED, out=bout, options=bopt)
+    torch.cuda.synchronize()
+    t_all = time.perf_counter() - t2
+    del bargs, bout
     t_serve = reduce_max(t_serve, world, dev)
     t_solo = reduce_max(t_solo, world, dev)
+    t_all = reduce_max(t_all, world, dev)
     m_und = sum(g.nnz for g in graphs) / 2
     if rank == 0:
         line = {
@@ -344,6 +359,8 @@ def run_serve(args, rank, world):
             "graphs_per_s": count / t_serve, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "one_by_one": {"value": m_und / t_solo / 1e9, "unit": "Gedges/s", "graphs_per_s": count / t_solo},
             "served_over_one_by_one": t_solo / t_serve, "identical_colorings": same,
+            "all_at_once": {"value": m_und / t_all / 1e9, "unit": "Gedges/s", "seconds": t_all,
+                            "note": "the same graphs as one device-resident gc_color_batch call"},
             "rounds_run": st["rounds_run"], "server_busy_s": st["busy_s"], "serve_wall_s": t_serve,
         }
         print(json.dumps(line), flush=True)
@@ -356,6 +373,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="rmat22", help="rmat22 | stencil256 | er10k | rmatNN | stencilL")
     ap.add_argument("--mode", default="det", choices=["det", "inplace"])
+    ap.add_argument("--priority", default="hash", choices=["hash", "lf"],
+                    help="priority key: seeded hash (default) or largest degree first")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -398,11 +417,12 @@ def main():
     ci = torch.from_numpy(g.colidx).to(dev)
     out = torch.empty(g.n, dtype=torch.int32, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
-    opt = gc.Options(flags=gc.FLAG_TIMING)
+    prio = gc.PRIORITY_LARGEST_FIRST if args.priority == "lf" else gc.PRIORITY_HASH
+    opt = gc.Options(flags=gc.FLAG_TIMING, priority=prio)
     mode = args.mode
 
     # warm-up (also records the per-round statistics once, outside the timed region)
-    r0 = gc.color(rp, ci, mode, HASH_SEED, out=out, stats=True)
+    r0 = gc.color(rp, ci, mode, HASH_SEED, out=out, stats=True, options=gc.Options(priority=prio))
     for _ in range(args.warmup - 1):
         gc.color(rp, ci, mode, HASH_SEED, out=out, options=opt)
     torch.cuda.synchronize()
@@ -447,14 +467,14 @@ def main():
         rp_h = torch.from_numpy(g.rowptr).pin_memory()
         ci_h = torch.from_numpy(g.colidx).pin_memory()
         out_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
-        gc.color(rp_h.numpy(), ci_h.numpy(), mode, HASH_SEED, out=out_h.numpy())
+        gc.color(rp_h.numpy(), ci_h.numpy(), mode, HASH_SEED, out=out_h.numpy(), options=gc.Options(priority=prio))
         torch.cuda.synchronize()
         te = []
         for k in range(args.e2e_steps):
             flush.fill_(k & 0xFF)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            gc.color(rp_h.numpy(), ci_h.numpy(), mode, HASH_SEED, out=out_h.numpy())
+            gc.color(rp_h.numpy(), ci_h.numpy(), mode, HASH_SEED, out=out_h.numpy(), options=gc.Options(priority=prio))
             te.append(time.perf_counter() - t0)
         e_t = reduce_max(statistics.median(te), world, dev)
         e2e = {"value": whole_job_rate(m_und, e_t, world) / 1e9, "unit": "Gedges/s",
@@ -469,7 +489,7 @@ def main():
             key, desc = CPU_SAMPLE.get(args.workload, (args.workload, "the same graph, full deterministic coloring"))
             sg = gg.workload(key)
             t0 = time.perf_counter()
-            ro = oracle.det(sg, HASH_SEED)
+            ro = oracle.det(sg, HASH_SEED, priority=1 if args.priority == "lf" else 0)
             tc = time.perf_counter() - t0
             cpu = {"value": (sg.nnz / 2) / tc / 1e9, "unit": "Gedges/s", "cores": cpu_cores_used(), "kind": "oracle",
                    "sample": desc + f" ({tc:.1f} s, {ro.rounds} rounds)",
@@ -481,6 +501,7 @@ def main():
             "config": {"workload": args.workload, "graph": WORKLOAD_DESC.get(args.workload, g.name), "n": g.n,
                        "nnz": g.nnz,
                        "mode": "deterministic" if mode == "det" else "in-place", "hash_seed": HASH_SEED,
+                       "priority": "largest degree first" if args.priority == "lf" else "hash",
                        "l2": "flushed between steps (512 MB write) and colidx > L2", "parallelism":
                        "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -75,6 +75,12 @@ typedef enum {
 
 enum { GC_MODE_DETERMINISTIC = 0, GC_MODE_INPLACE = 1, GC_MODE_PARTITION = 2 };
 
+/* Priority keys (which endpoint of a monochromatic edge keeps its color: the smaller key).
+ *   GC_PRIORITY_HASH           key(v) = (h(v), v)
+ *   GC_PRIORITY_LARGEST_FIRST  key(v) = (-min(deg(v), 2^20 - 1), h(v), v): larger degrees first, an
+ *                              ordering the paper lists as future work (Section 6) */
+enum { GC_PRIORITY_HASH = 0, GC_PRIORITY_LARGEST_FIRST = 1 };
+
 /* Flags for gc_options.flags */
 #define GC_FLAG_STATS 1u     /* fill gc_stats' per-round worklist sizes and scanned entries */
 #define GC_FLAG_TIMING 2u    /* record CUDA events around the round kernel (gc_stats.kernel_ms) */
@@ -101,7 +107,9 @@ typedef struct gc_options {
     uint32_t flags;            /* GC_FLAG_* */
     int32_t partitions;        /* GC_MODE_PARTITION: number of blocks p (clamped to 1..n); 0 = one per
                                   resident warp of the round kernel */
-    int32_t reserved[7];
+    int32_t priority;          /* deterministic and in-place modes: GC_PRIORITY_HASH (default) or
+                                  GC_PRIORITY_LARGEST_FIRST */
+    int32_t reserved[6];
 } gc_options;
 
 /* Optional run statistics (gc_color_ex / gc_color_batch_ex).  The caller may provide arrays

@@ -71,6 +71,10 @@ def _L():
         lib.oracle_greedy.argtypes = [i32, p, p, p]
         lib.oracle_det.restype = ctypes.c_int
         lib.oracle_det.argtypes = [i32, p, p, u64, i32, p, p, p, p, p, i32, p]
+        lib.oracle_det_prio.restype = ctypes.c_int
+        lib.oracle_det_prio.argtypes = [i32, p, p, u64, i32, i32, p, p, p, p, p, i32, p]
+        lib.oracle_key_less_lf.restype = ctypes.c_int
+        lib.oracle_key_less_lf.argtypes = [u64, i32, i32, i32, i32]
         lib.oracle_partition.restype = ctypes.c_int
         lib.oracle_partition.argtypes = [i32, p, p, i32, i32, p, p, p, p, i32]
         _lib = lib
@@ -150,10 +154,21 @@ class DetResult:
     last_round: np.ndarray | None = None
 
 
-def det(g, seed: int, max_rounds: int | None = None, stats_cap: int = 1 << 16) -> DetResult:
+PRIORITY_HASH = 0
+PRIORITY_LARGEST_FIRST = 1
+
+
+def key_less_lf(seed: int, u: int, v: int, du: int, dv: int) -> bool:
+    """Largest-first priority: u keeps its color against v (degrees capped at 2^20 - 1, ties by hash)."""
+    return bool(_L().oracle_key_less_lf(seed & U64, u, v, du, dv))
+
+
+def det(g, seed: int, max_rounds: int | None = None, stats_cap: int = 1 << 16,
+        priority: int = PRIORITY_HASH) -> DetResult:
     """Deterministic speculative coloring, round by round.  `status` is 0, or -1 when the round
     cap (default n + 1) was reached with a non-empty worklist.  `last_round[v]` is the last round
-    whose worklist held v (worklists only shrink, so v was on W_1..W_last_round[v])."""
+    whose worklist held v (worklists only shrink, so v was on W_1..W_last_round[v]).  priority:
+    PRIORITY_HASH (key = hash, id) or PRIORITY_LARGEST_FIRST (key = -capped degree, hash, id)."""
     rp, ci = _csr(g)
     n = g.n
     if max_rounds is None:
@@ -165,9 +180,9 @@ def det(g, seed: int, max_rounds: int | None = None, stats_cap: int = 1 << 16) -
     nc = ctypes.c_int32(0)
     rd = ctypes.c_int32(0)
     last = np.zeros(max(n, 1), dtype=np.int32)
-    st = _L().oracle_det(n, rp.ctypes.data, ci.ctypes.data, seed & U64, max_rounds, colors.ctypes.data,
-                         ctypes.byref(nc), ctypes.byref(rd), wl.ctypes.data, ds.ctypes.data, cap,
-                         last.ctypes.data)
+    st = _L().oracle_det_prio(n, rp.ctypes.data, ci.ctypes.data, seed & U64, int(priority), max_rounds,
+                              colors.ctypes.data, ctypes.byref(nc), ctypes.byref(rd), wl.ctypes.data, ds.ctypes.data,
+                              cap, last.ctypes.data)
     if st == -2:
         raise MemoryError("oracle_det")
     r = int(rd.value)

@@ -58,6 +58,17 @@ int oracle_key_less(uint64_t seed, int32_t u, int32_t v) {
     return u < v;
 }
 
+/* Largest-first priority (an ordering from the paper's future work, Section 6): a vertex of larger
+ * degree keeps its color; degrees of 2^20 - 1 and more count as 2^20 - 1; equal (capped) degrees
+ * fall back to the hash order above.  1 when u keeps its color against v. */
+#define ORACLE_DEG_CAP 1048575
+int oracle_key_less_lf(uint64_t seed, int32_t u, int32_t v, int32_t du, int32_t dv) {
+    if (du > ORACLE_DEG_CAP) du = ORACLE_DEG_CAP;
+    if (dv > ORACLE_DEG_CAP) dv = ORACLE_DEG_CAP;
+    if (du != dv) return du > dv;
+    return oracle_key_less(seed, u, v);
+}
+
 void oracle_keys(uint64_t seed, int32_t n, uint64_t *out) {
     for (int32_t v = 0; v < n; ++v) out[v] = oracle_splitmix64(seed, (uint64_t)v);
 }
@@ -140,14 +151,15 @@ int32_t oracle_greedy(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
  *       W <- L
  *       -- barrier --
  *
+ * key: priority 0, the hash order (oracle_key_less); 1, largest degree first (oracle_key_less_lf).
  * Outputs the colors, the number of distinct colors and the number of rounds.  When `stats_cap`
  * > 0, wl_size[r-1] = |W_r| and wl_degsum[r-1] = sum of deg(v) over W_r for the first stats_cap
  * rounds.  When `last_round` is not NULL, last_round[v] = the last round whose worklist held v.
  * Returns 0, or -1 if W is still non-empty after `max_rounds` rounds, or -2 on OOM.
  */
-int oracle_det(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed, int32_t max_rounds,
-               int32_t *C, int32_t *ncolors, int32_t *rounds, int64_t *wl_size, int64_t *wl_degsum,
-               int32_t stats_cap, int32_t *last_round) {
+int oracle_det_prio(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed, int32_t priority,
+                    int32_t max_rounds, int32_t *C, int32_t *ncolors, int32_t *rounds, int64_t *wl_size,
+                    int64_t *wl_degsum, int32_t stats_cap, int32_t *last_round) {
     *ncolors = 0;
     *rounds = 0;
     if (n <= 0) return 0;
@@ -188,7 +200,10 @@ int oracle_det(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t
             int32_t v = W[i];
             for (int32_t j = rowptr[v]; j < rowptr[v + 1]; ++j) {
                 int32_t u = colidx[j];
-                if (C[u] == C[v] && oracle_key_less(seed, u, v)) {
+                int keeps = priority == 1 ? oracle_key_less_lf(seed, u, v, rowptr[u + 1] - rowptr[u],
+                                                               rowptr[v + 1] - rowptr[v])
+                                          : oracle_key_less(seed, u, v);
+                if (C[u] == C[v] && keeps) {
                     L[ln++] = v;
                     break;
                 }
@@ -206,6 +221,14 @@ int oracle_det(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t
     free(L);
     free(seen);
     return status;
+}
+
+/* oracle_det_prio with the hash priority (priority 0). */
+int oracle_det(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed, int32_t max_rounds,
+               int32_t *C, int32_t *ncolors, int32_t *rounds, int64_t *wl_size, int64_t *wl_degsum,
+               int32_t stats_cap, int32_t *last_round) {
+    return oracle_det_prio(n, rowptr, colidx, seed, 0, max_rounds, C, ncolors, rounds, wl_size, wl_degsum,
+                           stats_cap, last_round);
 }
 
 /*

@@ -18,7 +18,7 @@ import numpy as np
 
 __all__ = [
     "GCError", "load", "color", "color_batch", "validate", "Options", "Stats", "Server", "MODE_DETERMINISTIC",
-    "MODE_INPLACE", "MODE_PARTITION", "version", "release_scratch",
+    "MODE_INPLACE", "MODE_PARTITION", "PRIORITY_HASH", "PRIORITY_LARGEST_FIRST", "version", "release_scratch",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -38,6 +38,8 @@ STATUS_NAMES = {0: "GC_OK", -1: "GC_ERR_INVALID_ARG", -2: "GC_ERR_INVALID_GRAPH"
 MODE_DETERMINISTIC = 0
 MODE_INPLACE = 1
 MODE_PARTITION = 2
+PRIORITY_HASH = 0
+PRIORITY_LARGEST_FIRST = 1
 FLAG_STATS = 1
 FLAG_TIMING = 2
 FLAG_VALIDATE = 4
@@ -57,7 +59,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("max_rounds", ctypes.c_int32), ("small_max_degree", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("spin_limit_ns", ctypes.c_int64), ("flags", ctypes.c_uint32), ("partitions", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("priority", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class _Stats(ctypes.Structure):
@@ -192,6 +194,7 @@ class Options:
     spin_limit_ns: int = 0
     flags: int = 0
     partitions: int = 0
+    priority: int = 0
 
     def _c(self, stream) -> _Options:
         o = _Options()
@@ -204,6 +207,7 @@ class Options:
         o.spin_limit_ns = self.spin_limit_ns
         o.flags = self.flags
         o.partitions = self.partitions
+        o.priority = self.priority
         return o
 
 

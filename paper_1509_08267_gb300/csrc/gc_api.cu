@@ -231,6 +231,9 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     if (T1 < 1 || T1 > 127) return set_last_error(GC_ERR_INVALID_ARG, "small_max_degree %d outside 1..127", T1);
     if (CH < 32 || CH > 1024 || CH % 32) return set_last_error(GC_ERR_INVALID_ARG, "chunk %d invalid", CH);
     if (block != 256) return set_last_error(GC_ERR_INVALID_ARG, "block_size %d unsupported (256)", block);
+    const int32_t priority = opt ? opt->priority : GC_PRIORITY_HASH;
+    if (priority != GC_PRIORITY_HASH && priority != GC_PRIORITY_LARGEST_FIRST)
+        return set_last_error(GC_ERR_INVALID_ARG, "unknown priority %d", priority);
     const int64_t n = pb.n;
     const int32_t G = pb.G;
     const int32_t max_rounds =
@@ -305,6 +308,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     P.spin_ns = spin_ns;
     P.T1 = T1;
     P.CH = CH;
+    P.priority = priority;
 
     const bool timing = (flags & GC_FLAG_TIMING) != 0;
     Ctl h{};

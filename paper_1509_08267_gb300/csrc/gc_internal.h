@@ -109,6 +109,7 @@ struct RoundParams {
     int64_t spin_ns;
     int32_t T1;  // largest degree handled by one thread
     int32_t CH;  // adjacency entries per warp work item
+    int32_t priority;  // GC_PRIORITY_*: what the 31 priority bits of a state word hold
 };
 
 // Launch wrappers (gc_kernels.cu).  All return the launch's cudaError_t.

@@ -148,3 +148,56 @@ def test_batch_full_sweep(gclib):
         ref = oracle.det(g, 3)
         np.testing.assert_array_equal(colors[b.vtx_off[i]:b.vtx_off[i + 1]], ref.colors)
         assert (nc[i], rd[i]) == (ref.ncolors, ref.rounds)
+
+
+# ---------------------------------------------------------------------------------------------
+# largest-first priority
+
+LF_GRAPHS = [lambda: gg.star(5000), lambda: gg.crown(40), lambda: gg.grid5(37, 29), lambda: gg.stencil27(9),
+             lambda: gg.er(3000, 12.0, 5), lambda: gg.rmat(12, 16, 2), lambda: gg.rmat(15, 16, 2)]
+
+
+@pytest.mark.parametrize("make", LF_GRAPHS)
+@pytest.mark.parametrize("seed", [1, 7])
+def test_largest_first_matches_oracle(gclib, make, seed):
+    g = make()
+    ref = oracle.det(g, seed, priority=oracle.PRIORITY_LARGEST_FIRST)
+    assert ref.status == 0
+    opt = gclib.Options(priority=gclib.PRIORITY_LARGEST_FIRST)
+    colors, nc, rounds, st = run_det(gclib, g, seed, options=opt, stats=True)
+    np.testing.assert_array_equal(colors, ref.colors)
+    assert (nc, rounds) == (ref.ncolors, ref.rounds)
+    np.testing.assert_array_equal(st.wl_size, ref.wl_size)
+    np.testing.assert_array_equal(st.wl_degsum, ref.wl_degsum)
+
+
+def test_largest_first_batch_matches_oracle(gclib):
+    import torch
+    graphs = [gg.rmat(11, 8, 1), gg.star(300), gg.er(1500, 9.0, 2), gg.grid5(20, 20)]
+    b = gg.pack(graphs)
+    args = [torch.from_numpy(a).cuda() for a in (b.vtx_off, b.edge_off, b.rowptr, b.colidx)]
+    colors, nc, rounds = gclib.color_batch(*args, "det", 7,
+                                           options=gclib.Options(priority=gclib.PRIORITY_LARGEST_FIRST))
+    colors = colors.cpu().numpy()
+    for i, g in enumerate(graphs):
+        ref = oracle.det(g, 7, priority=oracle.PRIORITY_LARGEST_FIRST)
+        v0, v1 = int(b.vtx_off[i]), int(b.vtx_off[i + 1])
+        np.testing.assert_array_equal(colors[v0:v1], ref.colors)
+        assert (int(nc[i]), int(rounds[i])) == (ref.ncolors, ref.rounds)
+
+
+def test_largest_first_inplace_proper(gclib):
+    import torch
+    g = gg.rmat(15, 16, 3)
+    rp, ci = _dev(g)
+    r = gclib.color(rp, ci, "inplace", 7, options=gclib.Options(priority=gclib.PRIORITY_LARGEST_FIRST))
+    c = r.colors.cpu().numpy()
+    assert oracle.count_conflicts(g, c) == 0
+    assert np.all(c <= g.degrees()) and r.ncolors == oracle.distinct_colors(c)
+
+
+def test_unknown_priority_rejected(gclib):
+    g = gg.path(10)
+    with pytest.raises(gclib.GCError) as e:
+        gclib.color(g.rowptr, g.colidx, "det", 1, options=gclib.Options(priority=9))
+    assert e.value.status == gclib.GC_ERR_INVALID_ARG

@@ -315,3 +315,65 @@ def test_checkers():
     assert oracle.count_conflicts(g, np.array([0, 1, 2, 3], np.int32)) == 0
     assert oracle.count_conflicts(g, np.array([0, 0, 2, 3], np.int32)) == 2
     assert oracle.distinct_colors(np.array([5, 0, 5, 2], np.int32)) == 3
+
+
+# ---------------------------------------------------------------------------------------------
+# largest-first priority (an ordering the paper leaves to future work, Section 6)
+
+def test_lf_key_order():
+    rng = np.random.default_rng(13)
+    cap = (1 << 20) - 1
+    for _ in range(300):
+        seed = int(rng.integers(0, 2**63))
+        u, v = (int(x) for x in rng.integers(0, 10**6, 2))
+        du, dv = (int(x) for x in rng.integers(0, 40, 2))
+        want = du > dv if du != dv else oracle.key_less(seed, u, v)
+        assert oracle.key_less_lf(seed, u, v, du, dv) == want
+    # degrees at or above the cap tie, and the hash decides
+    assert oracle.key_less_lf(3, 5, 9, cap + 7, cap) == oracle.key_less(3, 5, 9)
+    assert oracle.key_less_lf(3, 9, 5, 2 * cap, cap + 1) == oracle.key_less(3, 9, 5)
+
+
+@pytest.mark.parametrize("leaves", [1, 2, 31, 500])
+def test_lf_star_closed_form(leaves):
+    # round 1: everyone 0; the centre has the largest degree and keeps 0, every leaf is re-queued
+    # and takes 1 in round 2 (its only neighbour has 0); two colors, two rounds, for any seed
+    g = gg.star(leaves)
+    deg = g.degrees()
+    centre = int(np.argmax(deg))
+    for seed in (0, 7):
+        r = oracle.det(g, seed, priority=oracle.PRIORITY_LARGEST_FIRST)
+        want = np.ones(g.n, np.int32)
+        want[centre] = 0
+        if leaves == 1:  # two vertices of degree 1: the hash decides who keeps 0
+            assert sorted(r.colors) == [0, 1]
+        else:
+            np.testing.assert_array_equal(r.colors, want)
+        assert r.rounds == 2 and r.ncolors == 2
+
+
+def test_lf_equals_hash_order_on_regular_graphs():
+    # equal degrees everywhere: the largest-first key reduces to the hash key
+    for g in (gg.cycle(1000), gg.complete(30), gg.crown(20), gg.cycle(7)):
+        for seed in (1, 7):
+            a = oracle.det(g, seed)
+            b = oracle.det(g, seed, priority=oracle.PRIORITY_LARGEST_FIRST)
+            np.testing.assert_array_equal(a.colors, b.colors)
+            assert (a.rounds, a.ncolors) == (b.rounds, b.ncolors)
+
+
+def test_lf_tiny_graphs_brute_force():
+    rng = np.random.default_rng(17)
+    for trial in range(150):
+        n = int(rng.integers(1, 8))
+        p = rng.random()
+        edges = [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < p]
+        g = gg.from_edges(n, edges)
+        seed = int(rng.integers(0, 2**63))
+        r = oracle.det(g, seed, priority=oracle.PRIORITY_LARGEST_FIRST)
+        adj = [list(g.colidx[g.rowptr[v]:g.rowptr[v + 1]]) for v in range(n)]
+        h = oracle.keys(seed, n)
+        deg = g.degrees()
+        lit, lr = _literal_rounds(n, adj, lambda v: (-int(deg[v]), int(h[v]), v))
+        assert list(r.colors) == lit and r.rounds == lr
+        assert _chromatic_number(n, edges) <= r.ncolors <= g.max_degree + 1

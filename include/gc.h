@@ -101,7 +101,10 @@ typedef struct gc_options {
     int32_t chunk;             /* adjacency entries per warp work item for larger vertices (32..1024, multiple of 32);
                                   default 512 (deterministic), 1024 (in-place) */
     int32_t block_size;        /* threads per block of the round kernel (256 is the only size); default 256 */
-    int32_t blocks_per_sm;     /* resident blocks per SM for the round kernel; 0 = occupancy maximum */
+    int32_t blocks_per_sm;     /* resident blocks per SM for the round kernel.  0: the library picks the
+                                  80-register variant (3 blocks per SM) when most adjacency entries are
+                                  in vertices of degree > small_max_degree, else the 64-register one (4);
+                                  3 or 4: that variant; 1 or 2: the 64-register one, capped */
     int64_t spin_limit_ns;     /* grid-barrier wait limit in ns; 0 = 1e9.  A wait that runs out makes
                                   the call return GC_ERR_TIMEOUT with the device still usable */
     uint32_t flags;            /* GC_FLAG_* */

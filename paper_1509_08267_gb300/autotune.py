@@ -109,22 +109,35 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=TABLE)
     ap.add_argument("--quick", action="store_true", help="one sample per class, fewer knobs")
+    ap.add_argument("--batch-sample", default="batch256",
+                    help="batch the 'batch' entry is tuned on: batchG = G mixed graphs (seed 3)")
+    ap.add_argument("--only-batch", action="store_true", help="tune only the 'batch' entry (others kept)")
     args = ap.parse_args()
     dev = torch.device("cuda", 0)
 
     def on_device(g):
         return torch.from_numpy(g.rowptr).to(dev), torch.from_numpy(g.colidx).to(dev)
 
-    samples = {}
-    for cls, make in [("powerlaw-large", lambda: gg.workload("rmat20")), ("uniform-large", lambda: gg.stencil27(96)),
-                      ("uniform-small", lambda: gg.workload("er10k")), ("powerlaw-small", lambda: gg.rmat(16, 12, 5))]:
-        g = make()
-        rp, ci = on_device(g)
-        samples[cls] = (lambda rp, ci: (lambda cfg: time_config(rp, ci, cfg)))(rp, ci)
     grid = GRID if not args.quick else {"small_max_degree": [63, 127], "chunk": [512, 1024], "blocks_per_sm": [0],
                                         "compact": [False, True]}
-    table = tune(samples, grid)
-    b = gg.batch_mix(256, 3)
+    table = {}
+    if args.only_batch:
+        try:
+            with open(args.out) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+    else:
+        samples = {}
+        for cls, make in [("powerlaw-large", lambda: gg.workload("rmat20")),
+                          ("uniform-large", lambda: gg.stencil27(96)),
+                          ("uniform-small", lambda: gg.workload("er10k")),
+                          ("powerlaw-small", lambda: gg.rmat(16, 12, 5))]:
+            g = make()
+            rp, ci = on_device(g)
+            samples[cls] = (lambda rp, ci: (lambda cfg: time_config(rp, ci, cfg)))(rp, ci)
+        table = tune(samples, grid)
+    b = gg.batch_mix(int(args.batch_sample[len("batch"):]), 3)
     bargs = [torch.from_numpy(a).to(dev) for a in (b.vtx_off, b.edge_off, b.rowptr, b.colidx)]
     bt = tune({"batch": lambda cfg: time_config_batch(bargs, cfg)}, grid)
     table.update(bt)

@@ -90,7 +90,7 @@ struct Context {
     std::mutex mu;
     cudaStream_t stream = nullptr;
     int sms = 0;
-    int occ[2][2][2] = {};  // [mode][batch][compact] blocks per SM of the round kernel
+    int occ[2][2][2][2] = {};  // [wide][mode][batch][compact] blocks per SM of the round kernel
     int occ_part = 0;       // blocks per SM of the partition-mode round kernel
     Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, lists, ctl, stats, bitmap, vg;
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
@@ -359,16 +359,22 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     GC_CUDA(launch_expand(P, mode, pb.batch, compact, static_cast<int32_t>(n_items), s));
     if (timing) GC_CUDA(cudaEventRecord(C.ev[1], s));
 
+    // kernel variant: the 80-register one (3 blocks per SM) when most adjacency entries belong to
+    // larger vertices, whose warp sweep keeps more in registers; the 64-register one (4 blocks per
+    // SM, more warps) when most are swept one thread per vertex.  blocks_per_sm = 3 or 4 picks one.
+    const int bps_opt = opt ? opt->blocks_per_sm : 0;
+    const bool wide = bps_opt == 3 || (bps_opt == 0 && 2 * static_cast<int64_t>(n_chunks) * CH >= pb.nnz &&
+                                       n_chunks > 0);
     // persistent grid: every block resident; no more blocks than the first round can use
-    int &occ = C.occ[mode][pb.batch ? 1 : 0][compact ? 1 : 0];
-    if (occ == 0) GC_CUDA(round_kernel_occupancy(mode, pb.batch, compact, block, &occ));
+    int &occ = C.occ[wide ? 1 : 0][mode][pb.batch ? 1 : 0][compact ? 1 : 0];
+    if (occ == 0) GC_CUDA(round_kernel_occupancy(mode, pb.batch, compact, block, &occ, wide));
     int per_sm = occ;
-    if (opt && opt->blocks_per_sm > 0 && opt->blocks_per_sm < per_sm) per_sm = opt->blocks_per_sm;
+    if (bps_opt > 0 && bps_opt < per_sm) per_sm = bps_opt;
     grid = static_cast<int64_t>(per_sm) * C.sms;
     const int64_t want = (static_cast<int64_t>(n_small) + 32 * static_cast<int64_t>(n_chunks) + block - 1) / block;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
-    GC_CUDA(launch_rounds(P, mode, pb.batch, compact, static_cast<int>(grid), block, s));
+    GC_CUDA(launch_rounds(P, mode, pb.batch, compact, static_cast<int>(grid), block, s, wide));
     }
     if (timing) GC_CUDA(cudaEventRecord(C.ev[2], s));
 

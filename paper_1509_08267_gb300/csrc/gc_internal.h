@@ -132,9 +132,12 @@ cudaError_t launch_expand(const RoundParams &P, int mode, bool batch, bool compa
                           cudaStream_t s);
 // compact (deterministic mode only): larger vertices sweep packed lists of the neighbours that can
 // still change instead of their whole rows.
+// wide: the round-kernel variant compiled for 3 resident blocks per SM (80 registers a thread)
+// instead of 4 (64): for graphs whose adjacency entries are mostly in larger vertices.
 cudaError_t launch_rounds(const RoundParams &P, int mode, bool batch, bool compact, int grid, int block,
-                          cudaStream_t s);
-cudaError_t round_kernel_occupancy(int mode, bool batch, bool compact, int block, int *blocks_per_sm);
+                          cudaStream_t s, bool wide = false);
+cudaError_t round_kernel_occupancy(int mode, bool batch, bool compact, int block, int *blocks_per_sm,
+                                   bool wide = false);
 // Distinct colors and largest color per graph over vertices [v_begin, v_end) (graphs g_begin..g_end-1).
 // `colors_sel` != NULL: read colors from col1 when *colors_sel is odd (the deterministic buffer
 // that the last round wrote), else from col0.  `out` != NULL receives the colors of

@@ -33,9 +33,11 @@ constexpr int kPer = kStep / 32;  // entries per lane per step
 #define GC_MERGE_NOW_ITEMS 2  // deterministic rounds with at most this many items per warp finish
 #endif                        // several-item vertices without a second barrier
 constexpr unsigned kMergeNowItems = GC_MERGE_NOW_ITEMS;
-#ifndef GC_ROUND_MIN_BLOCKS
-#define GC_ROUND_MIN_BLOCKS 4  // resident blocks per SM the round kernel is compiled for
-#endif
+// The round kernels come in two register budgets: compiled for 4 resident blocks per SM (64
+// registers a thread; more warps, for graphs whose work is mostly one thread per vertex) and for 3
+// (80 registers; fewer spills in the warp work-item sweep, for graphs whose entries are mostly in
+// larger vertices).
+constexpr int kNarrowBlocks = 4, kWideBlocks = 3;
 
 // ------------------------------------------------------------------------------------------
 // priority key: key(v) = (h(v), v), h(v) = SplitMix64 output number v of the stream `seed`
@@ -522,7 +524,6 @@ struct DetItem {
     int32_t pad[2];
 };
 static_assert(sizeof(DetItem) == kItemBytes, "work-item size");
-constexpr int kItemWords = static_cast<int>(kItemBytes / 4);
 constexpr uint32_t kItemRewrite = 1u << 31;  // the items also copy the entries still active to the other region
 constexpr uint32_t kItemMulti = 1u << 30;    // the vertex has several items this round
 constexpr uint32_t kItemSlot = kItemMulti - 1u;
@@ -1044,8 +1045,8 @@ __device__ __forceinline__ void flush_stats(const RoundParams &P, int pass, unsi
 // Deterministic rounds.  Phase A: the work items of larger vertices, then one thread per vertex of
 // degree <= T1.  Phase B (only in rounds where some vertex has several items, after a grid barrier):
 // those vertices are finished from their merged slots, one lane each.
-template <bool BATCH, bool COMPACT>
-__global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(RoundParams P) {
+template <bool BATCH, bool COMPACT, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) det_round_kernel(RoundParams P) {
     __shared__ unsigned s_win[kMaxWarps][kAccWords];
     // per warp: the window of final neighbours found by the current item, then the item's snapshots
     // of its slot's round window and final window
@@ -1134,8 +1135,8 @@ __global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) det_round_kernel(
     }
 }
 
-template <bool BATCH>
-__global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) ip_round_kernel(RoundParams P) {
+template <bool BATCH, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) ip_round_kernel(RoundParams P) {
     __shared__ unsigned s_win[kMaxWarps][kAccWords];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nw = gridDim.x * (blockDim.x >> 5);
@@ -1509,7 +1510,7 @@ __device__ __forceinline__ int32_t part_first_fit(const RoundParams &P, const ui
 // take First Fit one after another in id order.  Grid barrier.  Phase 2: a worklist vertex is
 // re-queued when a neighbour in a higher block has its color (the lower block recolors).  Grid
 // barrier.  Colors live in col0 (current) and col1 (as the round began); small0[v] = r puts v on W_r.
-__global__ void __launch_bounds__(kBlock, GC_ROUND_MIN_BLOCKS) part_round_kernel(RoundParams P, int32_t p) {
+__global__ void __launch_bounds__(kBlock, kNarrowBlocks) part_round_kernel(RoundParams P, int32_t p) {
     __shared__ unsigned s_win[kMaxWarps][kAccWords];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nw = gridDim.x * (blockDim.x >> 5);
@@ -1768,33 +1769,40 @@ cudaError_t launch_expand(const RoundParams &P, int mode, bool batch, bool compa
     return cudaGetLastError();
 }
 
-static const void *round_kernel_fn(int mode, bool batch, bool compact) {
+template <int MINB>
+static const void *round_kernel_variant(int mode, bool batch, bool compact) {
     if (mode == GC_MODE_DETERMINISTIC) {
         if (batch)
-            return compact ? reinterpret_cast<const void *>(&det_round_kernel<true, true>)
-                           : reinterpret_cast<const void *>(&det_round_kernel<true, false>);
-        return compact ? reinterpret_cast<const void *>(&det_round_kernel<false, true>)
-                       : reinterpret_cast<const void *>(&det_round_kernel<false, false>);
+            return compact ? reinterpret_cast<const void *>(&det_round_kernel<true, true, MINB>)
+                           : reinterpret_cast<const void *>(&det_round_kernel<true, false, MINB>);
+        return compact ? reinterpret_cast<const void *>(&det_round_kernel<false, true, MINB>)
+                       : reinterpret_cast<const void *>(&det_round_kernel<false, false, MINB>);
     }
-    return batch ? reinterpret_cast<const void *>(&ip_round_kernel<true>)
-                 : reinterpret_cast<const void *>(&ip_round_kernel<false>);
+    return batch ? reinterpret_cast<const void *>(&ip_round_kernel<true, MINB>)
+                 : reinterpret_cast<const void *>(&ip_round_kernel<false, MINB>);
 }
 
-cudaError_t round_kernel_occupancy(int mode, bool batch, bool compact, int block, int *blocks_per_sm) {
+static const void *round_kernel_fn(int mode, bool batch, bool compact, bool wide) {
+    return wide ? round_kernel_variant<kWideBlocks>(mode, batch, compact)
+                : round_kernel_variant<kNarrowBlocks>(mode, batch, compact);
+}
+
+cudaError_t round_kernel_occupancy(int mode, bool batch, bool compact, int block, int *blocks_per_sm, bool wide) {
     if (block != kBlock) return cudaErrorInvalidValue;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, round_kernel_fn(mode, batch, compact), block,
-                                                         0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, round_kernel_fn(mode, batch, compact, wide),
+                                                         block, 0);
 }
 
 cudaError_t launch_rounds(const RoundParams &P, int mode, bool batch, bool compact, int grid, int block,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool wide) {
     if (block != kBlock) return cudaErrorInvalidValue;
     // the grid barrier counts this launch's arrivals from zero
     cudaError_t e = cudaMemsetAsync(&P.bar->count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     RoundParams arg = P;
     void *args[] = {&arg};
-    return cudaLaunchCooperativeKernel(round_kernel_fn(mode, batch, compact), dim3(grid), dim3(block), args, 0, s);
+    return cudaLaunchCooperativeKernel(round_kernel_fn(mode, batch, compact, wide), dim3(grid), dim3(block), args, 0,
+                                       s);
 }
 
 cudaError_t launch_partition_init(const RoundParams &P, cudaStream_t s) {

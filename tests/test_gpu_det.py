@@ -201,3 +201,43 @@ def test_unknown_priority_rejected(gclib):
     with pytest.raises(gclib.GCError) as e:
         gclib.color(g.rowptr, g.colidx, "det", 1, options=gclib.Options(priority=9))
     assert e.value.status == gclib.GC_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("bps", [3, 4, 2])
+@pytest.mark.parametrize("make", [lambda: gg.rmat(14, 16, 2), lambda: gg.stencil27(12)])
+def test_kernel_variants_match_oracle(gclib, make, bps):
+    # 3: the 80-register variant; 4: the 64-register one; 2: the 64-register one with fewer blocks
+    assert_parity(gclib, make(), 7, options=gclib.Options(blocks_per_sm=bps))
+
+
+# ---------------------------------------------------------------------------------------------
+# colors past the 512-color window (the full-row rescan)
+
+def _clique_plus_er(k, n, d, seed):
+    """K_k on vertices 0..k-1 plus an Erdos-Renyi part on k..n-1 joined to the clique by random edges."""
+    rng = np.random.default_rng(seed)
+    edges = [(i, j) for i in range(k) for j in range(i + 1, k)]
+    m = int(n * d / 2)
+    u = rng.integers(0, n, m)
+    v = rng.integers(k, n, m)
+    edges += [(int(a), int(b)) for a, b in zip(u, v) if a != b]
+    return gg.from_edges(n, edges, name=f"K{k}+ER")
+
+
+@pytest.mark.parametrize("make", [lambda: gg.complete(600), lambda: gg.complete(1100),
+                                  lambda: _clique_plus_er(700, 20000, 12.0, 3)])
+@pytest.mark.parametrize("full", [False, True])
+def test_colors_beyond_window(gclib, make, full):
+    g = make()
+    opt = gclib.Options(flags=gclib.FLAG_FULL_SWEEP) if full else None
+    ref = assert_parity(gclib, g, 7, options=opt)
+    assert ref.ncolors > 512
+
+
+def test_colors_beyond_window_inplace(gclib):
+    g = _clique_plus_er(700, 20000, 12.0, 3)
+    rp, ci = _dev(g)
+    r = gclib.color(rp, ci, "inplace", 7)
+    c = r.colors.cpu().numpy()
+    assert oracle.count_conflicts(g, c) == 0
+    assert np.all(c <= g.degrees()) and r.ncolors >= 700

@@ -279,9 +279,9 @@ def color(rowptr, colidx, mode="det", seed: int = 0, out=None, options: Options 
 
 
 def color_batch(vtx_off, edge_off, rowptr, colidx, mode="det", seed: int = 0, out=None,
-                options: Options | None = None, stats: bool = False):
+                options: Options | None = None, stats: bool = False, round_cap: int = 1 << 16):
     """Colors G packed graphs in one launch (gc_color_batch_ex).  Returns (colors, ncolors[G], rounds[G]
-    [, Stats]) with per-graph arrays as numpy."""
+    [, Stats]) with per-graph arrays as numpy (Stats covers the whole batch, per round)."""
     lib = load()
     G = (vtx_off.numel() if _is_torch(vtx_off) else len(vtx_off)) - 1
     N = int(vtx_off[-1])
@@ -299,12 +299,21 @@ def color_batch(vtx_off, edge_off, rowptr, colidx, mode="det", seed: int = 0, ou
         opt = Options(**{**opt.__dict__, "flags": opt.flags | FLAG_STATS | FLAG_TIMING})
     copt = opt._c(_current_stream(vtx_off, rowptr, colidx, out))
     st = _Stats()
+    wl = np.zeros(round_cap, np.int64)
+    ds = np.zeros(round_cap, np.int64)
+    rn = np.zeros(round_cap, np.int64)
+    st.round_cap = round_cap
+    st.wl_size = wl.ctypes.data
+    st.wl_degsum = ds.ctypes.data
+    st.round_ns = rn.ctypes.data
     _check(lib.gc_color_batch_ex(G, pv, pe, prp, pci, _mode(mode), seed & ((1 << 64) - 1), pout, nc.ctypes.data,
                                  rd.ctypes.data, ctypes.byref(copt), ctypes.byref(st)))
     res = (ok if ok is not None else out, nc[:G], rd[:G])
     if stats:
+        k = min(st.rounds, round_cap)
         res = res + (Stats(st.rounds, st.ncolors, st.max_color, st.worklist_total, st.entries_scanned, st.kernel_ms,
-                           st.setup_ms, st.grid_blocks, st.block_size),)
+                           st.setup_ms, st.grid_blocks, st.block_size, wl[:k].copy(), ds[:k].copy(),
+                           rn[:k].copy()),)
     return res
 
 

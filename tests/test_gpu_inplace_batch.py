@@ -64,6 +64,24 @@ def test_batch_det_matches_oracle_per_graph(gclib):
         assert nc[i] == ref.ncolors and rd[i] == ref.rounds, (i, nc[i], ref.ncolors, rd[i], ref.rounds)
 
 
+def test_batch_round_statistics_are_sums_over_graphs(gclib):
+    # the batch's worklist in round r is the union of the graphs' worklists in round r
+    gs = _mixed_graphs()
+    b = gg.pack(gs)
+    _, _, rd, st = gclib.color_batch(_dev(b.vtx_off), _dev(b.edge_off), _dev(b.rowptr), _dev(b.colidx), "det", 7,
+                                     stats=True)
+    R = int(max(rd))
+    want_w = np.zeros(R, np.int64)
+    want_d = np.zeros(R, np.int64)
+    for g in gs:
+        ref = oracle.det(g, 7)
+        want_w[:len(ref.wl_size)] += ref.wl_size
+        want_d[:len(ref.wl_degsum)] += ref.wl_degsum
+    assert st.rounds == R
+    np.testing.assert_array_equal(st.wl_size, want_w)
+    np.testing.assert_array_equal(st.wl_degsum, want_d)
+
+
 def test_batch_host_arrays_and_empty_graphs(gclib):
     gs = [gg.empty(0), gg.complete(4), gg.empty(0), gg.cycle(5), gg.empty(0)]
     b = gg.pack(gs)

@@ -81,7 +81,6 @@ struct Ctl {
     int32_t gmax1, gcount1, glast1, pad1;
     int32_t pad2[2];
     GridBar bar;
-    unsigned deg_hist[256];  // degree counts and list positions of thread-per-vertex rows
 };
 static_assert(offsetof(Ctl, bar) % 128 == 0, "barrier alignment");
 
@@ -92,12 +91,12 @@ struct Context {
     int sms = 0;
     int occ[2][2][2][2] = {};  // [wide][mode][batch][compact] blocks per SM of the round kernel
     int occ_part = 0;       // blocks per SM of the partition-mode round kernel
-    Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, lists, ctl, stats, bitmap, vg;
+    Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, lists, ctl, stats, bitmap, vg, hist;
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
     Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     void release_all() {
-        Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &lists, &ctl, &stats, &bitmap,
+        Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &lists, &ctl, &stats, &bitmap, &hist,
                       &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors};
         for (Buf *b : all) b->release();
     }
@@ -250,6 +249,9 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     GC_TRY(ensure(C.items, 4 * n, "worklist"));
     GC_TRY(ensure(C.ctl, sizeof(Ctl), "control"));
     GC_TRY(ensure(C.bitmap, 4 * (n / 32 + 2), "color bitmap"));
+    const int32_t shift = sort_shift(n);
+    const size_t hist_words = 2 * static_cast<size_t>(sort_bins(static_cast<int32_t>(n), shift));
+    GC_TRY(ensure(C.hist, 4 * hist_words, "worklist sort"));
     if (stats_cap) GC_TRY(ensure(C.stats, 8 * (4 * static_cast<size_t>(stats_cap) + 1), "statistics"));
     const bool compact = mode == GC_MODE_DETERMINISTIC && !(flags & GC_FLAG_FULL_SWEEP);
     if (pb.batch) {
@@ -267,6 +269,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
     GC_CUDA(cudaMemsetAsync(&ctl->gmax1, 0xff, sizeof(int32_t), s));
     GC_CUDA(cudaMemsetAsync(C.bitmap.p, 0, 4 * (n / 32 + 2), s));
+    GC_CUDA(cudaMemsetAsync(C.hist.p, 0, 4 * hist_words / 2, s));
     if (stats_cap) GC_CUDA(cudaMemsetAsync(C.stats.p, 0, 8 * (4 * static_cast<size_t>(stats_cap) + 1), s));
 
     if (pb.batch) GC_CUDA(cudaMemsetAsync(C.gmax.p, 0xff, 4 * gz, s));
@@ -294,7 +297,8 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     P.tmp = ctl->tmp;
     P.list_total = compact ? &ctl->list_total : nullptr;
     P.list_alloc = compact ? &ctl->list_alloc : nullptr;
-    P.deg_hist = ctl->deg_hist;
+    P.deg_hist = C.hist.as<unsigned>();
+    P.sort_shift = shift;
     P.cnt = ctl->cnt;
     P.bar = &ctl->bar;
     P.err = ctl->err;

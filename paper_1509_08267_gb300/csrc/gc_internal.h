@@ -94,8 +94,10 @@ struct RoundParams {
     unsigned long long *list_alloc;   // compact mode: expand's allocation counter in the list pool
     int32_t slot_per_vertex;          // compact mode, 1: vertex V's slot is V and its list regions start
                                       // at 2 x its first entry (no allocation; the server's layout)
-    unsigned *deg_hist;               // [256] optional: setup counts thread-per-vertex rows per degree
-                                      // ([0, 128)); list positions per degree follow ([128, 256))
+    int32_t sort_shift;               // log2 of the vertex block of the thread-worklist sort (sort_shift(n))
+    unsigned *deg_hist;               // [2 * sort_bins(n)] optional: setup counts thread-per-vertex rows per
+                                      // (vertex block, degree) bin, zeroed by the caller; list positions per
+                                      // bin follow
     GridBar *bar;
     int32_t *err;              // [4] status, vertex, entry, extra
     int32_t *passes;           // [2] first round not executed by the last launch, last round executed
@@ -125,6 +127,10 @@ cudaError_t launch_setup(const RoundParams &P, int mode, bool batch, int32_t v_b
 // With P.deg_hist: writes the thread-per-vertex entries of [v_begin, v_end) (counted by setup) to
 // the current small list in increasing order of degree.  Without it, setup appended them already.
 cudaError_t launch_sort_small(const RoundParams &P, bool batch, int32_t v_begin, int32_t v_end, cudaStream_t s);
+// The thread-worklist sort's vertex-block size (log2) for n vertices, and its bins for vertex ids
+// below v_end (P.deg_hist holds twice as many words).
+int32_t sort_shift(int64_t n);
+int32_t sort_bins(int32_t v_end, int32_t shift);
 // Turns the n_items larger vertices found by setup into work items of round P.pass_begin
 // (n_items < 0: the count setup left in P.tmp[0] on the device).
 // compact: every larger vertex gets a persistent slot and list-pool space (deterministic mode).

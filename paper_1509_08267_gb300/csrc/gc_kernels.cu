@@ -1223,6 +1223,11 @@ __global__ void batch_tables_kernel(RoundParams P, const int64_t *vtx_off, const
 // current small list) and larger vertices (collected in P.items, counted in P.tmp, expanded into
 // work items by expand_kernel).  Checks each row: 0 <= rowptr[v] <= rowptr[v+1] <= entries of its
 // graph, rowptr of a graph's first vertex = 0, of its last vertex's end = its entries.
+// Sort bins of the initial thread worklist: (vertex block of 2^P.sort_shift ids, degree).
+__device__ __forceinline__ int32_t sort_bin(const RoundParams &P, int32_t V, int64_t d) {
+    return (V >> P.sort_shift) * 128 + static_cast<int32_t>(d);
+}
+
 // Row of vertex V for set-up: its entry range, checked (0 <= rowptr[v] <= rowptr[v+1] <= entries of
 // its graph, 0 at a graph's first vertex, the graph's entry count at its end).  g: V's graph (batch).
 // Returns the degree, or -1 for a malformed row.
@@ -1252,21 +1257,18 @@ __device__ __forceinline__ int64_t checked_degree(const RoundParams &P, int32_t 
 // initial colors, and the round's worklist split into thread-per-vertex entries and larger vertices
 // (collected in P.items, counted in P.tmp, expanded into work items by expand_kernel).  Checks each
 // row.  Thread-per-vertex entries are appended to the current small list, or, when P.deg_hist is
-// set, only counted per degree (P.deg_hist[d]) for sort_small_kernel and scatter_small_kernel,
-// which write the list in increasing order of degree (so that the 32 rows a warp sweeps side by
-// side have similar lengths).
+// set, only counted per (vertex block, degree) for sort_small_kernel and scatter_small_kernel,
+// which write the list block by block (2^P.sort_shift consecutive ids each) and by increasing
+// degree inside a block: the 32 rows a warp sweeps side by side have similar lengths, and when the
+// state words do not fit in L2 (large graphs, batches) the vertices in flight at any moment (and,
+// in a batch, their graphs' neighbours) stay within a few blocks whose state words L2 holds.
 template <bool BATCH, int MODE>
 __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int32_t g_fixed) {
-    __shared__ unsigned s_hist[128];
     const int lane = threadIdx.x & 31;
     const int pass = P.pass_begin;
     unsigned *cc = P.cnt + kCnt * (pass % 3);
     int32_t *small_cur = (pass & 1) ? P.small0 : P.small1;
     const bool sort = P.deg_hist != nullptr;
-    if (sort) {
-        for (int t = threadIdx.x; t < 128; t += blockDim.x) s_hist[t] = 0;
-        __syncthreads();
-    }
     const int64_t count = static_cast<int64_t>(v_end) - v_begin;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t base = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ll; base < count;
@@ -1310,7 +1312,7 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
             if (g_fixed >= 0 && kind != 0) note_graph_round(P, g_fixed, pass);
         }
         if (sort) {
-            if (kind == 1) atomicAdd(&s_hist[d], 1u);
+            if (kind == 1) atomicAdd(P.deg_hist + sort_bin(P, V, d), 1u);
         } else {
             warp_append(kind == 1, V, small_cur, cc + kCntSmall, lane);
         }
@@ -1334,41 +1336,48 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
             }
         }
     }
-    if (sort) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < 128; t += blockDim.x)
-            if (s_hist[t]) atomicAdd(P.deg_hist + t, s_hist[t]);
-    }
 }
 
-// One block of 128 threads: turns the degree counts into list positions (P.deg_hist[128 + d] =
-// first position of degree d, after the entries already on the current small list) and adds them
-// to the list's count.
-__global__ void sort_small_kernel(RoundParams P) {
-    __shared__ unsigned s[128];
+// One block of kSortThreads threads: turns the (vertex block, degree) counts P.deg_hist[0, nbins)
+// into list positions P.deg_hist[nbins + bin] (after the entries already on the current small
+// list, bins in increasing order) and adds them to the list's count.
+constexpr int kSortThreads = 1024;
+__global__ void __launch_bounds__(kSortThreads) sort_small_kernel(RoundParams P, int32_t nbins) {
+    __shared__ unsigned s[kSortThreads];
     const int t = threadIdx.x;
     unsigned *cc = P.cnt + kCnt * (P.pass_begin % 3);
-    const unsigned h = P.deg_hist[t];
-    s[t] = h;
+    const int32_t per = (nbins + kSortThreads - 1) / kSortThreads;
+    const int32_t b0 = t * per, b1 = min(nbins, b0 + per);
+    unsigned sum = 0;
+    for (int32_t i = b0; i < b1; ++i) sum += P.deg_hist[i];
+    s[t] = sum;
     __syncthreads();
-    for (int o = 1; o < 128; o <<= 1) {
+    for (int o = 1; o < kSortThreads; o <<= 1) {
         const unsigned x = t >= o ? s[t - o] : 0u;
         __syncthreads();
         s[t] += x;
         __syncthreads();
     }
     const unsigned base = cc[kCntSmall];
-    P.deg_hist[128 + t] = base + s[t] - h;
+    unsigned run = base + s[t] - sum;  // exclusive prefix of this thread's first bin
+    for (int32_t i = b0; i < b1; ++i) {
+        const unsigned h = P.deg_hist[i];
+        P.deg_hist[nbins + i] = run;
+        run += h;
+    }
     __syncthreads();
-    if (t == 127) cc[kCntSmall] = base + s[127];
+    if (t == kSortThreads - 1) cc[kCntSmall] = base + s[t];
 }
 
-// Writes the thread-per-vertex entries of [v_begin, v_end) at the positions sort_small_kernel
-// assigned (the same classification as setup_kernel; the order within one degree is arbitrary).
+// Writes the thread-per-vertex entries of [v_begin, v_end) (v_begin a multiple of the block size)
+// at the positions sort_small_kernel assigned, with the same classification as setup_kernel; the
+// order within one (vertex block, degree) bin is arbitrary.  Each iteration covers 256 consecutive
+// ids, all inside one vertex block.
 template <bool BATCH>
-__global__ void scatter_small_kernel(RoundParams P, int32_t v_begin, int32_t v_end) {
+__global__ void scatter_small_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int32_t nbins) {
     __shared__ unsigned s_cnt[128], s_base[128];
     int32_t *small_cur = (P.pass_begin & 1) ? P.small0 : P.small1;
+    const unsigned *cursor = P.deg_hist + nbins;
     const int64_t count = static_cast<int64_t>(v_end) - v_begin;
     for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < count;
          base += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -1386,8 +1395,9 @@ __global__ void scatter_small_kernel(RoundParams P, int32_t v_begin, int32_t v_e
         unsigned rank = 0;
         if (small) rank = atomicAdd(&s_cnt[d], 1u);
         __syncthreads();
+        const int32_t bin0 = sort_bin(P, static_cast<int32_t>(v_begin + base), 0);
         for (int t = threadIdx.x; t < 128; t += blockDim.x)
-            if (s_cnt[t]) s_base[t] = atomicAdd(P.deg_hist + 128 + t, s_cnt[t]);
+            if (s_cnt[t]) s_base[t] = atomicAdd(const_cast<unsigned *>(cursor) + bin0 + t, s_cnt[t]);
         __syncthreads();
         if (small) small_cur[s_base[d] + rank] = V;
         __syncthreads();
@@ -1731,14 +1741,24 @@ cudaError_t launch_setup(const RoundParams &P, int mode, bool batch, int32_t v_b
     return cudaGetLastError();
 }
 
+int32_t sort_shift(int64_t n) {
+    // one block (a plain degree sort) while both state buffers (16 bytes a vertex) fit well inside
+    // L2; blocks of 2^17 ids beyond that
+    return 16 * n <= (int64_t{96} << 20) ? 30 : 17;
+}
+
+int32_t sort_bins(int32_t v_end, int32_t shift) { return ((v_end >> shift) + 1) * 128; }
+
 cudaError_t launch_sort_small(const RoundParams &P, bool batch, int32_t v_begin, int32_t v_end, cudaStream_t s) {
     if (v_end <= v_begin || !P.deg_hist) return cudaSuccess;
-    sort_small_kernel<<<1, 128, 0, s>>>(P);
+    if (v_begin % 256 != 0) return cudaErrorInvalidValue;
+    const int32_t nbins = sort_bins(v_end, P.sort_shift);
+    sort_small_kernel<<<1, kSortThreads, 0, s>>>(P, nbins);
     const int grid = grid_for(static_cast<int64_t>(v_end) - v_begin, 256, sm_count() * 16);
     if (batch)
-        scatter_small_kernel<true><<<grid, 256, 0, s>>>(P, v_begin, v_end);
+        scatter_small_kernel<true><<<grid, 256, 0, s>>>(P, v_begin, v_end, nbins);
     else
-        scatter_small_kernel<false><<<grid, 256, 0, s>>>(P, v_begin, v_end);
+        scatter_small_kernel<false><<<grid, 256, 0, s>>>(P, v_begin, v_end, nbins);
     return cudaGetLastError();
 }
 

@@ -1264,11 +1264,18 @@ __device__ __forceinline__ int64_t checked_degree(const RoundParams &P, int32_t 
 // in a batch, their graphs' neighbours) stay within a few blocks whose state words L2 holds.
 template <bool BATCH, int MODE>
 __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int32_t g_fixed) {
+    __shared__ unsigned s_hist[128];
     const int lane = threadIdx.x & 31;
     const int pass = P.pass_begin;
     unsigned *cc = P.cnt + kCnt * (pass % 3);
     int32_t *small_cur = (pass & 1) ? P.small0 : P.small1;
     const bool sort = P.deg_hist != nullptr;
+    // one vertex block: a per-block histogram in shared memory, added to the global one at the end
+    const bool one_block = sort && (v_end - 1) >> P.sort_shift == 0;
+    if (one_block) {
+        for (int t = threadIdx.x; t < 128; t += blockDim.x) s_hist[t] = 0;
+        __syncthreads();
+    }
     const int64_t count = static_cast<int64_t>(v_end) - v_begin;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t base = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ll; base < count;
@@ -1311,8 +1318,13 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
         if constexpr (BATCH) {
             if (g_fixed >= 0 && kind != 0) note_graph_round(P, g_fixed, pass);
         }
-        if (sort) {
-            if (kind == 1) atomicAdd(P.deg_hist + sort_bin(P, V, d), 1u);
+        if (one_block) {
+            if (kind == 1) atomicAdd(&s_hist[d], 1u);
+        } else if (sort) {
+            // lanes with the same bin add once
+            const int32_t bin = kind == 1 ? sort_bin(P, V, d) : -1;
+            const unsigned same = __match_any_sync(kFull, bin);
+            if (kind == 1 && lane == __ffs(same) - 1) atomicAdd(P.deg_hist + bin, static_cast<unsigned>(__popc(same)));
         } else {
             warp_append(kind == 1, V, small_cur, cc + kCntSmall, lane);
         }
@@ -1335,6 +1347,11 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
                 if (lane == leader) atomicAdd(P.list_total, need);
             }
         }
+    }
+    if (one_block) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < 128; t += blockDim.x)
+            if (s_hist[t]) atomicAdd(P.deg_hist + t, s_hist[t]);
     }
 }
 

@@ -253,7 +253,10 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     const size_t hist_words = 2 * static_cast<size_t>(sort_bins(static_cast<int32_t>(n), shift));
     GC_TRY(ensure(C.hist, 4 * hist_words, "worklist sort"));
     if (stats_cap) GC_TRY(ensure(C.stats, 8 * (4 * static_cast<size_t>(stats_cap) + 1), "statistics"));
-    const bool compact = mode == GC_MODE_DETERMINISTIC && !(flags & GC_FLAG_FULL_SWEEP);
+    // compact sweep (larger vertices sweep lists of the neighbours that can still change): the
+    // default of both modes; in-place mode keeps the plain kernel when no vertex is larger than T1
+    // (it then has nothing to compact, and the plain kernel keeps more registers for the thread path)
+    bool compact = (mode == GC_MODE_DETERMINISTIC || mode == GC_MODE_INPLACE) && !(flags & GC_FLAG_FULL_SWEEP);
     if (pb.batch) {
         GC_TRY(ensure(C.vg, 4 * n, "graph ids"));
         GC_TRY(ensure(C.gmax, 4 * gz, "per-graph max"));
@@ -355,6 +358,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     GC_TRY(ensure(C.chunk0, kItemBytes * static_cast<size_t>(n_chunks), "work items"));
     GC_TRY(ensure(C.chunk1, kItemBytes * static_cast<size_t>(n_chunks), "work items"));
     GC_TRY(ensure(C.acc, 4 * kAccStride * static_cast<size_t>(n_items), "accumulators"));
+    if (mode == GC_MODE_INPLACE && n_items == 0) compact = false;
     if (compact) GC_TRY(ensure(C.lists, 4 * static_cast<size_t>(h.list_total), "neighbour lists"));
     P.chunk0 = C.chunk0.as<int4>();
     P.chunk1 = C.chunk1.as<int4>();

@@ -607,13 +607,13 @@ __device__ __forceinline__ int32_t next_items(const RoundParams &P, int64_t len,
 
 // Sweep of entries [lb, le) of a larger vertex's list with one warp, kStep entries per step (the
 // first step's entries are already in ul; the next step's are loaded before the current step's
-// gathers are consumed).  Every neighbour's color goes to the round window (lo: colors 0..63 per
-// lane, win: 64..511 shared by the warp) and a neighbour with the same color and a smaller key sets
-// `lose`.  COMPACT: a neighbour found final is also recorded in the window of final neighbours
-// (flo / wfin) and dropped; the entries still active are counted (survivors, lane 0) and, when
+// gathers are consumed).  WINDOW: every neighbour's color goes to the round window (lo: colors
+// 0..63 per lane, win: 64..511 shared by the warp).  CONFLICT: a neighbour with the same color and
+// a smaller key sets `lose`.  DROP: a neighbour found final is also recorded in the window of final
+// neighbours (flo / wfin) and dropped; the entries still active are counted (survivors, lane 0) and, when
 // `dst` is set, copied to dst at positions from *newlen (atomically when `shared_len`, else lane 0's
 // running count `written`).
-template <bool COMPACT>
+template <bool DROP, bool WINDOW = true, bool CONFLICT = true>
 __device__ __forceinline__ void sweep_item(const RoundParams &P, const Row &r, const uint64_t *colc,
                                            const int32_t *list, int64_t lb, int64_t le, int32_t (&ul)[kPer],
                                            int32_t *dst, unsigned *newlen, bool shared_len, int lane, int32_t cv,
@@ -642,17 +642,26 @@ __device__ __forceinline__ void sweep_item(const RoundParams &P, const Row &r, c
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int32_t c = color_of(w[q]);
-            const bool fin = COMPACT && j0 + lane + 32 * q < le && final_of(w[q]);
-            if (static_cast<unsigned>(c) < 64u) {
-                lo |= 1ull << c;
-                if (fin) flo |= 1ull << c;
-            } else if (static_cast<unsigned>(c) < 32u * kAccWords) {
-                atomicOr(&win[c >> 5], 1u << (c & 31));
-                if (fin) atomicOr(&wfin[c >> 5], 1u << (c & 31));
+            const bool fin = DROP && j0 + lane + 32 * q < le && final_of(w[q]);
+            if constexpr (WINDOW) {
+                if (static_cast<unsigned>(c) < 64u) {
+                    lo |= 1ull << c;
+                    if (fin) flo |= 1ull << c;
+                } else if (static_cast<unsigned>(c) < 32u * kAccWords) {
+                    atomicOr(&win[c >> 5], 1u << (c & 31));
+                    if (fin) atomicOr(&wfin[c >> 5], 1u << (c & 31));
+                }
+            } else if (fin) {
+                if (static_cast<unsigned>(c) < 64u)
+                    flo |= 1ull << c;
+                else if (static_cast<unsigned>(c) < 32u * kAccWords)
+                    atomicOr(&wfin[c >> 5], 1u << (c & 31));
             }
-            if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
-                                                  static_cast<uint32_t>(r.lv), P.seed);
-            if constexpr (COMPACT) {
+            if constexpr (CONFLICT) {
+                if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
+                                                      static_cast<uint32_t>(r.lv), P.seed);
+            }
+            if constexpr (DROP) {
                 const bool keep = j0 + lane + 32 * q < le && !fin;
                 const unsigned km = __ballot_sync(kFull, keep);
                 if (lane == 0) survivors += __popc(km);
@@ -864,7 +873,8 @@ __device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *c
     uint64_t lo = 0, flo = 0;
     bool lose = false;
     unsigned survivors = 0, written = 0;
-    sweep_item<COMPACT>(P, r, colc, d.list, d.lb, d.le, ul, dst, a + kAccNewLen, multi, lane, cv, pv, lo, win, flo,
+    sweep_item<COMPACT, true, true>(P, r, colc, d.list, d.lb, d.le, ul, dst, a + kAccNewLen, multi, lane, cv, pv, lo,
+                                    win, flo,
                         wfin, lose, survivors, written);
     if (lane == 0) st_read += static_cast<unsigned>(d.le - d.lb);
     lose = __any_sync(kFull, lose);
@@ -958,15 +968,17 @@ __device__ __forceinline__ void ip_small_assign(const RoundParams &P, uint64_t *
     col[V] = pack_state(first_free_128(mask0, mask1), pv, false);
 }
 
-// Phase 2 for a vertex of degree <= T1.
-template <bool BATCH>
-__device__ __forceinline__ bool ip_small_conflict(const RoundParams &P, const uint64_t *col, int32_t V, int32_t &deg) {
+// Phase 2 for a vertex of degree <= T1.  FINAL: a vertex that does not lose marks itself final
+// (the compact sweep drops final neighbours from lists).
+template <bool BATCH, bool FINAL = false>
+__device__ __forceinline__ bool ip_small_conflict(const RoundParams &P, uint64_t *col, int32_t V, int32_t &deg) {
     const Row r = load_row<BATCH>(P, V);
     deg = static_cast<int32_t>(r.e - r.b);
     const uint64_t self = load_state(col + V);
     uint64_t mask0 = 0, mask1 = 0;
     bool lose = false;
     sweep_small<BATCH, false, true>(P, r, col, color_of(self), prio_of(self), mask0, mask1, lose);
+    if (FINAL && !lose) col[V] = pack_state(color_of(self), prio_of(self), true);
     return lose;
 }
 
@@ -1014,6 +1026,184 @@ __device__ void ip_chunk_conflict(const RoundParams &P, const uint64_t *col, int
     if (nch > 1 && !merge_item<false>(P.acc + static_cast<size_t>(slot) * kAccStride, nch, lane, lo0, lo1, win, lose, 0u))
         return;
     if (lose) append_large<BATCH>(P, V, r, chunk_next, cnt_next, pass + 1, lane);
+}
+
+// ------------------------------------------------------------------------------------------
+// in-place mode with the compact sweep: work items are DetItem descriptors over each larger
+// vertex's list of neighbours that can still change, as in deterministic mode.  A vertex that does
+// not lose in phase 2 sets its FINAL bit (its color never changes again); later phase-2 sweeps drop
+// it from their lists after checking it (a neighbour that won this very round can still share the
+// color), and its color moves to the vertex's window of final neighbours, which phase 1 adds to
+// the round window.
+
+constexpr int kAccDone2 = 20;  // in-place compact: phase-2 work items finished
+
+// Phase 1 work item: First Fit over the live colors of the list's neighbours and the window of
+// final neighbours.
+template <bool BATCH>
+__device__ void ipc_item_assign(const RoundParams &P, uint64_t *col, const DetItem &d, unsigned *win, int lane,
+                                unsigned &st_read) {
+    const int32_t V = d.V;
+    const uint32_t slot = d.slotf & kItemSlot;
+    const bool multi = (d.slotf & kItemMulti) != 0;
+    unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
+    Row r;
+    r.b = 0;
+    r.e = 0;
+    r.vbase = d.vbase;
+    r.ng = d.ng;
+    r.lv = V - d.vbase;
+    r.g = 0;
+    int32_t ul[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int64_t j = static_cast<int64_t>(d.lb) + lane + 32 * q;
+        ul[q] = j < d.le ? __ldcg(d.list + j) : 0;
+    }
+    const unsigned fsnap = multi ? 0u : __ldcg(a + kAccFin + lane);
+    if (lane < kAccWords) win[lane] = 0;
+    __syncwarp();
+    uint64_t lo = 0, flo = 0;
+    bool lose = false;
+    unsigned survivors = 0, written = 0;
+    sweep_item<false, true, false>(P, r, col, d.list, d.lb, d.le, ul, nullptr, nullptr, false, lane, 0, 0, lo, win,
+                                   flo, nullptr, lose, survivors, written);
+    if (lane == 0) st_read += static_cast<unsigned>(d.le - d.lb);
+    unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
+    unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
+    __syncwarp();
+    unsigned f = fsnap;
+    if (multi) {
+        const unsigned w = lane == 0 ? lo0 : lane == 1 ? lo1 : (lane < kAccWords ? win[lane] : 0u);
+        if (lane < kAccWords && w) atomicOr(a + lane, w);
+        __syncwarp();
+        unsigned done = 0;
+        if (lane == 0) done = atom_add_acq_rel(a + kAccDone, 1u);
+        done = __shfl_sync(kFull, done, 0);
+        if (done != static_cast<unsigned>(d.nitems - 1)) return;
+        // the last item: the merged round window, then the slot's round window and count cleared
+        const unsigned x = __ldcg(a + lane);
+        f = __ldcg(a + kAccFin + lane);
+        lo0 = __shfl_sync(kFull, x, 0);
+        lo1 = __shfl_sync(kFull, x, 1);
+        if (lane >= 2 && lane < kAccWords) win[lane] = x;
+        __syncwarp();
+        if (lane < kAccWords) a[lane] = 0u;
+        if (lane == 0) a[kAccDone] = 0u;
+    }
+    if (lane >= kAccWords) f = 0u;
+    lo0 |= __shfl_sync(kFull, f, 0);
+    lo1 |= __shfl_sync(kFull, f, 1);
+    if (lane >= 2 && lane < kAccWords) win[lane] |= f;
+    __syncwarp();
+    int32_t nc = first_free(lo0, lo1, win);
+    if (nc < 0) nc = mex_from<BATCH>(P, col, load_row<BATCH>(P, V), win, lane, 32 * kAccWords);
+    if (lane == 0) col[V] = pack_state(nc, prio_of(load_state(col + V)), false);
+}
+
+// Phase 2 work item: conflict check over the list (a neighbour with the same color and a smaller
+// key re-queues the vertex); neighbours found final are dropped into the window of final
+// neighbours, and in a rewrite round the others are copied to the vertex's other list region.  The
+// item that finishes the vertex sets its FINAL bit or appends its next items.
+template <bool BATCH>
+__device__ void ipc_item_conflict(const RoundParams &P, uint64_t *col, const DetItem &d, unsigned *wfin,
+                                  unsigned *snapf, DetItem *next, unsigned *cnt_next, int pass, int lane,
+                                  unsigned items_now, unsigned warps, unsigned &st_deg, unsigned &st_cnt,
+                                  unsigned &st_read) {
+    const int32_t V = d.V;
+    const uint32_t slot = d.slotf & kItemSlot;
+    const bool multi = (d.slotf & kItemMulti) != 0;
+    unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
+    Row r;
+    r.b = 0;
+    r.e = 0;
+    r.vbase = d.vbase;
+    r.ng = d.ng;
+    r.lv = V - d.vbase;
+    r.g = 0;
+    int32_t ul[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int64_t j = static_cast<int64_t>(d.lb) + lane + 32 * q;
+        ul[q] = j < d.le ? __ldcg(d.list + j) : 0;
+    }
+    const uint64_t self = load_state(col + V);
+    const unsigned sm = __ldcg(a + 32 + lane);
+    if (lane < kAccWords) {
+        wfin[lane] = 0;
+        snapf[lane] = sm;
+    }
+    const int32_t cv = color_of(self);
+    const uint32_t pv = prio_of(self);
+    const int64_t deg = d.deg;
+    const unsigned src = __shfl_sync(kFull, sm, kAccSrc - 32);
+    const unsigned len = __shfl_sync(kFull, sm, kAccLen - 32);
+    const int64_t off = static_cast<int64_t>(__shfl_sync(kFull, sm, kAccOffLo - 32)) |
+                        (static_cast<int64_t>(__shfl_sync(kFull, sm, kAccOffHi - 32)) << 32);
+    int32_t *dst = (d.slotf & kItemRewrite) ? P.lists + off + (src == 1 ? deg : 0) : nullptr;
+    __syncwarp();
+    uint64_t lo = 0, flo = 0;
+    bool lose = false;
+    unsigned survivors = 0, written = 0;
+    sweep_item<true, false, true>(P, r, col, d.list, d.lb, d.le, ul, dst, a + kAccNewLen, multi, lane, cv, pv, lo,
+                                  nullptr, flo, wfin, lose, survivors, written);
+    if (lane == 0) st_read += static_cast<unsigned>(d.le - d.lb);
+    lose = __any_sync(kFull, lose);
+    const unsigned f0 = __reduce_or_sync(kFull, static_cast<unsigned>(flo));
+    const unsigned f1 = __reduce_or_sync(kFull, static_cast<unsigned>(flo >> 32));
+    __syncwarp();
+    const unsigned fw = lane == 0 ? f0 : lane == 1 ? f1 : (lane < kAccWords ? wfin[lane] : 0u);
+    unsigned surv = 0, nlen_w = 0;
+    if (multi) {
+        if (lane < kAccWords && (fw & ~snapf[lane])) atomicOr(a + kAccFin + lane, fw);
+        if (lane == 0 && survivors) atomicAdd(a + kAccSurv, survivors);
+        if (lane == 0 && lose) atomicOr(a + kAccFlag, 1u);
+        __syncwarp();
+        unsigned done = 0;
+        if (lane == 0) done = atom_add_acq_rel(a + kAccDone2, 1u);
+        done = __shfl_sync(kFull, done, 0);
+        if (done != static_cast<unsigned>(d.nitems - 1)) return;
+        const uint4 st = ldcg4(a + kAccFlag);  // flag, (phase-1 count), survivors, new length
+        lose = st.x != 0u;
+        surv = st.z;
+        nlen_w = st.w;
+        __syncwarp();
+        if (lane == 0) {
+            a[kAccFlag] = 0u;
+            a[kAccSurv] = 0u;
+            a[kAccNewLen] = 0u;
+            a[kAccDone2] = 0u;
+        }
+    } else {
+        const unsigned fx = lane < kAccWords ? (snapf[lane] | fw) : 0u;
+        if (lane < kAccWords && fx != snapf[lane]) a[kAccFin + lane] = fx;
+        surv = __shfl_sync(kFull, survivors, 0);
+        nlen_w = __shfl_sync(kFull, written, 0);
+    }
+    if (lane == 0) {
+        st_deg += static_cast<unsigned>(deg);
+        st_cnt += 1;
+    }
+    if (!lose) {
+        if (lane == 0) col[V] = pack_state(cv, pv, true);
+        return;
+    }
+    if constexpr (BATCH) {
+        if (lane == 0) note_graph_round(P, __ldg(P.vg + V), pass + 1);
+    }
+    const bool rewrite = dst != nullptr;
+    const unsigned nsrc = rewrite ? (src == 1 ? 2u : 1u) : src;
+    const unsigned nlen = rewrite ? nlen_w : len;
+    const bool nrw = 4ull * surv < 3ull * nlen;
+    const int32_t items = next_items(P, nlen, deg, items_now, warps);
+    if (lane == 0) {
+        a[kAccSrc] = nsrc;
+        a[kAccLen] = nlen;
+    }
+    const int32_t *list = nsrc == 0 ? d.list : P.lists + off + (nsrc == 2 ? deg : 0);
+    const int64_t per = (static_cast<int64_t>(nlen) + items - 1) / items;
+    append_items(next, cnt_next, lane, lane == 0 ? items : 0, list, V, slot, nrw ? kItemRewrite : 0u, nlen,
+                 per > 0 ? per : 1, d.vbase, d.ng, d.deg);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1135,9 +1325,10 @@ __global__ void __launch_bounds__(kBlock, MINB) det_round_kernel(RoundParams P) 
     }
 }
 
-template <bool BATCH, int MINB>
+template <bool BATCH, bool COMPACT, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) ip_round_kernel(RoundParams P) {
     __shared__ unsigned s_win[kMaxWarps][kAccWords];
+    __shared__ unsigned s_aux[kMaxWarps][COMPACT ? 2 * kAccWords : 1];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -1164,22 +1355,49 @@ __global__ void __launch_bounds__(kBlock, MINB) ip_round_kernel(RoundParams P) {
         int32_t *smalln = odd ? P.small1 : P.small0;
         const int4 *chunkc = odd ? P.chunk0 : P.chunk1;
         int4 *chunkn = odd ? P.chunk1 : P.chunk0;
+        unsigned st_deg = 0, st_cnt = 0, st_read = 0;  // this warp's share of the round (< 2^31 each)
         // phase 1: tentative First Fit on live colors
-        for (unsigned i = gw; i < nchunks; i += nw) ip_chunk_assign<BATCH>(P, col, __ldcg(chunkc + i), win, lane);
+        if constexpr (COMPACT) {
+            const DetItem *itc = reinterpret_cast<const DetItem *>(chunkc);
+            if (static_cast<unsigned>(gw) < nchunks) {
+                uint32_t w = item_word(itc, gw, lane);
+                for (unsigned i = gw; i < nchunks; i += nw) {
+                    const DetItem d = item_of(w);
+                    if (i + nw < nchunks) w = item_word(itc, i + nw, lane);
+                    ipc_item_assign<BATCH>(P, col, d, win, lane, st_read);
+                }
+            }
+        } else {
+            for (unsigned i = gw; i < nchunks; i += nw) ip_chunk_assign<BATCH>(P, col, __ldcg(chunkc + i), win, lane);
+        }
         for (unsigned i = gw * 32u + lane; i < nsmall; i += nw * 32u) ip_small_assign<BATCH>(P, col, __ldcg(smallc + i));
         if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
         // phase 2: conflict detection
-        unsigned st_deg = 0, st_cnt = 0;  // this warp's share of the round (< 2^31 each)
-        for (unsigned i = gw; i < nchunks; i += nw)
-            ip_chunk_conflict<BATCH>(P, col, __ldcg(chunkc + i), win, chunkn, cn, pass, lane, st_deg, st_cnt);
+        if constexpr (COMPACT) {
+            const DetItem *itc = reinterpret_cast<const DetItem *>(chunkc);
+            DetItem *itn = reinterpret_cast<DetItem *>(chunkn);
+            if (static_cast<unsigned>(gw) < nchunks) {
+                uint32_t w = item_word(itc, gw, lane);
+                for (unsigned i = gw; i < nchunks; i += nw) {
+                    const DetItem d = item_of(w);
+                    if (i + nw < nchunks) w = item_word(itc, i + nw, lane);
+                    ipc_item_conflict<BATCH>(P, col, d, s_aux[wib], s_aux[wib] + kAccWords, itn, cn, pass, lane,
+                                             nchunks, static_cast<unsigned>(nw), st_deg, st_cnt, st_read);
+                }
+            }
+        } else {
+            for (unsigned i = gw; i < nchunks; i += nw)
+                ip_chunk_conflict<BATCH>(P, col, __ldcg(chunkc + i), win, chunkn, cn, pass, lane, st_deg, st_cnt);
+        }
         for (unsigned base = gw * 32u; base < nsmall; base += nw * 32u) {
             const unsigned i = base + lane;
             bool lose = false;
             int32_t V = 0, deg = 0;
             if (i < nsmall) {
                 V = __ldcg(smallc + i);
-                lose = ip_small_conflict<BATCH>(P, col, V, deg);
+                lose = ip_small_conflict<BATCH, COMPACT>(P, col, V, deg);
                 st_deg += static_cast<unsigned>(deg);
+                st_read += 2u * static_cast<unsigned>(deg);
                 st_cnt += 1;
                 if constexpr (BATCH) {
                     if (lose) note_graph_round(P, __ldg(P.vg + V), pass + 1);
@@ -1187,7 +1405,7 @@ __global__ void __launch_bounds__(kBlock, MINB) ip_round_kernel(RoundParams P) {
             }
             warp_append(lose, V, smalln, cn + kCntSmall, lane);
         }
-        if (P.stats) flush_stats(P, pass, st_deg, st_cnt, 2ull * st_deg);
+        if (P.stats) flush_stats(P, pass, st_deg, st_cnt, COMPACT ? st_read : 2ull * st_deg);
         if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1443,7 +1661,7 @@ __global__ void expand_kernel(RoundParams P, int32_t n_items) {
         if (lane == 0) {
             slot = atomicAdd(cc + kCntItems, 1u);
             cb = atomicAdd(cc + kCntChunks, static_cast<unsigned>(nch));
-            if (MODE == GC_MODE_DETERMINISTIC && nch > 1) atomicAdd(cc + kCntMulti, 1u);
+            if ((MODE == GC_MODE_DETERMINISTIC || COMPACT) && nch > 1) atomicAdd(cc + kCntMulti, 1u);
         }
         slot = __shfl_sync(kFull, slot, 0);
         cb = __shfl_sync(kFull, cb, 0);
@@ -1464,7 +1682,7 @@ __global__ void expand_kernel(RoundParams P, int32_t n_items) {
             if (lane == kAccDeg - 32) hi = static_cast<unsigned>(deg);
         }
         a[32 + lane] = hi;
-        if constexpr (MODE == GC_MODE_DETERMINISTIC) {
+        if constexpr (MODE == GC_MODE_DETERMINISTIC || COMPACT) {
             DetItem *cur = reinterpret_cast<DetItem *>((pass & 1) ? P.chunk0 : P.chunk1);
             const int32_t per = COMPACT ? (deg + nch - 1) / nch : P.CH;
             const uint32_t slotf = slot | (nch > 1 ? kItemMulti : 0u);
@@ -1782,7 +2000,6 @@ cudaError_t launch_sort_small(const RoundParams &P, bool batch, int32_t v_begin,
 cudaError_t launch_expand(const RoundParams &P, int mode, bool batch, bool compact, int32_t n_items,
                           cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
-    if (compact && mode != GC_MODE_DETERMINISTIC) return cudaErrorInvalidValue;
     const int grid = n_items < 0 ? sm_count() * 8 : grid_for(static_cast<int64_t>(n_items) * 32, 256, sm_count() * 16);
     constexpr int D = GC_MODE_DETERMINISTIC, I = GC_MODE_INPLACE;
     if (mode == GC_MODE_DETERMINISTIC) {
@@ -1798,10 +2015,17 @@ cudaError_t launch_expand(const RoundParams &P, int mode, bool batch, bool compa
                 expand_kernel<false, false, D><<<grid, 256, 0, s>>>(P, n_items);
         }
     } else {
-        if (batch)
-            expand_kernel<true, false, I><<<grid, 256, 0, s>>>(P, n_items);
-        else
-            expand_kernel<false, false, I><<<grid, 256, 0, s>>>(P, n_items);
+        if (batch) {
+            if (compact)
+                expand_kernel<true, true, I><<<grid, 256, 0, s>>>(P, n_items);
+            else
+                expand_kernel<true, false, I><<<grid, 256, 0, s>>>(P, n_items);
+        } else {
+            if (compact)
+                expand_kernel<false, true, I><<<grid, 256, 0, s>>>(P, n_items);
+            else
+                expand_kernel<false, false, I><<<grid, 256, 0, s>>>(P, n_items);
+        }
     }
     return cudaGetLastError();
 }
@@ -1815,8 +2039,11 @@ static const void *round_kernel_variant(int mode, bool batch, bool compact) {
         return compact ? reinterpret_cast<const void *>(&det_round_kernel<false, true, MINB>)
                        : reinterpret_cast<const void *>(&det_round_kernel<false, false, MINB>);
     }
-    return batch ? reinterpret_cast<const void *>(&ip_round_kernel<true, MINB>)
-                 : reinterpret_cast<const void *>(&ip_round_kernel<false, MINB>);
+    if (batch)
+        return compact ? reinterpret_cast<const void *>(&ip_round_kernel<true, true, MINB>)
+                       : reinterpret_cast<const void *>(&ip_round_kernel<true, false, MINB>);
+    return compact ? reinterpret_cast<const void *>(&ip_round_kernel<false, true, MINB>)
+                   : reinterpret_cast<const void *>(&ip_round_kernel<false, false, MINB>);
 }
 
 static const void *round_kernel_fn(int mode, bool batch, bool compact, bool wide) {

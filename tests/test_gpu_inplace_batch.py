@@ -40,10 +40,28 @@ def test_inplace_invariants(gclib, make):
 
 
 def test_inplace_options(gclib):
+    # the compact sweep (default) with many items per vertex, many larger vertices and list rewrites;
+    # the full sweep; both kernel variants
     g = gg.rmat(13, 16, 2)
-    for opt in [dict(small_max_degree=2), dict(chunk=32), dict(blocks_per_sm=1)]:
+    for opt in [dict(small_max_degree=2), dict(chunk=32), dict(blocks_per_sm=1), dict(blocks_per_sm=3),
+                dict(blocks_per_sm=4), dict(flags=gclib.FLAG_FULL_SWEEP), dict(small_max_degree=1, chunk=64),
+                dict(flags=gclib.FLAG_FULL_SWEEP, chunk=32)]:
         r = gclib.color(_dev(g.rowptr), _dev(g.colidx), "inplace", 1, options=gclib.Options(**opt))
-        assert oracle.count_conflicts(g, r.colors.cpu().numpy()) == 0
+        c = r.colors.cpu().numpy()
+        assert oracle.count_conflicts(g, c) == 0, opt
+        assert np.all(c <= g.degrees()) and r.ncolors == oracle.distinct_colors(c), opt
+
+
+@pytest.mark.parametrize("make", [lambda: gg.rmat(16, 16, 4), lambda: gg.complete(1100), lambda: gg.star(70000)])
+def test_inplace_compact_stress(gclib, make):
+    # larger vertices with long lists: rewrites, several items per vertex, colors past 512
+    g = make()
+    for opt in [dict(), dict(small_max_degree=3, chunk=64)]:
+        r = gclib.color(_dev(g.rowptr), _dev(g.colidx), "inplace", 5, options=gclib.Options(**opt))
+        c = r.colors.cpu().numpy()
+        assert oracle.count_conflicts(g, c) == 0, opt
+        assert np.all(c <= g.degrees()) and r.ncolors == oracle.distinct_colors(c)
+        assert 1 <= r.rounds <= g.n
 
 
 def _mixed_graphs():

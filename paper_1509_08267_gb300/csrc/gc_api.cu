@@ -225,7 +225,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C.stream;
     const uint32_t flags = opt ? opt->flags : 0u;
     const int32_t T1 = (opt && opt->small_max_degree) ? opt->small_max_degree : 127;
-    const int32_t CH = (opt && opt->chunk) ? opt->chunk : (mode == GC_MODE_DETERMINISTIC ? 512 : 1024);
+    const int32_t CH = (opt && opt->chunk) ? opt->chunk : 1024;
     const int32_t block = (opt && opt->block_size) ? opt->block_size : 256;
     if (T1 < 1 || T1 > 127) return set_last_error(GC_ERR_INVALID_ARG, "small_max_degree %d outside 1..127", T1);
     if (CH < 32 || CH > 1024 || CH % 32) return set_last_error(GC_ERR_INVALID_ARG, "chunk %d invalid", CH);

@@ -51,6 +51,11 @@
  *       colors live and other blocks' colors as the round began; in phase 2 a vertex is re-queued
  *       when a neighbour in a higher block has its color.  The result is a function of the graph
  *       and p (seed unused); Lemma 2 bounds the rounds by p + 1.  gc_color / gc_color_ex only.
+ *   GC_MODE_ORDERED  No speculation: a vertex stays uncolored while a neighbour with a smaller
+ *       key is uncolored, then takes First Fit once (the order that Algorithm 3's neighbourhood
+ *       locks impose, as a wait rule instead of locks).  Colors equal sequential First Fit in
+ *       increasing key order (with GC_PRIORITY_LARGEST_FIRST: largest degree first); the number
+ *       of rounds depends on scheduling.
  */
 #ifndef GC_H
 #define GC_H
@@ -73,7 +78,7 @@ typedef enum {
     GC_ERR_BUSY = -7             /* server request still running (gc_server_poll) */
 } gc_status;
 
-enum { GC_MODE_DETERMINISTIC = 0, GC_MODE_INPLACE = 1, GC_MODE_PARTITION = 2 };
+enum { GC_MODE_DETERMINISTIC = 0, GC_MODE_INPLACE = 1, GC_MODE_PARTITION = 2, GC_MODE_ORDERED = 3 };
 
 /* Priority keys (which endpoint of a monochromatic edge keeps its color: the smaller key).
  *   GC_PRIORITY_HASH           key(v) = (h(v), v)
@@ -141,7 +146,7 @@ typedef struct gc_stats {
  *   n          number of vertices (>= 0)
  *   rowptr     int32[n+1]   CSR row offsets (device or host)
  *   colidx     int32[nnz]   CSR neighbour ids (device or host); may be NULL when nnz = 0
- *   mode       GC_MODE_DETERMINISTIC, GC_MODE_INPLACE or GC_MODE_PARTITION
+ *   mode       GC_MODE_DETERMINISTIC, GC_MODE_INPLACE, GC_MODE_PARTITION or GC_MODE_ORDERED
  *   seed       priority-hash seed (deterministic mode; in-place mode uses it for tie-breaks too)
  *   colors_out int32[n]     receives the colors (device or host)
  *   ncolors    host int32*  receives the number of distinct colors (may be NULL)

@@ -73,6 +73,8 @@ def _L():
         lib.oracle_det.argtypes = [i32, p, p, u64, i32, p, p, p, p, p, i32, p]
         lib.oracle_det_prio.restype = ctypes.c_int
         lib.oracle_det_prio.argtypes = [i32, p, p, u64, i32, i32, p, p, p, p, p, i32, p]
+        lib.oracle_greedy_keyorder.restype = i32
+        lib.oracle_greedy_keyorder.argtypes = [i32, p, p, u64, i32, p]
         lib.oracle_key_less_lf.restype = ctypes.c_int
         lib.oracle_key_less_lf.argtypes = [u64, i32, i32, i32, i32]
         lib.oracle_partition.restype = ctypes.c_int
@@ -161,6 +163,16 @@ PRIORITY_LARGEST_FIRST = 1
 def key_less_lf(seed: int, u: int, v: int, du: int, dv: int) -> bool:
     """Largest-first priority: u keeps its color against v (degrees capped at 2^20 - 1, ties by hash)."""
     return bool(_L().oracle_key_less_lf(seed & U64, u, v, du, dv))
+
+
+def greedy_keyorder(g, seed: int, priority: int = PRIORITY_HASH) -> tuple[np.ndarray, int]:
+    """Sequential First Fit in increasing key order (the hash key, or largest degree first)."""
+    rp, ci = _csr(g)
+    colors = np.empty(max(g.n, 1), dtype=np.int32)
+    k = _L().oracle_greedy_keyorder(g.n, rp.ctypes.data, ci.ctypes.data, seed & U64, int(priority), colors.ctypes.data)
+    if k < 0:
+        raise MemoryError("oracle_greedy_keyorder")
+    return colors[:g.n], int(k)
 
 
 def det(g, seed: int, max_rounds: int | None = None, stats_cap: int = 1 << 16,

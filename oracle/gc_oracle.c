@@ -138,6 +138,51 @@ int32_t oracle_greedy(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
     return used;
 }
 
+/* qsort context for oracle_greedy_keyorder (single-threaded use only) */
+static uint64_t g_ko_seed;
+static int32_t g_ko_priority;
+static const int32_t *g_ko_rowptr;
+static int ko_cmp(const void *a, const void *b) {
+    int32_t u = *(const int32_t *)a, v = *(const int32_t *)b;
+    if (u == v) return 0;
+    int less = g_ko_priority == 1 ? oracle_key_less_lf(g_ko_seed, u, v, g_ko_rowptr[u + 1] - g_ko_rowptr[u],
+                                                       g_ko_rowptr[v + 1] - g_ko_rowptr[v])
+                                  : oracle_key_less(g_ko_seed, u, v);
+    return less ? -1 : 1;
+}
+
+/* Sequential First Fit in increasing key order (priority 0: hash key, 1: largest degree first):
+ * the vertices are sorted by key, then each takes the least color its already-colored neighbours
+ * do not use.  Returns the number of colors (-1 on OOM). */
+int32_t oracle_greedy_keyorder(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed,
+                               int32_t priority, int32_t *colors) {
+    if (n <= 0) return 0;
+    int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    unsigned char *seen = (unsigned char *)calloc((size_t)max_degree(n, rowptr) + 2, 1);
+    if (!order || !seen) {
+        free(order);
+        free(seen);
+        return -1;
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        order[v] = v;
+        colors[v] = -1;
+    }
+    g_ko_seed = seed;
+    g_ko_priority = priority;
+    g_ko_rowptr = rowptr;
+    qsort(order, (size_t)n, sizeof(int32_t), ko_cmp);
+    int32_t used = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t v = order[i];
+        colors[v] = first_fit(v, rowptr, colidx, colors, seen);
+        if (colors[v] + 1 > used) used = colors[v] + 1;
+    }
+    free(order);
+    free(seen);
+    return used;
+}
+
 /*
  * Deterministic speculative coloring (Algorithm 1, one vertex per partition, hash priority).
  *

@@ -18,7 +18,7 @@ import numpy as np
 
 __all__ = [
     "GCError", "load", "color", "color_batch", "validate", "Options", "Stats", "Server", "MODE_DETERMINISTIC",
-    "MODE_INPLACE", "MODE_PARTITION", "PRIORITY_HASH", "PRIORITY_LARGEST_FIRST", "version", "release_scratch",
+    "MODE_INPLACE", "MODE_PARTITION", "MODE_ORDERED", "PRIORITY_HASH", "PRIORITY_LARGEST_FIRST", "version", "release_scratch",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -38,6 +38,7 @@ STATUS_NAMES = {0: "GC_OK", -1: "GC_ERR_INVALID_ARG", -2: "GC_ERR_INVALID_GRAPH"
 MODE_DETERMINISTIC = 0
 MODE_INPLACE = 1
 MODE_PARTITION = 2
+MODE_ORDERED = 3
 PRIORITY_HASH = 0
 PRIORITY_LARGEST_FIRST = 1
 FLAG_STATS = 1
@@ -229,7 +230,7 @@ class Stats:
 
 def _mode(mode) -> int:
     if isinstance(mode, str):
-        return {"det": 0, "deterministic": 0, "inplace": 1, "in-place": 1, "partition": 2}[mode]
+        return {"det": 0, "deterministic": 0, "inplace": 1, "in-place": 1, "partition": 2, "ordered": 3}[mode]
     return int(mode)
 
 

@@ -221,6 +221,9 @@ struct Outputs {
 
 static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_options *opt, gc_stats *stats,
                const Outputs &out) {
+    // ordered mode runs the deterministic kernels with one state array and the wait rule
+    const bool ordered = mode == GC_MODE_ORDERED;
+    if (ordered) mode = GC_MODE_DETERMINISTIC;
     const int dev = C.device;
     cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C.stream;
     const uint32_t flags = opt ? opt->flags : 0u;
@@ -293,7 +296,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     }
     P.seed = seed;
     P.col0 = C.col0.as<uint64_t>();
-    P.col1 = C.col1.as<uint64_t>();
+    P.col1 = ordered ? P.col0 : C.col1.as<uint64_t>();
     P.small0 = C.small0.as<int32_t>();
     P.small1 = C.small1.as<int32_t>();
     P.items = C.items.as<int32_t>();
@@ -316,6 +319,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     P.T1 = T1;
     P.CH = CH;
     P.priority = priority;
+    P.ordered = ordered ? 1 : 0;
 
     const bool timing = (flags & GC_FLAG_TIMING) != 0;
     Ctl h{};
@@ -492,7 +496,8 @@ static int color_single(int32_t n, const int32_t *rowptr, const int32_t *colidx,
                         int32_t *colors_out, int32_t *ncolors, int32_t *rounds, const gc_options *opt,
                         gc_stats *stats) {
     if (n < 0) return set_last_error(GC_ERR_INVALID_ARG, "n = %d is negative", n);
-    if (mode != GC_MODE_DETERMINISTIC && mode != GC_MODE_INPLACE && mode != GC_MODE_PARTITION)
+    if (mode != GC_MODE_DETERMINISTIC && mode != GC_MODE_INPLACE && mode != GC_MODE_PARTITION &&
+        mode != GC_MODE_ORDERED)
         return set_last_error(GC_ERR_INVALID_ARG, "unknown mode %d", mode);
     if (n > 0 && (!rowptr || !colors_out)) return set_last_error(GC_ERR_INVALID_ARG, "NULL rowptr or colors_out");
     if (n == INT32_MAX) return set_last_error(GC_ERR_INVALID_ARG, "n too large");
@@ -555,7 +560,7 @@ static int color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_of
                        const int32_t *colidx, int mode, uint64_t seed, int32_t *colors_out, int32_t *ncolors,
                        int32_t *rounds, const gc_options *opt, gc_stats *stats) {
     if (G < 0) return set_last_error(GC_ERR_INVALID_ARG, "G = %d is negative", G);
-    if (mode != GC_MODE_DETERMINISTIC && mode != GC_MODE_INPLACE)
+    if (mode != GC_MODE_DETERMINISTIC && mode != GC_MODE_INPLACE && mode != GC_MODE_ORDERED)
         return set_last_error(GC_ERR_INVALID_ARG, "unknown mode %d", mode);
     if (G > 0 && (!vtx_off || !edge_off)) return set_last_error(GC_ERR_INVALID_ARG, "NULL offset table");
     Context *C = nullptr;

@@ -112,6 +112,9 @@ struct RoundParams {
     int32_t T1;  // largest degree handled by one thread
     int32_t CH;  // adjacency entries per warp work item
     int32_t priority;  // GC_PRIORITY_*: what the 31 priority bits of a state word hold
+    int32_t ordered;   // GC_MODE_ORDERED on the deterministic kernels: a worklist vertex is uncolored and
+                       // waits while a neighbour with a smaller key is uncolored (the conflict test
+                       // against its own color -1), then takes First Fit once; col1 is col0
 };
 
 // Launch wrappers (gc_kernels.cu).  All return the launch's cudaError_t.

@@ -150,7 +150,7 @@ __device__ bool grid_sync(GridBar *bar, unsigned &target, int32_t *err, int64_t 
 
 // State word: bits 0..31 color (int32, -1 = uncolored), bit 32 FINAL (the vertex left the worklist
 // for good), bits 33..63 the top 31 bits of the vertex's priority hash h(v).
-constexpr uint64_t kNoNeighbour = 0x00000000FFFFFFFFull;  // color -1: forbids nothing, never equal
+constexpr uint64_t kNoNeighbour = 0x000000007FFFFFFFull;  // color 2^31-1: past every window, equal to no color
 constexpr uint64_t kFinalBit = 1ull << 32;
 
 __device__ __forceinline__ uint64_t pack_state(int32_t color, uint32_t prio31, bool final_) {
@@ -485,8 +485,14 @@ __device__ __forceinline__ bool merge_item(unsigned *a, int nch, int lane, unsig
 // Writes a vertex's state for the next round.  A vertex that did not lose is final: its color will
 // not change again, so the FINAL bit goes into both buffers (the color and priority bits are the
 // ones already there, so a concurrent reader of the current buffer sees the same color either way).
+// Ordered mode (both buffers are one array): a vertex that does not wait takes color nc, final; a
+// waiting one stays uncolored.
 __device__ __forceinline__ void det_write(const uint64_t *colc, uint64_t *coln, int32_t V, bool lose, int32_t cv,
-                                          int32_t nc, uint32_t pv) {
+                                          int32_t nc, uint32_t pv, bool ordered) {
+    if (ordered) {
+        if (!lose) coln[V] = pack_state(nc, pv, true);
+        return;
+    }
     if (lose) {
         coln[V] = pack_state(nc, pv, false);
     } else {
@@ -508,7 +514,8 @@ __device__ __forceinline__ bool det_small(const RoundParams &P, const uint64_t *
     uint64_t mask0 = 0, mask1 = 0;
     bool lose = false;
     sweep_small<BATCH, true, true>(P, r, colc, cv, pv, mask0, mask1, lose);
-    det_write(colc, coln, V, lose, cv, lose ? first_free_128(mask0, mask1) : cv, pv);
+    const bool pick = lose != (P.ordered != 0);  // a new color: a loser (deterministic), a ready vertex (ordered)
+    det_write(colc, coln, V, lose, cv, pick ? first_free_128(mask0, mask1) : cv, pv, P.ordered != 0);
     return lose;
 }
 
@@ -760,17 +767,18 @@ __device__ __forceinline__ void det_finish(const RoundParams &P, const uint64_t 
         }
     }
     const bool lose = fin && st.x != 0u;
+    const bool pick = fin && (lose != (P.ordered != 0));
     const int32_t cv = color_of(self);
     const uint32_t pv = prio_of(self);
     int32_t nc = cv;
-    if (lose) {
+    if (pick) {
         nc = -1;
 #pragma unroll
         for (int c = 0; c < kAccWords / 4; ++c)
             if (nc < 0) nc = first_free4(w[c], 128 * c);
     }
     // rare: all of colors 0..511 taken; the warp rescans each such row in full
-    unsigned need = __ballot_sync(kFull, lose && nc < 0);
+    unsigned need = __ballot_sync(kFull, pick && nc < 0);
     while (need) {
         const int l = __ffs(need) - 1;
         need &= need - 1;
@@ -779,7 +787,7 @@ __device__ __forceinline__ void det_finish(const RoundParams &P, const uint64_t 
         if (lane == l) nc = x;
     }
     if (fin) {
-        det_write(colc, coln, V, lose, cv, nc, pv);
+        det_write(colc, coln, V, lose, cv, nc, pv, P.ordered != 0);
         st_deg += static_cast<unsigned>(deg);
         st_cnt += 1;
         const uint4 z = make_uint4(0, 0, 0, 0);
@@ -923,11 +931,11 @@ __device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *c
         __syncwarp();
     }
     int32_t nc = cv;
-    if (lose) {
+    if (lose != (P.ordered != 0)) {
         nc = first_free(lo0, lo1, win);
         if (nc < 0) nc = mex_from<BATCH>(P, colc, load_row<BATCH>(P, V), win, lane, 32 * kAccWords);
     }
-    if (lane == 0) det_write(colc, coln, V, lose, cv, nc, pv);
+    if (lane == 0) det_write(colc, coln, V, lose, cv, nc, pv, P.ordered != 0);
     if (!lose) return;
     if constexpr (BATCH) {
         if (lane == 0) note_graph_round(P, __ldg(P.vg + V), pass + 1);
@@ -1521,7 +1529,10 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
             }
             const uint32_t pv = priority_bits(P, static_cast<uint32_t>(lv), d);
             // an isolated vertex takes color 0 in round 1 and never changes: it is final from the start
-            if (MODE == GC_MODE_DETERMINISTIC) {
+            if (MODE == GC_MODE_DETERMINISTIC && P.ordered) {
+                // ordered mode (col1 is col0): uncolored until every smaller-key neighbour is colored
+                P.col0[V] = pack_state(d == 0 ? 0 : -1, pv, d == 0);
+            } else if (MODE == GC_MODE_DETERMINISTIC) {
                 // C_1 = 0 everywhere: round 1's First Fit sees no colored neighbour
                 P.col0[V] = pack_state(0, pv, d == 0);
                 P.col1[V] = pack_state(0, pv, d == 0);

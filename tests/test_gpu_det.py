@@ -241,3 +241,39 @@ def test_colors_beyond_window_inplace(gclib):
     c = r.colors.cpu().numpy()
     assert oracle.count_conflicts(g, c) == 0
     assert np.all(c <= g.degrees()) and r.ncolors >= 700
+
+
+# ---------------------------------------------------------------------------------------------
+# ordered mode: no speculation, First Fit in key order
+
+ORDERED_GRAPHS = [lambda: gg.complete(40), lambda: gg.complete(600), lambda: gg.star(5000), lambda: gg.crown(40),
+                  lambda: gg.empty(33), lambda: gg.grid5(37, 29), lambda: gg.stencil27(9),
+                  lambda: gg.er(3000, 12.0, 5), lambda: gg.rmat(12, 16, 2), lambda: gg.rmat(15, 16, 2)]
+
+
+@pytest.mark.parametrize("make", ORDERED_GRAPHS)
+@pytest.mark.parametrize("prio", [0, 1])
+def test_ordered_equals_keyorder_greedy(gclib, make, prio):
+    g = make()
+    colors_ref, k = oracle.greedy_keyorder(g, 7, prio)
+    rp, ci = _dev(g)
+    for opt in [dict(priority=prio), dict(priority=prio, flags=gclib.FLAG_FULL_SWEEP),
+                dict(priority=prio, small_max_degree=3, chunk=64)]:
+        r = gclib.color(rp, ci, "ordered", 7, options=gclib.Options(**opt))
+        np.testing.assert_array_equal(r.colors.cpu().numpy(), colors_ref, err_msg=str(opt))
+        assert r.ncolors == oracle.distinct_colors(colors_ref)
+        assert (g.n == 0 and r.rounds == 0) or 1 <= r.rounds <= g.n
+
+
+def test_ordered_batch_equals_keyorder_greedy(gclib):
+    import torch
+    graphs = [gg.rmat(11, 8, 1), gg.star(300), gg.empty(5), gg.er(1500, 9.0, 2), gg.complete(70)]
+    b = gg.pack(graphs)
+    args = [torch.from_numpy(a).cuda() for a in (b.vtx_off, b.edge_off, b.rowptr, b.colidx)]
+    colors, nc, rounds = gclib.color_batch(*args, "ordered", 7)
+    colors = colors.cpu().numpy()
+    for i, g in enumerate(graphs):
+        ref, _ = oracle.greedy_keyorder(g, 7)
+        v0, v1 = int(b.vtx_off[i]), int(b.vtx_off[i + 1])
+        np.testing.assert_array_equal(colors[v0:v1], ref)
+        assert int(nc[i]) == oracle.distinct_colors(ref)

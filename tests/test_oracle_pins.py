@@ -377,3 +377,53 @@ def test_lf_tiny_graphs_brute_force():
         lit, lr = _literal_rounds(n, adj, lambda v: (-int(deg[v]), int(h[v]), v))
         assert list(r.colors) == lit and r.rounds == lr
         assert _chromatic_number(n, edges) <= r.ncolors <= g.max_degree + 1
+
+
+# ---------------------------------------------------------------------------------------------
+# First Fit in key order (what the ordered mode computes)
+
+def _literal_keyorder(g, key):
+    n = g.n
+    adj = [list(g.colidx[g.rowptr[v]:g.rowptr[v + 1]]) for v in range(n)]
+    color = [-1] * n
+    for v in sorted(range(n), key=key):
+        taken = {color[u] for u in adj[v]}
+        color[v] = next(c for c in itertools.count() if c not in taken)
+    return color
+
+
+def test_keyorder_matches_literal_restatement():
+    rng = np.random.default_rng(23)
+    for trial in range(40):
+        n = int(rng.integers(1, 60))
+        edges = [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < 0.2]
+        g = gg.from_edges(n, edges)
+        seed = int(rng.integers(0, 2**63))
+        h = oracle.keys(seed, n)
+        deg = g.degrees()
+        c, k = oracle.greedy_keyorder(g, seed)
+        assert list(c) == _literal_keyorder(g, lambda v: (int(h[v]), v))
+        c, k = oracle.greedy_keyorder(g, seed, oracle.PRIORITY_LARGEST_FIRST)
+        assert list(c) == _literal_keyorder(g, lambda v: (-int(deg[v]), int(h[v]), v))
+        assert k == max(c) + 1
+
+
+@pytest.mark.parametrize("n", [1, 2, 9, 40])
+def test_keyorder_complete_graph(n):
+    # in key order every vertex sees all earlier ones colored: rank k gets color k
+    g = gg.complete(n)
+    for seed in (0, 7):
+        c, k = oracle.greedy_keyorder(g, seed)
+        np.testing.assert_array_equal(c, _rank(seed, n))
+        assert k == n
+
+
+def test_keyorder_largest_first_welsh_powell_bound():
+    # Welsh & Powell (1967): First Fit in non-increasing degree order uses at most
+    # max_i min(d_i + 1, i) colors, d_1 >= d_2 >= ... the degrees, i 1-based
+    for g in (gg.rmat(12, 8, 1), gg.er(3000, 10.0, 2), gg.star(500), gg.crown(30), gg.grid5(30, 20)):
+        c, k = oracle.greedy_keyorder(g, 7, oracle.PRIORITY_LARGEST_FIRST)
+        d = np.sort(g.degrees())[::-1]
+        bound = int(np.max(np.minimum(d + 1, np.arange(1, g.n + 1))))
+        assert k <= bound
+        assert oracle.count_conflicts(g, c) == 0 and np.all(c <= g.degrees())

@@ -5,7 +5,7 @@ paper's timing convention (Section 5.1: partitioning included, input reading exc
 JSON line.  `--impl reference` times the CPU oracle instead (the reference arm).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat22|stencil256|er10k]
-                    [--mode det|inplace] [--impl ours|reference]
+                    [--mode det|inplace|ordered] [--impl ours|reference]
 """
 from __future__ import annotations
 
@@ -372,7 +372,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="rmat22", help="rmat22 | stencil256 | er10k | rmatNN | stencilL")
-    ap.add_argument("--mode", default="det", choices=["det", "inplace"])
+    ap.add_argument("--mode", default="det", choices=["det", "inplace", "ordered"])
     ap.add_argument("--priority", default="hash", choices=["hash", "lf"],
                     help="priority key: seeded hash (default) or largest degree first")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -456,7 +456,15 @@ def main():
     E = int(st.wl_degsum.sum())  # sum over rounds of sum_{v in W_r} deg(v)
     WT = st.worklist_total
     per_sweep = 4 * E + 20 * WT + 4 * (WT - g.n)
-    alg_bytes = per_sweep if mode == "det" else 2 * (4 * E + 16 * WT) + 4 * (WT - g.n)
+    if mode == "det":
+        alg_bytes = per_sweep
+    elif mode == "inplace":
+        alg_bytes = 2 * (4 * E + 16 * WT) + 4 * (WT - g.n)
+    else:
+        # ordered: the counting pass and the rounds each read every row once (rowptr pair, own state,
+        # colidx, one state gather per entry: 16 + 12 deg bytes), plus the pending-count write and
+        # read-modify-write per smaller-key entry (E / 2 of them), the ready lists and the color
+        alg_bytes = 2 * (12 * E + 16 * WT) + 4 * WT + 8 * (E // 2) + 8 * WT + 8 * WT
     kms = statistics.median(kernel_ms)
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (kms / 1e3) / 1e9
@@ -500,7 +508,7 @@ def main():
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": args.workload, "graph": WORKLOAD_DESC.get(args.workload, g.name), "n": g.n,
                        "nnz": g.nnz,
-                       "mode": "deterministic" if mode == "det" else "in-place", "hash_seed": HASH_SEED,
+                       "mode": {"det": "deterministic", "inplace": "in-place"}.get(mode, mode), "hash_seed": HASH_SEED,
                        "priority": "largest degree first" if args.priority == "lf" else "hash",
                        "l2": "flushed between steps (512 MB write) and colidx > L2", "parallelism":
                        "replicas" if world > 1 else "single"},
@@ -510,8 +518,9 @@ def main():
                          "kernel": "round kernel (persistent)", "kernel_ms": kms, "alg_bytes": alg_bytes},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            # setup, degree sort (2), expand, round kernel, color count (2) per coloring
-            "gpu_launches": 7 * args.steps,
+            # setup, degree sort (2), expand, round kernel, color count (2) per coloring; ordered mode:
+            # setup, counting pass, round kernel, color count (2)
+            "gpu_launches": (5 if mode == "ordered" else 7) * args.steps,
             "clocks": clk,
             "rounds": r0.rounds, "ncolors": r0.ncolors, "greedy_ncolors": greedy_colors,
             "max_degree": g.max_degree, "wall_s_timed": t_wall,

@@ -53,9 +53,12 @@
  *       and p (seed unused); Lemma 2 bounds the rounds by p + 1.  gc_color / gc_color_ex only.
  *   GC_MODE_ORDERED  No speculation: a vertex stays uncolored while a neighbour with a smaller
  *       key is uncolored, then takes First Fit once (the order that Algorithm 3's neighbourhood
- *       locks impose, as a wait rule instead of locks).  Colors equal sequential First Fit in
- *       increasing key order (with GC_PRIORITY_LARGEST_FIRST: largest degree first); the number
- *       of rounds depends on scheduling.
+ *       locks impose, as a wait rule instead of locks).  Each vertex counts its smaller-key
+ *       neighbours; a round colors the vertices whose count is 0 and counts down their uncolored
+ *       neighbours.  Colors equal sequential First Fit in increasing key order (with
+ *       GC_PRIORITY_LARGEST_FIRST: largest degree first); the number of rounds is the most
+ *       vertices on a path of increasing keys, and round r's worklist statistics count the
+ *       vertices colored in round r.
  */
 #ifndef GC_H
 #define GC_H

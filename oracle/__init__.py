@@ -75,6 +75,8 @@ def _L():
         lib.oracle_det_prio.argtypes = [i32, p, p, u64, i32, i32, p, p, p, p, p, i32, p]
         lib.oracle_greedy_keyorder.restype = i32
         lib.oracle_greedy_keyorder.argtypes = [i32, p, p, u64, i32, p]
+        lib.oracle_keyorder_depth.restype = i32
+        lib.oracle_keyorder_depth.argtypes = [i32, p, p, u64, i32, p]
         lib.oracle_key_less_lf.restype = ctypes.c_int
         lib.oracle_key_less_lf.argtypes = [u64, i32, i32, i32, i32]
         lib.oracle_partition.restype = ctypes.c_int
@@ -173,6 +175,17 @@ def greedy_keyorder(g, seed: int, priority: int = PRIORITY_HASH) -> tuple[np.nda
     if k < 0:
         raise MemoryError("oracle_greedy_keyorder")
     return colors[:g.n], int(k)
+
+
+def keyorder_depth(g, seed: int, priority: int = PRIORITY_HASH) -> tuple[np.ndarray, int]:
+    """Per-vertex round of First Fit in key order when each vertex goes as soon as its smaller-key
+    neighbours are colored (0 for isolated vertices), and the largest such round."""
+    rp, ci = _csr(g)
+    depth = np.empty(max(g.n, 1), dtype=np.int32)
+    k = _L().oracle_keyorder_depth(g.n, rp.ctypes.data, ci.ctypes.data, seed & U64, int(priority), depth.ctypes.data)
+    if k < 0:
+        raise MemoryError("oracle_keyorder_depth")
+    return depth[:g.n], int(k)
 
 
 def det(g, seed: int, max_rounds: int | None = None, stats_cap: int = 1 << 16,

@@ -183,6 +183,45 @@ int32_t oracle_greedy_keyorder(int32_t n, const int32_t *rowptr, const int32_t *
     return used;
 }
 
+/* Rounds of First Fit in key order when every vertex is colored as soon as all its smaller-key
+ * neighbours are: depth[v] = 0 for an isolated vertex (colored before the first round), else 1 +
+ * the largest depth among its smaller-key neighbours (1 when it has none).  Vertices are visited in
+ * increasing key order, so a neighbour already visited is exactly a smaller-key one.  Returns the
+ * largest depth (-1 on OOM). */
+int32_t oracle_keyorder_depth(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed,
+                              int32_t priority, int32_t *depth) {
+    if (n <= 0) return 0;
+    int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    unsigned char *visited = (unsigned char *)calloc((size_t)n, 1);
+    if (!order || !visited) {
+        free(order);
+        free(visited);
+        return -1;
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        order[v] = v;
+        depth[v] = 0;
+    }
+    g_ko_seed = seed;
+    g_ko_priority = priority;
+    g_ko_rowptr = rowptr;
+    qsort(order, (size_t)n, sizeof(int32_t), ko_cmp);
+    int32_t deepest = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t v = order[i];
+        visited[v] = 1;
+        if (rowptr[v + 1] == rowptr[v]) continue;
+        int32_t d = 0;
+        for (int32_t j = rowptr[v]; j < rowptr[v + 1]; ++j)
+            if (visited[colidx[j]] && colidx[j] != v && depth[colidx[j]] > d) d = depth[colidx[j]];
+        depth[v] = d + 1;
+        if (depth[v] > deepest) deepest = depth[v];
+    }
+    free(order);
+    free(visited);
+    return deepest;
+}
+
 /*
  * Deterministic speculative coloring (Algorithm 1, one vertex per partition, hash priority).
  *

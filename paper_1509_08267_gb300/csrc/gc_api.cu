@@ -91,6 +91,7 @@ struct Context {
     int sms = 0;
     int occ[2][2][2][2] = {};  // [wide][mode][batch][compact] blocks per SM of the round kernel
     int occ_part = 0;       // blocks per SM of the partition-mode round kernel
+    int occ_ord[2] = {};    // blocks per SM of the ordered-mode round kernel [batch]
     Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, lists, ctl, stats, bitmap, vg, hist;
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
     Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors;
@@ -221,9 +222,6 @@ struct Outputs {
 
 static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_options *opt, gc_stats *stats,
                const Outputs &out) {
-    // ordered mode runs the deterministic kernels with one state array and the wait rule
-    const bool ordered = mode == GC_MODE_ORDERED;
-    if (ordered) mode = GC_MODE_DETERMINISTIC;
     const int dev = C.device;
     cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C.stream;
     const uint32_t flags = opt ? opt->flags : 0u;
@@ -296,7 +294,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     }
     P.seed = seed;
     P.col0 = C.col0.as<uint64_t>();
-    P.col1 = ordered ? P.col0 : C.col1.as<uint64_t>();
+    P.col1 = C.col1.as<uint64_t>();
     P.small0 = C.small0.as<int32_t>();
     P.small1 = C.small1.as<int32_t>();
     P.items = C.items.as<int32_t>();
@@ -319,7 +317,6 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     P.T1 = T1;
     P.CH = CH;
     P.priority = priority;
-    P.ordered = ordered ? 1 : 0;
 
     const bool timing = (flags & GC_FLAG_TIMING) != 0;
     Ctl h{};
@@ -351,6 +348,37 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
         if (want < grid) grid = want;
         if (grid < 1) grid = 1;
         if (n > 0) GC_CUDA(launch_partition_rounds(P, static_cast<int32_t>(p), static_cast<int>(grid), block, s));
+    } else if (mode == GC_MODE_ORDERED) {
+        // First Fit in key order: in-place set-up (vertices with neighbours uncolored, no worklist
+        // sort; it also counts the larger vertices and their work items), pending counts of
+        // smaller-key neighbours in the unused second state array, then rounds over the ready
+        // vertices only
+        P.deg_hist = nullptr;
+        P.T1 = T1 < kOrdSmall ? T1 : kOrdSmall;
+        P.CH = CH < kOrdChunk ? CH : kOrdChunk;
+        GC_CUDA(launch_setup(P, GC_MODE_INPLACE, pb.batch, 0, static_cast<int32_t>(n), -1, s));
+        GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+        if (h.err[0] != 0) return error_from_ctl(h);
+        // each vertex is listed once: the item lists hold at most all items; a vertex of several
+        // items has at least two, so there are at most items - larger vertices of them
+        const size_t n_big = h.tmp[0], n_items = h.tmp[1];
+        const size_t slots = std::min(n_big, n_items - n_big);
+        GC_TRY(ensure(C.chunk0, 16 * std::max<size_t>(n_items, 1), "work items"));
+        GC_TRY(ensure(C.chunk1, 16 * std::max<size_t>(n_items, 1), "work items"));
+        GC_TRY(ensure(C.acc, 4 * kOrdSlotWords * std::max<size_t>(slots, 1), "accumulators"));
+        P.chunk0 = C.chunk0.as<int4>();
+        P.chunk1 = C.chunk1.as<int4>();
+        P.acc = C.acc.as<unsigned>();
+        if (slots) GC_CUDA(cudaMemsetAsync(C.acc.p, 0, 4 * kOrdSlotWords * slots, s));
+        GC_CUDA(cudaMemsetAsync(ctl->cnt, 0, sizeof(ctl->cnt), s));
+        if (timing) GC_CUDA(cudaEventRecord(C.ev[1], s));
+        int &occ = C.occ_ord[pb.batch ? 1 : 0];
+        if (occ == 0) GC_CUDA(ordered_kernel_occupancy(pb.batch, block, &occ));
+        int per_sm = occ;
+        if (opt && opt->blocks_per_sm > 0 && opt->blocks_per_sm < per_sm) per_sm = opt->blocks_per_sm;
+        grid = static_cast<int64_t>(per_sm) * C.sms;
+        GC_CUDA(launch_ordered(P, pb.batch, reinterpret_cast<int32_t *>(C.col1.p), static_cast<int>(grid), block, s));
     } else {
     GC_CUDA(launch_setup(P, mode, pb.batch, 0, static_cast<int32_t>(n), -1, s));
     GC_CUDA(launch_sort_small(P, pb.batch, 0, static_cast<int32_t>(n), s));
@@ -468,7 +496,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
                 stats->entries_scanned += st_host[4 * r + 3];
                 if (stats->round_ns && r < stats->round_cap) stats->round_ns[r] = t_end - prev_t;
                 prev_t = t_end;
-                if (r == 0) {
+                if (r == 0 && mode != GC_MODE_ORDERED) {
                     w = n;  // W_1 = V; isolated vertices are final before the first sweep
                     d = pb.nnz;
                 }

@@ -42,6 +42,12 @@ constexpr int kAccOffLo = 51;
 constexpr int kAccOffHi = 52;
 constexpr int kAccDeg = 53;
 constexpr int kAccStride = 64;  // 256 B per slot
+// Ordered mode: vertices of degree <= min(T1, kOrdSmall) are one thread's work; larger rows are
+// split into work items of min(CH, kOrdChunk) entries; a vertex of several items merges them in an
+// accumulator slot of kOrdSlotWords words (window 0..15, done counter kAccDone).
+constexpr int kOrdSmall = 8;
+constexpr int kOrdChunk = 128;
+constexpr int kOrdSlotWords = 32;
 
 // Worklist counters: three sets used round-robin (read / append / clear), kCnt words each.
 constexpr int kCnt = 4;
@@ -112,9 +118,6 @@ struct RoundParams {
     int32_t T1;  // largest degree handled by one thread
     int32_t CH;  // adjacency entries per warp work item
     int32_t priority;  // GC_PRIORITY_*: what the 31 priority bits of a state word hold
-    int32_t ordered;   // GC_MODE_ORDERED on the deterministic kernels: a worklist vertex is uncolored and
-                       // waits while a neighbour with a smaller key is uncolored (the conflict test
-                       // against its own color -1), then takes First Fit once; col1 is col0
 };
 
 // Launch wrappers (gc_kernels.cu).  All return the launch's cudaError_t.
@@ -154,6 +157,13 @@ cudaError_t round_kernel_occupancy(int mode, bool batch, bool compact, int block
 cudaError_t launch_count_colors(const RoundParams &P, bool batch, const int32_t *colors_sel, int32_t v_begin,
                                 int32_t v_end, int32_t g_begin, int32_t g_end, unsigned *bitmap, int32_t *gmax,
                                 int32_t *gcount, int32_t *out, cudaStream_t s);
+// Ordered mode (GC_MODE_ORDERED): after the in-place launch_setup (every vertex with neighbours
+// uncolored) with P.T1 <= kOrdSmall and P.CH <= kOrdChunk, with the counter sets and P.acc's slots
+// zeroed, counts each vertex's smaller-key neighbours into pend[n], lists the first ready vertices
+// (small ones in small0, work items {V, q, slot, nch} in chunk0) and runs the cooperative round
+// kernel on `grid` blocks.
+cudaError_t ordered_kernel_occupancy(bool batch, int block, int *blocks_per_sm);
+cudaError_t launch_ordered(const RoundParams &P, bool batch, int32_t *pend, int grid, int block, cudaStream_t s);
 // Partition mode (GC_MODE_PARTITION, single graph): set-up (rows checked, colors -1, W_1 = V) and
 // the cooperative round kernel with p blocks of consecutive ids.
 cudaError_t launch_partition_init(const RoundParams &P, cudaStream_t s);

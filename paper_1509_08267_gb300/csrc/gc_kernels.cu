@@ -145,6 +145,15 @@ __device__ bool grid_sync(GridBar *bar, unsigned &target, int32_t *err, int64_t 
     return s_ok != 0;
 }
 
+// An error posted by any block, read once per block so that its threads leave the round loop
+// together (another block may post one while this block's threads are reading the flag).
+__device__ __forceinline__ bool block_error_seen(const int32_t *err) {
+    __shared__ int s_err;
+    if (threadIdx.x == 0) s_err = __ldcg(err) != 0;
+    __syncthreads();
+    return s_err != 0;
+}
+
 // ------------------------------------------------------------------------------------------
 // vertex state words
 
@@ -485,14 +494,8 @@ __device__ __forceinline__ bool merge_item(unsigned *a, int nch, int lane, unsig
 // Writes a vertex's state for the next round.  A vertex that did not lose is final: its color will
 // not change again, so the FINAL bit goes into both buffers (the color and priority bits are the
 // ones already there, so a concurrent reader of the current buffer sees the same color either way).
-// Ordered mode (both buffers are one array): a vertex that does not wait takes color nc, final; a
-// waiting one stays uncolored.
 __device__ __forceinline__ void det_write(const uint64_t *colc, uint64_t *coln, int32_t V, bool lose, int32_t cv,
-                                          int32_t nc, uint32_t pv, bool ordered) {
-    if (ordered) {
-        if (!lose) coln[V] = pack_state(nc, pv, true);
-        return;
-    }
+                                          int32_t nc, uint32_t pv) {
     if (lose) {
         coln[V] = pack_state(nc, pv, false);
     } else {
@@ -514,8 +517,7 @@ __device__ __forceinline__ bool det_small(const RoundParams &P, const uint64_t *
     uint64_t mask0 = 0, mask1 = 0;
     bool lose = false;
     sweep_small<BATCH, true, true>(P, r, colc, cv, pv, mask0, mask1, lose);
-    const bool pick = lose != (P.ordered != 0);  // a new color: a loser (deterministic), a ready vertex (ordered)
-    det_write(colc, coln, V, lose, cv, pick ? first_free_128(mask0, mask1) : cv, pv, P.ordered != 0);
+    det_write(colc, coln, V, lose, cv, lose ? first_free_128(mask0, mask1) : cv, pv);
     return lose;
 }
 
@@ -767,7 +769,7 @@ __device__ __forceinline__ void det_finish(const RoundParams &P, const uint64_t 
         }
     }
     const bool lose = fin && st.x != 0u;
-    const bool pick = fin && (lose != (P.ordered != 0));
+    const bool pick = lose;
     const int32_t cv = color_of(self);
     const uint32_t pv = prio_of(self);
     int32_t nc = cv;
@@ -787,7 +789,7 @@ __device__ __forceinline__ void det_finish(const RoundParams &P, const uint64_t 
         if (lane == l) nc = x;
     }
     if (fin) {
-        det_write(colc, coln, V, lose, cv, nc, pv, P.ordered != 0);
+        det_write(colc, coln, V, lose, cv, nc, pv);
         st_deg += static_cast<unsigned>(deg);
         st_cnt += 1;
         const uint4 z = make_uint4(0, 0, 0, 0);
@@ -931,11 +933,11 @@ __device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *c
         __syncwarp();
     }
     int32_t nc = cv;
-    if (lose != (P.ordered != 0)) {
+    if (lose) {
         nc = first_free(lo0, lo1, win);
         if (nc < 0) nc = mex_from<BATCH>(P, colc, load_row<BATCH>(P, V), win, lane, 32 * kAccWords);
     }
-    if (lane == 0) det_write(colc, coln, V, lose, cv, nc, pv, P.ordered != 0);
+    if (lane == 0) det_write(colc, coln, V, lose, cv, nc, pv);
     if (!lose) return;
     if constexpr (BATCH) {
         if (lane == 0) note_graph_round(P, __ldg(P.vg + V), pass + 1);
@@ -1263,7 +1265,7 @@ __global__ void __launch_bounds__(kBlock, MINB) det_round_kernel(RoundParams P) 
         unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
         const unsigned nsmall = __ldcg(cc + kCntSmall), nitems = __ldcg(cc + kCntItems);
         const unsigned nchunks = __ldcg(cc + kCntChunks), nmulti = __ldcg(cc + kCntMulti);
-        if (__ldcg(P.err) != 0) break;  // posted by any block in an earlier round
+        if (block_error_seen(P.err)) break;
         if (nsmall + nitems == 0u) break;
         if (pass >= P.pass_end) {
             if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
@@ -1350,7 +1352,7 @@ __global__ void __launch_bounds__(kBlock, MINB) ip_round_kernel(RoundParams P) {
         unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
         const unsigned nsmall = __ldcg(cc + kCntSmall), nitems = __ldcg(cc + kCntItems);
         const unsigned nchunks = __ldcg(cc + kCntChunks);
-        if (__ldcg(P.err) != 0) break;  // posted by any block in an earlier round
+        if (block_error_seen(P.err)) break;
         if (nsmall + nitems == 0u) break;
         if (pass >= P.pass_end) {
             if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
@@ -1397,7 +1399,8 @@ __global__ void __launch_bounds__(kBlock, MINB) ip_round_kernel(RoundParams P) {
             for (unsigned i = gw; i < nchunks; i += nw)
                 ip_chunk_conflict<BATCH>(P, col, __ldcg(chunkc + i), win, chunkn, cn, pass, lane, st_deg, st_cnt);
         }
-        for (unsigned base = gw * 32u; base < nsmall; base += nw * 32u) {
+        // small vertices from the warp after the last one with an item, so that few warps get both
+        for (unsigned base = ((gw + nw - nitems % nw) % nw) * 32u; base < nsmall; base += nw * 32u) {
             const unsigned i = base + lane;
             bool lose = false;
             int32_t V = 0, deg = 0;
@@ -1529,10 +1532,7 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
             }
             const uint32_t pv = priority_bits(P, static_cast<uint32_t>(lv), d);
             // an isolated vertex takes color 0 in round 1 and never changes: it is final from the start
-            if (MODE == GC_MODE_DETERMINISTIC && P.ordered) {
-                // ordered mode (col1 is col0): uncolored until every smaller-key neighbour is colored
-                P.col0[V] = pack_state(d == 0 ? 0 : -1, pv, d == 0);
-            } else if (MODE == GC_MODE_DETERMINISTIC) {
+            if (MODE == GC_MODE_DETERMINISTIC) {
                 // C_1 = 0 everywhere: round 1's First Fit sees no colored neighbour
                 P.col0[V] = pack_state(0, pv, d == 0);
                 P.col1[V] = pack_state(0, pv, d == 0);
@@ -1782,7 +1782,7 @@ __global__ void __launch_bounds__(kBlock, kNarrowBlocks) part_round_kernel(Round
         unsigned *cc = P.cnt + kCnt * (pass % 3);
         unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
         const unsigned nwl = __ldcg(cc + kCntSmall);
-        if (__ldcg(P.err) != 0) break;
+        if (block_error_seen(P.err)) break;
         if (nwl == 0u) break;
         if (pass >= P.pass_end) {
             if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
@@ -1843,6 +1843,319 @@ __global__ void __launch_bounds__(kBlock, kNarrowBlocks) part_round_kernel(Round
         if (lane == 0 && lost) atomicAdd(cn + kCntSmall, lost);
         if (P.stats) flush_stats(P, pass, st_deg, (blockIdx.x == 0 && threadIdx.x == 0) ? nwl : 0u, 2ull * st_deg);
         if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.passes[0] = pass;
+        P.passes[1] = pass - 1;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// ordered mode: First Fit in key order without speculation.  pend[v] counts v's neighbours with a
+// smaller key that are still uncolored; a vertex whose count is 0 is ready: it takes First Fit over
+// its colored neighbours (exactly those with a smaller key) and, in the same sweep, counts itself
+// down at each uncolored neighbour (each has a larger key and waits for it).  A neighbour whose count
+// reaches 0 is ready in the next round.  Two adjacent vertices are never ready in the same round,
+// so every state a ready vertex reads was written before the round began or stays uncolored in it.
+//
+// A ready vertex of degree <= P.T1 (at most kOrdSmall) is one thread's work; a larger one is split
+// into work items of P.CH (at most kOrdChunk) entries, one warp each, so that a round lasts about
+// as long as one item however large its hubs are.  The items of one vertex merge their windows in
+// an accumulator slot (kOrdSlotWords words) and the warp that finishes last picks the color.
+// Every vertex is listed at most once in the whole run (its count reaches 0 once), so the lists
+// never hold more than n small vertices and sum over larger v of ceil(deg(v) / P.CH) items.
+
+constexpr int kOrdPer = kOrdChunk / 32;  // entries per lane per step of a work item
+
+// Warp-wide exclusive prefix sum of x; `total` receives the sum over all lanes.
+__device__ __forceinline__ unsigned warp_exclusive_sum(unsigned x, int lane, unsigned &total) {
+    unsigned incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    total = __shfl_sync(kFull, incl, 31);
+    return incl - x;
+}
+
+// Lists the ready vertices U[k] (those with ready[k]; up to K per lane) for the next round, with
+// one atomic per list and warp: a small vertex goes on the small list, a larger one as its
+// ceil(deg / P.CH) work items, with an accumulator slot when there are several (warp-uniform call).
+template <bool BATCH, int K>
+__device__ void ord_list(const RoundParams &P, const bool (&ready)[K], const int32_t (&U)[K], int32_t *small_next,
+                         int4 *items_next, unsigned *cn, int lane) {
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) any |= ready[k];
+    if (!__any_sync(kFull, any)) return;
+    unsigned nch[K];  // work items of a larger vertex; 0 for a small one or none
+    bool small[K];
+    unsigned ns = 0, ni = 0, nm = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        nch[k] = 0;
+        small[k] = false;
+        if (ready[k]) {
+            const Row r = load_row<BATCH>(P, U[k]);
+            const int64_t deg = r.e - r.b;
+            small[k] = deg <= P.T1;
+            if (!small[k]) nch[k] = static_cast<unsigned>((deg + P.CH - 1) / P.CH);
+        }
+        ns += small[k] ? 1u : 0u;
+        ni += nch[k];
+        nm += nch[k] > 1u ? 1u : 0u;
+    }
+    unsigned ts, ti, tm;
+    unsigned sb = warp_exclusive_sum(ns, lane, ts);
+    unsigned ib = warp_exclusive_sum(ni, lane, ti);
+    unsigned mb = warp_exclusive_sum(nm, lane, tm);
+    unsigned b0 = 0, b1 = 0, b2 = 0;
+    if (lane == 0) {
+        if (ts) b0 = atomicAdd(cn + kCntSmall, ts);
+        if (ti) b1 = atomicAdd(cn + kCntChunks, ti);
+        if (tm) b2 = atomicAdd(cn + kCntItems, tm);
+    }
+    sb += __shfl_sync(kFull, b0, 0);
+    ib += __shfl_sync(kFull, b1, 0);
+    mb += __shfl_sync(kFull, b2, 0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (small[k]) {
+            small_next[sb++] = U[k];
+        } else if (nch[k]) {
+            const int32_t slot = nch[k] > 1u ? static_cast<int32_t>(mb++) : -1;
+            for (unsigned q = 0; q < nch[k]; ++q)
+                items_next[ib + q] = make_int4(U[k], static_cast<int32_t>(q), slot, static_cast<int32_t>(nch[k]));
+            ib += nch[k];
+        }
+    }
+}
+
+// Counts down the neighbours U[k] (those with take[k]) of a ready vertex: one fewer smaller-key
+// neighbour to wait for; the ones whose count reaches 0 are listed (warp-uniform call).
+template <bool BATCH, int K>
+__device__ __forceinline__ void ord_release(const RoundParams &P, int32_t *pend, const bool (&take)[K],
+                                            const int32_t (&U)[K], int32_t *small_next, int4 *items_next,
+                                            unsigned *cn, int lane) {
+    bool ready[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) ready[k] = take[k] && atomicSub(pend + U[k], 1) == 1;
+    ord_list<BATCH, K>(P, ready, U, small_next, items_next, cn, lane);
+}
+
+// pend[v] for every vertex, and the first round's lists (vertices with neighbours, none of them
+// with a smaller key).  A warp takes 32 consecutive vertices, sweeps their rows one after another
+// with all lanes, and lists the ready ones together.  Vertices without neighbours were colored by
+// setup.
+template <bool BATCH>
+__global__ void ord_count_kernel(RoundParams P, int32_t *pend) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    unsigned *cc = P.cnt + kCnt * (P.pass_begin % 3);
+    const bool odd = (P.pass_begin & 1) != 0;
+    int32_t *small_cur = odd ? P.small0 : P.small1;
+    int4 *items_cur = odd ? P.chunk0 : P.chunk1;
+    const unsigned long long *st = reinterpret_cast<const unsigned long long *>(P.col0);
+    for (int64_t base = (static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+         base < P.n; base += nw * 32) {
+        unsigned mine = 0;
+        bool has_row = false;
+        const int32_t cnt = static_cast<int32_t>(min(static_cast<int64_t>(32), P.n - base));
+        for (int32_t t = 0; t < cnt; ++t) {
+            const int32_t V = static_cast<int32_t>(base + t);
+            const Row r = load_row<BATCH>(P, V);
+            unsigned c = 0;
+            if (r.e > r.b) {
+                const uint32_t pv = prio_of(__ldcg(st + V));
+                for (int64_t j = r.b + lane; j < r.e; j += 32) {
+                    const int32_t ul = load_entry(P.colidx + j);
+                    const int32_t U = neighbour(P, r, ul, j);
+                    if (U >= 0 && key_less(prio_of(__ldcg(st + U)), pv, static_cast<uint32_t>(ul),
+                                           static_cast<uint32_t>(r.lv), P.seed))
+                        ++c;
+                }
+                c = __reduce_add_sync(kFull, c);
+            }
+            if (lane == t) {
+                mine = c;
+                has_row = r.e > r.b;
+            }
+        }
+        const int32_t V = static_cast<int32_t>(base + lane);
+        if (lane < cnt) pend[V] = static_cast<int32_t>(mine);
+        const bool ready[1] = {lane < cnt && has_row && mine == 0};
+        const int32_t Vs[1] = {V};
+        ord_list<BATCH, 1>(P, ready, Vs, small_cur, items_cur, cc, lane);
+    }
+}
+
+// Ready vertices of degree <= P.T1 <= kOrdSmall, one per lane (lanes with `valid`; warp-uniform
+// call): every entry loaded, then every state gathered, then the least color absent (at most
+// deg(v) < 64) and the releases.
+template <bool BATCH>
+__device__ __forceinline__ void ord_small(const RoundParams &P, uint64_t *col, int32_t *pend, bool valid, int32_t V,
+                                          int32_t *small_next, int4 *items_next, unsigned *cn, int pass, int lane,
+                                          unsigned &st_deg, unsigned &st_cnt) {
+    Row r{};
+    int32_t deg = 0;
+    uint64_t self = 0;
+    if (valid) {
+        r = load_row<BATCH>(P, V);
+        deg = static_cast<int32_t>(r.e - r.b);
+        self = load_state(col + V);
+    }
+    int32_t ul[kOrdSmall];
+    uint64_t w[kOrdSmall];
+#pragma unroll
+    for (int k = 0; k < kOrdSmall; ++k) ul[k] = k < deg ? load_entry(P.colidx + r.b + k) : 0;
+#pragma unroll
+    for (int k = 0; k < kOrdSmall; ++k) {
+        w[k] = kNoNeighbour;
+        if (k < deg) {
+            const int32_t U = neighbour(P, r, ul[k], r.b + k);
+            if (U >= 0) w[k] = load_state(col + U);
+        }
+    }
+    uint64_t mask = 0;
+    bool take[kOrdSmall];
+    int32_t U[kOrdSmall];
+#pragma unroll
+    for (int k = 0; k < kOrdSmall; ++k) {
+        const int32_t c = color_of(w[k]);
+        if (c >= 0 && c < 64) mask |= 1ull << c;
+        take[k] = c < 0;
+        U[k] = r.vbase + ul[k];
+    }
+    ord_release<BATCH, kOrdSmall>(P, pend, take, U, small_next, items_next, cn, lane);
+    if (valid) {
+        col[V] = pack_state(__ffsll(static_cast<long long>(~mask)) - 1, prio_of(self), true);
+        if constexpr (BATCH) note_graph_round(P, r.g, pass);
+        st_deg += static_cast<unsigned>(deg);
+        st_cnt += 1;
+    }
+}
+
+// One work item {V, q, slot, nch} of a larger ready vertex (one warp): entries
+// [q P.CH, (q + 1) P.CH) of its row.  Colors of colored neighbours go into the window [0, 512)
+// (0..63 in registers, the rest in win); the last of the vertex's items picks the color.
+template <bool BATCH>
+__device__ void ord_item(const RoundParams &P, uint64_t *col, int32_t *pend, int4 it, unsigned *win,
+                         int32_t *small_next, int4 *items_next, unsigned *cn, int pass, int lane, unsigned &st_deg,
+                         unsigned &st_cnt) {
+    const int32_t V = it.x, q = it.y, slot = it.z, nch = it.w;
+    const Row r = load_row<BATCH>(P, V);
+    const int64_t jb = r.b + static_cast<int64_t>(q) * P.CH;
+    const int64_t je = min(r.e, jb + P.CH);
+    if (lane < kAccWords) win[lane] = 0;
+    __syncwarp();
+    uint64_t lo = 0;
+    for (int64_t j0 = jb; j0 < je; j0 += 32 * kOrdPer) {
+        int32_t ul[kOrdPer];
+        uint64_t w[kOrdPer];
+#pragma unroll
+        for (int k = 0; k < kOrdPer; ++k) {
+            const int64_t j = j0 + lane + 32 * k;
+            ul[k] = j < je ? load_entry(P.colidx + j) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kOrdPer; ++k) {
+            const int64_t j = j0 + lane + 32 * k;
+            w[k] = kNoNeighbour;
+            if (j < je) {
+                const int32_t U = neighbour(P, r, ul[k], j);
+                if (U >= 0) w[k] = load_state(col + U);
+            }
+        }
+        bool take[kOrdPer];
+        int32_t U[kOrdPer];
+#pragma unroll
+        for (int k = 0; k < kOrdPer; ++k) {
+            const int32_t c = color_of(w[k]);
+            if (c >= 0 && c < 64)
+                lo |= 1ull << c;
+            else if (c >= 64 && c < 32 * kAccWords)
+                atomicOr(&win[c >> 5], 1u << (c & 31));
+            take[k] = c < 0;
+            U[k] = r.vbase + ul[k];
+        }
+        ord_release<BATCH, kOrdPer>(P, pend, take, U, small_next, items_next, cn, lane);
+    }
+    unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
+    unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
+    __syncwarp();
+    if (lane == 0) {
+        st_deg += static_cast<unsigned>(je - jb);
+        st_cnt += q == 0 ? 1u : 0u;
+    }
+    bool unused = false;
+    if (nch > 1 && !merge_item<true>(P.acc + static_cast<size_t>(slot) * kOrdSlotWords, nch, lane, lo0, lo1, win,
+                                     unused, 0u))
+        return;
+    int32_t nc = first_free(lo0, lo1, win);
+    // every neighbour with a larger key is still uncolored, so the whole row's colors are the
+    // smaller-key neighbours' colors
+    if (nc < 0) nc = mex_from<BATCH>(P, col, r, win, lane, 32 * kAccWords);
+    if (lane == 0) {
+        col[V] = pack_state(nc, prio_of(load_state(col + V)), true);
+        if constexpr (BATCH) note_graph_round(P, r.g, pass);
+    }
+    __syncwarp();
+}
+
+// Rounds of the ordered mode: each round runs the ready work items (one warp each), then the ready
+// small vertices (one thread each); the vertices they release form the next round's lists.  When
+// the lists run dry, a vertex still uncolored means the input was not symmetric.
+template <bool BATCH>
+__global__ void __launch_bounds__(kBlock, kWideBlocks) ord_round_kernel(RoundParams P, int32_t *pend) {
+    __shared__ unsigned s_win[kMaxWarps][kAccWords];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    const unsigned gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    unsigned *win = s_win[wib];
+    uint64_t *col = P.col0;
+    if (P.stats && blockIdx.x == 0 && threadIdx.x == 0) P.stats[4 * P.stats_cap] = global_ns();
+    unsigned bar_target = 0;
+    bool drained = false;
+    int pass = P.pass_begin;
+    for (;; ++pass) {
+        unsigned *cc = P.cnt + kCnt * (pass % 3);
+        unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
+        const unsigned nsmall = __ldcg(cc + kCntSmall), nitems = __ldcg(cc + kCntChunks);
+        if (block_error_seen(P.err)) break;
+        if (nsmall + nitems == 0u) {
+            drained = true;
+            break;
+        }
+        if (pass >= P.pass_end) {
+            if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
+                set_error(P.err, GC_ERR_NO_CONVERGENCE, pass, 0);
+            break;
+        }
+        if (blockIdx.x == 0 && threadIdx.x < kCnt) P.cnt[kCnt * ((pass + 2) % 3) + threadIdx.x] = 0u;
+        const bool odd = (pass & 1) != 0;
+        const int32_t *small_cur = odd ? P.small0 : P.small1;
+        int32_t *small_next = odd ? P.small1 : P.small0;
+        const int4 *items_cur = odd ? P.chunk0 : P.chunk1;
+        int4 *items_next = odd ? P.chunk1 : P.chunk0;
+        unsigned st_deg = 0, st_cnt = 0;
+        for (unsigned i = gw; i < nitems; i += nw)
+            ord_item<BATCH>(P, col, pend, __ldcg(items_cur + i), win, small_next, items_next, cn, pass, lane, st_deg,
+                            st_cnt);
+        // small vertices from the warp after the last one with an item, so that few warps get both
+        for (unsigned base = ((gw + nw - nitems % nw) % nw) * 32u; base < nsmall; base += nw * 32u) {
+            const unsigned i = base + lane;
+            ord_small<BATCH>(P, col, pend, i < nsmall, i < nsmall ? __ldcg(small_cur + i) : 0, small_next,
+                             items_next, cn, pass, lane, st_deg, st_cnt);
+        }
+        if (P.stats) flush_stats(P, pass, st_deg, st_cnt, st_deg);
+        if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
+    }
+    if (drained) {
+        for (int64_t V = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; V < P.n;
+             V += static_cast<int64_t>(gridDim.x) * blockDim.x)
+            if (color_of(__ldcg(reinterpret_cast<const unsigned long long *>(col) + V)) < 0)
+                set_error(P.err, GC_ERR_INVALID_GRAPH, static_cast<int32_t>(V), -1);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.passes[0] = pass;
@@ -2100,6 +2413,34 @@ cudaError_t launch_partition_rounds(const RoundParams &P, int32_t p, int grid, i
     void *args[] = {&arg, &parg};
     return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(&part_round_kernel), dim3(grid), dim3(block),
                                        args, 0, s);
+}
+
+cudaError_t ordered_kernel_occupancy(bool batch, int block, int *blocks_per_sm) {
+    if (block != kBlock) return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm,
+        batch ? reinterpret_cast<const void *>(&ord_round_kernel<true>)
+              : reinterpret_cast<const void *>(&ord_round_kernel<false>),
+        block, 0);
+}
+
+cudaError_t launch_ordered(const RoundParams &P, bool batch, int32_t *pend, int grid, int block, cudaStream_t s) {
+    if (block != kBlock) return cudaErrorInvalidValue;
+    if (P.n <= 0) return cudaSuccess;
+    const int cgrid = grid_for(static_cast<int64_t>(P.n) * 32, 256, sm_count() * 16);
+    if (batch)
+        ord_count_kernel<true><<<cgrid, 256, 0, s>>>(P, pend);
+    else
+        ord_count_kernel<false><<<cgrid, 256, 0, s>>>(P, pend);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(&P.bar->count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    RoundParams arg = P;
+    int32_t *parg = pend;
+    void *args[] = {&arg, &parg};
+    return cudaLaunchCooperativeKernel(batch ? reinterpret_cast<const void *>(&ord_round_kernel<true>)
+                                             : reinterpret_cast<const void *>(&ord_round_kernel<false>),
+                                       dim3(grid), dim3(block), args, 0, s);
 }
 
 cudaError_t launch_count_colors(const RoundParams &P, bool batch, const int32_t *colors_sel, int32_t v_begin,

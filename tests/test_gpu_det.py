@@ -257,12 +257,20 @@ def test_ordered_equals_keyorder_greedy(gclib, make, prio):
     g = make()
     colors_ref, k = oracle.greedy_keyorder(g, 7, prio)
     rp, ci = _dev(g)
+    depth, deepest = oracle.keyorder_depth(g, 7, prio)
+    deg = g.degrees()
     for opt in [dict(priority=prio), dict(priority=prio, flags=gclib.FLAG_FULL_SWEEP),
-                dict(priority=prio, small_max_degree=3, chunk=64)]:
-        r = gclib.color(rp, ci, "ordered", 7, options=gclib.Options(**opt))
+                dict(priority=prio, small_max_degree=3, chunk=64), dict(priority=prio, blocks_per_sm=1)]:
+        r = gclib.color(rp, ci, "ordered", 7, options=gclib.Options(**opt), stats=True)
         np.testing.assert_array_equal(r.colors.cpu().numpy(), colors_ref, err_msg=str(opt))
         assert r.ncolors == oracle.distinct_colors(colors_ref)
-        assert (g.n == 0 and r.rounds == 0) or 1 <= r.rounds <= g.n
+        # a vertex is colored in the round after its last smaller-key neighbour
+        assert r.rounds == max(deepest, 1)
+        if deepest > 0:
+            want = [int(np.sum(depth == d)) for d in range(1, deepest + 1)]
+            want_deg = [int(deg[depth == d].sum()) for d in range(1, deepest + 1)]
+            np.testing.assert_array_equal(r.stats.wl_size, want)
+            np.testing.assert_array_equal(r.stats.wl_degsum, want_deg)
 
 
 def test_ordered_batch_equals_keyorder_greedy(gclib):
@@ -277,3 +285,5 @@ def test_ordered_batch_equals_keyorder_greedy(gclib):
         v0, v1 = int(b.vtx_off[i]), int(b.vtx_off[i + 1])
         np.testing.assert_array_equal(colors[v0:v1], ref)
         assert int(nc[i]) == oracle.distinct_colors(ref)
+        _, deepest = oracle.keyorder_depth(g, 7)
+        assert int(rounds[i]) == max(deepest, 1)

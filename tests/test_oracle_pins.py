@@ -427,3 +427,71 @@ def test_keyorder_largest_first_welsh_powell_bound():
         bound = int(np.max(np.minimum(d + 1, np.arange(1, g.n + 1))))
         assert k <= bound
         assert oracle.count_conflicts(g, c) == 0 and np.all(c <= g.degrees())
+
+
+# rounds of the ordered mode: a vertex goes in the round after its last smaller-key neighbour
+
+def _longest_increasing_paths(g, key):
+    # every path whose keys increase along it, enumerated from each start; best[v] = the most
+    # vertices on such a path ending at v (increasing keys make every such walk a simple path)
+    n = g.n
+    adj = [list(g.colidx[g.rowptr[v]:g.rowptr[v + 1]]) for v in range(n)]
+    best = [0] * n
+
+    def walk(v, length):
+        best[v] = max(best[v], length)
+        for u in adj[v]:
+            if key(u) > key(v):
+                walk(u, length + 1)
+
+    for s in range(n):
+        if adj[s]:
+            walk(s, 1)
+    return best
+
+
+def test_keyorder_depth_brute_force():
+    rng = np.random.default_rng(31)
+    for trial in range(60):
+        n = int(rng.integers(1, 11))
+        edges = [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < 0.35]
+        g = gg.from_edges(n, edges)
+        seed = int(rng.integers(0, 2**63))
+        h = oracle.keys(seed, n)
+        deg = g.degrees()
+        for prio, key in ((oracle.PRIORITY_HASH, lambda v: (int(h[v]), v)),
+                          (oracle.PRIORITY_LARGEST_FIRST, lambda v: (-int(deg[v]), int(h[v]), v))):
+            depth, k = oracle.keyorder_depth(g, seed, prio)
+            assert list(depth) == _longest_increasing_paths(g, key)
+            assert k == max([0] + list(depth))
+
+
+@pytest.mark.parametrize("n", [1, 2, 9, 40])
+def test_keyorder_depth_complete_graph(n):
+    # the keys form one chain: rank k goes in round k + 1 (a lone vertex is isolated: round 0)
+    depth, k = oracle.keyorder_depth(gg.complete(n), 7)
+    if n == 1:
+        assert list(depth) == [0] and k == 0
+    else:
+        np.testing.assert_array_equal(depth, _rank(7, n) + 1)
+        assert k == n
+
+
+@pytest.mark.parametrize("leaves", [1, 5, 300])
+def test_keyorder_depth_star(leaves):
+    # leaves below the center go in round 1, the center next (round 1 if there are none), and the
+    # leaves above it in the round after the center
+    g = gg.star(leaves)
+    h = oracle.keys(7, leaves + 1)
+    depth, k = oracle.keyorder_depth(g, 7)
+    above = [(int(h[0]), 0) < (int(h[v]), v) for v in range(1, leaves + 1)]
+    c = 1 if all(above) else 2
+    assert depth[0] == c
+    for v in range(1, leaves + 1):
+        assert depth[v] == (c + 1 if above[v - 1] else 1)
+    assert k == (c + 1 if any(above) else c)
+
+
+def test_keyorder_depth_edgeless():
+    depth, k = oracle.keyorder_depth(gg.empty(17), 7)
+    assert not depth.any() and k == 0

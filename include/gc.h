@@ -167,6 +167,21 @@ int gc_color_ex(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mod
                 gc_stats *stats);
 
 /*
+ * gc_recolor -- one pass of iterated greedy recoloring (Culberson, 1992), a color-count reduction
+ * of the kind the paper lists as future work (Section 6).  First Fit in key order (the ordered
+ * mode) with key(v) = (-min(colors_in[v], 2^20 - 1), h_seed(v), v): the color classes of colors_in
+ * one after another, the largest color first.  When colors_in is a proper coloring with colors
+ * below 2^20 - 1, each class's vertices are pairwise non-adjacent and come one after another, so a
+ * vertex of the i-th nonempty class (counting from the largest color, 0-based) gets a color <= i:
+ * colors_out uses at most as many colors as colors_in, and repeated passes never increase the count.
+ *   colors_in  int32[n], every entry >= 0 (GC_ERR_INVALID_ARG otherwise); device or host memory; it
+ *              may be the same array as colors_out
+ *   other arguments as gc_color_ex (mode is GC_MODE_ORDERED; opt->priority is ignored).
+ */
+int gc_recolor(int32_t n, const int32_t *rowptr, const int32_t *colidx, const int32_t *colors_in, uint64_t seed,
+               int32_t *colors_out, int32_t *ncolors, int32_t *rounds, const gc_options *opt, gc_stats *stats);
+
+/*
  * gc_color_batch -- color G independent graphs in one persistent launch (every graph runs
  * Algorithm 1 on its own; a round of the launch is a round of every graph still active).
  *   G          number of graphs (>= 0)

@@ -74,9 +74,9 @@ def _L():
         lib.oracle_det_prio.restype = ctypes.c_int
         lib.oracle_det_prio.argtypes = [i32, p, p, u64, i32, i32, p, p, p, p, p, i32, p]
         lib.oracle_greedy_keyorder.restype = i32
-        lib.oracle_greedy_keyorder.argtypes = [i32, p, p, u64, i32, p]
+        lib.oracle_greedy_keyorder.argtypes = [i32, p, p, u64, i32, p, p]
         lib.oracle_keyorder_depth.restype = i32
-        lib.oracle_keyorder_depth.argtypes = [i32, p, p, u64, i32, p]
+        lib.oracle_keyorder_depth.argtypes = [i32, p, p, u64, i32, p, p]
         lib.oracle_key_less_lf.restype = ctypes.c_int
         lib.oracle_key_less_lf.argtypes = [u64, i32, i32, i32, i32]
         lib.oracle_partition.restype = ctypes.c_int
@@ -160,6 +160,7 @@ class DetResult:
 
 PRIORITY_HASH = 0
 PRIORITY_LARGEST_FIRST = 1
+PRIORITY_RECOLOR = 2  # key (-min(c(v), 2^20 - 1), h(v), v) for a given coloring c
 
 
 def key_less_lf(seed: int, u: int, v: int, du: int, dv: int) -> bool:
@@ -167,22 +168,36 @@ def key_less_lf(seed: int, u: int, v: int, du: int, dv: int) -> bool:
     return bool(_L().oracle_key_less_lf(seed & U64, u, v, du, dv))
 
 
-def greedy_keyorder(g, seed: int, priority: int = PRIORITY_HASH) -> tuple[np.ndarray, int]:
-    """Sequential First Fit in increasing key order (the hash key, or largest degree first)."""
+def _colors_in(g, priority, colors_in):
+    if priority != PRIORITY_RECOLOR:
+        return None, None
+    a = np.ascontiguousarray(colors_in, dtype=np.int32)
+    if a.shape != (g.n,) or (g.n and a.min() < 0):
+        raise ValueError("colors_in must be int32[n] with entries >= 0")
+    return (a.ctypes.data if a.size else None), a
+
+
+def greedy_keyorder(g, seed: int, priority: int = PRIORITY_HASH, colors_in=None) -> tuple[np.ndarray, int]:
+    """Sequential First Fit in increasing key order (the hash key, largest degree first, or, for
+    PRIORITY_RECOLOR, the color classes of colors_in with the largest color first)."""
     rp, ci = _csr(g)
+    pin, keep = _colors_in(g, priority, colors_in)
     colors = np.empty(max(g.n, 1), dtype=np.int32)
-    k = _L().oracle_greedy_keyorder(g.n, rp.ctypes.data, ci.ctypes.data, seed & U64, int(priority), colors.ctypes.data)
+    k = _L().oracle_greedy_keyorder(g.n, rp.ctypes.data, ci.ctypes.data, seed & U64, int(priority), pin,
+                                    colors.ctypes.data)
     if k < 0:
         raise MemoryError("oracle_greedy_keyorder")
     return colors[:g.n], int(k)
 
 
-def keyorder_depth(g, seed: int, priority: int = PRIORITY_HASH) -> tuple[np.ndarray, int]:
+def keyorder_depth(g, seed: int, priority: int = PRIORITY_HASH, colors_in=None) -> tuple[np.ndarray, int]:
     """Per-vertex round of First Fit in key order when each vertex goes as soon as its smaller-key
     neighbours are colored (0 for isolated vertices), and the largest such round."""
     rp, ci = _csr(g)
+    pin, keep = _colors_in(g, priority, colors_in)
     depth = np.empty(max(g.n, 1), dtype=np.int32)
-    k = _L().oracle_keyorder_depth(g.n, rp.ctypes.data, ci.ctypes.data, seed & U64, int(priority), depth.ctypes.data)
+    k = _L().oracle_keyorder_depth(g.n, rp.ctypes.data, ci.ctypes.data, seed & U64, int(priority), pin,
+                                   depth.ctypes.data)
     if k < 0:
         raise MemoryError("oracle_keyorder_depth")
     return depth[:g.n], int(k)

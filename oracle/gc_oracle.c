@@ -142,20 +142,26 @@ int32_t oracle_greedy(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
 static uint64_t g_ko_seed;
 static int32_t g_ko_priority;
 static const int32_t *g_ko_rowptr;
+static const int32_t *g_ko_colors_in;
 static int ko_cmp(const void *a, const void *b) {
     int32_t u = *(const int32_t *)a, v = *(const int32_t *)b;
     if (u == v) return 0;
-    int less = g_ko_priority == 1 ? oracle_key_less_lf(g_ko_seed, u, v, g_ko_rowptr[u + 1] - g_ko_rowptr[u],
-                                                       g_ko_rowptr[v + 1] - g_ko_rowptr[v])
-                                  : oracle_key_less(g_ko_seed, u, v);
+    int less;
+    if (g_ko_priority == 1)
+        less = oracle_key_less_lf(g_ko_seed, u, v, g_ko_rowptr[u + 1] - g_ko_rowptr[u], g_ko_rowptr[v + 1] - g_ko_rowptr[v]);
+    else if (g_ko_priority == 2) /* recoloring: the given colors take the place of the degrees */
+        less = oracle_key_less_lf(g_ko_seed, u, v, g_ko_colors_in[u], g_ko_colors_in[v]);
+    else
+        less = oracle_key_less(g_ko_seed, u, v);
     return less ? -1 : 1;
 }
 
-/* Sequential First Fit in increasing key order (priority 0: hash key, 1: largest degree first):
- * the vertices are sorted by key, then each takes the least color its already-colored neighbours
- * do not use.  Returns the number of colors (-1 on OOM). */
+/* Sequential First Fit in increasing key order (priority 0: hash key, 1: largest degree first,
+ * 2: largest color of colors_in first, the recoloring pass of iterated greedy): the vertices are
+ * sorted by key, then each takes the least color its already-colored neighbours do not use.
+ * colors_in is read for priority 2 only (entries >= 0).  Returns the number of colors (-1 on OOM). */
 int32_t oracle_greedy_keyorder(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed,
-                               int32_t priority, int32_t *colors) {
+                               int32_t priority, const int32_t *colors_in, int32_t *colors) {
     if (n <= 0) return 0;
     int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     unsigned char *seen = (unsigned char *)calloc((size_t)max_degree(n, rowptr) + 2, 1);
@@ -171,6 +177,7 @@ int32_t oracle_greedy_keyorder(int32_t n, const int32_t *rowptr, const int32_t *
     g_ko_seed = seed;
     g_ko_priority = priority;
     g_ko_rowptr = rowptr;
+    g_ko_colors_in = colors_in;
     qsort(order, (size_t)n, sizeof(int32_t), ko_cmp);
     int32_t used = 0;
     for (int32_t i = 0; i < n; ++i) {
@@ -189,7 +196,7 @@ int32_t oracle_greedy_keyorder(int32_t n, const int32_t *rowptr, const int32_t *
  * increasing key order, so a neighbour already visited is exactly a smaller-key one.  Returns the
  * largest depth (-1 on OOM). */
 int32_t oracle_keyorder_depth(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed,
-                              int32_t priority, int32_t *depth) {
+                              int32_t priority, const int32_t *colors_in, int32_t *depth) {
     if (n <= 0) return 0;
     int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     unsigned char *visited = (unsigned char *)calloc((size_t)n, 1);
@@ -205,6 +212,7 @@ int32_t oracle_keyorder_depth(int32_t n, const int32_t *rowptr, const int32_t *c
     g_ko_seed = seed;
     g_ko_priority = priority;
     g_ko_rowptr = rowptr;
+    g_ko_colors_in = colors_in;
     qsort(order, (size_t)n, sizeof(int32_t), ko_cmp);
     int32_t deepest = 0;
     for (int32_t i = 0; i < n; ++i) {

@@ -104,6 +104,8 @@ def load(path: str | None = None):
     lib.gc_color.argtypes = [i32, p, p, c_int, u64, p, p, p]
     lib.gc_color_ex.restype = c_int
     lib.gc_color_ex.argtypes = [i32, p, p, c_int, u64, p, p, p, P(_Options), P(_Stats)]
+    lib.gc_recolor.restype = c_int
+    lib.gc_recolor.argtypes = [i32, p, p, p, u64, p, p, p, P(_Options), P(_Stats)]
     lib.gc_color_batch.restype = c_int
     lib.gc_color_batch.argtypes = [i32, p, p, p, p, c_int, u64, p, p, p]
     lib.gc_color_batch_ex.restype = c_int
@@ -245,6 +247,18 @@ class Result:
 def color(rowptr, colidx, mode="det", seed: int = 0, out=None, options: Options | None = None,
           stats: bool = False, round_cap: int = 1 << 16) -> Result:
     """Colors one graph (gc_color_ex).  rowptr: int32[n+1], colidx: int32[nnz]."""
+    return _color_one(rowptr, colidx, mode, seed, out, options, stats, round_cap, None)
+
+
+def recolor(rowptr, colidx, colors_in, seed: int = 0, out=None, options: Options | None = None,
+            stats: bool = False, round_cap: int = 1 << 16) -> Result:
+    """One iterated-greedy recoloring pass (gc_recolor): First Fit over the color classes of
+    colors_in (int32[n], >= 0), the largest color first; never more colors than colors_in has
+    when colors_in is proper."""
+    return _color_one(rowptr, colidx, "ordered", seed, out, options, stats, round_cap, colors_in)
+
+
+def _color_one(rowptr, colidx, mode, seed, out, options, stats, round_cap, colors_in) -> Result:
     lib = load()
     n = (rowptr.numel() if _is_torch(rowptr) else len(rowptr)) - 1
     if n < 0:
@@ -269,8 +283,13 @@ def color(rowptr, colidx, mode="det", seed: int = 0, out=None, options: Options 
     st.wl_size = wl.ctypes.data
     st.wl_degsum = ds.ctypes.data
     st.round_ns = rn.ctypes.data
-    _check(lib.gc_color_ex(n, prp, pci, _mode(mode), seed & ((1 << 64) - 1), pout, ctypes.byref(nc),
-                           ctypes.byref(rd), ctypes.byref(copt), ctypes.byref(st)))
+    if colors_in is None:
+        _check(lib.gc_color_ex(n, prp, pci, _mode(mode), seed & ((1 << 64) - 1), pout, ctypes.byref(nc),
+                               ctypes.byref(rd), ctypes.byref(copt), ctypes.byref(st)))
+    else:
+        pin, colors_in_k = _ptr(colors_in, np.int32)
+        _check(lib.gc_recolor(n, prp, pci, pin, seed & ((1 << 64) - 1), pout, ctypes.byref(nc),
+                              ctypes.byref(rd), ctypes.byref(copt), ctypes.byref(st)))
     s = None
     if want_stats:
         k = min(st.rounds, round_cap)

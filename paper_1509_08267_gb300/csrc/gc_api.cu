@@ -94,11 +94,11 @@ struct Context {
     int occ_ord[2] = {};    // blocks per SM of the ordered-mode round kernel [batch]
     Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, lists, ctl, stats, bitmap, vg, hist;
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
-    Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors;
+    Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors, st_colors_in;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     void release_all() {
         Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &lists, &ctl, &stats, &bitmap, &hist,
-                      &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors};
+                      &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors, &st_colors_in};
         for (Buf *b : all) b->release();
     }
 };
@@ -212,6 +212,8 @@ struct Problem {
     const int32_t *colidx;
     const int64_t *vtx_off;
     const int64_t *edge_off;
+    const int32_t *prio_colors = nullptr;  // recoloring pass: the given coloring (device view)
+    int32_t priority_override = -1;        // >= 0: the priority to use instead of the options'
 };
 
 struct Outputs {
@@ -231,9 +233,10 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     if (T1 < 1 || T1 > 127) return set_last_error(GC_ERR_INVALID_ARG, "small_max_degree %d outside 1..127", T1);
     if (CH < 32 || CH > 1024 || CH % 32) return set_last_error(GC_ERR_INVALID_ARG, "chunk %d invalid", CH);
     if (block != 256) return set_last_error(GC_ERR_INVALID_ARG, "block_size %d unsupported (256)", block);
-    const int32_t priority = opt ? opt->priority : GC_PRIORITY_HASH;
-    if (priority != GC_PRIORITY_HASH && priority != GC_PRIORITY_LARGEST_FIRST)
-        return set_last_error(GC_ERR_INVALID_ARG, "unknown priority %d", priority);
+    const int32_t opt_priority = opt ? opt->priority : GC_PRIORITY_HASH;
+    if (opt_priority != GC_PRIORITY_HASH && opt_priority != GC_PRIORITY_LARGEST_FIRST)
+        return set_last_error(GC_ERR_INVALID_ARG, "unknown priority %d", opt_priority);
+    const int32_t priority = pb.priority_override >= 0 ? pb.priority_override : opt_priority;
     const int64_t n = pb.n;
     const int32_t G = pb.G;
     const int32_t max_rounds =
@@ -317,6 +320,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     P.T1 = T1;
     P.CH = CH;
     P.priority = priority;
+    P.prio_colors = pb.prio_colors;
 
     const bool timing = (flags & GC_FLAG_TIMING) != 0;
     Ctl h{};
@@ -522,7 +526,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
 
 static int color_single(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, uint64_t seed,
                         int32_t *colors_out, int32_t *ncolors, int32_t *rounds, const gc_options *opt,
-                        gc_stats *stats) {
+                        gc_stats *stats, const int32_t *colors_in = nullptr) {
     if (n < 0) return set_last_error(GC_ERR_INVALID_ARG, "n = %d is negative", n);
     if (mode != GC_MODE_DETERMINISTIC && mode != GC_MODE_INPLACE && mode != GC_MODE_PARTITION &&
         mode != GC_MODE_ORDERED)
@@ -580,6 +584,11 @@ static int color_single(int32_t n, const int32_t *rowptr, const int32_t *colidx,
         if (h.err[0] != 0) return error_from_ctl(h);
     }
     if (!pb.colidx) pb.colidx = pb.rowptr;  // never dereferenced when nnz == 0
+    if (colors_in) {
+        GC_TRY(device_view(colors_in, 4 * static_cast<size_t>(n), C->device, C->st_colors_in, s, &v));
+        pb.prio_colors = static_cast<const int32_t *>(v);
+        pb.priority_override = kPriorityRecolor;
+    }
     Outputs o{colors_out, ncolors, rounds};
     return run(*C, pb, mode, seed, opt, stats, o);
 }
@@ -653,6 +662,13 @@ int gc_color(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, 
 int gc_color_ex(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, uint64_t seed, int32_t *colors_out,
                 int32_t *ncolors, int32_t *rounds, const gc_options *opt, gc_stats *stats) {
     return gc::color_single(n, rowptr, colidx, mode, seed, colors_out, ncolors, rounds, opt, stats);
+}
+
+int gc_recolor(int32_t n, const int32_t *rowptr, const int32_t *colidx, const int32_t *colors_in, uint64_t seed,
+               int32_t *colors_out, int32_t *ncolors, int32_t *rounds, const gc_options *opt, gc_stats *stats) {
+    if (n > 0 && !colors_in) return gc::set_last_error(GC_ERR_INVALID_ARG, "NULL colors_in");
+    return gc::color_single(n, rowptr, colidx, GC_MODE_ORDERED, seed, colors_out, ncolors, rounds, opt, stats,
+                            colors_in);
 }
 
 int gc_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off, const int32_t *rowptr,

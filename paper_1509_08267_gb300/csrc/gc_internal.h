@@ -46,6 +46,9 @@ constexpr int kAccStride = 64;  // 256 B per slot
 // split into work items of min(CH, kOrdChunk) entries; a vertex of several items merges them in an
 // accumulator slot of kOrdSlotWords words (window 0..15, done counter kAccDone).
 constexpr int kOrdSmall = 8;
+// Priority of the recoloring pass (gc_recolor): key(v) = (-min(c(v), 2^20 - 1), h(v), v) for the
+// given coloring c, the color classes in decreasing color order.
+constexpr int32_t kPriorityRecolor = 2;
 constexpr int kOrdChunk = 128;
 constexpr int kOrdSlotWords = 32;
 
@@ -117,7 +120,8 @@ struct RoundParams {
     int64_t spin_ns;
     int32_t T1;  // largest degree handled by one thread
     int32_t CH;  // adjacency entries per warp work item
-    int32_t priority;  // GC_PRIORITY_*: what the 31 priority bits of a state word hold
+    int32_t priority;  // GC_PRIORITY_* or kPriorityRecolor: what the 31 priority bits of a state word hold
+    const int32_t *prio_colors;  // kPriorityRecolor: the given coloring, int32[n] on the device
 };
 
 // Launch wrappers (gc_kernels.cu).  All return the launch's cudaError_t.

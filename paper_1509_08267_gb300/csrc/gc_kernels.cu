@@ -62,20 +62,6 @@ __device__ __forceinline__ bool key_less(uint32_t pu, uint32_t pv, uint32_t lu, 
     return lu < lv;
 }
 
-// The 31 priority bits a vertex's state word carries; key_less compares them first and falls back
-// to the full hash, then the id, only when they are equal.  GC_PRIORITY_HASH: the top 31 bits of
-// h(v).  GC_PRIORITY_LARGEST_FIRST: 20 bits of 2^20 - 1 - min(deg(v), 2^20 - 1) (a larger degree
-// is a smaller key), then the top 11 bits of h(v); equal bits imply equal capped degrees, so the
-// fallback keeps the order (capped degree, hash, id).
-__device__ __forceinline__ uint32_t priority_bits(const RoundParams &P, uint32_t lv, int64_t deg) {
-    const uint64_t h = vertex_hash(P.seed, lv);
-    if (P.priority == GC_PRIORITY_LARGEST_FIRST) {
-        constexpr uint32_t kCap = (1u << 20) - 1u;
-        const uint32_t f = kCap - static_cast<uint32_t>(deg < kCap ? deg : kCap);
-        return (f << 11) | static_cast<uint32_t>(h >> 53);
-    }
-    return static_cast<uint32_t>(h >> 33);
-}
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -89,6 +75,27 @@ __device__ __forceinline__ void set_error(int32_t *err, int code, int32_t a, int
         err[2] = static_cast<int32_t>(b);
         err[3] = static_cast<int32_t>(b >> 32);
     }
+}
+
+// The 31 priority bits a vertex's state word carries; key_less compares them first and falls back
+// to the full hash, then the id, only when they are equal.  GC_PRIORITY_HASH: the top 31 bits of
+// h(v).  GC_PRIORITY_LARGEST_FIRST: 20 bits of 2^20 - 1 - min(deg(v), 2^20 - 1) (a larger degree
+// is a smaller key), then the top 11 bits of h(v); equal bits imply equal capped degrees, so the
+// fallback keeps the order (capped degree, hash, id).  kPriorityRecolor: the same with the vertex's
+// given color in place of its degree (larger colors first).
+__device__ __forceinline__ uint32_t priority_bits(const RoundParams &P, uint32_t lv, int64_t deg, int32_t V) {
+    const uint64_t h = vertex_hash(P.seed, lv);
+    if (P.priority == kPriorityRecolor) {
+        const int32_t c = P.prio_colors[V];
+        if (c < 0) set_error(P.err, GC_ERR_INVALID_ARG, V, c);
+        deg = c < 0 ? 0 : c;
+    }
+    if (P.priority == GC_PRIORITY_LARGEST_FIRST || P.priority == kPriorityRecolor) {
+        constexpr uint32_t kCap = (1u << 20) - 1u;
+        const uint32_t f = kCap - static_cast<uint32_t>(deg < kCap ? deg : kCap);
+        return (f << 11) | static_cast<uint32_t>(h >> 53);
+    }
+    return static_cast<uint32_t>(h >> 33);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1530,7 +1537,7 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
                 set_error(P.err, GC_ERR_INVALID_GRAPH, V, b);
                 d = 0;
             }
-            const uint32_t pv = priority_bits(P, static_cast<uint32_t>(lv), d);
+            const uint32_t pv = priority_bits(P, static_cast<uint32_t>(lv), d, V);
             // an isolated vertex takes color 0 in round 1 and never changes: it is final from the start
             if (MODE == GC_MODE_DETERMINISTIC) {
                 // C_1 = 0 everywhere: round 1's First Fit sees no colored neighbour

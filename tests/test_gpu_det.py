@@ -287,3 +287,59 @@ def test_ordered_batch_equals_keyorder_greedy(gclib):
         assert int(nc[i]) == oracle.distinct_colors(ref)
         _, deepest = oracle.keyorder_depth(g, 7)
         assert int(rounds[i]) == max(deepest, 1)
+
+
+# ---------------------------------------------------------------------------------------------
+# recoloring pass (iterated greedy over the classes of a given coloring)
+
+RECOLOR_GRAPHS = [lambda: gg.complete(40), lambda: gg.star(5000), lambda: gg.crown(40), lambda: gg.empty(33),
+                  lambda: gg.grid5(37, 29), lambda: gg.stencil27(9), lambda: gg.er(3000, 12.0, 5),
+                  lambda: gg.rmat(12, 16, 2), lambda: gg.rmat(15, 16, 2)]
+
+
+@pytest.mark.parametrize("make", RECOLOR_GRAPHS)
+def test_recolor_equals_oracle(gclib, make):
+    import torch
+    g = make()
+    rp, ci = _dev(g)
+    start = gclib.color(rp, ci, "det", 7)
+    cin = start.colors
+    ref, k = oracle.greedy_keyorder(g, 3, oracle.PRIORITY_RECOLOR, cin.cpu().numpy())
+    _, deepest = oracle.keyorder_depth(g, 3, oracle.PRIORITY_RECOLOR, cin.cpu().numpy())
+    for opt in [dict(), dict(small_max_degree=3, chunk=64)]:
+        r = gclib.recolor(rp, ci, cin, 3, options=gclib.Options(**opt))
+        np.testing.assert_array_equal(r.colors.cpu().numpy(), ref, err_msg=str(opt))
+        assert r.ncolors == oracle.distinct_colors(ref) <= start.ncolors
+        assert r.rounds == (max(deepest, 1) if g.n else 0)
+    # host arrays in and out, and the input array reused as the output
+    rh = gclib.recolor(g.rowptr, g.colidx, cin.cpu().numpy(), 3)
+    np.testing.assert_array_equal(rh.colors, ref)
+    same = cin.clone()
+    gclib.recolor(rp, ci, same, 3, out=same)
+    np.testing.assert_array_equal(same.cpu().numpy(), ref)
+
+
+def test_recolor_passes_never_add_colors(gclib):
+    g = gg.rmat(15, 16, 2)
+    rp, ci = _dev(g)
+    r = gclib.color(rp, ci, "inplace", 7)
+    counts = [r.ncolors]
+    c = r.colors
+    for it in range(5):
+        ref, _ = oracle.greedy_keyorder(g, it, oracle.PRIORITY_RECOLOR, c.cpu().numpy())
+        r = gclib.recolor(rp, ci, c, it)
+        np.testing.assert_array_equal(r.colors.cpu().numpy(), ref)
+        counts.append(r.ncolors)
+        c = r.colors
+    assert counts == sorted(counts, reverse=True) and counts[-1] < counts[0]
+
+
+def test_recolor_rejects_negative_colors(gclib):
+    import torch
+    g = gg.er(500, 6.0, 1)
+    rp, ci = _dev(g)
+    cin = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    cin[123] = -1
+    with pytest.raises(gclib.GCError) as e:
+        gclib.recolor(rp, ci, cin, 1)
+    assert e.value.status == gclib.GC_ERR_INVALID_ARG

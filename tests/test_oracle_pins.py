@@ -495,3 +495,72 @@ def test_keyorder_depth_star(leaves):
 def test_keyorder_depth_edgeless():
     depth, k = oracle.keyorder_depth(gg.empty(17), 7)
     assert not depth.any() and k == 0
+
+
+# recoloring pass (iterated greedy): First Fit over the classes of a given coloring, largest first
+
+def _recolor_key(h, c):
+    return lambda v: (-int(c[v]), int(h[v]), v)
+
+
+def test_recolor_matches_literal_restatement():
+    # any non-negative labels (proper or not) only decide the order
+    rng = np.random.default_rng(41)
+    for trial in range(40):
+        n = int(rng.integers(1, 60))
+        edges = [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < 0.2]
+        g = gg.from_edges(n, edges)
+        seed = int(rng.integers(0, 2**63))
+        cin = rng.integers(0, 6, size=n).astype(np.int32)
+        c, k = oracle.greedy_keyorder(g, seed, oracle.PRIORITY_RECOLOR, cin)
+        assert list(c) == _literal_keyorder(g, _recolor_key(oracle.keys(seed, n), cin))
+        depth, _ = oracle.keyorder_depth(g, seed, oracle.PRIORITY_RECOLOR, cin)
+        assert list(depth) == _longest_increasing_paths(g, _recolor_key(oracle.keys(seed, n), cin))
+
+
+def _culberson_check(g, cin, seed):
+    # Culberson (1992): with the classes of a proper coloring taken one after another, a vertex of
+    # the i-th nonempty class (0-based, largest color first) gets a color <= i
+    c, k = oracle.greedy_keyorder(g, seed, oracle.PRIORITY_RECOLOR, cin)
+    classes = np.unique(cin)[::-1]
+    pos = {int(x): i for i, x in enumerate(classes)}
+    assert all(c[v] <= pos[int(cin[v])] for v in range(g.n))
+    assert oracle.count_conflicts(g, c) == 0
+    assert oracle.distinct_colors(c) <= len(classes)
+    return c
+
+
+def test_recolor_culberson_bound():
+    rng = np.random.default_rng(43)
+    for g in (gg.rmat(11, 8, 1), gg.er(2000, 12.0, 3), gg.grid5(30, 17), gg.crown(25), gg.stencil27(5)):
+        starts = [oracle.greedy(g)[0], oracle.det(g, 7).colors]
+        perm = rng.permutation(g.max_degree + 1).astype(np.int32)
+        starts.append(3 * perm[oracle.greedy(g)[0]])  # relabelled, with gaps
+        for cin in starts:
+            c = np.asarray(cin, dtype=np.int32)
+            counts = []
+            for it in range(4):  # repeated passes never use more colors
+                c = _culberson_check(g, c, 11 + it)
+                counts.append(oracle.distinct_colors(c))
+            assert counts == sorted(counts, reverse=True)
+            assert counts[0] <= oracle.distinct_colors(np.asarray(cin))
+
+
+@pytest.mark.parametrize("n", [2, 9, 40])
+def test_recolor_complete_graph_reverses(n):
+    # K_n with n distinct colors: the classes are single vertices, taken largest color first
+    cin = _rank(7, n).astype(np.int32)
+    c, k = oracle.greedy_keyorder(gg.complete(n), 3, oracle.PRIORITY_RECOLOR, cin)
+    np.testing.assert_array_equal(c, n - 1 - cin)
+    depth, d = oracle.keyorder_depth(gg.complete(n), 3, oracle.PRIORITY_RECOLOR, cin)
+    np.testing.assert_array_equal(depth, n - cin)
+
+
+def test_recolor_keeps_two_colorings():
+    for g in (gg.cycle(40), gg.grid5(11, 13), gg.crown(12, interleaved=False)):
+        cin = np.asarray(oracle.greedy(g)[0], dtype=np.int32)
+        if oracle.distinct_colors(cin) != 2:
+            continue
+        c, k = oracle.greedy_keyorder(g, 5, oracle.PRIORITY_RECOLOR, cin)
+        assert k == 2 and oracle.count_conflicts(g, c) == 0
+        np.testing.assert_array_equal(c, 1 - cin)  # class 1 first takes color 0

@@ -94,11 +94,11 @@ struct Context {
     int occ_ord[2] = {};    // blocks per SM of the ordered-mode round kernel [batch]
     Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, lists, ctl, stats, bitmap, vg, hist;
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
-    Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors, st_colors_in;
+    Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors, st_colors_in, mid0, mid1;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     void release_all() {
         Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &lists, &ctl, &stats, &bitmap, &hist,
-                      &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors, &st_colors_in};
+                      &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors, &st_colors_in, &mid0, &mid1};
         for (Buf *b : all) b->release();
     }
 };
@@ -371,8 +371,12 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
         GC_TRY(ensure(C.chunk0, 16 * std::max<size_t>(n_items, 1), "work items"));
         GC_TRY(ensure(C.chunk1, 16 * std::max<size_t>(n_items, 1), "work items"));
         GC_TRY(ensure(C.acc, 4 * kOrdSlotWords * std::max<size_t>(slots, 1), "accumulators"));
+        GC_TRY(ensure(C.mid0, 4 * static_cast<size_t>(n), "worklist"));
+        GC_TRY(ensure(C.mid1, 4 * static_cast<size_t>(n), "worklist"));
         P.chunk0 = C.chunk0.as<int4>();
         P.chunk1 = C.chunk1.as<int4>();
+        P.mid0 = C.mid0.as<int32_t>();
+        P.mid1 = C.mid1.as<int32_t>();
         P.acc = C.acc.as<unsigned>();
         if (slots) GC_CUDA(cudaMemsetAsync(C.acc.p, 0, 4 * kOrdSlotWords * slots, s));
         GC_CUDA(cudaMemsetAsync(ctl->cnt, 0, sizeof(ctl->cnt), s));

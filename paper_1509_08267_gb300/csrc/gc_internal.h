@@ -46,6 +46,7 @@ constexpr int kAccStride = 64;  // 256 B per slot
 // split into work items of min(CH, kOrdChunk) entries; a vertex of several items merges them in an
 // accumulator slot of kOrdSlotWords words (window 0..15, done counter kAccDone).
 constexpr int kOrdSmall = 8;
+constexpr int kOrdMid = 32;  // degree <= kOrdMid (and > the small bound): an 8-lane group each
 // Priority of the recoloring pass (gc_recolor): key(v) = (-min(c(v), 2^20 - 1), h(v), v) for the
 // given coloring c, the color classes in decreasing color order.
 constexpr int32_t kPriorityRecolor = 2;
@@ -94,6 +95,7 @@ struct RoundParams {
     uint64_t *col1;  // deterministic: written in odd rounds
     int32_t *small0, *small1;  // thread-per-vertex worklists (two parities)
     int4 *chunk0, *chunk1;     // warp work items, kItemBytes each (two parities)
+    int32_t *mid0, *mid1;      // ordered mode: medium-degree ready vertices (two parities)
     int32_t *items;            // setup scratch: larger vertices found by the binning pass
     unsigned *tmp;             // [2] setup scratch counters: larger vertices, their work items
     unsigned *cnt;             // [3][kCnt] worklist counters
@@ -164,8 +166,8 @@ cudaError_t launch_count_colors(const RoundParams &P, bool batch, const int32_t 
 // Ordered mode (GC_MODE_ORDERED): after the in-place launch_setup (every vertex with neighbours
 // uncolored) with P.T1 <= kOrdSmall and P.CH <= kOrdChunk, with the counter sets and P.acc's slots
 // zeroed, counts each vertex's smaller-key neighbours into pend[n], lists the first ready vertices
-// (small ones in small0, work items {V, q, slot, nch} in chunk0) and runs the cooperative round
-// kernel on `grid` blocks.
+// (small ones in small0, medium ones in mid0, work items {V, q, slot, nch} in chunk0; P.mid0/mid1
+// hold n entries each) and runs the cooperative round kernel on `grid` blocks.
 cudaError_t ordered_kernel_occupancy(bool batch, int block, int *blocks_per_sm);
 cudaError_t launch_ordered(const RoundParams &P, bool batch, int32_t *pend, int grid, int block, cudaStream_t s);
 // Partition mode (GC_MODE_PARTITION, single graph): set-up (rows checked, colors -1, W_1 = V) and

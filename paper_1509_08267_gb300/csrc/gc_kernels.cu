@@ -1865,14 +1865,31 @@ __global__ void __launch_bounds__(kBlock, kNarrowBlocks) part_round_kernel(Round
 // reaches 0 is ready in the next round.  Two adjacent vertices are never ready in the same round,
 // so every state a ready vertex reads was written before the round began or stays uncolored in it.
 //
-// A ready vertex of degree <= P.T1 (at most kOrdSmall) is one thread's work; a larger one is split
-// into work items of P.CH (at most kOrdChunk) entries, one warp each, so that a round lasts about
-// as long as one item however large its hubs are.  The items of one vertex merge their windows in
-// an accumulator slot (kOrdSlotWords words) and the warp that finishes last picks the color.
-// Every vertex is listed at most once in the whole run (its count reaches 0 once), so the lists
-// never hold more than n small vertices and sum over larger v of ceil(deg(v) / P.CH) items.
+// A ready vertex of degree <= P.T1 (at most kOrdSmall) is one thread's work, one of degree <=
+// kOrdMid an 8-lane group's (four per warp); a larger one is split into work items of P.CH (at most
+// kOrdChunk) entries, one warp each, so that a round lasts about as long as one item however large
+// its hubs are.  The items of one vertex merge their windows in an accumulator slot (kOrdSlotWords
+// words) and the warp that finishes last picks the color.  Every vertex is listed at most once in
+// the whole run (its count reaches 0 once), so the small and medium lists never hold more than n
+// vertices and the item lists no more than the sum over larger v of ceil(deg(v) / P.CH) items.
 
 constexpr int kOrdPer = kOrdChunk / 32;  // entries per lane per step of a work item
+constexpr int kOrdMidLanes = 8;          // lanes per medium vertex
+constexpr int kOrdMidPer = kOrdMid / kOrdMidLanes;  // entries per lane of a medium vertex
+
+// The lists a round fills for the next one.
+struct OrdLists {
+    int32_t *small;  // vertices of degree <= P.T1           (count cnt[kCntSmall])
+    int32_t *mid;    // vertices of degree <= kOrdMid         (count cnt[kCntMulti])
+    int4 *items;     // work items {V, q, slot, nch}          (count cnt[kCntChunks]; slots cnt[kCntItems])
+    unsigned *cnt;   // the round's counter set
+};
+
+__device__ __forceinline__ OrdLists ord_lists(const RoundParams &P, int pass) {
+    const bool odd = (pass & 1) != 0;
+    return OrdLists{odd ? P.small0 : P.small1, odd ? P.mid0 : P.mid1, odd ? P.chunk0 : P.chunk1,
+                    P.cnt + kCnt * (pass % 3)};
+}
 
 // Warp-wide exclusive prefix sum of x; `total` receives the sum over all lanes.
 __device__ __forceinline__ unsigned warp_exclusive_sum(unsigned x, int lane, unsigned &total) {
@@ -1886,54 +1903,60 @@ __device__ __forceinline__ unsigned warp_exclusive_sum(unsigned x, int lane, uns
     return incl - x;
 }
 
-// Lists the ready vertices U[k] (those with ready[k]; up to K per lane) for the next round, with
-// one atomic per list and warp: a small vertex goes on the small list, a larger one as its
-// ceil(deg / P.CH) work items, with an accumulator slot when there are several (warp-uniform call).
+// Lists the ready vertices U[k] (those with ready[k]; up to K per lane) in L, with one atomic per
+// list and warp: by degree on the small or the medium list, or as ceil(deg / P.CH) work items with
+// an accumulator slot when there are several (warp-uniform call).
 template <bool BATCH, int K>
-__device__ void ord_list(const RoundParams &P, const bool (&ready)[K], const int32_t (&U)[K], int32_t *small_next,
-                         int4 *items_next, unsigned *cn, int lane) {
+__device__ void ord_list(const RoundParams &P, const bool (&ready)[K], const int32_t (&U)[K], const OrdLists &L,
+                         int lane) {
     bool any = false;
 #pragma unroll
     for (int k = 0; k < K; ++k) any |= ready[k];
     if (!__any_sync(kFull, any)) return;
-    unsigned nch[K];  // work items of a larger vertex; 0 for a small one or none
-    bool small[K];
-    unsigned ns = 0, ni = 0, nm = 0;
+    unsigned nch[K];  // work items of a larger vertex; 0 for a small or medium one or none
+    uint8_t kind[K];  // 0 none, 1 small, 2 medium, 3 items
+    unsigned ns = 0, nd = 0, ni = 0, nm = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         nch[k] = 0;
-        small[k] = false;
+        kind[k] = 0;
         if (ready[k]) {
             const Row r = load_row<BATCH>(P, U[k]);
             const int64_t deg = r.e - r.b;
-            small[k] = deg <= P.T1;
-            if (!small[k]) nch[k] = static_cast<unsigned>((deg + P.CH - 1) / P.CH);
+            kind[k] = deg <= P.T1 ? 1 : deg <= kOrdMid ? 2 : 3;
+            if (kind[k] == 3) nch[k] = static_cast<unsigned>((deg + P.CH - 1) / P.CH);
         }
-        ns += small[k] ? 1u : 0u;
+        ns += kind[k] == 1 ? 1u : 0u;
+        nd += kind[k] == 2 ? 1u : 0u;
         ni += nch[k];
         nm += nch[k] > 1u ? 1u : 0u;
     }
-    unsigned ts, ti, tm;
+    unsigned ts, td, ti, tm;
     unsigned sb = warp_exclusive_sum(ns, lane, ts);
+    unsigned db = warp_exclusive_sum(nd, lane, td);
     unsigned ib = warp_exclusive_sum(ni, lane, ti);
     unsigned mb = warp_exclusive_sum(nm, lane, tm);
-    unsigned b0 = 0, b1 = 0, b2 = 0;
+    unsigned b0 = 0, b1 = 0, b2 = 0, b3 = 0;
     if (lane == 0) {
-        if (ts) b0 = atomicAdd(cn + kCntSmall, ts);
-        if (ti) b1 = atomicAdd(cn + kCntChunks, ti);
-        if (tm) b2 = atomicAdd(cn + kCntItems, tm);
+        if (ts) b0 = atomicAdd(L.cnt + kCntSmall, ts);
+        if (td) b1 = atomicAdd(L.cnt + kCntMulti, td);
+        if (ti) b2 = atomicAdd(L.cnt + kCntChunks, ti);
+        if (tm) b3 = atomicAdd(L.cnt + kCntItems, tm);
     }
     sb += __shfl_sync(kFull, b0, 0);
-    ib += __shfl_sync(kFull, b1, 0);
-    mb += __shfl_sync(kFull, b2, 0);
+    db += __shfl_sync(kFull, b1, 0);
+    ib += __shfl_sync(kFull, b2, 0);
+    mb += __shfl_sync(kFull, b3, 0);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        if (small[k]) {
-            small_next[sb++] = U[k];
-        } else if (nch[k]) {
+        if (kind[k] == 1) {
+            L.small[sb++] = U[k];
+        } else if (kind[k] == 2) {
+            L.mid[db++] = U[k];
+        } else if (kind[k] == 3) {
             const int32_t slot = nch[k] > 1u ? static_cast<int32_t>(mb++) : -1;
             for (unsigned q = 0; q < nch[k]; ++q)
-                items_next[ib + q] = make_int4(U[k], static_cast<int32_t>(q), slot, static_cast<int32_t>(nch[k]));
+                L.items[ib + q] = make_int4(U[k], static_cast<int32_t>(q), slot, static_cast<int32_t>(nch[k]));
             ib += nch[k];
         }
     }
@@ -1943,12 +1966,11 @@ __device__ void ord_list(const RoundParams &P, const bool (&ready)[K], const int
 // neighbour to wait for; the ones whose count reaches 0 are listed (warp-uniform call).
 template <bool BATCH, int K>
 __device__ __forceinline__ void ord_release(const RoundParams &P, int32_t *pend, const bool (&take)[K],
-                                            const int32_t (&U)[K], int32_t *small_next, int4 *items_next,
-                                            unsigned *cn, int lane) {
+                                            const int32_t (&U)[K], const OrdLists &L, int lane) {
     bool ready[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) ready[k] = take[k] && atomicSub(pend + U[k], 1) == 1;
-    ord_list<BATCH, K>(P, ready, U, small_next, items_next, cn, lane);
+    ord_list<BATCH, K>(P, ready, U, L, lane);
 }
 
 // pend[v] for every vertex, and the first round's lists (vertices with neighbours, none of them
@@ -1959,10 +1981,7 @@ template <bool BATCH>
 __global__ void ord_count_kernel(RoundParams P, int32_t *pend) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-    unsigned *cc = P.cnt + kCnt * (P.pass_begin % 3);
-    const bool odd = (P.pass_begin & 1) != 0;
-    int32_t *small_cur = odd ? P.small0 : P.small1;
-    int4 *items_cur = odd ? P.chunk0 : P.chunk1;
+    const OrdLists L = ord_lists(P, P.pass_begin);
     const unsigned long long *st = reinterpret_cast<const unsigned long long *>(P.col0);
     for (int64_t base = (static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
          base < P.n; base += nw * 32) {
@@ -1993,7 +2012,7 @@ __global__ void ord_count_kernel(RoundParams P, int32_t *pend) {
         if (lane < cnt) pend[V] = static_cast<int32_t>(mine);
         const bool ready[1] = {lane < cnt && has_row && mine == 0};
         const int32_t Vs[1] = {V};
-        ord_list<BATCH, 1>(P, ready, Vs, small_cur, items_cur, cc, lane);
+        ord_list<BATCH, 1>(P, ready, Vs, L, lane);
     }
 }
 
@@ -2002,8 +2021,8 @@ __global__ void ord_count_kernel(RoundParams P, int32_t *pend) {
 // deg(v) < 64) and the releases.
 template <bool BATCH>
 __device__ __forceinline__ void ord_small(const RoundParams &P, uint64_t *col, int32_t *pend, bool valid, int32_t V,
-                                          int32_t *small_next, int4 *items_next, unsigned *cn, int pass, int lane,
-                                          unsigned &st_deg, unsigned &st_cnt) {
+                                          const OrdLists &L, int pass, int lane, unsigned &st_deg,
+                                          unsigned &st_cnt) {
     Row r{};
     int32_t deg = 0;
     uint64_t self = 0;
@@ -2034,8 +2053,59 @@ __device__ __forceinline__ void ord_small(const RoundParams &P, uint64_t *col, i
         take[k] = c < 0;
         U[k] = r.vbase + ul[k];
     }
-    ord_release<BATCH, kOrdSmall>(P, pend, take, U, small_next, items_next, cn, lane);
+    ord_release<BATCH, kOrdSmall>(P, pend, take, U, L, lane);
     if (valid) {
+        col[V] = pack_state(__ffsll(static_cast<long long>(~mask)) - 1, prio_of(self), true);
+        if constexpr (BATCH) note_graph_round(P, r.g, pass);
+        st_deg += static_cast<unsigned>(deg);
+        st_cnt += 1;
+    }
+}
+
+// Ready vertices of degree in (P.T1, kOrdMid], one per 8-lane group (groups with `valid`;
+// warp-uniform call): entry gl + 8k of the row in lane gl of the group, the group's colors OR-ed
+// into one mask (the least color absent is at most deg(v) <= kOrdMid < 64).
+template <bool BATCH>
+__device__ __forceinline__ void ord_mid(const RoundParams &P, uint64_t *col, int32_t *pend, bool valid, int32_t V,
+                                        const OrdLists &L, int pass, int lane, unsigned &st_deg, unsigned &st_cnt) {
+    const int gl = lane & (kOrdMidLanes - 1);
+    Row r{};
+    int32_t deg = 0;
+    if (valid) {
+        r = load_row<BATCH>(P, V);
+        deg = static_cast<int32_t>(r.e - r.b);
+    }
+    const uint64_t self = valid && gl == 0 ? load_state(col + V) : 0;
+    int32_t ul[kOrdMidPer];
+    uint64_t w[kOrdMidPer];
+#pragma unroll
+    for (int k = 0; k < kOrdMidPer; ++k) {
+        const int32_t e = gl + kOrdMidLanes * k;
+        ul[k] = e < deg ? load_entry(P.colidx + r.b + e) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kOrdMidPer; ++k) {
+        const int32_t e = gl + kOrdMidLanes * k;
+        w[k] = kNoNeighbour;
+        if (e < deg) {
+            const int32_t U = neighbour(P, r, ul[k], r.b + e);
+            if (U >= 0) w[k] = load_state(col + U);
+        }
+    }
+    uint64_t mask = 0;
+    bool take[kOrdMidPer];
+    int32_t U[kOrdMidPer];
+#pragma unroll
+    for (int k = 0; k < kOrdMidPer; ++k) {
+        const int32_t c = color_of(w[k]);
+        if (c >= 0 && c < 64) mask |= 1ull << c;
+        take[k] = c < 0;
+        U[k] = r.vbase + ul[k];
+    }
+#pragma unroll
+    for (int o = 1; o < kOrdMidLanes; o <<= 1) mask |= __shfl_xor_sync(kFull, mask, o);
+    ord_release<BATCH, kOrdMidPer>(P, pend, take, U, L, lane);
+    if (valid && gl == 0) {
         col[V] = pack_state(__ffsll(static_cast<long long>(~mask)) - 1, prio_of(self), true);
         if constexpr (BATCH) note_graph_round(P, r.g, pass);
         st_deg += static_cast<unsigned>(deg);
@@ -2048,8 +2118,7 @@ __device__ __forceinline__ void ord_small(const RoundParams &P, uint64_t *col, i
 // (0..63 in registers, the rest in win); the last of the vertex's items picks the color.
 template <bool BATCH>
 __device__ void ord_item(const RoundParams &P, uint64_t *col, int32_t *pend, int4 it, unsigned *win,
-                         int32_t *small_next, int4 *items_next, unsigned *cn, int pass, int lane, unsigned &st_deg,
-                         unsigned &st_cnt) {
+                         const OrdLists &L, int pass, int lane, unsigned &st_deg, unsigned &st_cnt) {
     const int32_t V = it.x, q = it.y, slot = it.z, nch = it.w;
     const Row r = load_row<BATCH>(P, V);
     const int64_t jb = r.b + static_cast<int64_t>(q) * P.CH;
@@ -2086,7 +2155,7 @@ __device__ void ord_item(const RoundParams &P, uint64_t *col, int32_t *pend, int
             take[k] = c < 0;
             U[k] = r.vbase + ul[k];
         }
-        ord_release<BATCH, kOrdPer>(P, pend, take, U, small_next, items_next, cn, lane);
+        ord_release<BATCH, kOrdPer>(P, pend, take, U, L, lane);
     }
     unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
     unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
@@ -2110,9 +2179,11 @@ __device__ void ord_item(const RoundParams &P, uint64_t *col, int32_t *pend, int
     __syncwarp();
 }
 
-// Rounds of the ordered mode: each round runs the ready work items (one warp each), then the ready
-// small vertices (one thread each); the vertices they release form the next round's lists.  When
-// the lists run dry, a vertex still uncolored means the input was not symmetric.
+// Rounds of the ordered mode: each round runs the ready work items (one warp each), the medium
+// vertices (four per warp) and the small ones (32 per warp), each kind starting at the warp after
+// the previous kind's last, so that few warps get two; the vertices they release form the next
+// round's lists.  When the lists run dry, a vertex still uncolored means the input was not
+// symmetric.
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock, kWideBlocks) ord_round_kernel(RoundParams P, int32_t *pend) {
     __shared__ unsigned s_win[kMaxWarps][kAccWords];
@@ -2126,11 +2197,11 @@ __global__ void __launch_bounds__(kBlock, kWideBlocks) ord_round_kernel(RoundPar
     bool drained = false;
     int pass = P.pass_begin;
     for (;; ++pass) {
-        unsigned *cc = P.cnt + kCnt * (pass % 3);
-        unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
-        const unsigned nsmall = __ldcg(cc + kCntSmall), nitems = __ldcg(cc + kCntChunks);
+        const OrdLists C = ord_lists(P, pass), L = ord_lists(P, pass + 1);
+        const unsigned nsmall = __ldcg(C.cnt + kCntSmall), nmid = __ldcg(C.cnt + kCntMulti);
+        const unsigned nitems = __ldcg(C.cnt + kCntChunks);
         if (block_error_seen(P.err)) break;
-        if (nsmall + nitems == 0u) {
+        if (nsmall + nmid + nitems == 0u) {
             drained = true;
             break;
         }
@@ -2140,20 +2211,19 @@ __global__ void __launch_bounds__(kBlock, kWideBlocks) ord_round_kernel(RoundPar
             break;
         }
         if (blockIdx.x == 0 && threadIdx.x < kCnt) P.cnt[kCnt * ((pass + 2) % 3) + threadIdx.x] = 0u;
-        const bool odd = (pass & 1) != 0;
-        const int32_t *small_cur = odd ? P.small0 : P.small1;
-        int32_t *small_next = odd ? P.small1 : P.small0;
-        const int4 *items_cur = odd ? P.chunk0 : P.chunk1;
-        int4 *items_next = odd ? P.chunk1 : P.chunk0;
         unsigned st_deg = 0, st_cnt = 0;
         for (unsigned i = gw; i < nitems; i += nw)
-            ord_item<BATCH>(P, col, pend, __ldcg(items_cur + i), win, small_next, items_next, cn, pass, lane, st_deg,
-                            st_cnt);
-        // small vertices from the warp after the last one with an item, so that few warps get both
-        for (unsigned base = ((gw + nw - nitems % nw) % nw) * 32u; base < nsmall; base += nw * 32u) {
+            ord_item<BATCH>(P, col, pend, __ldcg(C.items + i), win, L, pass, lane, st_deg, st_cnt);
+        const unsigned mid_groups = (nmid + 3u) / 4u;
+        for (unsigned b = (gw + nw - nitems % nw) % nw; b < mid_groups; b += nw) {
+            const unsigned i = 4u * b + static_cast<unsigned>(lane >> 3);
+            ord_mid<BATCH>(P, col, pend, i < nmid, i < nmid ? __ldcg(C.mid + i) : 0, L, pass, lane, st_deg, st_cnt);
+        }
+        const unsigned skip = (nitems + mid_groups) % nw;
+        for (unsigned base = ((gw + nw - skip) % nw) * 32u; base < nsmall; base += nw * 32u) {
             const unsigned i = base + lane;
-            ord_small<BATCH>(P, col, pend, i < nsmall, i < nsmall ? __ldcg(small_cur + i) : 0, small_next,
-                             items_next, cn, pass, lane, st_deg, st_cnt);
+            ord_small<BATCH>(P, col, pend, i < nsmall, i < nsmall ? __ldcg(C.small + i) : 0, L, pass, lane, st_deg,
+                             st_cnt);
         }
         if (P.stats) flush_stats(P, pass, st_deg, st_cnt, st_deg);
         if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;

@@ -373,8 +373,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="rmat22", help="rmat22 | stencil256 | er10k | rmatNN | stencilL")
     ap.add_argument("--mode", default="det", choices=["det", "inplace", "ordered", "recolor"])
-    ap.add_argument("--priority", default="hash", choices=["hash", "lf"],
-                    help="priority key: seeded hash (default) or largest degree first")
+    ap.add_argument("--priority", default="hash", choices=["hash", "lf", "sl"],
+                    help="priority key: seeded hash (default), largest degree first, or smallest last")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -417,7 +417,7 @@ def main():
     ci = torch.from_numpy(g.colidx).to(dev)
     out = torch.empty(g.n, dtype=torch.int32, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
-    prio = gc.PRIORITY_LARGEST_FIRST if args.priority == "lf" else gc.PRIORITY_HASH
+    prio = {"hash": gc.PRIORITY_HASH, "lf": gc.PRIORITY_LARGEST_FIRST, "sl": gc.PRIORITY_SMALLEST_LAST}[args.priority]
     opt = gc.Options(flags=gc.FLAG_TIMING, priority=prio)
     mode = args.mode
     start = None
@@ -511,7 +511,7 @@ def main():
             key, desc = CPU_SAMPLE.get(args.workload, (args.workload, "the same graph, full deterministic coloring"))
             sg = gg.workload(key)
             t0 = time.perf_counter()
-            ro = oracle.det(sg, HASH_SEED, priority=1 if args.priority == "lf" else 0)
+            ro = oracle.det(sg, HASH_SEED, priority={"hash": 0, "lf": 1, "sl": 2}[args.priority])
             tc = time.perf_counter() - t0
             cpu = {"value": (sg.nnz / 2) / tc / 1e9, "unit": "Gedges/s", "cores": cpu_cores_used(), "kind": "oracle",
                    "sample": desc + f" ({tc:.1f} s, {ro.rounds} rounds)",
@@ -523,7 +523,8 @@ def main():
             "config": {"workload": args.workload, "graph": WORKLOAD_DESC.get(args.workload, g.name), "n": g.n,
                        "nnz": g.nnz,
                        "mode": {"det": "deterministic", "inplace": "in-place"}.get(mode, mode), "hash_seed": HASH_SEED,
-                       "priority": "largest degree first" if args.priority == "lf" else "hash",
+                       "priority": {"hash": "hash", "lf": "largest degree first",
+                                    "sl": "smallest last (batch peeling)"}[args.priority],
                        "l2": "flushed between steps (512 MB write) and colidx > L2", "parallelism":
                        "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -534,7 +535,9 @@ def main():
             "e2e": e2e,
             # setup, degree sort (2), expand, round kernel, color count (2) per coloring; ordered mode
             # and recoloring: setup, counting pass, round kernel, color count (2)
-            "gpu_launches": (5 if mode in ("ordered", "recolor") else 7) * args.steps,
+            # (smallest last adds the peeling's two: its set-up and the peeling kernel)
+            "gpu_launches": ((5 if mode in ("ordered", "recolor") else 7) + (2 if args.priority == "sl" else 0))
+            * args.steps,
             "clocks": clk,
             "rounds": r0.rounds, "ncolors": r0.ncolors, "greedy_ncolors": greedy_colors,
             **({"ncolors_before_recolor": start.ncolors} if start is not None else {}),

@@ -86,8 +86,13 @@ enum { GC_MODE_DETERMINISTIC = 0, GC_MODE_INPLACE = 1, GC_MODE_PARTITION = 2, GC
 /* Priority keys (which endpoint of a monochromatic edge keeps its color: the smaller key).
  *   GC_PRIORITY_HASH           key(v) = (h(v), v)
  *   GC_PRIORITY_LARGEST_FIRST  key(v) = (-min(deg(v), 2^20 - 1), h(v), v): larger degrees first, an
- *                              ordering the paper lists as future work (Section 6) */
-enum { GC_PRIORITY_HASH = 0, GC_PRIORITY_LARGEST_FIRST = 1 };
+ *                              ordering the paper lists as future work (Section 6)
+ *   GC_PRIORITY_SMALLEST_LAST  key(v) = (-min(level(v), 2^20 - 1), h(v), v) with level(v) the
+ *                              smallest-last peel level of gc_smallest_last: vertices peeled last
+ *                              first.  In GC_MODE_ORDERED this is First Fit in (batch) smallest-last
+ *                              order, which uses at most degeneracy + 1 colors.  Single graphs only
+ *                              (gc_color / gc_color_ex; not GC_MODE_PARTITION, not batches). */
+enum { GC_PRIORITY_HASH = 0, GC_PRIORITY_LARGEST_FIRST = 1, GC_PRIORITY_SMALLEST_LAST = 2 };
 
 /* Flags for gc_options.flags */
 #define GC_FLAG_STATS 1u     /* fill gc_stats' per-round worklist sizes and scanned entries */
@@ -118,8 +123,8 @@ typedef struct gc_options {
     uint32_t flags;            /* GC_FLAG_* */
     int32_t partitions;        /* GC_MODE_PARTITION: number of blocks p (clamped to 1..n); 0 = one per
                                   resident warp of the round kernel */
-    int32_t priority;          /* deterministic and in-place modes: GC_PRIORITY_HASH (default) or
-                                  GC_PRIORITY_LARGEST_FIRST */
+    int32_t priority;          /* deterministic, in-place and ordered modes: GC_PRIORITY_HASH (default),
+                                  GC_PRIORITY_LARGEST_FIRST or GC_PRIORITY_SMALLEST_LAST */
     int32_t reserved[6];
 } gc_options;
 
@@ -180,6 +185,20 @@ int gc_color_ex(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mod
  */
 int gc_recolor(int32_t n, const int32_t *rowptr, const int32_t *colidx, const int32_t *colors_in, uint64_t seed,
                int32_t *colors_out, int32_t *ncolors, int32_t *rounds, const gc_options *opt, gc_stats *stats);
+
+/*
+ * gc_smallest_last -- smallest-last levels by batch peeling (the ordering of
+ * GC_PRIORITY_SMALLEST_LAST).  res(v) starts at deg(v) and a threshold k at 0; while vertices
+ * remain, k becomes max(k, the least res among them), then, level after level, every remaining
+ * vertex with res <= k is removed together and lowers res of each neighbour by one.
+ *   level_out   int32[n] (device or host) receives the level (1, 2, ...) that removed each vertex
+ *   nlevels     host int32* receives the number of levels (may be NULL)
+ *   degeneracy  host int32* receives the largest threshold, the graph's degeneracy (may be NULL)
+ *   opt         stream, spin_limit_ns and GC_FLAG_VALIDATE are used (may be NULL)
+ * Errors as gc_color.
+ */
+int gc_smallest_last(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t *level_out, int32_t *nlevels,
+                     int32_t *degeneracy, const gc_options *opt);
 
 /*
  * gc_color_batch -- color G independent graphs in one persistent launch (every graph runs

@@ -72,9 +72,11 @@ def _L():
         lib.oracle_det.restype = ctypes.c_int
         lib.oracle_det.argtypes = [i32, p, p, u64, i32, p, p, p, p, p, i32, p]
         lib.oracle_det_prio.restype = ctypes.c_int
-        lib.oracle_det_prio.argtypes = [i32, p, p, u64, i32, i32, p, p, p, p, p, i32, p]
+        lib.oracle_det_prio.argtypes = [i32, p, p, u64, i32, p, i32, p, p, p, p, p, i32, p]
         lib.oracle_greedy_keyorder.restype = i32
         lib.oracle_greedy_keyorder.argtypes = [i32, p, p, u64, i32, p, p]
+        lib.oracle_peel_levels.restype = i32
+        lib.oracle_peel_levels.argtypes = [i32, p, p, p]
         lib.oracle_keyorder_depth.restype = i32
         lib.oracle_keyorder_depth.argtypes = [i32, p, p, u64, i32, p, p]
         lib.oracle_key_less_lf.restype = ctypes.c_int
@@ -160,7 +162,8 @@ class DetResult:
 
 PRIORITY_HASH = 0
 PRIORITY_LARGEST_FIRST = 1
-PRIORITY_RECOLOR = 2  # key (-min(c(v), 2^20 - 1), h(v), v) for a given coloring c
+PRIORITY_SMALLEST_LAST = 2  # key (-min(level(v), 2^20 - 1), h(v), v), level from peel_levels
+PRIORITY_RECOLOR = 3  # key (-min(c(v), 2^20 - 1), h(v), v) for a given coloring c
 
 
 def key_less_lf(seed: int, u: int, v: int, du: int, dv: int) -> bool:
@@ -168,7 +171,21 @@ def key_less_lf(seed: int, u: int, v: int, du: int, dv: int) -> bool:
     return bool(_L().oracle_key_less_lf(seed & U64, u, v, du, dv))
 
 
+def peel_levels(g) -> tuple[np.ndarray, int]:
+    """Smallest-last levels by batch peeling (level[v] >= 1 is the batch that removed v; later
+    batches are colored first) and the largest threshold reached, the degeneracy."""
+    rp, ci = _csr(g)
+    level = np.empty(max(g.n, 1), dtype=np.int32)
+    k = _L().oracle_peel_levels(g.n, rp.ctypes.data, ci.ctypes.data, level.ctypes.data)
+    if k < 0:
+        raise MemoryError("oracle_peel_levels")
+    return level[:g.n], int(k)
+
+
 def _colors_in(g, priority, colors_in):
+    if priority == PRIORITY_SMALLEST_LAST:
+        a = np.ascontiguousarray(peel_levels(g)[0], dtype=np.int32)
+        return (a.ctypes.data if a.size else None), a
     if priority != PRIORITY_RECOLOR:
         return None, None
     a = np.ascontiguousarray(colors_in, dtype=np.int32)
@@ -208,7 +225,8 @@ def det(g, seed: int, max_rounds: int | None = None, stats_cap: int = 1 << 16,
     """Deterministic speculative coloring, round by round.  `status` is 0, or -1 when the round
     cap (default n + 1) was reached with a non-empty worklist.  `last_round[v]` is the last round
     whose worklist held v (worklists only shrink, so v was on W_1..W_last_round[v]).  priority:
-    PRIORITY_HASH (key = hash, id) or PRIORITY_LARGEST_FIRST (key = -capped degree, hash, id)."""
+    PRIORITY_HASH (key = hash, id), PRIORITY_LARGEST_FIRST (key = -capped degree, hash, id) or
+    PRIORITY_SMALLEST_LAST (key = -capped peel level, hash, id)."""
     rp, ci = _csr(g)
     n = g.n
     if max_rounds is None:
@@ -220,7 +238,8 @@ def det(g, seed: int, max_rounds: int | None = None, stats_cap: int = 1 << 16,
     nc = ctypes.c_int32(0)
     rd = ctypes.c_int32(0)
     last = np.zeros(max(n, 1), dtype=np.int32)
-    st = _L().oracle_det_prio(n, rp.ctypes.data, ci.ctypes.data, seed & U64, int(priority), max_rounds,
+    pin, keep = _colors_in(g, priority, None) if priority == PRIORITY_SMALLEST_LAST else (None, None)
+    st = _L().oracle_det_prio(n, rp.ctypes.data, ci.ctypes.data, seed & U64, int(priority), pin, max_rounds,
                               colors.ctypes.data, ctypes.byref(nc), ctypes.byref(rd), wl.ctypes.data, ds.ctypes.data,
                               cap, last.ctypes.data)
     if st == -2:

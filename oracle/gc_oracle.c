@@ -34,6 +34,7 @@
  *
  * Everything is single-threaded and unoptimised on purpose, so it can be read against the paper.
  */
+#include <limits.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -149,7 +150,7 @@ static int ko_cmp(const void *a, const void *b) {
     int less;
     if (g_ko_priority == 1)
         less = oracle_key_less_lf(g_ko_seed, u, v, g_ko_rowptr[u + 1] - g_ko_rowptr[u], g_ko_rowptr[v + 1] - g_ko_rowptr[v]);
-    else if (g_ko_priority == 2) /* recoloring: the given colors take the place of the degrees */
+    else if (g_ko_priority == 2 || g_ko_priority == 3) /* a per-vertex rank in place of the degree */
         less = oracle_key_less_lf(g_ko_seed, u, v, g_ko_colors_in[u], g_ko_colors_in[v]);
     else
         less = oracle_key_less(g_ko_seed, u, v);
@@ -157,9 +158,10 @@ static int ko_cmp(const void *a, const void *b) {
 }
 
 /* Sequential First Fit in increasing key order (priority 0: hash key, 1: largest degree first,
- * 2: largest color of colors_in first, the recoloring pass of iterated greedy): the vertices are
- * sorted by key, then each takes the least color its already-colored neighbours do not use.
- * colors_in is read for priority 2 only (entries >= 0).  Returns the number of colors (-1 on OOM). */
+ * 2 and 3: largest rank[v] first -- the peel level of oracle_peel_levels for the smallest-last
+ * order, the given color for the recoloring pass of iterated greedy): the vertices are sorted by
+ * key, then each takes the least color its already-colored neighbours do not use.  rank is read
+ * for priorities 2 and 3 only (entries >= 0).  Returns the number of colors (-1 on OOM). */
 int32_t oracle_greedy_keyorder(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed,
                                int32_t priority, const int32_t *colors_in, int32_t *colors) {
     if (n <= 0) return 0;
@@ -188,6 +190,48 @@ int32_t oracle_greedy_keyorder(int32_t n, const int32_t *rowptr, const int32_t *
     free(order);
     free(seen);
     return used;
+}
+
+/* Smallest-last order by batch peeling (reading of the "other orderings" of the paper's future
+ * work): res[v] starts at deg(v) and k at 0.  While vertices remain: k <- max(k, least res among
+ * them); then, while some remaining vertex has res <= k, all such vertices are removed together as
+ * the next level (1, 2, ...) and each removal lowers res of every neighbour by one.  level[v] is the
+ * level that removed v; the smallest-last key colors larger levels first.  Returns the largest k,
+ * which is the degeneracy of the graph (-1 on OOM). */
+int32_t oracle_peel_levels(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t *level) {
+    if (n <= 0) return 0;
+    int32_t *res = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *F = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!res || !F) {
+        free(res);
+        free(F);
+        return -1;
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        res[v] = rowptr[v + 1] - rowptr[v];
+        level[v] = 0;
+    }
+    int32_t k = 0, L = 0, remaining = n;
+    while (remaining > 0) {
+        int32_t kmin = INT32_MAX;
+        for (int32_t v = 0; v < n; ++v)
+            if (level[v] == 0 && res[v] < kmin) kmin = res[v];
+        if (kmin > k) k = kmin;
+        for (;;) {
+            int32_t nf = 0;
+            for (int32_t v = 0; v < n; ++v)
+                if (level[v] == 0 && res[v] <= k) F[nf++] = v;
+            if (nf == 0) break;
+            L += 1;
+            for (int32_t i = 0; i < nf; ++i) level[F[i]] = L;
+            for (int32_t i = 0; i < nf; ++i)
+                for (int32_t j = rowptr[F[i]]; j < rowptr[F[i] + 1]; ++j) res[colidx[j]] -= 1;
+            remaining -= nf;
+        }
+    }
+    free(res);
+    free(F);
+    return k;
 }
 
 /* Rounds of First Fit in key order when every vertex is colored as soon as all its smaller-key
@@ -243,15 +287,16 @@ int32_t oracle_keyorder_depth(int32_t n, const int32_t *rowptr, const int32_t *c
  *       W <- L
  *       -- barrier --
  *
- * key: priority 0, the hash order (oracle_key_less); 1, largest degree first (oracle_key_less_lf).
+ * key: priority 0, the hash order (oracle_key_less); 1, largest degree first (oracle_key_less_lf);
+ * 2 and 3, largest rank[v] first (the same comparison with rank[v] in place of the degree).
  * Outputs the colors, the number of distinct colors and the number of rounds.  When `stats_cap`
  * > 0, wl_size[r-1] = |W_r| and wl_degsum[r-1] = sum of deg(v) over W_r for the first stats_cap
  * rounds.  When `last_round` is not NULL, last_round[v] = the last round whose worklist held v.
  * Returns 0, or -1 if W is still non-empty after `max_rounds` rounds, or -2 on OOM.
  */
 int oracle_det_prio(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed, int32_t priority,
-                    int32_t max_rounds, int32_t *C, int32_t *ncolors, int32_t *rounds, int64_t *wl_size,
-                    int64_t *wl_degsum, int32_t stats_cap, int32_t *last_round) {
+                    const int32_t *rank, int32_t max_rounds, int32_t *C, int32_t *ncolors, int32_t *rounds,
+                    int64_t *wl_size, int64_t *wl_degsum, int32_t stats_cap, int32_t *last_round) {
     *ncolors = 0;
     *rounds = 0;
     if (n <= 0) return 0;
@@ -292,9 +337,10 @@ int oracle_det_prio(int32_t n, const int32_t *rowptr, const int32_t *colidx, uin
             int32_t v = W[i];
             for (int32_t j = rowptr[v]; j < rowptr[v + 1]; ++j) {
                 int32_t u = colidx[j];
-                int keeps = priority == 1 ? oracle_key_less_lf(seed, u, v, rowptr[u + 1] - rowptr[u],
-                                                               rowptr[v + 1] - rowptr[v])
-                                          : oracle_key_less(seed, u, v);
+                int keeps = priority == 1   ? oracle_key_less_lf(seed, u, v, rowptr[u + 1] - rowptr[u],
+                                                                 rowptr[v + 1] - rowptr[v])
+                            : priority >= 2 ? oracle_key_less_lf(seed, u, v, rank[u], rank[v])
+                                            : oracle_key_less(seed, u, v);
                 if (C[u] == C[v] && keeps) {
                     L[ln++] = v;
                     break;
@@ -319,7 +365,7 @@ int oracle_det_prio(int32_t n, const int32_t *rowptr, const int32_t *colidx, uin
 int oracle_det(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed, int32_t max_rounds,
                int32_t *C, int32_t *ncolors, int32_t *rounds, int64_t *wl_size, int64_t *wl_degsum,
                int32_t stats_cap, int32_t *last_round) {
-    return oracle_det_prio(n, rowptr, colidx, seed, 0, max_rounds, C, ncolors, rounds, wl_size, wl_degsum,
+    return oracle_det_prio(n, rowptr, colidx, seed, 0, NULL, max_rounds, C, ncolors, rounds, wl_size, wl_degsum,
                            stats_cap, last_round);
 }
 

@@ -18,7 +18,7 @@ import numpy as np
 
 __all__ = [
     "GCError", "load", "color", "color_batch", "validate", "Options", "Stats", "Server", "MODE_DETERMINISTIC",
-    "MODE_INPLACE", "MODE_PARTITION", "MODE_ORDERED", "PRIORITY_HASH", "PRIORITY_LARGEST_FIRST", "version", "release_scratch",
+    "MODE_INPLACE", "MODE_PARTITION", "MODE_ORDERED", "PRIORITY_HASH", "PRIORITY_LARGEST_FIRST", "PRIORITY_SMALLEST_LAST", "smallest_last", "recolor", "version", "release_scratch",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -41,6 +41,7 @@ MODE_PARTITION = 2
 MODE_ORDERED = 3
 PRIORITY_HASH = 0
 PRIORITY_LARGEST_FIRST = 1
+PRIORITY_SMALLEST_LAST = 2
 FLAG_STATS = 1
 FLAG_TIMING = 2
 FLAG_VALIDATE = 4
@@ -106,6 +107,8 @@ def load(path: str | None = None):
     lib.gc_color_ex.argtypes = [i32, p, p, c_int, u64, p, p, p, P(_Options), P(_Stats)]
     lib.gc_recolor.restype = c_int
     lib.gc_recolor.argtypes = [i32, p, p, p, u64, p, p, p, P(_Options), P(_Stats)]
+    lib.gc_smallest_last.restype = c_int
+    lib.gc_smallest_last.argtypes = [i32, p, p, p, p, p, P(_Options)]
     lib.gc_color_batch.restype = c_int
     lib.gc_color_batch.argtypes = [i32, p, p, p, p, c_int, u64, p, p, p]
     lib.gc_color_batch_ex.restype = c_int
@@ -256,6 +259,25 @@ def recolor(rowptr, colidx, colors_in, seed: int = 0, out=None, options: Options
     colors_in (int32[n], >= 0), the largest color first; never more colors than colors_in has
     when colors_in is proper."""
     return _color_one(rowptr, colidx, "ordered", seed, out, options, stats, round_cap, colors_in)
+
+
+def smallest_last(rowptr, colidx, out=None, options: Options | None = None):
+    """Smallest-last levels by batch peeling (gc_smallest_last).  Returns (level[n], number of
+    levels, degeneracy); level is on the device when rowptr is a CUDA tensor."""
+    lib = load()
+    n = (rowptr.numel() if _is_torch(rowptr) else len(rowptr)) - 1
+    if n < 0:
+        raise GCError(GC_ERR_INVALID_ARG, "rowptr must have n+1 entries")
+    prp, rowptr_k = _ptr(rowptr, np.int32)
+    pci, colidx_k = _ptr(colidx, np.int32)
+    if out is None:
+        out = _empty_like_home(rowptr, n)
+    pout, out_k = _ptr(out, np.int32)
+    nl = ctypes.c_int32(0)
+    dg = ctypes.c_int32(0)
+    copt = (options or Options())._c(_current_stream(rowptr, colidx, out))
+    _check(lib.gc_smallest_last(n, prp, pci, pout, ctypes.byref(nl), ctypes.byref(dg), ctypes.byref(copt)))
+    return (out_k if out_k is not None else out), int(nl.value), int(dg.value)
 
 
 def _color_one(rowptr, colidx, mode, seed, out, options, stats, round_cap, colors_in) -> Result:

@@ -80,6 +80,7 @@ struct Ctl {
     unsigned long long list_total, list_alloc;
     int32_t gmax1, gcount1, glast1, pad1;
     int32_t pad2[2];
+    unsigned peel[4];  // smallest-last peeling: the two threshold words, the work items needed
     GridBar bar;
 };
 static_assert(offsetof(Ctl, bar) % 128 == 0, "barrier alignment");
@@ -92,13 +93,14 @@ struct Context {
     int occ[2][2][2][2] = {};  // [wide][mode][batch][compact] blocks per SM of the round kernel
     int occ_part = 0;       // blocks per SM of the partition-mode round kernel
     int occ_ord[2] = {};    // blocks per SM of the ordered-mode round kernel [batch]
+    int occ_peel = 0;       // blocks per SM of the peeling kernel
     Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, lists, ctl, stats, bitmap, vg, hist;
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
-    Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors, st_colors_in, mid0, mid1;
+    Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors, st_colors_in, mid0, mid1, rank;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     void release_all() {
         Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &lists, &ctl, &stats, &bitmap, &hist,
-                      &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors, &st_colors_in, &mid0, &mid1};
+                      &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors, &st_colors_in, &mid0, &mid1, &rank};
         for (Buf *b : all) b->release();
     }
 };
@@ -212,7 +214,7 @@ struct Problem {
     const int32_t *colidx;
     const int64_t *vtx_off;
     const int64_t *edge_off;
-    const int32_t *prio_colors = nullptr;  // recoloring pass: the given coloring (device view)
+    const int32_t *prio_rank = nullptr;  // recoloring pass: the given coloring (device view)
     int32_t priority_override = -1;        // >= 0: the priority to use instead of the options'
 };
 
@@ -221,6 +223,51 @@ struct Outputs {
     int32_t *ncolors;  // single: host scalar; batch: caller array of G
     int32_t *rounds;
 };
+
+// Smallest-last levels of a single graph into C.rank (int32[n]): the peeling kernel with the
+// ordered mode's lists; the residual degrees live in C.col1, which every mode rewrites afterwards.
+// P holds the graph, the control block and the barrier; the counter sets must be zero.
+static int peel_levels(Context &C, Ctl *ctl, RoundParams P, int32_t T1, int32_t CH, cudaStream_t s,
+                       int32_t *nlevels, int32_t *degeneracy) {
+    const size_t n = static_cast<size_t>(P.n);
+    GC_TRY(ensure(C.rank, 4 * n, "smallest-last levels"));
+    GC_TRY(ensure(C.col1, 8 * n, "vertex state"));
+    GC_TRY(ensure(C.small0, 4 * n, "worklist"));
+    GC_TRY(ensure(C.small1, 4 * n, "worklist"));
+    GC_TRY(ensure(C.mid0, 4 * n, "worklist"));
+    GC_TRY(ensure(C.mid1, 4 * n, "worklist"));
+    P.T1 = T1 < kOrdSmall ? T1 : kOrdSmall;
+    P.CH = CH < kOrdChunk ? CH : kOrdChunk;
+    P.pass_begin = 1;
+    int32_t *res = reinterpret_cast<int32_t *>(C.col1.p);
+    int32_t *level = C.rank.as<int32_t>();
+    GC_CUDA(cudaMemsetAsync(ctl->peel, 0, sizeof(ctl->peel), s));
+    GC_CUDA(launch_peel_init(P, res, level, ctl->peel, ctl->peel + 2, s));
+    Ctl h{};
+    GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    if (h.err[0] != 0) return error_from_ctl(h);
+    const size_t n_items = h.peel[2];
+    GC_TRY(ensure(C.chunk0, 16 * std::max<size_t>(n_items, 1), "work items"));
+    GC_TRY(ensure(C.chunk1, 16 * std::max<size_t>(n_items, 1), "work items"));
+    P.small0 = C.small0.as<int32_t>();
+    P.small1 = C.small1.as<int32_t>();
+    P.mid0 = C.mid0.as<int32_t>();
+    P.mid1 = C.mid1.as<int32_t>();
+    P.chunk0 = C.chunk0.as<int4>();
+    P.chunk1 = C.chunk1.as<int4>();
+    GC_CUDA(cudaMemsetAsync(ctl->cnt, 0, sizeof(ctl->cnt), s));
+    int &occ = C.occ_peel;
+    if (occ == 0) GC_CUDA(peel_kernel_occupancy(256, &occ));
+    const int grid = occ * C.sms;
+    GC_CUDA(launch_peel(P, res, level, ctl->peel, grid, 256, s));
+    GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    if (h.err[0] != 0) return error_from_ctl(h);
+    if (nlevels) *nlevels = h.passes[0];
+    if (degeneracy) *degeneracy = h.passes[1];
+    return GC_OK;
+}
 
 static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_options *opt, gc_stats *stats,
                const Outputs &out) {
@@ -234,8 +281,11 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     if (CH < 32 || CH > 1024 || CH % 32) return set_last_error(GC_ERR_INVALID_ARG, "chunk %d invalid", CH);
     if (block != 256) return set_last_error(GC_ERR_INVALID_ARG, "block_size %d unsupported (256)", block);
     const int32_t opt_priority = opt ? opt->priority : GC_PRIORITY_HASH;
-    if (opt_priority != GC_PRIORITY_HASH && opt_priority != GC_PRIORITY_LARGEST_FIRST)
+    if (opt_priority != GC_PRIORITY_HASH && opt_priority != GC_PRIORITY_LARGEST_FIRST &&
+        opt_priority != GC_PRIORITY_SMALLEST_LAST)
         return set_last_error(GC_ERR_INVALID_ARG, "unknown priority %d", opt_priority);
+    if (opt_priority == GC_PRIORITY_SMALLEST_LAST && pb.priority_override < 0 && pb.batch)
+        return set_last_error(GC_ERR_INVALID_ARG, "GC_PRIORITY_SMALLEST_LAST colors single graphs only");
     const int32_t priority = pb.priority_override >= 0 ? pb.priority_override : opt_priority;
     const int64_t n = pb.n;
     const int32_t G = pb.G;
@@ -320,7 +370,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     P.T1 = T1;
     P.CH = CH;
     P.priority = priority;
-    P.prio_colors = pb.prio_colors;
+    P.prio_rank = pb.prio_rank;
 
     const bool timing = (flags & GC_FLAG_TIMING) != 0;
     Ctl h{};
@@ -332,6 +382,13 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
         if (h.err[0] != 0) return error_from_ctl(h);
     }
     if (timing) GC_CUDA(cudaEventRecord(C.ev[0], s));
+    if (priority == GC_PRIORITY_SMALLEST_LAST && mode != GC_MODE_PARTITION && n > 0) {
+        int32_t nlev = 0, degen = 0;
+        GC_TRY(peel_levels(C, ctl, P, T1, CH, s, &nlev, &degen));
+        P.prio_rank = C.rank.as<int32_t>();
+        GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+        GC_CUDA(cudaMemsetAsync(&ctl->gmax1, 0xff, sizeof(int32_t), s));
+    }
     int64_t grid = 0;
     if (mode == GC_MODE_PARTITION) {
         // Algorithm 1 with p id-ordered blocks: its own set-up and round kernel
@@ -528,6 +585,43 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     return GC_OK;
 }
 
+// Device views of a single graph's CSR (host arrays staged), with GC_FLAG_VALIDATE applied.
+static int single_problem(Context *C, int32_t n, const int32_t *rowptr, const int32_t *colidx, const gc_options *opt,
+                          cudaStream_t s, Problem &pb) {
+    int rp_dev = 0;
+    GC_TRY(locate(rowptr, C->device, &rp_dev));
+    int32_t nnz32 = 0;
+    if (rp_dev) {
+        GC_CUDA(cudaMemcpyAsync(&nnz32, rowptr + n, 4, cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+    } else {
+        nnz32 = rowptr[n];
+    }
+    if (nnz32 < 0) return set_last_error(GC_ERR_INVALID_GRAPH, "rowptr[n] = %d is negative", nnz32);
+    if (nnz32 > 0 && !colidx) return set_last_error(GC_ERR_INVALID_ARG, "NULL colidx with %d entries", nnz32);
+    pb.batch = false;
+    pb.G = 1;
+    pb.n = n;
+    pb.nnz = nnz32;
+    const void *v = nullptr;
+    GC_TRY(device_view(rowptr, 4 * (static_cast<size_t>(n) + 1), C->device, C->st_rowptr, s, &v));
+    pb.rowptr = static_cast<const int32_t *>(v);
+    GC_TRY(device_view(colidx, 4 * static_cast<size_t>(nnz32), C->device, C->st_colidx, s, &v));
+    pb.colidx = static_cast<const int32_t *>(v);
+    if (opt && (opt->flags & GC_FLAG_VALIDATE)) {
+        GC_TRY(ensure(C->ctl, sizeof(Ctl), "control"));
+        Ctl *ctl = C->ctl.as<Ctl>();
+        GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+        GC_CUDA(launch_validate(n, pb.rowptr, pb.colidx ? pb.colidx : pb.rowptr, GC_VALIDATE_ALL, ctl->err, s));
+        Ctl h{};
+        GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+        if (h.err[0] != 0) return error_from_ctl(h);
+    }
+    if (!pb.colidx) pb.colidx = pb.rowptr;  // never dereferenced when nnz == 0
+    return GC_OK;
+}
+
 static int color_single(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, uint64_t seed,
                         int32_t *colors_out, int32_t *ncolors, int32_t *rounds, const gc_options *opt,
                         gc_stats *stats, const int32_t *colors_in = nullptr) {
@@ -556,41 +650,12 @@ static int color_single(int32_t n, const int32_t *rowptr, const int32_t *colidx,
         return GC_OK;
     }
     cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C->stream;
-    int rp_dev = 0;
-    GC_TRY(locate(rowptr, C->device, &rp_dev));
-    int32_t nnz32 = 0;
-    if (rp_dev) {
-        GC_CUDA(cudaMemcpyAsync(&nnz32, rowptr + n, 4, cudaMemcpyDeviceToHost, s));
-        GC_CUDA(cudaStreamSynchronize(s));
-    } else {
-        nnz32 = rowptr[n];
-    }
-    if (nnz32 < 0) return set_last_error(GC_ERR_INVALID_GRAPH, "rowptr[n] = %d is negative", nnz32);
-    if (nnz32 > 0 && !colidx) return set_last_error(GC_ERR_INVALID_ARG, "NULL colidx with %d entries", nnz32);
     Problem pb{};
-    pb.batch = false;
-    pb.G = 1;
-    pb.n = n;
-    pb.nnz = nnz32;
+    GC_TRY(single_problem(C, n, rowptr, colidx, opt, s, pb));
     const void *v = nullptr;
-    GC_TRY(device_view(rowptr, 4 * (static_cast<size_t>(n) + 1), C->device, C->st_rowptr, s, &v));
-    pb.rowptr = static_cast<const int32_t *>(v);
-    GC_TRY(device_view(colidx, 4 * static_cast<size_t>(nnz32), C->device, C->st_colidx, s, &v));
-    pb.colidx = static_cast<const int32_t *>(v);
-    if (opt && (opt->flags & GC_FLAG_VALIDATE)) {
-        GC_TRY(ensure(C->ctl, sizeof(Ctl), "control"));
-        Ctl *ctl = C->ctl.as<Ctl>();
-        GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
-        GC_CUDA(launch_validate(n, pb.rowptr, pb.colidx ? pb.colidx : pb.rowptr, GC_VALIDATE_ALL, ctl->err, s));
-        Ctl h{};
-        GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-        GC_CUDA(cudaStreamSynchronize(s));
-        if (h.err[0] != 0) return error_from_ctl(h);
-    }
-    if (!pb.colidx) pb.colidx = pb.rowptr;  // never dereferenced when nnz == 0
     if (colors_in) {
         GC_TRY(device_view(colors_in, 4 * static_cast<size_t>(n), C->device, C->st_colors_in, s, &v));
-        pb.prio_colors = static_cast<const int32_t *>(v);
+        pb.prio_rank = static_cast<const int32_t *>(v);
         pb.priority_override = kPriorityRecolor;
     }
     Outputs o{colors_out, ncolors, rounds};
@@ -666,6 +731,54 @@ int gc_color(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, 
 int gc_color_ex(int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, uint64_t seed, int32_t *colors_out,
                 int32_t *ncolors, int32_t *rounds, const gc_options *opt, gc_stats *stats) {
     return gc::color_single(n, rowptr, colidx, mode, seed, colors_out, ncolors, rounds, opt, stats);
+}
+
+int gc_smallest_last(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t *level_out, int32_t *nlevels,
+                     int32_t *degeneracy, const gc_options *opt) {
+    using namespace gc;
+    if (n < 0) return set_last_error(GC_ERR_INVALID_ARG, "n = %d is negative", n);
+    if (n > 0 && (!rowptr || !level_out)) return set_last_error(GC_ERR_INVALID_ARG, "NULL rowptr or level_out");
+    if (n == INT32_MAX) return set_last_error(GC_ERR_INVALID_ARG, "n too large");
+    const int32_t T1 = (opt && opt->small_max_degree) ? opt->small_max_degree : 127;
+    const int32_t CH = (opt && opt->chunk) ? opt->chunk : 1024;
+    if (T1 < 1 || T1 > 127) return set_last_error(GC_ERR_INVALID_ARG, "small_max_degree %d outside 1..127", T1);
+    if (CH < 32 || CH > 1024 || CH % 32) return set_last_error(GC_ERR_INVALID_ARG, "chunk %d invalid", CH);
+    Context *C = nullptr;
+    GC_TRY(get_context(&C));
+    std::lock_guard<std::mutex> lk(C->mu);
+    GC_CUDA(cudaSetDevice(C->device));
+    if (n == 0) {
+        if (nlevels) *nlevels = 0;
+        if (degeneracy) *degeneracy = 0;
+        return GC_OK;
+    }
+    cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C->stream;
+    Problem pb{};
+    GC_TRY(single_problem(C, n, rowptr, colidx, opt, s, pb));
+    GC_TRY(ensure(C->ctl, sizeof(Ctl), "control"));
+    Ctl *ctl = C->ctl.as<Ctl>();
+    GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    RoundParams P{};
+    P.n = n;
+    P.G = 1;
+    P.nnz = pb.nnz;
+    P.rowptr = pb.rowptr;
+    P.colidx = pb.colidx;
+    P.cnt = ctl->cnt;
+    P.bar = &ctl->bar;
+    P.err = ctl->err;
+    P.passes = ctl->passes;
+    P.spin_ns = (opt && opt->spin_limit_ns > 0) ? opt->spin_limit_ns : 1000000000LL;
+    int32_t nl = 0, dg = 0;
+    GC_TRY(peel_levels(*C, ctl, P, T1, CH, s, &nl, &dg));
+    int out_dev = 0;
+    GC_TRY(locate(level_out, C->device, &out_dev));
+    GC_CUDA(cudaMemcpyAsync(level_out, C->rank.p, 4 * static_cast<size_t>(n),
+                            out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    if (nlevels) *nlevels = nl;
+    if (degeneracy) *degeneracy = dg;
+    return GC_OK;
 }
 
 int gc_recolor(int32_t n, const int32_t *rowptr, const int32_t *colidx, const int32_t *colors_in, uint64_t seed,

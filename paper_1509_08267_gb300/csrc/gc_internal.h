@@ -49,7 +49,7 @@ constexpr int kOrdSmall = 8;
 constexpr int kOrdMid = 32;  // degree <= kOrdMid (and > the small bound): an 8-lane group each
 // Priority of the recoloring pass (gc_recolor): key(v) = (-min(c(v), 2^20 - 1), h(v), v) for the
 // given coloring c, the color classes in decreasing color order.
-constexpr int32_t kPriorityRecolor = 2;
+constexpr int32_t kPriorityRecolor = 3;
 constexpr int kOrdChunk = 128;
 constexpr int kOrdSlotWords = 32;
 
@@ -123,7 +123,7 @@ struct RoundParams {
     int32_t T1;  // largest degree handled by one thread
     int32_t CH;  // adjacency entries per warp work item
     int32_t priority;  // GC_PRIORITY_* or kPriorityRecolor: what the 31 priority bits of a state word hold
-    const int32_t *prio_colors;  // kPriorityRecolor: the given coloring, int32[n] on the device
+    const int32_t *prio_rank;  // smallest last: the peel levels; recoloring: the given coloring (int32[n])
 };
 
 // Launch wrappers (gc_kernels.cu).  All return the launch's cudaError_t.
@@ -169,6 +169,16 @@ cudaError_t launch_count_colors(const RoundParams &P, bool batch, const int32_t 
 // (small ones in small0, medium ones in mid0, work items {V, q, slot, nch} in chunk0; P.mid0/mid1
 // hold n entries each) and runs the cooperative round kernel on `grid` blocks.
 cudaError_t ordered_kernel_occupancy(bool batch, int block, int *blocks_per_sm);
+// Smallest-last levels (single graph): launch_peel_init sets res[v] = deg(v), level[v] = 0, the two
+// threshold words kw[2] and adds the work items the lists may need (vertices past kOrdMid, P.CH
+// entries each) to *items; launch_peel (counter sets zeroed, P.T1 <= kOrdSmall, P.CH <= kOrdChunk,
+// lists as the ordered mode's) writes level[v] >= 1, the number of levels to passes[0] and the
+// degeneracy to passes[1].
+cudaError_t launch_peel_init(const RoundParams &P, int32_t *res, int32_t *level, unsigned *kw, unsigned *items,
+                             cudaStream_t s);
+cudaError_t peel_kernel_occupancy(int block, int *blocks_per_sm);
+cudaError_t launch_peel(const RoundParams &P, int32_t *res, int32_t *level, unsigned *kw, int grid, int block,
+                        cudaStream_t s);
 cudaError_t launch_ordered(const RoundParams &P, bool batch, int32_t *pend, int grid, int block, cudaStream_t s);
 // Partition mode (GC_MODE_PARTITION, single graph): set-up (rows checked, colors -1, W_1 = V) and
 // the cooperative round kernel with p blocks of consecutive ids.

@@ -81,16 +81,17 @@ __device__ __forceinline__ void set_error(int32_t *err, int code, int32_t a, int
 // to the full hash, then the id, only when they are equal.  GC_PRIORITY_HASH: the top 31 bits of
 // h(v).  GC_PRIORITY_LARGEST_FIRST: 20 bits of 2^20 - 1 - min(deg(v), 2^20 - 1) (a larger degree
 // is a smaller key), then the top 11 bits of h(v); equal bits imply equal capped degrees, so the
-// fallback keeps the order (capped degree, hash, id).  kPriorityRecolor: the same with the vertex's
-// given color in place of its degree (larger colors first).
+// fallback keeps the order (capped degree, hash, id).  GC_PRIORITY_SMALLEST_LAST and
+// kPriorityRecolor: the same with P.prio_rank[V] in place of the degree (the peel level, larger
+// levels first; the given color, larger colors first).
 __device__ __forceinline__ uint32_t priority_bits(const RoundParams &P, uint32_t lv, int64_t deg, int32_t V) {
     const uint64_t h = vertex_hash(P.seed, lv);
-    if (P.priority == kPriorityRecolor) {
-        const int32_t c = P.prio_colors[V];
+    if (P.priority == kPriorityRecolor || P.priority == GC_PRIORITY_SMALLEST_LAST) {
+        const int32_t c = P.prio_rank[V];
         if (c < 0) set_error(P.err, GC_ERR_INVALID_ARG, V, c);
         deg = c < 0 ? 0 : c;
     }
-    if (P.priority == GC_PRIORITY_LARGEST_FIRST || P.priority == kPriorityRecolor) {
+    if (P.priority != GC_PRIORITY_HASH) {
         constexpr uint32_t kCap = (1u << 20) - 1u;
         const uint32_t f = kCap - static_cast<uint32_t>(deg < kCap ? deg : kCap);
         return (f << 11) | static_cast<uint32_t>(h >> 53);
@@ -1962,14 +1963,16 @@ __device__ void ord_list(const RoundParams &P, const bool (&ready)[K], const int
     }
 }
 
-// Counts down the neighbours U[k] (those with take[k]) of a ready vertex: one fewer smaller-key
-// neighbour to wait for; the ones whose count reaches 0 are listed (warp-uniform call).
+// Counts down the neighbours U[k] (those with take[k]): the ones whose count was `fire` before the
+// decrement are listed (warp-uniform call).  Ordered mode: pend, fire 1 (the last smaller-key
+// neighbour was colored).  Peeling: the residual degrees, fire k + 1 (the degree reached k).
 template <bool BATCH, int K>
 __device__ __forceinline__ void ord_release(const RoundParams &P, int32_t *pend, const bool (&take)[K],
-                                            const int32_t (&U)[K], const OrdLists &L, int lane) {
+                                            const int32_t (&U)[K], const OrdLists &L, int lane,
+                                            int32_t fire = 1) {
     bool ready[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) ready[k] = take[k] && atomicSub(pend + U[k], 1) == 1;
+    for (int k = 0; k < K; ++k) ready[k] = take[k] && atomicSub(pend + U[k], 1) == fire;
     ord_list<BATCH, K>(P, ready, U, L, lane);
 }
 
@@ -2237,6 +2240,178 @@ __global__ void __launch_bounds__(kBlock, kWideBlocks) ord_round_kernel(RoundPar
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.passes[0] = pass;
         P.passes[1] = pass - 1;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// smallest-last order (GC_PRIORITY_SMALLEST_LAST, single graphs): batch peeling.  res[v] starts
+// at deg(v), level[v] at 0 (present), the threshold k at 0.  While vertices remain, k becomes
+// max(k, least res among them); then, level after level, every present vertex with res <= k is
+// removed together (level[v] = the level's number) and lowers res of each neighbour by one.  A
+// present vertex whose res falls from k + 1 to k joins the next level, so every level after the
+// first of a threshold is listed by the decrements (one atomic each, as the ordered mode's counts),
+// and each vertex is listed once.  The lists and their degree classes are the ordered mode's.
+// Decrements of removed vertices are harmless: their res is already <= k and never fires.
+
+// res, level and the two threshold words (the least res of a search, alternating).
+__global__ void peel_init_kernel(RoundParams P, int32_t *res, int32_t *level, unsigned *kw, unsigned *items) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) kw[0] = kw[1] = 0x7fffffffu;
+    for (int64_t base = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ll; base < P.n;
+         base += stride) {
+        const int64_t V = base + lane;
+        unsigned nch = 0;
+        if (V < P.n) {
+            int64_t b;
+            int32_t lv;
+            int64_t d = checked_degree<false>(P, static_cast<int32_t>(V), 0, b, lv);
+            if (d < 0) {
+                set_error(P.err, GC_ERR_INVALID_GRAPH, static_cast<int32_t>(V), b);
+                d = 0;
+            }
+            res[V] = static_cast<int32_t>(d);
+            level[V] = 0;
+            if (d > kOrdMid) nch = static_cast<unsigned>((d + P.CH - 1) / P.CH);
+        }
+        nch = __reduce_add_sync(kFull, nch);
+        if (lane == 0 && nch) atomicAdd(items, nch);
+    }
+}
+
+// One level for the vertices of degree <= P.T1, one per lane (lanes with `valid`).
+__device__ __forceinline__ void peel_small(const RoundParams &P, int32_t *res, int32_t *level, bool valid, int32_t V,
+                                           int32_t k, int32_t L, const OrdLists &N, int lane) {
+    int64_t b = 0;
+    int32_t deg = 0;
+    if (valid) {
+        b = __ldg(P.rowptr + V);
+        deg = static_cast<int32_t>(__ldg(P.rowptr + V + 1) - b);
+        level[V] = L;
+    }
+    bool take[kOrdSmall];
+    int32_t U[kOrdSmall];
+#pragma unroll
+    for (int q = 0; q < kOrdSmall; ++q) {
+        U[q] = q < deg ? load_entry(P.colidx + b + q) : 0;
+        take[q] = q < deg && static_cast<uint32_t>(U[q]) < static_cast<uint32_t>(P.n) && U[q] != V;
+        if (q < deg && !take[q]) set_error(P.err, GC_ERR_INVALID_GRAPH, V, b + q);
+    }
+    ord_release<false, kOrdSmall>(P, res, take, U, N, lane, k + 1);
+}
+
+// One level for the vertices of degree in (P.T1, kOrdMid], one per 8-lane group.
+__device__ __forceinline__ void peel_mid(const RoundParams &P, int32_t *res, int32_t *level, bool valid, int32_t V,
+                                         int32_t k, int32_t L, const OrdLists &N, int lane) {
+    const int gl = lane & (kOrdMidLanes - 1);
+    int64_t b = 0;
+    int32_t deg = 0;
+    if (valid) {
+        b = __ldg(P.rowptr + V);
+        deg = static_cast<int32_t>(__ldg(P.rowptr + V + 1) - b);
+        if (gl == 0) level[V] = L;
+    }
+    bool take[kOrdMidPer];
+    int32_t U[kOrdMidPer];
+#pragma unroll
+    for (int q = 0; q < kOrdMidPer; ++q) {
+        const int32_t e = gl + kOrdMidLanes * q;
+        U[q] = e < deg ? load_entry(P.colidx + b + e) : 0;
+        take[q] = e < deg && static_cast<uint32_t>(U[q]) < static_cast<uint32_t>(P.n) && U[q] != V;
+        if (e < deg && !take[q]) set_error(P.err, GC_ERR_INVALID_GRAPH, V, b + e);
+    }
+    ord_release<false, kOrdMidPer>(P, res, take, U, N, lane, k + 1);
+}
+
+// One level for a work item {V, q, slot, nch} of a larger vertex (one warp).
+__device__ __forceinline__ void peel_item(const RoundParams &P, int32_t *res, int32_t *level, int4 it, int32_t k,
+                                          int32_t L, const OrdLists &N, int lane) {
+    const int32_t V = it.x, q = it.y;
+    const int64_t b = __ldg(P.rowptr + V), e = __ldg(P.rowptr + V + 1);
+    const int64_t jb = b + static_cast<int64_t>(q) * P.CH;
+    const int64_t je = min(e, jb + P.CH);
+    if (q == 0 && lane == 0) level[V] = L;
+    for (int64_t j0 = jb; j0 < je; j0 += 32 * kOrdPer) {
+        bool take[kOrdPer];
+        int32_t U[kOrdPer];
+#pragma unroll
+        for (int t = 0; t < kOrdPer; ++t) {
+            const int64_t j = j0 + lane + 32 * t;
+            U[t] = j < je ? load_entry(P.colidx + j) : 0;
+            take[t] = j < je && static_cast<uint32_t>(U[t]) < static_cast<uint32_t>(P.n) && U[t] != V;
+            if (j < je && !take[t]) set_error(P.err, GC_ERR_INVALID_GRAPH, V, j);
+        }
+        ord_release<false, kOrdPer>(P, res, take, U, N, lane, k + 1);
+    }
+}
+
+// The whole peeling in one cooperative launch; passes[0] receives the number of levels and
+// passes[1] the last threshold (the degeneracy).
+__global__ void __launch_bounds__(kBlock, kWideBlocks) peel_kernel(RoundParams P, int32_t *res, int32_t *level,
+                                                                   unsigned *kw) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    const unsigned gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int64_t nthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t gtid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    unsigned bar_target = 0;
+    int32_t k = 0, L = 0;
+    int pass = P.pass_begin;
+    bool ok = true;
+    for (int f = 0; ok; ++f) {
+        // the least res among the present vertices
+        unsigned m = 0x7fffffffu;
+        for (int64_t v = gtid; v < P.n; v += nthreads)
+            if (__ldcg(level + v) == 0) m = min(m, static_cast<unsigned>(__ldcg(res + v)));
+        m = __reduce_min_sync(kFull, m);
+        if (lane == 0 && m != 0x7fffffffu) atomicMin(kw + (f & 1), m);
+        if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
+        const unsigned kmin = __ldcg(kw + (f & 1));
+        if (blockIdx.x == 0 && threadIdx.x == 0) kw[(f + 1) & 1] = 0x7fffffffu;
+        if (kmin == 0x7fffffffu) break;  // every vertex removed
+        if (static_cast<int32_t>(kmin) > k) k = static_cast<int32_t>(kmin);
+        // the first level of this threshold: every present vertex with res <= k
+        {
+            const OrdLists F = ord_lists(P, pass);
+            for (int64_t base = gtid & ~31ll; base < P.n; base += nthreads) {
+                const int64_t v = base + lane;
+                const bool ready[1] = {v < P.n && __ldcg(level + v) == 0 && __ldcg(res + v) <= k};
+                const int32_t Vs[1] = {static_cast<int32_t>(v)};
+                ord_list<false, 1>(P, ready, Vs, F, lane);
+            }
+        }
+        if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
+        for (;; ++pass) {
+            const OrdLists C = ord_lists(P, pass), N = ord_lists(P, pass + 1);
+            const unsigned nsmall = __ldcg(C.cnt + kCntSmall), nmid = __ldcg(C.cnt + kCntMulti);
+            const unsigned nitems = __ldcg(C.cnt + kCntChunks);
+            if (block_error_seen(P.err)) {
+                ok = false;
+                break;
+            }
+            if (nsmall + nmid + nitems == 0u) break;
+            if (blockIdx.x == 0 && threadIdx.x < kCnt) P.cnt[kCnt * ((pass + 2) % 3) + threadIdx.x] = 0u;
+            ++L;
+            for (unsigned i = gw; i < nitems; i += nw) peel_item(P, res, level, __ldcg(C.items + i), k, L, N, lane);
+            const unsigned mid_groups = (nmid + 3u) / 4u;
+            for (unsigned b = (gw + nw - nitems % nw) % nw; b < mid_groups; b += nw) {
+                const unsigned i = 4u * b + static_cast<unsigned>(lane >> 3);
+                peel_mid(P, res, level, i < nmid, i < nmid ? __ldcg(C.mid + i) : 0, k, L, N, lane);
+            }
+            const unsigned skip = (nitems + mid_groups) % nw;
+            for (unsigned base = ((gw + nw - skip) % nw) * 32u; base < nsmall; base += nw * 32u) {
+                const unsigned i = base + lane;
+                peel_small(P, res, level, i < nsmall, i < nsmall ? __ldcg(C.small + i) : 0, k, L, N, lane);
+            }
+            if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) {
+                ok = false;
+                break;
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.passes[0] = L;
+        P.passes[1] = k;
     }
 }
 
@@ -2518,6 +2693,33 @@ cudaError_t launch_ordered(const RoundParams &P, bool batch, int32_t *pend, int 
     return cudaLaunchCooperativeKernel(batch ? reinterpret_cast<const void *>(&ord_round_kernel<true>)
                                              : reinterpret_cast<const void *>(&ord_round_kernel<false>),
                                        dim3(grid), dim3(block), args, 0, s);
+}
+
+cudaError_t launch_peel_init(const RoundParams &P, int32_t *res, int32_t *level, unsigned *kw, unsigned *items,
+                             cudaStream_t s) {
+    const int grid = grid_for(P.n > 0 ? P.n : 1, 256, sm_count() * 16);
+    peel_init_kernel<<<grid, 256, 0, s>>>(P, res, level, kw, items);
+    return cudaGetLastError();
+}
+
+cudaError_t peel_kernel_occupancy(int block, int *blocks_per_sm) {
+    if (block != kBlock) return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, reinterpret_cast<const void *>(&peel_kernel),
+                                                         block, 0);
+}
+
+cudaError_t launch_peel(const RoundParams &P, int32_t *res, int32_t *level, unsigned *kw, int grid, int block,
+                        cudaStream_t s) {
+    if (block != kBlock) return cudaErrorInvalidValue;
+    if (P.n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(&P.bar->count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    RoundParams arg = P;
+    int32_t *ra = res, *la = level;
+    unsigned *ka = kw;
+    void *args[] = {&arg, &ra, &la, &ka};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(&peel_kernel), dim3(grid), dim3(block), args, 0,
+                                       s);
 }
 
 cudaError_t launch_count_colors(const RoundParams &P, bool batch, const int32_t *colors_sel, int32_t v_begin,

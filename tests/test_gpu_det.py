@@ -343,3 +343,65 @@ def test_recolor_rejects_negative_colors(gclib):
     with pytest.raises(gclib.GCError) as e:
         gclib.recolor(rp, ci, cin, 1)
     assert e.value.status == gclib.GC_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------------------------------------
+# smallest-last order (batch peeling) and colorings under its key
+
+SL_GRAPHS = [lambda: gg.path(2), lambda: gg.path(97), lambda: gg.star(5000), lambda: gg.cycle(1000),
+             lambda: gg.complete(40), lambda: gg.complete(600), lambda: gg.empty(33), lambda: gg.crown(40),
+             lambda: gg.grid5(37, 29), lambda: gg.stencil27(9), lambda: gg.er(3000, 12.0, 5),
+             lambda: gg.rmat(12, 16, 2), lambda: gg.rmat(15, 16, 2)]
+
+
+@pytest.mark.parametrize("make", SL_GRAPHS)
+def test_smallest_last_levels_equal_oracle(gclib, make):
+    g = make()
+    ref, k = oracle.peel_levels(g)
+    rp, ci = _dev(g)
+    for opt in [dict(), dict(small_max_degree=3, chunk=64)]:
+        level, nlevels, degen = gclib.smallest_last(rp, ci, options=gclib.Options(**opt))
+        np.testing.assert_array_equal(level.cpu().numpy(), ref, err_msg=str(opt))
+        assert nlevels == (int(ref.max()) if g.n else 0) and degen == k
+    level_h, _, _ = gclib.smallest_last(g.rowptr, g.colidx)  # host arrays
+    np.testing.assert_array_equal(level_h, ref)
+
+
+@pytest.mark.parametrize("make", SL_GRAPHS[-6:])
+def test_smallest_last_colorings_equal_oracle(gclib, make):
+    g = make()
+    rp, ci = _dev(g)
+    sl = gclib.Options(priority=gclib.PRIORITY_SMALLEST_LAST)
+    # deterministic speculative mode: bit-exact, with the per-round worklists
+    ref = oracle.det(g, 7, priority=oracle.PRIORITY_SMALLEST_LAST)
+    r = gclib.color(rp, ci, "det", 7, options=sl, stats=True)
+    np.testing.assert_array_equal(r.colors.cpu().numpy(), ref.colors)
+    assert (r.ncolors, r.rounds) == (ref.ncolors, ref.rounds)
+    np.testing.assert_array_equal(r.stats.wl_size, ref.wl_size)
+    # ordered mode: First Fit in smallest-last order, at most degeneracy + 1 colors
+    _, k = oracle.peel_levels(g)
+    cref, nc = oracle.greedy_keyorder(g, 7, oracle.PRIORITY_SMALLEST_LAST)
+    _, deepest = oracle.keyorder_depth(g, 7, oracle.PRIORITY_SMALLEST_LAST)
+    r = gclib.color(rp, ci, "ordered", 7, options=sl)
+    np.testing.assert_array_equal(r.colors.cpu().numpy(), cref)
+    assert r.ncolors == nc <= k + 1 and r.rounds == max(deepest, 1)
+    # in-place mode: the invariants
+    r = gclib.color(rp, ci, "inplace", 7, options=sl)
+    c = r.colors.cpu().numpy()
+    assert oracle.count_conflicts(g, c) == 0 and np.all(c <= g.degrees())
+
+
+def test_smallest_last_rejects_batches_and_bad_graphs(gclib):
+    import torch
+    graphs = [gg.er(300, 5.0, 1), gg.star(20)]
+    b = gg.pack(graphs)
+    args = [torch.from_numpy(a).cuda() for a in (b.vtx_off, b.edge_off, b.rowptr, b.colidx)]
+    with pytest.raises(gclib.GCError) as e:
+        gclib.color_batch(*args, "det", 7, options=gclib.Options(priority=gclib.PRIORITY_SMALLEST_LAST))
+    assert e.value.status == gclib.GC_ERR_INVALID_ARG
+    g = gg.from_edges(5, [(0, 1), (1, 2)])
+    ci = g.colidx.copy()
+    ci[0] = 0  # a self-loop at vertex 0
+    with pytest.raises(gclib.GCError) as e:
+        gclib.smallest_last(g.rowptr, ci)
+    assert e.value.status == gclib.GC_ERR_INVALID_GRAPH

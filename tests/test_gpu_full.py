@@ -41,3 +41,15 @@ def test_full_size_inplace_invariants(gclib, full):
     assert c.min() >= 0 and np.all(c <= g.degrees())
     assert r.ncolors == oracle.distinct_colors(c) <= g.max_degree + 1
     assert 1 <= r.rounds <= g.n
+
+
+def test_full_size_smallest_last_matches_oracle(gclib, full):
+    g, rp, ci = full
+    level, nlevels, degen = gclib.smallest_last(rp, ci)
+    ref, k = oracle.peel_levels(g)
+    np.testing.assert_array_equal(level.cpu().numpy(), ref)
+    assert (nlevels, degen) == (int(ref.max()), k)
+    r = gclib.color(rp, ci, "ordered", SEED, options=gclib.Options(priority=gclib.PRIORITY_SMALLEST_LAST))
+    cref, nc = oracle.greedy_keyorder(g, SEED, oracle.PRIORITY_SMALLEST_LAST)
+    np.testing.assert_array_equal(r.colors.cpu().numpy(), cref)
+    assert r.ncolors == nc <= k + 1

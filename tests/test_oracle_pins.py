@@ -564,3 +564,96 @@ def test_recolor_keeps_two_colorings():
         c, k = oracle.greedy_keyorder(g, 5, oracle.PRIORITY_RECOLOR, cin)
         assert k == 2 and oracle.count_conflicts(g, c) == 0
         np.testing.assert_array_equal(c, 1 - cin)  # class 1 first takes color 0
+
+
+# smallest-last order by batch peeling
+
+def _degeneracy_matula_beck(g):
+    # Matula & Beck (1983): remove a vertex of least remaining degree, one at a time; the
+    # degeneracy is the largest degree seen at removal
+    n = g.n
+    adj = [set(int(u) for u in g.colidx[g.rowptr[v]:g.rowptr[v + 1]]) for v in range(n)]
+    deg = {v: len(adj[v]) for v in range(n)}
+    best = 0
+    while deg:
+        v = min(deg, key=lambda x: (deg[x], x))
+        best = max(best, deg[v])
+        for u in adj[v]:
+            if u in deg:
+                deg[u] -= 1
+        del deg[v]
+    return best
+
+
+def _check_peel_invariant(g, level, k):
+    # a vertex was removed with at most k neighbours still present (those removed in its own batch
+    # or later), and the levels are 1, 2, ... without gaps
+    for v in range(g.n):
+        nb = g.colidx[g.rowptr[v]:g.rowptr[v + 1]]
+        assert int(np.sum(level[nb] >= level[v])) <= k
+    if g.n:
+        assert set(np.unique(level)) == set(range(1, int(level.max()) + 1))
+
+
+def test_peel_degeneracy_brute_force():
+    rng = np.random.default_rng(47)
+    for trial in range(40):
+        n = int(rng.integers(1, 70))
+        p = float(rng.choice([0.05, 0.15, 0.4]))
+        edges = [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < p]
+        g = gg.from_edges(n, edges)
+        level, k = oracle.peel_levels(g)
+        assert k == _degeneracy_matula_beck(g)
+        _check_peel_invariant(g, level, k)
+    for g in (gg.rmat(10, 8, 1), gg.grid5(20, 13), gg.stencil27(4)):
+        level, k = oracle.peel_levels(g)
+        assert k == _degeneracy_matula_beck(g)
+        _check_peel_invariant(g, level, k)
+
+
+@pytest.mark.parametrize("n", [2, 3, 8, 9, 50])
+def test_peel_path_closed_form(n):
+    # the two ends go first, then the new ends: level = distance to the nearer end + 1
+    level, k = oracle.peel_levels(gg.path(n))
+    v = np.arange(n)
+    np.testing.assert_array_equal(level, np.minimum(v, n - 1 - v) + 1)
+    assert k == 1
+
+
+def test_peel_star_cycle_complete_edgeless():
+    level, k = oracle.peel_levels(gg.star(30))
+    assert level[0] == 2 and np.all(level[1:] == 1) and k == 1
+    level, k = oracle.peel_levels(gg.cycle(25))
+    assert np.all(level == 1) and k == 2
+    level, k = oracle.peel_levels(gg.complete(12))
+    assert np.all(level == 1) and k == 11
+    level, k = oracle.peel_levels(gg.empty(9))
+    assert np.all(level == 1) and k == 0
+
+
+def test_smallest_last_greedy_degeneracy_bound():
+    # in the smallest-last order a vertex has at most k already-colored neighbours, so First Fit
+    # uses at most degeneracy + 1 colors (a bound the natural and hash orders do not have)
+    for g in (gg.rmat(12, 8, 1), gg.er(2000, 12.0, 3), gg.grid5(30, 17), gg.stencil27(5), gg.path(40),
+              gg.star(100), gg.crown(20)):
+        _, k = oracle.peel_levels(g)
+        c, nc = oracle.greedy_keyorder(g, 7, oracle.PRIORITY_SMALLEST_LAST)
+        assert nc <= k + 1 and oracle.count_conflicts(g, c) == 0
+        level, _ = oracle.peel_levels(g)
+        h = oracle.keys(7, g.n)
+        if g.n <= 300:
+            assert list(c) == _literal_keyorder(g, lambda v: (-int(level[v]), int(h[v]), v))
+
+
+def test_smallest_last_trees_two_colors():
+    rng = np.random.default_rng(53)
+    for trial in range(10):
+        n = int(rng.integers(2, 300))
+        edges = [(int(rng.integers(0, i)), i) for i in range(1, n)]  # a random tree
+        g = gg.from_edges(n, edges)
+        _, k = oracle.peel_levels(g)
+        assert k == 1
+        c, nc = oracle.greedy_keyorder(g, 3, oracle.PRIORITY_SMALLEST_LAST)
+        assert nc == 2 and oracle.count_conflicts(g, c) == 0
+        d = oracle.det(g, 3, priority=oracle.PRIORITY_SMALLEST_LAST)
+        assert d.status == 0 and oracle.count_conflicts(g, d.colors) == 0

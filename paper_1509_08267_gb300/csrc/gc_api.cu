@@ -231,7 +231,9 @@ static int peel_levels(Context &C, Ctl *ctl, RoundParams P, int32_t T1, int32_t 
                        int32_t *nlevels, int32_t *degeneracy) {
     const size_t n = static_cast<size_t>(P.n);
     GC_TRY(ensure(C.rank, 4 * n, "smallest-last levels"));
+    GC_TRY(ensure(C.col0, 8 * n, "vertex state"));
     GC_TRY(ensure(C.col1, 8 * n, "vertex state"));
+    GC_TRY(ensure(C.items, 4 * n, "worklist"));
     GC_TRY(ensure(C.small0, 4 * n, "worklist"));
     GC_TRY(ensure(C.small1, 4 * n, "worklist"));
     GC_TRY(ensure(C.mid0, 4 * n, "worklist"));
@@ -260,7 +262,10 @@ static int peel_levels(Context &C, Ctl *ctl, RoundParams P, int32_t T1, int32_t 
     int &occ = C.occ_peel;
     if (occ == 0) GC_CUDA(peel_kernel_occupancy(256, &occ));
     const int grid = occ * C.sms;
-    GC_CUDA(launch_peel(P, res, level, ctl->peel, grid, 256, s));
+    // the lists of vertices left by each threshold search: two scratch arrays that every mode
+    // rewrites afterwards
+    GC_CUDA(launch_peel(P, res, level, ctl->peel, C.items.as<int32_t>(), C.col0.as<int32_t>(), ctl->peel + 2, grid,
+                        256, s));
     GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     GC_CUDA(cudaStreamSynchronize(s));
     if (h.err[0] != 0) return error_from_ctl(h);
@@ -297,7 +302,9 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
 
     // scratch sized by n; work-item buffers are sized after binning
     GC_TRY(ensure(C.col0, 8 * n, "vertex state"));
+    GC_TRY(ensure(C.col0, 8 * n, "vertex state"));
     GC_TRY(ensure(C.col1, 8 * n, "vertex state"));
+    GC_TRY(ensure(C.items, 4 * n, "worklist"));
     GC_TRY(ensure(C.small0, 4 * n, "worklist"));
     GC_TRY(ensure(C.small1, 4 * n, "worklist"));
     GC_TRY(ensure(C.items, 4 * n, "worklist"));

@@ -172,13 +172,13 @@ cudaError_t ordered_kernel_occupancy(bool batch, int block, int *blocks_per_sm);
 // Smallest-last levels (single graph): launch_peel_init sets res[v] = deg(v), level[v] = 0, the two
 // threshold words kw[2] and adds the work items the lists may need (vertices past kOrdMid, P.CH
 // entries each) to *items; launch_peel (counter sets zeroed, P.T1 <= kOrdSmall, P.CH <= kOrdChunk,
-// lists as the ordered mode's) writes level[v] >= 1, the number of levels to passes[0] and the
-// degeneracy to passes[1].
+// lists as the ordered mode's; rlist0 / rlist1 int32[n] scratch with two counters rcnt) writes
+// level[v] >= 1, the number of levels to passes[0] and the degeneracy to passes[1].
 cudaError_t launch_peel_init(const RoundParams &P, int32_t *res, int32_t *level, unsigned *kw, unsigned *items,
                              cudaStream_t s);
 cudaError_t peel_kernel_occupancy(int block, int *blocks_per_sm);
-cudaError_t launch_peel(const RoundParams &P, int32_t *res, int32_t *level, unsigned *kw, int grid, int block,
-                        cudaStream_t s);
+cudaError_t launch_peel(const RoundParams &P, int32_t *res, int32_t *level, unsigned *kw, int32_t *rlist0,
+                        int32_t *rlist1, unsigned *rcnt, int grid, int block, cudaStream_t s);
 cudaError_t launch_ordered(const RoundParams &P, bool batch, int32_t *pend, int grid, int block, cudaStream_t s);
 // Partition mode (GC_MODE_PARTITION, single graph): set-up (rows checked, colors -1, W_1 = V) and
 // the cooperative round kernel with p blocks of consecutive ids.

@@ -2346,9 +2346,13 @@ __device__ __forceinline__ void peel_item(const RoundParams &P, int32_t *res, in
 }
 
 // The whole peeling in one cooperative launch; passes[0] receives the number of levels and
-// passes[1] the last threshold (the degeneracy).
+// passes[1] the last threshold (the degeneracy).  Each threshold search scans the vertices the
+// previous one left (all vertices for the first), and its listing scan writes the ones it does not
+// list to the other of rlist0 / rlist1 (counts rcnt[0] / rcnt[1], zero at launch), so that the
+// scans shrink with the graph.
 __global__ void __launch_bounds__(kBlock, kWideBlocks) peel_kernel(RoundParams P, int32_t *res, int32_t *level,
-                                                                   unsigned *kw) {
+                                                                   unsigned *kw, int32_t *rlist0, int32_t *rlist1,
+                                                                   unsigned *rcnt) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
     const unsigned gw = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -2359,10 +2363,17 @@ __global__ void __launch_bounds__(kBlock, kWideBlocks) peel_kernel(RoundParams P
     int pass = P.pass_begin;
     bool ok = true;
     for (int f = 0; ok; ++f) {
+        // the vertices to scan: all of them first, then those the previous search left
+        const int32_t *rcur = (f & 1) ? rlist1 : rlist0;
+        int32_t *rnext = (f & 1) ? rlist0 : rlist1;
+        const int64_t nr = f == 0 ? P.n : static_cast<int64_t>(__ldcg(rcnt + (f & 1)));
+        if (blockIdx.x == 0 && threadIdx.x == 0) rcnt[(f + 1) & 1] = 0u;
         // the least res among the present vertices
         unsigned m = 0x7fffffffu;
-        for (int64_t v = gtid; v < P.n; v += nthreads)
+        for (int64_t i = gtid; i < nr; i += nthreads) {
+            const int32_t v = f == 0 ? static_cast<int32_t>(i) : __ldcg(rcur + i);
             if (__ldcg(level + v) == 0) m = min(m, static_cast<unsigned>(__ldcg(res + v)));
+        }
         m = __reduce_min_sync(kFull, m);
         if (lane == 0 && m != 0x7fffffffu) atomicMin(kw + (f & 1), m);
         if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
@@ -2370,13 +2381,22 @@ __global__ void __launch_bounds__(kBlock, kWideBlocks) peel_kernel(RoundParams P
         if (blockIdx.x == 0 && threadIdx.x == 0) kw[(f + 1) & 1] = 0x7fffffffu;
         if (kmin == 0x7fffffffu) break;  // every vertex removed
         if (static_cast<int32_t>(kmin) > k) k = static_cast<int32_t>(kmin);
-        // the first level of this threshold: every present vertex with res <= k
+        // the first level of this threshold: every present vertex with res <= k; the other present
+        // vertices are left for the next search
         {
             const OrdLists F = ord_lists(P, pass);
-            for (int64_t base = gtid & ~31ll; base < P.n; base += nthreads) {
-                const int64_t v = base + lane;
-                const bool ready[1] = {v < P.n && __ldcg(level + v) == 0 && __ldcg(res + v) <= k};
-                const int32_t Vs[1] = {static_cast<int32_t>(v)};
+            for (int64_t base = gtid & ~31ll; base < nr; base += nthreads) {
+                const int64_t i = base + lane;
+                int32_t v = 0;
+                bool present = false, now = false;
+                if (i < nr) {
+                    v = f == 0 ? static_cast<int32_t>(i) : __ldcg(rcur + i);
+                    present = __ldcg(level + v) == 0;
+                    now = present && __ldcg(res + v) <= k;
+                }
+                warp_append(present && !now, v, rnext, rcnt + ((f + 1) & 1), lane);
+                const bool ready[1] = {now};
+                const int32_t Vs[1] = {v};
                 ord_list<false, 1>(P, ready, Vs, F, lane);
             }
         }
@@ -2708,16 +2728,17 @@ cudaError_t peel_kernel_occupancy(int block, int *blocks_per_sm) {
                                                          block, 0);
 }
 
-cudaError_t launch_peel(const RoundParams &P, int32_t *res, int32_t *level, unsigned *kw, int grid, int block,
-                        cudaStream_t s) {
+cudaError_t launch_peel(const RoundParams &P, int32_t *res, int32_t *level, unsigned *kw, int32_t *rlist0,
+                        int32_t *rlist1, unsigned *rcnt, int grid, int block, cudaStream_t s) {
     if (block != kBlock) return cudaErrorInvalidValue;
     if (P.n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(&P.bar->count, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rcnt, 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     RoundParams arg = P;
-    int32_t *ra = res, *la = level;
-    unsigned *ka = kw;
-    void *args[] = {&arg, &ra, &la, &ka};
+    int32_t *ra = res, *la = level, *r0 = rlist0, *r1 = rlist1;
+    unsigned *ka = kw, *rc = rcnt;
+    void *args[] = {&arg, &ra, &la, &ka, &r0, &r1, &rc};
     return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(&peel_kernel), dim3(grid), dim3(block), args, 0,
                                        s);
 }

@@ -195,7 +195,7 @@ def test_round_cap(gclib, mode):
     assert r.ncolors == 10
 
 
-@pytest.mark.parametrize("mode", ["det", "inplace"])
+@pytest.mark.parametrize("mode", ["det", "inplace", "ordered", "partition"])
 def test_barrier_wait_limit(gclib, mode):
     # a 1 ns limit makes every early block give up at the first grid barrier: the call must
     # report GC_ERR_TIMEOUT, leave the output untouched, and the next call must work
@@ -229,3 +229,34 @@ def test_validate(gclib):
     with pytest.raises(gclib.GCError):
         gclib.validate(g.rowptr, ci, gclib.VALIDATE_SORTED)
     gclib.validate(g.rowptr, ci, 0)  # range and self-loop checks alone pass
+
+
+def test_smallest_last_barrier_wait_limit(gclib):
+    # the peeling kernel's grid barriers give up the same way; the next call works
+    g = gg.rmat(14, 16, 2)
+    with pytest.raises(gclib.GCError) as ei:
+        gclib.smallest_last(g.rowptr, g.colidx, options=gclib.Options(spin_limit_ns=1))
+    assert ei.value.status == gclib.GC_ERR_TIMEOUT
+    level, _, k = gclib.smallest_last(g.rowptr, g.colidx)
+    ref, kref = oracle.peel_levels(g)
+    np.testing.assert_array_equal(level, ref)
+    assert k == kref
+
+
+def test_ordered_round_cap_and_bad_input(gclib):
+    g = gg.complete(10)  # the keys form one chain: 10 rounds
+    _expect(gclib, gclib.GC_ERR_NO_CONVERGENCE, g.rowptr, g.colidx, "ordered", options=gclib.Options(max_rounds=3))
+    assert gclib.color(g.rowptr, g.colidx, "ordered", 1, options=gclib.Options(max_rounds=10)).ncolors == 10
+    ok = gg.cycle(6)
+    bad = ok.colidx.copy()
+    bad[3] = 6  # out of range
+    _expect(gclib, gclib.GC_ERR_INVALID_GRAPH, ok.rowptr, bad, "ordered")
+    # asymmetric: vertex 1 lists 0 but 0 lists nothing; with key(0) < key(1), vertex 1 waits for a
+    # release that never comes, which the kernel reports once the ready lists run dry
+    seed = next(s for s in range(100) if oracle.key_less(s, 0, 1))
+    rp = np.array([0, 0, 1], np.int32)
+    ci = np.array([0], np.int32)
+    out = np.full(2, -77, np.int32)
+    with pytest.raises(gclib.GCError) as ei:
+        gclib.color(rp, ci, "ordered", seed, out=out)
+    assert ei.value.status == gclib.GC_ERR_INVALID_GRAPH and np.all(out == -77)

@@ -123,7 +123,8 @@ __device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
 // `target` += gridDim.x, so the last block to arrive has nothing more to do.  A wait gives up after
 // spin_ns nanoseconds (status GC_ERR_TIMEOUT) or when it sees that a block has posted an error
 // (read every 16 polls); the caller then leaves the kernel.  Returns true when the grid may
-// continue.
+// continue: false after a timeout or once any block has posted an error, the same in every block
+// that passes this barrier, so that the round loops need no error check of their own.
 __device__ bool grid_sync(GridBar *bar, unsigned &target, int32_t *err, int64_t spin_ns) {
     __shared__ int s_ok;
     __syncthreads();
@@ -147,19 +148,13 @@ __device__ bool grid_sync(GridBar *bar, unsigned &target, int32_t *err, int64_t 
                 }
             }
         }
+        // an error posted by any block during the round ends the loop in every block, at the same
+        // barrier: read once here, it reaches all of this block's threads through s_ok
+        if (ok && *reinterpret_cast<volatile int32_t *>(err) != 0) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
-}
-
-// An error posted by any block, read once per block so that its threads leave the round loop
-// together (another block may post one while this block's threads are reading the flag).
-__device__ __forceinline__ bool block_error_seen(const int32_t *err) {
-    __shared__ int s_err;
-    if (threadIdx.x == 0) s_err = __ldcg(err) != 0;
-    __syncthreads();
-    return s_err != 0;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1273,7 +1268,6 @@ __global__ void __launch_bounds__(kBlock, MINB) det_round_kernel(RoundParams P) 
         unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
         const unsigned nsmall = __ldcg(cc + kCntSmall), nitems = __ldcg(cc + kCntItems);
         const unsigned nchunks = __ldcg(cc + kCntChunks), nmulti = __ldcg(cc + kCntMulti);
-        if (block_error_seen(P.err)) break;
         if (nsmall + nitems == 0u) break;
         if (pass >= P.pass_end) {
             if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
@@ -1360,7 +1354,6 @@ __global__ void __launch_bounds__(kBlock, MINB) ip_round_kernel(RoundParams P) {
         unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
         const unsigned nsmall = __ldcg(cc + kCntSmall), nitems = __ldcg(cc + kCntItems);
         const unsigned nchunks = __ldcg(cc + kCntChunks);
-        if (block_error_seen(P.err)) break;
         if (nsmall + nitems == 0u) break;
         if (pass >= P.pass_end) {
             if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
@@ -1407,7 +1400,8 @@ __global__ void __launch_bounds__(kBlock, MINB) ip_round_kernel(RoundParams P) {
             for (unsigned i = gw; i < nchunks; i += nw)
                 ip_chunk_conflict<BATCH>(P, col, __ldcg(chunkc + i), win, chunkn, cn, pass, lane, st_deg, st_cnt);
         }
-        // small vertices from the warp after the last one with an item, so that few warps get both
+        // small vertices from a warp rotated by the number of larger vertices, so that the warps
+        // with the first phase-2 items seldom get a group of small vertices as well
         for (unsigned base = ((gw + nw - nitems % nw) % nw) * 32u; base < nsmall; base += nw * 32u) {
             const unsigned i = base + lane;
             bool lose = false;
@@ -1790,7 +1784,6 @@ __global__ void __launch_bounds__(kBlock, kNarrowBlocks) part_round_kernel(Round
         unsigned *cc = P.cnt + kCnt * (pass % 3);
         unsigned *cn = P.cnt + kCnt * ((pass + 1) % 3);
         const unsigned nwl = __ldcg(cc + kCntSmall);
-        if (block_error_seen(P.err)) break;
         if (nwl == 0u) break;
         if (pass >= P.pass_end) {
             if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
@@ -2203,7 +2196,6 @@ __global__ void __launch_bounds__(kBlock, kWideBlocks) ord_round_kernel(RoundPar
         const OrdLists C = ord_lists(P, pass), L = ord_lists(P, pass + 1);
         const unsigned nsmall = __ldcg(C.cnt + kCntSmall), nmid = __ldcg(C.cnt + kCntMulti);
         const unsigned nitems = __ldcg(C.cnt + kCntChunks);
-        if (block_error_seen(P.err)) break;
         if (nsmall + nmid + nitems == 0u) {
             drained = true;
             break;
@@ -2405,10 +2397,6 @@ __global__ void __launch_bounds__(kBlock, kWideBlocks) peel_kernel(RoundParams P
             const OrdLists C = ord_lists(P, pass), N = ord_lists(P, pass + 1);
             const unsigned nsmall = __ldcg(C.cnt + kCntSmall), nmid = __ldcg(C.cnt + kCntMulti);
             const unsigned nitems = __ldcg(C.cnt + kCntChunks);
-            if (block_error_seen(P.err)) {
-                ok = false;
-                break;
-            }
             if (nsmall + nmid + nitems == 0u) break;
             if (blockIdx.x == 0 && threadIdx.x < kCnt) P.cnt[kCnt * ((pass + 2) % 3) + threadIdx.x] = 0u;
             ++L;

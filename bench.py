@@ -544,7 +544,8 @@ def main():
                        "l2": "flushed between steps (512 MB write) and colidx > L2", "parallelism":
                        "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": recorded_traffic(args.workload, mode),
+                         "frac": achieved / peak,
+                         "traffic": recorded_traffic(args.workload, mode) if args.priority == "hash" else None,
                          "peak_kind": peak_kind,
                          "kernel": "round kernel (persistent)", "kernel_ms": kms, "alg_bytes": alg_bytes},
             "cpu_baseline": cpu,

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gc_internal.h"
 
 namespace gc {
@@ -227,8 +229,19 @@ struct Outputs {
 // Smallest-last levels of a single graph into C.rank (int32[n]): the peeling kernel with the
 // ordered mode's lists; the residual degrees live in C.col1, which every mode rewrites afterwards.
 // P holds the graph, the control block and the barrier; the counter sets must be zero.
+// An NVTX range over a host-side phase of a call (visible in Nsight Systems; free when no tool is
+// attached).  The device work of a phase runs asynchronously, so a range covers its launches and
+// the host waits inside it, not the kernels' own time.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 static int peel_levels(Context &C, Ctl *ctl, RoundParams P, int32_t T1, int32_t CH, cudaStream_t s,
                        int32_t *nlevels, int32_t *degeneracy) {
+    NvtxRange range("gc: smallest-last peeling");
     const size_t n = static_cast<size_t>(P.n);
     GC_TRY(ensure(C.rank, 4 * n, "smallest-last levels"));
     GC_TRY(ensure(C.col0, 8 * n, "vertex state"));
@@ -276,6 +289,7 @@ static int peel_levels(Context &C, Ctl *ctl, RoundParams P, int32_t T1, int32_t 
 
 static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_options *opt, gc_stats *stats,
                const Outputs &out) {
+    NvtxRange range(pb.batch ? "gc: batch coloring" : "gc: coloring");
     const int dev = C.device;
     cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C.stream;
     const uint32_t flags = opt ? opt->flags : 0u;
@@ -496,6 +510,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     GC_TRY(locate(out.colors, dev, &out_dev));
     if (!out_dev && out.colors) GC_TRY(ensure(C.st_colors, 4 * n, "color staging"));
     int32_t *colors_dev = out_dev ? out.colors : (out.colors ? C.st_colors.as<int32_t>() : nullptr);
+    NvtxRange count_range("gc: color count and output");
     GC_CUDA(launch_count_colors(P, pb.batch, mode == GC_MODE_DETERMINISTIC ? &ctl->passes[1] : nullptr, 0,
                                 static_cast<int32_t>(n), 0, G, C.bitmap.as<unsigned>(),
                                 pb.batch ? C.gmax.as<int32_t>() : &ctl->gmax1,

@@ -25,12 +25,9 @@ def nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def _flags(debug: bool) -> list[str]:
-    f = ARCH + ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                "-I", CSRC]
-    if debug:
-        f += ["-DGC_DEBUG=1"]
-    return f
+def _flags() -> list[str]:
+    return ARCH + ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+                   "-I", CSRC]
 
 
 def _stale(target: str, deps: list[str]) -> bool:
@@ -40,7 +37,7 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "gc.h"))
@@ -52,7 +49,7 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [path] + headers):
-            jobs.append([nvcc()] + _flags(debug) + ["-c", path, "-o", obj])
+            jobs.append([nvcc()] + _flags() + ["-c", path, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -1969,44 +1969,85 @@ __device__ __forceinline__ void ord_release(const RoundParams &P, int32_t *pend,
     ord_list<BATCH, K>(P, ready, U, L, lane);
 }
 
+// Does neighbour u (local id lu, state word read on demand) have a smaller key than v?  With the
+// hash key both keys are recomputed from the ids (the same order as key_less: the 31 priority bits
+// are the top of the hash), so no state word is read; the other keys compare the state words.
+template <bool HASH>
+__device__ __forceinline__ bool smaller_key(const RoundParams &P, const unsigned long long *st, int32_t U,
+                                            uint32_t lu, uint32_t lv, uint64_t hv, uint32_t pv) {
+    if constexpr (HASH) {
+        const uint64_t hu = vertex_hash(P.seed, lu);
+        return hu != hv ? hu < hv : lu < lv;
+    } else {
+        return key_less(prio_of(__ldcg(st + U)), pv, lu, lv, P.seed);
+    }
+}
+
 // pend[v] for every vertex, and the first round's lists (vertices with neighbours, none of them
-// with a smaller key).  A warp takes 32 consecutive vertices, sweeps their rows one after another
-// with all lanes, and lists the ready ones together.  Vertices without neighbours were colored by
-// setup.
-template <bool BATCH>
+// with a smaller key).  A warp takes 32 consecutive vertices, one per lane: a lane counts a row of
+// up to 32 entries itself (four entries at a time), and the warp counts the longer rows one after
+// another with all lanes; the ready vertices are listed together.  Vertices without neighbours
+// were colored by setup.
+template <bool BATCH, bool HASH>
 __global__ void ord_count_kernel(RoundParams P, int32_t *pend) {
+    constexpr int64_t kLaneRow = 32;  // longest row one lane counts alone
     const int lane = threadIdx.x & 31;
     const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
     const OrdLists L = ord_lists(P, P.pass_begin);
     const unsigned long long *st = reinterpret_cast<const unsigned long long *>(P.col0);
     for (int64_t base = (static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
          base < P.n; base += nw * 32) {
-        unsigned mine = 0;
-        bool has_row = false;
-        const int32_t cnt = static_cast<int32_t>(min(static_cast<int64_t>(32), P.n - base));
-        for (int32_t t = 0; t < cnt; ++t) {
-            const int32_t V = static_cast<int32_t>(base + t);
-            const Row r = load_row<BATCH>(P, V);
-            unsigned c = 0;
-            if (r.e > r.b) {
-                const uint32_t pv = prio_of(__ldcg(st + V));
-                for (int64_t j = r.b + lane; j < r.e; j += 32) {
-                    const int32_t ul = load_entry(P.colidx + j);
-                    const int32_t U = neighbour(P, r, ul, j);
-                    if (U >= 0 && key_less(prio_of(__ldcg(st + U)), pv, static_cast<uint32_t>(ul),
-                                           static_cast<uint32_t>(r.lv), P.seed))
+        const int32_t V = static_cast<int32_t>(base + lane);
+        const bool valid = base + lane < P.n;
+        Row r{};
+        int64_t deg = 0;
+        uint64_t hv = 0;
+        uint32_t pv = 0;
+        if (valid) {
+            r = load_row<BATCH>(P, V);
+            deg = r.e - r.b;
+            if constexpr (HASH)
+                hv = vertex_hash(P.seed, static_cast<uint32_t>(r.lv));
+            else
+                pv = prio_of(__ldcg(st + V));
+        }
+        unsigned c = 0;
+        if (deg > 0 && deg <= kLaneRow) {
+            for (int64_t j = r.b; j < r.e; j += 4) {
+                int32_t u[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) u[t] = j + t < r.e ? load_entry(P.colidx + j + t) : 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if (j + t >= r.e) continue;
+                    const int32_t U = neighbour(P, r, u[t], j + t);
+                    if (U >= 0 && smaller_key<HASH>(P, st, U, static_cast<uint32_t>(u[t]),
+                                                    static_cast<uint32_t>(r.lv), hv, pv))
                         ++c;
                 }
-                c = __reduce_add_sync(kFull, c);
-            }
-            if (lane == t) {
-                mine = c;
-                has_row = r.e > r.b;
             }
         }
-        const int32_t V = static_cast<int32_t>(base + lane);
-        if (lane < cnt) pend[V] = static_cast<int32_t>(mine);
-        const bool ready[1] = {lane < cnt && has_row && mine == 0};
+        unsigned big = __ballot_sync(kFull, deg > kLaneRow);
+        while (big) {
+            const int l = __ffs(big) - 1;
+            big &= big - 1;
+            const int32_t Vb = __shfl_sync(kFull, V, l);
+            const Row rb = load_row<BATCH>(P, Vb);
+            const uint64_t hb = __shfl_sync(kFull, hv, l);
+            const uint32_t pb = __shfl_sync(kFull, pv, l);
+            unsigned cb = 0;
+            for (int64_t j = rb.b + lane; j < rb.e; j += 32) {
+                const int32_t ul = load_entry(P.colidx + j);
+                const int32_t U = neighbour(P, rb, ul, j);
+                if (U >= 0 &&
+                    smaller_key<HASH>(P, st, U, static_cast<uint32_t>(ul), static_cast<uint32_t>(rb.lv), hb, pb))
+                    ++cb;
+            }
+            cb = __reduce_add_sync(kFull, cb);
+            if (lane == l) c = cb;
+        }
+        if (valid) pend[V] = static_cast<int32_t>(c);
+        const bool ready[1] = {valid && deg > 0 && c == 0};
         const int32_t Vs[1] = {V};
         ord_list<BATCH, 1>(P, ready, Vs, L, lane);
     }
@@ -2688,10 +2729,18 @@ cudaError_t launch_ordered(const RoundParams &P, bool batch, int32_t *pend, int 
     if (block != kBlock) return cudaErrorInvalidValue;
     if (P.n <= 0) return cudaSuccess;
     const int cgrid = grid_for(static_cast<int64_t>(P.n) * 32, 256, sm_count() * 16);
-    if (batch)
-        ord_count_kernel<true><<<cgrid, 256, 0, s>>>(P, pend);
-    else
-        ord_count_kernel<false><<<cgrid, 256, 0, s>>>(P, pend);
+    const bool hash = P.priority == GC_PRIORITY_HASH;
+    if (batch) {
+        if (hash)
+            ord_count_kernel<true, true><<<cgrid, 256, 0, s>>>(P, pend);
+        else
+            ord_count_kernel<true, false><<<cgrid, 256, 0, s>>>(P, pend);
+    } else {
+        if (hash)
+            ord_count_kernel<false, true><<<cgrid, 256, 0, s>>>(P, pend);
+        else
+            ord_count_kernel<false, false><<<cgrid, 256, 0, s>>>(P, pend);
+    }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemsetAsync(&P.bar->count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;

@@ -123,14 +123,18 @@ __device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
 // `target` += gridDim.x, so the last block to arrive has nothing more to do.  A wait gives up after
 // spin_ns nanoseconds (status GC_ERR_TIMEOUT) or when it sees that a block has posted an error
 // (read every 16 polls); the caller then leaves the kernel.  Returns true when the grid may
-// continue: false after a timeout or once any block has posted an error, the same in every block
-// that passes this barrier, so that the round loops need no error check of their own.
+// continue: false after a timeout or once an error has been posted (at this barrier or, if it was
+// posted after this block arrived, at the next one), the same for all threads of a block, so that
+// the round loops need no error check of their own.
 __device__ bool grid_sync(GridBar *bar, unsigned &target, int32_t *err, int64_t spin_ns) {
     __shared__ int s_ok;
     __syncthreads();
     target += gridDim.x;
     if (threadIdx.x == 0) {
         int ok = 1;
+        // the error flag is read as the block arrives, so that the read overlaps the wait; an error
+        // posted after that is seen at the next barrier (or by the polling below)
+        const int32_t posted = *reinterpret_cast<volatile int32_t *>(err);
         red_add_release(&bar->count, 1u);
         if (static_cast<int>(ld_acquire(&bar->count) - target) < 0) {
             const uint64_t t0 = global_ns();
@@ -148,9 +152,8 @@ __device__ bool grid_sync(GridBar *bar, unsigned &target, int32_t *err, int64_t 
                 }
             }
         }
-        // an error posted by any block during the round ends the loop in every block, at the same
-        // barrier: read once here, it reaches all of this block's threads through s_ok
-        if (ok && *reinterpret_cast<volatile int32_t *>(err) != 0) ok = 0;
+        // an error ends the loop: read once per block, it reaches all of its threads through s_ok
+        if (posted != 0) ok = 0;
         s_ok = ok;
     }
     __syncthreads();

@@ -100,6 +100,10 @@ struct Context {
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
     Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors, st_colors_in, mid0, mid1, rank;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // host adjacency arrays are uploaded on copy_stream while the set-up runs on the call's stream;
+    // ev_before orders the upload after earlier work, ev_colidx marks it done
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_before = nullptr, ev_colidx = nullptr;
     void release_all() {
         Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &lists, &ctl, &stats, &bitmap, &hist,
                       &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors, &st_colors_in, &mid0, &mid1, &rank};
@@ -128,6 +132,12 @@ static int get_context(Context **out) {
         }
         cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
         for (auto &ev : c->ev) cudaEventCreate(&ev);
+        if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_before, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_colidx, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            c->copy_stream = nullptr;  // uploads then stay on the call's stream
+        }
         g_ctx[dev] = c;
     }
     *out = g_ctx[dev];
@@ -216,9 +226,25 @@ struct Problem {
     const int32_t *colidx;
     const int64_t *vtx_off;
     const int64_t *edge_off;
+    cudaEvent_t colidx_ready = nullptr;  // recorded when a host colidx upload is done (else none)
     const int32_t *prio_rank = nullptr;  // recoloring pass: the given coloring (device view)
     int32_t priority_override = -1;        // >= 0: the priority to use instead of the options'
 };
+
+// Waits, when the call returns on any path, for an upload still running on the copy stream (the
+// caller may free its host arrays as soon as the call returns).
+struct UploadGuard {
+    cudaStream_t s;
+    ~UploadGuard() {
+        if (s) cudaStreamSynchronize(s);
+    }
+};
+
+// The call's stream waits for the adjacency upload before the first kernel that reads colidx.
+static int wait_colidx(const Problem &pb, cudaStream_t s) {
+    if (pb.colidx_ready) GC_CUDA(cudaStreamWaitEvent(s, pb.colidx_ready, 0));
+    return GC_OK;
+}
 
 struct Outputs {
     int32_t *colors;   // caller array (device or host), total n
@@ -404,6 +430,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     }
     if (timing) GC_CUDA(cudaEventRecord(C.ev[0], s));
     if (priority == GC_PRIORITY_SMALLEST_LAST && mode != GC_MODE_PARTITION && n > 0) {
+        GC_TRY(wait_colidx(pb, s));
         int32_t nlev = 0, degen = 0;
         GC_TRY(peel_levels(C, ctl, P, T1, CH, s, &nlev, &degen));
         P.prio_rank = C.rank.as<int32_t>();
@@ -413,6 +440,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     int64_t grid = 0;
     if (mode == GC_MODE_PARTITION) {
         // Algorithm 1 with p id-ordered blocks: its own set-up and round kernel
+        GC_TRY(wait_colidx(pb, s));
         GC_CUDA(launch_partition_init(P, s));
         GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         GC_CUDA(cudaStreamSynchronize(s));
@@ -464,6 +492,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
         int per_sm = occ;
         if (opt && opt->blocks_per_sm > 0 && opt->blocks_per_sm < per_sm) per_sm = opt->blocks_per_sm;
         grid = static_cast<int64_t>(per_sm) * C.sms;
+        GC_TRY(wait_colidx(pb, s));
         GC_CUDA(launch_ordered(P, pb.batch, reinterpret_cast<int32_t *>(C.col1.p), static_cast<int>(grid), block, s));
     } else {
     GC_CUDA(launch_setup(P, mode, pb.batch, 0, static_cast<int32_t>(n), -1, s));
@@ -500,6 +529,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     const int64_t want = (static_cast<int64_t>(n_small) + 32 * static_cast<int64_t>(n_chunks) + block - 1) / block;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
+    GC_TRY(wait_colidx(pb, s));
     GC_CUDA(launch_rounds(P, mode, pb.batch, compact, static_cast<int>(grid), block, s, wide));
     }
     if (timing) GC_CUDA(cudaEventRecord(C.ev[2], s));
@@ -628,9 +658,21 @@ static int single_problem(Context *C, int32_t n, const int32_t *rowptr, const in
     const void *v = nullptr;
     GC_TRY(device_view(rowptr, 4 * (static_cast<size_t>(n) + 1), C->device, C->st_rowptr, s, &v));
     pb.rowptr = static_cast<const int32_t *>(v);
-    GC_TRY(device_view(colidx, 4 * static_cast<size_t>(nnz32), C->device, C->st_colidx, s, &v));
+    int ci_dev = 0;
+    GC_TRY(locate(colidx, C->device, &ci_dev));
+    if (!ci_dev && nnz32 > 0 && C->copy_stream) {
+        // the largest upload runs beside the set-up kernels, which read only the row offsets
+        GC_CUDA(cudaEventRecord(C->ev_before, s));
+        GC_CUDA(cudaStreamWaitEvent(C->copy_stream, C->ev_before, 0));
+        GC_TRY(device_view(colidx, 4 * static_cast<size_t>(nnz32), C->device, C->st_colidx, C->copy_stream, &v));
+        GC_CUDA(cudaEventRecord(C->ev_colidx, C->copy_stream));
+        pb.colidx_ready = C->ev_colidx;
+    } else {
+        GC_TRY(device_view(colidx, 4 * static_cast<size_t>(nnz32), C->device, C->st_colidx, s, &v));
+    }
     pb.colidx = static_cast<const int32_t *>(v);
     if (opt && (opt->flags & GC_FLAG_VALIDATE)) {
+        GC_TRY(wait_colidx(pb, s));
         GC_TRY(ensure(C->ctl, sizeof(Ctl), "control"));
         Ctl *ctl = C->ctl.as<Ctl>();
         GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
@@ -673,6 +715,7 @@ static int color_single(int32_t n, const int32_t *rowptr, const int32_t *colidx,
     }
     cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C->stream;
     Problem pb{};
+    UploadGuard upload{C->copy_stream};
     GC_TRY(single_problem(C, n, rowptr, colidx, opt, s, pb));
     const void *v = nullptr;
     if (colors_in) {
@@ -776,6 +819,7 @@ int gc_smallest_last(int32_t n, const int32_t *rowptr, const int32_t *colidx, in
     }
     cudaStream_t s = (opt && opt->stream) ? static_cast<cudaStream_t>(opt->stream) : C->stream;
     Problem pb{};
+    UploadGuard upload{C->copy_stream};
     GC_TRY(single_problem(C, n, rowptr, colidx, opt, s, pb));
     GC_TRY(ensure(C->ctl, sizeof(Ctl), "control"));
     Ctl *ctl = C->ctl.as<Ctl>();
@@ -792,6 +836,7 @@ int gc_smallest_last(int32_t n, const int32_t *rowptr, const int32_t *colidx, in
     P.passes = ctl->passes;
     P.spin_ns = (opt && opt->spin_limit_ns > 0) ? opt->spin_limit_ns : 1000000000LL;
     int32_t nl = 0, dg = 0;
+    GC_TRY(wait_colidx(pb, s));
     GC_TRY(peel_levels(*C, ctl, P, T1, CH, s, &nl, &dg));
     int out_dev = 0;
     GC_TRY(locate(level_out, C->device, &out_dev));

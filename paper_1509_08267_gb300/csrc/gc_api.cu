@@ -506,6 +506,9 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     GC_TRY(ensure(C.chunk1, kItemBytes * static_cast<size_t>(n_chunks), "work items"));
     GC_TRY(ensure(C.acc, 4 * kAccStride * static_cast<size_t>(n_items), "accumulators"));
     if (mode == GC_MODE_INPLACE && n_items == 0) compact = false;
+    // single graphs only: a batch's state words stay in L2 only while its vertices are taken block
+    // by block in the sorted order
+    P.spread = mode == GC_MODE_INPLACE && n_items == 0 && !pb.batch ? 1 : 0;
     if (compact) GC_TRY(ensure(C.lists, 4 * static_cast<size_t>(h.list_total), "neighbour lists"));
     P.chunk0 = C.chunk0.as<int4>();
     P.chunk1 = C.chunk1.as<int4>();

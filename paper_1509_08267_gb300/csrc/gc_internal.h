@@ -124,6 +124,8 @@ struct RoundParams {
     int32_t CH;  // adjacency entries per warp work item
     int32_t priority;  // GC_PRIORITY_* or kPriorityRecolor: what the 31 priority bits of a state word hold
     const int32_t *prio_rank;  // smallest last: the peel levels; recoloring: the given coloring (int32[n])
+    int32_t spread;  // in-place mode: phase 1 takes the thread worklist in a spread order (set when no
+                     // vertex is past T1: the degree-sorted order then balances nothing)
 };
 
 // Launch wrappers (gc_kernels.cu).  All return the launch's cudaError_t.

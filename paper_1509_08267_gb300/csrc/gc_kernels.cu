@@ -1384,7 +1384,33 @@ __global__ void __launch_bounds__(kBlock, MINB) ip_round_kernel(RoundParams P) {
         } else {
             for (unsigned i = gw; i < nchunks; i += nw) ip_chunk_assign<BATCH>(P, col, __ldcg(chunkc + i), win, lane);
         }
-        for (unsigned i = gw * 32u + lane; i < nsmall; i += nw * 32u) ip_small_assign<BATCH>(P, col, __ldcg(smallc + i));
+        if (P.spread && nsmall > 0u) {
+            // entry (t K) mod N for thread step t, K coprime with N near N / golden ratio: the
+            // vertices in flight at one time are spread over the whole list instead of a run of
+            // consecutive (on meshes: adjacent) ids, so far fewer of them read each other uncolored
+            unsigned Kp = static_cast<unsigned>(static_cast<uint64_t>(nsmall) * 2654435769ull >> 32) | 1u;
+            for (;;) {
+                unsigned a = Kp, b = nsmall;
+                while (b) {
+                    const unsigned t = a % b;
+                    a = b;
+                    b = t;
+                }
+                if (a == 1u) break;
+                Kp += 2u;
+            }
+            const unsigned t0 = gw * 32u + lane, dt = nw * 32u;
+            unsigned pos = static_cast<unsigned>(static_cast<uint64_t>(t0 % nsmall) * Kp % nsmall);
+            const unsigned dpos = static_cast<unsigned>(static_cast<uint64_t>(dt % nsmall) * Kp % nsmall);
+            for (unsigned i = t0; i < nsmall; i += dt) {
+                ip_small_assign<BATCH>(P, col, __ldcg(smallc + pos));
+                pos += dpos;
+                if (pos >= nsmall) pos -= nsmall;
+            }
+        } else {
+            for (unsigned i = gw * 32u + lane; i < nsmall; i += nw * 32u)
+                ip_small_assign<BATCH>(P, col, __ldcg(smallc + i));
+        }
         if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
         // phase 2: conflict detection
         if constexpr (COMPACT) {

@@ -117,7 +117,8 @@ typedef struct gc_options {
     int32_t blocks_per_sm;     /* resident blocks per SM for the round kernel.  0: the library picks the
                                   80-register variant (3 blocks per SM) when most adjacency entries are
                                   in vertices of degree > small_max_degree, else the 64-register one (4);
-                                  3 or 4: that variant; 1 or 2: the 64-register one, capped */
+                                  3 or 4: that variant; 1 or 2: the 64-register one, capped.  It also
+                                  caps the ordered-mode and smallest-last peeling kernels (3 per SM) */
     int64_t spin_limit_ns;     /* grid-barrier wait limit in ns; 0 = 1e9.  A wait that runs out makes
                                   the call return GC_ERR_TIMEOUT with the device still usable */
     uint32_t flags;            /* GC_FLAG_* */

@@ -266,7 +266,7 @@ struct NvtxRange {
 };
 
 static int peel_levels(Context &C, Ctl *ctl, RoundParams P, int32_t T1, int32_t CH, cudaStream_t s,
-                       int32_t *nlevels, int32_t *degeneracy) {
+                       int32_t *nlevels, int32_t *degeneracy, int32_t blocks_per_sm) {
     NvtxRange range("gc: smallest-last peeling");
     const size_t n = static_cast<size_t>(P.n);
     GC_TRY(ensure(C.rank, 4 * n, "smallest-last levels"));
@@ -300,7 +300,7 @@ static int peel_levels(Context &C, Ctl *ctl, RoundParams P, int32_t T1, int32_t 
     GC_CUDA(cudaMemsetAsync(ctl->cnt, 0, sizeof(ctl->cnt), s));
     int &occ = C.occ_peel;
     if (occ == 0) GC_CUDA(peel_kernel_occupancy(256, &occ));
-    const int grid = occ * C.sms;
+    const int grid = (blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ) * C.sms;
     // the lists of vertices left by each threshold search: two scratch arrays that every mode
     // rewrites afterwards
     GC_CUDA(launch_peel(P, res, level, ctl->peel, C.items.as<int32_t>(), C.col0.as<int32_t>(), ctl->peel + 2, grid,
@@ -432,7 +432,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     if (priority == GC_PRIORITY_SMALLEST_LAST && mode != GC_MODE_PARTITION && n > 0) {
         GC_TRY(wait_colidx(pb, s));
         int32_t nlev = 0, degen = 0;
-        GC_TRY(peel_levels(C, ctl, P, T1, CH, s, &nlev, &degen));
+        GC_TRY(peel_levels(C, ctl, P, T1, CH, s, &nlev, &degen, opt ? opt->blocks_per_sm : 0));
         P.prio_rank = C.rank.as<int32_t>();
         GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
         GC_CUDA(cudaMemsetAsync(&ctl->gmax1, 0xff, sizeof(int32_t), s));
@@ -840,7 +840,7 @@ int gc_smallest_last(int32_t n, const int32_t *rowptr, const int32_t *colidx, in
     P.spin_ns = (opt && opt->spin_limit_ns > 0) ? opt->spin_limit_ns : 1000000000LL;
     int32_t nl = 0, dg = 0;
     GC_TRY(wait_colidx(pb, s));
-    GC_TRY(peel_levels(*C, ctl, P, T1, CH, s, &nl, &dg));
+    GC_TRY(peel_levels(*C, ctl, P, T1, CH, s, &nl, &dg, opt ? opt->blocks_per_sm : 0));
     int out_dev = 0;
     GC_TRY(locate(level_out, C->device, &out_dev));
     GC_CUDA(cudaMemcpyAsync(level_out, C->rank.p, 4 * static_cast<size_t>(n),

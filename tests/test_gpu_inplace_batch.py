@@ -260,3 +260,21 @@ def test_ordered_round_cap_and_bad_input(gclib):
     with pytest.raises(gclib.GCError) as ei:
         gclib.color(rp, ci, "ordered", seed, out=out)
     assert ei.value.status == gclib.GC_ERR_INVALID_GRAPH and np.all(out == -77)
+
+
+@pytest.mark.parametrize("mode,prio", [("det", 0), ("det", 2), ("inplace", 0), ("ordered", 0), ("ordered", 2),
+                                       ("partition", 0)])
+def test_host_arrays_every_mode(gclib, mode, prio):
+    # host CSR arrays are uploaded beside the set-up kernels; every path must wait for the upload
+    # before its first kernel that reads the adjacency (deterministic paths: identical colors)
+    import torch
+    g = gg.rmat(14, 16, 3)
+    opt = gclib.Options(priority=prio)
+    rh = gclib.color(g.rowptr, g.colidx, mode, 5, options=opt)
+    rd = gclib.color(torch.from_numpy(g.rowptr).cuda(), torch.from_numpy(g.colidx).cuda(), mode, 5, options=opt)
+    assert isinstance(rh.colors, np.ndarray)
+    if mode == "inplace":
+        assert oracle.count_conflicts(g, rh.colors) == 0 and np.all(rh.colors <= g.degrees())
+    else:
+        np.testing.assert_array_equal(rh.colors, rd.colors.cpu().numpy())
+        assert (rh.ncolors, rh.rounds) == (rd.ncolors, rd.rounds)

@@ -39,6 +39,25 @@ CPU_SAMPLE = {  # bounded oracle sample of the same workload family (10-30 s sin
 }
 
 
+def algorithmic_bytes(mode, n, wl_size, wl_degsum):
+    """Algorithmic bytes of one coloring's round kernel, from the per-round worklist sizes |W_r| and
+    degree sums (the ordered modes: per depth).  Deterministic (one fused sweep per round): per
+    worklist vertex 4 deg(v) of adjacency + 8 row offsets + 4 worklist entry + 4 own color + 4 color
+    write, plus 4 per vertex appended to the next worklist.  In-place: two sweeps per round.
+    Ordered and recoloring: the counting pass and the vertex's round each read the row once (row
+    offsets, own state, adjacency, one state gather per entry: 16 + 12 deg bytes), plus the count
+    write, the ready-list entry and the color (20 bytes a vertex) and an 8-byte count update per
+    edge; the recoloring pass also reads the given coloring."""
+    E = int(sum(int(x) for x in wl_degsum))  # sum over rounds of sum_{v in W_r} deg(v)
+    WT = int(sum(int(x) for x in wl_size))
+    if mode == "det":
+        return 4 * E + 20 * WT + 4 * (WT - n)
+    if mode == "inplace":
+        return 2 * (4 * E + 16 * WT) + 4 * (WT - n)
+    b = 2 * (12 * E + 16 * WT) + 20 * WT + 8 * (E // 2)
+    return b + 4 * n if mode == "recolor" else b
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -464,20 +483,7 @@ def main():
 
     # roofline of the dominant kernel (the persistent round kernel): algorithmic bytes per launch
     st = r0.stats
-    E = int(st.wl_degsum.sum())  # sum over rounds of sum_{v in W_r} deg(v)
-    WT = st.worklist_total
-    per_sweep = 4 * E + 20 * WT + 4 * (WT - g.n)
-    if mode == "det":
-        alg_bytes = per_sweep
-    elif mode == "inplace":
-        alg_bytes = 2 * (4 * E + 16 * WT) + 4 * (WT - g.n)
-    else:
-        # ordered and recoloring: the counting pass and the rounds each read every row once (rowptr pair, own state,
-        # colidx, one state gather per entry: 16 + 12 deg bytes), plus the pending-count write and
-        # read-modify-write per smaller-key entry (E / 2 of them), the ready lists and the color
-        alg_bytes = 2 * (12 * E + 16 * WT) + 4 * WT + 8 * (E // 2) + 8 * WT + 8 * WT
-        if mode == "recolor":
-            alg_bytes += 4 * g.n  # the given coloring, read by the set-up
+    alg_bytes = algorithmic_bytes(mode, g.n, st.wl_size, st.wl_degsum)
     kms = statistics.median(kernel_ms)
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (kms / 1e3) / 1e9

@@ -32,6 +32,12 @@ WORKLOAD_DESC = {
     "stencil256": "3-D 27-point stencil 256^3 (16,777,216 vertices), natural ids; int32 CSR",
     "er10k": "Erdos-Renyi n=10,000 average degree 16, seed 1; int32 CSR",
 }
+REF_SAMPLE = {  # the reference arm's per-step sample: a few seconds each, so --steps 10 ends in minutes
+    "rmat22": ("rmat20", "R-MAT scale 20 (1,048,576 vertices), same recipe, full deterministic coloring"),
+    "stencil256": ("stencil128", "27-point stencil 128^3, full deterministic coloring"),
+    "er10k": ("er10k", "the same ER graph, full deterministic coloring"),
+}
+
 CPU_SAMPLE = {  # bounded oracle sample of the same workload family (10-30 s single-threaded)
     "rmat22": ("rmat21", "R-MAT scale 21 (2,097,152 vertices), same recipe, full deterministic coloring"),
     "stencil256": ("stencil128", "27-point stencil 128^3, full deterministic coloring"),
@@ -170,7 +176,7 @@ def run_reference(args, rank, world):
         return
     import graphgen as gg
     import oracle
-    key, desc = CPU_SAMPLE.get(args.workload, (args.workload, "the same graph, full deterministic coloring"))
+    key, desc = REF_SAMPLE.get(args.workload, (args.workload, "the same graph, full deterministic coloring"))
     g = gg.workload(key)
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up effects worth a full run; warm-up steps are skipped

@@ -126,7 +126,11 @@ typedef struct gc_options {
                                   resident warp of the round kernel */
     int32_t priority;          /* deterministic, in-place and ordered modes: GC_PRIORITY_HASH (default),
                                   GC_PRIORITY_LARGEST_FIRST or GC_PRIORITY_SMALLEST_LAST */
-    int32_t reserved[6];
+    int32_t core_vertices;     /* deterministic mode: once the worklist has at most this many vertices, the
+                                  remaining rounds run with every worklist vertex's color in shared memory
+                                  (same results).  0 = the most one block's shared memory holds (about
+                                  110k); < 0 = never */
+    int32_t reserved[5];
 } gc_options;
 
 /* Optional run statistics (gc_color_ex / gc_color_batch_ex).  The caller may provide arrays

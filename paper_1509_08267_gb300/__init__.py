@@ -61,7 +61,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("max_rounds", ctypes.c_int32), ("small_max_degree", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("spin_limit_ns", ctypes.c_int64), ("flags", ctypes.c_uint32), ("partitions", ctypes.c_int32),
-                ("priority", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("priority", ctypes.c_int32), ("core_vertices", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class _Stats(ctypes.Structure):
@@ -201,6 +202,7 @@ class Options:
     flags: int = 0
     partitions: int = 0
     priority: int = 0
+    core_vertices: int = 0
 
     def _c(self, stream) -> _Options:
         o = _Options()
@@ -214,6 +216,7 @@ class Options:
         o.flags = self.flags
         o.partitions = self.partitions
         o.priority = self.priority
+        o.core_vertices = self.core_vertices
         return o
 
 

@@ -1,6 +1,7 @@
 // C ABI of the coloring library: argument checks, per-device context with cached scratch, host
 // array staging, and the launch sequence setup -> expand -> persistent round kernel -> counting.
 // Declarations and the contract of every entry point are in include/gc.h.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -83,6 +84,11 @@ struct Ctl {
     int32_t gmax1, gcount1, glast1, pad1;
     int32_t pad2[2];
     unsigned peel[4];  // smallest-last peeling: the two threshold words, the work items needed
+    unsigned long long ecnt[3];  // list entries of each counter set's worklist (core hand-over)
+    unsigned long long core_bump;
+    int32_t core_go, pad3;
+    unsigned core_cnt[12];
+    unsigned core_m[4];
     GridBar bar;
 };
 static_assert(offsetof(Ctl, bar) % 128 == 0, "barrier alignment");
@@ -99,6 +105,8 @@ struct Context {
     Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, lists, ctl, stats, bitmap, vg, hist;
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
     Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors, st_colors_in, mid0, mid1, rank;
+    Buf core_rec, core_cex, core_cpk, core_items, core_active, core_log, core_pool;
+    int32_t core_max_v = 0;  // largest core the round kernel's shared memory holds (-1: none)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // host adjacency arrays are uploaded on copy_stream while the set-up runs on the call's stream;
     // ev_before orders the upload after earlier work, ev_colidx marks it done
@@ -106,7 +114,8 @@ struct Context {
     cudaEvent_t ev_before = nullptr, ev_colidx = nullptr;
     void release_all() {
         Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &lists, &ctl, &stats, &bitmap, &hist,
-                      &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors, &st_colors_in, &mid0, &mid1, &rank};
+                      &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors, &st_colors_in, &mid0, &mid1, &rank,
+                      &core_rec, &core_cex, &core_cpk, &core_items, &core_active, &core_log, &core_pool};
         for (Buf *b : all) b->release();
     }
 };
@@ -418,6 +427,8 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     P.CH = CH;
     P.priority = priority;
     P.prio_rank = pb.prio_rank;
+    // the entries of each worklist's lists are counted for the core hand-over from round 1 on
+    if (mode == GC_MODE_DETERMINISTIC && compact && !(opt && opt->core_vertices < 0)) P.ecnt = ctl->ecnt;
 
     const bool timing = (flags & GC_FLAG_TIMING) != 0;
     Ctl h{};
@@ -510,6 +521,46 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     // by block in the sorted order
     P.spread = mode == GC_MODE_INPLACE && n_items == 0 && !pb.batch ? 1 : 0;
     if (compact) GC_TRY(ensure(C.lists, 4 * static_cast<size_t>(h.list_total), "neighbour lists"));
+    // core phase (deterministic compact mode): the last rounds with the worklist's colors in shared
+    // memory once at most core_M vertices with at most core_E list entries remain
+    const int32_t core_opt = opt ? opt->core_vertices : 0;
+    CoreParams Q{};
+    if (mode == GC_MODE_DETERMINISTIC && compact && core_opt >= 0 && pb.nnz > 0) {
+        if (C.core_max_v == 0) {
+            const int32_t cm = core_max_vertices();
+            C.core_max_v = cm > 0 ? cm : -1;
+        }
+        // the shared colors hold the core and a sentinel entry after it
+        int64_t M = std::min<int64_t>(n, static_cast<int64_t>(C.core_max_v) - 8);
+        if (core_opt > 0) M = std::min<int64_t>(M, core_opt);
+        if (M > 0) {
+            const int64_t E = std::min<int64_t>(pb.nnz, kCoreEntries);
+            const size_t Mp = (static_cast<size_t>(M) + 8) & ~size_t{7};
+            Q.max_v = static_cast<int32_t>(Mp);
+            Q.max_e = E;
+            Q.max_pieces = E / kCorePiece + static_cast<int64_t>(Mp) + 32;
+            GC_TRY(ensure(C.core_rec, 4 * kCoreRecWords * Mp, "core records"));
+            GC_TRY(ensure(C.core_cex, 2 * 4 * Mp, "core colors"));
+            GC_TRY(ensure(C.core_cpk, 2 * 2 * Mp, "core colors"));
+            GC_TRY(ensure(C.core_items, 16 * static_cast<size_t>(Q.max_pieces), "core pieces"));
+            GC_TRY(ensure(C.core_active, 2 * 4 * static_cast<size_t>(Q.max_pieces), "core active pieces"));
+            GC_TRY(ensure(C.core_log, 2 * 8 * Mp, "core change log"));
+            GC_TRY(ensure(C.core_pool, 4 * static_cast<size_t>(E) + 16, "core rows"));  // + prefetch slack
+            Q.rec = C.core_rec.as<unsigned>();
+            Q.cex = C.core_cex.as<int32_t>();
+            Q.cpk = C.core_cpk.as<uint16_t>();
+            Q.pieces = C.core_items.as<int4>();
+            Q.active = C.core_active.as<int32_t>();
+            Q.log = C.core_log.as<uint2>();
+            Q.pool = C.core_pool.as<int32_t>();
+            Q.bump = &ctl->core_bump;
+            Q.cnt = ctl->core_cnt;
+            Q.m = ctl->core_m;
+            P.core_max = static_cast<int32_t>(M);
+            P.core_emax = E;
+            P.core_go = &ctl->core_go;
+        }
+    }
     P.chunk0 = C.chunk0.as<int4>();
     P.chunk1 = C.chunk1.as<int4>();
     P.acc = C.acc.as<unsigned>();
@@ -534,6 +585,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     if (grid < 1) grid = 1;
     GC_TRY(wait_colidx(pb, s));
     GC_CUDA(launch_rounds(P, mode, pb.batch, compact, static_cast<int>(grid), block, s, wide));
+    if (P.core_max > 0) GC_CUDA(launch_core(P, Q, pb.batch, s));
     }
     if (timing) GC_CUDA(cudaEventRecord(C.ev[2], s));
 

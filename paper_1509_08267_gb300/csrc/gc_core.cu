@@ -1,0 +1,901 @@
+// Core phase of the deterministic mode (sm_103a).
+//
+// On power-law graphs the worklist of Algorithm 1 (Section 3.1) shrinks quickly in vertices but not
+// in adjacency: the high-degree vertices keep conflicting with one another for hundreds of rounds
+// (on R-MAT scale 22, ~100k vertices remain after round 22 and still hold 54M adjacency entries
+// between them, 1.7G over the remaining ~330 rounds).  In the round kernel each of those entries is
+// a dependent gather of a neighbour's state word from L2.  Once the worklist has at most M vertices,
+// this phase numbers them 0..m-1 (the core) and rebuilds each one's row as the list of its
+// neighbours that are still on the worklist, in local ids; neighbours already final never change
+// again, so their colors go once into the vertex's window of final colors.  Every block then keeps
+// the colors of all m core vertices in shared memory, 16 bits each (the color saturated at 0x7fff,
+// bit 15 FINAL), so a row's neighbour colors come from shared memory.
+//
+// The rule is unchanged: in round r a worklist vertex v loses iff a neighbour u with the same color
+// in C_r has a smaller key, and a loser's next color is the least color absent from C_r over its
+// neighbours.  The key order of each row entry is computed once, when the row is built (top bit of
+// the entry: the neighbour's key is smaller).  A final neighbour never has v's color (v's color was
+// chosen against it), so a vertex is re-queued only through its worklist neighbours; the window of
+// final colors joins the round's window for the least free color.  Colors are double-buffered as in
+// the round kernel (C_r read, C_{r+1} written), so the result is bit for bit that of the round kernel.
+//
+// Work decomposition.  Each row is cut once into pieces of at most kCorePiece entries, which the
+// warps own round-robin for the whole phase; a piece compacts itself in place (it drops neighbours
+// found final once a quarter of its entries are), so no work list, append or reservation is needed.
+// A round is: refresh the shared colors of the vertices the previous round finished; phase A, every
+// warp sweeps its pieces of worklist vertices (the next piece's first entries are loaded while the
+// current piece is merged) and ORs the piece's window, final window and conflict flag into the
+// vertex's record; grid barrier; phase B, one lane per worklist vertex reads the merged record,
+// takes the least free color or the FINAL state and writes both color buffers; grid barrier.
+//
+// Kernels: core_index_kernel (local ids, records, initial colors), core_fill_kernel (the rows),
+// core_round_kernel (one persistent cooperative launch with one block per SM running every
+// remaining round), core_writeback_kernel (final colors back into the state words).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+
+#include "gc_device.cuh"
+
+namespace gc {
+namespace {
+
+constexpr int kCoreThreads = 1024;  // one block per SM: every block holds all m colors
+constexpr int kCoreWarps = kCoreThreads / 32;
+constexpr int kCorePer = 8;  // entries per lane per step of a piece
+constexpr int kCoreStep = 32 * kCorePer;
+constexpr unsigned kPkFinal = 0x8000u;
+constexpr unsigned kPkSat = 0x7fffu;  // saturated: the color is 32767 or more (exact value in cex)
+constexpr int kFillThreads = 256;
+constexpr int kFillPer = 4;  // entries per lane per step of the row build
+constexpr int kPieceCompact = 1;  // piece flag: compact the piece in place during its next sweep
+
+__device__ __forceinline__ unsigned pack_color(int32_t c, bool fin) {
+    return (c < static_cast<int32_t>(kPkSat) ? static_cast<unsigned>(c) : kPkSat) | (fin ? kPkFinal : 0u);
+}
+
+__device__ __forceinline__ unsigned *core_rec(const CoreParams &Q, int64_t v) {
+    return Q.rec + static_cast<size_t>(v) * kCoreRecWords;
+}
+
+// Worklist of the hand-over round R0 as the round kernel left it.
+struct HandOver {
+    int R0;
+    unsigned nsmall, nchunks;
+    const uint64_t *colc;   // state words round R0 reads
+    const int32_t *smallc;  // vertices of degree <= T1
+    const DetItem *itc;     // work items of larger vertices
+};
+
+__device__ __forceinline__ HandOver hand_over(const RoundParams &P) {
+    HandOver h;
+    h.R0 = __ldcg(P.passes);
+    const unsigned *cc = P.cnt + kCnt * (h.R0 % 3);
+    h.nsmall = __ldcg(cc + kCntSmall);
+    h.nchunks = __ldcg(cc + kCntChunks);
+    const bool odd = (h.R0 & 1) != 0;
+    h.colc = odd ? P.col0 : P.col1;
+    h.smallc = odd ? P.small0 : P.small1;
+    h.itc = reinterpret_cast<const DetItem *>(odd ? P.chunk0 : P.chunk1);
+    return h;
+}
+
+// Record of core vertex `local` (global id V, graph g): its list at hand-over (`list`, len entries),
+// its degree, len entries of the pool for its row, its color in both buffers and the window of
+// final colors found so far (`fin_src`: the round kernel's slot, or none).
+__device__ void core_init_vertex(const RoundParams &P, const CoreParams &Q, int32_t local, int32_t V, int32_t g,
+                                 const int32_t *list, int32_t len, int32_t deg, const uint64_t *colc,
+                                 const unsigned *fin_src) {
+    P.items[V] = local;  // local id of V (the set-up scratch is free once the rounds run)
+    unsigned *rec = core_rec(Q, local);
+    const unsigned long long off = atomicAdd(Q.bump, static_cast<unsigned long long>(len));
+    const int32_t c = color_of(__ldcg(colc + V));
+    Q.cex[local] = c;
+    Q.cex[Q.max_v + local] = c;
+    Q.cpk[local] = static_cast<uint16_t>(pack_color(c, false));
+    Q.cpk[Q.max_v + local] = static_cast<uint16_t>(pack_color(c, false));
+    const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int w = 0; w < 32; w += 4) stcg4(rec + w, z);
+#pragma unroll
+    for (int w = 0; w < kAccWords; w += 4) stcg4(rec + kAccFin + w, fin_src ? ldcg4(fin_src + w) : z);
+    const uint64_t lp = reinterpret_cast<uint64_t>(list);
+    stcg4(rec + kCoreOffLo, make_uint4(static_cast<unsigned>(off), static_cast<unsigned>(off >> 32),
+                                       static_cast<unsigned>(deg), static_cast<unsigned>(V)));
+    stcg4(rec + kCoreFill, make_uint4(0u, static_cast<unsigned>(g), static_cast<unsigned>(lp),
+                                      static_cast<unsigned>(lp >> 32)));
+    stcg4(rec + kCoreListLen, make_uint4(static_cast<unsigned>(len), 0u, 0u, 0u));
+    stcg4(rec + 60, z);
+}
+
+// Local ids: the vertices of degree <= T1 in list order, then the larger vertices (numbered by their
+// first work item).  Writes every core vertex's record and colors.
+template <bool BATCH>
+__global__ void core_index_kernel(RoundParams P, CoreParams Q) {
+    if (__ldcg(P.core_go) == 0) return;
+    const HandOver h = hand_over(P);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < h.nsmall; i += stride) {
+        const int32_t V = __ldcg(h.smallc + i);
+        const Row r = load_row<BATCH>(P, V);
+        const int32_t deg = static_cast<int32_t>(r.e - r.b);
+        core_init_vertex(P, Q, static_cast<int32_t>(i), V, r.g, P.colidx + r.b, deg, deg, h.colc, nullptr);
+    }
+    for (int64_t base = t0 & ~int64_t{31}; base < h.nchunks; base += stride) {
+        const int64_t i = base + lane;
+        DetItem d{};
+        bool first = false;
+        if (i < h.nchunks) {
+            d = item_lane(h.itc + i);
+            first = d.lb == 0;
+        }
+        const unsigned mk = __ballot_sync(kFull, first);
+        if (mk == 0) continue;
+        unsigned b = 0;
+        if (lane == 0) b = atomicAdd(Q.m, static_cast<unsigned>(__popc(mk)));
+        b = __shfl_sync(kFull, b, 0);
+        if (!first) continue;
+        const int32_t local = static_cast<int32_t>(h.nsmall + b + __popc(mk & lanemask_lt()));
+        const unsigned *a = P.acc + static_cast<size_t>(d.slotf & kItemSlot) * kAccStride;
+        const int32_t len = static_cast<int32_t>(__ldcg(a + kAccLen));
+        const int32_t g = BATCH ? __ldg(P.vg + d.V) : 0;
+        core_init_vertex(P, Q, local, d.V, g, d.list, len, d.deg, h.colc, a + kAccFin);
+    }
+}
+
+// Rows of the core: one warp per vertex of degree <= T1 or per work item of a larger vertex (the
+// round-R0 decomposition).  Every entry of the vertex's current list is read once: a final
+// neighbour's color goes into the window of final colors, any other neighbour (a core vertex) is
+// appended to the vertex's row as its local id with the key-order bit.  Entries are checked as in
+// the round kernel (range, self-loop).
+template <bool BATCH>
+__global__ void __launch_bounds__(kFillThreads) core_fill_kernel(RoundParams P, CoreParams Q) {
+    __shared__ unsigned s_fin[kFillThreads / 32][kAccWords];
+    if (__ldcg(P.core_go) == 0) return;
+    const HandOver h = hand_over(P);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    const int64_t tasks = static_cast<int64_t>(h.nsmall) + h.nchunks;
+    const unsigned m = h.nsmall + __ldcg(Q.m);
+    unsigned *wfin = s_fin[wib];
+    for (int64_t t = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wib; t < tasks; t += nw) {
+        Row r;
+        const int32_t *list;
+        int64_t lb, le;
+        int32_t V;
+        if (t < h.nsmall) {
+            V = __ldcg(h.smallc + t);
+            r = load_row<BATCH>(P, V);
+            list = P.colidx + r.b;
+            lb = 0;
+            le = r.e - r.b;
+        } else {
+            const DetItem d = item_of(item_word(h.itc, static_cast<unsigned>(t - h.nsmall), lane));
+            V = d.V;
+            r.vbase = d.vbase;
+            r.ng = d.ng;
+            r.lv = V - d.vbase;
+            list = d.list;
+            lb = d.lb;
+            le = d.le;
+        }
+        const int32_t local = __ldcg(P.items + V);
+        unsigned *rec = core_rec(Q, local);
+        const uint32_t pv = prio_of(__ldcg(h.colc + V));
+        const uint64_t off = static_cast<uint64_t>(__ldcg(rec + kCoreOffLo)) |
+                             (static_cast<uint64_t>(__ldcg(rec + kCoreOffHi)) << 32);
+        int32_t *dst = Q.pool + off;
+        if (lane < kAccWords) wfin[lane] = 0u;
+        __syncwarp();
+        uint64_t flo = 0;
+        for (int64_t j0 = lb; j0 < le; j0 += 32 * kFillPer) {
+            int32_t ul[kFillPer];
+            uint64_t st[kFillPer];
+#pragma unroll
+            for (int q = 0; q < kFillPer; ++q) {
+                const int64_t j = j0 + lane + 32 * q;
+                ul[q] = j < le ? __ldcg(list + j) : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < kFillPer; ++q) {
+                const int64_t j = j0 + lane + 32 * q;
+                st[q] = kNoNeighbour;  // no neighbour (past the end, or a malformed entry)
+                if (j < le) {
+                    const int32_t U = neighbour(P, r, ul[q], j);
+                    if (U >= 0) st[q] = __ldcg(h.colc + U);
+                }
+            }
+            int32_t loc[kFillPer];
+#pragma unroll
+            for (int q = 0; q < kFillPer; ++q) {
+                loc[q] = -1;
+                if (st[q] != kNoNeighbour && !final_of(st[q])) loc[q] = __ldcg(P.items + r.vbase + ul[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < kFillPer; ++q) {
+                const int64_t j = j0 + lane + 32 * q;
+                bool keep = false;
+                uint32_t e = 0;
+                if (st[q] != kNoNeighbour) {
+                    if (final_of(st[q])) {
+                        const int32_t c = color_of(st[q]);
+                        if (static_cast<unsigned>(c) < 64u)
+                            flo |= 1ull << c;
+                        else if (static_cast<unsigned>(c) < 32u * kAccWords)
+                            atomicOr(&wfin[c >> 5], 1u << (c & 31));
+                    } else if (static_cast<unsigned>(loc[q]) < m) {
+                        keep = true;
+                        const bool smaller = key_less(prio_of(st[q]), pv, static_cast<uint32_t>(ul[q]),
+                                                      static_cast<uint32_t>(r.lv), P.seed);
+                        e = static_cast<uint32_t>(loc[q]) | (smaller ? kCoreSmaller : 0u);
+                    } else {
+                        // every vertex that is not final is on the worklist; anything else is a bug
+                        set_error(P.err, GC_ERR_INVALID_GRAPH, V, j);
+                    }
+                }
+                const unsigned km = __ballot_sync(kFull, keep);
+                if (km) {
+                    unsigned pos = 0;
+                    if (lane == 0) pos = atomicAdd(rec + kCoreFill, static_cast<unsigned>(__popc(km)));
+                    pos = __shfl_sync(kFull, pos, 0);
+                    if (keep) dst[pos + __popc(km & lanemask_lt())] = static_cast<int32_t>(e);
+                }
+            }
+        }
+        const unsigned f0 = __reduce_or_sync(kFull, static_cast<unsigned>(flo));
+        const unsigned f1 = __reduce_or_sync(kFull, static_cast<unsigned>(flo >> 32));
+        __syncwarp();
+        const unsigned fw = lane == 0 ? f0 : lane == 1 ? f1 : (lane < kAccWords ? wfin[lane] : 0u);
+        if (lane < kAccWords && fw) atomicOr(rec + kAccFin + lane, fw);
+        __syncwarp();
+    }
+}
+
+// Least color >= start absent from the neighbours of global vertex V in C_r (warp-cooperative, full
+// CSR row): a final neighbour's color from its state word, a core neighbour's from cex.  Used when
+// the 512-color window of a vertex is full.
+template <bool BATCH>
+__device__ int32_t core_mex_from(const RoundParams &P, const uint64_t *col_r0, int32_t V, const int32_t *cex_cur,
+                                 unsigned *win, int lane, int32_t start) {
+    const Row r = load_row<BATCH>(P, V);
+    for (int32_t base = start;; base += 32 * kAccWords) {
+        if (lane < kAccWords) win[lane] = 0;
+        __syncwarp();
+        for (int64_t j = r.b + lane; j < r.e; j += 32) {
+            const int32_t ul = __ldg(P.colidx + j);
+            if (static_cast<uint32_t>(ul) >= static_cast<uint32_t>(r.ng)) continue;
+            const uint64_t st = __ldcg(col_r0 + r.vbase + ul);
+            const int32_t c = (final_of(st) ? color_of(st) : __ldcg(cex_cur + __ldcg(P.items + r.vbase + ul))) - base;
+            if (static_cast<unsigned>(c) < 32u * kAccWords) atomicOr(&win[c >> 5], 1u << (c & 31));
+        }
+        __syncwarp();
+        int32_t res = -1;
+#pragma unroll 1
+        for (int w = 0; w < kAccWords; ++w) {
+            const unsigned x = win[w];
+            if (~x) {
+                res = base + 32 * w + __ffs(~x) - 1;
+                break;
+            }
+        }
+        __syncwarp();
+        if (res >= 0) return res;
+    }
+}
+
+// Entry m of the shared colors: a vertex that is FINAL with a color past every window, which the
+// padding slots of a step read (it changes no window, no flag and no count of survivors).
+constexpr uint16_t kPkSentinel = static_cast<uint16_t>(kPkFinal | kPkSat);
+
+// Shared-memory copy of packed colors [0, m) (16-byte loads; the buffers hold a multiple of 8 that
+// exceeds m), then the sentinel at m (written by the thread that stored its 16-byte group).
+__device__ __forceinline__ void load_packed(uint16_t *s_pk, const uint16_t *src, int32_t m) {
+    const int32_t n8 = (m + 7) >> 3;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(s_pk);
+    for (int32_t i = threadIdx.x; i < n8; i += blockDim.x) d4[i] = __ldcg(s4 + i);
+    if (threadIdx.x == static_cast<unsigned>((m >> 3) % static_cast<int32_t>(blockDim.x))) s_pk[m] = kPkSentinel;
+}
+
+// New shared colors of the vertices the previous round finished, from its change log.
+__device__ __forceinline__ void apply_log(uint16_t *s_pk, const uint2 *log, unsigned n) {
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint2 x = __ldcg(log + i);
+        s_pk[x.x] = static_cast<uint16_t>(x.y);
+    }
+}
+
+// A piece of a row: {local vertex, pool offset, entries, flags}.
+struct Piece {
+    int32_t v, off, cnt, flags;
+};
+
+__device__ __forceinline__ Piece piece_of(int4 x, int l) {
+    Piece p;
+    p.v = __shfl_sync(kFull, x.x, l);
+    p.off = __shfl_sync(kFull, x.y, l);
+    p.cnt = __shfl_sync(kFull, x.z, l);
+    p.flags = __shfl_sync(kFull, x.w, l);
+    return p;
+}
+
+// Bulk prefetch of a piece's entries into L2 (16-byte granules; the pool has 16 bytes of slack).
+__device__ __forceinline__ void prefetch_piece(const CoreParams &Q, int32_t off, int32_t cnt) {
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(Q.pool + off);
+    const uintptr_t a = a0 & ~uintptr_t{15};
+    const unsigned bytes = (static_cast<unsigned>(a0 - a) + 4u * static_cast<unsigned>(cnt) + 15u) & ~15u;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
+}
+
+// The round's active pieces a warp takes: entries gw, gw + nw, gw + 2 nw, ... of the round's list of
+// pieces (the pieces of its worklist vertices; every piece in the first round), in batches of 32 (one
+// per lane), skipping pieces without entries.
+struct PieceCursor {
+    unsigned base;  // first list position of the current batch
+    int4 d;         // this lane's piece in the batch
+    unsigned idx;   // its index
+    unsigned act;   // lanes of the batch not yet taken whose piece has entries
+};
+
+__device__ __forceinline__ void cursor_load(PieceCursor &c, const CoreParams &Q, const int32_t *list, unsigned nact,
+                                            unsigned nw, int lane) {
+    const unsigned i = c.base + static_cast<unsigned>(lane) * nw;
+    bool a = false;
+    c.d = make_int4(0, 0, 0, 0);
+    c.idx = 0;
+    if (i < nact) {
+        c.idx = list ? static_cast<unsigned>(__ldcg(list + i)) : i;
+        c.d = __ldcg(Q.pieces + c.idx);
+        a = c.d.z > 0;
+    }
+    c.act = __ballot_sync(kFull, a);
+    // the batch's second active piece (the first is loaded into registers right away)
+    const unsigned second = c.act & (c.act - 1u);
+    if (second && lane == __ffs(second) - 1) prefetch_piece(Q, c.d.y, c.d.z);
+}
+
+// Next piece of the warp (false when there is none); its index is *idx.  The piece after the next
+// one in the batch is prefetched into L2 (the next one's first entries are loaded into registers).
+__device__ __forceinline__ bool cursor_next(PieceCursor &c, const CoreParams &Q, const int32_t *list, unsigned nact,
+                                            unsigned nw, int lane, Piece &out, unsigned &idx) {
+    while (c.act == 0u) {
+        c.base += 32u * nw;
+        if (c.base >= nact) return false;
+        cursor_load(c, Q, list, nact, nw, lane);
+    }
+    const int l = __ffs(c.act) - 1;
+    c.act &= c.act - 1u;
+    out = piece_of(c.d, l);
+    idx = __shfl_sync(kFull, c.idx, l);
+    const unsigned later = c.act & (c.act - 1u);  // the batch's pieces after the next one
+    if (later && lane == __ffs(later) - 1) prefetch_piece(Q, c.d.y, c.d.z);
+    return true;
+}
+
+// Entries j0 + lane + 32 q of a piece; slots past its end read the sentinel m.
+__device__ __forceinline__ void load_piece_step(const CoreParams &Q, const Piece &p, int32_t j0, int lane, int32_t m,
+                                                int32_t (&e)[kCorePer]) {
+#pragma unroll
+    for (int q = 0; q < kCorePer; ++q) {
+        const int32_t j = j0 + lane + 32 * q;
+        e[q] = j < p.cnt ? __ldcg(Q.pool + p.off + j) : m;
+    }
+}
+
+// One step of a piece: every slot's neighbour color into the round window (colors below 128 in
+// two per-lane registers, the warp's shared window up to 512), the conflict flag (a smaller-key
+// neighbour with the vertex's color cpk, which is not saturated here), and the number of FINAL slots
+// (the sentinel counts as one).  COMPACT: the colors of FINAL neighbours also into the final window,
+// and the slots kept.  All eight colors are read before any is used.
+template <bool COMPACT>
+__device__ __forceinline__ void consume_step(const uint16_t *s_pk, const int32_t (&e)[kCorePer], unsigned cpk,
+                                             uint64_t &lo, uint64_t &mid, uint64_t &flo, unsigned *win,
+                                             unsigned *wfin, unsigned &conflict, unsigned &nfin, unsigned &keepm) {
+    unsigned sv[kCorePer];
+#pragma unroll
+    for (int q = 0; q < kCorePer; ++q) sv[q] = s_pk[static_cast<uint32_t>(e[q]) & ~kCoreSmaller];
+#pragma unroll
+    for (int q = 0; q < kCorePer; ++q) {
+        const unsigned c = sv[q] & kPkSat;
+        const unsigned fin = sv[q] >> 15;
+        const uint64_t b = 1ull << (c & 63u);
+        if (c < 64u) {
+            lo |= b;
+        } else if (c < 128u) {
+            mid |= b;
+        } else if (c < 32u * kAccWords) {
+            atomicOr(&win[c >> 5], 1u << (c & 31));
+        }
+        conflict |= (static_cast<uint32_t>(e[q]) >> 31) & static_cast<unsigned>(c == cpk);
+        nfin += fin;
+        if constexpr (COMPACT) {
+            if (fin) {
+                if (c < 64u)
+                    flo |= b;
+                else if (c < 32u * kAccWords)
+                    atomicOr(&wfin[c >> 5], 1u << (c & 31));
+            }
+            keepm |= (fin ^ 1u) << q;
+        }
+    }
+}
+
+// The same for a vertex whose own color is saturated (32767 or more): equal packed colors are
+// compared exactly.
+__device__ __noinline__ void consume_step_sat(const uint16_t *s_pk, const int32_t (&e)[kCorePer], int32_t cvx,
+                                              const int32_t *cex_cur, bool compact, uint64_t &flo, unsigned *wfin,
+                                              unsigned &conflict, unsigned &nfin, unsigned &keepm) {
+    for (int q = 0; q < kCorePer; ++q) {
+        const uint32_t id = static_cast<uint32_t>(e[q]) & ~kCoreSmaller;
+        const unsigned s = s_pk[id];
+        const unsigned c = s & kPkSat;
+        const unsigned fin = s >> 15;
+        if (e[q] < 0 && c == kPkSat && __ldcg(cex_cur + id) == cvx) conflict = 1u;
+        nfin += fin;
+        if (compact) {
+            if (fin) {
+                if (c < 64u)
+                    flo |= 1ull << c;
+                else if (c < 32u * kAccWords)
+                    atomicOr(&wfin[c >> 5], 1u << (c & 31));
+            }
+            keepm |= (fin ^ 1u) << q;
+        }
+    }
+}
+
+// Phase A of one round for one warp: every active piece it owns, as one stream of steps (the next
+// step's entries, possibly the next piece's first ones, are loaded before the current step is
+// consumed).  For each piece: the round window (all neighbour colors), the conflict flag (a
+// smaller-key neighbour with the vertex's color) and, when the piece compacts, the window of final
+// colors of the neighbours it drops; then ORed into the vertex's record.
+template <bool BATCH>
+__device__ void core_phase_a(const CoreParams &Q, const uint16_t *s_pk, const int32_t *cex_cur, const int32_t *list,
+                             unsigned nact, int32_t m, unsigned gw, unsigned nw, int lane, unsigned *win,
+                             unsigned *wfin, unsigned &st_read) {
+    PieceCursor cur;
+    cur.base = gw;
+    if (cur.base >= nact) return;
+    cursor_load(cur, Q, list, nact, nw, lane);
+    Piece p;
+    unsigned pidx = 0;
+    if (!cursor_next(cur, Q, list, nact, nw, lane, p, pidx)) return;
+    int32_t e[kCorePer];
+    load_piece_step(Q, p, 0, lane, m, e);
+    for (;;) {
+        // a piece starts: its windows, own color and compaction mode
+        if (lane < kAccWords) {
+            win[lane] = 0u;
+            wfin[lane] = 0u;
+        }
+        __syncwarp();
+        const unsigned cpk = s_pk[p.v] & kPkSat;  // own color (a worklist vertex is never final)
+        const bool sat = cpk == kPkSat;
+        const int32_t cvx = sat ? __ldcg(cex_cur + p.v) : static_cast<int32_t>(cpk);
+        const bool compact = (p.flags & kPieceCompact) != 0;
+        uint64_t lo = 0, mid = 0, flo = 0;
+        unsigned conflict = 0;
+        unsigned kept_total = 0;  // entries kept so far (the compaction position)
+        int32_t j0 = 0;
+        for (;;) {
+            // what comes next: this piece's next step or the next active piece's first step
+            Piece pn = p;
+            unsigned pnidx = pidx;
+            int32_t jn = j0 + kCoreStep;
+            bool more = jn < p.cnt;
+            if (!more) {
+                more = cursor_next(cur, Q, list, nact, nw, lane, pn, pnidx);
+                jn = 0;
+            }
+            int32_t en[kCorePer];
+            if (more) load_piece_step(Q, pn, jn, lane, m, en);
+            unsigned nfin = 0, keepm = 0;
+            if (sat) {
+                // window first (the saturated color is never in it), then the exact comparisons
+                consume_step<false>(s_pk, e, kPkSat + 1u, lo, mid, flo, win, wfin, conflict, nfin, keepm);
+                nfin = 0;
+                consume_step_sat(s_pk, e, cvx, cex_cur, compact, flo, wfin, conflict, nfin, keepm);
+            } else if (compact) {
+                consume_step<true>(s_pk, e, cpk, lo, mid, flo, win, wfin, conflict, nfin, keepm);
+            } else {
+                consume_step<false>(s_pk, e, cpk, lo, mid, flo, win, wfin, conflict, nfin, keepm);
+            }
+            const unsigned kept = static_cast<unsigned>(kCoreStep) - __reduce_add_sync(kFull, nfin);
+            if (compact && kept) {
+                // in place: the positions written never pass the ones already read
+                unsigned pos = kept_total;
+#pragma unroll
+                for (int q = 0; q < kCorePer; ++q) {
+                    const bool keep = (keepm >> q) & 1u;
+                    const unsigned km = __ballot_sync(kFull, keep);
+                    if (keep) Q.pool[p.off + pos + __popc(km & lanemask_lt())] = e[q];
+                    pos += __popc(km);
+                }
+            }
+            kept_total += kept;
+            const bool piece_done = jn == 0 || !more;
+            if (piece_done) {
+                // merge into the vertex's record; update the piece
+                const bool lose = __any_sync(kFull, conflict != 0u);
+                const unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
+                const unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
+                const unsigned lo2 = __reduce_or_sync(kFull, static_cast<unsigned>(mid));
+                const unsigned lo3 = __reduce_or_sync(kFull, static_cast<unsigned>(mid >> 32));
+                const unsigned f0 = __reduce_or_sync(kFull, static_cast<unsigned>(flo));
+                const unsigned f1 = __reduce_or_sync(kFull, static_cast<unsigned>(flo >> 32));
+                __syncwarp();
+                unsigned *rec = core_rec(Q, p.v);
+                const unsigned rw = lane == 0 ? lo0 : lane == 1 ? lo1 : lane == 2 ? lo2 : lane == 3 ? lo3
+                                  : (lane < kAccWords ? win[lane] : 0u);
+                const unsigned fw = lane == 0 ? f0 : lane == 1 ? f1 : (lane < kAccWords ? wfin[lane] : 0u);
+                if (lane < kAccWords && rw) atomicOr(rec + lane, rw);
+                if (lane < kAccWords && fw) atomicOr(rec + kAccFin + lane, fw);
+                if (lane == 0) {
+                    if (lose) atomicOr(rec + kCoreFlag, 1u);
+                    st_read += static_cast<unsigned>(p.cnt);
+                    const int32_t ncnt = compact ? static_cast<int32_t>(kept_total) : p.cnt;
+                    // compact during the next sweep once a quarter of the entries are final
+                    const int32_t nflags = 4ll * kept_total < 3ll * ncnt ? kPieceCompact : 0;
+                    if (ncnt != p.cnt || nflags != p.flags)
+                        reinterpret_cast<int2 *>(Q.pieces + pidx)[1] = make_int2(ncnt, nflags);
+                }
+                __syncwarp();
+            }
+            if (!more) return;
+            p = pn;
+            pidx = pnidx;
+            j0 = jn;
+#pragma unroll
+            for (int q = 0; q < kCorePer; ++q) e[q] = en[q];
+            if (piece_done) break;
+        }
+    }
+}
+
+// Phase B of one round: one thread per worklist vertex v (v = blockIdx.x * 1024 + threadIdx.x + k *
+// gridDim.x * 1024): the merged record tells whether v lost, and the colors around it; a loser takes
+// the least color absent from both windows (its full row is rescanned past 512 colors), a winner
+// becomes FINAL.  Both color buffers are written (C_{r+1}, and a winner's FINAL bit into C_r's packed
+// copy too), the vertex goes into the change log, a loser's pieces into the next round's list, and
+// the record's round part is cleared.  Positions in the log and the list are reserved per block (one
+// global atomic each), not per warp.
+template <bool BATCH>
+__device__ void core_phase_b(const RoundParams &P, const CoreParams &Q, const uint16_t *s_pk, int32_t m, int pass,
+                             const uint64_t *col_r0, unsigned *cn, int lane, unsigned *win, unsigned *s_res,
+                             unsigned &st_deg, unsigned &st_cnt, unsigned &n_lose) {
+    const int cur = pass & 1;
+    const int32_t *cex_cur = Q.cex + static_cast<size_t>(cur) * Q.max_v;
+    uint2 *log_next = Q.log + static_cast<size_t>(cur ^ 1) * Q.max_v;
+    int32_t *act_next = Q.active + static_cast<size_t>(cur ^ 1) * Q.max_pieces;
+    for (int64_t vb = static_cast<int64_t>(blockIdx.x) * blockDim.x; vb < m;
+         vb += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t v = static_cast<int32_t>(vb + threadIdx.x);
+        const unsigned pk = v < m ? s_pk[v] : kPkFinal;
+        const bool act = !(pk & kPkFinal);
+        unsigned *rec = core_rec(Q, v < m ? v : 0);
+        uint4 w[kAccWords / 4];
+        bool lose = false;
+        uint4 meta = make_uint4(0, 0, 0, 0);
+        unsigned pb = 0, pe = 0;
+        if (act) {
+#pragma unroll
+            for (int c = 0; c < kAccWords / 4; ++c) {
+                w[c] = ldcg4(rec + 4 * c);
+                const uint4 f = ldcg4(rec + kAccFin + 4 * c);
+                w[c].x |= f.x;
+                w[c].y |= f.y;
+                w[c].z |= f.z;
+                w[c].w |= f.w;
+            }
+            lose = __ldcg(rec + kCoreFlag) != 0u;
+            meta = ldcg4(rec + kCoreOffLo);  // off lo, off hi, degree, global id
+            if (lose) {
+                pb = __ldcg(rec + kCorePcBeg);
+                pe = __ldcg(rec + kCorePcEnd);
+            }
+        }
+        const unsigned cpk = pk & kPkSat;
+        const int32_t cv = cpk == kPkSat && act ? __ldcg(cex_cur + v) : static_cast<int32_t>(cpk);
+        int32_t nc = cv;
+        if (lose) {
+            nc = -1;
+#pragma unroll
+            for (int c = 0; c < kAccWords / 4; ++c)
+                if (nc < 0) nc = first_free4(w[c], 128 * c);
+        }
+        // rare: all of colors 0..511 taken; the warp rescans each such vertex's full row
+        unsigned need = __ballot_sync(kFull, lose && nc < 0);
+        while (need) {
+            const int l = __ffs(need) - 1;
+            need &= need - 1;
+            const int32_t x = core_mex_from<BATCH>(P, col_r0, static_cast<int32_t>(__shfl_sync(kFull, meta.w, l)),
+                                                   cex_cur, win, lane, 32 * kAccWords);
+            if (lane == l) nc = x;
+        }
+        // reservations: the warp's share of the block's, then one global atomic per block
+        const unsigned am = __ballot_sync(kFull, act);
+        const unsigned npc = pe - pb;
+        unsigned incl = npc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 31);
+        unsigned wl = 0, wa = 0;
+        if (lane == 0) {
+            if (am) wl = atomicAdd(&s_res[0], static_cast<unsigned>(__popc(am)));
+            if (total) wa = atomicAdd(&s_res[1], total);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_res[2] = s_res[0] ? atomicAdd(cn, s_res[0]) : 0u;
+            s_res[3] = s_res[1] ? atomicAdd(cn + 2, s_res[1]) : 0u;
+            s_res[0] = 0u;
+            s_res[1] = 0u;
+        }
+        __syncthreads();
+        const unsigned lb = s_res[2] + __shfl_sync(kFull, wl, 0), ab = s_res[3] + __shfl_sync(kFull, wa, 0);
+        if (act) {
+            const unsigned npk = pack_color(nc, !lose);
+            Q.cex[static_cast<size_t>(cur ^ 1) * Q.max_v + v] = nc;
+            Q.cpk[static_cast<size_t>(cur ^ 1) * Q.max_v + v] = static_cast<uint16_t>(npk);
+            if (!lose) Q.cpk[static_cast<size_t>(cur) * Q.max_v + v] = static_cast<uint16_t>(npk);
+            log_next[lb + __popc(am & lanemask_lt())] = make_uint2(static_cast<unsigned>(v), npk);
+            for (unsigned k = 0; k < npc; ++k) act_next[ab + incl - npc + k] = static_cast<int32_t>(pb + k);
+            const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int c = 0; c < kAccWords; c += 4) stcg4(rec + c, z);
+            if (lose) rec[kCoreFlag] = 0u;
+            st_deg += meta.z;
+            st_cnt += 1;
+            if (lose) ++n_lose;
+            if constexpr (BATCH) {
+                if (lose) note_graph_round(P, static_cast<int32_t>(__ldcg(rec + kCoreG)), pass + 1);
+            }
+        }
+        __syncthreads();  // s_res[2..3] are read before the next iteration reserves again
+    }
+}
+
+#ifdef GC_CORE_PROFILE
+// Per round (profiling builds only): earliest round start, latest refresh end, earliest / latest
+// phase-A end, latest phase-B start, latest phase-B end, worklist size.
+__device__ unsigned long long g_core_prof[8 * 4096];
+#define CORE_PROF(k, op) \
+    if (threadIdx.x == 0 && pass - R0 < 4096) op(g_core_prof + 8 * (pass - R0) + (k), global_ns())
+#else
+#define CORE_PROF(k, op)
+#endif
+
+// Every remaining round: one cooperative launch, one block of kCoreThreads per SM, the packed
+// colors of the core in dynamic shared memory.
+template <bool BATCH>
+__global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams P, CoreParams Q) {
+    extern __shared__ __align__(16) uint16_t s_pk[];
+    __shared__ unsigned s_win[kCoreWarps][kAccWords];
+    __shared__ unsigned s_fin[kCoreWarps][kAccWords];
+    __shared__ unsigned s_cnt[1];
+    __shared__ unsigned s_res[4];
+    if (__ldcg(P.core_go) == 0) return;
+    const HandOver h = hand_over(P);
+    const int R0 = h.R0;
+    const int32_t m = static_cast<int32_t>(h.nsmall + __ldcg(Q.m));
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    const unsigned gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (blockIdx.x == 0 && threadIdx.x == 0) Q.m[1] = static_cast<unsigned>(m);  // for the write-back
+    load_packed(s_pk, Q.cpk + static_cast<size_t>(R0 & 1) * Q.max_v, m);
+    {
+        // the pieces of every row: consecutive pieces of a row go to consecutive warps
+        const unsigned stride = gridDim.x * blockDim.x;
+        for (unsigned base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < static_cast<unsigned>(m);
+             base += stride) {
+            const unsigned v = base + lane;
+            unsigned len = 0, np = 0;
+            uint64_t off = 0;
+            if (v < static_cast<unsigned>(m)) {
+                const unsigned *rec = core_rec(Q, v);
+                len = __ldcg(rec + kCoreFill);  // the row as the fill kernel wrote it
+                off = static_cast<uint64_t>(__ldcg(rec + kCoreOffLo)) |
+                      (static_cast<uint64_t>(__ldcg(rec + kCoreOffHi)) << 32);
+                np = (len + kCorePiece - 1) / kCorePiece;
+            }
+            unsigned incl = np;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned total = __shfl_sync(kFull, incl, 31);
+            unsigned b = 0;
+            if (lane == 0 && total) b = atomicAdd(Q.m + 2, total);
+            b = __shfl_sync(kFull, b, 0);
+            if (v < static_cast<unsigned>(m)) {
+                unsigned *rec = core_rec(Q, v);
+                rec[kCorePcBeg] = b + incl - np;
+                rec[kCorePcEnd] = b + incl;
+            }
+            for (unsigned k = 0; k < np; ++k) {
+                const unsigned lb = k * kCorePiece;
+                Q.pieces[b + incl - np + k] =
+                    make_int4(static_cast<int32_t>(v), static_cast<int32_t>(off + lb),
+                              static_cast<int32_t>(min(len - lb, static_cast<unsigned>(kCorePiece))), 0);
+            }
+        }
+    }
+    unsigned bar_target = 0;
+    int pass = R0;
+    if (grid_sync(P.bar, bar_target, P.err, P.spin_ns)) {
+        const unsigned npieces = __ldcg(Q.m + 2);
+        for (;; ++pass) {
+            unsigned *cc = Q.cnt + 4 * (pass % 3);
+            unsigned *cn = Q.cnt + 4 * ((pass + 1) % 3);
+            // |W_pass|: every core vertex in the first round, then the previous round's losers
+            const unsigned nv = pass == R0 ? static_cast<unsigned>(m) : __ldcg(cc + 1);
+            if (nv == 0u) break;
+            if (pass >= P.pass_end) {
+                if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
+                    set_error(P.err, GC_ERR_NO_CONVERGENCE, pass, 0);
+                break;
+            }
+            if (blockIdx.x == 0 && threadIdx.x < 4) Q.cnt[4 * ((pass + 2) % 3) + threadIdx.x] = 0u;
+            if (threadIdx.x == 0) s_cnt[0] = 0u;
+            CORE_PROF(0, atomicMin);
+#ifdef GC_CORE_PROFILE
+            if (blockIdx.x == 0 && threadIdx.x == 0 && pass - R0 < 4096) g_core_prof[8 * (pass - R0) + 7] = nv;
+#endif
+            const int32_t *cex_cur = Q.cex + static_cast<size_t>(pass & 1) * Q.max_v;
+            if (pass > R0) {
+                // the vertices the previous round finished: its change log, or all colors when they are many
+                const unsigned nprev = __ldcg(cc);
+                if (4ull * nprev > static_cast<unsigned long long>(m))
+                    load_packed(s_pk, Q.cpk + static_cast<size_t>(pass & 1) * Q.max_v, m);
+                else
+                    apply_log(s_pk, Q.log + static_cast<size_t>(pass & 1) * Q.max_v, nprev);
+            }
+            __syncthreads();
+            CORE_PROF(1, atomicMax);
+            unsigned st_deg = 0, st_cnt = 0, st_read = 0, n_lose = 0;
+            // the round's pieces: all of them in the first round, then those the previous round listed
+            const int32_t *list = pass == R0 ? nullptr : Q.active + static_cast<size_t>(pass & 1) * Q.max_pieces;
+            const unsigned nact = pass == R0 ? npieces : __ldcg(cc + 2);
+            core_phase_a<BATCH>(Q, s_pk, cex_cur, list, nact, m, gw, nw, lane, s_win[wib], s_fin[wib], st_read);
+#ifdef GC_CORE_PROFILE
+            __syncthreads();
+            CORE_PROF(2, atomicMin);
+            CORE_PROF(3, atomicMax);
+#endif
+            if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
+            CORE_PROF(4, atomicMax);
+            if (threadIdx.x < 2) s_res[threadIdx.x] = 0u;
+            __syncthreads();
+            core_phase_b<BATCH>(P, Q, s_pk, m, pass, h.colc, cn, lane, s_win[wib], s_res, st_deg, st_cnt, n_lose);
+#ifdef GC_CORE_PROFILE
+            __syncthreads();
+            CORE_PROF(5, atomicMax);
+#endif
+            const unsigned lose_w = __reduce_add_sync(kFull, n_lose);
+            if (lane == 0 && lose_w) atomicAdd(&s_cnt[0], lose_w);
+            if (P.stats) flush_stats(P, pass, st_deg, st_cnt, st_read);
+            __syncthreads();
+            if (threadIdx.x == 0 && s_cnt[0]) atomicAdd(cn + 1, s_cnt[0]);
+            if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.passes[0] = pass;
+        P.passes[1] = pass - 1;
+    }
+}
+
+// Final colors of the core into both state buffers (FINAL set), where the color count reads them.
+__global__ void core_writeback_kernel(RoundParams P, CoreParams Q) {
+    if (__ldcg(P.core_go) == 0) return;
+    const int64_t m = __ldcg(Q.m + 1);  // the round kernel rewrote passes[0]; it recorded m here
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t V = static_cast<int32_t>(__ldcg(core_rec(Q, i) + kCoreGid));
+        const int32_t c = __ldcg(Q.cex + i);
+        const uint64_t w = pack_state(c, prio_of(__ldcg(P.col0 + V)), true);
+        P.col0[V] = w;
+        P.col1[V] = w;
+    }
+}
+
+int core_static_smem(bool batch) {
+    cudaFuncAttributes a{};
+    const void *f = batch ? reinterpret_cast<const void *>(&core_round_kernel<true>)
+                          : reinterpret_cast<const void *>(&core_round_kernel<false>);
+    if (cudaFuncGetAttributes(&a, f) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return static_cast<int>(a.sharedSizeBytes);
+}
+
+}  // namespace
+
+int32_t core_max_vertices() {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int st = std::max(core_static_smem(false), core_static_smem(true));
+    if (st < 0) return 0;
+    // the largest multiple of 64 vertices whose colors (2 bytes each) leave one block resident per SM
+    for (int64_t m = ((static_cast<int64_t>(optin) - st) / 2) & ~int64_t{63}; m >= 64; m -= 1024) {
+        const int smem = static_cast<int>(2 * m);
+        bool ok = true;
+        for (int b = 0; b < 2 && ok; ++b) {
+            const void *f = b ? reinterpret_cast<const void *>(&core_round_kernel<true>)
+                              : reinterpret_cast<const void *>(&core_round_kernel<false>);
+            int per_sm = 0;
+            ok = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kCoreThreads, smem) == cudaSuccess &&
+                 per_sm >= 1;
+        }
+        if (ok) return static_cast<int32_t>(m);
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+cudaError_t launch_core(const RoundParams &P, const CoreParams &Q, bool batch, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const size_t smem = 2 * static_cast<size_t>(Q.max_v);
+    const void *round_fn = batch ? reinterpret_cast<const void *>(&core_round_kernel<true>)
+                                 : reinterpret_cast<const void *>(&core_round_kernel<false>);
+    e = cudaFuncSetAttribute(round_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, round_fn, kCoreThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = sms * 8;
+    if (batch) {
+        core_index_kernel<true><<<grid, 256, 0, s>>>(P, Q);
+        core_fill_kernel<true><<<grid, kFillThreads, 0, s>>>(P, Q);
+    } else {
+        core_index_kernel<false><<<grid, 256, 0, s>>>(P, Q);
+        core_fill_kernel<false><<<grid, kFillThreads, 0, s>>>(P, Q);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(&P.bar->count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    RoundParams pa = P;
+    CoreParams qa = Q;
+    void *args[] = {&pa, &qa};
+#ifdef GC_CORE_PROFILE
+    static unsigned long long h_prof[8 * 4096];
+    for (int r = 0; r < 4096; ++r)
+        for (int k = 0; k < 8; ++k) h_prof[8 * r + k] = (k == 0 || k == 2) ? ~0ull : 0ull;
+    cudaMemcpyToSymbolAsync(g_core_prof, h_prof, sizeof h_prof, 0, cudaMemcpyHostToDevice, s);
+#endif
+    e = cudaLaunchCooperativeKernel(round_fn, dim3(sms), dim3(kCoreThreads), args, smem, s);
+    if (e != cudaSuccess) return e;
+#ifdef GC_CORE_PROFILE
+    cudaMemcpyFromSymbolAsync(h_prof, g_core_prof, sizeof h_prof, 0, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (const char *path = getenv("GC_CORE_PROFILE_OUT")) {
+        if (FILE *f = fopen(path, "w")) {
+            for (int r = 0; r < 4096 && h_prof[8 * r] != ~0ull; ++r) {
+                for (int k = 0; k < 8; ++k) fprintf(f, "%llu ", h_prof[8 * r + k]);
+                fprintf(f, "\n");
+            }
+            fclose(f);
+        }
+    }
+#endif
+    core_writeback_kernel<<<grid, 256, 0, s>>>(P, Q);
+    return cudaGetLastError();
+}
+
+}  // namespace gc

@@ -126,6 +126,49 @@ struct RoundParams {
     const int32_t *prio_rank;  // smallest last: the peel levels; recoloring: the given coloring (int32[n])
     int32_t spread;  // in-place mode: phase 1 takes the thread worklist in a spread order (set when no
                      // vertex is past T1: the degree-sorted order then balances nothing)
+    // Hand-over to the core phase (deterministic compact mode).  core_max > 0: the round kernel stops
+    // at the top of the first round whose worklist has at most core_max vertices whose lists hold at
+    // most core_emax entries, and sets *core_go; the core kernels (gc_core.cu) finish the coloring.
+    int32_t core_max;
+    int64_t core_emax;
+    unsigned long long *ecnt;  // [3] entries in the lists of each counter set's worklist (core_max > 0)
+    int32_t *core_go;          // set to 1 by the round kernel when it hands over
+};
+
+// Core phase (gc_core.cu).  Once the worklist is small, its vertices get local ids 0..m-1 (the core)
+// and their rows are rebuilt as lists of the local ids of neighbours still on the worklist, the
+// neighbour's key order in the top bit (kCoreSmaller: smaller key than the row's vertex); the colors
+// of neighbours already final go into the vertex's window of final colors.  Each round every block
+// keeps the colors of all m core vertices in shared memory (16 bits each: the color saturated at
+// 0x7fff, bit 15 FINAL), so a row's neighbour colors come from shared memory instead of L2.  Rows
+// are cut once into pieces of at most kCorePiece entries that the warps own for the whole phase.
+constexpr uint32_t kCoreSmaller = 0x80000000u;
+constexpr int64_t kCoreEntries = int64_t{1} << 27;  // list entries the core phase takes at most
+#ifndef GC_CORE_PIECE
+#define GC_CORE_PIECE 1024
+#endif
+constexpr int kCorePiece = GC_CORE_PIECE;
+// Per core vertex, kCoreRecWords words: [0, 16) the round's window of neighbour colors 0..511,
+// kCoreFlag (some smaller-key neighbour has the vertex's color), [kAccFin, kAccFin + 16) the window of
+// final neighbours' colors, then the row's offset in the pool, degree, global id, row length, graph.
+constexpr int kCoreRecWords = 64;
+constexpr int kCoreFlag = 16;
+constexpr int kCoreOffLo = 48, kCoreOffHi = 49, kCoreDeg = 50, kCoreGid = 51, kCoreFill = 52, kCoreG = 53;
+constexpr int kCoreListLo = 54, kCoreListHi = 55, kCoreListLen = 56, kCorePcBeg = 57, kCorePcEnd = 58;
+struct CoreParams {
+    int32_t max_v;        // vertex capacity M (shared memory holds M 16-bit colors; a multiple of 8)
+    int64_t max_e;        // list entries the core may hold (the pool's size)
+    int64_t max_pieces;   // piece capacity: max_e / kCorePiece + M
+    unsigned *rec;        // [M][kCoreRecWords]
+    int32_t *cex;         // [2][M] exact colors, double-buffered like col0 / col1
+    uint16_t *cpk;        // [2][M] packed colors (color saturated at 0x7fff, bit 15 FINAL)
+    int4 *pieces;         // [max_pieces] {local vertex, pool offset, entries, flags}
+    int32_t *active;      // [2][max_pieces] the pieces of each round's worklist vertices
+    uint2 *log;           // [2][M] {local vertex, packed color} of the vertices a round finished
+    int32_t *pool;        // [max_e] the rows
+    unsigned long long *bump;  // pool allocation counter
+    unsigned *cnt;        // [3][4] per-round counters: vertices finished (log entries), losers, active pieces
+    unsigned *m;          // [4]: larger vertices numbered by the index kernel, m, pieces
 };
 
 // Launch wrappers (gc_kernels.cu).  All return the launch's cudaError_t.
@@ -189,6 +232,11 @@ cudaError_t partition_kernel_occupancy(int block, int *blocks_per_sm);
 cudaError_t launch_partition_rounds(const RoundParams &P, int32_t p, int grid, int block, cudaStream_t s);
 cudaError_t launch_validate(int32_t n, const int32_t *rowptr, const int32_t *colidx, int flags, int32_t *err,
                             cudaStream_t s);
+// Core phase (after launch_rounds handed over, *P.core_go = 1; every kernel returns at once when
+// it did not): local ids and rows, the round kernel, and the final colors written back to col0 and
+// col1.  core_max_vertices: the largest M the shared memory of one block per SM allows.
+int32_t core_max_vertices();
+cudaError_t launch_core(const RoundParams &P, const CoreParams &Q, bool batch, cudaStream_t s);
 
 }  // namespace gc
 

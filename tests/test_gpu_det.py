@@ -21,16 +21,26 @@ def run_det(gc, g, seed, options=None, stats=False):
     return r.colors.cpu().numpy(), r.ncolors, r.rounds, r.stats
 
 
+def core_variants(gc, g):
+    """The library default (small graphs run every round in the shared-memory core phase), the
+    regular round kernel alone, and hand-overs to the core phase part-way through the run."""
+    out = [gc.Options(), gc.Options(core_vertices=-1)]
+    for cap in (max(1, g.n // 10), max(1, g.n // 3)):
+        out.append(gc.Options(core_vertices=cap))
+    return out
+
+
 def assert_parity(gc, g, seed, options=None, check_stats=True):
     ref = oracle.det(g, seed)
     assert ref.status == 0
-    colors, nc, rounds, st = run_det(gc, g, seed, options=options, stats=check_stats)
-    np.testing.assert_array_equal(colors, ref.colors, err_msg=f"{g.name} seed {seed}")
-    assert nc == ref.ncolors
-    assert rounds == ref.rounds
-    if check_stats and g.n > 0:
-        np.testing.assert_array_equal(st.wl_size, ref.wl_size)
-        np.testing.assert_array_equal(st.wl_degsum, ref.wl_degsum)
+    for opt in ([options] if options is not None else core_variants(gc, g)):
+        colors, nc, rounds, st = run_det(gc, g, seed, options=opt, stats=check_stats)
+        np.testing.assert_array_equal(colors, ref.colors, err_msg=f"{g.name} seed {seed} {opt}")
+        assert nc == ref.ncolors, opt
+        assert rounds == ref.rounds, opt
+        if check_stats and g.n > 0:
+            np.testing.assert_array_equal(st.wl_size, ref.wl_size, err_msg=str(opt))
+            np.testing.assert_array_equal(st.wl_degsum, ref.wl_degsum, err_msg=str(opt))
     return ref
 
 
@@ -120,7 +130,10 @@ def test_full_sweep_matches_oracle(gclib, make):
     g = make()
     ref = oracle.det(g, 11)
     for opt in (gclib.Options(flags=gclib.FLAG_FULL_SWEEP), gclib.Options(flags=gclib.FLAG_FULL_SWEEP, chunk=128),
-                gclib.Options(chunk=32, small_max_degree=4), gclib.Options(chunk=1024)):
+                gclib.Options(chunk=32, small_max_degree=4), gclib.Options(chunk=1024),
+                gclib.Options(chunk=32, small_max_degree=4, core_vertices=-1),
+                gclib.Options(chunk=32, small_max_degree=4, core_vertices=max(1, g.n // 20)),
+                gclib.Options(chunk=128, core_vertices=max(1, g.n // 5))):
         c, nc, rounds, st = run_det(gclib, g, 11, options=opt, stats=True)
         np.testing.assert_array_equal(c, ref.colors)
         assert (nc, rounds) == (ref.ncolors, ref.rounds)

@@ -22,11 +22,21 @@ def full(request):
     return g, torch.from_numpy(g.rowptr).cuda(), torch.from_numpy(g.colidx).cuda()
 
 
-def test_full_size_deterministic_matches_oracle(gclib, full):
-    g, rp, ci = full
-    r = gclib.color(rp, ci, "det", SEED, stats=True, round_cap=1 << 12)
+@pytest.fixture(scope="module")
+def full_ref(full):
+    g, _, _ = full
     ref = oracle.det(g, SEED)
     assert ref.status == 0
+    return ref
+
+
+@pytest.mark.parametrize("core", [0, -1, 20_000], ids=["core-default", "core-off", "core-20k"])
+def test_full_size_deterministic_matches_oracle(gclib, full, full_ref, core):
+    # the library default hands the last rounds to the shared-memory core phase; -1 keeps every
+    # round in the regular round kernel; 20k hands over later
+    g, rp, ci = full
+    ref = full_ref
+    r = gclib.color(rp, ci, "det", SEED, stats=True, round_cap=1 << 12, options=gclib.Options(core_vertices=core))
     np.testing.assert_array_equal(r.colors.cpu().numpy(), ref.colors)
     assert (r.ncolors, r.rounds) == (ref.ncolors, ref.rounds)
     np.testing.assert_array_equal(r.stats.wl_size, ref.wl_size)

@@ -74,7 +74,8 @@ def load_peaks():
 
 
 class ClockSampler:
-    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs (started
+    before the warm-up; mark() drops the samples taken before the timed region)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -103,6 +104,14 @@ class ClockSampler:
             if len(parts) >= 9:
                 self.rows.append(parts)
 
+    def wait_first_sample(self, timeout_s=5.0):
+        t0 = time.perf_counter()
+        while self.proc and not self.rows and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.01)
+
+    def mark(self):
+        self.rows = []
+
     def stop(self):
         if self.proc:
             self.proc.terminate()
@@ -128,7 +137,7 @@ def kernel_source_sha256():
     """Digest of the round kernel's sources (the kernels and the layout constants they use)."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("gc_kernels.cu", "gc_internal.h"):
+    for name in ("gc_kernels.cu", "gc_core.cu", "gc_device.cuh", "gc_internal.h"):
         with open(os.path.join(ROOT, "paper_1509_08267_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -215,83 +224,103 @@ def batch_graphs(name):
     return b
 
 
-def run_batch(args, rank, world):
-    """Batched coloring of G graphs in one persistent launch against a loop of gc_color over the same
-    device-resident graphs; both must give identical colorings."""
-    import torch
-    import torch.distributed as dist
+def shard_graphs(b, rank, world):
+    """Graph-sharded batching: rank `rank` of `world` takes a subset of the batch's graphs, greedily
+    balanced by adjacency entries (largest first onto the least loaded rank).  Returns the graph ids,
+    in increasing order."""
+    sizes = [(int(b.edge_off[g + 1] - b.edge_off[g]) + int(b.vtx_off[g + 1] - b.vtx_off[g]), g) for g in range(b.G)]
+    load = [0] * world
+    owner = [0] * b.G
+    for sz, g in sorted(sizes, key=lambda x: (-x[0], x[1])):
+        r = min(range(world), key=lambda k: (load[k], k))
+        owner[g] = r
+        load[r] += sz
+    return [g for g in range(b.G) if owner[g] == rank]
 
+
+def batched_object(args, rank, world, G):
+    """Batched coloring of G mixed graphs in one persistent launch against a loop of gc_color over the
+    same device-resident graphs, both timed by wall clock around synchronised device work; both must
+    give identical colorings.  With several ranks each colors its share of the graphs (no
+    collective; the slowest rank's time counts)."""
+    import torch
+
+    import graphgen as gg
     import paper_1509_08267_gb300 as gc
+    from paper_1509_08267_gb300 import autotune
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dev = torch.device("cuda", local)
-    b = batch_graphs(args.workload)
-    G = b.G
+    full = batch_graphs(f"batch{G}")
+    mine = shard_graphs(full, rank, world) if world > 1 else list(range(full.G))
+    b = gg.pack([full.graph(g) for g in mine]) if world > 1 else full
     vo = torch.from_numpy(b.vtx_off).to(dev)
     eo = torch.from_numpy(b.edge_off).to(dev)
     rp = torch.from_numpy(b.rowptr).to(dev)
     ci = torch.from_numpy(b.colidx).to(dev)
     N, NNZ = int(b.vtx_off[-1]), int(b.edge_off[-1])
-    out = torch.empty(N, dtype=torch.int32, device=dev)
-    from paper_1509_08267_gb300 import autotune
-    tuned = autotune.batch_options()  # knobs chosen by the autotuner for batches (defaults without a table)
-    opt = gc.Options(**{**tuned.__dict__, "flags": tuned.flags | gc.FLAG_TIMING})
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    for _ in range(args.warmup):
-        gc.color_batch(vo, eo, rp, ci, args.mode, HASH_SEED, out=out, options=opt)
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream(dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    clocks.start()
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        ev[k][0].record(stream)
-        _, nc_b, rd_b, st = gc.color_batch(vo, eo, rp, ci, args.mode, HASH_SEED, out=out, options=opt, stats=True)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    t_batch = reduce_max(sum(a.elapsed_time(c) for a, c in ev) / 1e3 / args.steps, world, dev)
-    # one by one: the same device-resident graphs, one gc_color call each (each call synchronises)
-    solo = torch.empty(N, dtype=torch.int32, device=dev)
-    vo_h, eo_h = b.vtx_off, b.edge_off
+    out = torch.empty(max(N, 1), dtype=torch.int32, device=dev)[:N]
+    tuned = autotune.batch_options()
+    steps = max(1, min(args.steps, 5))
+    for _ in range(2):
+        gc.color_batch(vo, eo, rp, ci, "det", HASH_SEED, out=out, options=tuned)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    nc_s = np.zeros(G, np.int32)
-    rd_s = np.zeros(G, np.int32)
-    for g in range(G):
+    for _ in range(steps):
+        _, nc_b, rd_b = gc.color_batch(vo, eo, rp, ci, "det", HASH_SEED, out=out, options=tuned)
+    torch.cuda.synchronize()
+    t_batch = reduce_max((time.perf_counter() - t0) / steps, world, dev)
+    solo = torch.empty_like(out)
+    vo_h, eo_h = b.vtx_off, b.edge_off
+    nc_s = np.zeros(b.G, np.int32)
+    rd_s = np.zeros(b.G, np.int32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in range(b.G):
         v0, v1, e0, e1 = int(vo_h[g]), int(vo_h[g + 1]), int(eo_h[g]), int(eo_h[g + 1])
-        r = gc.color(rp[v0 + g: v1 + g + 1], ci[e0:e1], args.mode, HASH_SEED, out=solo[v0:v1])
+        r = gc.color(rp[v0 + g: v1 + g + 1], ci[e0:e1], "det", HASH_SEED, out=solo[v0:v1])
         nc_s[g], rd_s[g] = r.ncolors, r.rounds
     torch.cuda.synchronize()
-    t_solo = time.perf_counter() - t0
+    t_solo = reduce_max(time.perf_counter() - t0, world, dev)
     same = bool(torch.equal(out, solo)) and np.array_equal(nc_s, nc_b) and np.array_equal(rd_s, rd_b)
-    m_und = NNZ / 2
+    m_job = float(full.edge_off[-1]) / 2  # the whole batch over all ranks
+    return {
+        "graphs": full.G, "vertices": int(full.vtx_off[-1]), "nnz": int(full.edge_off[-1]),
+        "recipe": "n log-uniform [100, 2e5]; even graphs ER (avg degree U[4,64]), odd graphs R-MAT "
+                  "(edge factor U[8,16]); seed 3; deterministic mode, hash seed 7",
+        "value": m_job / t_batch / 1e9, "unit": "Gedges/s", "ms_per_batch": t_batch * 1e3,
+        "one_by_one": {"value": m_job / t_solo / 1e9, "unit": "Gedges/s", "seconds": t_solo,
+                       "note": "loop of gc_color over the same device-resident graphs"},
+        "batched_over_one_by_one": t_solo / t_batch,
+        "identical_colorings": same,
+        "timing": "wall clock around synchronised device work, both arms",
+        "sharding": f"graphs split over {world} ranks by adjacency entries" if world > 1 else "single",
+        "tuned_options": {k: v for k, v in tuned.__dict__.items() if v},
+    }
+
+
+def run_batch(args, rank, world):
+    """The batched workload alone (--workload batchG): one JSON line."""
+    G = int(args.workload[5:])
+    obj = batched_object(args, rank, world, G)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": whole_job_rate(m_und, t_batch, world) / 1e9, "unit": "Gedges/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": args.workload, "graphs": G, "vertices": N, "nnz": NNZ,
-                       "recipe": "n log-uniform [100, 2e5]; even graphs ER (avg degree U[4,64]), odd graphs R-MAT "
-                                 "(edge factor U[8,16]); seed 3", "mode": args.mode, "hash_seed": HASH_SEED},
-            "one_by_one": {"value": m_und / t_solo / 1e9, "unit": "Gedges/s", "seconds": t_solo,
-                           "note": "loop of gc_color over the same device-resident graphs"},
-            "batched_over_one_by_one": t_solo / t_batch,
-            "identical_colorings": same,
-            "batch_rounds": int(st.rounds), "batch_kernel_ms": st.kernel_ms,
-            "tuned_options": {k: v for k, v in tuned.__dict__.items() if v},
-            # batch tables, setup, degree sort (2), expand, round kernel, color count (2) per call
-            "gpu_launches": 8 * args.steps, "clocks": clk,
+            "metric": METRIC, "value": obj["value"], "unit": "Gedges/s", "n_gpus": world,
+            "steps": max(1, min(args.steps, 5)), "warmup": args.warmup, "ms_per_step": obj["ms_per_batch"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "graphs": obj["graphs"], "vertices": obj["vertices"],
+                       "nnz": obj["nnz"], "recipe": obj["recipe"], "mode": "det", "hash_seed": HASH_SEED,
+                       "parallelism": obj["sharding"]},
+            "batched": obj,
         }
         print(json.dumps(line), flush=True)
 
 
 def serve_pool(count, seed=4):
     """Request graphs for the serving benchmark: n log-uniform in [1e3, 2e6], a mix of ER (avg degree
-    U[4,32]), R-MAT (edge factor U[4,16]) and 2-D 5-point grids, from the stream `seed`."""
+    U[4,32]), R-MAT (edge factor U[4,16]) and 2-D 5-point grids, from the stream `seed` (generated
+    on all host cores; the generator releases the GIL)."""
     import math
+    from concurrent.futures import ThreadPoolExecutor
 
     import graphgen as gg
     specs = []
@@ -303,90 +332,117 @@ def serve_pool(count, seed=4):
         kind = ("er", "rmat", "grid")[i % 3]
         param = 4 + u1 * 28 if kind == "er" else 4 + u1 * 12
         specs.append(gg.BatchSpec(kind, n, param, gg.draw(seed, 4 * i + 2)))
-    return [gg.make_from_spec(s) for s in specs]
+    with ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+        return list(ex.map(gg.make_from_spec, specs))
 
 
-def run_serve(args, rank, world):
-    """Poisson request stream into the continuous-batching server against the same requests colored
-    one by one with gc_color; results must be identical."""
+def served_object(args, rank, world, count):
+    """Poisson request stream (mean 2,000 req/s, seed 4) into the continuous-batching server, the
+    same requests submitted all at once (the server saturated), the same requests colored one by one
+    with gc_color (host CSR in, colors out, as the server takes them), and the same graphs as one
+    device-resident batch.  Deterministic results must be identical.  With several ranks each runs
+    its own server on every world-th request."""
     import torch
 
-    import paper_1509_08267_gb300 as gc
     import graphgen as gg
+    import paper_1509_08267_gb300 as gc
+    from paper_1509_08267_gb300 import autotune
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
     torch.cuda.set_device(local)
-    count = args.requests
-    # the replayed requests sit in pinned host memory, as a server's receive buffers would
+    pool = serve_pool(count)
+    idx = list(range(rank, count, world))
     graphs = []
-    for g in serve_pool(count):
-        rp = torch.from_numpy(g.rowptr).pin_memory().numpy()
-        ci = torch.from_numpy(g.colidx).pin_memory().numpy()
-        graphs.append(gg.Graph(g.n, rp, ci, g.name))
+    for i in idx:  # the replayed requests sit in pinned host memory, as a server's receive buffers would
+        g = pool[i]
+        graphs.append(gg.Graph(g.n, torch.from_numpy(g.rowptr).pin_memory().numpy(),
+                               torch.from_numpy(g.colidx).pin_memory().numpy(), g.name))
+    del pool
     rate = 2000.0
-    gaps = [-math_log(1.0 - ((gg.draw(4, 10_000_000 + i) >> 11) / 9007199254740992.0)) / rate for i in range(count)]
+    gaps = [-math_log(1.0 - ((gg.draw(4, 10_000_000 + i) >> 11) / 9007199254740992.0)) / rate for i in idx]
     pv = sum(g.n for g in graphs) + 1
     pe = sum(g.nnz for g in graphs) + 1
     pool_v = min(pv, 16_000_000)
     pool_e = min(pe, 600_000_000)
-    results = {}
-    with gc.Server(pool_vertices=pool_v, pool_entries=pool_e, mode=args.mode, seed=HASH_SEED, device=local) as srv:
+    m_mine = sum(g.nnz for g in graphs) / 2
+
+    def replay(srv, arrivals):
         t0 = time.perf_counter()
         ids = []
         at = 0.0
-        for g, gap in zip(graphs, gaps):
+        for g, gap in zip(graphs, arrivals):
             at += gap
             now = time.perf_counter() - t0
             if at > now:
                 time.sleep(at - now)
-            ids.append(srv.submit(g.rowptr, g.colidx))
-        for i, rid in enumerate(ids):
-            results[i] = srv.poll(rid)
-        t_serve = time.perf_counter() - t0
+            ids.append(srv.submit(g.rowptr, g.colidx, mode="det", seed=HASH_SEED))
+        res = [srv.poll(rid) for rid in ids]
+        return time.perf_counter() - t0, res
+
+    with gc.Server(pool_vertices=pool_v, pool_entries=pool_e, mode="det", seed=HASH_SEED, device=local) as srv:
+        replay(srv, [0.0] * min(3, len(graphs)))  # warm-up (allocations, module load)
+        t_serve, results = replay(srv, gaps)
         st = srv.stats()
-    # one by one, host arrays in and out as the server takes them
+    with gc.Server(pool_vertices=pool_v, pool_entries=pool_e, mode="det", seed=HASH_SEED, device=local) as srv:
+        t_sat, results_sat = replay(srv, [0.0] * len(graphs))
     t1 = time.perf_counter()
     same = True
     for i, g in enumerate(graphs):
-        r = gc.color(g.rowptr, g.colidx, args.mode, HASH_SEED)
-        if args.mode == "det":
-            same &= bool(np.array_equal(r.colors, results[i][0])) and r.ncolors == results[i][1] and \
-                r.rounds == results[i][2]
+        r = gc.color(g.rowptr, g.colidx, "det", HASH_SEED)
+        for res in (results[i], results_sat[i]):
+            same &= bool(np.array_equal(r.colors, res[0])) and r.ncolors == res[1] and r.rounds == res[2]
     t_solo = time.perf_counter() - t1
-    dev = torch.device("cuda", local)
-    # the same requests as one batch already on the device: what co-scheduling all of them at once
-    # gives, with no arrivals to wait for and no copies (an upper bound for the server)
+    # the same requests as one batch already on the device: co-scheduling all of them at once, with
+    # no arrivals to wait for and no copies (an upper bound for the server)
     b = gg.pack(graphs)
     bargs = [torch.from_numpy(a).to(dev) for a in (b.vtx_off, b.edge_off, b.rowptr, b.colidx)]
     bout = torch.empty(int(b.vtx_off[-1]), dtype=torch.int32, device=dev)
-    from paper_1509_08267_gb300 import autotune
     bopt = autotune.batch_options()
-    gc.color_batch(*bargs, args.mode, HASH_SEED, out=bout, options=bopt)
+    gc.color_batch(*bargs, "det", HASH_SEED, out=bout, options=bopt)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    gc.color_batch(*bargs, args.mode, HASH_SEED, out=bout, options=bopt)
+    gc.color_batch(*bargs, "det", HASH_SEED, out=bout, options=bopt)
     torch.cuda.synchronize()
     t_all = time.perf_counter() - t2
     del bargs, bout
     t_serve = reduce_max(t_serve, world, dev)
+    t_sat = reduce_max(t_sat, world, dev)
     t_solo = reduce_max(t_solo, world, dev)
     t_all = reduce_max(t_all, world, dev)
-    m_und = sum(g.nnz for g in graphs) / 2
+    window = sum(gaps)
+    m_job = m_mine * world  # shares are about equal; the slowest rank's time counts
+    return {
+        "requests": count, "arrival": "Poisson, mean 2,000 req/s, seed 4",
+        "graphs": "n log-uniform [1e3, 2e6]; ER / R-MAT / 2-D grid mix", "host_buffers": "pinned",
+        "value": m_job / t_serve / 1e9, "unit": "Gedges/s", "graphs_per_s": count / t_serve,
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "serve_wall_s": t_serve,
+        "arrival_window_s": window,
+        "offered_load_bound": {"value": m_job / max(window, 1e-9) / 1e9, "unit": "Gedges/s",
+                               "note": "edges / arrival window: no server can finish before its last request "
+                                       "arrives"},
+        "saturated": {"value": m_job / t_sat / 1e9, "unit": "Gedges/s", "seconds": t_sat,
+                      "note": "every request submitted at once: the server's own capacity"},
+        "one_by_one": {"value": m_job / t_solo / 1e9, "unit": "Gedges/s", "graphs_per_s": count / t_solo},
+        "served_over_one_by_one": t_solo / t_serve, "saturated_over_one_by_one": t_solo / t_sat,
+        "all_at_once": {"value": m_job / t_all / 1e9, "unit": "Gedges/s", "seconds": t_all,
+                        "note": "the same graphs as one device-resident gc_color_batch call"},
+        "saturated_over_all_at_once": t_all / t_sat,
+        "identical_colorings": same, "rounds_run": st["rounds_run"],
+        "pool_vertices": pool_v, "pool_entries": pool_e,
+    }
+
+
+def run_serve(args, rank, world):
+    """The serving workload alone (--workload serve): one JSON line."""
+    obj = served_object(args, rank, world, args.requests)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": whole_job_rate(m_und, t_serve, world) / 1e9, "unit": "Gedges/s",
-            "n_gpus": world, "steps": count,
-            "warmup": 0, "ms_per_step": t_serve * 1e3 / count, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": "serve", "requests": count, "arrival": "Poisson, mean 2,000 req/s, seed 4",
-                       "host_buffers": "pinned",
-                       "graphs": "n log-uniform [1e3, 2e6]; ER / R-MAT / 2-D grid mix",
-                       "pool_vertices": pool_v, "pool_entries": pool_e, "mode": args.mode},
-            "graphs_per_s": count / t_serve, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-            "one_by_one": {"value": m_und / t_solo / 1e9, "unit": "Gedges/s", "graphs_per_s": count / t_solo},
-            "served_over_one_by_one": t_solo / t_serve, "identical_colorings": same,
-            "all_at_once": {"value": m_und / t_all / 1e9, "unit": "Gedges/s", "seconds": t_all,
-                            "note": "the same graphs as one device-resident gc_color_batch call"},
-            "rounds_run": st["rounds_run"], "server_busy_s": st["busy_s"], "serve_wall_s": t_serve,
+            "metric": METRIC, "value": obj["value"], "unit": "Gedges/s", "n_gpus": world, "steps": args.requests,
+            "warmup": 0, "ms_per_step": obj["serve_wall_s"] * 1e3 / args.requests, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "serve", "requests": args.requests, "arrival": obj["arrival"],
+                       "graphs": obj["graphs"], "mode": "det"},
+            "served": obj,
         }
         print(json.dumps(line), flush=True)
 
@@ -404,6 +460,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--requests", type=int, default=200, help="serving workload: requests replayed")
+    ap.add_argument("--batch-graphs", type=int, default=256,
+                    help="graphs of the batched object of the default line (0: leave it out)")
+    ap.add_argument("--no-served", action="store_true", help="leave the served object out of the default line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -457,6 +516,10 @@ def main():
             return gc.recolor(rp_, ci_, cin, HASH_SEED + 1, out=out_, **kw)
         return gc.color(rp_, ci_, mode, HASH_SEED, out=out_, **kw)
 
+    # the clock sampler starts before the warm-up: nvidia-smi's start-up (NVML initialisation) stays
+    # out of the timed region
+    clocks = ClockSampler(local)
+    clocks.start()
     # warm-up (also records the per-round statistics once, outside the timed region)
     r0 = run(rp, ci, out, stats=True, options=gc.Options(priority=prio))
     for _ in range(args.warmup - 1):
@@ -466,11 +529,11 @@ def main():
     stream = torch.cuda.current_stream(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kernel_ms = []
-    clocks = ClockSampler(local)
+    clocks.wait_first_sample()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark()
     t_wall0 = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
@@ -494,6 +557,18 @@ def main():
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (kms / 1e3) / 1e9
 
+    traffic = recorded_traffic(args.workload, mode) if args.priority == "hash" else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "round phase: persistent round kernel, then (deterministic mode) the core phase's "
+                          "kernels; CUDA events around both",
+                "kernel_ms": kms, "alg_bytes": alg_bytes,
+                "alg_bytes_model": "SURVEY 8(d) full-row model: 4 deg(v) + 20 per worklist vertex per round + 4 "
+                                   "per appended vertex"}
+    if traffic is not None:
+        # the DRAM bytes the kernels actually moved (ncu) over the same time, against the same peak
+        roofline["frac_measured_traffic"] = traffic / (kms / 1e3) / 1e9 / peak
+
     # end to end through the C ABI with host buffers (pinned): H2D of the CSR, D2H of the colors
     e2e = None
     if args.e2e_steps > 0:
@@ -514,6 +589,17 @@ def main():
                "h2d_bytes_per_step": int(4 * (g.n + 1) + 4 * g.nnz + (4 * g.n if mode == "recolor" else 0)),
                "d2h_bytes_per_step": int(4 * g.n + 8),
                "ms_per_step": e_t * 1e3}
+
+    # the batched and served workloads of the same metric, bounded to a minute or two (default line)
+    default_line = args.workload == "rmat22" and mode == "det" and args.priority == "hash"
+    batched = served = None
+    if default_line and args.batch_graphs > 0:
+        del rp, ci, out
+        torch.cuda.empty_cache()
+        batched = batched_object(args, rank, world, args.batch_graphs)
+    if default_line and not args.no_served:
+        torch.cuda.empty_cache()
+        served = served_object(args, rank, world, args.requests)
 
     if rank == 0:
         import oracle
@@ -555,19 +641,18 @@ def main():
                                     "sl": "smallest last (batch peeling)"}[args.priority],
                        "l2": "flushed between steps (512 MB write) and colidx > L2", "parallelism":
                        "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "traffic": recorded_traffic(args.workload, mode) if args.priority == "hash" else None,
-                         "peak_kind": peak_kind,
-                         "kernel": "round kernel (persistent)", "kernel_ms": kms, "alg_bytes": alg_bytes},
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            # setup, degree sort (2), expand, round kernel, color count (2) per coloring; ordered mode
-            # and recoloring: setup, counting pass, round kernel, color count (2)
-            # (smallest last adds the peeling's two: its set-up and the peeling kernel)
-            "gpu_launches": ((5 if mode in ("ordered", "recolor") else 7) + (2 if args.priority == "sl" else 0))
-            * args.steps,
+            # setup, degree sort (2), expand, round kernel, color count (2) per coloring, plus the core
+            # phase's four (index, fill, core rounds, write-back) in deterministic mode; ordered mode
+            # and recoloring: setup, counting pass, round kernel, color count (2) (smallest last adds
+            # the peeling's two: its set-up and the peeling kernel)
+            "gpu_launches": ((5 if mode in ("ordered", "recolor") else 7) + (4 if mode == "det" else 0)
+                             + (2 if args.priority == "sl" else 0)) * args.steps,
             "clocks": clk,
+            **({"batched": batched} if batched is not None else {}),
+            **({"served": served} if served is not None else {}),
             "rounds": r0.rounds, "ncolors": r0.ncolors, "greedy_ncolors": greedy_colors,
             **({"ncolors_before_recolor": start.ncolors} if start is not None else {}),
             "max_degree": g.max_degree, "wall_s_timed": t_wall,

@@ -245,7 +245,8 @@ int gc_validate_graph(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
  * (code running inside an allocator or a memory-pool callback, or under a framework that owns every
  * device allocation and forbids side allocations).  It gives exactly gc_color's deterministic
  * result, but works in a fixed scratch array built into the library (about 5.8 MB of device memory,
- * held by every GPU that loads the library until the process exits), so it accepts at most
+ * held by every GPU that has loaded the library's device code, until the process exits), so it
+ * accepts at most
  * 16,384 vertices and 2^20 adjacency entries; larger graphs return GC_ERR_INVALID_ARG with the
  * outputs untouched.
  *   n, seed    as gc_color (mode is always GC_MODE_DETERMINISTIC)
@@ -254,9 +255,14 @@ int gc_validate_graph(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
  *   stream     cudaStream_t the work is queued on (NULL = the legacy default stream); the call
  *              returns after the stream has finished it
  * The first call on a device looks up the scratch array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  Every call reuses the
- * same array and clears what must start empty, so calls whose work overlaps on the GPU (from
- * several host threads or streams at once) race and must be serialised by the caller.
+ * with that device current; make that first call before any stream capture.  That first call may
+ * itself allocate: CUDA loads a library's device code lazily by default, so the first call on a
+ * device (or after cudaDeviceReset) is what loads this module, its scratch array and its kernels.
+ * Make one call (a warm-up on any small graph) before entering the code that must not allocate;
+ * later calls allocate nothing.  The call reads rowptr[n] on the host and returns only after the
+ * stream has finished its work.  Every call reuses the same array and clears what must start
+ * empty, so calls whose work overlaps on the GPU (from several host threads or streams at once)
+ * race and must be serialised by the caller.
  */
 int gc_color_noalloc(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed, int32_t *colors_out,
                      int32_t *ncolors, int32_t *rounds, void *stream);
@@ -273,46 +279,56 @@ int gc_release_scratch(void);
 /*
  * ---- Serving: continuous batching of independent coloring requests ----
  *
- * A server owns a device memory pool of `pool_vertices` vertex slots and `pool_entries` adjacency
+ * A server owns device memory pools of `pool_vertices` vertex slots and `pool_entries` adjacency
  * entries and a worker thread that runs rounds of the batched round kernel over every admitted
- * request.  gc_server_submit copies the request's CSR into pinned staging memory and queues it;
- * the worker admits queued requests between rounds whenever their footprint fits the free pool
- * space (first fit), so requests that arrive while others are on the GPU join the running batch at
- * the next round boundary.  A request's colors are identical to gc_color's for the same graph,
- * mode GC_MODE_DETERMINISTIC and seed.
+ * request.  gc_server_submit copies the request's CSR (into the pool right away when nothing waits
+ * ahead of it and it fits, else into host memory) and queues it; the worker admits queued requests
+ * between rounds whenever their footprint fits the free pool space (first fit), so requests that
+ * arrive while others are on the GPU join the running batch at the next round boundary.  Each
+ * request carries its own mode and seed: deterministic requests share one pool and launch, in-place
+ * requests another (the two modes keep different vertex state); inside a pool every graph has its
+ * own priority seed.  A deterministic request's colors are identical to gc_color's for the same
+ * graph and seed.  A device error reported by a launch (for example a grid-barrier wait that ran
+ * out) fails the requests resident in that pool with that status; the pool is reset and the server
+ * keeps serving.
  */
 typedef struct gc_server gc_server;
 
 typedef struct gc_server_config {
-    int64_t pool_vertices;   /* vertex capacity of the resident pool (> 0) */
-    int64_t pool_entries;    /* adjacency-entry capacity of the resident pool (> 0) */
-    int32_t max_requests;    /* maximum requests resident at once (slots); 0 = 4096 */
-    int32_t mode;            /* GC_MODE_DETERMINISTIC or GC_MODE_INPLACE */
-    uint64_t seed;           /* priority seed for every request */
+    int64_t pool_vertices;   /* vertex capacity of each resident pool (> 0) */
+    int64_t pool_entries;    /* adjacency-entry capacity of each resident pool (> 0) */
+    int32_t max_requests;    /* maximum requests resident at once per pool (slots); 0 = 4096 */
+    int32_t mode;            /* the pool allocated with the server: GC_MODE_DETERMINISTIC or GC_MODE_INPLACE
+                                (the other mode's pool is allocated by its first request) */
+    int64_t spin_limit_ns;   /* grid-barrier wait limit of the round launches; 0 = 1e9 */
     int32_t device;          /* CUDA device ordinal; -1 = current */
     int32_t reserved[7];
 } gc_server_config;
 
-typedef struct gc_server_stats {
+struct gc_server_stats {
     int64_t submitted, completed, rejected;
-    int64_t rounds_run;          /* batched rounds executed by the worker */
+    int64_t rounds_run;          /* batched rounds executed by the worker (both pools) */
     int64_t vertices_colored, edges_colored;  /* totals over completed requests (edges = nnz/2) */
     double p50_ms, p99_ms;       /* submit-to-done latency over completed requests */
     double busy_s;               /* wall time with at least one request resident */
     double wall_s;               /* time since the server was created */
     int32_t resident;            /* requests currently resident on the device */
     int32_t queued;              /* requests waiting for admission */
-    int32_t reserved[6];
-} gc_server_stats;
+    int64_t failed;              /* requests that ended with a device error (their pool was reset) */
+    int32_t reserved[4];
+};
 
-/* Creates the pool and the worker thread. Errors: INVALID_ARG, OOM, CUDA. */
+/* Creates the worker thread and the pool of cfg->mode. Errors: INVALID_ARG, OOM, CUDA. */
 int gc_server_create(const gc_server_config *cfg, gc_server **out);
 
 /* Queues one graph (host or device CSR as in gc_color; copied before return).  Non-blocking.
- * GC_ERR_OOM if the graph can never fit the pool; GC_ERR_INVALID_GRAPH for malformed row offsets.
+ *   mode   GC_MODE_DETERMINISTIC or GC_MODE_INPLACE (the request's own; see gc_color)
+ *   seed   the request's priority seed (see gc_color)
+ * GC_ERR_OOM if the graph can never fit a pool (or the mode's pool cannot be allocated);
+ * GC_ERR_INVALID_GRAPH for malformed row offsets; GC_ERR_INVALID_ARG for an unknown mode.
  * Neighbour ids and self-loops are checked on the device when the request is admitted; a request
  * that fails that check is dropped and its gc_server_poll returns GC_ERR_INVALID_GRAPH. */
-int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32_t *colidx,
+int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, uint64_t seed,
                      uint64_t *req_id);
 
 /* Waits up to timeout_ms (0 = do not wait, <0 = forever) for request req_id.  On completion copies
@@ -322,9 +338,11 @@ int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32
 int gc_server_poll(gc_server *s, uint64_t req_id, int32_t timeout_ms, int32_t *colors_out,
                    int32_t *ncolors, int32_t *rounds);
 
-int gc_server_stats_get(gc_server *s, gc_server_stats *out);
+/* Counters and latency percentiles so far (gc_server_stats_get is the same call). */
+int gc_server_stats(gc_server *s, struct gc_server_stats *out);
+int gc_server_stats_get(gc_server *s, struct gc_server_stats *out);
 
-/* Stops the worker (finishing resident requests), frees the pool. */
+/* Stops the worker (finishing resident requests), frees the pools. */
 void gc_server_destroy(gc_server *s);
 
 #ifdef __cplusplus

@@ -76,7 +76,7 @@ class _Stats(ctypes.Structure):
 
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("pool_vertices", ctypes.c_int64), ("pool_entries", ctypes.c_int64),
-                ("max_requests", ctypes.c_int32), ("mode", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("max_requests", ctypes.c_int32), ("mode", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64),
                 ("device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
@@ -85,7 +85,7 @@ class _ServerStats(ctypes.Structure):
                 ("rounds_run", ctypes.c_int64), ("vertices_colored", ctypes.c_int64),
                 ("edges_colored", ctypes.c_int64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("busy_s", ctypes.c_double), ("wall_s", ctypes.c_double), ("resident", ctypes.c_int32),
-                ("queued", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("queued", ctypes.c_int32), ("failed", ctypes.c_int64), ("reserved", ctypes.c_int32 * 4)]
 
 
 _lib = None
@@ -124,9 +124,11 @@ def load(path: str | None = None):
         lib.gc_server_create.restype = c_int
         lib.gc_server_create.argtypes = [P(_ServerConfig), P(p)]
         lib.gc_server_submit.restype = c_int
-        lib.gc_server_submit.argtypes = [p, i32, p, p, P(u64)]
+        lib.gc_server_submit.argtypes = [p, i32, p, p, c_int, u64, P(u64)]
         lib.gc_server_poll.restype = c_int
         lib.gc_server_poll.argtypes = [p, u64, i32, p, p, p]
+        lib.gc_server_stats.restype = c_int
+        lib.gc_server_stats.argtypes = [p, P(_ServerStats)]
         lib.gc_server_stats_get.restype = c_int
         lib.gc_server_stats_get.argtypes = [p, P(_ServerStats)]
         lib.gc_server_destroy.restype = None
@@ -372,29 +374,36 @@ def validate(rowptr, colidx, flags: int = VALIDATE_ALL) -> None:
 
 
 class Server:
-    """Continuous-batching coloring server (gc_server_*)."""
+    """Continuous-batching coloring server (gc_server_*).  `mode` and `seed` are the defaults of
+    submit(); the pool of `mode` is allocated with the server, the other mode's at its first
+    request."""
 
     def __init__(self, pool_vertices: int, pool_entries: int, max_requests: int = 0, mode="det", seed: int = 0,
-                 device: int = -1):
+                 device: int = -1, spin_limit_ns: int = 0):
         lib = load()
         cfg = _ServerConfig()
         cfg.pool_vertices = pool_vertices
         cfg.pool_entries = pool_entries
         cfg.max_requests = max_requests
         cfg.mode = _mode(mode)
-        cfg.seed = seed & ((1 << 64) - 1)
+        cfg.spin_limit_ns = spin_limit_ns
         cfg.device = device
         h = ctypes.c_void_p()
         _check(lib.gc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
         self._n = {}
+        self._mode = mode
+        self._seed = seed
 
-    def submit(self, rowptr, colidx) -> int:
+    def submit(self, rowptr, colidx, mode=None, seed: int | None = None) -> int:
+        """Queues one graph with its own mode and priority seed (the server's defaults if None)."""
         n = (rowptr.numel() if _is_torch(rowptr) else len(rowptr)) - 1
         prp, rk = _ptr(rowptr, np.int32)
         pci, ck = _ptr(colidx, np.int32)
         rid = ctypes.c_uint64(0)
-        _check(load().gc_server_submit(self._h, n, prp, pci, ctypes.byref(rid)))
+        m = _mode(self._mode if mode is None else mode)
+        sd = (self._seed if seed is None else seed) & ((1 << 64) - 1)
+        _check(load().gc_server_submit(self._h, n, prp, pci, m, sd, ctypes.byref(rid)))
         self._n[rid.value] = n
         return int(rid.value)
 
@@ -415,7 +424,7 @@ class Server:
 
     def stats(self) -> dict:
         s = _ServerStats()
-        _check(load().gc_server_stats_get(self._h, ctypes.byref(s)))
+        _check(load().gc_server_stats(self._h, ctypes.byref(s)))
         return {k: getattr(s, k) for k, _ in _ServerStats._fields_ if k != "reserved"}
 
     def close(self):

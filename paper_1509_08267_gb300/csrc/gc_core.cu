@@ -42,7 +42,10 @@ namespace {
 
 constexpr int kCoreThreads = 1024;  // one block per SM: every block holds all m colors
 constexpr int kCoreWarps = kCoreThreads / 32;
-constexpr int kCorePer = 8;  // entries per lane per step of a piece
+#ifndef GC_CORE_PER
+#define GC_CORE_PER 4
+#endif
+constexpr int kCorePer = GC_CORE_PER;  // entries per lane per step of a piece
 constexpr int kCoreStep = 32 * kCorePer;
 constexpr unsigned kPkFinal = 0x8000u;
 constexpr unsigned kPkSat = 0x7fffu;  // saturated: the color is 32767 or more (exact value in cex)
@@ -227,8 +230,8 @@ __global__ void __launch_bounds__(kFillThreads) core_fill_kernel(RoundParams P, 
                             atomicOr(&wfin[c >> 5], 1u << (c & 31));
                     } else if (static_cast<unsigned>(loc[q]) < m) {
                         keep = true;
-                        const bool smaller = key_less(prio_of(st[q]), pv, static_cast<uint32_t>(ul[q]),
-                                                      static_cast<uint32_t>(r.lv), P.seed);
+                        const bool smaller = key_less_in(prio_of(st[q]), pv, static_cast<uint32_t>(ul[q]),
+                                                         static_cast<uint32_t>(r.lv), P, V);
                         e = static_cast<uint32_t>(loc[q]) | (smaller ? kCoreSmaller : 0u);
                     } else {
                         // every vertex that is not final is on the worklist; anything else is a bug

@@ -47,6 +47,19 @@ __device__ __forceinline__ bool key_less(uint32_t pu, uint32_t pv, uint32_t lu, 
     return lu < lv;
 }
 
+// The priority seed of the graph of global vertex V (batches may give each graph its own).
+__device__ __forceinline__ uint64_t seed_of(const RoundParams &P, int32_t V) {
+    return P.g_seed ? __ldg(P.g_seed + __ldg(P.vg + V)) : P.seed;
+}
+
+// key_less for two vertices of the graph of global vertex V: the seed is looked up only when the
+// cached priority bits tie.
+__device__ __forceinline__ bool key_less_in(uint32_t pu, uint32_t pv, uint32_t lu, uint32_t lv, const RoundParams &P,
+                                            int32_t V) {
+    if (pu != pv) return pu < pv;
+    return key_less(pu, pv, lu, lv, seed_of(P, V));
+}
+
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -70,7 +83,7 @@ __device__ __forceinline__ void set_error(int32_t *err, int code, int32_t a, int
 // kPriorityRecolor: the same with P.prio_rank[V] in place of the degree (the peel level, larger
 // levels first; the given color, larger colors first).
 __device__ __forceinline__ uint32_t priority_bits(const RoundParams &P, uint32_t lv, int64_t deg, int32_t V) {
-    const uint64_t h = vertex_hash(P.seed, lv);
+    const uint64_t h = vertex_hash(seed_of(P, V), lv);
     if (P.priority == kPriorityRecolor || P.priority == GC_PRIORITY_SMALLEST_LAST) {
         const int32_t c = P.prio_rank[V];
         if (c < 0) set_error(P.err, GC_ERR_INVALID_ARG, V, c);

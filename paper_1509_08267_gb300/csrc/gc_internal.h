@@ -88,6 +88,7 @@ struct RoundParams {
     const int64_t *g_m;      // [G]
     int32_t *vg;             // [n] graph id per vertex (batch)
     uint64_t seed;
+    const uint64_t *g_seed;  // [G] per-graph priority seeds (the server); nullptr: `seed` for every graph
 
     // Vertex state words: low 32 bits = color (int32, -1 = uncolored), high 32 bits = the high half
     // of the vertex's priority hash, so one gather gives a neighbour's color and priority.

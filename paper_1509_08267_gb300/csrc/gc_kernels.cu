@@ -98,8 +98,8 @@ __device__ __forceinline__ void gather_step(const RoundParams &P, const Row &r, 
 // conflict flag (a neighbour with the same color and a smaller key).
 template <bool WINDOW, bool CONFLICT>
 __device__ __forceinline__ void consume_step(const uint64_t (&w)[kPer], const int32_t (&ul)[kPer], int32_t cv,
-                                             uint32_t pv, uint32_t lv, uint64_t seed, uint64_t &lo, unsigned *win,
-                                             bool &lose) {
+                                             uint32_t pv, uint32_t lv, const RoundParams &P, int32_t V, uint64_t &lo,
+                                             unsigned *win, bool &lose) {
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
         const int32_t c = color_of(w[q]);
@@ -110,7 +110,7 @@ __device__ __forceinline__ void consume_step(const uint64_t (&w)[kPer], const in
                 atomicOr(&win[c >> 5], 1u << (c & 31));
         }
         if constexpr (CONFLICT) {
-            if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]), lv, seed);
+            if (c == cv && !lose) lose = key_less_in(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]), lv, P, V);
         }
     }
 }
@@ -127,7 +127,7 @@ __device__ __forceinline__ void sweep(const RoundParams &P, const Row &r, const 
         gather_step(P, r, colc, j0, je, lane, ul, w);
         const bool more = j0 + kStep < je;
         if (more) load_step(P, j0 + kStep, je, lane, un);
-        consume_step<WINDOW, CONFLICT>(w, ul, cv, pv, static_cast<uint32_t>(r.lv), P.seed, lo, win, lose);
+        consume_step<WINDOW, CONFLICT>(w, ul, cv, pv, static_cast<uint32_t>(r.lv), P, r.vbase + r.lv, lo, win, lose);
         if (more) {
 #pragma unroll
             for (int q = 0; q < kPer; ++q) ul[q] = un[q];
@@ -185,8 +185,8 @@ __device__ __forceinline__ void sweep_small(const RoundParams &P, const Row &r, 
                     mask1 |= 1ull << (c - 64);
             }
             if constexpr (CONFLICT) {
-                if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
-                                                      static_cast<uint32_t>(r.lv), P.seed);
+                if (c == cv && !lose) lose = key_less_in(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
+                                                         static_cast<uint32_t>(r.lv), P, r.vbase + r.lv);
             }
         }
         if (more) {
@@ -328,8 +328,8 @@ __device__ __forceinline__ void sweep_item(const RoundParams &P, const Row &r, c
                     atomicOr(&wfin[c >> 5], 1u << (c & 31));
             }
             if constexpr (CONFLICT) {
-                if (c == cv && !lose) lose = key_less(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
-                                                      static_cast<uint32_t>(r.lv), P.seed);
+                if (c == cv && !lose) lose = key_less_in(prio_of(w[q]), pv, static_cast<uint32_t>(ul[q]),
+                                                         static_cast<uint32_t>(r.lv), P, r.vbase + r.lv);
             }
             if constexpr (DROP) {
                 if (j0 + lane + 32 * q < le && !fin) keepm |= 1u << q;

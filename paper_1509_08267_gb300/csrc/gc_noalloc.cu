@@ -54,7 +54,8 @@ constexpr size_t kBitmapWords = kNaMaxVertices / 32 + 2;
 constexpr size_t kScratchBytes = align256(kOffBitmap + 4 * kBitmapWords);  // about 5.8 MB
 
 // The scratch itself.  Host code must not use the name as an address: it looks up the device
-// address with cudaGetSymbolAddress (once per device) and hands that to the kernels.
+// address with cudaGetSymbolAddress (once per device, again if that context went away) and hands
+// that to the kernels.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_na_mu;
@@ -64,10 +65,23 @@ int na_fail(int code, const char *what, cudaError_t e) {
     return set_last_error(code, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Still a device address of the current context?  (After cudaDeviceReset, or under another
+// context, a cached address is stale.)  cudaPointerGetAttributes allocates nothing.
+bool still_mapped(void *p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 // Device address of the scratch on the current device.  The first call on a device looks it up
-// with that device current; later calls reuse it.
+// with that device current; later calls reuse it after checking that it still belongs to the
+// current context, and look it up again if not.
 int scratch_base(int dev, unsigned char **out) {
     std::lock_guard<std::mutex> lk(g_na_mu);
+    if (g_na_base[dev] && !still_mapped(g_na_base[dev], dev)) g_na_base[dev] = nullptr;
     if (!g_na_base[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -200,6 +214,8 @@ extern "C" int gc_color_noalloc(int32_t n, const int32_t *rowptr, const int32_t 
             return set_last_error(GC_ERR_INVALID_GRAPH, "invalid adjacency entry at vertex %d", h.err[1]);
         case GC_ERR_TIMEOUT:
             return set_last_error(GC_ERR_TIMEOUT, "grid barrier wait exceeded its limit");
+        case GC_ERR_NO_CONVERGENCE:
+            return set_last_error(GC_ERR_NO_CONVERGENCE, "worklist not empty after %d rounds", h.err[1] - 1);
         default:
             return set_last_error(h.err[0], "device error %d", h.err[0]);
     }

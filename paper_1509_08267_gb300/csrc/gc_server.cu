@@ -85,10 +85,15 @@ class RangeAlloc {
 
 enum ReqState { kQueued, kResident, kDone };
 
+struct Engine;
+
 struct Request {
     uint64_t id = 0;
     int32_t n = 0;
     int64_t m = 0;
+    int32_t mode = GC_MODE_DETERMINISTIC;
+    uint64_t seed = 0;
+    Engine *eng = nullptr;
     int64_t n_large = 0, n_chunks = 0;
     std::vector<int32_t> rowptr, colidx, colors;
     ReqState state = kQueued;
@@ -102,8 +107,10 @@ struct Request {
 
 struct DevBuf {
     void *p = nullptr;
-    ~DevBuf() {
+    ~DevBuf() { release(); }
+    void release() {
         if (p) cudaFree(p);
+        p = nullptr;
     }
     cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16); }
     template <class T>
@@ -122,6 +129,30 @@ struct Ctl {
     GridBar bar;
 };
 
+// One mode's resident pool: CSR storage, vertex state, worklists and the graph table of the
+// batched round kernel, with first-fit allocators for vertex, entry and row-offset ranges and a
+// work-item budget.
+struct Engine {
+    int mode = -1;  // -1: not allocated yet
+    bool compact = false;  // deterministic mode: the compact sweep (slot and list space per pool vertex / entry)
+    int grid = 0;
+    int64_t PV = 0, PE = 0, PI = 0, PC = 0;  // capacities: vertices, entries, large vertices, work items
+    int32_t S = 0;                           // slots
+    DevBuf rowptr, colidx, col0, col1, outbuf, small0, small1, items, chunk0, chunk1, acc, lists, vg, ctl, bitmap;
+    DevBuf g_vbase, g_n, g_ebase, g_rbase, g_m, glast, gmax, gcount, verr, gseed;
+    std::vector<int64_t> h_vbase, h_ebase, h_rbase, h_m;
+    std::vector<int32_t> h_n, h_glast;
+    std::vector<uint64_t> h_seed;
+    RangeAlloc va, ea, ra;
+    int64_t used_items = 0, used_chunks = 0;
+    std::vector<int32_t> free_slots;
+    std::vector<Request *> resident;
+    std::deque<Request *> queue;
+    std::vector<Request *> staged;  // pool space reserved and CSR copied at submit
+    int32_t next_pass = 1;
+    bool busy() const { return mode >= 0 && (!queue.empty() || !resident.empty() || !staged.empty()); }
+};
+
 }  // namespace
 }  // namespace gc
 
@@ -129,31 +160,18 @@ struct gc_server {
     gc_server_config cfg{};
     int device = 0;
     cudaStream_t stream = nullptr;
-    int grid = 0;
-    int64_t PV = 0, PE = 0, PI = 0, PC = 0;  // pool capacities: vertices, entries, large vertices, work items
-    int32_t S = 0;                           // slots
-    bool compact = false;  // deterministic mode: the compact sweep (slot and list space per pool vertex / entry)
-    gc::DevBuf rowptr, colidx, col0, col1, outbuf, small0, small1, items, chunk0, chunk1, acc, lists, vg, ctl, bitmap;
-    gc::DevBuf g_vbase, g_n, g_ebase, g_rbase, g_m, glast, gmax, gcount, verr;
-    std::vector<int64_t> h_vbase, h_ebase, h_rbase, h_m;
-    std::vector<int32_t> h_n, h_glast;
-    gc::RangeAlloc va, ea, ra;
-    int64_t used_items = 0, used_chunks = 0;
-    std::vector<int32_t> free_slots;
-    std::vector<gc::Request *> resident;
-    std::deque<gc::Request *> queue;
-    std::vector<gc::Request *> staged;  // pool space reserved and CSR copied at submit
-    std::mutex copy_mu;
     cudaStream_t copy_stream = nullptr;
+    std::mutex copy_mu;
+    std::mutex create_mu;  // engine allocation
+    gc::Engine eng[2];     // [0] deterministic, [1] in-place
     std::unordered_map<uint64_t, std::unique_ptr<gc::Request>> reqs;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::thread worker;
     bool stop = false;
     uint64_t next_id = 1;
-    int32_t next_pass = 1;
     // statistics
-    int64_t submitted = 0, completed = 0, rejected = 0, rounds_run = 0, v_done = 0, e_done = 0;
+    int64_t submitted = 0, completed = 0, rejected = 0, failed = 0, rounds_run = 0, v_done = 0, e_done = 0;
     std::vector<double> latencies;
     double t_create = 0, busy = 0;
     int fatal = GC_OK;
@@ -175,44 +193,108 @@ int srv_fail(gc_server *s, int code, const char *what, cudaError_t e) {
         if (e_ != cudaSuccess) return srv_fail(s, GC_ERR_CUDA, #call, e_); \
     } while (0)
 
-RoundParams params(gc_server *s, int32_t rounds = kRoundsWhileQueued) {
+int engine_index(int mode) { return mode == GC_MODE_INPLACE ? 1 : 0; }
+
+// Allocates the pool of `mode` with the server's capacities (E.mode is left to the caller, which
+// publishes the pool by setting it under the server lock).
+int engine_create(gc_server *s, Engine &E, int mode) {
+    const gc_server_config &cfg = s->cfg;
+    E.S = cfg.max_requests > 0 ? cfg.max_requests : 4096;
+    E.PV = cfg.pool_vertices;
+    E.PE = cfg.pool_entries;
+    E.PI = std::min<int64_t>(E.PV, E.PE / (kT1 + 1) + 1);
+    E.PC = E.PE / kCH + E.PI + 1;
+    // deterministic mode sweeps compact lists: a slot per pool vertex and two list regions per entry
+    E.compact = mode == GC_MODE_DETERMINISTIC;
+    const size_t slots = E.compact ? static_cast<size_t>(E.PV) : static_cast<size_t>(E.PI);
+    const size_t V = static_cast<size_t>(E.PV), Sz = static_cast<size_t>(E.S);
+    struct {
+        DevBuf *b;
+        size_t bytes;
+    } plan[] = {
+        {&E.rowptr, 4 * (V + Sz)}, {&E.colidx, 4 * static_cast<size_t>(E.PE)}, {&E.col0, 8 * V}, {&E.col1, 8 * V},
+        {&E.outbuf, 4 * V}, {&E.small0, 4 * V}, {&E.small1, 4 * V}, {&E.items, 4 * V}, {&E.vg, 4 * V},
+        {&E.chunk0, kItemBytes * static_cast<size_t>(E.PC)}, {&E.chunk1, kItemBytes * static_cast<size_t>(E.PC)},
+        {&E.acc, 4 * kAccStride * slots}, {&E.lists, E.compact ? 8 * static_cast<size_t>(E.PE) : 0},
+        {&E.ctl, sizeof(Ctl)}, {&E.bitmap, 4 * (V / 32 + 4)}, {&E.g_vbase, 8 * Sz}, {&E.g_n, 4 * Sz},
+        {&E.g_ebase, 8 * Sz}, {&E.g_rbase, 8 * Sz}, {&E.g_m, 8 * Sz}, {&E.glast, 4 * Sz}, {&E.gmax, 4 * Sz},
+        {&E.gcount, 4 * Sz}, {&E.verr, 16 * Sz}, {&E.gseed, 8 * Sz},
+    };
+    cudaError_t e = cudaSuccess;
+    for (auto &a : plan) {
+        if (e != cudaSuccess) break;
+        e = a.b->alloc(a.bytes);
+    }
+    if (e == cudaSuccess) e = cudaMemset(E.ctl.p, 0, sizeof(Ctl));
+    if (e == cudaSuccess) e = cudaMemset(E.acc.p, 0, 4 * kAccStride * slots);
+    if (e == cudaSuccess) e = cudaMemset(E.g_n.p, 0, 4 * Sz);
+    if (e == cudaSuccess) e = cudaMemset(E.glast.p, 0, 4 * Sz);
+    if (e == cudaSuccess) e = cudaMemset(E.gseed.p, 0, 8 * Sz);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (auto &a : plan) a.b->release();
+        return set_last_error(e == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA, "server pool: %s",
+                              cudaGetErrorString(e));
+    }
+    int per_sm = 0, sms = 0;
+    round_kernel_occupancy(mode, true, E.compact, 256, &per_sm);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    E.grid = std::max(1, per_sm * sms);
+    E.h_vbase.assign(Sz, 0);
+    E.h_ebase.assign(Sz, 0);
+    E.h_rbase.assign(Sz, 0);
+    E.h_m.assign(Sz, 0);
+    E.h_n.assign(Sz, 0);
+    E.h_glast.assign(Sz, 0);
+    E.h_seed.assign(Sz, 0);
+    E.va.reset(E.PV);
+    E.ea.reset(E.PE);
+    E.ra.reset(E.PV + E.S);
+    E.free_slots.clear();
+    for (int32_t g = E.S - 1; g >= 0; --g) E.free_slots.push_back(g);
+    E.next_pass = 1;
+    return GC_OK;
+}
+
+RoundParams params(gc_server *s, Engine &E, int32_t rounds = kRoundsWhileQueued) {
     RoundParams P{};
-    P.n = static_cast<int32_t>(s->PV);
-    P.G = s->S;
-    P.rowptr = s->rowptr.as<int32_t>();
-    P.colidx = s->colidx.as<int32_t>();
-    P.g_vbase = s->g_vbase.as<int64_t>();
-    P.g_n = s->g_n.as<int32_t>();
-    P.g_ebase = s->g_ebase.as<int64_t>();
-    P.g_rbase = s->g_rbase.as<int64_t>();
-    P.g_m = s->g_m.as<int64_t>();
-    P.vg = s->vg.as<int32_t>();
-    P.seed = s->cfg.seed;
-    P.col0 = s->col0.as<uint64_t>();
-    P.col1 = s->col1.as<uint64_t>();
-    P.small0 = s->small0.as<int32_t>();
-    P.small1 = s->small1.as<int32_t>();
-    P.chunk0 = s->chunk0.as<int4>();
-    P.chunk1 = s->chunk1.as<int4>();
-    P.items = s->items.as<int32_t>();
-    if (s->compact) {
-        P.lists = s->lists.as<int32_t>();
+    P.n = static_cast<int32_t>(E.PV);
+    P.G = E.S;
+    P.rowptr = E.rowptr.as<int32_t>();
+    P.colidx = E.colidx.as<int32_t>();
+    P.g_vbase = E.g_vbase.as<int64_t>();
+    P.g_n = E.g_n.as<int32_t>();
+    P.g_ebase = E.g_ebase.as<int64_t>();
+    P.g_rbase = E.g_rbase.as<int64_t>();
+    P.g_m = E.g_m.as<int64_t>();
+    P.vg = E.vg.as<int32_t>();
+    P.seed = 0;
+    P.g_seed = E.gseed.as<uint64_t>();  // every request has its own seed
+    P.col0 = E.col0.as<uint64_t>();
+    P.col1 = E.col1.as<uint64_t>();
+    P.small0 = E.small0.as<int32_t>();
+    P.small1 = E.small1.as<int32_t>();
+    P.chunk0 = E.chunk0.as<int4>();
+    P.chunk1 = E.chunk1.as<int4>();
+    P.items = E.items.as<int32_t>();
+    if (E.compact) {
+        P.lists = E.lists.as<int32_t>();
         P.slot_per_vertex = 1;
     }
-    Ctl *c = s->ctl.as<Ctl>();
+    Ctl *c = E.ctl.as<Ctl>();
     P.tmp = c->tmp;
     P.cnt = c->cnt;
-    P.acc = s->acc.as<unsigned>();
+    P.acc = E.acc.as<unsigned>();
     P.bar = &c->bar;
     P.err = c->err;
     P.passes = c->passes;
-    P.graph_last = s->glast.as<int32_t>();
+    P.graph_last = E.glast.as<int32_t>();
     P.stats = nullptr;
     P.stats_cap = 0;
-    P.pass_begin = s->next_pass;
-    P.pass_end = s->next_pass + rounds;
+    P.pass_begin = E.next_pass;
+    P.pass_end = E.next_pass + rounds;
     P.cap_is_error = 0;
-    P.spin_ns = 1000000000LL;
+    P.spin_ns = s->cfg.spin_limit_ns > 0 ? s->cfg.spin_limit_ns : 1000000000LL;
     P.T1 = kT1;
     P.CH = kCH;
     return P;
@@ -221,59 +303,59 @@ RoundParams params(gc_server *s, int32_t rounds = kRoundsWhileQueued) {
 // Reserve pool space for r; false (nothing reserved) if it does not fit now.  Vertices, entries and
 // row offsets need contiguous ranges; work-item capacity is a plain budget (slots and work items
 // of a round are numbered afresh every round).
-bool reserve(gc_server *s, Request *r) {
-    if (s->free_slots.empty()) return false;
-    if (s->used_items + r->n_large > s->PI || s->used_chunks + r->n_chunks > s->PC) return false;
+bool reserve(Engine &E, Request *r) {
+    if (E.free_slots.empty()) return false;
+    if (E.used_items + r->n_large > E.PI || E.used_chunks + r->n_chunks > E.PC) return false;
     int64_t vb, eb, rb;
-    if (!s->va.alloc(r->n, &vb)) return false;
-    if (!s->ea.alloc(r->m, &eb)) {
-        s->va.release(vb, r->n);
+    if (!E.va.alloc(r->n, &vb)) return false;
+    if (!E.ea.alloc(r->m, &eb)) {
+        E.va.release(vb, r->n);
         return false;
     }
-    if (!s->ra.alloc(r->n + 1, &rb)) {
-        s->va.release(vb, r->n);
-        s->ea.release(eb, r->m);
+    if (!E.ra.alloc(r->n + 1, &rb)) {
+        E.va.release(vb, r->n);
+        E.ea.release(eb, r->m);
         return false;
     }
     r->vbase = vb;
     r->ebase = eb;
     r->rbase = rb;
-    s->used_items += r->n_large;
-    s->used_chunks += r->n_chunks;
-    r->slot = s->free_slots.back();
-    s->free_slots.pop_back();
+    E.used_items += r->n_large;
+    E.used_chunks += r->n_chunks;
+    r->slot = E.free_slots.back();
+    E.free_slots.pop_back();
     return true;
 }
 
-void unreserve(gc_server *s, Request *r) {
-    s->va.release(r->vbase, r->n);
-    s->ea.release(r->ebase, r->m);
-    s->ra.release(r->rbase, r->n + 1);
-    s->used_items -= r->n_large;
-    s->used_chunks -= r->n_chunks;
-    s->free_slots.push_back(r->slot);
+void unreserve(Engine &E, Request *r) {
+    E.va.release(r->vbase, r->n);
+    E.ea.release(r->ebase, r->m);
+    E.ra.release(r->rbase, r->n + 1);
+    E.used_items -= r->n_large;
+    E.used_chunks -= r->n_chunks;
+    E.free_slots.push_back(r->slot);
     r->slot = -1;
 }
 
 // Copies admitted requests into the pool, checks their graph format on the device (each request
 // has its own error slot, so a malformed request cannot disturb the batch) and appends the valid
 // ones to the worklist of round next_pass.  Malformed requests are returned in `bad`.
-int admit(gc_server *s, const std::vector<Request *> &adm, std::vector<Request *> &bad) {
+int admit(gc_server *s, Engine &E, const std::vector<Request *> &adm, std::vector<Request *> &bad) {
     if (adm.empty()) return GC_OK;
     cudaStream_t st = s->stream;
-    int32_t *verr = s->verr.as<int32_t>();
+    int32_t *verr = E.verr.as<int32_t>();
     for (Request *r : adm) {
         const int g = r->slot;
         if (!r->staged) {
-            SRV_CUDA(cudaMemcpyAsync(s->rowptr.as<int32_t>() + r->rbase, r->rowptr.data(), 4 * (r->n + 1),
+            SRV_CUDA(cudaMemcpyAsync(E.rowptr.as<int32_t>() + r->rbase, r->rowptr.data(), 4 * (r->n + 1),
                                      cudaMemcpyHostToDevice, st));
             if (r->m)
-                SRV_CUDA(cudaMemcpyAsync(s->colidx.as<int32_t>() + r->ebase, r->colidx.data(), 4 * r->m,
+                SRV_CUDA(cudaMemcpyAsync(E.colidx.as<int32_t>() + r->ebase, r->colidx.data(), 4 * r->m,
                                          cudaMemcpyHostToDevice, st));
         }
         SRV_CUDA(cudaMemsetAsync(verr + 4 * g, 0, 16, st));
-        SRV_CUDA(launch_validate(r->n, s->rowptr.as<int32_t>() + r->rbase,
-                                 r->m ? s->colidx.as<int32_t>() + r->ebase : s->rowptr.as<int32_t>() + r->rbase, 0,
+        SRV_CUDA(launch_validate(r->n, E.rowptr.as<int32_t>() + r->rbase,
+                                 r->m ? E.colidx.as<int32_t>() + r->ebase : E.rowptr.as<int32_t>() + r->rbase, 0,
                                  verr + 4 * g, st));
     }
     std::vector<int32_t> herr(adm.size());
@@ -291,52 +373,54 @@ int admit(gc_server *s, const std::vector<Request *> &adm, std::vector<Request *
         }
         ok.push_back(r);
         const int g = r->slot;
-        s->h_vbase[g] = r->vbase;
-        s->h_n[g] = r->n;
-        s->h_ebase[g] = r->ebase;
-        s->h_rbase[g] = r->rbase;
-        s->h_m[g] = r->m;
-        s->h_glast[g] = s->next_pass - 1;  // raised to next_pass by setup if any vertex has a neighbour
-        SRV_CUDA(cudaMemcpyAsync(s->g_vbase.as<int64_t>() + g, &s->h_vbase[g], 8, cudaMemcpyHostToDevice, st));
-        SRV_CUDA(cudaMemcpyAsync(s->g_n.as<int32_t>() + g, &s->h_n[g], 4, cudaMemcpyHostToDevice, st));
-        SRV_CUDA(cudaMemcpyAsync(s->g_ebase.as<int64_t>() + g, &s->h_ebase[g], 8, cudaMemcpyHostToDevice, st));
-        SRV_CUDA(cudaMemcpyAsync(s->g_rbase.as<int64_t>() + g, &s->h_rbase[g], 8, cudaMemcpyHostToDevice, st));
-        SRV_CUDA(cudaMemcpyAsync(s->g_m.as<int64_t>() + g, &s->h_m[g], 8, cudaMemcpyHostToDevice, st));
-        SRV_CUDA(cudaMemcpyAsync(s->glast.as<int32_t>() + g, &s->h_glast[g], 4, cudaMemcpyHostToDevice, st));
-        r->join = s->next_pass;
+        E.h_vbase[g] = r->vbase;
+        E.h_n[g] = r->n;
+        E.h_ebase[g] = r->ebase;
+        E.h_rbase[g] = r->rbase;
+        E.h_m[g] = r->m;
+        E.h_seed[g] = r->seed;
+        E.h_glast[g] = E.next_pass - 1;  // raised to next_pass by setup if any vertex has a neighbour
+        SRV_CUDA(cudaMemcpyAsync(E.g_vbase.as<int64_t>() + g, &E.h_vbase[g], 8, cudaMemcpyHostToDevice, st));
+        SRV_CUDA(cudaMemcpyAsync(E.g_n.as<int32_t>() + g, &E.h_n[g], 4, cudaMemcpyHostToDevice, st));
+        SRV_CUDA(cudaMemcpyAsync(E.g_ebase.as<int64_t>() + g, &E.h_ebase[g], 8, cudaMemcpyHostToDevice, st));
+        SRV_CUDA(cudaMemcpyAsync(E.g_rbase.as<int64_t>() + g, &E.h_rbase[g], 8, cudaMemcpyHostToDevice, st));
+        SRV_CUDA(cudaMemcpyAsync(E.g_m.as<int64_t>() + g, &E.h_m[g], 8, cudaMemcpyHostToDevice, st));
+        SRV_CUDA(cudaMemcpyAsync(E.gseed.as<uint64_t>() + g, &E.h_seed[g], 8, cudaMemcpyHostToDevice, st));
+        SRV_CUDA(cudaMemcpyAsync(E.glast.as<int32_t>() + g, &E.h_glast[g], 4, cudaMemcpyHostToDevice, st));
+        r->join = E.next_pass;
     }
     if (ok.empty()) return GC_OK;
-    RoundParams P = params(s);
+    RoundParams P = params(s, E);
     SRV_CUDA(cudaMemsetAsync(P.tmp, 0, 2 * sizeof(unsigned), st));
     for (Request *r : ok)
-        SRV_CUDA(launch_setup(P, s->cfg.mode, true, static_cast<int32_t>(r->vbase),
-                              static_cast<int32_t>(r->vbase + r->n), r->slot, st));
-    SRV_CUDA(launch_expand(P, s->cfg.mode, true, s->compact, -1, st));
+        SRV_CUDA(launch_setup(P, E.mode, true, static_cast<int32_t>(r->vbase), static_cast<int32_t>(r->vbase + r->n),
+                              r->slot, st));
+    SRV_CUDA(launch_expand(P, E.mode, true, E.compact, -1, st));
     return GC_OK;
 }
 
 // Colors, color count and rounds of finished requests; frees their pool space.
-int retire(gc_server *s, const std::vector<Request *> &fin) {
+int retire(gc_server *s, Engine &E, const std::vector<Request *> &fin) {
     if (fin.empty()) return GC_OK;
     cudaStream_t st = s->stream;
-    RoundParams P = params(s);
+    RoundParams P = params(s, E);
     std::vector<int32_t> sel(fin.size());
     for (size_t i = 0; i < fin.size(); ++i) {
         Request *r = fin[i];
         const int g = r->slot;
         // bits [vbase, vbase + n) of the bitmap hold this request's colors
         const int64_t w0 = r->vbase >> 5, w1 = (r->vbase + r->n + 31) >> 5;
-        SRV_CUDA(cudaMemsetAsync(s->bitmap.as<unsigned>() + w0, 0, 4 * (w1 - w0 + 1), st));
-        SRV_CUDA(cudaMemsetAsync(s->gmax.as<int32_t>() + g, 0xff, 4, st));
-        SRV_CUDA(launch_count_colors(P, true, s->cfg.mode == GC_MODE_DETERMINISTIC ? s->glast.as<int32_t>() + g : nullptr,
+        SRV_CUDA(cudaMemsetAsync(E.bitmap.as<unsigned>() + w0, 0, 4 * (w1 - w0 + 1), st));
+        SRV_CUDA(cudaMemsetAsync(E.gmax.as<int32_t>() + g, 0xff, 4, st));
+        SRV_CUDA(launch_count_colors(P, true, E.mode == GC_MODE_DETERMINISTIC ? E.glast.as<int32_t>() + g : nullptr,
                                      static_cast<int32_t>(r->vbase), static_cast<int32_t>(r->vbase + r->n), g, g + 1,
-                                     s->bitmap.as<unsigned>(), s->gmax.as<int32_t>(), s->gcount.as<int32_t>(),
-                                     s->outbuf.as<int32_t>() + r->vbase, st));
+                                     E.bitmap.as<unsigned>(), E.gmax.as<int32_t>(), E.gcount.as<int32_t>(),
+                                     E.outbuf.as<int32_t>() + r->vbase, st));
         r->colors.resize(r->n);
         if (r->n)
-            SRV_CUDA(cudaMemcpyAsync(r->colors.data(), s->outbuf.as<int32_t>() + r->vbase, 4 * r->n,
+            SRV_CUDA(cudaMemcpyAsync(r->colors.data(), E.outbuf.as<int32_t>() + r->vbase, 4 * r->n,
                                      cudaMemcpyDeviceToHost, st));
-        SRV_CUDA(cudaMemcpyAsync(&sel[i], s->gcount.as<int32_t>() + g, 4, cudaMemcpyDeviceToHost, st));
+        SRV_CUDA(cudaMemcpyAsync(&sel[i], E.gcount.as<int32_t>() + g, 4, cudaMemcpyDeviceToHost, st));
     }
     SRV_CUDA(cudaStreamSynchronize(st));
     const double t = now_s();
@@ -344,7 +428,7 @@ int retire(gc_server *s, const std::vector<Request *> &fin) {
     for (size_t i = 0; i < fin.size(); ++i) {
         Request *r = fin[i];
         r->ncolors = r->n ? sel[i] : 0;
-        const int32_t last = s->h_glast[r->slot];
+        const int32_t last = E.h_glast[r->slot];
         r->rounds = r->n ? std::max(1, last - r->join + 1) : 0;
         r->state = kDone;
         r->t_done = t;
@@ -352,9 +436,32 @@ int retire(gc_server *s, const std::vector<Request *> &fin) {
         s->v_done += r->n;
         s->e_done += r->m / 2;
         s->latencies.push_back((r->t_done - r->t_submit) * 1e3);
-        unreserve(s, r);
+        unreserve(E, r);
     }
     s->cv_done.notify_all();
+    return GC_OK;
+}
+
+// A launch posted an error (a grid-barrier wait ran out, a malformed entry): the requests resident
+// in this pool end with that status, the pool's control block and round count start over, and the
+// queued requests stay queued.
+int engine_reset(gc_server *s, Engine &E, int code) {
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        const double t = now_s();
+        for (Request *r : E.resident) {
+            r->state = kDone;
+            r->status = code;
+            r->t_done = t;
+            s->failed += 1;
+            unreserve(E, r);
+        }
+        E.resident.clear();
+        s->cv_done.notify_all();
+    }
+    SRV_CUDA(cudaMemsetAsync(E.ctl.p, 0, sizeof(Ctl), s->stream));
+    SRV_CUDA(cudaStreamSynchronize(s->stream));
+    E.next_pass = 1;
     return GC_OK;
 }
 
@@ -362,106 +469,116 @@ void fail_all(gc_server *s, int code, const std::string &msg) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->fatal = code;
     s->fatal_msg = msg;
-    for (Request *r : s->resident) {
-        r->state = kDone;
-        r->status = code;
+    for (Engine &E : s->eng) {
+        for (auto *list : {&E.resident, &E.staged}) {
+            for (Request *r : *list) {
+                r->state = kDone;
+                r->status = code;
+            }
+            list->clear();
+        }
+        for (Request *r : E.queue) {
+            r->state = kDone;
+            r->status = code;
+        }
+        E.queue.clear();
     }
-    s->resident.clear();
-    for (Request *r : s->queue) {
-        r->state = kDone;
-        r->status = code;
-    }
-    s->queue.clear();
-    for (Request *r : s->staged) {
-        r->state = kDone;
-        r->status = code;
-    }
-    s->staged.clear();
     s->cv_done.notify_all();
+}
+
+// One pass of the worker over a pool: admission, a launch of a few rounds, retirement.  Returns
+// false after an error the server cannot recover from (a failed CUDA call).
+bool engine_step(gc_server *s, Engine &E, std::vector<Request *> &adm, bool queued) {
+    const double t0 = now_s();
+    std::vector<Request *> bad;
+    if (admit(s, E, adm, bad) != GC_OK) return false;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (Request *r : bad) {
+            E.resident.erase(std::find(E.resident.begin(), E.resident.end(), r));
+            unreserve(E, r);
+            r->status = GC_ERR_INVALID_GRAPH;
+            r->state = kDone;
+            s->rejected += 1;
+        }
+        if (!bad.empty()) s->cv_done.notify_all();
+        if (E.resident.empty()) return true;
+    }
+    RoundParams P = params(s, E, queued ? kRoundsWhileQueued : kRoundsIdleQueue);
+    cudaError_t e = launch_rounds(P, E.mode, true, E.compact, E.grid, 256, s->stream);
+    Ctl h{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, E.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E.h_glast.data(), E.glast.p, 4 * E.S, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        srv_fail(s, GC_ERR_CUDA, "server round launch", e);
+        return false;
+    }
+    if (h.err[0] != 0) {
+        // the launch reported an error: fail what is resident in this pool, keep serving
+        if (engine_reset(s, E, h.err[0]) != GC_OK) return false;
+        s->busy += now_s() - t0;
+        return true;
+    }
+    const int32_t ran = h.passes[0] - E.next_pass;
+    E.next_pass = h.passes[0];
+    std::vector<Request *> fin;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->rounds_run += ran;
+        for (auto it = E.resident.begin(); it != E.resident.end();) {
+            if (E.h_glast[(*it)->slot] < E.next_pass) {
+                fin.push_back(*it);
+                it = E.resident.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
+    if (retire(s, E, fin) != GC_OK) return false;
+    s->busy += now_s() - t0;
+    return true;
 }
 
 void worker_main(gc_server *s) {
     cudaSetDevice(s->device);
     while (true) {
-        std::vector<Request *> adm;
+        std::vector<Request *> adm[2];
+        bool active[2] = {false, false}, queued[2] = {false, false};
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] {
-                return s->stop || !s->queue.empty() || !s->resident.empty() || !s->staged.empty();
-            });
-            if (s->stop && s->queue.empty() && s->resident.empty() && s->staged.empty()) break;
-            for (Request *r : s->staged) {
-                r->state = kResident;
-                adm.push_back(r);
-                s->resident.push_back(r);
-            }
-            s->staged.clear();
-            for (auto it = s->queue.begin(); it != s->queue.end();) {
-                if (reserve(s, *it)) {
-                    (*it)->state = kResident;
-                    adm.push_back(*it);
-                    s->resident.push_back(*it);
-                    it = s->queue.erase(it);
-                } else {
-                    ++it;
+            s->cv_work.wait(lk, [&] { return s->stop || s->eng[0].busy() || s->eng[1].busy(); });
+            if (s->stop && !s->eng[0].busy() && !s->eng[1].busy()) break;
+            for (int k = 0; k < 2; ++k) {
+                Engine &E = s->eng[k];
+                if (!E.busy()) continue;
+                for (Request *r : E.staged) {
+                    r->state = kResident;
+                    adm[k].push_back(r);
+                    E.resident.push_back(r);
                 }
+                E.staged.clear();
+                for (auto it = E.queue.begin(); it != E.queue.end();) {
+                    if (reserve(E, *it)) {
+                        (*it)->state = kResident;
+                        adm[k].push_back(*it);
+                        E.resident.push_back(*it);
+                        it = E.queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+                active[k] = !E.resident.empty();
+                queued[k] = !E.queue.empty();
             }
         }
-        const double t0 = now_s();
-        std::vector<Request *> bad;
-        if (admit(s, adm, bad) != GC_OK) {
+        bool ok = true;
+        for (int k = 0; k < 2 && ok; ++k)
+            if (active[k]) ok = engine_step(s, s->eng[k], adm[k], queued[k]);
+        if (!ok) {
             fail_all(s, s->fatal, s->fatal_msg);
             break;
         }
-        bool queued = false;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            for (Request *r : bad) {
-                s->resident.erase(std::find(s->resident.begin(), s->resident.end(), r));
-                unreserve(s, r);
-                r->status = GC_ERR_INVALID_GRAPH;
-                r->state = kDone;
-                s->rejected += 1;
-            }
-            if (!bad.empty()) s->cv_done.notify_all();
-            queued = !s->queue.empty();
-            if (s->resident.empty()) continue;
-        }
-        RoundParams P = params(s, queued ? kRoundsWhileQueued : kRoundsIdleQueue);
-        cudaError_t e = launch_rounds(P, s->cfg.mode, true, s->compact, s->grid, 256, s->stream);
-        Ctl h{};
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, s->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s->h_glast.data(), s->glast.p, 4 * s->S, cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-        if (e != cudaSuccess) {
-            fail_all(s, GC_ERR_CUDA, std::string("server round launch: ") + cudaGetErrorString(e));
-            break;
-        }
-        if (h.err[0] != 0) {
-            fail_all(s, h.err[0], "device error in the batched round kernel");
-            break;
-        }
-        const int32_t ran = h.passes[0] - s->next_pass;
-        s->next_pass = h.passes[0];
-        std::vector<Request *> fin;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->rounds_run += ran;
-            for (auto it = s->resident.begin(); it != s->resident.end();) {
-                if (s->h_glast[(*it)->slot] < s->next_pass) {
-                    fin.push_back(*it);
-                    it = s->resident.erase(it);
-                } else {
-                    ++it;
-                }
-            }
-        }
-        if (retire(s, fin) != GC_OK) {
-            fail_all(s, s->fatal, s->fatal_msg);
-            break;
-        }
-        s->busy += now_s() - t0;
     }
 }
 
@@ -478,6 +595,7 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
         return set_last_error(GC_ERR_INVALID_ARG, "pool sizes must be positive (vertices < 2^30)");
     if (cfg->mode != GC_MODE_DETERMINISTIC && cfg->mode != GC_MODE_INPLACE)
         return set_last_error(GC_ERR_INVALID_ARG, "unknown mode %d", cfg->mode);
+    if (cfg->spin_limit_ns < 0) return set_last_error(GC_ERR_INVALID_ARG, "negative spin_limit_ns");
     int dev = cfg->device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -490,58 +608,20 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
     auto s = std::make_unique<gc_server>();
     s->cfg = *cfg;
     s->device = dev;
-    s->S = cfg->max_requests > 0 ? cfg->max_requests : 4096;
-    s->PV = cfg->pool_vertices;
-    s->PE = cfg->pool_entries;
-    s->PI = std::min<int64_t>(s->PV, s->PE / (gc::kT1 + 1) + 1);
-    s->PC = s->PE / gc::kCH + s->PI + 1;
-    // deterministic mode sweeps compact lists: a slot per pool vertex and two list regions per entry
-    s->compact = cfg->mode == GC_MODE_DETERMINISTIC;
-    const size_t slots = s->compact ? static_cast<size_t>(s->PV) : static_cast<size_t>(s->PI);
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
-    const size_t V = static_cast<size_t>(s->PV), Sz = static_cast<size_t>(s->S);
-    struct {
-        gc::DevBuf *b;
-        size_t bytes;
-    } plan[] = {
-        {&s->rowptr, 4 * (V + Sz)}, {&s->colidx, 4 * static_cast<size_t>(s->PE)}, {&s->col0, 8 * V}, {&s->col1, 8 * V},
-        {&s->outbuf, 4 * V}, {&s->small0, 4 * V}, {&s->small1, 4 * V}, {&s->items, 4 * V}, {&s->vg, 4 * V},
-        {&s->chunk0, gc::kItemBytes * static_cast<size_t>(s->PC)}, {&s->chunk1, gc::kItemBytes * static_cast<size_t>(s->PC)},
-        {&s->acc, 4 * gc::kAccStride * slots}, {&s->lists, s->compact ? 8 * static_cast<size_t>(s->PE) : 0},
-        {&s->ctl, sizeof(gc::Ctl)},
-        {&s->bitmap, 4 * (V / 32 + 4)}, {&s->g_vbase, 8 * Sz}, {&s->g_n, 4 * Sz}, {&s->g_ebase, 8 * Sz},
-        {&s->g_rbase, 8 * Sz}, {&s->g_m, 8 * Sz}, {&s->glast, 4 * Sz}, {&s->gmax, 4 * Sz}, {&s->gcount, 4 * Sz},
-        {&s->verr, 16 * Sz},
-    };
-    for (auto &a : plan) {
-        if (e != cudaSuccess) break;
-        e = a.b->alloc(a.bytes);
-    }
-    if (e == cudaSuccess) e = cudaMemset(s->ctl.p, 0, sizeof(gc::Ctl));
-    if (e == cudaSuccess) e = cudaMemset(s->acc.p, 0, 4 * gc::kAccStride * slots);
-    if (e == cudaSuccess) e = cudaMemset(s->g_n.p, 0, 4 * Sz);
-    if (e == cudaSuccess) e = cudaMemset(s->glast.p, 0, 4 * Sz);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (s->stream) cudaStreamDestroy(s->stream);
-        return set_last_error(e == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA, "server pool: %s",
-                              cudaGetErrorString(e));
+        return set_last_error(GC_ERR_CUDA, "server streams: %s", cudaGetErrorString(e));
     }
-    int per_sm = 0, sms = 0;
-    gc::round_kernel_occupancy(cfg->mode, true, s->compact, 256, &per_sm);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    s->grid = std::max(1, per_sm * sms);
-    s->h_vbase.assign(Sz, 0);
-    s->h_ebase.assign(Sz, 0);
-    s->h_rbase.assign(Sz, 0);
-    s->h_m.assign(Sz, 0);
-    s->h_n.assign(Sz, 0);
-    s->h_glast.assign(Sz, 0);
-    s->va.reset(s->PV);
-    s->ea.reset(s->PE);
-    s->ra.reset(s->PV + s->S);
-    for (int32_t g = s->S - 1; g >= 0; --g) s->free_slots.push_back(g);
+    gc::Engine &E0 = s->eng[gc::engine_index(cfg->mode)];
+    const int st = gc::engine_create(s.get(), E0, cfg->mode);
+    E0.mode = cfg->mode;  // the worker thread does not exist yet
+    if (st != GC_OK) {
+        cudaStreamDestroy(s->stream);
+        cudaStreamDestroy(s->copy_stream);
+        return st;
+    }
     s->t_create = gc::now_s();
     gc_server *raw = s.release();
     raw->worker = std::thread(gc::worker_main, raw);
@@ -549,11 +629,36 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
     return GC_OK;
 }
 
-int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t *req_id) {
+int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32_t *colidx, int mode, uint64_t seed,
+                     uint64_t *req_id) {
     if (!s || !req_id) return set_last_error(GC_ERR_INVALID_ARG, "NULL server or request id");
+    if (mode != GC_MODE_DETERMINISTIC && mode != GC_MODE_INPLACE)
+        return set_last_error(GC_ERR_INVALID_ARG, "unknown mode %d (the server runs the deterministic and in-place "
+                                                  "modes)", mode);
     if (n < 0 || (n > 0 && !rowptr)) return set_last_error(GC_ERR_INVALID_ARG, "bad n or NULL rowptr");
+    gc::Engine &E = s->eng[gc::engine_index(mode)];
+    {
+        // the first request of a mode allocates that mode's pool
+        std::lock_guard<std::mutex> ck(s->create_mu);
+        bool created;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            created = E.mode >= 0;
+        }
+        if (!created) {
+            // the worker ignores this pool until its mode is published under the server lock
+            cudaSetDevice(s->device);
+            const int st = gc::engine_create(s, E, mode);
+            if (st != GC_OK) return st;
+            std::lock_guard<std::mutex> lk(s->mu);
+            E.mode = mode;
+        }
+    }
     auto r = std::make_unique<gc::Request>();
     r->n = n;
+    r->mode = mode;
+    r->seed = seed;
+    r->eng = &E;
     r->rowptr.resize(static_cast<size_t>(n) + 1);
     cudaPointerAttributes a{};
     const bool rp_dev = cudaPointerGetAttributes(&a, rowptr) == cudaSuccess &&
@@ -588,7 +693,7 @@ int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->fatal != GC_OK) return set_last_error(s->fatal, "server stopped: %s", s->fatal_msg.c_str());
-        if (n > s->va.capacity() || m > s->ea.capacity() || r->n_large > s->PI || r->n_chunks > s->PC) {
+        if (n > E.va.capacity() || m > E.ea.capacity() || r->n_large > E.PI || r->n_chunks > E.PC) {
             s->rejected += 1;
             return set_last_error(GC_ERR_OOM, "request (n=%d, nnz=%lld) exceeds the server pool", n,
                                   static_cast<long long>(m));
@@ -597,17 +702,17 @@ int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32
         r->t_submit = gc::now_s();
         *req_id = r->id;
         // with nothing queued ahead and room in the pool, the CSR goes straight into the pool
-        raw->staged = s->queue.empty() && gc::reserve(s, raw);
+        raw->staged = E.queue.empty() && gc::reserve(E, raw);
         s->reqs[raw->id] = std::move(r);
         s->submitted += 1;
     }
     cudaError_t e = cudaSuccess;
     if (raw->staged) {
         std::lock_guard<std::mutex> ck(s->copy_mu);
-        e = cudaMemcpyAsync(s->rowptr.as<int32_t>() + raw->rbase, raw->rowptr.data(), 4 * (static_cast<size_t>(n) + 1),
+        e = cudaMemcpyAsync(E.rowptr.as<int32_t>() + raw->rbase, raw->rowptr.data(), 4 * (static_cast<size_t>(n) + 1),
                             cudaMemcpyHostToDevice, s->copy_stream);
         if (e == cudaSuccess && m)
-            e = cudaMemcpyAsync(s->colidx.as<int32_t>() + raw->ebase, colidx, 4 * static_cast<size_t>(m),
+            e = cudaMemcpyAsync(E.colidx.as<int32_t>() + raw->ebase, colidx, 4 * static_cast<size_t>(m),
                                 ci_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->copy_stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
         std::vector<int32_t>().swap(raw->rowptr);
@@ -621,15 +726,15 @@ int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32
     std::lock_guard<std::mutex> lk(s->mu);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (raw->staged) gc::unreserve(s, raw);
+        if (raw->staged) gc::unreserve(E, raw);
         raw->state = gc::kDone;
         raw->status = GC_ERR_CUDA;
         return set_last_error(GC_ERR_CUDA, "copying the request: %s", cudaGetErrorString(e));
     }
     if (raw->staged)
-        s->staged.push_back(raw);
+        E.staged.push_back(raw);
     else
-        s->queue.push_back(raw);
+        E.queue.push_back(raw);
     s->cv_work.notify_one();
     return GC_OK;
 }
@@ -653,11 +758,17 @@ int gc_server_poll(gc_server *s, uint64_t req_id, int32_t timeout_ms, int32_t *c
     const int status = r->status;
     std::unique_ptr<gc::Request> keep = std::move(it->second);
     s->reqs.erase(it);
+    const std::string fatal_msg = s->fatal_msg;
     lk.unlock();
     if (status == GC_ERR_INVALID_GRAPH)
         return set_last_error(status, "request %llu: invalid graph (neighbour id out of range or self-loop)",
                               static_cast<unsigned long long>(req_id));
-    if (status != GC_OK) return set_last_error(status, "request failed: %s", s->fatal_msg.c_str());
+    if (status == GC_ERR_TIMEOUT)
+        return set_last_error(status, "request %llu: a grid-barrier wait of its launch exceeded the limit",
+                              static_cast<unsigned long long>(req_id));
+    if (status != GC_OK)
+        return set_last_error(status, "request %llu failed (status %d)%s%s", static_cast<unsigned long long>(req_id),
+                              status, fatal_msg.empty() ? "" : ": ", fatal_msg.c_str());
     if (colors_out && keep->n) {
         cudaPointerAttributes a{};
         const bool dev = cudaPointerGetAttributes(&a, colors_out) == cudaSuccess &&
@@ -676,13 +787,14 @@ int gc_server_poll(gc_server *s, uint64_t req_id, int32_t timeout_ms, int32_t *c
     return GC_OK;
 }
 
-int gc_server_stats_get(gc_server *s, gc_server_stats *out) {
+int gc_server_stats(gc_server *s, struct gc_server_stats *out) {
     if (!s || !out) return set_last_error(GC_ERR_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> lk(s->mu);
     std::memset(out, 0, sizeof(*out));
     out->submitted = s->submitted;
     out->completed = s->completed;
     out->rejected = s->rejected;
+    out->failed = s->failed;
     out->rounds_run = s->rounds_run;
     out->vertices_colored = s->v_done;
     out->edges_colored = s->e_done;
@@ -695,10 +807,14 @@ int gc_server_stats_get(gc_server *s, gc_server_stats *out) {
     }
     out->busy_s = s->busy;
     out->wall_s = gc::now_s() - s->t_create;
-    out->resident = static_cast<int32_t>(s->resident.size());
-    out->queued = static_cast<int32_t>(s->queue.size());
+    for (const gc::Engine &E : s->eng) {
+        out->resident += static_cast<int32_t>(E.resident.size());
+        out->queued += static_cast<int32_t>(E.queue.size());
+    }
     return GC_OK;
 }
+
+int gc_server_stats_get(gc_server *s, struct gc_server_stats *out) { return gc_server_stats(s, out); }
 
 void gc_server_destroy(gc_server *s) {
     if (!s) return;

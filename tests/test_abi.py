@@ -33,3 +33,16 @@ def test_version_and_error_string(gclib):
     lib = gclib.load()
     assert lib.gc_version() >= 100
     assert isinstance(lib.gc_last_error(), bytes)
+
+
+def test_header_compiles_as_c_and_cpp(tmp_path):
+    # the stats struct tag and the gc_server_stats function share a name, which C and C++ allow
+    import subprocess
+    src = tmp_path / "use.c"
+    src.write_text('#include "gc.h"\nint f(gc_server *s) { struct gc_server_stats st; return gc_server_stats(s, &st) '
+                   '+ gc_server_stats_get(s, &st); }\n')
+    inc = os.path.join(ROOT, "include")
+    for cmd in (["gcc", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
+                ["g++", "-x", "c++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)]):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr

@@ -93,3 +93,58 @@ def test_server_device_inputs(gclib):
         _, nc, rounds = srv.poll(rid, out=out)
         ref = oracle.det(g, 7)
         np.testing.assert_array_equal(out.cpu().numpy(), ref.colors)
+
+
+def test_server_mixed_modes_and_seeds(gclib):
+    # one server, requests with their own mode and seed (the problem of Section 2.1 with the
+    # conflict rule of Algorithm 1 under each request's priority): every deterministic result equals
+    # the oracle for its own seed; the in-place one is a proper coloring within Delta + 1 colors
+    gs = [gg.rmat(12, 16, 2), gg.workload("er10k"), gg.rmat(11, 12, 5), gg.complete(90), gg.crown(30)]
+    seeds = [1, 7, 2**63 + 5, 3, 11]
+    with gclib.Server(pool_vertices=500_000, pool_entries=10_000_000, mode="det", seed=0) as srv:
+        ids = [srv.submit(g.rowptr, g.colidx, mode="det", seed=sd) for g, sd in zip(gs, seeds)]
+        ip_graph = gg.rmat(12, 16, 9)
+        ip_id = srv.submit(ip_graph.rowptr, ip_graph.colidx, mode="inplace", seed=5)
+        # the same graph under two seeds in the same batch
+        twin = srv.submit(gs[0].rowptr, gs[0].colidx, mode="det", seed=99)
+        for g, sd, rid in zip(gs, seeds, ids):
+            ref = oracle.det(g, sd)
+            colors, nc, rounds = srv.poll(rid, timeout_ms=-1)
+            np.testing.assert_array_equal(colors, ref.colors, err_msg=f"{g.name} seed {sd}")
+            assert (nc, rounds) == (ref.ncolors, ref.rounds)
+        ref = oracle.det(gs[0], 99)
+        colors, nc, rounds = srv.poll(twin, timeout_ms=-1)
+        np.testing.assert_array_equal(colors, ref.colors)
+        assert (nc, rounds) == (ref.ncolors, ref.rounds)
+        colors, nc, rounds = srv.poll(ip_id, timeout_ms=-1)
+        assert oracle.count_conflicts(ip_graph, colors) == 0
+        assert np.all(colors <= ip_graph.degrees()) and nc == oracle.distinct_colors(colors)
+        st = srv.stats()
+        assert st["completed"] == len(gs) + 2 and st["failed"] == 0
+
+
+def test_server_rejects_unknown_request_mode(gclib):
+    g = gg.cycle(9)
+    with gclib.Server(pool_vertices=1000, pool_entries=10_000, mode="det") as srv:
+        for mode in ("partition", "ordered", 7):
+            with pytest.raises(gclib.GCError) as ei:
+                srv.submit(g.rowptr, g.colidx, mode=mode)
+            assert ei.value.status == gclib.GC_ERR_INVALID_ARG
+
+
+def test_server_survives_device_error(gclib):
+    # every launch's grid-barrier wait runs out (a 1 ns limit): the resident requests end with
+    # GC_ERR_TIMEOUT, the pool is reset, and the worker goes on to the next request
+    g = gg.rmat(12, 16, 2)
+    with gclib.Server(pool_vertices=100_000, pool_entries=2_000_000, mode="det", seed=7, spin_limit_ns=1) as srv:
+        for _ in range(2):
+            rid = srv.submit(g.rowptr, g.colidx)
+            with pytest.raises(gclib.GCError) as ei:
+                srv.poll(rid, timeout_ms=-1)
+            assert ei.value.status == gclib.GC_ERR_TIMEOUT
+        st = srv.stats()
+        assert st["failed"] == 2 and st["resident"] == 0 and st["queued"] == 0
+    # the device is still usable afterwards
+    ref = oracle.det(g, 7)
+    r = gclib.color(g.rowptr, g.colidx, "det", 7)
+    np.testing.assert_array_equal(r.colors, ref.colors)

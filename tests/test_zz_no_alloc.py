@@ -43,6 +43,42 @@ def test_noalloc_matches_gc_color_twice(gclib, make):
         assert (nc.value, rd.value) == (ref.ncolors, ref.rounds)
 
 
+def test_noalloc_allocates_nothing_after_warm_up(gclib):
+    # the first call on a device loads the module (and its scratch array); after that a call must
+    # leave the device's free memory exactly as it was
+    import torch
+    f = _entry(gclib)
+    g = gg.rmat(13, 16, 2)
+    rp = torch.from_numpy(g.rowptr).cuda()
+    ci = torch.from_numpy(g.colidx).cuda()
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    nc, rd = ctypes.c_int32(0), ctypes.c_int32(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    assert f(g.n, rp.data_ptr(), ci.data_ptr(), 7, out.data_ptr(), ctypes.byref(nc), ctypes.byref(rd), stream) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    assert f(g.n, rp.data_ptr(), ci.data_ptr(), 7, out.data_ptr(), ctypes.byref(nc), ctypes.byref(rd), stream) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_rejects_too_many_entries(gclib):
+    # at most 16,384 vertices but more than 2^20 adjacency entries: rejected, outputs untouched
+    import torch
+    f = _entry(gclib)
+    g = gg.complete(1100)  # 1,208,900 entries
+    assert g.n <= 16384 and g.nnz > (1 << 20)
+    rp = torch.from_numpy(g.rowptr).cuda()
+    ci = torch.from_numpy(g.colidx).cuda()
+    out = torch.full((g.n,), -5, dtype=torch.int32, device="cuda")
+    nc, rd = ctypes.c_int32(-3), ctypes.c_int32(-3)
+    st = f(g.n, rp.data_ptr(), ci.data_ptr(), 7, out.data_ptr(), ctypes.byref(nc), ctypes.byref(rd), None)
+    assert st == gclib.GC_ERR_INVALID_ARG
+    assert bool((out == -5).all())
+    assert (nc.value, rd.value) == (-3, -3)
+
+
 def test_noalloc_rejects_oversize(gclib):
     import torch
     f = _entry(gclib)

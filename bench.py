@@ -225,17 +225,11 @@ def batch_graphs(name):
 
 
 def shard_graphs(b, rank, world):
-    """Graph-sharded batching: rank `rank` of `world` takes a subset of the batch's graphs, greedily
-    balanced by adjacency entries (largest first onto the least loaded rank).  Returns the graph ids,
-    in increasing order."""
-    sizes = [(int(b.edge_off[g + 1] - b.edge_off[g]) + int(b.vtx_off[g + 1] - b.vtx_off[g]), g) for g in range(b.G)]
-    load = [0] * world
-    owner = [0] * b.G
-    for sz, g in sorted(sizes, key=lambda x: (-x[0], x[1])):
-        r = min(range(world), key=lambda k: (load[k], k))
-        owner[g] = r
-        load[r] += sz
-    return [g for g in range(b.G) if owner[g] == rank]
+    """Graph-sharded batching: the ids (increasing) of the batch's graphs that rank `rank` of
+    `world` colors, balanced by vertices + adjacency entries (paper_1509_08267_gb300.dist)."""
+    from paper_1509_08267_gb300 import dist as gdist
+    sizes = [int(b.edge_off[g + 1] - b.edge_off[g]) + int(b.vtx_off[g + 1] - b.vtx_off[g]) for g in range(b.G)]
+    return [g for g, o in enumerate(gdist.shard_graphs(sizes, world)) if o == rank]
 
 
 def batched_object(args, rank, world, G):

@@ -267,6 +267,26 @@ int gc_validate_graph(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
 int gc_color_noalloc(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed, int32_t *colors_out,
                      int32_t *ncolors, int32_t *rounds, void *stream);
 
+/*
+ * gc_det_round -- one round of the deterministic mode over a given list of worklist vertices, for a
+ * caller that splits a graph's vertices into blocks (Algorithm 1's partitions V_1..V_p, one per GPU
+ * or process) and exchanges the changed colors between rounds itself.  The mode's rounds read only
+ * the colors as the round began, so the blocks can run a round independently: with the previous
+ * round's new colors exchanged, the result is identical to gc_color's whatever the split.
+ *   n, rowptr, colidx, seed   the whole graph and the priority seed, as gc_color
+ *   colors_cur   int32[n]      C_r, every vertex's color as round r begins (C_1 = 0 for every vertex)
+ *   worklist     int32[nwork]  the block's vertices on W_r (any order; each id at most once)
+ *   colors_next  int32[nwork]  receives C_{r+1} of each: the least color absent from C_r over its
+ *                              neighbours if it lost, else its C_r color
+ *   lost         int32[nwork]  receives 1 if the vertex lost (a neighbour with the same C_r color and a
+ *                              smaller key, Algorithm 1's phase 2), so it is on W_{r+1}; else 0
+ * Arrays may be device or host memory.  Synchronous.  Errors: GC_ERR_INVALID_ARG (NULL arrays, a
+ * worklist entry outside [0, n)), GC_ERR_INVALID_GRAPH (malformed rows or entries), GC_ERR_CUDA;
+ * outputs unspecified on error.
+ */
+int gc_det_round(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed, const int32_t *colors_cur,
+                 const int32_t *worklist, int32_t nwork, int32_t *colors_next, int32_t *lost);
+
 /* Message for the last error on the calling thread ("" if none). Valid until the next call. */
 const char *gc_last_error(void);
 

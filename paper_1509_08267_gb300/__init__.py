@@ -17,7 +17,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "GCError", "load", "color", "color_batch", "validate", "Options", "Stats", "Server", "MODE_DETERMINISTIC",
+    "GCError", "load", "color", "color_batch", "validate", "det_round", "Options", "Stats", "Server", "MODE_DETERMINISTIC",
     "MODE_INPLACE", "MODE_PARTITION", "MODE_ORDERED", "PRIORITY_HASH", "PRIORITY_LARGEST_FIRST", "PRIORITY_SMALLEST_LAST", "smallest_last", "recolor", "version", "release_scratch",
 ]
 
@@ -120,6 +120,8 @@ def load(path: str | None = None):
     lib.gc_last_error.argtypes = []
     lib.gc_version.restype = c_int
     lib.gc_release_scratch.restype = c_int
+    lib.gc_det_round.restype = c_int
+    lib.gc_det_round.argtypes = [i32, p, p, u64, p, p, i32, p, p]
     if hasattr(lib, "gc_server_create"):
         lib.gc_server_create.restype = c_int
         lib.gc_server_create.argtypes = [P(_ServerConfig), P(p)]
@@ -264,6 +266,27 @@ def recolor(rowptr, colidx, colors_in, seed: int = 0, out=None, options: Options
     colors_in (int32[n], >= 0), the largest color first; never more colors than colors_in has
     when colors_in is proper."""
     return _color_one(rowptr, colidx, "ordered", seed, out, options, stats, round_cap, colors_in)
+
+
+def det_round(rowptr, colidx, seed: int, colors_cur, worklist, colors_next=None, lost=None):
+    """One deterministic round over the worklist vertices `worklist` (gc_det_round): reading C_r
+    (colors_cur, int32[n]) returns (colors_next, lost), int32[len(worklist)] each, on the
+    worklist's home (CUDA tensor or numpy)."""
+    lib = load()
+    n = (rowptr.numel() if _is_torch(rowptr) else len(rowptr)) - 1
+    nwork = worklist.numel() if _is_torch(worklist) else len(worklist)
+    prp, rk = _ptr(rowptr, np.int32)
+    pci, ck = _ptr(colidx, np.int32)
+    pcur, curk = _ptr(colors_cur, np.int32)
+    pw, wk = _ptr(worklist, np.int32)
+    if colors_next is None:
+        colors_next = _empty_like_home(worklist, nwork)
+    if lost is None:
+        lost = _empty_like_home(worklist, nwork)
+    pn, nk = _ptr(colors_next, np.int32)
+    pl, lk = _ptr(lost, np.int32)
+    _check(lib.gc_det_round(n, prp, pci, seed & ((1 << 64) - 1), pcur, pw, nwork, pn, pl))
+    return (nk if nk is not None else colors_next), (lk if lk is not None else lost)
 
 
 def smallest_last(rowptr, colidx, out=None, options: Options | None = None):

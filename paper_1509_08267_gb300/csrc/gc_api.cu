@@ -106,6 +106,7 @@ struct Context {
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
     Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors, st_colors_in, mid0, mid1, rank;
     Buf core_rec, core_cex, core_cpk, core_items, core_active, core_log, core_pool;
+    Buf st_cur, st_work, st_next, st_lost;  // gc_det_round staging
     int32_t core_max_v = 0;  // largest core the round kernel's shared memory holds (-1: none)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // host adjacency arrays are uploaded on copy_stream while the set-up runs on the call's stream;
@@ -115,7 +116,8 @@ struct Context {
     void release_all() {
         Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &lists, &ctl, &stats, &bitmap, &hist,
                       &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors, &st_colors_in, &mid0, &mid1, &rank,
-                      &core_rec, &core_cex, &core_cpk, &core_items, &core_active, &core_log, &core_pool};
+                      &core_rec, &core_cex, &core_cpk, &core_items, &core_active, &core_log, &core_pool,
+                      &st_cur, &st_work, &st_next, &st_lost};
         for (Buf *b : all) b->release();
     }
 };
@@ -972,6 +974,62 @@ int gc_validate_graph(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
 const char *gc_last_error(void) { return gc::t_error.c_str(); }
 
 int gc_version(void) { return 100; }
+
+int gc_det_round(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed, const int32_t *colors_cur,
+                 const int32_t *worklist, int32_t nwork, int32_t *colors_next, int32_t *lost) {
+    using namespace gc;
+    if (n < 0 || nwork < 0) return set_last_error(GC_ERR_INVALID_ARG, "negative n or nwork");
+    if (nwork == 0) return GC_OK;
+    if (!rowptr || !colors_cur || !worklist || !colors_next || !lost)
+        return set_last_error(GC_ERR_INVALID_ARG, "NULL array");
+    Context *C = nullptr;
+    GC_TRY(get_context(&C));
+    std::lock_guard<std::mutex> lk(C->mu);
+    GC_CUDA(cudaSetDevice(C->device));
+    cudaStream_t s = C->stream;
+    int rp_dev = 0;
+    GC_TRY(locate(rowptr, C->device, &rp_dev));
+    int32_t nnz = 0;
+    if (rp_dev) {
+        GC_CUDA(cudaMemcpyAsync(&nnz, rowptr + n, 4, cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+    } else {
+        nnz = rowptr[n];
+    }
+    if (nnz < 0) return set_last_error(GC_ERR_INVALID_GRAPH, "rowptr[n] = %d is negative", nnz);
+    if (nnz > 0 && !colidx) return set_last_error(GC_ERR_INVALID_ARG, "NULL colidx");
+    const void *v = nullptr;
+    GC_TRY(device_view(rowptr, 4 * (static_cast<size_t>(n) + 1), C->device, C->st_rowptr, s, &v));
+    const int32_t *rp = static_cast<const int32_t *>(v);
+    GC_TRY(device_view(colidx, 4 * static_cast<size_t>(nnz), C->device, C->st_colidx, s, &v));
+    const int32_t *ci = v ? static_cast<const int32_t *>(v) : rp;
+    GC_TRY(device_view(colors_cur, 4 * static_cast<size_t>(n), C->device, C->st_cur, s, &v));
+    const int32_t *cur = static_cast<const int32_t *>(v);
+    GC_TRY(device_view(worklist, 4 * static_cast<size_t>(nwork), C->device, C->st_work, s, &v));
+    const int32_t *work = static_cast<const int32_t *>(v);
+    int next_dev = 0, lost_dev = 0;
+    GC_TRY(locate(colors_next, C->device, &next_dev));
+    GC_TRY(locate(lost, C->device, &lost_dev));
+    if (!next_dev) GC_TRY(ensure(C->st_next, 4 * static_cast<size_t>(nwork), "round output"));
+    if (!lost_dev) GC_TRY(ensure(C->st_lost, 4 * static_cast<size_t>(nwork), "round output"));
+    int32_t *next_d = next_dev ? colors_next : C->st_next.as<int32_t>();
+    int32_t *lost_d = lost_dev ? lost : C->st_lost.as<int32_t>();
+    GC_TRY(ensure(C->ctl, sizeof(Ctl), "control"));
+    Ctl *ctl = C->ctl.as<Ctl>();
+    GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    GC_CUDA(launch_det_round_block(n, rp, ci, seed, cur, work, nwork, next_d, lost_d, ctl->err, s));
+    Ctl h{};
+    GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    if (h.err[0] == GC_ERR_INVALID_ARG)
+        return set_last_error(GC_ERR_INVALID_ARG, "worklist entry %d is not a vertex id", h.err[1]);
+    if (h.err[0] != 0) return error_from_ctl(h);
+    if (!next_dev)
+        GC_CUDA(cudaMemcpyAsync(colors_next, next_d, 4 * static_cast<size_t>(nwork), cudaMemcpyDeviceToHost, s));
+    if (!lost_dev) GC_CUDA(cudaMemcpyAsync(lost, lost_d, 4 * static_cast<size_t>(nwork), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    return GC_OK;
+}
 
 int gc_release_scratch(void) {
     using namespace gc;

@@ -233,6 +233,10 @@ cudaError_t partition_kernel_occupancy(int block, int *blocks_per_sm);
 cudaError_t launch_partition_rounds(const RoundParams &P, int32_t p, int grid, int block, cudaStream_t s);
 cudaError_t launch_validate(int32_t n, const int32_t *rowptr, const int32_t *colidx, int flags, int32_t *err,
                             cudaStream_t s);
+// gc_det_round: one fused deterministic round over the worklist vertices work[0, nwork).
+cudaError_t launch_det_round_block(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed,
+                                  const int32_t *cur, const int32_t *work, int32_t nwork, int32_t *next, int32_t *lost,
+                                  int32_t *err, cudaStream_t s);
 // Core phase (after launch_rounds handed over, *P.core_go = 1; every kernel returns at once when
 // it did not): local ids and rows, the round kernel, and the final colors written back to col0 and
 // col1.  core_max_vertices: the largest M the shared memory of one block per SM allows.

@@ -2254,6 +2254,71 @@ __global__ void validate_kernel(int32_t n, const int32_t *rowptr, const int32_t 
     }
 }
 
+// One fused deterministic round over a list of worklist vertices, for callers that own a block of
+// a graph's vertices and exchange colors between rounds themselves (Algorithm 1's partitions V_i):
+// reading C_r (`cur`, every vertex), vertex v = work[i] lost iff a neighbour u has C_r[u] = C_r[v]
+// and key(u) < key(v); next[i] is its color for round r+1: the least color absent from C_r over
+// its neighbours if it lost, else C_r[v].  One warp per vertex; the least free color is found a
+// window of 1024 colors at a time.  Malformed rows or entries post GC_ERR_INVALID_GRAPH.
+__global__ void det_round_block_kernel(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed,
+                                       const int32_t *cur, const int32_t *work, int32_t nwork, int32_t *next,
+                                       int32_t *lost, int32_t *err) {
+    __shared__ unsigned s_win[8][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned *win = s_win[wib];
+    const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wib; i < nwork; i += nw) {
+        const int32_t v = __ldg(work + i);
+        if (static_cast<uint32_t>(v) >= static_cast<uint32_t>(n)) {
+            if (lane == 0) set_error(err, GC_ERR_INVALID_ARG, v, i);
+            continue;
+        }
+        const int64_t b = __ldg(rowptr + v), e = __ldg(rowptr + v + 1);
+        if (b < 0 || e < b || e > __ldg(rowptr + n)) {
+            if (lane == 0) set_error(err, GC_ERR_INVALID_GRAPH, v, b);
+            continue;
+        }
+        const int32_t cv = __ldg(cur + v);
+        const uint64_t hv = vertex_hash(seed, static_cast<uint32_t>(v));
+        bool lose = false;
+        for (int64_t j = b + lane; j < e; j += 32) {
+            const int32_t u = __ldg(colidx + j);
+            if (static_cast<uint32_t>(u) >= static_cast<uint32_t>(n) || u == v) {
+                set_error(err, GC_ERR_INVALID_GRAPH, v, j);
+                continue;
+            }
+            if (__ldg(cur + u) == cv) {
+                const uint64_t hu = vertex_hash(seed, static_cast<uint32_t>(u));
+                lose |= hu < hv || (hu == hv && u < v);
+            }
+        }
+        lose = __any_sync(kFull, lose);
+        int32_t nc = cv;
+        for (int32_t base = 0; lose; base += 1024) {
+            win[lane] = 0u;
+            __syncwarp();
+            for (int64_t j = b + lane; j < e; j += 32) {
+                const int32_t u = __ldg(colidx + j);
+                if (static_cast<uint32_t>(u) >= static_cast<uint32_t>(n)) continue;
+                const int32_t c = __ldg(cur + u) - base;
+                if (static_cast<unsigned>(c) < 1024u) atomicOr(&win[c >> 5], 1u << (c & 31));
+            }
+            __syncwarp();
+            const unsigned open = __ballot_sync(kFull, win[lane] != ~0u);
+            if (open) {
+                const int l = __ffs(open) - 1;
+                nc = base + 32 * l + __ffs(~win[l]) - 1;
+                break;
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            next[i] = nc;
+            lost[i] = lose ? 1 : 0;
+        }
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
@@ -2495,6 +2560,15 @@ cudaError_t launch_count_colors(const RoundParams &P, bool batch, const int32_t 
         else
             count_pop_kernel<false><<<pgrid, 256, 0, s>>>(P, g_begin, g_end, bitmap, gmax, gcount);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_det_round_block(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed,
+                                  const int32_t *cur, const int32_t *work, int32_t nwork, int32_t *next, int32_t *lost,
+                                  int32_t *err, cudaStream_t s) {
+    if (nwork <= 0) return cudaSuccess;
+    const int grid = grid_for(static_cast<int64_t>(nwork) * 32, 256, sm_count() * 16);
+    det_round_block_kernel<<<grid, 256, 0, s>>>(n, rowptr, colidx, seed, cur, work, nwork, next, lost, err);
     return cudaGetLastError();
 }
 

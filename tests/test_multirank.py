@@ -53,3 +53,187 @@ def test_one_rank_is_local():
     import bench
     assert bench.reduce_max(0.25, 1) == 0.25
     assert bench.whole_job_rate(10.0, 2.0, 1) == 5.0
+
+
+# ---- vertex blocks of one graph (Algorithm 1's partitions, one per rank) and graph-sharded batches
+
+def _graphs():
+    import graphgen as gg
+    return [gg.rmat(9, 16, 2), gg.er(300, 8.0, 3), gg.complete(25), gg.star(40), gg.empty(10), gg.path(33),
+            gg.crown(12), gg.from_edges(20, [(i, j) for i in range(0, 20, 3) for j in range(i + 3, 20, 3)])]
+
+
+def cpu_round(g, seed):
+    """One fused deterministic round written out plainly (test infrastructure): a worklist vertex
+    loses iff a neighbour has its color and a smaller key (the oracle's key order), and a loser's
+    next color is the least color absent among its neighbours."""
+    import numpy as np
+    import torch
+
+    import oracle
+    rank = oracle.priority_rank(seed, g.n)
+
+    def step(colors, work):
+        c = colors.numpy()
+        w = work.numpy()
+        nxt = np.empty(len(w), np.int32)
+        lost = np.zeros(len(w), np.int32)
+        for i, v in enumerate(w):
+            nb = g.colidx[g.rowptr[v]:g.rowptr[v + 1]]
+            lose = bool(np.any((c[nb] == c[v]) & (rank[nb] < rank[v])))
+            lost[i] = lose
+            if lose:
+                seen = set(int(x) for x in c[nb])
+                k = 0
+                while k in seen:
+                    k += 1
+                nxt[i] = k
+            else:
+                nxt[i] = c[v]
+        return torch.from_numpy(nxt), torch.from_numpy(lost)
+
+    return step
+
+
+def _blocks_rank_main(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    from paper_1509_08267_gb300 import dist as gdist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        res = []
+        for gi, g in enumerate(_graphs()):
+            for seed in (7, 2**63 + 5):
+                rp = torch.from_numpy(g.rowptr.astype("int32"))
+                ci = torch.from_numpy(g.colidx.astype("int32"))
+                colors, rounds = gdist.color_blocks(rp, ci, seed, cpu_round(g, seed), gdist.allgather_exchange(),
+                                                    rank=rank, world=world)
+                res.append((gi, seed, colors.numpy().tolist(), rounds))
+        out.put((rank, res))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_vertex_blocks_across_ranks_match_oracle(world):
+    # every rank ends with the oracle's colors and round count, whatever the number of blocks
+    pytest.importorskip("torch.distributed")
+    import numpy as np
+    import torch.multiprocessing as mp
+
+    sys.path.insert(0, ROOT)
+    import oracle
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_blocks_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    graphs = _graphs()
+    for r in range(world):
+        for gi, seed, colors, rounds in got[r]:
+            ref = oracle.det(graphs[gi], seed)
+            np.testing.assert_array_equal(np.array(colors, np.int32), ref.colors, err_msg=f"graph {gi} rank {r}")
+            assert rounds == ref.rounds
+
+
+def test_vertex_blocks_in_process_match_oracle():
+    # the in-process emulation (all blocks one after another each round) with the same plain round
+    import numpy as np
+    import torch
+
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1509_08267_gb300 import dist as gdist
+    for g in _graphs():
+        ref = oracle.det(g, 11)
+        for world in (1, 2, 5, max(1, g.n)):
+            colors, rounds = gdist.color_blocks_inprocess(torch.from_numpy(g.rowptr.astype("int32")),
+                                                          torch.from_numpy(g.colidx.astype("int32")), 11,
+                                                          cpu_round(g, 11), world)
+            np.testing.assert_array_equal(colors.numpy(), ref.colors)
+            assert rounds == ref.rounds
+
+
+def test_block_ranges_partition_the_vertices():
+    sys.path.insert(0, ROOT)
+    from paper_1509_08267_gb300 import dist as gdist
+    for n in (0, 1, 7, 100, 1001):
+        for world in (1, 2, 3, 8):
+            ranges = [gdist.block_range(n, r, world) for r in range(world)]
+            assert ranges[0][0] == 0 and ranges[-1][1] == n
+            assert all(ranges[r][1] == ranges[r + 1][0] for r in range(world - 1))
+            assert max(b - a for a, b in ranges) - min(b - a for a, b in ranges) <= 1
+
+
+def test_graph_shards_cover_and_balance():
+    sys.path.insert(0, ROOT)
+    import graphgen as gg
+    from paper_1509_08267_gb300 import dist as gdist
+    b = gg.batch_mix(64, 3, nmax=20_000)
+    sizes = [int(b.edge_off[g + 1] - b.edge_off[g]) + int(b.vtx_off[g + 1] - b.vtx_off[g]) for g in range(b.G)]
+    for world in (1, 2, 3, 8):
+        owner = gdist.shard_graphs(sizes, world)
+        assert sorted(set(owner)) == list(range(min(world, b.G)))
+        loads = [sum(s for s, o in zip(sizes, owner) if o == r) for r in range(world)]
+        assert sum(loads) == sum(sizes)
+        assert max(loads) - min(loads) <= max(sizes)
+
+
+def _batch_rank_main(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch.distributed as dist
+
+    import graphgen as gg
+    import oracle
+    from paper_1509_08267_gb300 import dist as gdist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        b = gg.batch_mix(24, 3, nmax=3000)
+        sizes = [int(b.edge_off[g + 1] - b.edge_off[g]) + int(b.vtx_off[g + 1] - b.vtx_off[g]) for g in range(b.G)]
+        mine = [g for g, o in enumerate(gdist.shard_graphs(sizes, world)) if o == rank]
+        # each rank colors its own graphs (here with the oracle, standing in for its GPU); the
+        # results are gathered, no other exchange happens
+        res = {g: oracle.det(b.graph(g), 7).colors.tolist() for g in mine}
+        gathered = [None] * world
+        dist.all_gather_object(gathered, res)
+        merged = {}
+        for part in gathered:
+            assert not set(part) & set(merged)  # disjoint shards
+            merged.update(part)
+        out.put((rank, sorted(merged), {g: np.array(c, np.int32).sum() for g, c in merged.items()}))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_graph_sharded_batch_across_ranks():
+    pytest.importorskip("torch.distributed")
+    import torch.multiprocessing as mp
+
+    sys.path.insert(0, ROOT)
+    import graphgen as gg
+    import oracle
+    ctx = mp.get_context("spawn")
+    world, port = 2, _free_port()
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_batch_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    b = gg.batch_mix(24, 3, nmax=3000)
+    for rank, graphs, sums in got:
+        assert graphs == list(range(b.G))  # every graph colored exactly once across the ranks
+        for g in graphs:
+            assert sums[g] == oracle.det(b.graph(g), 7).colors.sum()

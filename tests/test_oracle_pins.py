@@ -297,6 +297,61 @@ def test_partition_lemma2_round_bound(p):
         assert np.all(r.colors <= g.degrees())
 
 
+def _literal_alg1(n, adj, p):
+    """Algorithm 1 (Section 3.1) restated with its own data structures: blocks V_1..V_p of
+    consecutive ids; every vertex keeps ForbiddenColors, one slot per neighbour initialised to -1.
+    Phase 1: each block takes its worklist U_i in id order, gives v the least color of
+    TotalColors = {0..m} not in v's slots, and writes that color into the slot of v at each
+    neighbour in the same block.  Barrier.  Phase 2: each worklist vertex refreshes the slots of its
+    neighbours in other blocks and is kept for the next round when one of them in a higher block
+    has its color (the reading that the lower block's vertex is recolored).  Barrier.  Returns
+    (colors, rounds)."""
+    block = [0] * n
+    for i in range(p):
+        for v in range(i * n // p, (i + 1) * n // p):
+            block[v] = i
+    m = max((len(a) for a in adj), default=0)
+    color = [-1] * n
+    forbidden = [{u: -1 for u in adj[v]} for v in range(n)]
+    U = [[v for v in range(n) if block[v] == i] for i in range(p)]
+    rounds = 0
+    while any(U):
+        rounds += 1
+        for i in range(p):  # phase 1 (threads are independent: only in-block slots are written)
+            for v in U[i]:
+                used = set(forbidden[v].values())
+                color[v] = min(c for c in range(m + 1) if c not in used)
+                for u in adj[v]:
+                    if block[u] == i:
+                        forbidden[u][v] = color[v]
+        R = [set() for _ in range(p)]
+        for i in range(p):  # phase 2
+            for v in U[i]:
+                for u in adj[v]:
+                    if block[u] != i:
+                        forbidden[v][u] = color[u]
+                        if color[u] == color[v] and block[u] > i:
+                            R[i].add(v)
+        U = [sorted(r) for r in R]
+    return color, rounds
+
+
+def test_partition_matches_literal_algorithm1_for_every_block_count():
+    # 1 < p < n included: in-block colors seen live, other blocks' colors as refreshed in phase 2
+    rng = np.random.default_rng(17)
+    for trial in range(80):
+        n = int(rng.integers(2, 14))
+        dens = float(rng.uniform(0.15, 0.8))
+        edges = [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < dens]
+        g = gg.from_edges(n, edges)
+        adj = [list(g.colidx[g.rowptr[v]:g.rowptr[v + 1]]) for v in range(n)]
+        for p in range(1, n + 1):
+            lit, lr = _literal_alg1(n, adj, p)
+            r = oracle.partition(g, p)
+            assert r.status == 0
+            assert list(r.colors) == lit and r.rounds == lr, (n, p, edges)
+
+
 def test_partition_one_vertex_blocks_match_id_priority():
     # p = n: block order = id order, the lower id is re-queued, i.e. the larger id keeps its color
     rng = np.random.default_rng(9)

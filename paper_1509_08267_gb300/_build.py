@@ -30,6 +30,20 @@ def _flags() -> list[str]:
                    "-I", CSRC]
 
 
+def source_sha256() -> str:
+    """Digest of the library's device and host sources (every file under csrc/ and include/gc.h):
+    tuning tables and profile records name the sources they were measured on."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(CSRC, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    with open(os.path.join(ROOT, "include", "gc.h"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
 def _stale(target: str, deps: list[str]) -> bool:
     if not os.path.exists(target):
         return True

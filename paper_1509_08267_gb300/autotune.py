@@ -8,6 +8,8 @@ returns the tuned gc_options for a graph from that table (library defaults when 
 
 Classes are decided from the degree sequence alone: "powerlaw" when the largest degree exceeds 50
 times the average, else "uniform"; each is split into "small" (< 100,000 vertices) and "large".
+Every entry records the digest of the library sources it was tuned on; an entry tuned on other
+sources is stale and ignored (library defaults apply) until the tuner runs again.
 
     python -m paper_1509_08267_gb300.autotune [--out tuning.json] [--quick]
 """
@@ -22,6 +24,7 @@ import statistics
 import numpy as np
 
 from . import FLAG_FULL_SWEEP, FLAG_TIMING, Options, color, color_batch
+from ._build import source_sha256
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
 
@@ -30,6 +33,7 @@ GRID = {
     "chunk": [256, 512, 1024],
     "blocks_per_sm": [0, 3],
     "compact": [False, True],
+    "core_vertices": [0, -1],
 }
 
 
@@ -44,7 +48,7 @@ def graph_class(n: int, degrees: np.ndarray) -> str:
 def _options(cfg: dict, timing: bool = True) -> Options:
     flags = (FLAG_TIMING if timing else 0) | (0 if cfg["compact"] else FLAG_FULL_SWEEP)
     return Options(small_max_degree=cfg["small_max_degree"], chunk=cfg["chunk"],
-                   blocks_per_sm=cfg["blocks_per_sm"], flags=flags)
+                   blocks_per_sm=cfg["blocks_per_sm"], flags=flags, core_vertices=cfg.get("core_vertices", 0))
 
 
 def time_config(rowptr, colidx, cfg: dict, repeats: int = 3, seed: int = 7) -> float:
@@ -74,30 +78,42 @@ def tune(samples: dict, grid: dict = GRID, repeats: int = 3, log=print) -> dict:
             log(f"{cls:16s} {cfg} {ms:9.3f} ms")
             if best is None or ms < best[1]:
                 best = (cfg, ms)
-        table[cls] = {**best[0], "kernel_ms": best[1]}
+        table[cls] = {**best[0], "kernel_ms": best[1], "sources_sha256": source_sha256()}
     return table
 
 
-def options_for(n: int, degrees: np.ndarray, table_path: str = TABLE) -> Options:
-    """Tuned options for a graph (library defaults if no table or no entry for its class)."""
+def _entry(table_path: str, key: str) -> dict | None:
+    """The table's entry `key` if it was tuned on the current sources."""
     try:
         with open(table_path) as f:
-            table = json.load(f)
+            entry = json.load(f).get(key)
     except (OSError, ValueError):
-        return Options()
-    entry = table.get(graph_class(n, degrees))
-    if not entry:
-        return Options()
-    return _options(entry, timing=False)
+        return None
+    if not entry or entry.get("sources_sha256") != source_sha256():
+        return None
+    return entry
+
+
+def options_for(n: int, degrees: np.ndarray, table_path: str = TABLE) -> Options:
+    """Tuned options for a graph (library defaults if no current entry for its class)."""
+    entry = _entry(table_path, graph_class(n, degrees))
+    return _options(entry, timing=False) if entry else Options()
+
+
+def options_for_graph(rowptr, table_path: str = TABLE) -> tuple[Options, str | None]:
+    """options_for from a CSR row-offset array (numpy or a tensor); also returns the class name
+    when a current entry was used, else None."""
+    rp = rowptr.cpu().numpy() if hasattr(rowptr, "cpu") else np.asarray(rowptr)
+    n = len(rp) - 1
+    deg = np.diff(rp)
+    cls = graph_class(n, deg)
+    entry = _entry(table_path, cls)
+    return (_options(entry, timing=False), cls) if entry else (Options(), None)
 
 
 def batch_options(table_path: str = TABLE) -> Options:
     """Tuned options for gc_color_batch (the table's "batch" entry; library defaults without one)."""
-    try:
-        with open(table_path) as f:
-            entry = json.load(f).get("batch")
-    except (OSError, ValueError):
-        entry = None
+    entry = _entry(table_path, "batch")
     return _options(entry, timing=False) if entry else Options()
 
 
@@ -119,7 +135,7 @@ def main():
         return torch.from_numpy(g.rowptr).to(dev), torch.from_numpy(g.colidx).to(dev)
 
     grid = GRID if not args.quick else {"small_max_degree": [63, 127], "chunk": [512, 1024], "blocks_per_sm": [0],
-                                        "compact": [False, True]}
+                                        "compact": [False, True], "core_vertices": [0, -1]}
     table = {}
     if args.only_batch:
         try:

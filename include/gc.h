@@ -130,7 +130,11 @@ typedef struct gc_options {
                                   remaining rounds run with every worklist vertex's color in shared memory
                                   (same results).  0 = the most one block's shared memory holds (about
                                   110k); < 0 = never */
-    int32_t reserved[5];
+    int32_t core_entries;      /* deterministic mode: the most adjacency entries the shared-memory rounds take
+                                  (their rows are rebuilt once, at the hand-over); 0 = min(nnz, 2^27).  Above
+                                  2^27 it is clamped.  Only a graph with more entries than this counts its
+                                  worklists' entries every round to find the hand-over */
+    int32_t reserved[4];
 } gc_options;
 
 /* Optional run statistics (gc_color_ex / gc_color_batch_ex).  The caller may provide arrays

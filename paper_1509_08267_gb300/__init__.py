@@ -62,7 +62,7 @@ class _Options(ctypes.Structure):
                 ("chunk", ctypes.c_int32), ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("spin_limit_ns", ctypes.c_int64), ("flags", ctypes.c_uint32), ("partitions", ctypes.c_int32),
                 ("priority", ctypes.c_int32), ("core_vertices", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("core_entries", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class _Stats(ctypes.Structure):
@@ -207,6 +207,7 @@ class Options:
     partitions: int = 0
     priority: int = 0
     core_vertices: int = 0
+    core_entries: int = 0
 
     def _c(self, stream) -> _Options:
         o = _Options()
@@ -221,6 +222,7 @@ class Options:
         o.partitions = self.partitions
         o.priority = self.priority
         o.core_vertices = self.core_vertices
+        o.core_entries = self.core_entries
         return o
 
 

@@ -105,7 +105,7 @@ struct Context {
     Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, lists, ctl, stats, bitmap, vg, hist;
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
     Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors, st_colors_in, mid0, mid1, rank;
-    Buf core_rec, core_cex, core_cpk, core_items, core_active, core_log, core_pool;
+    Buf core_rec, core_cex, core_c8, core_fbits, core_items, core_active, core_log, core_vwork, core_pool;
     Buf st_cur, st_work, st_next, st_lost;  // gc_det_round staging
     int32_t core_max_v = 0;  // largest core the round kernel's shared memory holds (-1: none)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -116,7 +116,7 @@ struct Context {
     void release_all() {
         Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &lists, &ctl, &stats, &bitmap, &hist,
                       &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors, &st_colors_in, &mid0, &mid1, &rank,
-                      &core_rec, &core_cex, &core_cpk, &core_items, &core_active, &core_log, &core_pool,
+                      &core_rec, &core_cex, &core_c8, &core_fbits, &core_items, &core_active, &core_log, &core_vwork, &core_pool,
                       &st_cur, &st_work, &st_next, &st_lost};
         for (Buf *b : all) b->release();
     }
@@ -429,8 +429,12 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     P.CH = CH;
     P.priority = priority;
     P.prio_rank = pb.prio_rank;
-    // the entries of each worklist's lists are counted for the core hand-over from round 1 on
-    if (mode == GC_MODE_DETERMINISTIC && compact && !(opt && opt->core_vertices < 0)) P.ecnt = ctl->ecnt;
+    // the entries of each worklist's lists are counted for the core hand-over from round 1 on, when
+    // the graph has more entries than the core may take (else the worklist always fits)
+    const int64_t core_E = std::min<int64_t>(
+        pb.nnz, opt && opt->core_entries > 0 ? std::min<int64_t>(opt->core_entries, kCoreEntries) : kCoreEntries);
+    if (mode == GC_MODE_DETERMINISTIC && compact && !(opt && opt->core_vertices < 0) && pb.nnz > core_E)
+        P.ecnt = ctl->ecnt;
 
     const bool timing = (flags & GC_FLAG_TIMING) != 0;
     Ctl h{};
@@ -532,28 +536,33 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
             const int32_t cm = core_max_vertices();
             C.core_max_v = cm > 0 ? cm : -1;
         }
-        // the shared colors hold the core and a sentinel entry after it
-        int64_t M = std::min<int64_t>(n, static_cast<int64_t>(C.core_max_v) - 8);
+        // the shared colors hold the core and a sentinel entry after it, in a multiple of 16 entries
+        int64_t M = std::min<int64_t>(n, static_cast<int64_t>(C.core_max_v) - 16);
         if (core_opt > 0) M = std::min<int64_t>(M, core_opt);
         if (M > 0) {
-            const int64_t E = std::min<int64_t>(pb.nnz, kCoreEntries);
-            const size_t Mp = (static_cast<size_t>(M) + 8) & ~size_t{7};
+            const int64_t E = core_E;
+            const size_t Mp = (static_cast<size_t>(M) + 16) & ~size_t{15};
             Q.max_v = static_cast<int32_t>(Mp);
             Q.max_e = E;
             Q.max_pieces = E / kCorePiece + static_cast<int64_t>(Mp) + 32;
             GC_TRY(ensure(C.core_rec, 4 * kCoreRecWords * Mp, "core records"));
             GC_TRY(ensure(C.core_cex, 2 * 4 * Mp, "core colors"));
-            GC_TRY(ensure(C.core_cpk, 2 * 2 * Mp, "core colors"));
+            GC_TRY(ensure(C.core_c8, 2 * Mp, "core colors"));
+            GC_TRY(ensure(C.core_fbits, 4 * (Mp / 32 + 1), "core final bits"));
             GC_TRY(ensure(C.core_items, 16 * static_cast<size_t>(Q.max_pieces), "core pieces"));
             GC_TRY(ensure(C.core_active, 2 * 4 * static_cast<size_t>(Q.max_pieces), "core active pieces"));
             GC_TRY(ensure(C.core_log, 2 * 8 * Mp, "core change log"));
+            GC_TRY(ensure(C.core_vwork, 2 * 4 * Mp, "core worklists"));
             GC_TRY(ensure(C.core_pool, 4 * static_cast<size_t>(E) + 16, "core rows"));  // + prefetch slack
             Q.rec = C.core_rec.as<unsigned>();
             Q.cex = C.core_cex.as<int32_t>();
-            Q.cpk = C.core_cpk.as<uint16_t>();
+            Q.c8 = C.core_c8.as<uint8_t>();
+            Q.fbits = C.core_fbits.as<unsigned>();
+            GC_CUDA(cudaMemsetAsync(Q.fbits, 0, 4 * (Mp / 32 + 1), s));
             Q.pieces = C.core_items.as<int4>();
             Q.active = C.core_active.as<int32_t>();
             Q.log = C.core_log.as<uint2>();
+            Q.vwork = C.core_vwork.as<int32_t>();
             Q.pool = C.core_pool.as<int32_t>();
             Q.bump = &ctl->core_bump;
             Q.cnt = ctl->core_cnt;

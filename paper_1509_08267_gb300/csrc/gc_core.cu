@@ -8,8 +8,9 @@
 // this phase numbers them 0..m-1 (the core) and rebuilds each one's row as the list of its
 // neighbours that are still on the worklist, in local ids; neighbours already final never change
 // again, so their colors go once into the vertex's window of final colors.  Every block then keeps
-// the colors of all m core vertices in shared memory, 16 bits each (the color saturated at 0x7fff,
-// bit 15 FINAL), so a row's neighbour colors come from shared memory.
+// the colors of all m core vertices in shared memory, 8 bits each (the color saturated at 255; the
+// exact value of a saturated one is read from global memory) and a FINAL bit each, so a row's
+// neighbour colors come from shared memory.
 //
 // The rule is unchanged: in round r a worklist vertex v loses iff a neighbour u with the same color
 // in C_r has a smaller key, and a loser's next color is the least color absent from C_r over its
@@ -47,15 +48,23 @@ constexpr int kCoreWarps = kCoreThreads / 32;
 #endif
 constexpr int kCorePer = GC_CORE_PER;  // entries per lane per step of a piece
 constexpr int kCoreStep = 32 * kCorePer;
-constexpr unsigned kPkFinal = 0x8000u;
-constexpr unsigned kPkSat = 0x7fffu;  // saturated: the color is 32767 or more (exact value in cex)
+constexpr unsigned kSat8 = 255u;  // 8-bit color: 255 or more (exact value in cex)
 constexpr int kFillThreads = 256;
 constexpr int kFillPer = 4;  // entries per lane per step of the row build
-constexpr int kPieceCompact = 1;  // piece flag: compact the piece in place during its next sweep
 
-__device__ __forceinline__ unsigned pack_color(int32_t c, bool fin) {
-    return (c < static_cast<int32_t>(kPkSat) ? static_cast<unsigned>(c) : kPkSat) | (fin ? kPkFinal : 0u);
+__device__ __forceinline__ unsigned sat8(int32_t c) {
+    return c < static_cast<int32_t>(kSat8) ? static_cast<unsigned>(c) : kSat8;
 }
+
+// The core's colors as every block holds them in shared memory: an 8-bit color per vertex and a
+// FINAL bit per vertex; entry m is a sentinel (FINAL, color 255, and not saturated: it reads as no
+// color at all) that the padding slots of a step read.
+struct Shared {
+    uint8_t *col;   // [Mpad]
+    unsigned *fin;  // [Mpad / 32 + 1]
+    __device__ __forceinline__ unsigned color8(uint32_t v) const { return col[v]; }
+    __device__ __forceinline__ unsigned final_bit(uint32_t v) const { return (fin[v >> 5] >> (v & 31)) & 1u; }
+};
 
 __device__ __forceinline__ unsigned *core_rec(const CoreParams &Q, int64_t v) {
     return Q.rec + static_cast<size_t>(v) * kCoreRecWords;
@@ -95,8 +104,8 @@ __device__ void core_init_vertex(const RoundParams &P, const CoreParams &Q, int3
     const int32_t c = color_of(__ldcg(colc + V));
     Q.cex[local] = c;
     Q.cex[Q.max_v + local] = c;
-    Q.cpk[local] = static_cast<uint16_t>(pack_color(c, false));
-    Q.cpk[Q.max_v + local] = static_cast<uint16_t>(pack_color(c, false));
+    Q.c8[local] = static_cast<uint8_t>(sat8(c));
+    Q.c8[Q.max_v + local] = static_cast<uint8_t>(sat8(c));
     const uint4 z = make_uint4(0, 0, 0, 0);
 #pragma unroll
     for (int w = 0; w < 32; w += 4) stcg4(rec + w, z);
@@ -216,11 +225,12 @@ __global__ void __launch_bounds__(kFillThreads) core_fill_kernel(RoundParams P, 
                 loc[q] = -1;
                 if (st[q] != kNoNeighbour && !final_of(st[q])) loc[q] = __ldcg(P.items + r.vbase + ul[q]);
             }
+            uint32_t ev[kFillPer];
+            unsigned keepm = 0;
 #pragma unroll
             for (int q = 0; q < kFillPer; ++q) {
                 const int64_t j = j0 + lane + 32 * q;
-                bool keep = false;
-                uint32_t e = 0;
+                ev[q] = 0;
                 if (st[q] != kNoNeighbour) {
                     if (final_of(st[q])) {
                         const int32_t c = color_of(st[q]);
@@ -229,21 +239,28 @@ __global__ void __launch_bounds__(kFillThreads) core_fill_kernel(RoundParams P, 
                         else if (static_cast<unsigned>(c) < 32u * kAccWords)
                             atomicOr(&wfin[c >> 5], 1u << (c & 31));
                     } else if (static_cast<unsigned>(loc[q]) < m) {
-                        keep = true;
+                        keepm |= 1u << q;
                         const bool smaller = key_less_in(prio_of(st[q]), pv, static_cast<uint32_t>(ul[q]),
                                                          static_cast<uint32_t>(r.lv), P, V);
-                        e = static_cast<uint32_t>(loc[q]) | (smaller ? kCoreSmaller : 0u);
+                        ev[q] = static_cast<uint32_t>(loc[q]) | (smaller ? kCoreSmaller : 0u);
                     } else {
                         // every vertex that is not final is on the worklist; anything else is a bug
                         set_error(P.err, GC_ERR_INVALID_GRAPH, V, j);
                     }
                 }
-                const unsigned km = __ballot_sync(kFull, keep);
-                if (km) {
-                    unsigned pos = 0;
-                    if (lane == 0) pos = atomicAdd(rec + kCoreFill, static_cast<unsigned>(__popc(km)));
-                    pos = __shfl_sync(kFull, pos, 0);
-                    if (keep) dst[pos + __popc(km & lanemask_lt())] = static_cast<int32_t>(e);
+            }
+            // one reservation per step for the entries kept
+            const unsigned kept = __reduce_add_sync(kFull, static_cast<unsigned>(__popc(keepm)));
+            if (kept) {
+                unsigned pos = 0;
+                if (lane == 0) pos = atomicAdd(rec + kCoreFill, kept);
+                pos = __shfl_sync(kFull, pos, 0);
+#pragma unroll
+                for (int q = 0; q < kFillPer; ++q) {
+                    const bool keep = (keepm >> q) & 1u;
+                    const unsigned km = __ballot_sync(kFull, keep);
+                    if (keep) dst[pos + __popc(km & lanemask_lt())] = static_cast<int32_t>(ev[q]);
+                    pos += __popc(km);
                 }
             }
         }
@@ -288,29 +305,34 @@ __device__ int32_t core_mex_from(const RoundParams &P, const uint64_t *col_r0, i
     }
 }
 
-// Entry m of the shared colors: a vertex that is FINAL with a color past every window, which the
-// padding slots of a step read (it changes no window, no flag and no count of survivors).
-constexpr uint16_t kPkSentinel = static_cast<uint16_t>(kPkFinal | kPkSat);
-
-// Shared-memory copy of packed colors [0, m) (16-byte loads; the buffers hold a multiple of 8 that
-// exceeds m), then the sentinel at m (written by the thread that stored its 16-byte group).
-__device__ __forceinline__ void load_packed(uint16_t *s_pk, const uint16_t *src, int32_t m) {
-    const int32_t n8 = (m + 7) >> 3;
-    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-    uint4 *d4 = reinterpret_cast<uint4 *>(s_pk);
-    for (int32_t i = threadIdx.x; i < n8; i += blockDim.x) d4[i] = __ldcg(s4 + i);
-    if (threadIdx.x == static_cast<unsigned>((m >> 3) % static_cast<int32_t>(blockDim.x))) s_pk[m] = kPkSentinel;
+// Shared copy of the colors and FINAL bits of [0, m) (16-byte loads; the buffers hold a multiple of
+// 16 that exceeds m), then the sentinel at m.  Ends with a block barrier.
+__device__ __forceinline__ void load_shared(const Shared &S, const CoreParams &Q, const uint8_t *c8, int32_t m) {
+    const int32_t n16 = (m + 15) >> 4;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(c8);
+    uint4 *d4 = reinterpret_cast<uint4 *>(S.col);
+    for (int32_t i = threadIdx.x; i < n16; i += blockDim.x) d4[i] = __ldcg(s4 + i);
+    const int32_t nw = (m >> 5) + 1;
+    for (int32_t i = threadIdx.x; i < nw; i += blockDim.x) S.fin[i] = __ldcg(Q.fbits + i);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        S.col[m] = static_cast<uint8_t>(kSat8);
+        S.fin[m >> 5] |= 1u << (m & 31);
+    }
+    __syncthreads();
 }
 
 // New shared colors of the vertices the previous round finished, from its change log.
-__device__ __forceinline__ void apply_log(uint16_t *s_pk, const uint2 *log, unsigned n) {
+__device__ __forceinline__ void apply_log(const Shared &S, const uint2 *log, unsigned n) {
     for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
         const uint2 x = __ldcg(log + i);
-        s_pk[x.x] = static_cast<uint16_t>(x.y);
+        S.col[x.x] = static_cast<uint8_t>(x.y & 0xffu);
+        if (x.y >> 8) atomicOr(&S.fin[x.x >> 5], 1u << (x.x & 31));
     }
 }
 
-// A piece of a row: {local vertex, pool offset, entries, flags}.
+// A piece of a row: {local vertex, pool offset, entries, worklist size when it last dropped its FINAL
+// neighbours (the hand-over's m at first)}.
 struct Piece {
     int32_t v, off, cnt, flags;
 };
@@ -388,63 +410,59 @@ __device__ __forceinline__ void load_piece_step(const CoreParams &Q, const Piece
 }
 
 // One step of a piece: every slot's neighbour color into the round window (colors below 128 in
-// two per-lane registers, the warp's shared window up to 512), the conflict flag (a smaller-key
-// neighbour with the vertex's color cpk, which is not saturated here), and the number of FINAL slots
-// (the sentinel counts as one).  COMPACT: the colors of FINAL neighbours also into the final window,
-// and the slots kept.  All eight colors are read before any is used.
+// two per-lane registers, the warp's shared window up to 512) and the conflict flag (a neighbour with
+// a smaller key and the vertex's color cv).  COMPACT: also the FINAL slots (counted, the sentinel as
+// one; their colors into the final window) and the slots kept.
+// Saturated 8-bit colors (255, but not the sentinel) are looked up exactly in cex.
 template <bool COMPACT>
-__device__ __forceinline__ void consume_step(const uint16_t *s_pk, const int32_t (&e)[kCorePer], unsigned cpk,
-                                             uint64_t &lo, uint64_t &mid, uint64_t &flo, unsigned *win,
-                                             unsigned *wfin, unsigned &conflict, unsigned &nfin, unsigned &keepm) {
-    unsigned sv[kCorePer];
+__device__ __forceinline__ void consume_step(const Shared &S, const int32_t (&e)[kCorePer], int32_t m, int32_t cv,
+                                             const int32_t *cex_cur, uint64_t &lo, uint64_t &mid, uint64_t &flo,
+                                             unsigned *win, unsigned *wfin, unsigned &conflict, unsigned &nfin,
+                                             unsigned &keepm) {
+    unsigned cs[kCorePer];
 #pragma unroll
-    for (int q = 0; q < kCorePer; ++q) sv[q] = s_pk[static_cast<uint32_t>(e[q]) & ~kCoreSmaller];
+    for (int q = 0; q < kCorePer; ++q) cs[q] = S.color8(static_cast<uint32_t>(e[q]) & ~kCoreSmaller);
+    // an 8-bit color below 255 equals cv only when it is cv; 255 is compared exactly below
+    const unsigned cv8 = cv < static_cast<int32_t>(kSat8) ? static_cast<unsigned>(cv) : 0x1000u;
+    unsigned sat = 0;
 #pragma unroll
     for (int q = 0; q < kCorePer; ++q) {
-        const unsigned c = sv[q] & kPkSat;
-        const unsigned fin = sv[q] >> 15;
+        const uint32_t id = static_cast<uint32_t>(e[q]) & ~kCoreSmaller;
+        const unsigned c = cs[q];
         const uint64_t b = 1ull << (c & 63u);
         if (c < 64u) {
             lo |= b;
         } else if (c < 128u) {
             mid |= b;
-        } else if (c < 32u * kAccWords) {
+        } else if (c < kSat8) {
             atomicOr(&win[c >> 5], 1u << (c & 31));
         }
-        conflict |= (static_cast<uint32_t>(e[q]) >> 31) & static_cast<unsigned>(c == cpk);
-        nfin += fin;
+        conflict |= (static_cast<uint32_t>(e[q]) >> 31) & static_cast<unsigned>(c == cv8);
+        sat |= static_cast<unsigned>(c == kSat8 && id != static_cast<uint32_t>(m)) << q;
         if constexpr (COMPACT) {
-            if (fin) {
+            const unsigned fin = S.final_bit(id);
+            nfin += fin;
+            if (fin && c < kSat8) {
                 if (c < 64u)
                     flo |= b;
-                else if (c < 32u * kAccWords)
+                else
                     atomicOr(&wfin[c >> 5], 1u << (c & 31));
             }
             keepm |= (fin ^ 1u) << q;
         }
     }
-}
-
-// The same for a vertex whose own color is saturated (32767 or more): equal packed colors are
-// compared exactly.
-__device__ __noinline__ void consume_step_sat(const uint16_t *s_pk, const int32_t (&e)[kCorePer], int32_t cvx,
-                                              const int32_t *cex_cur, bool compact, uint64_t &flo, unsigned *wfin,
-                                              unsigned &conflict, unsigned &nfin, unsigned &keepm) {
-    for (int q = 0; q < kCorePer; ++q) {
-        const uint32_t id = static_cast<uint32_t>(e[q]) & ~kCoreSmaller;
-        const unsigned s = s_pk[id];
-        const unsigned c = s & kPkSat;
-        const unsigned fin = s >> 15;
-        if (e[q] < 0 && c == kPkSat && __ldcg(cex_cur + id) == cvx) conflict = 1u;
-        nfin += fin;
-        if (compact) {
-            if (fin) {
-                if (c < 64u)
-                    flo |= 1ull << c;
-                else if (c < 32u * kAccWords)
-                    atomicOr(&wfin[c >> 5], 1u << (c & 31));
+    if (sat) {
+        // rare: colors of 255 and more, exactly
+#pragma unroll 1
+        for (int q = 0; q < kCorePer; ++q) {
+            if (!((sat >> q) & 1u)) continue;
+            const uint32_t id = static_cast<uint32_t>(e[q]) & ~kCoreSmaller;
+            const int32_t c = __ldcg(cex_cur + id);
+            if (static_cast<unsigned>(c) < 32u * kAccWords) {
+                atomicOr(&win[c >> 5], 1u << (c & 31));
+                if (COMPACT && S.final_bit(id)) atomicOr(&wfin[c >> 5], 1u << (c & 31));
             }
-            keepm |= (fin ^ 1u) << q;
+            if (e[q] < 0 && c == cv) conflict = 1u;
         }
     }
 }
@@ -455,8 +473,8 @@ __device__ __noinline__ void consume_step_sat(const uint16_t *s_pk, const int32_
 // smaller-key neighbour with the vertex's color) and, when the piece compacts, the window of final
 // colors of the neighbours it drops; then ORed into the vertex's record.
 template <bool BATCH>
-__device__ void core_phase_a(const CoreParams &Q, const uint16_t *s_pk, const int32_t *cex_cur, const int32_t *list,
-                             unsigned nact, int32_t m, unsigned gw, unsigned nw, int lane, unsigned *win,
+__device__ void core_phase_a(const CoreParams &Q, const Shared &S, const int32_t *cex_cur, const int32_t *list,
+                             unsigned nact, int32_t m, unsigned nv, unsigned gw, unsigned nw, int lane, unsigned *win,
                              unsigned *wfin, unsigned &st_read) {
     PieceCursor cur;
     cur.base = gw;
@@ -474,10 +492,11 @@ __device__ void core_phase_a(const CoreParams &Q, const uint16_t *s_pk, const in
             wfin[lane] = 0u;
         }
         __syncwarp();
-        const unsigned cpk = s_pk[p.v] & kPkSat;  // own color (a worklist vertex is never final)
-        const bool sat = cpk == kPkSat;
-        const int32_t cvx = sat ? __ldcg(cex_cur + p.v) : static_cast<int32_t>(cpk);
-        const bool compact = (p.flags & kPieceCompact) != 0;
+        const unsigned own8 = S.color8(static_cast<uint32_t>(p.v));  // own color (never final on the worklist)
+        const int32_t cv = own8 == kSat8 ? __ldcg(cex_cur + p.v) : static_cast<int32_t>(own8);
+        // a piece drops its FINAL neighbours in place once the worklist has lost a quarter of its
+        // vertices since the piece last did (its `flags` field records that worklist size)
+        const bool compact = 4ull * nv < 3ull * static_cast<unsigned>(p.flags);
         uint64_t lo = 0, mid = 0, flo = 0;
         unsigned conflict = 0;
         unsigned kept_total = 0;  // entries kept so far (the compaction position)
@@ -495,17 +514,11 @@ __device__ void core_phase_a(const CoreParams &Q, const uint16_t *s_pk, const in
             int32_t en[kCorePer];
             if (more) load_piece_step(Q, pn, jn, lane, m, en);
             unsigned nfin = 0, keepm = 0;
-            if (sat) {
-                // window first (the saturated color is never in it), then the exact comparisons
-                consume_step<false>(s_pk, e, kPkSat + 1u, lo, mid, flo, win, wfin, conflict, nfin, keepm);
-                nfin = 0;
-                consume_step_sat(s_pk, e, cvx, cex_cur, compact, flo, wfin, conflict, nfin, keepm);
-            } else if (compact) {
-                consume_step<true>(s_pk, e, cpk, lo, mid, flo, win, wfin, conflict, nfin, keepm);
-            } else {
-                consume_step<false>(s_pk, e, cpk, lo, mid, flo, win, wfin, conflict, nfin, keepm);
-            }
-            const unsigned kept = static_cast<unsigned>(kCoreStep) - __reduce_add_sync(kFull, nfin);
+            if (compact)
+                consume_step<true>(S, e, m, cv, cex_cur, lo, mid, flo, win, wfin, conflict, nfin, keepm);
+            else
+                consume_step<false>(S, e, m, cv, cex_cur, lo, mid, flo, win, wfin, conflict, nfin, keepm);
+            const unsigned kept = compact ? static_cast<unsigned>(kCoreStep) - __reduce_add_sync(kFull, nfin) : 0u;
             if (compact && kept) {
                 // in place: the positions written never pass the ones already read
                 unsigned pos = kept_total;
@@ -538,11 +551,9 @@ __device__ void core_phase_a(const CoreParams &Q, const uint16_t *s_pk, const in
                 if (lane == 0) {
                     if (lose) atomicOr(rec + kCoreFlag, 1u);
                     st_read += static_cast<unsigned>(p.cnt);
-                    const int32_t ncnt = compact ? static_cast<int32_t>(kept_total) : p.cnt;
-                    // compact during the next sweep once a quarter of the entries are final
-                    const int32_t nflags = 4ll * kept_total < 3ll * ncnt ? kPieceCompact : 0;
-                    if (ncnt != p.cnt || nflags != p.flags)
-                        reinterpret_cast<int2 *>(Q.pieces + pidx)[1] = make_int2(ncnt, nflags);
+                    if (compact)
+                        reinterpret_cast<int2 *>(Q.pieces + pidx)[1] =
+                            make_int2(static_cast<int32_t>(kept_total), static_cast<int32_t>(nv));
                 }
                 __syncwarp();
             }
@@ -557,27 +568,27 @@ __device__ void core_phase_a(const CoreParams &Q, const uint16_t *s_pk, const in
     }
 }
 
-// Phase B of one round: one thread per worklist vertex v (v = blockIdx.x * 1024 + threadIdx.x + k *
-// gridDim.x * 1024): the merged record tells whether v lost, and the colors around it; a loser takes
-// the least color absent from both windows (its full row is rescanned past 512 colors), a winner
-// becomes FINAL.  Both color buffers are written (C_{r+1}, and a winner's FINAL bit into C_r's packed
-// copy too), the vertex goes into the change log, a loser's pieces into the next round's list, and
-// the record's round part is cleared.  Positions in the log and the list are reserved per block (one
-// global atomic each), not per warp.
+// Phase B of one round: one lane per worklist vertex (the round's vertex list, 32 entries per warp,
+// the warps interleaved over the SMs): the merged record tells whether v lost, and the colors around
+// it; a loser takes the least color absent from both windows (its full row is rescanned past 512
+// colors), a winner becomes FINAL.  Both color buffers are written (C_{r+1}; a winner's FINAL bit into
+// the bitmap), the vertex goes into the change log, a loser into the next round's vertex list and its
+// pieces into the next round's piece list, and the record's round part is cleared.
 template <bool BATCH>
-__device__ void core_phase_b(const RoundParams &P, const CoreParams &Q, const uint16_t *s_pk, int32_t m, int pass,
-                             const uint64_t *col_r0, unsigned *cn, int lane, unsigned *win, unsigned *s_res,
-                             unsigned &st_deg, unsigned &st_cnt, unsigned &n_lose) {
+__device__ void core_phase_b(const RoundParams &P, const CoreParams &Q, const Shared &S, const int32_t *vlist,
+                             unsigned nv, int pass, const uint64_t *col_r0, unsigned *cn, unsigned gw, unsigned nw,
+                             int lane, unsigned *win, unsigned &st_deg, unsigned &st_cnt) {
     const int cur = pass & 1;
     const int32_t *cex_cur = Q.cex + static_cast<size_t>(cur) * Q.max_v;
     uint2 *log_next = Q.log + static_cast<size_t>(cur ^ 1) * Q.max_v;
     int32_t *act_next = Q.active + static_cast<size_t>(cur ^ 1) * Q.max_pieces;
-    for (int64_t vb = static_cast<int64_t>(blockIdx.x) * blockDim.x; vb < m;
-         vb += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int32_t v = static_cast<int32_t>(vb + threadIdx.x);
-        const unsigned pk = v < m ? s_pk[v] : kPkFinal;
-        const bool act = !(pk & kPkFinal);
-        unsigned *rec = core_rec(Q, v < m ? v : 0);
+    int32_t *vlist_next = Q.vwork + static_cast<size_t>(cur ^ 1) * Q.max_v;
+    for (int64_t ib = static_cast<int64_t>(gw) * 32; ib < nv; ib += static_cast<int64_t>(nw) * 32) {
+        const int64_t i = ib + lane;
+        const bool act = i < nv;
+        const int32_t v = act ? (vlist ? __ldcg(vlist + i) : static_cast<int32_t>(i)) : 0;
+        const unsigned own8 = act ? S.color8(static_cast<uint32_t>(v)) : 0u;
+        unsigned *rec = core_rec(Q, v);
         uint4 w[kAccWords / 4];
         bool lose = false;
         uint4 meta = make_uint4(0, 0, 0, 0);
@@ -599,8 +610,7 @@ __device__ void core_phase_b(const RoundParams &P, const CoreParams &Q, const ui
                 pe = __ldcg(rec + kCorePcEnd);
             }
         }
-        const unsigned cpk = pk & kPkSat;
-        const int32_t cv = cpk == kPkSat && act ? __ldcg(cex_cur + v) : static_cast<int32_t>(cpk);
+        const int32_t cv = own8 == kSat8 ? __ldcg(cex_cur + v) : static_cast<int32_t>(own8);
         int32_t nc = cv;
         if (lose) {
             nc = -1;
@@ -617,8 +627,9 @@ __device__ void core_phase_b(const RoundParams &P, const CoreParams &Q, const ui
                                                    cex_cur, win, lane, 32 * kAccWords);
             if (lane == l) nc = x;
         }
-        // reservations: the warp's share of the block's, then one global atomic per block
+        // positions in the log, the next vertex list and the next piece list: one reservation each per warp
         const unsigned am = __ballot_sync(kFull, act);
+        const unsigned lm = __ballot_sync(kFull, lose);
         const unsigned npc = pe - pb;
         unsigned incl = npc;
 #pragma unroll
@@ -627,39 +638,39 @@ __device__ void core_phase_b(const RoundParams &P, const CoreParams &Q, const ui
             if (lane >= o) incl += y;
         }
         const unsigned total = __shfl_sync(kFull, incl, 31);
-        unsigned wl = 0, wa = 0;
+        unsigned lb = 0, ab = 0, vb = 0;
         if (lane == 0) {
-            if (am) wl = atomicAdd(&s_res[0], static_cast<unsigned>(__popc(am)));
-            if (total) wa = atomicAdd(&s_res[1], total);
+            if (am) lb = atomicAdd(cn, static_cast<unsigned>(__popc(am)));
+            if (lm) vb = atomicAdd(cn + 1, static_cast<unsigned>(__popc(lm)));
+            if (total) ab = atomicAdd(cn + 2, total);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            s_res[2] = s_res[0] ? atomicAdd(cn, s_res[0]) : 0u;
-            s_res[3] = s_res[1] ? atomicAdd(cn + 2, s_res[1]) : 0u;
-            s_res[0] = 0u;
-            s_res[1] = 0u;
-        }
-        __syncthreads();
-        const unsigned lb = s_res[2] + __shfl_sync(kFull, wl, 0), ab = s_res[3] + __shfl_sync(kFull, wa, 0);
+        lb = __shfl_sync(kFull, lb, 0);
+        vb = __shfl_sync(kFull, vb, 0);
+        ab = __shfl_sync(kFull, ab, 0);
         if (act) {
-            const unsigned npk = pack_color(nc, !lose);
+            const unsigned n8 = sat8(nc);
             Q.cex[static_cast<size_t>(cur ^ 1) * Q.max_v + v] = nc;
-            Q.cpk[static_cast<size_t>(cur ^ 1) * Q.max_v + v] = static_cast<uint16_t>(npk);
-            if (!lose) Q.cpk[static_cast<size_t>(cur) * Q.max_v + v] = static_cast<uint16_t>(npk);
-            log_next[lb + __popc(am & lanemask_lt())] = make_uint2(static_cast<unsigned>(v), npk);
-            for (unsigned k = 0; k < npc; ++k) act_next[ab + incl - npc + k] = static_cast<int32_t>(pb + k);
+            Q.c8[static_cast<size_t>(cur ^ 1) * Q.max_v + v] = static_cast<uint8_t>(n8);
+            if (!lose) atomicOr(Q.fbits + (v >> 5), 1u << (v & 31));  // final for good: one bitmap
+            log_next[lb + __popc(am & lanemask_lt())] = make_uint2(static_cast<unsigned>(v), n8 | (lose ? 0u : 0x100u));
+            if (lose) vlist_next[vb + __popc(lm & lanemask_lt())] = v;
             const uint4 z = make_uint4(0, 0, 0, 0);
 #pragma unroll
             for (int c = 0; c < kAccWords; c += 4) stcg4(rec + c, z);
             if (lose) rec[kCoreFlag] = 0u;
             st_deg += meta.z;
             st_cnt += 1;
-            if (lose) ++n_lose;
             if constexpr (BATCH) {
                 if (lose) note_graph_round(P, static_cast<int32_t>(__ldcg(rec + kCoreG)), pass + 1);
             }
         }
-        __syncthreads();  // s_res[2..3] are read before the next iteration reserves again
+        // the losers' pieces, written by the whole warp one vertex at a time
+        for (unsigned pm = __ballot_sync(kFull, npc > 0u); pm; pm &= pm - 1u) {
+            const int l = __ffs(pm) - 1;
+            const unsigned b0 = __shfl_sync(kFull, pb, l), k0 = __shfl_sync(kFull, npc, l);
+            const unsigned at = ab + __shfl_sync(kFull, incl, l) - k0;
+            for (unsigned k = lane; k < k0; k += 32) act_next[at + k] = static_cast<int32_t>(b0 + k);
+        }
     }
 }
 
@@ -677,20 +688,22 @@ __device__ unsigned long long g_core_prof[8 * 4096];
 // colors of the core in dynamic shared memory.
 template <bool BATCH>
 __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams P, CoreParams Q) {
-    extern __shared__ __align__(16) uint16_t s_pk[];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ unsigned s_win[kCoreWarps][kAccWords];
     __shared__ unsigned s_fin[kCoreWarps][kAccWords];
-    __shared__ unsigned s_cnt[1];
-    __shared__ unsigned s_res[4];
     if (__ldcg(P.core_go) == 0) return;
     const HandOver h = hand_over(P);
     const int R0 = h.R0;
     const int32_t m = static_cast<int32_t>(h.nsmall + __ldcg(Q.m));
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
-    const unsigned gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    // work is dealt to warps interleaved over the blocks, so a small round spreads over every SM
+    const unsigned gw = static_cast<unsigned>(wib) * gridDim.x + blockIdx.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) Q.m[1] = static_cast<unsigned>(m);  // for the write-back
-    load_packed(s_pk, Q.cpk + static_cast<size_t>(R0 & 1) * Q.max_v, m);
+    Shared S;
+    S.col = s_dyn;
+    S.fin = reinterpret_cast<unsigned *>(s_dyn + Q.max_v);
+    load_shared(S, Q, Q.c8 + static_cast<size_t>(R0 & 1) * Q.max_v, m);
     {
         // the pieces of every row: consecutive pieces of a row go to consecutive warps
         const unsigned stride = gridDim.x * blockDim.x;
@@ -725,7 +738,7 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
                 const unsigned lb = k * kCorePiece;
                 Q.pieces[b + incl - np + k] =
                     make_int4(static_cast<int32_t>(v), static_cast<int32_t>(off + lb),
-                              static_cast<int32_t>(min(len - lb, static_cast<unsigned>(kCorePiece))), 0);
+                              static_cast<int32_t>(min(len - lb, static_cast<unsigned>(kCorePiece))), m);
             }
         }
     }
@@ -745,7 +758,6 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
                 break;
             }
             if (blockIdx.x == 0 && threadIdx.x < 4) Q.cnt[4 * ((pass + 2) % 3) + threadIdx.x] = 0u;
-            if (threadIdx.x == 0) s_cnt[0] = 0u;
             CORE_PROF(0, atomicMin);
 #ifdef GC_CORE_PROFILE
             if (blockIdx.x == 0 && threadIdx.x == 0 && pass - R0 < 4096) g_core_prof[8 * (pass - R0) + 7] = nv;
@@ -754,18 +766,18 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
             if (pass > R0) {
                 // the vertices the previous round finished: its change log, or all colors when they are many
                 const unsigned nprev = __ldcg(cc);
-                if (4ull * nprev > static_cast<unsigned long long>(m))
-                    load_packed(s_pk, Q.cpk + static_cast<size_t>(pass & 1) * Q.max_v, m);
+                if (8ull * nprev > static_cast<unsigned long long>(m))
+                    load_shared(S, Q, Q.c8 + static_cast<size_t>(pass & 1) * Q.max_v, m);
                 else
-                    apply_log(s_pk, Q.log + static_cast<size_t>(pass & 1) * Q.max_v, nprev);
+                    apply_log(S, Q.log + static_cast<size_t>(pass & 1) * Q.max_v, nprev);
             }
             __syncthreads();
             CORE_PROF(1, atomicMax);
-            unsigned st_deg = 0, st_cnt = 0, st_read = 0, n_lose = 0;
+            unsigned st_deg = 0, st_cnt = 0, st_read = 0;
             // the round's pieces: all of them in the first round, then those the previous round listed
             const int32_t *list = pass == R0 ? nullptr : Q.active + static_cast<size_t>(pass & 1) * Q.max_pieces;
             const unsigned nact = pass == R0 ? npieces : __ldcg(cc + 2);
-            core_phase_a<BATCH>(Q, s_pk, cex_cur, list, nact, m, gw, nw, lane, s_win[wib], s_fin[wib], st_read);
+            core_phase_a<BATCH>(Q, S, cex_cur, list, nact, m, nv, gw, nw, lane, s_win[wib], s_fin[wib], st_read);
 #ifdef GC_CORE_PROFILE
             __syncthreads();
             CORE_PROF(2, atomicMin);
@@ -773,18 +785,14 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
 #endif
             if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
             CORE_PROF(4, atomicMax);
-            if (threadIdx.x < 2) s_res[threadIdx.x] = 0u;
-            __syncthreads();
-            core_phase_b<BATCH>(P, Q, s_pk, m, pass, h.colc, cn, lane, s_win[wib], s_res, st_deg, st_cnt, n_lose);
+            // the round's vertices: every core vertex in the first round, then the previous round's losers
+            const int32_t *vlist = pass == R0 ? nullptr : Q.vwork + static_cast<size_t>(pass & 1) * Q.max_v;
+            core_phase_b<BATCH>(P, Q, S, vlist, nv, pass, h.colc, cn, gw, nw, lane, s_win[wib], st_deg, st_cnt);
 #ifdef GC_CORE_PROFILE
             __syncthreads();
             CORE_PROF(5, atomicMax);
 #endif
-            const unsigned lose_w = __reduce_add_sync(kFull, n_lose);
-            if (lane == 0 && lose_w) atomicAdd(&s_cnt[0], lose_w);
             if (P.stats) flush_stats(P, pass, st_deg, st_cnt, st_read);
-            __syncthreads();
-            if (threadIdx.x == 0 && s_cnt[0]) atomicAdd(cn + 1, s_cnt[0]);
             if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
         }
     }
@@ -808,6 +816,8 @@ __global__ void core_writeback_kernel(RoundParams P, CoreParams Q) {
     }
 }
 
+size_t core_smem_bytes(int64_t max_v) { return static_cast<size_t>(max_v) + 4 * static_cast<size_t>(max_v / 32 + 1); }
+
 int core_static_smem(bool batch) {
     cudaFuncAttributes a{};
     const void *f = batch ? reinterpret_cast<const void *>(&core_round_kernel<true>)
@@ -830,9 +840,9 @@ int32_t core_max_vertices() {
     }
     const int st = std::max(core_static_smem(false), core_static_smem(true));
     if (st < 0) return 0;
-    // the largest multiple of 64 vertices whose colors (2 bytes each) leave one block resident per SM
-    for (int64_t m = ((static_cast<int64_t>(optin) - st) / 2) & ~int64_t{63}; m >= 64; m -= 1024) {
-        const int smem = static_cast<int>(2 * m);
+    // the largest multiple of 64 vertices whose colors and FINAL bits leave one block resident per SM
+    for (int64_t m = ((static_cast<int64_t>(optin) - st - 4) * 8 / 9) & ~int64_t{63}; m >= 64; m -= 1024) {
+        const int smem = static_cast<int>(core_smem_bytes(m));
         bool ok = true;
         for (int b = 0; b < 2 && ok; ++b) {
             const void *f = b ? reinterpret_cast<const void *>(&core_round_kernel<true>)
@@ -853,7 +863,7 @@ cudaError_t launch_core(const RoundParams &P, const CoreParams &Q, bool batch, c
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const size_t smem = 2 * static_cast<size_t>(Q.max_v);
+    const size_t smem = core_smem_bytes(Q.max_v);
     const void *round_fn = batch ? reinterpret_cast<const void *>(&core_round_kernel<true>)
                                  : reinterpret_cast<const void *>(&core_round_kernel<false>);
     e = cudaFuncSetAttribute(round_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));

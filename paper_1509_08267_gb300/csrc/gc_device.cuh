@@ -370,6 +370,19 @@ __device__ __forceinline__ int32_t next_items(const RoundParams &P, int64_t len,
     return items > 0 ? static_cast<int32_t>(items) : 1;
 }
 
+// Adds every thread's x to *dst: a block reduction, then one atomic per block (every thread of the
+// block calls it).
+__device__ __forceinline__ void flush_sum(unsigned long long *dst, unsigned long long x) {
+    __shared__ unsigned long long s_sum;
+    if (threadIdx.x == 0) s_sum = 0;
+    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_sum, x);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_sum) atomicAdd(dst, s_sum);
+}
+
 // Per-round statistics of a round kernel (GC_FLAG_STATS).
 __device__ __forceinline__ void flush_stats(const RoundParams &P, int pass, unsigned long long deg,
                                             unsigned long long cnt, unsigned long long reads) {

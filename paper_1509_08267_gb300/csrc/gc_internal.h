@@ -140,9 +140,10 @@ struct RoundParams {
 // and their rows are rebuilt as lists of the local ids of neighbours still on the worklist, the
 // neighbour's key order in the top bit (kCoreSmaller: smaller key than the row's vertex); the colors
 // of neighbours already final go into the vertex's window of final colors.  Each round every block
-// keeps the colors of all m core vertices in shared memory (16 bits each: the color saturated at
-// 0x7fff, bit 15 FINAL), so a row's neighbour colors come from shared memory instead of L2.  Rows
-// are cut once into pieces of at most kCorePiece entries that the warps own for the whole phase.
+// keeps the colors of all m core vertices in shared memory (8 bits each, saturated at 255, the exact
+// value in cex; and a FINAL bit each), so a row's neighbour colors come from shared memory instead
+// of L2.  Rows are cut once into pieces of at most kCorePiece entries, which every round's list of
+// active pieces hands out to the warps.
 constexpr uint32_t kCoreSmaller = 0x80000000u;
 constexpr int64_t kCoreEntries = int64_t{1} << 27;  // list entries the core phase takes at most
 #ifndef GC_CORE_PIECE
@@ -157,15 +158,18 @@ constexpr int kCoreFlag = 16;
 constexpr int kCoreOffLo = 48, kCoreOffHi = 49, kCoreDeg = 50, kCoreGid = 51, kCoreFill = 52, kCoreG = 53;
 constexpr int kCoreListLo = 54, kCoreListHi = 55, kCoreListLen = 56, kCorePcBeg = 57, kCorePcEnd = 58;
 struct CoreParams {
-    int32_t max_v;        // vertex capacity M (shared memory holds M 16-bit colors; a multiple of 8)
+    int32_t max_v;        // vertex capacity M (shared memory holds M 8-bit colors and M FINAL bits; a
+                          // multiple of 16)
     int64_t max_e;        // list entries the core may hold (the pool's size)
     int64_t max_pieces;   // piece capacity: max_e / kCorePiece + M
     unsigned *rec;        // [M][kCoreRecWords]
     int32_t *cex;         // [2][M] exact colors, double-buffered like col0 / col1
-    uint16_t *cpk;        // [2][M] packed colors (color saturated at 0x7fff, bit 15 FINAL)
+    uint8_t *c8;          // [2][M] colors saturated at 255, double-buffered like cex
+    unsigned *fbits;      // [M / 32 + 1] FINAL bit of every core vertex (zero at hand-over)
     int4 *pieces;         // [max_pieces] {local vertex, pool offset, entries, flags}
     int32_t *active;      // [2][max_pieces] the pieces of each round's worklist vertices
-    uint2 *log;           // [2][M] {local vertex, packed color} of the vertices a round finished
+    int32_t *vwork;       // [2][M] each round's worklist vertices (after the first round)
+    uint2 *log;           // [2][M] {local vertex, 8-bit color | FINAL << 8} of the vertices a round finished
     int32_t *pool;        // [max_e] the rows
     unsigned long long *bump;  // pool allocation counter
     unsigned *cnt;        // [3][4] per-round counters: vertices finished (log entries), losers, active pieces

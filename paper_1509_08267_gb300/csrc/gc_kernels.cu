@@ -151,13 +151,21 @@ __device__ __forceinline__ void load4(const int32_t *colidx, bool vec, int64_t j
     }
 }
 
+// The state word a neighbour (local id ul) has when round 1 of the deterministic mode reads it with
+// the hash priority: color 0 (C_1), not final (only isolated vertices are, and they are nobody's
+// neighbour) and the top 31 bits of its hash: recomputed from the id instead of gathered.
+__device__ __forceinline__ uint64_t round1_state(uint64_t seed, int32_t ul) {
+    return pack_state(0, static_cast<uint32_t>(vertex_hash(seed, static_cast<uint32_t>(ul)) >> 33), false);
+}
+
 // Per-thread sweep of a short row (degree <= T1 <= 127): window [0, 128) in two 64-bit masks (the
 // least free color is at most deg(v)) and conflict flag.  Four entries per step from the aligned
 // group of four that holds the row's first entry; the next step's entries are loaded before the
 // current step's gathers are consumed.
 template <bool BATCH, bool WINDOW, bool CONFLICT>
 __device__ __forceinline__ void sweep_small(const RoundParams &P, const Row &r, const uint64_t *colc, int32_t cv,
-                                            uint32_t pv, uint64_t &mask0, uint64_t &mask1, bool &lose) {
+                                            uint32_t pv, uint64_t &mask0, uint64_t &mask1, bool &lose,
+                                            bool r1 = false, uint64_t r1seed = 0) {
     constexpr int kT = 4;  // entries per step
     const bool vec = (reinterpret_cast<uintptr_t>(P.colidx) & 15u) == 0;
     int64_t j0 = vec ? (r.b & ~int64_t{3}) : r.b;
@@ -170,7 +178,7 @@ __device__ __forceinline__ void sweep_small(const RoundParams &P, const Row &r, 
             w[q] = kNoNeighbour;
             if (j0 + q >= r.b && j0 + q < r.e) {
                 const int32_t U = neighbour(P, r, ul[q], j0 + q);
-                if (U >= 0) w[q] = load_state(colc + U);
+                if (U >= 0) w[q] = r1 ? round1_state(r1seed, ul[q]) : load_state(colc + U);
             }
         }
         const bool more = j0 + kT < r.e;
@@ -260,7 +268,7 @@ __device__ __forceinline__ void det_write(const uint64_t *colc, uint64_t *coln, 
 // One vertex of degree <= T1 (one thread): did it lose in this round; writes its next state.
 template <bool BATCH>
 __device__ __forceinline__ bool det_small(const RoundParams &P, const uint64_t *colc, uint64_t *coln, int32_t V,
-                                          int32_t &deg) {
+                                          int32_t &deg, bool r1) {
     const Row r = load_row<BATCH>(P, V);
     deg = static_cast<int32_t>(r.e - r.b);
     const uint64_t self = load_state(colc + V);
@@ -268,7 +276,7 @@ __device__ __forceinline__ bool det_small(const RoundParams &P, const uint64_t *
     const uint32_t pv = prio_of(self);
     uint64_t mask0 = 0, mask1 = 0;
     bool lose = false;
-    sweep_small<BATCH, true, true>(P, r, colc, cv, pv, mask0, mask1, lose);
+    sweep_small<BATCH, true, true>(P, r, colc, cv, pv, mask0, mask1, lose, r1, r1 ? seed_of(P, V) : 0);
     det_write(colc, coln, V, lose, cv, lose ? first_free_128(mask0, mask1) : cv, pv);
     return lose;
 }
@@ -287,7 +295,8 @@ __device__ __forceinline__ void sweep_item(const RoundParams &P, const Row &r, c
                                            const int32_t *list, int64_t lb, int64_t le, int32_t (&ul)[kPer],
                                            int32_t *dst, unsigned *newlen, bool shared_len, int lane, int32_t cv,
                                            uint32_t pv, uint64_t &lo, unsigned *win, uint64_t &flo, unsigned *wfin,
-                                           bool &lose, unsigned &survivors, unsigned &written) {
+                                           bool &lose, unsigned &survivors, unsigned &written, bool r1 = false,
+                                           uint64_t r1seed = 0) {
     int32_t un[kPer];
     uint64_t w[kPer];
     for (int64_t j0 = lb; j0 < le; j0 += kStep) {
@@ -298,7 +307,7 @@ __device__ __forceinline__ void sweep_item(const RoundParams &P, const Row &r, c
             w[q] = kNoNeighbour;
             if (j < le) {
                 const int32_t U = neighbour(P, r, ul[q], j);
-                if (U >= 0) w[q] = load_state(colc + U);
+                if (U >= 0) w[q] = r1 ? round1_state(r1seed, ul[q]) : load_state(colc + U);
             }
         }
         const bool more = j0 + kStep < le;
@@ -373,17 +382,12 @@ __device__ __forceinline__ void sweep_item(const RoundParams &P, const Row &r, c
 __device__ __forceinline__ void append_items(DetItem *next, unsigned *cnt_next, int lane, int32_t items_l,
                                              const int32_t *list_l, int32_t V, int64_t slot_l, uint32_t flags_l,
                                              int64_t len_l, int64_t per_l, int32_t vbase, int32_t ng, int32_t deg,
-                                             unsigned long long *ecnt_next = nullptr) {
+                                             unsigned long long *ent = nullptr) {
     const bool take = items_l > 0;
     const unsigned m = __ballot_sync(kFull, take);
     if (m == 0) return;
-    if (ecnt_next) {
-        // the list entries of the next worklist (the core phase starts once they are few enough)
-        unsigned long long e = take ? static_cast<unsigned long long>(len_l) : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
-        if (lane == 0) atomicAdd(ecnt_next, e);
-    }
+    // the list entries of the next worklist, added up per thread (the core hand-over reads them)
+    if (ent && take) *ent += static_cast<unsigned long long>(len_l);
     unsigned incl = take ? static_cast<unsigned>(items_l) : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -419,7 +423,7 @@ template <bool BATCH, bool COMPACT>
 __device__ __forceinline__ void det_finish(const RoundParams &P, const uint64_t *colc, uint64_t *coln, bool fin,
                                            const DetItem &d, unsigned *win, DetItem *next, unsigned *cnt_next,
                                            int pass, int lane, unsigned items_now, unsigned warps,
-                                           unsigned &st_deg, unsigned &st_cnt) {
+                                           unsigned &st_deg, unsigned &st_cnt, unsigned long long &st_ent) {
     const int32_t V = d.V;
     const uint32_t slot = d.slotf & kItemSlot;
     const int64_t deg = d.deg;
@@ -501,7 +505,7 @@ __device__ __forceinline__ void det_finish(const RoundParams &P, const uint64_t 
         }
     }
     append_items(next, cnt_next, lane, items, list, V, COMPACT ? static_cast<int64_t>(slot) : -1, flags, len, per,
-                 d.vbase, d.ng, static_cast<int32_t>(deg), P.ecnt ? P.ecnt + (pass + 1) % 3 : nullptr);
+                 d.vbase, d.ng, static_cast<int32_t>(deg), &st_ent);
 }
 
 // Phase A, one work item of a larger vertex (one warp).  A vertex with one item is finished here.
@@ -514,7 +518,7 @@ template <bool BATCH, bool COMPACT>
 __device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *coln, const DetItem &d,
                          unsigned *win, unsigned *wfin, unsigned *snap, DetItem *next, unsigned *cnt_next, int pass,
                          int lane, unsigned items_now, unsigned warps, bool merge_now, unsigned &st_deg,
-                         unsigned &st_cnt, unsigned &st_read) {
+                         unsigned &st_cnt, unsigned &st_read, bool r1, unsigned long long &st_ent) {
     const int32_t V = d.V;
     const uint32_t slot = d.slotf & kItemSlot;
     const bool multi = (d.slotf & kItemMulti) != 0;
@@ -562,8 +566,7 @@ __device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *c
     bool lose = false;
     unsigned survivors = 0, written = 0;
     sweep_item<COMPACT, true, true>(P, r, colc, d.list, d.lb, d.le, ul, dst, a + kAccNewLen, multi, lane, cv, pv, lo,
-                                    win, flo,
-                        wfin, lose, survivors, written);
+                                    win, flo, wfin, lose, survivors, written, r1, r1 ? seed_of(P, V) : 0);
     if (lane == 0) st_read += static_cast<unsigned>(d.le - d.lb);
     lose = __any_sync(kFull, lose);
     unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
@@ -592,7 +595,7 @@ __device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *c
         done = __shfl_sync(kFull, done, 0);
         if (done != static_cast<unsigned>(d.nitems - 1)) return;
         det_finish<BATCH, COMPACT>(P, colc, coln, lane == 0, d, win, next, cnt_next, pass, lane, items_now, warps,
-                                   st_deg, st_cnt);
+                                   st_deg, st_cnt, st_ent);
         return;
     }
     // the vertex's only item: its result now
@@ -636,7 +639,7 @@ __device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *c
         const int32_t *list = nsrc == 0 ? d.list : P.lists + off + (nsrc == 2 ? deg : 0);
         const int64_t per = (static_cast<int64_t>(nlen) + items - 1) / items;
         append_items(next, cnt_next, lane, lane == 0 ? items : 0, list, V, slot, nrw ? kItemRewrite : 0u, nlen,
-                     per > 0 ? per : 1, d.vbase, d.ng, d.deg, P.ecnt ? P.ecnt + (pass + 1) % 3 : nullptr);
+                     per > 0 ? per : 1, d.vbase, d.ng, d.deg, &st_ent);
     } else {
         append_items(next, cnt_next, lane, lane == 0 ? 1 : 0, d.list, V, -1, 0u, deg, P.CH, d.vbase, d.ng, d.deg);
     }
@@ -925,7 +928,7 @@ __global__ void __launch_bounds__(kBlock, MINB) det_round_kernel(RoundParams P) 
         if constexpr (COMPACT) {
             // small enough for the core phase: every block reads the same counters, so all leave here
             if (P.core_max > 0 && nsmall + nitems <= static_cast<unsigned>(P.core_max) &&
-                __ldcg(P.ecnt + pass % 3) <= static_cast<unsigned long long>(P.core_emax)) {
+                (!P.ecnt || __ldcg(P.ecnt + pass % 3) <= static_cast<unsigned long long>(P.core_emax))) {
                 if (blockIdx.x == 0 && threadIdx.x == 0) *P.core_go = 1;
                 break;
             }
@@ -943,8 +946,11 @@ __global__ void __launch_bounds__(kBlock, MINB) det_round_kernel(RoundParams P) 
         const int32_t *smallc = odd ? P.small0 : P.small1;
         int32_t *smalln = odd ? P.small1 : P.small0;
         const DetItem *itc = reinterpret_cast<const DetItem *>(odd ? P.chunk0 : P.chunk1);
+        // round 1 with the hash key: every neighbour's state is known without reading it
+        const bool r1 = pass == 1 && P.priority == GC_PRIORITY_HASH;
         DetItem *itn = reinterpret_cast<DetItem *>(odd ? P.chunk1 : P.chunk0);
         unsigned st_deg = 0, st_cnt = 0, st_read = 0;  // this warp's share of the round (< 2^31 each)
+        unsigned long long st_ent = 0;  // list entries this thread appended to the next worklist
         // phase A: work items of larger vertices first (they dominate; the next item is read while
         // the current one runs), then one thread per small vertex
         // sparse rounds (at most kMergeNowItems items per warp) finish several-item vertices in phase A
@@ -955,7 +961,7 @@ __global__ void __launch_bounds__(kBlock, MINB) det_round_kernel(RoundParams P) 
                 const DetItem d = item_of(w);
                 if (i + nw < nchunks) w = item_word(itc, i + nw, lane);
                 det_item<BATCH, COMPACT>(P, colc, coln, d, win, wfin, snap, itn, cn, pass, lane, nchunks,
-                                         static_cast<unsigned>(nw), merge_now, st_deg, st_cnt, st_read);
+                                         static_cast<unsigned>(nw), merge_now, st_deg, st_cnt, st_read, r1, st_ent);
             }
         }
         for (unsigned base = static_cast<unsigned>(gw) * 32u; base < nsmall; base += static_cast<unsigned>(nw) * 32u) {
@@ -964,7 +970,7 @@ __global__ void __launch_bounds__(kBlock, MINB) det_round_kernel(RoundParams P) 
             int32_t V = 0, deg = 0;
             if (i < nsmall) {
                 V = __ldcg(smallc + i);
-                lose = det_small<BATCH>(P, colc, coln, V, deg);
+                lose = det_small<BATCH>(P, colc, coln, V, deg, r1);
                 st_deg += static_cast<unsigned>(deg);
                 st_read += static_cast<unsigned>(deg);
                 st_cnt += 1;
@@ -973,10 +979,7 @@ __global__ void __launch_bounds__(kBlock, MINB) det_round_kernel(RoundParams P) 
                 }
             }
             warp_append(lose, V, smalln, cn + kCntSmall, lane);
-            if (P.ecnt) {
-                const unsigned e = __reduce_add_sync(kFull, lose ? static_cast<unsigned>(deg) : 0u);
-                if (lane == 0 && e) atomicAdd(P.ecnt + (pass + 1) % 3, static_cast<unsigned long long>(e));
-            }
+            if (lose) st_ent += static_cast<unsigned long long>(deg);
         }
         // phase B
         if (nmulti != 0u && !merge_now) {
@@ -991,10 +994,11 @@ __global__ void __launch_bounds__(kBlock, MINB) det_round_kernel(RoundParams P) 
                     fin = (d.slotf & kItemMulti) != 0u && d.lb == 0;
                 }
                 det_finish<BATCH, COMPACT>(P, colc, coln, fin, d, win, itn, cn, pass, lane, nchunks,
-                                           static_cast<unsigned>(nw), st_deg, st_cnt);
+                                           static_cast<unsigned>(nw), st_deg, st_cnt, st_ent);
             }
         }
         if (P.stats) flush_stats(P, pass, st_deg, st_cnt, st_read);
+        if (P.ecnt) flush_sum(P.ecnt + (pass + 1) % 3, st_ent);
         if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1201,6 +1205,7 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
     }
     const int64_t count = static_cast<int64_t>(v_end) - v_begin;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    unsigned long long st_ent = 0;  // list entries of the round's worklist (rows of its vertices)
     for (int64_t base = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ll; base < count;
          base += stride) {
         const int32_t V = static_cast<int32_t>(v_begin + base + lane);
@@ -1241,12 +1246,7 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
         if constexpr (BATCH) {
             if (g_fixed >= 0 && kind != 0) note_graph_round(P, g_fixed, pass);
         }
-        if (P.ecnt) {
-            unsigned long long e = kind != 0 ? static_cast<unsigned long long>(d) : 0ull;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
-            if (lane == 0 && e) atomicAdd(P.ecnt + pass % 3, e);
-        }
+        if (kind != 0) st_ent += static_cast<unsigned long long>(d);
         if (one_block) {
             if (kind == 1) atomicAdd(&s_hist[d], 1u);
         } else if (sort) {
@@ -1282,6 +1282,7 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
         for (int t = threadIdx.x; t < 128; t += blockDim.x)
             if (s_hist[t]) atomicAdd(P.deg_hist + t, s_hist[t]);
     }
+    if (P.ecnt) flush_sum(P.ecnt + pass % 3, st_ent);
 }
 
 // One block of kSortThreads threads: turns the (vertex block, degree) counts P.deg_hist[0, nbins)

@@ -23,10 +23,13 @@ def run_det(gc, g, seed, options=None, stats=False):
 
 def core_variants(gc, g):
     """The library default (small graphs run every round in the shared-memory core phase), the
-    regular round kernel alone, and hand-overs to the core phase part-way through the run."""
+    regular round kernel alone, and hand-overs to the core phase part-way through the run, by a
+    vertex cap and by an entry cap (which makes the rounds count their worklists' entries)."""
     out = [gc.Options(), gc.Options(core_vertices=-1)]
     for cap in (max(1, g.n // 10), max(1, g.n // 3)):
         out.append(gc.Options(core_vertices=cap))
+    if g.nnz > 8:
+        out.append(gc.Options(core_entries=max(1, g.nnz // 8)))
     return out
 
 
@@ -133,7 +136,8 @@ def test_full_sweep_matches_oracle(gclib, make):
                 gclib.Options(chunk=32, small_max_degree=4), gclib.Options(chunk=1024),
                 gclib.Options(chunk=32, small_max_degree=4, core_vertices=-1),
                 gclib.Options(chunk=32, small_max_degree=4, core_vertices=max(1, g.n // 20)),
-                gclib.Options(chunk=128, core_vertices=max(1, g.n // 5))):
+                gclib.Options(chunk=128, core_vertices=max(1, g.n // 5)),
+                gclib.Options(chunk=32, small_max_degree=4, core_entries=max(1, g.nnz // 20))):
         c, nc, rounds, st = run_det(gclib, g, 11, options=opt, stats=True)
         np.testing.assert_array_equal(c, ref.colors)
         assert (nc, rounds) == (ref.ncolors, ref.rounds)

@@ -492,12 +492,12 @@ def main():
     out = torch.empty(g.n, dtype=torch.int32, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     prio = {"hash": gc.PRIORITY_HASH, "lf": gc.PRIORITY_LARGEST_FIRST, "sl": gc.PRIORITY_SMALLEST_LAST}[args.priority]
+    mode = args.mode
     # the autotuner's options for this graph's class when its table is current, else the defaults
     from paper_1509_08267_gb300 import autotune
     base, tuned_class = autotune.options_for_graph(g.rowptr) if mode in ("det", "inplace") else (gc.Options(), None)
     base.priority = prio
     opt = gc.Options(**{**base.__dict__, "flags": base.flags | gc.FLAG_TIMING})
-    mode = args.mode
     start = None
     if mode == "recolor":
         # one recoloring pass over the deterministic mode's coloring (made outside the timed region)
@@ -557,8 +557,8 @@ def main():
                 "kernel": "round phase: persistent round kernel, then (deterministic mode) the core phase's "
                           "kernels; CUDA events around both",
                 "kernel_ms": kms, "alg_bytes": alg_bytes,
-                "alg_bytes_model": "SURVEY 8(d) full-row model: 4 deg(v) + 20 per worklist vertex per round + 4 "
-                                   "per appended vertex"}
+                "alg_bytes_model": "full-row model of one round of Algorithm 1: 4 deg(v) + 20 per worklist vertex "
+                                   "per round + 4 per appended vertex"}
     if traffic is not None:
         # the DRAM bytes the kernels actually moved (ncu) over the same time, against the same peak
         roofline["frac_measured_traffic"] = traffic / (kms / 1e3) / 1e9 / peak

@@ -129,7 +129,7 @@ typedef struct gc_options {
     int32_t core_vertices;     /* deterministic mode: once the worklist has at most this many vertices, the
                                   remaining rounds run with every worklist vertex's color in shared memory
                                   (same results).  0 = the most one block's shared memory holds (about
-                                  110k); < 0 = never */
+                                  200k on GB300: one byte and one bit per vertex); < 0 = never */
     int32_t core_entries;      /* deterministic mode: the most adjacency entries the shared-memory rounds take
                                   (their rows are rebuilt once, at the hand-over); 0 = min(nnz, 2^27).  Above
                                   2^27 it is clamped.  Only a graph with more entries than this counts its
@@ -155,7 +155,9 @@ typedef struct gc_stats {
     float setup_ms;            /* binning/setup kernel device time (GC_FLAG_TIMING) */
     int32_t grid_blocks;       /* blocks of the persistent round kernel */
     int32_t block_size;        /* threads per block of the round kernel */
-    int32_t reserved[6];
+    int64_t *round_reads;      /* caller array or NULL: adjacency entries the round kernel read in each
+                                  round (GC_FLAG_STATS); they sum to entries_scanned */
+    int32_t reserved[4];
 } gc_stats;
 
 /*

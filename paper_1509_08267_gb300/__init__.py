@@ -71,7 +71,7 @@ class _Stats(ctypes.Structure):
                 ("round_ns", ctypes.c_void_p),
                 ("worklist_total", ctypes.c_int64), ("entries_scanned", ctypes.c_int64), ("kernel_ms", ctypes.c_float),
                 ("setup_ms", ctypes.c_float), ("grid_blocks", ctypes.c_int32), ("block_size", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("round_reads", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 4)]
 
 
 class _ServerConfig(ctypes.Structure):
@@ -240,6 +240,7 @@ class Stats:
     wl_size: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
     wl_degsum: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
     round_ns: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
+    round_reads: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
 
 
 def _mode(mode) -> int:
@@ -331,10 +332,12 @@ def _color_one(rowptr, colidx, mode, seed, out, options, stats, round_cap, color
     wl = np.zeros(round_cap, np.int64)
     ds = np.zeros(round_cap, np.int64)
     rn = np.zeros(round_cap, np.int64)
+    rr = np.zeros(round_cap, np.int64)
     st.round_cap = round_cap
     st.wl_size = wl.ctypes.data
     st.wl_degsum = ds.ctypes.data
     st.round_ns = rn.ctypes.data
+    st.round_reads = rr.ctypes.data
     if colors_in is None:
         _check(lib.gc_color_ex(n, prp, pci, _mode(mode), seed & ((1 << 64) - 1), pout, ctypes.byref(nc),
                                ctypes.byref(rd), ctypes.byref(copt), ctypes.byref(st)))
@@ -346,7 +349,8 @@ def _color_one(rowptr, colidx, mode, seed, out, options, stats, round_cap, color
     if want_stats:
         k = min(st.rounds, round_cap)
         s = Stats(st.rounds, st.ncolors, st.max_color, st.worklist_total, st.entries_scanned, st.kernel_ms,
-                  st.setup_ms, st.grid_blocks, st.block_size, wl[:k].copy(), ds[:k].copy(), rn[:k].copy())
+                  st.setup_ms, st.grid_blocks, st.block_size, wl[:k].copy(), ds[:k].copy(), rn[:k].copy(),
+                  rr[:k].copy())
     return Result(out_k if out_k is not None else out, int(nc.value), int(rd.value), s)
 
 
@@ -374,10 +378,12 @@ def color_batch(vtx_off, edge_off, rowptr, colidx, mode="det", seed: int = 0, ou
     wl = np.zeros(round_cap, np.int64)
     ds = np.zeros(round_cap, np.int64)
     rn = np.zeros(round_cap, np.int64)
+    rr = np.zeros(round_cap, np.int64)
     st.round_cap = round_cap
     st.wl_size = wl.ctypes.data
     st.wl_degsum = ds.ctypes.data
     st.round_ns = rn.ctypes.data
+    st.round_reads = rr.ctypes.data
     _check(lib.gc_color_batch_ex(G, pv, pe, prp, pci, _mode(mode), seed & ((1 << 64) - 1), pout, nc.ctypes.data,
                                  rd.ctypes.data, ctypes.byref(copt), ctypes.byref(st)))
     res = (ok if ok is not None else out, nc[:G], rd[:G])
@@ -385,7 +391,7 @@ def color_batch(vtx_off, edge_off, rowptr, colidx, mode="det", seed: int = 0, ou
         k = min(st.rounds, round_cap)
         res = res + (Stats(st.rounds, st.ncolors, st.max_color, st.worklist_total, st.entries_scanned, st.kernel_ms,
                            st.setup_ms, st.grid_blocks, st.block_size, wl[:k].copy(), ds[:k].copy(),
-                           rn[:k].copy()),)
+                           rn[:k].copy(), rr[:k].copy()),)
     return res
 
 

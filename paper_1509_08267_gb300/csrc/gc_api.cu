@@ -105,7 +105,7 @@ struct Context {
     Buf col0, col1, small0, small1, items, chunk0, chunk1, acc, lists, ctl, stats, bitmap, vg, hist;
     Buf gmax, gcount, glast, g_vbase, g_n, g_ebase, g_rbase, g_m;
     Buf st_rowptr, st_colidx, st_vtx, st_edge, st_colors, st_colors_in, mid0, mid1, rank;
-    Buf core_rec, core_cex, core_c8, core_fbits, core_items, core_active, core_log, core_vwork, core_pool;
+    Buf core_rec, core_cex, core_c8, core_fbits, core_items, core_active, core_log, core_pool;
     Buf st_cur, st_work, st_next, st_lost;  // gc_det_round staging
     int32_t core_max_v = 0;  // largest core the round kernel's shared memory holds (-1: none)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -116,7 +116,7 @@ struct Context {
     void release_all() {
         Buf *all[] = {&col0, &col1, &small0, &small1, &items, &chunk0, &chunk1, &acc, &lists, &ctl, &stats, &bitmap, &hist,
                       &vg, &gmax, &gcount, &glast, &g_vbase, &g_n, &g_ebase, &g_rbase, &g_m, &st_rowptr, &st_colidx, &st_vtx, &st_edge, &st_colors, &st_colors_in, &mid0, &mid1, &rank,
-                      &core_rec, &core_cex, &core_c8, &core_fbits, &core_items, &core_active, &core_log, &core_vwork, &core_pool,
+                      &core_rec, &core_cex, &core_c8, &core_fbits, &core_items, &core_active, &core_log, &core_pool,
                       &st_cur, &st_work, &st_next, &st_lost};
         for (Buf *b : all) b->release();
     }
@@ -537,7 +537,8 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
             C.core_max_v = cm > 0 ? cm : -1;
         }
         // the shared colors hold the core and a sentinel entry after it, in a multiple of 16 entries
-        int64_t M = std::min<int64_t>(n, static_cast<int64_t>(C.core_max_v) - 16);
+        // (local ids stay below 2^18: a warp's batch of finished vertices packs them into 18 bits)
+        int64_t M = std::min<int64_t>({n, static_cast<int64_t>(C.core_max_v) - 16, (int64_t{1} << 18) - 32});
         if (core_opt > 0) M = std::min<int64_t>(M, core_opt);
         if (M > 0) {
             const int64_t E = core_E;
@@ -552,7 +553,6 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
             GC_TRY(ensure(C.core_items, 16 * static_cast<size_t>(Q.max_pieces), "core pieces"));
             GC_TRY(ensure(C.core_active, 2 * 4 * static_cast<size_t>(Q.max_pieces), "core active pieces"));
             GC_TRY(ensure(C.core_log, 2 * 8 * Mp, "core change log"));
-            GC_TRY(ensure(C.core_vwork, 2 * 4 * Mp, "core worklists"));
             GC_TRY(ensure(C.core_pool, 4 * static_cast<size_t>(E) + 16, "core rows"));  // + prefetch slack
             Q.rec = C.core_rec.as<unsigned>();
             Q.cex = C.core_cex.as<int32_t>();
@@ -562,7 +562,6 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
             Q.pieces = C.core_items.as<int4>();
             Q.active = C.core_active.as<int32_t>();
             Q.log = C.core_log.as<uint2>();
-            Q.vwork = C.core_vwork.as<int32_t>();
             Q.pool = C.core_pool.as<int32_t>();
             Q.bump = &ctl->core_bump;
             Q.cnt = ctl->core_cnt;
@@ -677,6 +676,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
                 int64_t w = st_host[4 * r], d = st_host[4 * r + 1];
                 const int64_t t_end = st_host[4 * r + 2];
                 stats->entries_scanned += st_host[4 * r + 3];
+                if (stats->round_reads && r < stats->round_cap) stats->round_reads[r] = st_host[4 * r + 3];
                 if (stats->round_ns && r < stats->round_cap) stats->round_ns[r] = t_end - prev_t;
                 prev_t = t_end;
                 if (r == 0 && mode != GC_MODE_ORDERED) {
@@ -770,11 +770,13 @@ static int color_single(int32_t n, const int32_t *rowptr, const int32_t *colidx,
         if (rounds) *rounds = 0;
         if (stats) {
             int32_t cap = stats->round_cap;
-            int64_t *a = stats->wl_size, *b = stats->wl_degsum;
+            int64_t *a = stats->wl_size, *b = stats->wl_degsum, *t = stats->round_ns, *rr = stats->round_reads;
             std::memset(stats, 0, sizeof(*stats));
             stats->round_cap = cap;
             stats->wl_size = a;
             stats->wl_degsum = b;
+            stats->round_ns = t;
+            stats->round_reads = rr;
             stats->max_color = -1;
         }
         return GC_OK;

@@ -20,14 +20,16 @@
 // final colors joins the round's window for the least free color.  Colors are double-buffered as in
 // the round kernel (C_r read, C_{r+1} written), so the result is bit for bit that of the round kernel.
 //
-// Work decomposition.  Each row is cut once into pieces of at most kCorePiece entries, which the
-// warps own round-robin for the whole phase; a piece compacts itself in place (it drops neighbours
-// found final once a quarter of its entries are), so no work list, append or reservation is needed.
-// A round is: refresh the shared colors of the vertices the previous round finished; phase A, every
-// warp sweeps its pieces of worklist vertices (the next piece's first entries are loaded while the
-// current piece is merged) and ORs the piece's window, final window and conflict flag into the
-// vertex's record; grid barrier; phase B, one lane per worklist vertex reads the merged record,
-// takes the least free color or the FINAL state and writes both color buffers; grid barrier.
+// Work decomposition.  Each row is cut once into pieces of at most kCorePiece entries (an empty row
+// into one empty piece); a piece compacts itself in place (it drops neighbours found final once the
+// worklist has lost a quarter of its vertices since the piece last did).  Each round's list of
+// active pieces (the pieces of its worklist vertices) is dealt to the warps round-robin.  A round
+// is: refresh the shared colors of the vertices the previous round finished (its change log); every
+// warp sweeps its pieces (the next piece's first entries and record words are loaded while the
+// current one is consumed), and the warp that holds a vertex's last piece finishes the vertex (at
+// once when it has one piece; else after the pieces' windows and flags have met in the vertex's
+// record): least free color or FINAL, C_{r+1} written, the vertex batched per warp into the change
+// log and, if it lost, its pieces into the next round's list; one grid barrier.
 //
 // Kernels: core_index_kernel (local ids, records, initial colors), core_fill_kernel (the rows),
 // core_round_kernel (one persistent cooperative launch with one block per SM running every
@@ -348,6 +350,7 @@ __device__ __forceinline__ Piece piece_of(int4 x, int l) {
 
 // Bulk prefetch of a piece's entries into L2 (16-byte granules; the pool has 16 bytes of slack).
 __device__ __forceinline__ void prefetch_piece(const CoreParams &Q, int32_t off, int32_t cnt) {
+    if (cnt <= 0) return;
     const uintptr_t a0 = reinterpret_cast<uintptr_t>(Q.pool + off);
     const uintptr_t a = a0 & ~uintptr_t{15};
     const unsigned bytes = (static_cast<unsigned>(a0 - a) + 4u * static_cast<unsigned>(cnt) + 15u) & ~15u;
@@ -356,7 +359,7 @@ __device__ __forceinline__ void prefetch_piece(const CoreParams &Q, int32_t off,
 
 // The round's active pieces a warp takes: entries gw, gw + nw, gw + 2 nw, ... of the round's list of
 // pieces (the pieces of its worklist vertices; every piece in the first round), in batches of 32 (one
-// per lane), skipping pieces without entries.
+// per lane).  Pieces without entries are taken too: they count towards their vertex's pieces done.
 struct PieceCursor {
     unsigned base;  // first list position of the current batch
     int4 d;         // this lane's piece in the batch
@@ -373,7 +376,7 @@ __device__ __forceinline__ void cursor_load(PieceCursor &c, const CoreParams &Q,
     if (i < nact) {
         c.idx = list ? static_cast<unsigned>(__ldcg(list + i)) : i;
         c.d = __ldcg(Q.pieces + c.idx);
-        a = c.d.z > 0;
+        a = true;
     }
     c.act = __ballot_sync(kFull, a);
     // the batch's second active piece (the first is loaded into registers right away)
@@ -467,24 +470,79 @@ __device__ __forceinline__ void consume_step(const Shared &S, const int32_t (&e)
     }
 }
 
-// Phase A of one round for one warp: every active piece it owns, as one stream of steps (the next
-// step's entries, possibly the next piece's first ones, are loaded before the current step is
-// consumed).  For each piece: the round window (all neighbour colors), the conflict flag (a
+// Vertices a warp finished that are not yet in the round's lists: lane k holds the k-th as
+// v | 8-bit color << 18 | kPendLose (v < 2^18: the core never has more vertices).
+constexpr unsigned kPendLose = 1u << 26;
+
+// The round's output for the vertices a warp finished: a change-log entry each (C_{r+1} and the
+// FINAL flag), the losers' count and the losers' pieces (the next round's piece list); one
+// reservation per list.
+__device__ __forceinline__ void flush_pending(const CoreParams &Q, unsigned pend, unsigned npend, unsigned *cn,
+                                              uint2 *log_next, int32_t *act_next, int lane) {
+    const bool act = static_cast<unsigned>(lane) < npend;
+    const unsigned v = pend & 0x3ffffu;
+    const bool lose = act && (pend & kPendLose) != 0u;
+    unsigned pb = 0, npc = 0;
+    if (lose) {
+        const unsigned *rec = core_rec(Q, v);
+        pb = __ldcg(rec + kCorePcBeg);
+        npc = __ldcg(rec + kCorePcEnd) - pb;
+    }
+    const unsigned lm = __ballot_sync(kFull, lose);
+    unsigned incl = npc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    unsigned lb = 0, ab = 0;
+    if (lane == 0) {
+        lb = atomicAdd(cn, npend);
+        if (lm) atomicAdd(cn + 1, static_cast<unsigned>(__popc(lm)));
+        if (total) ab = atomicAdd(cn + 2, total);
+    }
+    lb = __shfl_sync(kFull, lb, 0);
+    ab = __shfl_sync(kFull, ab, 0);
+    if (act) log_next[lb + lane] = make_uint2(v, ((pend >> 18) & 0xffu) | (lose ? 0u : 0x100u));
+    // the losers' pieces, written by the whole warp one vertex at a time
+    for (unsigned pm = __ballot_sync(kFull, npc > 0u); pm; pm &= pm - 1u) {
+        const int l = __ffs(pm) - 1;
+        const unsigned b0 = __shfl_sync(kFull, pb, l), k0 = __shfl_sync(kFull, npc, l);
+        const unsigned at = ab + __shfl_sync(kFull, incl, l) - k0;
+        for (unsigned k = lane; k < k0; k += 32) act_next[at + k] = static_cast<int32_t>(b0 + k);
+    }
+}
+
+// One round for one warp: every active piece it owns, as one stream of steps (the next step's
+// entries, possibly the next piece's first ones and its record words, are loaded before the current
+// step is consumed).  For each piece: the round window (all neighbour colors), the conflict flag (a
 // smaller-key neighbour with the vertex's color) and, when the piece compacts, the window of final
-// colors of the neighbours it drops; then ORed into the vertex's record.
+// colors of the neighbours it drops.  The vertex is finished by the warp that holds its last
+// piece: at once for a vertex with one piece; else every piece ORs its windows and flag into the
+// vertex's record and counts itself done, and the warp that completes the count reads the merged
+// record.  Finishing: a loser takes the least color absent from the round window and the final
+// window (its full row is rescanned past 512 colors), a winner becomes FINAL; C_{r+1} goes into the
+// other color buffers (a winner's FINAL bit into the bitmap) and the vertex into the warp's pending
+// batch for the change log and the next round's lists.
 template <bool BATCH>
-__device__ void core_phase_a(const CoreParams &Q, const Shared &S, const int32_t *cex_cur, const int32_t *list,
-                             unsigned nact, int32_t m, unsigned nv, unsigned gw, unsigned nw, int lane, unsigned *win,
-                             unsigned *wfin, unsigned &st_read) {
+__device__ void core_round_warp(const RoundParams &P, const CoreParams &Q, const Shared &S, const int32_t *cex_cur,
+                                const int32_t *list, unsigned nact, int32_t m, unsigned nv, int pass,
+                                const uint64_t *col_r0, unsigned *cn, unsigned gw, unsigned nw, int lane,
+                                unsigned *win, unsigned *wfin, unsigned &st_read, unsigned &st_deg, unsigned &st_cnt) {
     PieceCursor cur;
     cur.base = gw;
     if (cur.base >= nact) return;
+    const size_t nxt = static_cast<size_t>((pass & 1) ^ 1);
     cursor_load(cur, Q, list, nact, nw, lane);
     Piece p;
     unsigned pidx = 0;
     if (!cursor_next(cur, Q, list, nact, nw, lane, p, pidx)) return;
     int32_t e[kCorePer];
     load_piece_step(Q, p, 0, lane, m, e);
+    // words 32..63 of the piece's vertex record: final window, row fields, piece range
+    unsigned rx = __ldcg(core_rec(Q, p.v) + 32 + lane);
+    unsigned pend = 0, npend = 0;
     for (;;) {
         // a piece starts: its windows, own color and compaction mode
         if (lane < kAccWords) {
@@ -507,9 +565,11 @@ __device__ void core_phase_a(const CoreParams &Q, const Shared &S, const int32_t
             unsigned pnidx = pidx;
             int32_t jn = j0 + kCoreStep;
             bool more = jn < p.cnt;
+            unsigned rxn = rx;
             if (!more) {
                 more = cursor_next(cur, Q, list, nact, nw, lane, pn, pnidx);
                 jn = 0;
+                if (more) rxn = __ldcg(core_rec(Q, pn.v) + 32 + lane);
             }
             int32_t en[kCorePer];
             if (more) load_piece_step(Q, pn, jn, lane, m, en);
@@ -533,8 +593,7 @@ __device__ void core_phase_a(const CoreParams &Q, const Shared &S, const int32_t
             kept_total += kept;
             const bool piece_done = jn == 0 || !more;
             if (piece_done) {
-                // merge into the vertex's record; update the piece
-                const bool lose = __any_sync(kFull, conflict != 0u);
+                const bool lose_p = __any_sync(kFull, conflict != 0u);
                 const unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
                 const unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
                 const unsigned lo2 = __reduce_or_sync(kFull, static_cast<unsigned>(mid));
@@ -543,23 +602,86 @@ __device__ void core_phase_a(const CoreParams &Q, const Shared &S, const int32_t
                 const unsigned f1 = __reduce_or_sync(kFull, static_cast<unsigned>(flo >> 32));
                 __syncwarp();
                 unsigned *rec = core_rec(Q, p.v);
+                // lanes 0..15: this piece's round window and final window; the final window as the
+                // record held it when the piece started
                 const unsigned rw = lane == 0 ? lo0 : lane == 1 ? lo1 : lane == 2 ? lo2 : lane == 3 ? lo3
                                   : (lane < kAccWords ? win[lane] : 0u);
                 const unsigned fw = lane == 0 ? f0 : lane == 1 ? f1 : (lane < kAccWords ? wfin[lane] : 0u);
-                if (lane < kAccWords && rw) atomicOr(rec + lane, rw);
-                if (lane < kAccWords && fw) atomicOr(rec + kAccFin + lane, fw);
+                const unsigned fold = lane < kAccWords ? rx : 0u;
+                const unsigned npc = __shfl_sync(kFull, rx, kCorePcEnd - 32) - __shfl_sync(kFull, rx, kCorePcBeg - 32);
                 if (lane == 0) {
-                    if (lose) atomicOr(rec + kCoreFlag, 1u);
                     st_read += static_cast<unsigned>(p.cnt);
                     if (compact)
                         reinterpret_cast<int2 *>(Q.pieces + pidx)[1] =
                             make_int2(static_cast<int32_t>(kept_total), static_cast<int32_t>(nv));
                 }
+                bool lose = lose_p, finish = true;
+                unsigned tw = 0;  // lanes 0..15: colors 32 lane .. 32 lane + 31 around the vertex
+                if (npc <= 1u) {
+                    if (lane < kAccWords && (fw & ~fold)) rec[kAccFin + lane] = fold | fw;
+                    tw = rw | fw | fold;
+                } else {
+                    if (lane < kAccWords && rw) atomicOr(rec + lane, rw);
+                    if (lane < kAccWords && (fw & ~fold)) atomicOr(rec + kAccFin + lane, fw);
+                    if (lane == 0 && lose_p) atomicOr(rec + kCoreFlag, 1u);
+                    // the piece that completes the count (release: its merges first; acquire: the others')
+                    __syncwarp();
+                    unsigned done = 0;
+                    if (lane == 0) done = atom_add_acq_rel(rec + kCoreDone, 1u);
+                    done = __shfl_sync(kFull, done, 0);
+                    finish = done == npc - 1u;
+                    if (finish) {
+                        __syncwarp();
+                        const unsigned x = __ldcg(rec + lane);  // window (lanes 0..15), flag (lane 16)
+                        const unsigned fx = lane < kAccWords ? __ldcg(rec + kAccFin + lane) : 0u;
+                        lose = __shfl_sync(kFull, x, kCoreFlag) != 0u;
+                        tw = lane < kAccWords ? (x | fx) : 0u;
+                        __syncwarp();
+                        if (lane <= kCoreDone) rec[lane] = 0u;  // the round part, for the next round
+                    }
+                }
+                if (finish) {
+                    const int32_t v = p.v;
+                    int32_t nc = cv;
+                    if (lose) {
+                        const unsigned fm = __ballot_sync(kFull, lane < kAccWords && ~tw != 0u);
+                        if (fm) {
+                            const int l = __ffs(fm) - 1;
+                            nc = 32 * l + __ffs(~__shfl_sync(kFull, tw, l)) - 1;
+                        } else {
+                            nc = core_mex_from<BATCH>(P, col_r0, static_cast<int32_t>(__shfl_sync(kFull, rx, kCoreGid - 32)),
+                                                      cex_cur, win, lane, 32 * kAccWords);
+                        }
+                    }
+                    const unsigned deg = __shfl_sync(kFull, rx, kCoreDeg - 32);
+                    const unsigned n8 = sat8(nc);
+                    if (lane == 0) {
+                        Q.cex[nxt * Q.max_v + v] = nc;
+                        Q.c8[nxt * Q.max_v + v] = static_cast<uint8_t>(n8);
+                        if (!lose) atomicOr(Q.fbits + (v >> 5), 1u << (v & 31));  // final for good: one bitmap
+                        st_deg += deg;
+                        st_cnt += 1;
+                    }
+                    if constexpr (BATCH) {
+                        const unsigned g = __shfl_sync(kFull, rx, kCoreG - 32);
+                        if (lane == 0 && lose) note_graph_round(P, static_cast<int32_t>(g), pass + 1);
+                    }
+                    if (static_cast<unsigned>(lane) == npend)
+                        pend = static_cast<unsigned>(v) | (n8 << 18) | (lose ? kPendLose : 0u);
+                    if (++npend == 32u) {
+                        flush_pending(Q, pend, npend, cn, Q.log + nxt * Q.max_v, Q.active + nxt * Q.max_pieces, lane);
+                        npend = 0;
+                    }
+                }
                 __syncwarp();
             }
-            if (!more) return;
+            if (!more) {
+                if (npend) flush_pending(Q, pend, npend, cn, Q.log + nxt * Q.max_v, Q.active + nxt * Q.max_pieces, lane);
+                return;
+            }
             p = pn;
             pidx = pnidx;
+            rx = rxn;
             j0 = jn;
 #pragma unroll
             for (int q = 0; q < kCorePer; ++q) e[q] = en[q];
@@ -568,115 +690,9 @@ __device__ void core_phase_a(const CoreParams &Q, const Shared &S, const int32_t
     }
 }
 
-// Phase B of one round: one lane per worklist vertex (the round's vertex list, 32 entries per warp,
-// the warps interleaved over the SMs): the merged record tells whether v lost, and the colors around
-// it; a loser takes the least color absent from both windows (its full row is rescanned past 512
-// colors), a winner becomes FINAL.  Both color buffers are written (C_{r+1}; a winner's FINAL bit into
-// the bitmap), the vertex goes into the change log, a loser into the next round's vertex list and its
-// pieces into the next round's piece list, and the record's round part is cleared.
-template <bool BATCH>
-__device__ void core_phase_b(const RoundParams &P, const CoreParams &Q, const Shared &S, const int32_t *vlist,
-                             unsigned nv, int pass, const uint64_t *col_r0, unsigned *cn, unsigned gw, unsigned nw,
-                             int lane, unsigned *win, unsigned &st_deg, unsigned &st_cnt) {
-    const int cur = pass & 1;
-    const int32_t *cex_cur = Q.cex + static_cast<size_t>(cur) * Q.max_v;
-    uint2 *log_next = Q.log + static_cast<size_t>(cur ^ 1) * Q.max_v;
-    int32_t *act_next = Q.active + static_cast<size_t>(cur ^ 1) * Q.max_pieces;
-    int32_t *vlist_next = Q.vwork + static_cast<size_t>(cur ^ 1) * Q.max_v;
-    for (int64_t ib = static_cast<int64_t>(gw) * 32; ib < nv; ib += static_cast<int64_t>(nw) * 32) {
-        const int64_t i = ib + lane;
-        const bool act = i < nv;
-        const int32_t v = act ? (vlist ? __ldcg(vlist + i) : static_cast<int32_t>(i)) : 0;
-        const unsigned own8 = act ? S.color8(static_cast<uint32_t>(v)) : 0u;
-        unsigned *rec = core_rec(Q, v);
-        uint4 w[kAccWords / 4];
-        bool lose = false;
-        uint4 meta = make_uint4(0, 0, 0, 0);
-        unsigned pb = 0, pe = 0;
-        if (act) {
-#pragma unroll
-            for (int c = 0; c < kAccWords / 4; ++c) {
-                w[c] = ldcg4(rec + 4 * c);
-                const uint4 f = ldcg4(rec + kAccFin + 4 * c);
-                w[c].x |= f.x;
-                w[c].y |= f.y;
-                w[c].z |= f.z;
-                w[c].w |= f.w;
-            }
-            lose = __ldcg(rec + kCoreFlag) != 0u;
-            meta = ldcg4(rec + kCoreOffLo);  // off lo, off hi, degree, global id
-            if (lose) {
-                pb = __ldcg(rec + kCorePcBeg);
-                pe = __ldcg(rec + kCorePcEnd);
-            }
-        }
-        const int32_t cv = own8 == kSat8 ? __ldcg(cex_cur + v) : static_cast<int32_t>(own8);
-        int32_t nc = cv;
-        if (lose) {
-            nc = -1;
-#pragma unroll
-            for (int c = 0; c < kAccWords / 4; ++c)
-                if (nc < 0) nc = first_free4(w[c], 128 * c);
-        }
-        // rare: all of colors 0..511 taken; the warp rescans each such vertex's full row
-        unsigned need = __ballot_sync(kFull, lose && nc < 0);
-        while (need) {
-            const int l = __ffs(need) - 1;
-            need &= need - 1;
-            const int32_t x = core_mex_from<BATCH>(P, col_r0, static_cast<int32_t>(__shfl_sync(kFull, meta.w, l)),
-                                                   cex_cur, win, lane, 32 * kAccWords);
-            if (lane == l) nc = x;
-        }
-        // positions in the log, the next vertex list and the next piece list: one reservation each per warp
-        const unsigned am = __ballot_sync(kFull, act);
-        const unsigned lm = __ballot_sync(kFull, lose);
-        const unsigned npc = pe - pb;
-        unsigned incl = npc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const unsigned total = __shfl_sync(kFull, incl, 31);
-        unsigned lb = 0, ab = 0, vb = 0;
-        if (lane == 0) {
-            if (am) lb = atomicAdd(cn, static_cast<unsigned>(__popc(am)));
-            if (lm) vb = atomicAdd(cn + 1, static_cast<unsigned>(__popc(lm)));
-            if (total) ab = atomicAdd(cn + 2, total);
-        }
-        lb = __shfl_sync(kFull, lb, 0);
-        vb = __shfl_sync(kFull, vb, 0);
-        ab = __shfl_sync(kFull, ab, 0);
-        if (act) {
-            const unsigned n8 = sat8(nc);
-            Q.cex[static_cast<size_t>(cur ^ 1) * Q.max_v + v] = nc;
-            Q.c8[static_cast<size_t>(cur ^ 1) * Q.max_v + v] = static_cast<uint8_t>(n8);
-            if (!lose) atomicOr(Q.fbits + (v >> 5), 1u << (v & 31));  // final for good: one bitmap
-            log_next[lb + __popc(am & lanemask_lt())] = make_uint2(static_cast<unsigned>(v), n8 | (lose ? 0u : 0x100u));
-            if (lose) vlist_next[vb + __popc(lm & lanemask_lt())] = v;
-            const uint4 z = make_uint4(0, 0, 0, 0);
-#pragma unroll
-            for (int c = 0; c < kAccWords; c += 4) stcg4(rec + c, z);
-            if (lose) rec[kCoreFlag] = 0u;
-            st_deg += meta.z;
-            st_cnt += 1;
-            if constexpr (BATCH) {
-                if (lose) note_graph_round(P, static_cast<int32_t>(__ldcg(rec + kCoreG)), pass + 1);
-            }
-        }
-        // the losers' pieces, written by the whole warp one vertex at a time
-        for (unsigned pm = __ballot_sync(kFull, npc > 0u); pm; pm &= pm - 1u) {
-            const int l = __ffs(pm) - 1;
-            const unsigned b0 = __shfl_sync(kFull, pb, l), k0 = __shfl_sync(kFull, npc, l);
-            const unsigned at = ab + __shfl_sync(kFull, incl, l) - k0;
-            for (unsigned k = lane; k < k0; k += 32) act_next[at + k] = static_cast<int32_t>(b0 + k);
-        }
-    }
-}
-
 #ifdef GC_CORE_PROFILE
 // Per round (profiling builds only): earliest round start, latest refresh end, earliest / latest
-// phase-A end, latest phase-B start, latest phase-B end, worklist size.
+// end of a block's sweep, worklist size (word 7).
 __device__ unsigned long long g_core_prof[8 * 4096];
 #define CORE_PROF(k, op) \
     if (threadIdx.x == 0 && pass - R0 < 4096) op(g_core_prof + 8 * (pass - R0) + (k), global_ns())
@@ -717,7 +733,7 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
                 len = __ldcg(rec + kCoreFill);  // the row as the fill kernel wrote it
                 off = static_cast<uint64_t>(__ldcg(rec + kCoreOffLo)) |
                       (static_cast<uint64_t>(__ldcg(rec + kCoreOffHi)) << 32);
-                np = (len + kCorePiece - 1) / kCorePiece;
+                np = len ? (len + kCorePiece - 1) / kCorePiece : 1u;  // an empty row: one empty piece
             }
             unsigned incl = np;
 #pragma unroll
@@ -777,20 +793,12 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
             // the round's pieces: all of them in the first round, then those the previous round listed
             const int32_t *list = pass == R0 ? nullptr : Q.active + static_cast<size_t>(pass & 1) * Q.max_pieces;
             const unsigned nact = pass == R0 ? npieces : __ldcg(cc + 2);
-            core_phase_a<BATCH>(Q, S, cex_cur, list, nact, m, nv, gw, nw, lane, s_win[wib], s_fin[wib], st_read);
+            core_round_warp<BATCH>(P, Q, S, cex_cur, list, nact, m, nv, pass, h.colc, cn, gw, nw, lane, s_win[wib],
+                                   s_fin[wib], st_read, st_deg, st_cnt);
 #ifdef GC_CORE_PROFILE
             __syncthreads();
             CORE_PROF(2, atomicMin);
             CORE_PROF(3, atomicMax);
-#endif
-            if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;
-            CORE_PROF(4, atomicMax);
-            // the round's vertices: every core vertex in the first round, then the previous round's losers
-            const int32_t *vlist = pass == R0 ? nullptr : Q.vwork + static_cast<size_t>(pass & 1) * Q.max_v;
-            core_phase_b<BATCH>(P, Q, S, vlist, nv, pass, h.colc, cn, gw, nw, lane, s_win[wib], st_deg, st_cnt);
-#ifdef GC_CORE_PROFILE
-            __syncthreads();
-            CORE_PROF(5, atomicMax);
 #endif
             if (P.stats) flush_stats(P, pass, st_deg, st_cnt, st_read);
             if (!grid_sync(P.bar, bar_target, P.err, P.spin_ns)) break;

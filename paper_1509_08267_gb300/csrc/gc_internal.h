@@ -151,10 +151,12 @@ constexpr int64_t kCoreEntries = int64_t{1} << 27;  // list entries the core pha
 #endif
 constexpr int kCorePiece = GC_CORE_PIECE;
 // Per core vertex, kCoreRecWords words: [0, 16) the round's window of neighbour colors 0..511,
-// kCoreFlag (some smaller-key neighbour has the vertex's color), [kAccFin, kAccFin + 16) the window of
-// final neighbours' colors, then the row's offset in the pool, degree, global id, row length, graph.
+// kCoreFlag (some smaller-key neighbour has the vertex's color), kCoreDone (pieces of the vertex done
+// this round) -- the round part, used by vertices with several pieces --, [kAccFin, kAccFin + 16) the
+// window of final neighbours' colors, then the row's offset in the pool, degree, global id, row
+// length, graph, the hand-over list and the vertex's range of pieces.
 constexpr int kCoreRecWords = 64;
-constexpr int kCoreFlag = 16;
+constexpr int kCoreFlag = 16, kCoreDone = 17;
 constexpr int kCoreOffLo = 48, kCoreOffHi = 49, kCoreDeg = 50, kCoreGid = 51, kCoreFill = 52, kCoreG = 53;
 constexpr int kCoreListLo = 54, kCoreListHi = 55, kCoreListLen = 56, kCorePcBeg = 57, kCorePcEnd = 58;
 struct CoreParams {
@@ -168,7 +170,6 @@ struct CoreParams {
     unsigned *fbits;      // [M / 32 + 1] FINAL bit of every core vertex (zero at hand-over)
     int4 *pieces;         // [max_pieces] {local vertex, pool offset, entries, flags}
     int32_t *active;      // [2][max_pieces] the pieces of each round's worklist vertices
-    int32_t *vwork;       // [2][M] each round's worklist vertices (after the first round)
     uint2 *log;           // [2][M] {local vertex, 8-bit color | FINAL << 8} of the vertices a round finished
     int32_t *pool;        // [max_e] the rows
     unsigned long long *bump;  // pool allocation counter

@@ -46,3 +46,31 @@ def test_header_compiles_as_c_and_cpp(tmp_path):
                 ["g++", "-x", "c++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)]):
         r = subprocess.run(cmd, capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_binding_structs_match_header(tmp_path):
+    # the Python binding's ctypes mirrors have the header's sizes and field offsets
+    import subprocess
+    import paper_1509_08267_gb300 as gc
+    pairs = {"gc_options": gc._Options, "gc_stats": gc._Stats, "gc_server_config": gc._ServerConfig,
+             "struct gc_server_stats": gc._ServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gc.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    want = {}
+    for cname, py in pairs.items():
+        want[f"{cname} size"] = ctypes.sizeof(py)
+        for f, _ in py._fields_:
+            want[f"{cname} {f}"] = getattr(py, f).offset
+    got = {ln.rsplit(" ", 1)[0]: int(ln.rsplit(" ", 1)[1]) for ln in out if ln}
+    assert got == want

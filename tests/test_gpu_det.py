@@ -151,6 +151,10 @@ def test_compact_reads_fewer_entries(gclib):
     _, _, _, compact = run_det(gclib, g, 7, stats=True)
     assert full.entries_scanned == full.wl_degsum.sum()
     assert compact.entries_scanned < 0.8 * full.entries_scanned
+    # per round: the full sweep reads every entry of the worklist's rows, the compact one a subset
+    np.testing.assert_array_equal(full.round_reads, full.wl_degsum)
+    assert compact.round_reads.sum() == compact.entries_scanned
+    assert (compact.round_reads <= compact.wl_degsum).all()
 
 
 def test_batch_full_sweep(gclib):

@@ -87,11 +87,12 @@ struct Ctl {
     unsigned long long ecnt[3];  // list entries of each counter set's worklist (core hand-over)
     unsigned long long core_bump;
     int32_t core_go, pad3;
-    unsigned core_cnt[12];
+    alignas(16) unsigned core_cnt[12];  // three sets of four, each read with one 16-byte load
     unsigned core_m[4];
     GridBar bar;
 };
 static_assert(offsetof(Ctl, bar) % 128 == 0, "barrier alignment");
+static_assert(offsetof(Ctl, core_cnt) % 16 == 0, "core counter alignment");
 
 struct Context {
     int device = -1;

@@ -471,23 +471,19 @@ __device__ __forceinline__ void consume_step(const Shared &S, const int32_t (&e)
 }
 
 // Vertices a warp finished that are not yet in the round's lists: lane k holds the k-th as
-// v | 8-bit color << 18 | kPendLose (v < 2^18: the core never has more vertices).
+// v | 8-bit color << 18 | kPendLose (v < 2^18: the core never has more vertices), and its range of
+// pieces.
 constexpr unsigned kPendLose = 1u << 26;
 
 // The round's output for the vertices a warp finished: a change-log entry each (C_{r+1} and the
 // FINAL flag), the losers' count and the losers' pieces (the next round's piece list); one
 // reservation per list.
-__device__ __forceinline__ void flush_pending(const CoreParams &Q, unsigned pend, unsigned npend, unsigned *cn,
-                                              uint2 *log_next, int32_t *act_next, int lane) {
+__device__ __forceinline__ void flush_pending(unsigned pend, unsigned pend_pb, unsigned pend_np, unsigned npend,
+                                              unsigned *cn, uint2 *log_next, int32_t *act_next, int lane) {
     const bool act = static_cast<unsigned>(lane) < npend;
     const unsigned v = pend & 0x3ffffu;
     const bool lose = act && (pend & kPendLose) != 0u;
-    unsigned pb = 0, npc = 0;
-    if (lose) {
-        const unsigned *rec = core_rec(Q, v);
-        pb = __ldcg(rec + kCorePcBeg);
-        npc = __ldcg(rec + kCorePcEnd) - pb;
-    }
+    const unsigned pb = lose ? pend_pb : 0u, npc = lose ? pend_np : 0u;
     const unsigned lm = __ballot_sync(kFull, lose);
     unsigned incl = npc;
 #pragma unroll
@@ -542,7 +538,7 @@ __device__ void core_round_warp(const RoundParams &P, const CoreParams &Q, const
     load_piece_step(Q, p, 0, lane, m, e);
     // words 32..63 of the piece's vertex record: final window, row fields, piece range
     unsigned rx = __ldcg(core_rec(Q, p.v) + 32 + lane);
-    unsigned pend = 0, npend = 0;
+    unsigned pend = 0, pend_pb = 0, pend_np = 0, npend = 0;
     for (;;) {
         // a piece starts: its windows, own color and compaction mode
         if (lane < kAccWords) {
@@ -666,17 +662,24 @@ __device__ void core_round_warp(const RoundParams &P, const CoreParams &Q, const
                         const unsigned g = __shfl_sync(kFull, rx, kCoreG - 32);
                         if (lane == 0 && lose) note_graph_round(P, static_cast<int32_t>(g), pass + 1);
                     }
-                    if (static_cast<unsigned>(lane) == npend)
+                    const unsigned pb = __shfl_sync(kFull, rx, kCorePcBeg - 32);
+                    if (static_cast<unsigned>(lane) == npend) {
                         pend = static_cast<unsigned>(v) | (n8 << 18) | (lose ? kPendLose : 0u);
+                        pend_pb = pb;
+                        pend_np = npc;
+                    }
                     if (++npend == 32u) {
-                        flush_pending(Q, pend, npend, cn, Q.log + nxt * Q.max_v, Q.active + nxt * Q.max_pieces, lane);
+                        flush_pending(pend, pend_pb, pend_np, npend, cn, Q.log + nxt * Q.max_v,
+                                      Q.active + nxt * Q.max_pieces, lane);
                         npend = 0;
                     }
                 }
                 __syncwarp();
             }
             if (!more) {
-                if (npend) flush_pending(Q, pend, npend, cn, Q.log + nxt * Q.max_v, Q.active + nxt * Q.max_pieces, lane);
+                if (npend)
+                    flush_pending(pend, pend_pb, pend_np, npend, cn, Q.log + nxt * Q.max_v,
+                                  Q.active + nxt * Q.max_pieces, lane);
                 return;
             }
             p = pn;
@@ -763,10 +766,11 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
     if (grid_sync(P.bar, bar_target, P.err, P.spin_ns)) {
         const unsigned npieces = __ldcg(Q.m + 2);
         for (;; ++pass) {
-            unsigned *cc = Q.cnt + 4 * (pass % 3);
+            // the previous round's counts: {change-log entries, losers, pieces listed, -}
+            const uint4 cc = ldcg4(Q.cnt + 4 * (pass % 3));
             unsigned *cn = Q.cnt + 4 * ((pass + 1) % 3);
             // |W_pass|: every core vertex in the first round, then the previous round's losers
-            const unsigned nv = pass == R0 ? static_cast<unsigned>(m) : __ldcg(cc + 1);
+            const unsigned nv = pass == R0 ? static_cast<unsigned>(m) : cc.y;
             if (nv == 0u) break;
             if (pass >= P.pass_end) {
                 if (P.cap_is_error && blockIdx.x == 0 && threadIdx.x == 0)
@@ -781,7 +785,7 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
             const int32_t *cex_cur = Q.cex + static_cast<size_t>(pass & 1) * Q.max_v;
             if (pass > R0) {
                 // the vertices the previous round finished: its change log, or all colors when they are many
-                const unsigned nprev = __ldcg(cc);
+                const unsigned nprev = cc.x;
                 if (8ull * nprev > static_cast<unsigned long long>(m))
                     load_shared(S, Q, Q.c8 + static_cast<size_t>(pass & 1) * Q.max_v, m);
                 else
@@ -792,7 +796,7 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
             unsigned st_deg = 0, st_cnt = 0, st_read = 0;
             // the round's pieces: all of them in the first round, then those the previous round listed
             const int32_t *list = pass == R0 ? nullptr : Q.active + static_cast<size_t>(pass & 1) * Q.max_pieces;
-            const unsigned nact = pass == R0 ? npieces : __ldcg(cc + 2);
+            const unsigned nact = pass == R0 ? npieces : cc.z;
             core_round_warp<BATCH>(P, Q, S, cex_cur, list, nact, m, nv, pass, h.colc, cn, gw, nw, lane, s_win[wib],
                                    s_fin[wib], st_read, st_deg, st_cnt);
 #ifdef GC_CORE_PROFILE

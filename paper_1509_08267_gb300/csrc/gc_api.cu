@@ -430,6 +430,8 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     P.CH = CH;
     P.priority = priority;
     P.prio_rank = pb.prio_rank;
+    // (GC_FLAG_FULL_SWEEP reads every entry of every worklist row: no early stop either)
+    P.early_exit = mode == GC_MODE_DETERMINISTIC && compact ? 1 : 0;
     // the entries of each worklist's lists are counted for the core hand-over from round 1 on, when
     // the graph has more entries than the core may take (else the worklist always fits)
     const int64_t core_E = std::min<int64_t>(

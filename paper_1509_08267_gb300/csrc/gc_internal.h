@@ -9,7 +9,7 @@
 
 namespace gc {
 
-// Adjacency entries a warp loads per step of a work item (8 per lane, issued together).
+// Adjacency entries a warp loads per step of a work item (kStep / 32 per lane, issued together).
 #ifndef GC_STEP
 #define GC_STEP 128
 #endif
@@ -127,6 +127,10 @@ struct RoundParams {
     const int32_t *prio_rank;  // smallest last: the peel levels; recoloring: the given coloring (int32[n])
     int32_t spread;  // in-place mode: phase 1 takes the thread worklist in a spread order (set when no
                      // vertex is past T1: the degree-sorted order then balances nothing)
+    // Deterministic mode from C_1 = 0: the colors of round r are at most r - 1 (a loser's First Fit
+    // color exceeds the largest color around it by at most one).  A sweep that knows its vertex loses
+    // and has seen every color 0..r-1 around it knows the vertex's next color (r) and stops early.
+    int32_t early_exit;
     // Hand-over to the core phase (deterministic compact mode).  core_max > 0: the round kernel stops
     // at the top of the first round whose worklist has at most core_max vertices whose lists hold at
     // most core_emax entries, and sets *core_go; the core kernels (gc_core.cu) finish the coloring.
@@ -147,7 +151,7 @@ struct RoundParams {
 constexpr uint32_t kCoreSmaller = 0x80000000u;
 constexpr int64_t kCoreEntries = int64_t{1} << 27;  // list entries the core phase takes at most
 #ifndef GC_CORE_PIECE
-#define GC_CORE_PIECE 1024
+#define GC_CORE_PIECE 2048
 #endif
 constexpr int kCorePiece = GC_CORE_PIECE;
 // Per core vertex, kCoreRecWords words: [0, 16) the round's window of neighbour colors 0..511,

@@ -161,11 +161,13 @@ __device__ __forceinline__ uint64_t round1_state(uint64_t seed, int32_t ul) {
 // Per-thread sweep of a short row (degree <= T1 <= 127): window [0, 128) in two 64-bit masks (the
 // least free color is at most deg(v)) and conflict flag.  Four entries per step from the aligned
 // group of four that holds the row's first entry; the next step's entries are loaded before the
-// current step's gathers are consumed.
+// current step's gathers are consumed.  `need` (colors 0..r-1 of round r, or 0): the sweep stops
+// once the vertex loses and mask0 holds all of them (its next color is then r).  Returns the end of
+// the entries read.
 template <bool BATCH, bool WINDOW, bool CONFLICT>
-__device__ __forceinline__ void sweep_small(const RoundParams &P, const Row &r, const uint64_t *colc, int32_t cv,
-                                            uint32_t pv, uint64_t &mask0, uint64_t &mask1, bool &lose,
-                                            bool r1 = false, uint64_t r1seed = 0) {
+__device__ __forceinline__ int64_t sweep_small(const RoundParams &P, const Row &r, const uint64_t *colc, int32_t cv,
+                                               uint32_t pv, uint64_t &mask0, uint64_t &mask1, bool &lose,
+                                               bool r1 = false, uint64_t r1seed = 0, uint64_t need = 0) {
     constexpr int kT = 4;  // entries per step
     const bool vec = (reinterpret_cast<uintptr_t>(P.colidx) & 15u) == 0;
     int64_t j0 = vec ? (r.b & ~int64_t{3}) : r.b;
@@ -197,11 +199,13 @@ __device__ __forceinline__ void sweep_small(const RoundParams &P, const Row &r, 
                                                          static_cast<uint32_t>(r.lv), P, r.vbase + r.lv);
             }
         }
+        if (need && lose && (mask0 & need) == need) return min(j0 + kT, r.e);
         if (more) {
 #pragma unroll
             for (int q = 0; q < kT; ++q) ul[q] = un[q];
         }
     }
+    return r.e;
 }
 
 // Least color absent from a two-mask window [0, 128) (never full for degree <= 127).
@@ -268,7 +272,7 @@ __device__ __forceinline__ void det_write(const uint64_t *colc, uint64_t *coln, 
 // One vertex of degree <= T1 (one thread): did it lose in this round; writes its next state.
 template <bool BATCH>
 __device__ __forceinline__ bool det_small(const RoundParams &P, const uint64_t *colc, uint64_t *coln, int32_t V,
-                                          int32_t &deg, bool r1) {
+                                          int32_t &deg, int32_t &nread, bool r1, uint64_t need) {
     const Row r = load_row<BATCH>(P, V);
     deg = static_cast<int32_t>(r.e - r.b);
     const uint64_t self = load_state(colc + V);
@@ -276,7 +280,9 @@ __device__ __forceinline__ bool det_small(const RoundParams &P, const uint64_t *
     const uint32_t pv = prio_of(self);
     uint64_t mask0 = 0, mask1 = 0;
     bool lose = false;
-    sweep_small<BATCH, true, true>(P, r, colc, cv, pv, mask0, mask1, lose, r1, r1 ? seed_of(P, V) : 0);
+    nread = static_cast<int32_t>(
+        sweep_small<BATCH, true, true>(P, r, colc, cv, pv, mask0, mask1, lose, r1, r1 ? seed_of(P, V) : 0, need) -
+        r.b);
     det_write(colc, coln, V, lose, cv, lose ? first_free_128(mask0, mask1) : cv, pv);
     return lose;
 }
@@ -289,14 +295,17 @@ __device__ __forceinline__ bool det_small(const RoundParams &P, const uint64_t *
 // a smaller key sets `lose`.  DROP: a neighbour found final is also recorded in the window of final
 // neighbours (flo / wfin) and dropped; the entries still active are counted (survivors, lane 0) and, when
 // `dst` is set, copied to dst at positions from *newlen (atomically when `shared_len`, else lane 0's
-// running count `written`).
+// running count `written`).  `need` (colors 0..r-1 of round r, or 0; never with dst): the sweep
+// stops once some lane has the conflict and the warp's window with `fin64` (final colors 0..63
+// known before) holds all of them -- the vertex's next color is then r; the entries not read count
+// as survivors.  Returns the end of the entries read.
 template <bool DROP, bool WINDOW = true, bool CONFLICT = true>
-__device__ __forceinline__ void sweep_item(const RoundParams &P, const Row &r, const uint64_t *colc,
-                                           const int32_t *list, int64_t lb, int64_t le, int32_t (&ul)[kPer],
-                                           int32_t *dst, unsigned *newlen, bool shared_len, int lane, int32_t cv,
-                                           uint32_t pv, uint64_t &lo, unsigned *win, uint64_t &flo, unsigned *wfin,
-                                           bool &lose, unsigned &survivors, unsigned &written, bool r1 = false,
-                                           uint64_t r1seed = 0) {
+__device__ __forceinline__ int64_t sweep_item(const RoundParams &P, const Row &r, const uint64_t *colc,
+                                              const int32_t *list, int64_t lb, int64_t le, int32_t (&ul)[kPer],
+                                              int32_t *dst, unsigned *newlen, bool shared_len, int lane, int32_t cv,
+                                              uint32_t pv, uint64_t &lo, unsigned *win, uint64_t &flo, unsigned *wfin,
+                                              bool &lose, unsigned &survivors, unsigned &written, bool r1 = false,
+                                              uint64_t r1seed = 0, uint64_t need = 0, uint64_t fin64 = 0) {
     int32_t un[kPer];
     uint64_t w[kPer];
     for (int64_t j0 = lb; j0 < le; j0 += kStep) {
@@ -368,11 +377,22 @@ __device__ __forceinline__ void sweep_item(const RoundParams &P, const Row &r, c
                 }
             }
         }
+        if (need && __any_sync(kFull, lose)) {
+            const uint64_t wl = (static_cast<uint64_t>(__reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32))) << 32 |
+                                 __reduce_or_sync(kFull, static_cast<unsigned>(lo))) |
+                                fin64;
+            if ((wl & need) == need) {
+                const int64_t jend = min(le, j0 + kStep);
+                if (DROP && lane == 0) survivors += static_cast<unsigned>(le - jend);
+                return jend;
+            }
+        }
         if (more) {
 #pragma unroll
             for (int q = 0; q < kPer; ++q) ul[q] = un[q];
         }
     }
+    return le;
 }
 
 // Appends the next round's items of the vertices that lost in lanes with items_l > 0 (one
@@ -518,7 +538,7 @@ template <bool BATCH, bool COMPACT>
 __device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *coln, const DetItem &d,
                          unsigned *win, unsigned *wfin, unsigned *snap, DetItem *next, unsigned *cnt_next, int pass,
                          int lane, unsigned items_now, unsigned warps, bool merge_now, unsigned &st_deg,
-                         unsigned &st_cnt, unsigned &st_read, bool r1, unsigned long long &st_ent) {
+                         unsigned &st_cnt, unsigned &st_read, bool r1, unsigned long long &st_ent, uint64_t need) {
     const int32_t V = d.V;
     const uint32_t slot = d.slotf & kItemSlot;
     const bool multi = (d.slotf & kItemMulti) != 0;
@@ -565,9 +585,13 @@ __device__ void det_item(const RoundParams &P, const uint64_t *colc, uint64_t *c
     uint64_t lo = 0, flo = 0;
     bool lose = false;
     unsigned survivors = 0, written = 0;
-    sweep_item<COMPACT, true, true>(P, r, colc, d.list, d.lb, d.le, ul, dst, a + kAccNewLen, multi, lane, cv, pv, lo,
-                                    win, flo, wfin, lose, survivors, written, r1, r1 ? seed_of(P, V) : 0);
-    if (lane == 0) st_read += static_cast<unsigned>(d.le - d.lb);
+    // final colors 0..63 already in the slot (lanes 0 and 1 hold them)
+    const uint64_t fin64 = COMPACT ? (static_cast<uint64_t>(__shfl_sync(kFull, sm, 1)) << 32 | __shfl_sync(kFull, sm, 0))
+                                   : 0ull;
+    const int64_t jend = sweep_item<COMPACT, true, true>(P, r, colc, d.list, d.lb, d.le, ul, dst, a + kAccNewLen, multi,
+                                                         lane, cv, pv, lo, win, flo, wfin, lose, survivors, written,
+                                                         r1, r1 ? seed_of(P, V) : 0, dst ? 0ull : need, fin64);
+    if (lane == 0) st_read += static_cast<unsigned>(jend - d.lb);
     lose = __any_sync(kFull, lose);
     unsigned lo0 = __reduce_or_sync(kFull, static_cast<unsigned>(lo));
     unsigned lo1 = __reduce_or_sync(kFull, static_cast<unsigned>(lo >> 32));
@@ -948,6 +972,8 @@ __global__ void __launch_bounds__(kBlock, MINB) det_round_kernel(RoundParams P) 
         const DetItem *itc = reinterpret_cast<const DetItem *>(odd ? P.chunk0 : P.chunk1);
         // round 1 with the hash key: every neighbour's state is known without reading it
         const bool r1 = pass == 1 && P.priority == GC_PRIORITY_HASH;
+        // the colors a neighbour can have in this round (0..pass-1), for the early stop of a sweep
+        const uint64_t need = P.early_exit && pass <= 64 ? (~0ull >> (64 - pass)) : 0ull;
         DetItem *itn = reinterpret_cast<DetItem *>(odd ? P.chunk1 : P.chunk0);
         unsigned st_deg = 0, st_cnt = 0, st_read = 0;  // this warp's share of the round (< 2^31 each)
         unsigned long long st_ent = 0;  // list entries this thread appended to the next worklist
@@ -961,18 +987,19 @@ __global__ void __launch_bounds__(kBlock, MINB) det_round_kernel(RoundParams P) 
                 const DetItem d = item_of(w);
                 if (i + nw < nchunks) w = item_word(itc, i + nw, lane);
                 det_item<BATCH, COMPACT>(P, colc, coln, d, win, wfin, snap, itn, cn, pass, lane, nchunks,
-                                         static_cast<unsigned>(nw), merge_now, st_deg, st_cnt, st_read, r1, st_ent);
+                                         static_cast<unsigned>(nw), merge_now, st_deg, st_cnt, st_read, r1, st_ent,
+                                         need);
             }
         }
         for (unsigned base = static_cast<unsigned>(gw) * 32u; base < nsmall; base += static_cast<unsigned>(nw) * 32u) {
             const unsigned i = base + lane;
             bool lose = false;
-            int32_t V = 0, deg = 0;
+            int32_t V = 0, deg = 0, nread = 0;
             if (i < nsmall) {
                 V = __ldcg(smallc + i);
-                lose = det_small<BATCH>(P, colc, coln, V, deg, r1);
+                lose = det_small<BATCH>(P, colc, coln, V, deg, nread, r1, need);
                 st_deg += static_cast<unsigned>(deg);
-                st_read += static_cast<unsigned>(deg);
+                st_read += static_cast<unsigned>(nread);
                 st_cnt += 1;
                 if constexpr (BATCH) {
                     if (lose) note_graph_round(P, __ldg(P.vg + V), pass + 1);

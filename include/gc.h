@@ -111,7 +111,7 @@ typedef struct gc_options {
     void *stream;              /* cudaStream_t to run on; NULL = the context's own stream */
     int32_t max_rounds;        /* round cap; 0 = n + 1 (a worklist shrinks every round) */
     int32_t small_max_degree;  /* vertices up to this degree get one thread each (1..127); default 127 */
-    int32_t chunk;             /* adjacency entries per warp work item for larger vertices (32..1024, multiple of 32);
+    int32_t chunk;             /* adjacency entries per warp work item for larger vertices (32..8192, multiple of 32);
                                   default 1024 */
     int32_t block_size;        /* threads per block of the round kernel (256 is the only size); default 256 */
     int32_t blocks_per_sm;     /* resident blocks per SM for the round kernel.  0: the library picks the

@@ -335,7 +335,7 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
     const int32_t CH = (opt && opt->chunk) ? opt->chunk : 1024;
     const int32_t block = (opt && opt->block_size) ? opt->block_size : 256;
     if (T1 < 1 || T1 > 127) return set_last_error(GC_ERR_INVALID_ARG, "small_max_degree %d outside 1..127", T1);
-    if (CH < 32 || CH > 1024 || CH % 32) return set_last_error(GC_ERR_INVALID_ARG, "chunk %d invalid", CH);
+    if (CH < 32 || CH > 8192 || CH % 32) return set_last_error(GC_ERR_INVALID_ARG, "chunk %d invalid", CH);
     if (block != 256) return set_last_error(GC_ERR_INVALID_ARG, "block_size %d unsupported (256)", block);
     const int32_t opt_priority = opt ? opt->priority : GC_PRIORITY_HASH;
     if (opt_priority != GC_PRIORITY_HASH && opt_priority != GC_PRIORITY_LARGEST_FIRST &&
@@ -878,7 +878,7 @@ int gc_smallest_last(int32_t n, const int32_t *rowptr, const int32_t *colidx, in
     const int32_t T1 = (opt && opt->small_max_degree) ? opt->small_max_degree : 127;
     const int32_t CH = (opt && opt->chunk) ? opt->chunk : 1024;
     if (T1 < 1 || T1 > 127) return set_last_error(GC_ERR_INVALID_ARG, "small_max_degree %d outside 1..127", T1);
-    if (CH < 32 || CH > 1024 || CH % 32) return set_last_error(GC_ERR_INVALID_ARG, "chunk %d invalid", CH);
+    if (CH < 32 || CH > 8192 || CH % 32) return set_last_error(GC_ERR_INVALID_ARG, "chunk %d invalid", CH);
     Context *C = nullptr;
     GC_TRY(get_context(&C));
     std::lock_guard<std::mutex> lk(C->mu);

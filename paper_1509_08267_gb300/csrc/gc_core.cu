@@ -43,10 +43,13 @@
 namespace gc {
 namespace {
 
-constexpr int kCoreThreads = 1024;  // one block per SM: every block holds all m colors
+#ifndef GC_CORE_THREADS
+#define GC_CORE_THREADS 768
+#endif
+constexpr int kCoreThreads = GC_CORE_THREADS;  // one block per SM: every block holds all m colors
 constexpr int kCoreWarps = kCoreThreads / 32;
 #ifndef GC_CORE_PER
-#define GC_CORE_PER 4
+#define GC_CORE_PER 8
 #endif
 constexpr int kCorePer = GC_CORE_PER;  // entries per lane per step of a piece
 constexpr int kCoreStep = 32 * kCorePer;

@@ -259,7 +259,7 @@ def batched_object(args, rank, world, G):
         _, nc_b, rd_b = gc.color_batch(vo, eo, rp, ci, "det", HASH_SEED, out=out, options=tuned)
     torch.cuda.synchronize()
     t_batch = reduce_max((time.perf_counter() - t0) / steps, world, dev)
-    solo = torch.empty_like(out)
+    solo = torch.zeros_like(out)  # written once here: no first-touch cost inside the timed loop
     vo_h, eo_h = b.vtx_off, b.edge_off
     nc_s = np.zeros(b.G, np.int32)
     rd_s = np.zeros(b.G, np.int32)
@@ -375,13 +375,18 @@ def served_object(args, rank, world, count):
         st = srv.stats()
     with gc.Server(pool_vertices=pool_v, pool_entries=pool_e, mode="det", seed=HASH_SEED, device=local) as srv:
         t_sat, results_sat = replay(srv, [0.0] * len(graphs))
+    # one by one (host CSR in, colors out, as the server takes them); the library's staging buffers
+    # are grown first on the largest request, and the comparisons run after the timed loop
+    big = max(range(len(graphs)), key=lambda i: graphs[i].nnz)
+    gc.color(graphs[big].rowptr, graphs[big].colidx, "det", HASH_SEED)
     t1 = time.perf_counter()
+    solo_res = [gc.color(g.rowptr, g.colidx, "det", HASH_SEED) for g in graphs]
+    t_solo = time.perf_counter() - t1
     same = True
-    for i, g in enumerate(graphs):
-        r = gc.color(g.rowptr, g.colidx, "det", HASH_SEED)
+    for i, r in enumerate(solo_res):
         for res in (results[i], results_sat[i]):
             same &= bool(np.array_equal(r.colors, res[0])) and r.ncolors == res[1] and r.rounds == res[2]
-    t_solo = time.perf_counter() - t1
+    del solo_res
     # the same requests as one batch already on the device: co-scheduling all of them at once, with
     # no arrivals to wait for and no copies (an upper bound for the server)
     b = gg.pack(graphs)
@@ -491,6 +496,8 @@ def main():
     ci = torch.from_numpy(g.colidx).to(dev)
     out = torch.empty(g.n, dtype=torch.int32, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    # first touch outside the timed region: the first write of fresh device pages cost ~250 ms once
+    flush.fill_(0)
     prio = {"hash": gc.PRIORITY_HASH, "lf": gc.PRIORITY_LARGEST_FIRST, "sl": gc.PRIORITY_SMALLEST_LAST}[args.priority]
     mode = args.mode
     # the autotuner's options for this graph's class when its table is current, else the defaults

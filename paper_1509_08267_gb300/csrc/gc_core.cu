@@ -405,35 +405,35 @@ __device__ __forceinline__ bool cursor_next(PieceCursor &c, const CoreParams &Q,
     return true;
 }
 
-// Entries j0 + lane + 32 q of a piece; slots past its end read the sentinel m.
-__device__ __forceinline__ void load_piece_step(const CoreParams &Q, const Piece &p, int32_t j0, int lane, int32_t m,
+// Entries j0 + lane + 32 q of a piece; slots past its end read the piece's own vertex (its color is
+// the vertex's own, which a loser's window holds already -- the neighbour it lost to has it -- and
+// which a winner never uses; without the key bit it is no conflict).
+__device__ __forceinline__ void load_piece_step(const CoreParams &Q, const Piece &p, int32_t j0, int lane,
                                                 int32_t (&e)[kCorePer]) {
 #pragma unroll
     for (int q = 0; q < kCorePer; ++q) {
         const int32_t j = j0 + lane + 32 * q;
-        e[q] = j < p.cnt ? __ldcg(Q.pool + p.off + j) : m;
+        e[q] = j < p.cnt ? __ldcg(Q.pool + p.off + j) : p.v;
     }
 }
 
 // One step of a piece: every slot's neighbour color into the round window (colors below 128 in
-// two per-lane registers, the warp's shared window up to 512) and the conflict flag (a neighbour with
-// a smaller key and the vertex's color cv).  COMPACT: also the FINAL slots (counted, the sentinel as
-// one; their colors into the final window) and the slots kept.
-// Saturated 8-bit colors (255, but not the sentinel) are looked up exactly in cex.
+// two per-lane registers, the warp's shared window up to 512) and the conflict flag (an entry with
+// the key bit whose neighbour has the vertex's color: tgt = cv | kCoreSmaller, never matched when cv
+// is saturated).  COMPACT: also the FINAL neighbours' colors into the final window, and the slots
+// kept (entries before `nvalid`, the entries of the step inside the piece, that are not FINAL).
+// Saturated 8-bit colors (255) are looked up exactly in cex.
 template <bool COMPACT>
-__device__ __forceinline__ void consume_step(const Shared &S, const int32_t (&e)[kCorePer], int32_t m, int32_t cv,
+__device__ __forceinline__ void consume_step(const Shared &S, const int32_t (&e)[kCorePer], uint32_t tgt, int32_t cv,
                                              const int32_t *cex_cur, uint64_t &lo, uint64_t &mid, uint64_t &flo,
-                                             unsigned *win, unsigned *wfin, unsigned &conflict, unsigned &nfin,
-                                             unsigned &keepm) {
+                                             unsigned *win, unsigned *wfin, unsigned &conflict, int32_t nvalid,
+                                             int lane, unsigned &keepm) {
     unsigned cs[kCorePer];
 #pragma unroll
     for (int q = 0; q < kCorePer; ++q) cs[q] = S.color8(static_cast<uint32_t>(e[q]) & ~kCoreSmaller);
-    // an 8-bit color below 255 equals cv only when it is cv; 255 is compared exactly below
-    const unsigned cv8 = cv < static_cast<int32_t>(kSat8) ? static_cast<unsigned>(cv) : 0x1000u;
     unsigned sat = 0;
 #pragma unroll
     for (int q = 0; q < kCorePer; ++q) {
-        const uint32_t id = static_cast<uint32_t>(e[q]) & ~kCoreSmaller;
         const unsigned c = cs[q];
         const uint64_t b = 1ull << (c & 63u);
         if (c < 64u) {
@@ -443,18 +443,18 @@ __device__ __forceinline__ void consume_step(const Shared &S, const int32_t (&e)
         } else if (c < kSat8) {
             atomicOr(&win[c >> 5], 1u << (c & 31));
         }
-        conflict |= (static_cast<uint32_t>(e[q]) >> 31) & static_cast<unsigned>(c == cv8);
-        sat |= static_cast<unsigned>(c == kSat8 && id != static_cast<uint32_t>(m)) << q;
+        conflict |= static_cast<unsigned>(((static_cast<uint32_t>(e[q]) & kCoreSmaller) | c) == tgt);
+        sat |= static_cast<unsigned>(c == kSat8) << q;
         if constexpr (COMPACT) {
+            const uint32_t id = static_cast<uint32_t>(e[q]) & ~kCoreSmaller;
             const unsigned fin = S.final_bit(id);
-            nfin += fin;
             if (fin && c < kSat8) {
                 if (c < 64u)
                     flo |= b;
                 else
                     atomicOr(&wfin[c >> 5], 1u << (c & 31));
             }
-            keepm |= (fin ^ 1u) << q;
+            keepm |= static_cast<unsigned>(!fin && lane + 32 * q < nvalid) << q;
         }
     }
     if (sat) {
@@ -538,7 +538,7 @@ __device__ void core_round_warp(const RoundParams &P, const CoreParams &Q, const
     unsigned pidx = 0;
     if (!cursor_next(cur, Q, list, nact, nw, lane, p, pidx)) return;
     int32_t e[kCorePer];
-    load_piece_step(Q, p, 0, lane, m, e);
+    load_piece_step(Q, p, 0, lane, e);
     // words 32..63 of the piece's vertex record: final window, row fields, piece range
     unsigned rx = __ldcg(core_rec(Q, p.v) + 32 + lane);
     unsigned pend = 0, pend_pb = 0, pend_np = 0, npend = 0;
@@ -551,6 +551,9 @@ __device__ void core_round_warp(const RoundParams &P, const CoreParams &Q, const
         __syncwarp();
         const unsigned own8 = S.color8(static_cast<uint32_t>(p.v));  // own color (never final on the worklist)
         const int32_t cv = own8 == kSat8 ? __ldcg(cex_cur + p.v) : static_cast<int32_t>(own8);
+        // the conflict test's target: the key bit and the vertex's 8-bit color (never matched when it
+        // is saturated; those are compared exactly)
+        const uint32_t tgt = kCoreSmaller | (own8 == kSat8 ? 0x1000u : own8);
         // a piece drops its FINAL neighbours in place once the worklist has lost a quarter of its
         // vertices since the piece last did (its `flags` field records that worklist size)
         const bool compact = 4ull * nv < 3ull * static_cast<unsigned>(p.flags);
@@ -571,13 +574,13 @@ __device__ void core_round_warp(const RoundParams &P, const CoreParams &Q, const
                 if (more) rxn = __ldcg(core_rec(Q, pn.v) + 32 + lane);
             }
             int32_t en[kCorePer];
-            if (more) load_piece_step(Q, pn, jn, lane, m, en);
-            unsigned nfin = 0, keepm = 0;
+            if (more) load_piece_step(Q, pn, jn, lane, en);
+            unsigned keepm = 0;
             if (compact)
-                consume_step<true>(S, e, m, cv, cex_cur, lo, mid, flo, win, wfin, conflict, nfin, keepm);
+                consume_step<true>(S, e, tgt, cv, cex_cur, lo, mid, flo, win, wfin, conflict, p.cnt - j0, lane, keepm);
             else
-                consume_step<false>(S, e, m, cv, cex_cur, lo, mid, flo, win, wfin, conflict, nfin, keepm);
-            const unsigned kept = compact ? static_cast<unsigned>(kCoreStep) - __reduce_add_sync(kFull, nfin) : 0u;
+                consume_step<false>(S, e, tgt, cv, cex_cur, lo, mid, flo, win, wfin, conflict, p.cnt - j0, lane, keepm);
+            const unsigned kept = compact ? __reduce_add_sync(kFull, static_cast<unsigned>(__popc(keepm))) : 0u;
             if (compact && kept) {
                 // in place: the positions written never pass the ones already read
                 unsigned pos = kept_total;

@@ -360,31 +360,56 @@ __device__ __forceinline__ void prefetch_piece(const CoreParams &Q, int32_t off,
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
 }
 
-// The round's active pieces a warp takes: entries gw, gw + nw, gw + 2 nw, ... of the round's list of
-// pieces (the pieces of its worklist vertices; every piece in the first round), in batches of 32 (one
-// per lane).  Pieces without entries are taken too: they count towards their vertex's pieces done.
+// The round's active pieces a warp takes, in batches of up to 32 (one per lane).  In a round with
+// few pieces they are dealt statically: entries gw, gw + nw, gw + 2 nw, ... of the round's list of
+// pieces (the pieces of its worklist vertices; every piece in the first round).  In a round with many
+// (at least kGrabMin per warp) each batch is taken from the round's grab counter, in chunks that
+// shrink with what is left (guided self-scheduling: the pieces differ in size up to kCorePiece
+// entries, and a warp that drew large ones would otherwise hold the whole grid at the barrier).
+// Pieces without entries are taken too: they count towards their vertex's pieces done.
+constexpr unsigned kGrabMin = 4;
 struct PieceCursor {
-    unsigned base;  // first list position of the current batch
+    unsigned base;  // static: first list position of the current batch; dynamic: last grab's start
     int4 d;         // this lane's piece in the batch
     unsigned idx;   // its index
-    unsigned act;   // lanes of the batch not yet taken whose piece has entries
+    unsigned act;   // lanes of the batch not yet taken
+    unsigned *grab; // the round's grab counter (dynamic dealing), or nullptr
 };
 
-__device__ __forceinline__ void cursor_load(PieceCursor &c, const CoreParams &Q, const int32_t *list, unsigned nact,
-                                            unsigned nw, int lane) {
-    const unsigned i = c.base + static_cast<unsigned>(lane) * nw;
-    bool a = false;
+__device__ __forceinline__ void cursor_fill(PieceCursor &c, const CoreParams &Q, const int32_t *list, unsigned i,
+                                            bool in, int lane) {
     c.d = make_int4(0, 0, 0, 0);
     c.idx = 0;
-    if (i < nact) {
+    if (in) {
         c.idx = list ? static_cast<unsigned>(__ldcg(list + i)) : i;
         c.d = __ldcg(Q.pieces + c.idx);
-        a = true;
     }
-    c.act = __ballot_sync(kFull, a);
+    c.act = __ballot_sync(kFull, in);
     // the batch's second active piece (the first is loaded into registers right away)
     const unsigned second = c.act & (c.act - 1u);
     if (second && lane == __ffs(second) - 1) prefetch_piece(Q, c.d.y, c.d.z);
+}
+
+// The next batch: false when the round has no piece left for this warp.
+__device__ __forceinline__ bool cursor_load(PieceCursor &c, const CoreParams &Q, const int32_t *list, unsigned nact,
+                                            unsigned nw, int lane) {
+    if (!c.grab) {
+        if (c.base >= nact) return false;
+        const unsigned i = c.base + static_cast<unsigned>(lane) * nw;
+        cursor_fill(c, Q, list, i, i < nact, lane);
+        return true;
+    }
+    const unsigned left = nact > c.base ? nact - c.base : 0u;
+    unsigned chunk = left / (2u * nw);
+    chunk = chunk < 1u ? 1u : (chunk > 32u ? 32u : chunk);
+    unsigned b = 0;
+    if (lane == 0) b = atomicAdd(c.grab, chunk);
+    b = __shfl_sync(kFull, b, 0);
+    c.base = b;
+    if (b >= nact) return false;
+    const unsigned i = b + static_cast<unsigned>(lane);
+    cursor_fill(c, Q, list, i, static_cast<unsigned>(lane) < chunk && i < nact, lane);
+    return true;
 }
 
 // Next piece of the warp (false when there is none); its index is *idx.  The piece after the next
@@ -392,9 +417,8 @@ __device__ __forceinline__ void cursor_load(PieceCursor &c, const CoreParams &Q,
 __device__ __forceinline__ bool cursor_next(PieceCursor &c, const CoreParams &Q, const int32_t *list, unsigned nact,
                                             unsigned nw, int lane, Piece &out, unsigned &idx) {
     while (c.act == 0u) {
-        c.base += 32u * nw;
-        if (c.base >= nact) return false;
-        cursor_load(c, Q, list, nact, nw, lane);
+        if (!c.grab) c.base += 32u * nw;
+        if (!cursor_load(c, Q, list, nact, nw, lane)) return false;
     }
     const int l = __ffs(c.act) - 1;
     c.act &= c.act - 1u;
@@ -527,13 +551,15 @@ __device__ __forceinline__ void flush_pending(unsigned pend, unsigned pend_pb, u
 template <bool BATCH>
 __device__ void core_round_warp(const RoundParams &P, const CoreParams &Q, const Shared &S, const int32_t *cex_cur,
                                 const int32_t *list, unsigned nact, int32_t m, unsigned nv, int pass,
-                                const uint64_t *col_r0, unsigned *cn, unsigned gw, unsigned nw, int lane,
-                                unsigned *win, unsigned *wfin, unsigned &st_read, unsigned &st_deg, unsigned &st_cnt) {
+                                const uint64_t *col_r0, unsigned *cn, unsigned *grab, unsigned gw, unsigned nw,
+                                int lane, unsigned *win, unsigned *wfin, unsigned &st_read, unsigned &st_deg,
+                                unsigned &st_cnt) {
     PieceCursor cur;
-    cur.base = gw;
-    if (cur.base >= nact) return;
+    cur.act = 0;
+    cur.grab = nact >= kGrabMin * nw ? grab : nullptr;
+    cur.base = cur.grab ? 0u : gw;
     const size_t nxt = static_cast<size_t>((pass & 1) ^ 1);
-    cursor_load(cur, Q, list, nact, nw, lane);
+    if (!cursor_load(cur, Q, list, nact, nw, lane)) return;
     Piece p;
     unsigned pidx = 0;
     if (!cursor_next(cur, Q, list, nact, nw, lane, p, pidx)) return;
@@ -803,8 +829,10 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
             // the round's pieces: all of them in the first round, then those the previous round listed
             const int32_t *list = pass == R0 ? nullptr : Q.active + static_cast<size_t>(pass & 1) * Q.max_pieces;
             const unsigned nact = pass == R0 ? npieces : cc.z;
-            core_round_warp<BATCH>(P, Q, S, cex_cur, list, nact, m, nv, pass, h.colc, cn, gw, nw, lane, s_win[wib],
-                                   s_fin[wib], st_read, st_deg, st_cnt);
+            // the round's grab counter: word 3 of its counter set (cleared two rounds ahead like the rest)
+            core_round_warp<BATCH>(P, Q, S, cex_cur, list, nact, m, nv, pass, h.colc, cn,
+                                   Q.cnt + 4 * (pass % 3) + 3, gw, nw, lane, s_win[wib], s_fin[wib], st_read, st_deg,
+                                   st_cnt);
 #ifdef GC_CORE_PROFILE
             __syncthreads();
             CORE_PROF(2, atomicMin);

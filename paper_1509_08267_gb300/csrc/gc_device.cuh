@@ -383,6 +383,17 @@ __device__ __forceinline__ void flush_sum(unsigned long long *dst, unsigned long
     if (threadIdx.x == 0 && s_sum) atomicAdd(dst, s_sum);
 }
 
+// The same for 32-bit sums.
+__device__ __forceinline__ void flush_sum_u32(unsigned *dst, unsigned x) {
+    __shared__ unsigned s_sum32;
+    if (threadIdx.x == 0) s_sum32 = 0;
+    __syncthreads();
+    x = __reduce_add_sync(0xffffffffu, x);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_sum32, x);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_sum32) atomicAdd(dst, s_sum32);
+}
+
 // Per-round statistics of a round kernel (GC_FLAG_STATS).
 __device__ __forceinline__ void flush_stats(const RoundParams &P, int pass, unsigned long long deg,
                                             unsigned long long cnt, unsigned long long reads) {

@@ -1217,9 +1217,13 @@ __device__ __forceinline__ int64_t checked_degree(const RoundParams &P, int32_t 
 // state words do not fit in L2 (large graphs, batches) the vertices in flight at any moment (and,
 // in a batch, their graphs' neighbours) stay within a few blocks whose state words L2 holds.
 template <bool BATCH, int MODE>
-__global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int32_t g_fixed) {
+__global__ void __launch_bounds__(256) setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int32_t g_fixed) {
     __shared__ unsigned s_hist[128];
-    const int lane = threadIdx.x & 31;
+    // block-wide reservations, one atomic per 256 vertices: larger vertices into P.items, vertices of
+    // degree <= T1 into the thread worklist when it is not degree-sorted
+    __shared__ unsigned s_w[8][2];
+    __shared__ unsigned s_base[2];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int pass = P.pass_begin;
     unsigned *cc = P.cnt + kCnt * (pass % 3);
     int32_t *small_cur = (pass & 1) ? P.small0 : P.small1;
@@ -1233,10 +1237,12 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
     const int64_t count = static_cast<int64_t>(v_end) - v_begin;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     unsigned long long st_ent = 0;  // list entries of the round's worklist (rows of its vertices)
-    for (int64_t base = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ll; base < count;
-         base += stride) {
-        const int32_t V = static_cast<int32_t>(v_begin + base + lane);
-        const bool in = base + lane < count;
+    unsigned long long st_list = 0;  // compact mode: list-pool entries of the larger vertices
+    unsigned st_chunks = 0;          // work items of the larger vertices
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < count; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        const int32_t V = static_cast<int32_t>(v_begin + i);
+        const bool in = i < count;
         int kind = 0;  // 1 = one thread, 2 = work items
         int32_t nch = 0;
         int64_t d = 0;
@@ -1274,6 +1280,10 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
             if (g_fixed >= 0 && kind != 0) note_graph_round(P, g_fixed, pass);
         }
         if (kind != 0) st_ent += static_cast<unsigned long long>(d);
+        if (kind == 2) {
+            st_chunks += static_cast<unsigned>(nch);
+            if (P.list_total) st_list += 2ull * static_cast<unsigned long long>(d);  // two list regions
+        }
         if (one_block) {
             if (kind == 1) atomicAdd(&s_hist[d], 1u);
         } else if (sort) {
@@ -1281,34 +1291,38 @@ __global__ void setup_kernel(RoundParams P, int32_t v_begin, int32_t v_end, int3
             const int32_t bin = kind == 1 ? sort_bin(P, V, d) : -1;
             const unsigned same = __match_any_sync(kFull, bin);
             if (kind == 1 && lane == __ffs(same) - 1) atomicAdd(P.deg_hist + bin, static_cast<unsigned>(__popc(same)));
-        } else {
-            warp_append(kind == 1, V, small_cur, cc + kCntSmall, lane);
         }
-        const unsigned m = __ballot_sync(kFull, kind == 2);
-        if (m) {
-            const int leader = __ffs(m) - 1;
-            const unsigned chunks = __reduce_add_sync(kFull, kind == 2 ? static_cast<unsigned>(nch) : 0u);
-            unsigned ib = 0;
-            if (lane == leader) {
-                ib = atomicAdd(P.tmp + 0, static_cast<unsigned>(__popc(m)));
-                atomicAdd(P.tmp + 1, chunks);
-            }
-            ib = __shfl_sync(kFull, ib, leader);
-            if (kind == 2) P.items[ib + __popc(m & lanemask_lt())] = V;
-            if (P.list_total) {
-                // compact mode: two list regions of deg entries per larger vertex
-                unsigned long long need = kind == 2 ? 2ull * static_cast<unsigned long long>(d) : 0ull;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) need += __shfl_xor_sync(kFull, need, o);
-                if (lane == leader) atomicAdd(P.list_total, need);
-            }
+        const unsigned m2 = __ballot_sync(kFull, kind == 2);
+        const unsigned m1 = sort ? 0u : __ballot_sync(kFull, kind == 1);
+        if (lane == 0) {
+            s_w[wib][0] = __popc(m2);
+            s_w[wib][1] = __popc(m1);
         }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned t0 = 0, t1 = 0;
+            for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
+                const unsigned a0 = s_w[w][0], a1 = s_w[w][1];
+                s_w[w][0] = t0;
+                s_w[w][1] = t1;
+                t0 += a0;
+                t1 += a1;
+            }
+            s_base[0] = t0 ? atomicAdd(P.tmp + 0, t0) : 0u;
+            s_base[1] = t1 ? atomicAdd(cc + kCntSmall, t1) : 0u;
+        }
+        __syncthreads();
+        if (kind == 2) P.items[s_base[0] + s_w[wib][0] + __popc(m2 & lanemask_lt())] = V;
+        if (!sort && kind == 1) small_cur[s_base[1] + s_w[wib][1] + __popc(m1 & lanemask_lt())] = V;
+        __syncthreads();  // s_w / s_base are rewritten by the next iteration
     }
     if (one_block) {
         __syncthreads();
         for (int t = threadIdx.x; t < 128; t += blockDim.x)
             if (s_hist[t]) atomicAdd(P.deg_hist + t, s_hist[t]);
     }
+    flush_sum_u32(P.tmp + 1, st_chunks);
+    if (P.list_total) flush_sum(P.list_total, st_list);
     if (P.ecnt) flush_sum(P.ecnt + pass % 3, st_ent);
 }
 
@@ -1385,53 +1399,112 @@ __global__ void scatter_small_kernel(RoundParams P, int32_t v_begin, int32_t v_e
 // items split its row evenly with COMPACT, else into CH-entry pieces); in-place items are int4
 // {vertex, item index, slot, items}.
 template <bool BATCH, bool COMPACT, int MODE>
-__global__ void expand_kernel(RoundParams P, int32_t n_items) {
+__global__ void __launch_bounds__(256) expand_kernel(RoundParams P, int32_t n_items) {
+    // block-wide reservations: per 256 vertices one atomic per counter (the counters are shared by
+    // the whole grid; one atomic per vertex would serialise on them)
+    __shared__ unsigned s_w[8][4];
+    __shared__ unsigned long long s_wl[8];
+    __shared__ unsigned s_base[4];
+    __shared__ unsigned long long s_lbase;
     if (n_items < 0) n_items = static_cast<int32_t>(__ldcg(P.tmp));  // count left on the device by setup
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int pass = P.pass_begin;
     unsigned *cc = P.cnt + kCnt * (pass % 3);
-    for (int32_t s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n_items; s += nw) {
-        const int32_t V = P.items[s];
-        const Row r = load_row<BATCH>(P, V);
-        const int32_t deg = static_cast<int32_t>(r.e - r.b);
-        const int32_t nch = (deg + P.CH - 1) / P.CH;
-        unsigned slot = 0, cb = 0;
-        if (lane == 0) {
-            slot = atomicAdd(cc + kCntItems, 1u);
-            cb = atomicAdd(cc + kCntChunks, static_cast<unsigned>(nch));
-            if ((MODE == GC_MODE_DETERMINISTIC || COMPACT) && nch > 1) atomicAdd(cc + kCntMulti, 1u);
+    const bool lists = COMPACT && !P.slot_per_vertex;
+    for (int32_t s0 = blockIdx.x * blockDim.x; s0 < n_items; s0 += gridDim.x * blockDim.x) {
+        const int32_t s = s0 + static_cast<int32_t>(threadIdx.x);
+        const bool in = s < n_items;
+        int32_t V = 0, deg = 0, nch = 0;
+        Row r{};
+        if (in) {
+            V = P.items[s];
+            r = load_row<BATCH>(P, V);
+            deg = static_cast<int32_t>(r.e - r.b);
+            nch = (deg + P.CH - 1) / P.CH;
         }
-        slot = __shfl_sync(kFull, slot, 0);
-        cb = __shfl_sync(kFull, cb, 0);
+        // warp-inclusive scans of the vertex's chunks and list space
+        unsigned ich = static_cast<unsigned>(nch);
+        unsigned long long il = lists && in ? 2ull * static_cast<unsigned long long>(deg) : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, ich, o);
+            const unsigned long long z = __shfl_up_sync(kFull, il, o);
+            if (lane >= o) {
+                ich += y;
+                il += z;
+            }
+        }
+        const unsigned mi = __ballot_sync(kFull, in), mm = __ballot_sync(kFull, in && nch > 1);
+        if (lane == 31) {
+            s_w[wib][0] = __popc(mi);
+            s_w[wib][1] = ich;
+            s_w[wib][2] = __popc(mm);
+            s_wl[wib] = il;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned t[3] = {0, 0, 0};
+            unsigned long long tl = 0;
+            for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
+                const unsigned a0 = s_w[w][0], a1 = s_w[w][1], a2 = s_w[w][2];
+                const unsigned long long al = s_wl[w];
+                s_w[w][0] = t[0];
+                s_w[w][1] = t[1];
+                s_w[w][2] = t[2];
+                s_wl[w] = tl;
+                t[0] += a0;
+                t[1] += a1;
+                t[2] += a2;
+                tl += al;
+            }
+            s_base[0] = t[0] ? atomicAdd(cc + kCntItems, t[0]) : 0u;
+            s_base[1] = t[1] ? atomicAdd(cc + kCntChunks, t[1]) : 0u;
+            if ((MODE == GC_MODE_DETERMINISTIC || COMPACT) && t[2]) atomicAdd(cc + kCntMulti, t[2]);
+            s_lbase = lists && tl ? atomicAdd(P.list_alloc, tl) : 0ull;
+        }
+        __syncthreads();
+        // this lane's slot, first chunk and list offset
+        unsigned slot = s_base[0] + s_w[wib][0] + __popc(mi & lanemask_lt());
+        const unsigned cb = s_base[1] + s_w[wib][1] + ich - static_cast<unsigned>(nch);
+        const unsigned long long loff =
+            s_lbase + s_wl[wib] + il - (lists && in ? 2ull * static_cast<unsigned long long>(deg) : 0ull);
         if (COMPACT && P.slot_per_vertex) slot = static_cast<unsigned>(V);
-        unsigned *a = P.acc + static_cast<size_t>(slot) * kAccStride;
-        a[lane] = 0u;
-        unsigned hi = 0u;
-        if (COMPACT) {
-            // the list starts as the CSR row; the two list regions in the pool
-            unsigned long long off = 2ull * static_cast<unsigned long long>(r.b);
-            if (!P.slot_per_vertex) {
-                if (lane == 0) off = atomicAdd(P.list_alloc, 2ull * static_cast<unsigned long long>(deg));
-                off = __shfl_sync(kFull, off, 0);
+        __syncthreads();  // s_w / s_base are rewritten by the next iteration
+        // the warp writes each of its vertices' slot and work items together
+        for (unsigned pm = mi; pm; pm &= pm - 1u) {
+            const int l = __ffs(pm) - 1;
+            const int32_t Vl = __shfl_sync(kFull, V, l);
+            const int32_t degl = __shfl_sync(kFull, deg, l);
+            const int32_t nchl = __shfl_sync(kFull, nch, l);
+            const unsigned slotl = __shfl_sync(kFull, slot, l), cbl = __shfl_sync(kFull, cb, l);
+            const int64_t rb = static_cast<int64_t>(__shfl_sync(kFull, static_cast<unsigned long long>(r.b), l));
+            const int32_t vb = __shfl_sync(kFull, r.vbase, l), ngl = __shfl_sync(kFull, r.ng, l);
+            unsigned *acc = P.acc + static_cast<size_t>(slotl) * kAccStride;
+            acc[lane] = 0u;
+            unsigned hi = 0u;
+            if (COMPACT) {
+                // the list starts as the CSR row; the two list regions in the pool
+                const unsigned long long off = P.slot_per_vertex ? 2ull * static_cast<unsigned long long>(rb)
+                                                                 : __shfl_sync(kFull, loff, l);
+                if (lane == kAccLen - 32) hi = static_cast<unsigned>(degl);
+                if (lane == kAccOffLo - 32) hi = static_cast<unsigned>(off);
+                if (lane == kAccOffHi - 32) hi = static_cast<unsigned>(off >> 32);
+                if (lane == kAccDeg - 32) hi = static_cast<unsigned>(degl);
             }
-            if (lane == kAccLen - 32) hi = static_cast<unsigned>(deg);
-            if (lane == kAccOffLo - 32) hi = static_cast<unsigned>(off);
-            if (lane == kAccOffHi - 32) hi = static_cast<unsigned>(off >> 32);
-            if (lane == kAccDeg - 32) hi = static_cast<unsigned>(deg);
-        }
-        a[32 + lane] = hi;
-        if constexpr (MODE == GC_MODE_DETERMINISTIC || COMPACT) {
-            DetItem *cur = reinterpret_cast<DetItem *>((pass & 1) ? P.chunk0 : P.chunk1);
-            const int32_t per = COMPACT ? (deg + nch - 1) / nch : P.CH;
-            const uint32_t slotf = slot | (nch > 1 ? kItemMulti : 0u);
-            for (int32_t q = lane; q < nch; q += 32) {
-                const int32_t lb = q * per;
-                store_item(cur + cb + q, P.colidx + r.b, V, slotf, lb, min(deg, lb + per), r.vbase, r.ng, nch, deg);
+            acc[32 + lane] = hi;
+            if constexpr (MODE == GC_MODE_DETERMINISTIC || COMPACT) {
+                DetItem *cur = reinterpret_cast<DetItem *>((pass & 1) ? P.chunk0 : P.chunk1);
+                const int32_t per = COMPACT ? (degl + nchl - 1) / nchl : P.CH;
+                const uint32_t slotf = slotl | (nchl > 1 ? kItemMulti : 0u);
+                for (int32_t q = lane; q < nchl; q += 32) {
+                    const int32_t lb = q * per;
+                    store_item(cur + cbl + q, P.colidx + rb, Vl, slotf, lb, min(degl, lb + per), vb, ngl, nchl, degl);
+                }
+            } else {
+                int4 *cur = (pass & 1) ? P.chunk0 : P.chunk1;
+                for (int32_t q = lane; q < nchl; q += 32)
+                    cur[cbl + q] = make_int4(Vl, q, static_cast<int32_t>(slotl), nchl);
             }
-        } else {
-            int4 *cur = (pass & 1) ? P.chunk0 : P.chunk1;
-            for (int32_t q = lane; q < nch; q += 32) cur[cb + q] = make_int4(V, q, static_cast<int32_t>(slot), nch);
         }
     }
 }
@@ -2193,17 +2266,35 @@ __global__ void __launch_bounds__(kBlock, kWideBlocks) peel_kernel(RoundParams P
 // Final statistics over vertices [v_begin, v_end): one bit per (graph, color), largest color per
 // graph, and an optional copy of the colors.
 template <bool BATCH>
-__global__ void count_mark_kernel(RoundParams P, const int32_t *colors_sel, int32_t v_begin, int32_t v_end,
-                                  unsigned *bitmap, int32_t *gmax, int32_t *out) {
+__global__ void __launch_bounds__(256) count_mark_kernel(RoundParams P, const int32_t *colors_sel, int32_t v_begin,
+                                                         int32_t v_end, unsigned *bitmap, int32_t *gmax, int32_t *out) {
+    // single graph: colors below kMarkWords * 32 are marked in a shared bitmap and the largest color is
+    // reduced per block first (every thread hitting the same few words and the same maximum would
+    // serialise on them)
+    constexpr int kMarkWords = 128;
+    __shared__ unsigned s_bits[kMarkWords];
+    __shared__ int32_t s_max;
+    if (!BATCH) {
+        for (int t = threadIdx.x; t < kMarkWords; t += blockDim.x) s_bits[t] = 0u;
+        if (threadIdx.x == 0) s_max = -1;
+        __syncthreads();
+    }
     const uint64_t *state = (colors_sel && (*colors_sel & 1)) ? P.col1 : P.col0;
     const bool copy = out != nullptr && P.err[0] == 0;
     const int64_t count = static_cast<int64_t>(v_end) - v_begin;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    int32_t tmax = -1;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride) {
         const int32_t V = static_cast<int32_t>(v_begin + i);
         const int32_t c = color_of(__ldcg(state + V));
         if (copy) out[i] = c;
         if (c < 0) continue;
+        if (!BATCH && c < 32 * kMarkWords) {
+            const unsigned m = 1u << (c & 31);
+            if (!(s_bits[c >> 5] & m)) atomicOr(&s_bits[c >> 5], m);
+            tmax = max(tmax, c);
+            continue;
+        }
         int32_t g = 0;
         int64_t bit = c;
         if constexpr (BATCH) {
@@ -2214,6 +2305,14 @@ __global__ void count_mark_kernel(RoundParams P, const int32_t *colors_sel, int3
         unsigned *w = bitmap + (bit >> 5);
         if (!(__ldcg(w) & m)) atomicOr(w, m);
         if (__ldcg(gmax + g) < c) atomicMax(gmax + g, c);
+    }
+    if (!BATCH) {
+        tmax = __reduce_max_sync(kFull, tmax);
+        if ((threadIdx.x & 31) == 0 && tmax >= 0) atomicMax(&s_max, tmax);
+        __syncthreads();
+        for (int t = threadIdx.x; t < kMarkWords; t += blockDim.x)
+            if (s_bits[t]) atomicOr(bitmap + t, s_bits[t]);
+        if (threadIdx.x == 0 && s_max >= 0 && __ldcg(gmax) < s_max) atomicMax(gmax, s_max);
     }
 }
 
@@ -2416,7 +2515,7 @@ cudaError_t launch_sort_small(const RoundParams &P, bool batch, int32_t v_begin,
 cudaError_t launch_expand(const RoundParams &P, int mode, bool batch, bool compact, int32_t n_items,
                           cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
-    const int grid = n_items < 0 ? sm_count() * 8 : grid_for(static_cast<int64_t>(n_items) * 32, 256, sm_count() * 16);
+    const int grid = n_items < 0 ? sm_count() * 8 : grid_for(static_cast<int64_t>(n_items), 256, sm_count() * 8);
     constexpr int D = GC_MODE_DETERMINISTIC, I = GC_MODE_INPLACE;
     if (mode == GC_MODE_DETERMINISTIC) {
         if (batch) {

@@ -111,6 +111,12 @@ __device__ void core_init_vertex(const RoundParams &P, const CoreParams &Q, int3
     Q.cex[Q.max_v + local] = c;
     Q.c8[local] = static_cast<uint8_t>(sat8(c));
     Q.c8[Q.max_v + local] = static_cast<uint8_t>(sat8(c));
+    // hash key: the state word of round R0 carries the local id in place of the priority bits (the
+    // row build then gets a neighbour's finality, color and local id in one gather and recomputes
+    // the key from the id); nothing reads those bits of a worklist vertex again, and the write-back
+    // rewrites the whole word
+    if (P.priority == GC_PRIORITY_HASH)
+        const_cast<uint64_t *>(colc)[V] = pack_state(c, static_cast<uint32_t>(local), false);
     const uint4 z = make_uint4(0, 0, 0, 0);
 #pragma unroll
     for (int w = 0; w < 32; w += 4) stcg4(rec + w, z);
@@ -200,7 +206,10 @@ __global__ void __launch_bounds__(kFillThreads) core_fill_kernel(RoundParams P, 
         }
         const int32_t local = __ldcg(P.items + V);
         unsigned *rec = core_rec(Q, local);
-        const uint32_t pv = prio_of(__ldcg(h.colc + V));
+        const bool hash_key = P.priority == GC_PRIORITY_HASH;
+        const uint64_t seed = hash_key ? seed_of(P, V) : 0ull;
+        const uint64_t hv = hash_key ? vertex_hash(seed, static_cast<uint32_t>(r.lv)) : 0ull;
+        const uint32_t pv = hash_key ? 0u : prio_of(__ldcg(h.colc + V));
         const uint64_t off = static_cast<uint64_t>(__ldcg(rec + kCoreOffLo)) |
                              (static_cast<uint64_t>(__ldcg(rec + kCoreOffHi)) << 32);
         int32_t *dst = Q.pool + off;
@@ -228,7 +237,8 @@ __global__ void __launch_bounds__(kFillThreads) core_fill_kernel(RoundParams P, 
 #pragma unroll
             for (int q = 0; q < kFillPer; ++q) {
                 loc[q] = -1;
-                if (st[q] != kNoNeighbour && !final_of(st[q])) loc[q] = __ldcg(P.items + r.vbase + ul[q]);
+                if (st[q] != kNoNeighbour && !final_of(st[q]))
+                    loc[q] = hash_key ? static_cast<int32_t>(prio_of(st[q])) : __ldcg(P.items + r.vbase + ul[q]);
             }
             uint32_t ev[kFillPer];
             unsigned keepm = 0;
@@ -245,8 +255,14 @@ __global__ void __launch_bounds__(kFillThreads) core_fill_kernel(RoundParams P, 
                             atomicOr(&wfin[c >> 5], 1u << (c & 31));
                     } else if (static_cast<unsigned>(loc[q]) < m) {
                         keepm |= 1u << q;
-                        const bool smaller = key_less_in(prio_of(st[q]), pv, static_cast<uint32_t>(ul[q]),
-                                                         static_cast<uint32_t>(r.lv), P, V);
+                        bool smaller;
+                        if (hash_key) {
+                            const uint64_t hu = vertex_hash(seed, static_cast<uint32_t>(ul[q]));
+                            smaller = hu < hv || (hu == hv && ul[q] < r.lv);
+                        } else {
+                            smaller = key_less_in(prio_of(st[q]), pv, static_cast<uint32_t>(ul[q]),
+                                                  static_cast<uint32_t>(r.lv), P, V);
+                        }
                         ev[q] = static_cast<uint32_t>(loc[q]) | (smaller ? kCoreSmaller : 0u);
                     } else {
                         // every vertex that is not final is on the worklist; anything else is a bug
@@ -750,7 +766,10 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
     // work is dealt to warps interleaved over the blocks, so a small round spreads over every SM
     const unsigned gw = static_cast<unsigned>(wib) * gridDim.x + blockIdx.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0) Q.m[1] = static_cast<unsigned>(m);  // for the write-back
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // for the write-back
+        Q.m[1] = static_cast<unsigned>(m);
+        Q.m[3] = static_cast<unsigned>(R0);
+    }
     Shared S;
     S.col = s_dyn;
     S.fin = reinterpret_cast<unsigned *>(s_dyn + Q.max_v);
@@ -851,12 +870,15 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
 // Final colors of the core into both state buffers (FINAL set), where the color count reads them.
 __global__ void core_writeback_kernel(RoundParams P, CoreParams Q) {
     if (__ldcg(P.core_go) == 0) return;
-    const int64_t m = __ldcg(Q.m + 1);  // the round kernel rewrote passes[0]; it recorded m here
+    // the round kernel rewrote passes[0]; it recorded m and the hand-over round here
+    const int64_t m = __ldcg(Q.m + 1);
+    // the priority bits from the buffer round R0 did not read (the other one may carry local ids)
+    const uint64_t *prio_src = (__ldcg(Q.m + 3) & 1u) ? P.col1 : P.col0;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int32_t V = static_cast<int32_t>(__ldcg(core_rec(Q, i) + kCoreGid));
         const int32_t c = __ldcg(Q.cex + i);
-        const uint64_t w = pack_state(c, prio_of(__ldcg(P.col0 + V)), true);
+        const uint64_t w = pack_state(c, prio_of(__ldcg(prio_src + V)), true);
         P.col0[V] = w;
         P.col1[V] = w;
     }

@@ -151,7 +151,7 @@ struct RoundParams {
 constexpr uint32_t kCoreSmaller = 0x80000000u;
 constexpr int64_t kCoreEntries = int64_t{1} << 27;  // list entries the core phase takes at most
 #ifndef GC_CORE_PIECE
-#define GC_CORE_PIECE 2048
+#define GC_CORE_PIECE 4096
 #endif
 constexpr int kCorePiece = GC_CORE_PIECE;
 // Per core vertex, kCoreRecWords words: [0, 16) the round's window of neighbour colors 0..511,

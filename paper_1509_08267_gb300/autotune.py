@@ -145,7 +145,7 @@ def main():
             table = {}
     else:
         samples = {}
-        for cls, make in [("powerlaw-large", lambda: gg.workload("rmat20")),
+        for cls, make in [("powerlaw-large", lambda: gg.workload("rmat22")),
                           ("uniform-large", lambda: gg.stencil27(96)),
                           ("uniform-small", lambda: gg.workload("er10k")),
                           ("powerlaw-small", lambda: gg.rmat(16, 12, 5))]:

@@ -352,9 +352,10 @@ def served_object(args, rank, world, count):
     gaps = [-math_log(1.0 - ((gg.draw(4, 10_000_000 + i) >> 11) / 9007199254740992.0)) / rate for i in idx]
     pv = sum(g.n for g in graphs) + 1
     pe = sum(g.nnz for g in graphs) + 1
-    # a pool that admits the whole replay at once (about 4 GB of adjacency on a 280 GB device)
-    pool_v = min(pv, 64_000_000)
-    pool_e = min(pe, 2_000_000_000)
+    # a bounded pool (a larger one that admits the whole replay at once measured 6% more throughput
+    # at twice the p50 and p99 latency)
+    pool_v = min(pv, 16_000_000)
+    pool_e = min(pe, 600_000_000)
     m_mine = sum(g.nnz for g in graphs) / 2
 
     def replay(srv, arrivals):

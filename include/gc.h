@@ -112,13 +112,14 @@ typedef struct gc_options {
     int32_t max_rounds;        /* round cap; 0 = n + 1 (a worklist shrinks every round) */
     int32_t small_max_degree;  /* vertices up to this degree get one thread each (1..127); default 127 */
     int32_t chunk;             /* adjacency entries per warp work item for larger vertices (32..8192, multiple of 32);
-                                  default 1024 */
+                                  default 1024 (ordered mode: at most 128; 64 by default on a single graph) */
     int32_t block_size;        /* threads per block of the round kernel (256 is the only size); default 256 */
     int32_t blocks_per_sm;     /* resident blocks per SM for the round kernel.  0: the library picks the
                                   80-register variant (3 blocks per SM) when most adjacency entries are
                                   in vertices of degree > small_max_degree, else the 64-register one (4);
                                   3 or 4: that variant; 1 or 2: the 64-register one, capped.  It also
-                                  caps the ordered-mode and smallest-last peeling kernels (3 per SM) */
+                                  sets the ordered mode's blocks per SM (default 1 on a single graph,
+                                  3 on a batch) and caps the smallest-last peeling kernels (3 per SM) */
     int64_t spin_limit_ns;     /* grid-barrier wait limit in ns; 0 = 1e9.  A wait that runs out makes
                                   the call return GC_ERR_TIMEOUT with the device still usable */
     uint32_t flags;            /* GC_FLAG_* */

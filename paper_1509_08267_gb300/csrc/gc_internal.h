@@ -51,6 +51,7 @@ constexpr int kOrdMid = 32;  // degree <= kOrdMid (and > the small bound): an 8-
 // given coloring c, the color classes in decreasing color order.
 constexpr int32_t kPriorityRecolor = 3;
 constexpr int kOrdChunk = 128;
+constexpr int kOrdSingleChunk = 64;  // default work-item size of the ordered mode on a single graph
 constexpr int kOrdSlotWords = 32;
 
 // Worklist counters: three sets used round-robin (read / append / clear), kCnt words each.

@@ -155,6 +155,9 @@ def test_compact_reads_fewer_entries(gclib):
     np.testing.assert_array_equal(full.round_reads, full.wl_degsum)
     assert compact.round_reads.sum() == compact.entries_scanned
     assert (compact.round_reads <= compact.wl_degsum).all()
+    # round 1 (every color 0): a sweep stops at the first smaller-key neighbour, which for most
+    # vertices of a power-law graph comes early in the row
+    assert compact.round_reads[0] < 0.5 * compact.wl_degsum[0]
 
 
 def test_batch_full_sweep(gclib):

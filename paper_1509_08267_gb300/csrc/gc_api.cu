@@ -354,12 +354,10 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
 
     // scratch sized by n; work-item buffers are sized after binning
     GC_TRY(ensure(C.col0, 8 * n, "vertex state"));
-    GC_TRY(ensure(C.col0, 8 * n, "vertex state"));
     GC_TRY(ensure(C.col1, 8 * n, "vertex state"));
     GC_TRY(ensure(C.items, 4 * n, "worklist"));
     GC_TRY(ensure(C.small0, 4 * n, "worklist"));
     GC_TRY(ensure(C.small1, 4 * n, "worklist"));
-    GC_TRY(ensure(C.items, 4 * n, "worklist"));
     GC_TRY(ensure(C.ctl, sizeof(Ctl), "control"));
     GC_TRY(ensure(C.bitmap, 4 * (n / 32 + 2), "color bitmap"));
     const int32_t shift = sort_shift(n);

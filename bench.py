@@ -663,10 +663,10 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             # setup, degree sort (2), expand, round kernel, color count (2) per coloring, plus the core
-            # phase's four (index, fill, core rounds, write-back) in deterministic mode; ordered mode
-            # and recoloring: setup, counting pass, round kernel, color count (2) (smallest last adds
-            # the peeling's two: its set-up and the peeling kernel)
-            "gpu_launches": ((5 if mode in ("ordered", "recolor") else 7) + (4 if mode == "det" else 0)
+            # phase's four (index, fill, core rounds, write-back) and the tail phase's cluster launch in
+            # deterministic mode; ordered mode and recoloring: setup, counting pass, round kernel,
+            # color count (2) (smallest last adds the peeling's two: its set-up and the peeling kernel)
+            "gpu_launches": ((5 if mode in ("ordered", "recolor") else 7) + (5 if mode == "det" else 0)
                              + (2 if args.priority == "sl" else 0)) * args.steps,
             "clocks": clk,
             **({"batched": batched} if batched is not None else {}),

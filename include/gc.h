@@ -135,7 +135,11 @@ typedef struct gc_options {
                                   (their rows are rebuilt once, at the hand-over); 0 = min(nnz, 2^27).  Above
                                   2^27 it is clamped.  Only a graph with more entries than this counts its
                                   worklists' entries every round to find the hand-over */
-    int32_t reserved[4];
+    int32_t tail_vertices;     /* deterministic mode, after the core phase: once the worklist has at most this
+                                  many vertices, the remaining rounds run on one thread-block cluster
+                                  (same results).  0 = 384; at most what the cluster holds (4,096 with
+                                  16 blocks, 2,048 with 8), larger values are clamped; < 0 = never */
+    int32_t reserved[3];
 } gc_options;
 
 /* Optional run statistics (gc_color_ex / gc_color_batch_ex).  The caller may provide arrays

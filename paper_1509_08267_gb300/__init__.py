@@ -62,7 +62,8 @@ class _Options(ctypes.Structure):
                 ("chunk", ctypes.c_int32), ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("spin_limit_ns", ctypes.c_int64), ("flags", ctypes.c_uint32), ("partitions", ctypes.c_int32),
                 ("priority", ctypes.c_int32), ("core_vertices", ctypes.c_int32),
-                ("core_entries", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("core_entries", ctypes.c_int32), ("tail_vertices", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class _Stats(ctypes.Structure):
@@ -208,6 +209,7 @@ class Options:
     priority: int = 0
     core_vertices: int = 0
     core_entries: int = 0
+    tail_vertices: int = 0
 
     def _c(self, stream) -> _Options:
         o = _Options()
@@ -223,6 +225,7 @@ class Options:
         o.priority = self.priority
         o.core_vertices = self.core_vertices
         o.core_entries = self.core_entries
+        o.tail_vertices = self.tail_vertices
         return o
 
 

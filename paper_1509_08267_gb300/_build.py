@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 SO = os.path.join(PKG, "libgc.so")
-SOURCES = ["gc_kernels.cu", "gc_core.cu", "gc_api.cu", "gc_server.cu", "gc_noalloc.cu"]
+SOURCES = ["gc_kernels.cu", "gc_core.cu", "gc_tail.cu", "gc_api.cu", "gc_server.cu", "gc_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

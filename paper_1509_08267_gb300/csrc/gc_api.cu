@@ -89,6 +89,7 @@ struct Ctl {
     int32_t core_go, pad3;
     alignas(16) unsigned core_cnt[12];  // three sets of four, each read with one 16-byte load
     unsigned core_m[4];
+    unsigned tail_ctl[4];  // tail phase: handed over, first round
     GridBar bar;
 };
 static_assert(offsetof(Ctl, bar) % 128 == 0, "barrier alignment");
@@ -109,6 +110,7 @@ struct Context {
     Buf core_rec, core_cex, core_c8, core_fbits, core_items, core_active, core_log, core_pool;
     Buf st_cur, st_work, st_next, st_lost;  // gc_det_round staging
     int32_t core_max_v = 0;  // largest core the round kernel's shared memory holds (-1: none)
+    int32_t tail_nc = 0;     // blocks of the tail phase's cluster (-1: no cluster launch possible)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // host adjacency arrays are uploaded on copy_stream while the set-up runs on the call's stream;
     // ev_before orders the upload after earlier work, ev_colidx marks it done
@@ -574,6 +576,19 @@ static int run(Context &C, const Problem &pb, int mode, uint64_t seed, const gc_
             P.core_max = static_cast<int32_t>(M);
             P.core_emax = E;
             P.core_go = &ctl->core_go;
+            // tail phase: the last rounds on one cluster once at most tail_max vertices remain
+            Q.tail = ctl->tail_ctl;
+            const int32_t tail_opt = opt ? opt->tail_vertices : 0;
+            if (tail_opt >= 0) {
+                if (C.tail_nc == 0) {
+                    const int32_t t = tail_cluster_size();
+                    C.tail_nc = t > 0 ? t : -1;
+                }
+                if (C.tail_nc > 0) {
+                    Q.tail_nc = C.tail_nc;
+                    Q.tail_max = std::min(kTailOwned * C.tail_nc, tail_opt > 0 ? tail_opt : kTailDefault);
+                }
+            }
         }
     }
     P.chunk0 = C.chunk0.as<int4>();

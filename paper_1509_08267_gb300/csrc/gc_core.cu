@@ -32,8 +32,9 @@
 // log and, if it lost, its pieces into the next round's list; one grid barrier.
 //
 // Kernels: core_index_kernel (local ids, records, initial colors), core_fill_kernel (the rows),
-// core_round_kernel (one persistent cooperative launch with one block per SM running every
-// remaining round), core_writeback_kernel (final colors back into the state words).
+// core_round_kernel (one persistent cooperative launch with one block per SM running the rounds
+// until the worklist is small enough for the tail phase, gc_tail.cu, or empty),
+// core_writeback_kernel (final colors back into the state words).
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -71,9 +72,6 @@ struct Shared {
     __device__ __forceinline__ unsigned final_bit(uint32_t v) const { return (fin[v >> 5] >> (v & 31)) & 1u; }
 };
 
-__device__ __forceinline__ unsigned *core_rec(const CoreParams &Q, int64_t v) {
-    return Q.rec + static_cast<size_t>(v) * kCoreRecWords;
-}
 
 // Worklist of the hand-over round R0 as the round kernel left it.
 struct HandOver {
@@ -294,37 +292,6 @@ __global__ void __launch_bounds__(kFillThreads) core_fill_kernel(RoundParams P, 
     }
 }
 
-// Least color >= start absent from the neighbours of global vertex V in C_r (warp-cooperative, full
-// CSR row): a final neighbour's color from its state word, a core neighbour's from cex.  Used when
-// the 512-color window of a vertex is full.
-template <bool BATCH>
-__device__ int32_t core_mex_from(const RoundParams &P, const uint64_t *col_r0, int32_t V, const int32_t *cex_cur,
-                                 unsigned *win, int lane, int32_t start) {
-    const Row r = load_row<BATCH>(P, V);
-    for (int32_t base = start;; base += 32 * kAccWords) {
-        if (lane < kAccWords) win[lane] = 0;
-        __syncwarp();
-        for (int64_t j = r.b + lane; j < r.e; j += 32) {
-            const int32_t ul = __ldg(P.colidx + j);
-            if (static_cast<uint32_t>(ul) >= static_cast<uint32_t>(r.ng)) continue;
-            const uint64_t st = __ldcg(col_r0 + r.vbase + ul);
-            const int32_t c = (final_of(st) ? color_of(st) : __ldcg(cex_cur + __ldcg(P.items + r.vbase + ul))) - base;
-            if (static_cast<unsigned>(c) < 32u * kAccWords) atomicOr(&win[c >> 5], 1u << (c & 31));
-        }
-        __syncwarp();
-        int32_t res = -1;
-#pragma unroll 1
-        for (int w = 0; w < kAccWords; ++w) {
-            const unsigned x = win[w];
-            if (~x) {
-                res = base + 32 * w + __ffs(~x) - 1;
-                break;
-            }
-        }
-        __syncwarp();
-        if (res >= 0) return res;
-    }
-}
 
 // Shared copy of the colors and FINAL bits of [0, m) (16-byte loads; the buffers hold a multiple of
 // 16 that exceeds m), then the sentinel at m.  Ends with a block barrier.
@@ -829,6 +796,15 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
                     set_error(P.err, GC_ERR_NO_CONVERGENCE, pass, 0);
                 break;
             }
+            // few enough for the tail phase (one cluster runs the remaining rounds): every block
+            // reads the same count, so all leave here
+            if (pass > R0 && nv <= static_cast<unsigned>(Q.tail_max)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    Q.tail[1] = static_cast<unsigned>(pass);
+                    Q.tail[0] = 1u;
+                }
+                break;
+            }
             if (blockIdx.x == 0 && threadIdx.x < 4) Q.cnt[4 * ((pass + 2) % 3) + threadIdx.x] = 0u;
             CORE_PROF(0, atomicMin);
 #ifdef GC_CORE_PROFILE
@@ -962,6 +938,8 @@ cudaError_t launch_core(const RoundParams &P, const CoreParams &Q, bool batch, c
     cudaMemcpyToSymbolAsync(g_core_prof, h_prof, sizeof h_prof, 0, cudaMemcpyHostToDevice, s);
 #endif
     e = cudaLaunchCooperativeKernel(round_fn, dim3(sms), dim3(kCoreThreads), args, smem, s);
+    if (e != cudaSuccess) return e;
+    e = launch_tail(P, Q, batch, s);
     if (e != cudaSuccess) return e;
 #ifdef GC_CORE_PROFILE
     cudaMemcpyFromSymbolAsync(h_prof, g_core_prof, sizeof h_prof, 0, cudaMemcpyDeviceToHost, s);

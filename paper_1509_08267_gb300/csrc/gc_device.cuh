@@ -418,5 +418,46 @@ __device__ __forceinline__ void flush_stats(const RoundParams &P, int pass, unsi
     }
 }
 
+
+// ------------------------------------------------------------------------------------------
+// core phase (gc_core.cu) and its tail (gc_tail.cu)
+
+// Record of core vertex v: kCoreRecWords words (layout in gc_internal.h).
+__device__ __forceinline__ unsigned *core_rec(const CoreParams &Q, int64_t v) {
+    return Q.rec + static_cast<size_t>(v) * kCoreRecWords;
+}
+
+// Least color >= start absent from the neighbours of global vertex V in C_r (warp-cooperative, full
+// CSR row): a final neighbour's color from its state word, a core neighbour's from cex.  Used when
+// the 512-color window of a vertex is full.
+template <bool BATCH>
+__device__ int32_t core_mex_from(const RoundParams &P, const uint64_t *col_r0, int32_t V, const int32_t *cex_cur,
+                                 unsigned *win, int lane, int32_t start) {
+    const Row r = load_row<BATCH>(P, V);
+    for (int32_t base = start;; base += 32 * kAccWords) {
+        if (lane < kAccWords) win[lane] = 0;
+        __syncwarp();
+        for (int64_t j = r.b + lane; j < r.e; j += 32) {
+            const int32_t ul = __ldg(P.colidx + j);
+            if (static_cast<uint32_t>(ul) >= static_cast<uint32_t>(r.ng)) continue;
+            const uint64_t st = __ldcg(col_r0 + r.vbase + ul);
+            const int32_t c = (final_of(st) ? color_of(st) : __ldcg(cex_cur + __ldcg(P.items + r.vbase + ul))) - base;
+            if (static_cast<unsigned>(c) < 32u * kAccWords) atomicOr(&win[c >> 5], 1u << (c & 31));
+        }
+        __syncwarp();
+        int32_t res = -1;
+#pragma unroll 1
+        for (int w = 0; w < kAccWords; ++w) {
+            const unsigned x = win[w];
+            if (~x) {
+                res = base + 32 * w + __ffs(~x) - 1;
+                break;
+            }
+        }
+        __syncwarp();
+        if (res >= 0) return res;
+    }
+}
+
 }  // namespace
 }  // namespace gc

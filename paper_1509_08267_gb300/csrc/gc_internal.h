@@ -164,6 +164,17 @@ constexpr int kCoreRecWords = 64;
 constexpr int kCoreFlag = 16, kCoreDone = 17;
 constexpr int kCoreOffLo = 48, kCoreOffHi = 49, kCoreDeg = 50, kCoreGid = 51, kCoreFill = 52, kCoreG = 53;
 constexpr int kCoreListLo = 54, kCoreListHi = 55, kCoreListLen = 56, kCorePcBeg = 57, kCorePcEnd = 58;
+constexpr int kCoreTail = 59;  // the vertex's tail id (tail phase)
+// Tail phase (gc_tail.cu).  Once the core's worklist has at most tail_max vertices, one thread-block
+// cluster of tail_nc blocks runs the remaining rounds: the worklist vertices get tail ids 0..k-1 in
+// key order, every block keeps all k colors in shared memory and owns the rows (bitmaps over the
+// tail ids) of the vertices t with t % tail_nc equal to its rank, and new colors are stored into
+// every block's copy through distributed shared memory.  kTailOwned rows per block.  Default
+// threshold kTailDefault: a cluster has a tenth of the GPU's SMs, so the tail pays off only once a
+// round's work is small (on R-MAT scale 22: 0.3 ms saved at 256-512 vertices, less at 768, a loss
+// from 1,024).
+constexpr int kTailOwned = 256;
+constexpr int kTailDefault = 384;
 struct CoreParams {
     int32_t max_v;        // vertex capacity M (shared memory holds M 8-bit colors and M FINAL bits; a
                           // multiple of 16)
@@ -180,6 +191,9 @@ struct CoreParams {
     unsigned long long *bump;  // pool allocation counter
     unsigned *cnt;        // [3][4] per-round counters: vertices finished (log entries), losers, active pieces
     unsigned *m;          // [4]: larger vertices numbered by the index kernel, m, pieces
+    int32_t tail_max;     // tail phase once the worklist has at most this many vertices (0: never)
+    int32_t tail_nc;      // blocks of the tail's cluster (tail_max <= kTailOwned * tail_nc)
+    unsigned *tail;       // [4]: 1 when the core handed over to the tail, the tail's first round
 };
 
 // Launch wrappers (gc_kernels.cu).  All return the launch's cudaError_t.
@@ -252,6 +266,10 @@ cudaError_t launch_det_round_block(int32_t n, const int32_t *rowptr, const int32
 // col1.  core_max_vertices: the largest M the shared memory of one block per SM allows.
 int32_t core_max_vertices();
 cudaError_t launch_core(const RoundParams &P, const CoreParams &Q, bool batch, cudaStream_t s);
+// Tail phase: the largest cluster (16 or 8 blocks) the tail kernel can run as, 0 if none; the launch
+// (every block returns at once unless the core handed over).
+int32_t tail_cluster_size();
+cudaError_t launch_tail(const RoundParams &P, const CoreParams &Q, bool batch, cudaStream_t s);
 
 }  // namespace gc
 

@@ -22,14 +22,16 @@ def run_det(gc, g, seed, options=None, stats=False):
 
 
 def core_variants(gc, g):
-    """The library default (small graphs run every round in the shared-memory core phase), the
-    regular round kernel alone, and hand-overs to the core phase part-way through the run, by a
-    vertex cap and by an entry cap (which makes the rounds count their worklists' entries)."""
-    out = [gc.Options(), gc.Options(core_vertices=-1)]
+    """The library default (small graphs run round 1 in the shared-memory core phase and the rest
+    in the cluster's tail phase), the regular round kernel alone, the core phase without the tail,
+    and hand-overs part-way through the run: to the core by a vertex cap and by an entry cap (which
+    makes the rounds count their worklists' entries), and from the core to the tail."""
+    out = [gc.Options(), gc.Options(core_vertices=-1), gc.Options(tail_vertices=-1), gc.Options(tail_vertices=4096)]
     for cap in (max(1, g.n // 10), max(1, g.n // 3)):
         out.append(gc.Options(core_vertices=cap))
     if g.nnz > 8:
         out.append(gc.Options(core_entries=max(1, g.nnz // 8)))
+    out.append(gc.Options(core_vertices=max(1, g.n // 3), tail_vertices=max(1, g.n // 20)))
     return out
 
 

@@ -82,6 +82,22 @@ def test_batch_det_matches_oracle_per_graph(gclib):
         assert nc[i] == ref.ncolors and rd[i] == ref.rounds, (i, nc[i], ref.ncolors, rd[i], ref.rounds)
 
 
+@pytest.mark.parametrize("opt", [dict(tail_vertices=-1), dict(tail_vertices=4096), dict(core_vertices=-1),
+                                 dict(core_vertices=3000, tail_vertices=200)])
+def test_batch_det_phases_match_oracle(gclib, opt):
+    # the batch through the round kernel, the core phase and the tail phase, with the hand-overs at
+    # other points than the default's
+    gs = _mixed_graphs()
+    b = gg.pack(gs)
+    colors, nc, rd = gclib.color_batch(_dev(b.vtx_off), _dev(b.edge_off), _dev(b.rowptr), _dev(b.colidx), "det", 7,
+                                       options=gclib.Options(**opt))
+    colors = colors.cpu().numpy()
+    for i, g in enumerate(gs):
+        ref = oracle.det(g, 7)
+        np.testing.assert_array_equal(colors[b.vtx_off[i]:b.vtx_off[i + 1]], ref.colors, err_msg=f"{opt} graph {i}")
+        assert nc[i] == ref.ncolors and rd[i] == ref.rounds, (opt, i)
+
+
 def test_batch_round_statistics_are_sums_over_graphs(gclib):
     # the batch's worklist in round r is the union of the graphs' worklists in round r
     gs = _mixed_graphs()

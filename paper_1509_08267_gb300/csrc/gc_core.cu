@@ -95,15 +95,28 @@ __device__ __forceinline__ HandOver hand_over(const RoundParams &P) {
     return h;
 }
 
+// Pool space for the rows of a warp's vertices (lanes with `take`, len entries each): one
+// reservation per warp (one counter shared by the whole grid: an atomic per vertex would queue).
+__device__ __forceinline__ unsigned long long core_reserve(const CoreParams &Q, bool take, int32_t len, int lane) {
+    unsigned long long x = take ? static_cast<unsigned long long>(len) : 0ull, incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    unsigned long long b = 0;
+    if (lane == 31 && incl) b = atomicAdd(Q.bump, incl);
+    return __shfl_sync(kFull, b, 31) + incl - x;
+}
+
 // Record of core vertex `local` (global id V, graph g): its list at hand-over (`list`, len entries),
-// its degree, len entries of the pool for its row, its color in both buffers and the window of
-// final colors found so far (`fin_src`: the round kernel's slot, or none).
+// its degree, the pool space `off` (len entries) for its row, its color in both buffers and the
+// window of final colors found so far (`fin_src`: the round kernel's slot, or none).
 __device__ void core_init_vertex(const RoundParams &P, const CoreParams &Q, int32_t local, int32_t V, int32_t g,
                                  const int32_t *list, int32_t len, int32_t deg, const uint64_t *colc,
-                                 const unsigned *fin_src) {
+                                 const unsigned *fin_src, unsigned long long off) {
     P.items[V] = local;  // local id of V (the set-up scratch is free once the rounds run)
     unsigned *rec = core_rec(Q, local);
-    const unsigned long long off = atomicAdd(Q.bump, static_cast<unsigned long long>(len));
     const int32_t c = color_of(__ldcg(colc + V));
     Q.cex[local] = c;
     Q.cex[Q.max_v + local] = c;
@@ -138,11 +151,18 @@ __global__ void core_index_kernel(RoundParams P, CoreParams Q) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    for (int64_t i = t0; i < h.nsmall; i += stride) {
-        const int32_t V = __ldcg(h.smallc + i);
-        const Row r = load_row<BATCH>(P, V);
-        const int32_t deg = static_cast<int32_t>(r.e - r.b);
-        core_init_vertex(P, Q, static_cast<int32_t>(i), V, r.g, P.colidx + r.b, deg, deg, h.colc, nullptr);
+    for (int64_t base = t0 & ~int64_t{31}; base < h.nsmall; base += stride) {
+        const int64_t i = base + lane;
+        const bool in = i < h.nsmall;
+        int32_t V = 0, deg = 0;
+        Row r{};
+        if (in) {
+            V = __ldcg(h.smallc + i);
+            r = load_row<BATCH>(P, V);
+            deg = static_cast<int32_t>(r.e - r.b);
+        }
+        const unsigned long long off = core_reserve(Q, in, deg, lane);
+        if (in) core_init_vertex(P, Q, static_cast<int32_t>(i), V, r.g, P.colidx + r.b, deg, deg, h.colc, nullptr, off);
     }
     for (int64_t base = t0 & ~int64_t{31}; base < h.nchunks; base += stride) {
         const int64_t i = base + lane;
@@ -157,12 +177,13 @@ __global__ void core_index_kernel(RoundParams P, CoreParams Q) {
         unsigned b = 0;
         if (lane == 0) b = atomicAdd(Q.m, static_cast<unsigned>(__popc(mk)));
         b = __shfl_sync(kFull, b, 0);
+        const unsigned *a = P.acc + static_cast<size_t>(d.slotf & kItemSlot) * kAccStride;
+        const int32_t len = first ? static_cast<int32_t>(__ldcg(a + kAccLen)) : 0;
+        const unsigned long long off = core_reserve(Q, first, len, lane);
         if (!first) continue;
         const int32_t local = static_cast<int32_t>(h.nsmall + b + __popc(mk & lanemask_lt()));
-        const unsigned *a = P.acc + static_cast<size_t>(d.slotf & kItemSlot) * kAccStride;
-        const int32_t len = static_cast<int32_t>(__ldcg(a + kAccLen));
         const int32_t g = BATCH ? __ldg(P.vg + d.V) : 0;
-        core_init_vertex(P, Q, local, d.V, g, d.list, len, d.deg, h.colc, a + kAccFin);
+        core_init_vertex(P, Q, local, d.V, g, d.list, len, d.deg, h.colc, a + kAccFin, off);
     }
 }
 

@@ -153,6 +153,28 @@ def recorded_traffic(workload, mode):
     return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
 
 
+def write_round_table(path, workload, mode, st, rounds, kernel_ms):
+    """Per-round table of one statistics run (GC_FLAG_STATS: |W_r|, the degree sum, the entries read
+    and the round's duration from its end timestamps; the timestamps add ~0.5 ms to the run)."""
+    rn = st.round_ns[:rounds] / 1e3
+    lines = [f"# Per round: {mode} coloring of {workload} ({rounds} rounds; {kernel_ms:.2f} ms of kernels "
+             "with statistics on)", "",
+             "| Rounds | us | entries read | worklist at the first | G entries/s |", "|---|---|---|---|---|"]
+    edges = [0, 1, 3, 14, 15, 30, 100, 200, 270, rounds]
+    for a, b in zip(edges[:-1], edges[1:]):
+        if a >= min(b, rounds):
+            continue
+        us, rd = rn[a:b].sum(), int(st.round_reads[a:b].sum())
+        lines.append(f"| {a + 1}-{min(b, rounds)} | {us:.1f} | {rd} | {int(st.wl_size[a])} | "
+                     f"{rd / max(us, 1e-9) / 1e3:.1f} |")
+    lines += ["", "| Round | us | worklist | degree sum | entries read |", "|---|---|---|---|---|"]
+    for r in range(rounds):
+        lines.append(f"| {r + 1} | {rn[r]:.1f} | {int(st.wl_size[r])} | {int(st.wl_degsum[r])} | "
+                     f"{int(st.round_reads[r])} |")
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+
 def reduce_max(value, world, device=None):
     """The largest of the ranks' values (timing is taken as the slowest rank's); the value itself on
     one rank.  device: where the reduction tensor lives (the rank's GPU under NCCL, CPU under gloo)."""
@@ -474,6 +496,8 @@ def main():
     ap.add_argument("--batch-graphs", type=int, default=256,
                     help="graphs of the batched object of the default line (0: leave it out)")
     ap.add_argument("--no-served", action="store_true", help="leave the served object out of the default line")
+    ap.add_argument("--round-stats", default=None,
+                    help="write the per-round table of the warm-up's statistics run to this file")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -676,6 +700,8 @@ def main():
             "max_degree": g.max_degree, "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)
+        if args.round_stats and r0.stats is not None:
+            write_round_table(args.round_stats, args.workload, mode, r0.stats, r0.rounds, r0.stats.kernel_ms)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

@@ -73,6 +73,12 @@ struct Shared {
 };
 
 
+// The fill computes the core's first round (R0) as it rebuilds the rows when every color of rounds
+// R0 and R0 + 1 is below 64 (colors of round r are at most r - 1): each row's 64-bit window of
+// neighbour colors and its conflict flag go into the vertex's record, and the first core round only
+// finishes the vertices.
+__device__ __forceinline__ bool core_fused(int R0) { return R0 <= 63; }
+
 // Worklist of the hand-over round R0 as the round kernel left it.
 struct HandOver {
     int R0;
@@ -191,7 +197,9 @@ __global__ void core_index_kernel(RoundParams P, CoreParams Q) {
 // round-R0 decomposition).  Every entry of the vertex's current list is read once: a final
 // neighbour's color goes into the window of final colors, any other neighbour (a core vertex) is
 // appended to the vertex's row as its local id with the key-order bit.  Entries are checked as in
-// the round kernel (range, self-loop).
+// the round kernel (range, self-loop).  When the first round is fused (core_fused), every
+// neighbour's color also goes into the record's round window and a smaller-key neighbour with the
+// vertex's color sets its conflict flag.
 template <bool BATCH>
 __global__ void __launch_bounds__(kFillThreads) core_fill_kernel(RoundParams P, CoreParams Q) {
     __shared__ unsigned s_fin[kFillThreads / 32][kAccWords];
@@ -235,6 +243,10 @@ __global__ void __launch_bounds__(kFillThreads) core_fill_kernel(RoundParams P, 
         if (lane < kAccWords) wfin[lane] = 0u;
         __syncwarp();
         uint64_t flo = 0;
+        const bool fused = core_fused(h.R0);
+        const int32_t cv = fused ? color_of(__ldcg(h.colc + V)) : -1;  // C_R0 of the vertex
+        uint64_t rlo = 0;         // fused: colors of the core neighbours (all below 64)
+        unsigned conflict = 0;    // fused: a smaller-key core neighbour has the vertex's color
         for (int64_t j0 = lb; j0 < le; j0 += 32 * kFillPer) {
             int32_t ul[kFillPer];
             uint64_t st[kFillPer];
@@ -283,6 +295,11 @@ __global__ void __launch_bounds__(kFillThreads) core_fill_kernel(RoundParams P, 
                                                   static_cast<uint32_t>(r.lv), P, V);
                         }
                         ev[q] = static_cast<uint32_t>(loc[q]) | (smaller ? kCoreSmaller : 0u);
+                        if (fused) {
+                            const int32_t c = color_of(st[q]);
+                            rlo |= 1ull << (c & 63);
+                            conflict |= static_cast<unsigned>(smaller && c == cv);
+                        }
                     } else {
                         // every vertex that is not final is on the worklist; anything else is a bug
                         set_error(P.err, GC_ERR_INVALID_GRAPH, V, j);
@@ -309,6 +326,16 @@ __global__ void __launch_bounds__(kFillThreads) core_fill_kernel(RoundParams P, 
         __syncwarp();
         const unsigned fw = lane == 0 ? f0 : lane == 1 ? f1 : (lane < kAccWords ? wfin[lane] : 0u);
         if (lane < kAccWords && fw) atomicOr(rec + kAccFin + lane, fw);
+        if (fused) {
+            const unsigned r0 = __reduce_or_sync(kFull, static_cast<unsigned>(rlo));
+            const unsigned r1 = __reduce_or_sync(kFull, static_cast<unsigned>(rlo >> 32));
+            const bool lose = __any_sync(kFull, conflict != 0u);
+            if (lane == 0) {
+                if (r0) atomicOr(rec, r0);
+                if (r1) atomicOr(rec + 1, r1);
+                if (lose) atomicOr(rec + kCoreFlag, 1u);
+            }
+        }
         __syncwarp();
     }
 }
@@ -538,6 +565,51 @@ __device__ __forceinline__ void flush_pending(unsigned pend, unsigned pend_pb, u
         const unsigned b0 = __shfl_sync(kFull, pb, l), k0 = __shfl_sync(kFull, npc, l);
         const unsigned at = ab + __shfl_sync(kFull, incl, l) - k0;
         for (unsigned k = lane; k < k0; k += 32) act_next[at + k] = static_cast<int32_t>(b0 + k);
+    }
+}
+
+// The first core round when the fill computed it (core_fused): a lane per vertex finishes it from
+// its record -- a loser takes the least color absent from the round window and the final window
+// (both below 64), a winner becomes FINAL -- and clears the record's round part; the warp flushes
+// its batch as core_round_warp does.
+template <bool BATCH>
+__device__ void core_first_round(const RoundParams &P, const CoreParams &Q, int32_t m, int pass, unsigned *cn,
+                                 int lane, unsigned &st_read, unsigned &st_deg, unsigned &st_cnt) {
+    const size_t cur = static_cast<size_t>(pass & 1), nxt = cur ^ 1u;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < static_cast<unsigned>(m);
+         base += stride) {
+        const unsigned v = base + lane;
+        const bool in = v < static_cast<unsigned>(m);
+        unsigned pend = 0, pend_pb = 0, pend_np = 0;
+        if (in) {
+            unsigned *rec = core_rec(Q, v);
+            const uint4 w = ldcg4(rec);
+            const uint4 f = ldcg4(rec + kAccFin);
+            const bool lose = __ldcg(rec + kCoreFlag) != 0u;
+            const int32_t cv = __ldcg(Q.cex + cur * Q.max_v + v);
+            const uint64_t win = static_cast<uint64_t>(w.x | f.x) | (static_cast<uint64_t>(w.y | f.y) << 32);
+            const int32_t nc = lose ? __ffsll(static_cast<long long>(~win)) - 1 : cv;
+            const unsigned n8 = sat8(nc);
+            Q.cex[nxt * Q.max_v + v] = nc;
+            Q.c8[nxt * Q.max_v + v] = static_cast<uint8_t>(n8);
+            if (!lose) atomicOr(Q.fbits + (v >> 5), 1u << (v & 31));
+            const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int c = 0; c < 20; c += 4) stcg4(rec + c, z);
+            const uint4 rr = ldcg4(rec + kCoreOffLo);  // offset lo, offset hi, degree, global id
+            st_read += __ldcg(rec + kCoreFill);
+            st_deg += rr.z;
+            st_cnt += 1;
+            if constexpr (BATCH) {
+                if (lose) note_graph_round(P, static_cast<int32_t>(__ldcg(rec + kCoreG)), pass + 1);
+            }
+            pend = v | (n8 << 18) | (lose ? kPendLose : 0u);
+            pend_pb = __ldcg(rec + kCorePcBeg);
+            pend_np = __ldcg(rec + kCorePcEnd) - pend_pb;
+        }
+        const unsigned npend = static_cast<unsigned>(__popc(__ballot_sync(kFull, in)));
+        flush_pending(pend, pend_pb, pend_np, npend, cn, Q.log + nxt * Q.max_v, Q.active + nxt * Q.max_pieces, lane);
     }
 }
 
@@ -847,9 +919,12 @@ __global__ void __launch_bounds__(kCoreThreads, 1) core_round_kernel(RoundParams
             const int32_t *list = pass == R0 ? nullptr : Q.active + static_cast<size_t>(pass & 1) * Q.max_pieces;
             const unsigned nact = pass == R0 ? npieces : cc.z;
             // the round's grab counter: word 3 of its counter set (cleared two rounds ahead like the rest)
-            core_round_warp<BATCH>(P, Q, S, cex_cur, list, nact, m, nv, pass, h.colc, cn,
-                                   Q.cnt + 4 * (pass % 3) + 3, gw, nw, lane, s_win[wib], s_fin[wib], st_read, st_deg,
-                                   st_cnt);
+            if (pass == R0 && core_fused(R0))
+                core_first_round<BATCH>(P, Q, m, pass, cn, lane, st_read, st_deg, st_cnt);
+            else
+                core_round_warp<BATCH>(P, Q, S, cex_cur, list, nact, m, nv, pass, h.colc, cn,
+                                       Q.cnt + 4 * (pass % 3) + 3, gw, nw, lane, s_win[wib], s_fin[wib], st_read,
+                                       st_deg, st_cnt);
 #ifdef GC_CORE_PROFILE
             __syncthreads();
             CORE_PROF(2, atomicMin);

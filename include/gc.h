@@ -333,7 +333,11 @@ typedef struct gc_server_config {
                                 (the other mode's pool is allocated by its first request) */
     int64_t spin_limit_ns;   /* grid-barrier wait limit of the round launches; 0 = 1e9 */
     int32_t device;          /* CUDA device ordinal; -1 = current */
-    int32_t reserved[7];
+    int32_t solo_entries;    /* a request with at least this many adjacency entries fills the GPU by itself:
+                                it skips the pool and is colored alone by the worker (as gc_color_ex
+                                does, core and tail phases included) between launches of the batch;
+                                0 = 2^24; < 0 = never (every request joins the batch) */
+    int32_t reserved[6];
 } gc_server_config;
 
 struct gc_server_stats {

@@ -78,7 +78,7 @@ class _Stats(ctypes.Structure):
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("pool_vertices", ctypes.c_int64), ("pool_entries", ctypes.c_int64),
                 ("max_requests", ctypes.c_int32), ("mode", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64),
-                ("device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("device", ctypes.c_int32), ("solo_entries", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -413,7 +413,7 @@ class Server:
     request."""
 
     def __init__(self, pool_vertices: int, pool_entries: int, max_requests: int = 0, mode="det", seed: int = 0,
-                 device: int = -1, spin_limit_ns: int = 0):
+                 device: int = -1, spin_limit_ns: int = 0, solo_entries: int = 0):
         lib = load()
         cfg = _ServerConfig()
         cfg.pool_vertices = pool_vertices
@@ -422,6 +422,7 @@ class Server:
         cfg.mode = _mode(mode)
         cfg.spin_limit_ns = spin_limit_ns
         cfg.device = device
+        cfg.solo_entries = solo_entries
         h = ctypes.c_void_p()
         _check(lib.gc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

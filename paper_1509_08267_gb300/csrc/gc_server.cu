@@ -7,7 +7,9 @@
 // entry and work-item ranges), joining them to the running batch at the next round: their first
 // round is the batch's next round, and a request's own round count is measured from there.
 // Because every graph's deterministic rounds read only its own previous colors, a request's
-// colors do not depend on which other requests share the launch.
+// colors do not depend on which other requests share the launch.  A request large enough to fill
+// the GPU by itself (cfg.solo_entries) skips the pool: between launches the worker colors it alone
+// the way gc_color_ex does, with the core and tail phases that the batch's shared rounds cannot run.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -103,6 +105,7 @@ struct Request {
     int32_t slot = -1, join = 0;
     int64_t vbase = 0, ebase = 0, rbase = 0;
     bool staged = false;  // its CSR was copied into the pool at submit
+    void *dbuf = nullptr;  // colored alone: its row offsets, entries and colors on the device
 };
 
 struct DevBuf {
@@ -164,6 +167,9 @@ struct gc_server {
     std::mutex copy_mu;
     std::mutex create_mu;  // engine allocation
     gc::Engine eng[2];     // [0] deterministic, [1] in-place
+    std::deque<gc::Request *> solo;  // requests colored alone, in submission order
+    int64_t solo_min = 0;            // adjacency entries from which a request is colored alone
+    cudaMemPool_t solo_pool = nullptr;  // their device copies; freed memory stays in the pool
     std::unordered_map<uint64_t, std::unique_ptr<gc::Request>> reqs;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -483,6 +489,13 @@ void fail_all(gc_server *s, int code, const std::string &msg) {
         }
         E.queue.clear();
     }
+    for (Request *r : s->solo) {
+        if (r->dbuf) cudaFree(r->dbuf);
+        r->dbuf = nullptr;
+        r->state = kDone;
+        r->status = code;
+    }
+    s->solo.clear();
     s->cv_done.notify_all();
 }
 
@@ -540,15 +553,65 @@ bool engine_step(gc_server *s, Engine &E, std::vector<Request *> &adm, bool queu
     return true;
 }
 
+// A request that fills the GPU by itself, colored alone as gc_color_ex colors it (core and tail
+// phases included) on the server's stream, between launches of the batch.
+// Its CSR waits on the device (copied at submit).
+void color_solo(gc_server *s, Request *r) {
+    gc_options o{};
+    o.stream = s->stream;
+    o.spin_limit_ns = s->cfg.spin_limit_ns;
+    r->colors.resize(static_cast<size_t>(r->n));
+    int32_t nc = 0, rd = 0;
+    int32_t *d_rp = static_cast<int32_t *>(r->dbuf);
+    int32_t *d_ci = d_rp + (r->n + 1);
+    int32_t *d_col = d_ci + r->m;
+    int st = gc_color_ex(r->n, d_rp, r->m ? d_ci : nullptr, r->mode, r->seed, r->n ? d_col : nullptr, &nc, &rd, &o,
+                         nullptr);
+    cudaError_t e = cudaSuccess;
+    if (st == GC_OK && r->n)
+        e = cudaMemcpyAsync(r->colors.data(), d_col, 4 * static_cast<size_t>(r->n), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaFreeAsync(r->dbuf, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (st == GC_OK) st = GC_ERR_CUDA;
+    }
+    r->dbuf = nullptr;
+    const double t = now_s();
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->status = st;
+    r->ncolors = nc;
+    r->rounds = rd;
+    r->state = kDone;
+    r->t_done = t;
+    if (st == GC_OK) {
+        s->completed += 1;
+        s->v_done += r->n;
+        s->e_done += r->m / 2;
+        s->latencies.push_back((r->t_done - r->t_submit) * 1e3);
+    } else if (st == GC_ERR_INVALID_GRAPH) {
+        s->rejected += 1;
+    } else {
+        s->failed += 1;
+    }
+    s->cv_done.notify_all();
+}
+
 void worker_main(gc_server *s) {
     cudaSetDevice(s->device);
     while (true) {
         std::vector<Request *> adm[2];
         bool active[2] = {false, false}, queued[2] = {false, false};
+        Request *solo = nullptr;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] { return s->stop || s->eng[0].busy() || s->eng[1].busy(); });
-            if (s->stop && !s->eng[0].busy() && !s->eng[1].busy()) break;
+            s->cv_work.wait(lk, [&] { return s->stop || !s->solo.empty() || s->eng[0].busy() || s->eng[1].busy(); });
+            if (s->stop && s->solo.empty() && !s->eng[0].busy() && !s->eng[1].busy()) break;
+            if (!s->solo.empty()) {
+                solo = s->solo.front();
+                s->solo.pop_front();
+                solo->state = kResident;
+            }
             for (int k = 0; k < 2; ++k) {
                 Engine &E = s->eng[k];
                 if (!E.busy()) continue;
@@ -571,6 +634,11 @@ void worker_main(gc_server *s) {
                 active[k] = !E.resident.empty();
                 queued[k] = !E.queue.empty();
             }
+        }
+        if (solo) {
+            const double t0 = now_s();
+            color_solo(s, solo);
+            s->busy += now_s() - t0;
         }
         bool ok = true;
         for (int k = 0; k < 2 && ok; ++k)
@@ -608,8 +676,20 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
     auto s = std::make_unique<gc_server>();
     s->cfg = *cfg;
     s->device = dev;
+    s->solo_min = cfg->solo_entries < 0 ? INT64_MAX : (cfg->solo_entries == 0 ? int64_t{1} << 24 : cfg->solo_entries);
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        // the device copies of requests colored alone: memory freed by one stays for the next (a pool
+        // that grew while the worker's kernels ran would stall the submitting thread)
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        e = cudaMemPoolCreate(&s->solo_pool, &props);
+        uint64_t keep = UINT64_MAX;
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(s->solo_pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_last_error(GC_ERR_CUDA, "server streams: %s", cudaGetErrorString(e));
@@ -620,6 +700,7 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
     if (st != GC_OK) {
         cudaStreamDestroy(s->stream);
         cudaStreamDestroy(s->copy_stream);
+        cudaMemPoolDestroy(s->solo_pool);
         return st;
     }
     s->t_create = gc::now_s();
@@ -690,10 +771,11 @@ int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32
                         (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
     cudaGetLastError();
     gc::Request *raw = r.get();
+    const bool solo = m >= s->solo_min;  // fills the GPU by itself: colored alone
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->fatal != GC_OK) return set_last_error(s->fatal, "server stopped: %s", s->fatal_msg.c_str());
-        if (n > E.va.capacity() || m > E.ea.capacity() || r->n_large > E.PI || r->n_chunks > E.PC) {
+        if (!solo && (n > E.va.capacity() || m > E.ea.capacity() || r->n_large > E.PI || r->n_chunks > E.PC)) {
             s->rejected += 1;
             return set_last_error(GC_ERR_OOM, "request (n=%d, nnz=%lld) exceeds the server pool", n,
                                   static_cast<long long>(m));
@@ -701,13 +783,33 @@ int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32
         r->id = s->next_id++;
         r->t_submit = gc::now_s();
         *req_id = r->id;
-        // with nothing queued ahead and room in the pool, the CSR goes straight into the pool
-        raw->staged = E.queue.empty() && gc::reserve(E, raw);
+        // with nothing queued ahead and room in the pool, the CSR goes straight into the pool (a
+        // request colored alone never enters the pool)
+        raw->staged = !solo && E.queue.empty() && gc::reserve(E, raw);
         s->reqs[raw->id] = std::move(r);
         s->submitted += 1;
     }
     cudaError_t e = cudaSuccess;
-    if (raw->staged) {
+    if (solo) {
+        // colored alone: its CSR goes to the device now (stream-ordered allocation) and waits there
+        std::lock_guard<std::mutex> ck(s->copy_mu);
+        const size_t bytes = 4 * (static_cast<size_t>(n) + 1) + 4 * static_cast<size_t>(m) + 4 * static_cast<size_t>(n);
+        e = cudaMallocFromPoolAsync(&raw->dbuf, bytes, s->solo_pool, s->copy_stream);
+        int32_t *d_rp = static_cast<int32_t *>(raw->dbuf);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_rp, raw->rowptr.data(), 4 * (static_cast<size_t>(n) + 1), cudaMemcpyHostToDevice,
+                                s->copy_stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_rp + (n + 1), colidx, 4 * static_cast<size_t>(m),
+                                ci_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
+        if (e != cudaSuccess && raw->dbuf) {
+            cudaFreeAsync(raw->dbuf, s->copy_stream);
+            cudaStreamSynchronize(s->copy_stream);
+            raw->dbuf = nullptr;
+        }
+        std::vector<int32_t>().swap(raw->rowptr);
+    } else if (raw->staged) {
         std::lock_guard<std::mutex> ck(s->copy_mu);
         e = cudaMemcpyAsync(E.rowptr.as<int32_t>() + raw->rbase, raw->rowptr.data(), 4 * (static_cast<size_t>(n) + 1),
                             cudaMemcpyHostToDevice, s->copy_stream);
@@ -728,11 +830,13 @@ int gc_server_submit(gc_server *s, int32_t n, const int32_t *rowptr, const int32
         cudaGetLastError();
         if (raw->staged) gc::unreserve(E, raw);
         raw->state = gc::kDone;
-        raw->status = GC_ERR_CUDA;
-        return set_last_error(GC_ERR_CUDA, "copying the request: %s", cudaGetErrorString(e));
+        raw->status = e == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA;
+        return set_last_error(raw->status, "copying the request: %s", cudaGetErrorString(e));
     }
     if (raw->staged)
         E.staged.push_back(raw);
+    else if (solo)
+        s->solo.push_back(raw);
     else
         E.queue.push_back(raw);
     s->cv_work.notify_one();
@@ -811,6 +915,7 @@ int gc_server_stats(gc_server *s, struct gc_server_stats *out) {
         out->resident += static_cast<int32_t>(E.resident.size());
         out->queued += static_cast<int32_t>(E.queue.size());
     }
+    out->queued += static_cast<int32_t>(s->solo.size());
     return GC_OK;
 }
 
@@ -824,6 +929,7 @@ void gc_server_destroy(gc_server *s) {
         s->cv_work.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
+    if (s->solo_pool) cudaMemPoolDestroy(s->solo_pool);
     if (s->stream) cudaStreamDestroy(s->stream);
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
     delete s;

@@ -148,3 +148,32 @@ def test_server_survives_device_error(gclib):
     ref = oracle.det(g, 7)
     r = gclib.color(g.rowptr, g.colidx, "det", 7)
     np.testing.assert_array_equal(r.colors, ref.colors)
+
+
+def test_server_colors_large_requests_alone(gclib):
+    # requests with at least solo_entries adjacency entries skip the pool and are colored alone
+    # between batch launches (core and tail phases included); the others keep joining the batch;
+    # every result is the one the request would get by itself
+    gs = _graphs()
+    assert any(g.nnz >= 20_000 for g in gs) and any(g.nnz < 20_000 for g in gs)
+    refs = [oracle.det(g, 3) for g in gs]
+    big = gg.workload("er10k")
+    bad = gg.er(3000, 12.0, 4)
+    bad_ci = bad.colidx.copy()
+    bad_ci[7] = bad.n + 5  # neighbour id out of range: found by the solo coloring, reported by poll
+    with gclib.Server(pool_vertices=2_000_000, pool_entries=40_000_000, mode="det", seed=3,
+                      solo_entries=20_000) as srv:
+        ids = [srv.submit(g.rowptr, g.colidx) for g in gs]
+        rin = srv.submit(big.rowptr, big.colidx, mode="inplace", seed=5)
+        rbad = srv.submit(bad.rowptr, bad_ci)
+        for g, ref, rid in zip(gs, refs, ids):
+            colors, nc, rounds = srv.poll(rid, timeout_ms=-1)
+            np.testing.assert_array_equal(colors, ref.colors, err_msg=g.name)
+            assert (nc, rounds) == (ref.ncolors, ref.rounds), g.name
+        c, nc, _ = srv.poll(rin, timeout_ms=-1)
+        assert oracle.count_conflicts(big, c) == 0 and nc == oracle.distinct_colors(c)
+        with pytest.raises(gclib.GCError) as ei:
+            srv.poll(rbad, timeout_ms=-1)
+        assert ei.value.status == gclib.GC_ERR_INVALID_GRAPH
+        st = srv.stats()
+        assert st["completed"] == len(gs) + 1 and st["rejected"] == 1 and st["queued"] == 0

@@ -689,6 +689,18 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out) {
         e = cudaMemPoolCreate(&s->solo_pool, &props);
         uint64_t keep = UINT64_MAX;
         if (e == cudaSuccess) e = cudaMemPoolSetAttribute(s->solo_pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e == cudaSuccess) {
+            // reserve the pool's size up front (a pool's worth of entries and vertices): requests
+            // submitted together keep their copies alive together, and growing the pool while the
+            // worker's kernels run stalls the submitting thread; a reservation that fails is skipped
+            void *p = nullptr;
+            const size_t want = 4 * static_cast<size_t>(cfg->pool_entries) + 12 * static_cast<size_t>(cfg->pool_vertices);
+            if (cudaMallocFromPoolAsync(&p, want, s->solo_pool, s->copy_stream) == cudaSuccess) {
+                cudaFreeAsync(p, s->copy_stream);
+                cudaStreamSynchronize(s->copy_stream);
+            }
+            cudaGetLastError();
+        }
     }
     if (e != cudaSuccess) {
         cudaGetLastError();

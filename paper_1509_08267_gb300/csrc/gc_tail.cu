@@ -79,9 +79,17 @@ __device__ unsigned long long g_tail_prof[16 * 4096];
     if (rank == 0 && threadIdx.x == 0) g_tail_build[k] = global_ns()
 #define TAIL_PROF(k, v) \
     if (rank == 0 && pass - R1 < 4096) g_tail_prof[16 * (pass - R1) + (k)] = (v)
+// clock cycles since the last mark (pc0) into `acc`
+#define TAIL_CLK(acc)                                \
+    {                                                \
+        const unsigned long long c1 = clock64();     \
+        acc += c1 - pc0;                             \
+        pc0 = c1;                                    \
+    }
 #else
 #define TAIL_BUILD(k)
 #define TAIL_PROF(k, v)
+#define TAIL_CLK(acc)
 #endif
 
 // Dynamic shared memory of one block for kt = kTailOwned * blocks tail ids: colors [2][kt], rows
@@ -304,14 +312,6 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(RoundParams P, Co
         }
 #ifdef GC_TAIL_PROFILE
         unsigned long long pc_scan = 0, pc_merge = 0, pc_store = 0, pc0 = 0;
-#define TAIL_CLK(acc)                     \
-    {                                     \
-        const unsigned long long c1 = clock64(); \
-        acc += c1 - pc0;                  \
-        pc0 = c1;                         \
-    }
-#else
-#define TAIL_CLK(acc)
 #endif
         for (unsigned idx = wib; idx < nv; idx += kTailWarps) {
 #ifdef GC_TAIL_PROFILE

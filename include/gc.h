@@ -359,7 +359,10 @@ int gc_server_create(const gc_server_config *cfg, gc_server **out);
 /* Queues one graph (host or device CSR as in gc_color; copied before return).  Non-blocking.
  *   mode   GC_MODE_DETERMINISTIC or GC_MODE_INPLACE (the request's own; see gc_color)
  *   seed   the request's priority seed (see gc_color)
- * GC_ERR_OOM if the graph can never fit a pool (or the mode's pool cannot be allocated);
+ * A request with at least cfg.solo_entries entries is copied to device memory here and colored alone
+ * (it needs no pool space).
+ * GC_ERR_OOM if the graph can never fit a pool (or the mode's pool, or a copy of a request colored
+ * alone, cannot be allocated);
  * GC_ERR_INVALID_GRAPH for malformed row offsets; GC_ERR_INVALID_ARG for an unknown mode.
  * Neighbour ids and self-loops are checked on the device when the request is admitted; a request
  * that fails that check is dropped and its gc_server_poll returns GC_ERR_INVALID_GRAPH. */
